@@ -1,0 +1,349 @@
+"""Pins of the CPU oracle against facts fixed by the paper or by mathematics.
+
+Every test here runs on the CPU (no GPU marker).  Each one is chosen so that
+a plausible slip in the oracle (a dropped term, a wrong sign, a wrong index
+or scale, a transposed operand) fails it.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import analysis, cycle, gradient, hierarchy, problem, smoothers, transfer
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- operator
+
+
+def test_operator_matches_loop_restatement_and_is_symmetric():
+    for (nx, ny, k, b2) in [(4, 6, 3.0, 0.0), (6, 4, 7.5, 0.7), (8, 8, 12.0, 1 / 12)]:
+        h = 1.0 / 8
+        A = problem.helmholtz_matrix(nx, ny, h, k, b2).toarray()
+        B = problem.helmholtz_dense_rowwise(nx, ny, h, k, b2)
+        assert np.array_equal(A, B)
+        assert np.abs(A - A.T).max() == 0.0          # complex symmetric
+
+
+def test_zero_wavenumber_is_neumann_laplacian():
+    # k = 0: the Sommerfeld condition becomes du/dn = 0, so constants are in
+    # the kernel (row sums vanish) and the matrix is real, symmetric and
+    # positive semi-definite with a one-dimensional kernel.
+    A = problem.helmholtz_matrix(7, 5, 0.1, 0.0).toarray()
+    assert np.abs(A.imag).max() == 0
+    assert np.abs(A.sum(axis=1)).max() < 1e-9
+    ev = np.linalg.eigvalsh(A.real)
+    assert ev[0] > -1e-9 and ev[1] > 1e-3
+
+
+def test_absorbing_boundary_and_shift_signs():
+    # Im(x^H A x) = -sum_boundary (k/h)|x|^2 <= 0 and the CSL shift adds
+    # -beta2 sum w k^2 |x|^2 (strictly negative for x != 0).
+    nx = ny = 10
+    h = 0.1
+    k = 6.25
+    rng = np.random.default_rng(0)
+    A = problem.helmholtz_matrix(nx, ny, h, k, 0.0)
+    C = problem.helmholtz_matrix(nx, ny, h, k, 0.7)
+    x = rng.standard_normal(121) + 1j * rng.standard_normal(121)
+    xb = x.reshape(11, 11).copy()
+    xb[1:-1, 1:-1] = 0
+    qa = np.vdot(x, A @ x).imag
+    assert np.isclose(qa, -(k / h) * np.sum(np.abs(xb) ** 2), rtol=1e-12)
+    w = problem.boundary_weights(nx, ny).ravel()
+    qc = np.vdot(x, C @ x).imag
+    assert np.isclose(qc - qa, -0.7 * k * k * np.sum(w * np.abs(x) ** 2), rtol=1e-12)
+
+
+def _mms_error(n, k=5.0, k1=3.0, k2=-2.0):
+    """Manufactured solution u = exp(i(k1 x + k2 y)) (1 + x y): max nodal error."""
+    h = 1.0 / n
+    y, x = np.meshgrid(np.linspace(0, 1, n + 1), np.linspace(0, 1, n + 1), indexing="ij")
+    e = np.exp(1j * (k1 * x + k2 * y))
+    u = e * (1 + x * y)
+    # -Lap u - k^2 u for u = e * q, q = 1 + x y:  -Lap u = (k1^2+k2^2) u - 2 i e (k1 q_x + k2 q_y)
+    lap = (k1**2 + k2**2) * u - 2j * e * (k1 * y + k2 * x)
+    f = lap - k * k * u
+
+    def ux(xx, yy):
+        return np.exp(1j * (k1 * xx + k2 * yy)) * (1j * k1 * (1 + xx * yy) + yy)
+
+    def uy(xx, yy):
+        return np.exp(1j * (k1 * xx + k2 * yy)) * (1j * k2 * (1 + xx * yy) + xx)
+
+    def g(i, j, di, dj):
+        xx, yy = i * h, j * h
+        du_dn = di * ux(xx, yy) + dj * uy(xx, yy)
+        uu = np.exp(1j * (k1 * xx + k2 * yy)) * (1 + xx * yy)
+        return du_dn - 1j * k * uu
+
+    b = problem.sommerfeld_rhs(n, n, h, f, g)
+    A = problem.helmholtz_matrix(n, n, h, k, 0.0).tocsc()
+    sol = spla.spsolve(A, b)
+    return np.abs(sol - u.ravel()).max()
+
+
+def test_manufactured_solution_second_order():
+    errs = [_mms_error(n) for n in (16, 32, 64, 128)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.85) and np.all(rates < 2.2), rates
+
+
+# ---------------------------------------------------------------- transfers
+
+
+def test_prolongation_matches_handwritten_eq_xex():
+    ref = np.array([[float(v) for v in r] for r in _table("bezier_p1_n4.txt")])
+    assert np.array_equal(transfer.prolongation_1d(4).toarray(), ref)
+
+
+def test_prolongation_reproduces_linear_functions_inside():
+    n = 16
+    P = transfer.prolongation_1d(n).toarray()
+    J = np.arange(n // 2 + 1)
+    for a, b in [(1.0, 0.0), (0.3, 2.0), (-1.0, 0.25)]:
+        fine = P @ (a + b * 2 * J)                   # coarse samples of a + b x
+        i = np.arange(n + 1)
+        assert np.allclose(fine[1:-1], (a + b * i)[1:-1], rtol=0, atol=1e-13)
+    # 2D tensor product reproduces bilinear functions at interior nodes
+    P2 = transfer.prolongation(n, n).toarray()
+    Jy, Jx = np.meshgrid(J, J, indexing="ij")
+    iy, ix = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    f = (P2 @ (1 + 2 * Jx * 2 * Jy).ravel()).reshape(n + 1, n + 1)
+    assert np.allclose(f[1:-1, 1:-1], (1 + ix * iy)[1:-1, 1:-1], atol=1e-12)
+
+
+def test_restriction_scale_and_cgc_invariance():
+    n = 8
+    R = transfer.restriction(n, n).toarray()
+    inner = R.reshape(5, 5, -1)[1:-1, 1:-1].reshape(9, -1)
+    assert np.allclose(inner.sum(axis=1), 1.0)
+    # column stencil of P is [1 4 6 4 1]/8 x [1 4 6 4 1]/8
+    P1 = transfer.prolongation_1d(n).toarray()
+    assert np.allclose(P1[2:7, 2], np.array([1, 4, 6, 4, 1]) / 8)
+    A = problem.helmholtz_matrix(n, n, 1 / n, 5.0).toarray()
+    P = transfer.prolongation(n, n).toarray()
+    M1 = P @ np.linalg.solve(R @ A @ P, R)
+    M2 = P @ np.linalg.solve((3 * R) @ A @ P, 3 * R)
+    assert np.allclose(M1, M2, rtol=0, atol=1e-14 * np.abs(M1).max())
+
+
+# ---------------------------------------------------------------- Galerkin
+
+
+def _galerkin_1d(n, op):
+    P = transfer.prolongation_1d(n)
+    return (0.5 * P.T) @ op @ P
+
+
+def test_galerkin_equals_kronecker_form():
+    # Constant k: C = W_y (x) G_x + H_y (x) W_x with 1D factors, and the
+    # Galerkin product of a Kronecker product is the Kronecker product of the
+    # 1D Galerkin products.  Coarsening the 1D factors separately must give
+    # the same A_l as the 2D sparse product R C P.
+    nx, ny, h, k, b2 = 16, 8, 1 / 16, 10.0, 0.7
+    H = hierarchy.build_hierarchy(nx, ny, h, k, b2, levels=3)
+
+    def factors(n):
+        L = sp.diags([-np.ones(n), 2 * np.ones(n + 1), -np.ones(n)], [-1, 0, 1]).tolil()
+        L[0, 0] = L[n, n] = 1.0
+        w = np.ones(n + 1)
+        w[0] = w[-1] = 0.5
+        Bd = np.zeros(n + 1)
+        Bd[0] = Bd[-1] = 1.0
+        return L.tocsr(), sp.diags(w), sp.diags(Bd)
+
+    Lx, Wx, Bx = factors(nx)
+    Ly, Wy, By = factors(ny)
+    G = Lx / h**2 - (1 + 1j * b2) * k * k * Wx - 1j * k / h * Bx
+    Hy = Ly / h**2 - 1j * k / h * By
+    for lev in (1, 2):
+        Gx, Wxl, Hyl, Wyl = G, Wx, Hy, Wy
+        cx, cy = nx, ny
+        for _ in range(lev):
+            Gx, Wxl = _galerkin_1d(cx, Gx), _galerkin_1d(cx, Wxl)
+            Hyl, Wyl = _galerkin_1d(cy, Hyl), _galerkin_1d(cy, Wyl)
+            cx, cy = cx // 2, cy // 2
+        K = sp.kron(Wyl, Gx) + sp.kron(Hyl, Wxl)
+        D = (K - H.A[lev]).toarray()
+        assert np.abs(D).max() <= 1e-13 * np.abs(H.A[lev].toarray()).max()
+    # the fine level itself
+    K0 = sp.kron(Wy, G) + sp.kron(Hy, Wx)
+    assert np.abs((K0 - H.C0).toarray()).max() <= 1e-12 * np.abs(H.C0.toarray()).max()
+
+
+def test_galerkin_stencil_radius_symmetry_translation():
+    nx = ny = 32
+    H = hierarchy.build_hierarchy(nx, ny, 1 / 32, 20.0, 0.7)
+    assert [s for s in H.sizes] == [(32, 32), (16, 16), (8, 8), (4, 4), (2, 2)]
+    assert hierarchy.stencil_radius(H.A[0], 32) == 1
+    assert hierarchy.stencil_radius(H.A[1], 16) == 2
+    assert hierarchy.stencil_radius(H.A[2], 8) == 3
+    assert hierarchy.stencil_radius(H.A[3], 4) == 3
+    for A in H.A:
+        assert np.abs((A - A.T).toarray()).max() <= 1e-12 * np.abs(A.toarray()).max()
+    S = hierarchy.stencil_of(H.A[1], 16, 16, 2)
+    inner = S[4:13, 4:13].reshape(-1, 5, 5)
+    assert np.abs(inner - inner[0]).max() <= 1e-12 * np.abs(inner[0]).max()
+
+
+def test_level_sizes_rule():
+    assert hierarchy.level_sizes(1280, 1280)[-1] == (5, 5)
+    assert len(hierarchy.level_sizes(1280, 1280)) == 9
+    assert hierarchy.level_sizes(32, 32)[-1] == (2, 2)      # 9 < 10 unknowns
+    assert hierarchy.level_sizes(2560, 896)[-1] == (20, 7)
+    assert hierarchy.level_sizes(6, 6) == [(6, 6), (3, 3)]
+    assert hierarchy.level_sizes(32, 32, levels=2) == [(32, 32), (16, 16)]
+
+
+# ---------------------------------------------------------------- smoothers
+
+
+def test_jacobi_fixed_point_and_convergence_on_dominant_system():
+    n = 8
+    A = problem.helmholtz_matrix(n, n, 1 / n, 2.0, 0.0).tocsr()
+    b = np.random.default_rng(1).standard_normal(81) + 0j
+    xs = spla.spsolve(A.tocsc(), b)
+    assert np.allclose(smoothers.jacobi(A, xs, b, 4.5, 3), xs, rtol=1e-12)
+    # strongly shifted (diagonally dominant) system: Jacobi converges
+    D = A + sp.diags(np.full(81, 4.0 * n * n))
+    xd = spla.spsolve(D.tocsc(), b)
+    x = smoothers.jacobi(D, np.zeros(81, complex), b, 1.0, 400)
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_gmres3_is_residual_minimiser():
+    n = 12
+    A = problem.helmholtz_matrix(n, n, 1 / n, 7.5, 0.0).tocsr()
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal(169) + 1j * rng.standard_normal(169)
+    x0 = rng.standard_normal(169) + 1j * rng.standard_normal(169)
+    x1 = smoothers.gmres_step(A, x0, b, 3)
+    r0 = b - A @ x0
+    K = np.stack([r0, A @ r0, A @ (A @ r0)], axis=1)    # Krylov basis, no Arnoldi
+    y = np.linalg.lstsq(A @ K, r0, rcond=None)[0]
+    best = np.linalg.norm(r0 - A @ (K @ y))
+    got = np.linalg.norm(b - A @ x1)
+    assert abs(got - best) <= 1e-10 * np.linalg.norm(r0)
+    assert got <= np.linalg.norm(r0)
+    # A = identity: the first Arnoldi vector is invariant, one step solves
+    I = sp.identity(169, dtype=complex, format="csr")
+    assert np.allclose(smoothers.gmres_step(I, x0, b), b, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- cycle
+
+
+def test_two_level_cycle_equals_dense_two_grid_map():
+    # Eq. (tgi1): T0 = (I - P Ac^-1 R A)(I - X^-1 A) propagates the error of
+    # one smoothing sweep followed by the coarse-grid correction, i.e. a
+    # two-level cycle with nu_pre = 1, nu_post = 0 and an exact coarse solve.
+    n, k = 16, 10.0
+    h = 1 / n
+    H = hierarchy.build_hierarchy(n, n, h, k, 0.7, levels=2)
+    A, P, R, Ac = analysis.two_grid_parts(n, n, h, k, 0.7)
+    T0 = analysis.two_grid_matrix(A, P, R, Ac, 4.5, 1)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(289) + 1j * rng.standard_normal(289)
+    x0 = rng.standard_normal(289) + 1j * rng.standard_normal(289)
+    x1 = cycle.mg_cycle(H, 0, x0, b, cycle.CycleOptions(1, "jacobi", 1, 0, 4.5))
+    xs = np.linalg.solve(A, b)
+    ref = T0 @ x0 + (np.eye(289) - T0) @ xs
+    assert np.linalg.norm(x1 - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_converged_cycle_matches_direct_solve():
+    n, k = 32, 20.0
+    h = 1 / n
+    H = hierarchy.build_hierarchy(n, n, h, k, 0.7)
+    b = problem.point_source_rhs(n, n, h, 16, 16)
+    r = cycle.mg_solve(H, b, 1e-12, cycle.CycleOptions(1, "gmres3", 2, 2))
+    assert r.converged
+    xs = spla.spsolve(H.A[0].tocsc(), b)
+    assert np.linalg.norm(r.x - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_table_conv1_two_grid_norms():
+    # Table conv1: Bezier + CSL gives ||T0|| < 1 for every k, within 0.02 of
+    # the printed values; linear interpolation on A and C stays above 1.
+    rows = _table("table_conv1.txt")
+    for r in rows[:3]:                       # k = 5, 10, 20 (k = 30 is slow)
+        k = float(r[0])
+        n = int(round(k / 0.625))
+        bc = analysis.two_grid_norm(n, n, 1 / n, k, 0.7, coarsen_on="C")
+        assert bc < 1.0 and abs(bc - float(r[4].rstrip("+"))) < 0.02, (k, bc)
+        la = analysis.two_grid_norm(n, n, 1 / n, k, 0.7, kind="linear", coarsen_on="A")
+        lc = analysis.two_grid_norm(n, n, 1 / n, k, 0.7, kind="linear", coarsen_on="C")
+        assert la > 1.0 and lc > 1.0
+        ba = analysis.two_grid_norm(n, n, 1 / n, k, 0.7, coarsen_on="A")
+        assert (ba < 1.0) == r[3].endswith("+"), (k, ba)
+
+
+def test_gmres_counts_track_table_cons2g():
+    # Table cons2g (beta2 = 1/k, GMRES(3)): V and W counts at k = 50 within
+    # 30 % (+-1 cycle) of the printed values, non-increasing in nu.
+    rows = _table("table_cons2g.txt")
+    k, n = 50.0, 80
+    H = hierarchy.build_hierarchy(n, n, 1 / n, k, 1 / k)
+    b = problem.point_source_rhs(n, n, 1 / n, 40, 40)
+    prev = {1: 10**9, 2: 10**9}
+    for r in rows:
+        nu = int(r[0])
+        for gamma, col in ((1, 1), (2, 2)):
+            c = cycle.mg_solve(H, b, 1e-5, cycle.CycleOptions(gamma, "gmres3", nu, nu)).cycles
+            ref = int(r[col])
+            assert abs(c - ref) <= max(1, 0.3 * ref), (nu, gamma, c, ref)
+            assert c <= prev[gamma]
+            prev[gamma] = c
+
+
+def test_jacobi_h_independence_trend():
+    # Table tabhind: omega-Jacobi V-cycle counts at fixed k do not grow with
+    # refinement (within 25 %).  Exact counts are not pinned.
+    k = 15.0
+    counts = []
+    for n in (64, 128):
+        H = hierarchy.build_hierarchy(n, n, 1 / n, k, 0.7)
+        b = problem.point_source_rhs(n, n, 1 / n, n // 2, n // 2)
+        counts.append(cycle.mg_solve(H, b, 1e-5, cycle.CycleOptions(1, "jacobi", 4, 4)).cycles)
+    assert max(counts) <= 1.25 * min(counts), counts
+
+
+# ---------------------------------------------------------------- gradient
+
+
+def test_adjoint_gradient_matches_central_differences():
+    n = 16
+    h = 25.0
+    omega_f = 2 * np.pi * 3.0
+    rng = np.random.default_rng(4)
+    m0 = np.full((n + 1, n + 1), 1.0 / 2000.0**2)
+    m = m0 * (1 + 0.1 * rng.uniform(-1, 1, m0.shape))
+    N = (n + 1) ** 2
+    F = np.zeros((N, 2), complex)
+    F[(n - 1) * (n + 1) + 4, 0] = 1 / h**2
+    F[(n - 1) * (n + 1) + 12, 1] = 1 / h**2
+    rec = np.array([(n - 1) * (n + 1) + i for i in range(1, n)])
+    D, _ = gradient.forward(n, n, h, m0, omega_f, F)
+    D = D[rec]
+    g = gradient.gradient(n, n, h, m, omega_f, F, rec, D)
+    for t in range(3):
+        d = rng.standard_normal(m.shape) * m0
+        eps = 1e-4
+        Lp = gradient.misfit(n, n, h, m + eps * d, omega_f, F, rec, D)
+        Lm = gradient.misfit(n, n, h, m - eps * d, omega_f, F, rec, D)
+        fd = (Lp - Lm) / (2 * eps)
+        ad = float(np.sum(g * d))
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
