@@ -1,0 +1,336 @@
+"""Benchmark: DOF-solves/s of the stand-alone Helmholtz multigrid solver to a
+relative residual of 1e-6 on one GB300 (or N replicas under torchrun).
+
+Workload (default): constant-k MP 2-A at k = 800, kh = 0.625 (n = 1280
+intervals, 1281^2 unknowns), unit point source at the centre, GMRES(3)
+smoothing with complex shift beta2 = 1/k, complex64 cycles inside FP64
+iterative refinement.  One step = one complete solve from x0 = 0 (setup of
+the hierarchy excluded and reported separately).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-solves/s to rel. residual 1e-6 (FP64 vs mixed, batched); % HBM roofline"
+UNIT = "DOF-solves/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--k", type=float, default=800.0)
+    p.add_argument("--n", type=int, default=0, help="intervals per side (default k/0.625)")
+    p.add_argument("--smoother", default="gmres3", choices=["jacobi", "gmres3"])
+    p.add_argument("--cycle", default="V", choices=["V", "W"])
+    p.add_argument("--nu", type=int, default=2, help="pre = post smoothing steps")
+    p.add_argument("--beta2", type=float, default=-1.0, help="complex shift (default 1/k for GMRES, 0.7 Jacobi)")
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--batch", type=int, default=1)
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--no-fp64-line", action="store_true", help="skip the FP64 comparison solve")
+    p.add_argument("--cpu-sample-cycles", type=int, default=2)
+    a = p.parse_args()
+    if a.warmup < 3:
+        p.error("--warmup must be >= 3")
+    if a.n == 0:
+        a.n = int(round(a.k / 0.625))
+    if a.beta2 < 0:
+        a.beta2 = 1.0 / a.k if a.smoother == "gmres3" else 0.7
+    return a
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(per_rank_seconds, units_per_rank):
+    """Whole-job throughput: all units over the slowest rank's time."""
+    t = max(per_rank_seconds)
+    return sum(units_per_rank) / t, t
+
+
+def workload_config(a):
+    return {
+        "workload": f"MP 2-A constant k={a.k:g}, kh={a.k / a.n:.3f}, {a.n + 1}x{a.n + 1} unknowns, centre point source",
+        "unknowns": (a.n + 1) ** 2,
+        "rhs_per_gpu": a.batch,
+        "smoother": a.smoother,
+        "cycle": f"{a.cycle}({a.nu},{a.nu})",
+        "beta2": a.beta2,
+        "precision": a.precision,
+        "tol": a.tol,
+        "l2": "L2 flushed between timed solves (256 MiB write)",
+        "parallelism": "replicas",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    def __init__(self, gpu):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+
+def oracle_cycle_seconds(a, ncycles):  # noqa: D401
+    """Time ``ncycles`` oracle cycles on the full workload (setup excluded)."""
+    import synth
+    from oracle import cycle as oc
+    from oracle import hierarchy as oh
+    h = 1.0 / a.n
+    b = synth.point_source(a.n, a.n, h).ravel()
+    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2)
+    opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
+    x = np.zeros_like(b)
+    t0 = time.perf_counter()
+    for _ in range(ncycles):
+        x = oc.mg_cycle(H, 0, x, b, opt)
+        _ = np.linalg.norm(b - H.A[0] @ x)     # the per-cycle stopping test
+    return (time.perf_counter() - t0) / ncycles
+
+
+def run_reference(a):
+    """The oracle as the reference arm: W untimed and K timed oracle cycles on
+    the full workload (one cycle per step), scaled to a whole solve with the
+    cycle count of the method on this workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    from oracle import cycle as oc
+    from oracle import hierarchy as oh
+    h = 1.0 / a.n
+    b = synth.point_source(a.n, a.n, h).ravel()
+    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2)
+    opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
+    x = np.zeros_like(b)
+    for _ in range(a.warmup):
+        x = oc.mg_cycle(H, 0, x, b, opt)
+        _ = np.linalg.norm(b - H.A[0] @ x)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        x = oc.mg_cycle(H, 0, x, b, opt)
+        _ = np.linalg.norm(b - H.A[0] @ x)
+    tc = (time.perf_counter() - t0) / a.steps
+    cycles_needed = _cycles_from_cache(a)
+    N = (a.n + 1) ** 2 * a.batch
+    value = N / (tc * cycles_needed) if cycles_needed else None
+    sample = (f"{a.steps} timed oracle cycles (after {a.warmup} untimed) on the full workload, one core, "
+              f"scaled to {cycles_needed} cycles per solve (profiles/bench_cycles.json)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": tc * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128", "data": "synthetic", "config": workload_config(a),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def _cycles_from_cache(a):
+    p = os.path.join(ROOT, "profiles", "bench_cycles.json")
+    try:
+        d = json.load(open(p))
+        return int(d.get(f"{a.k:g}/{a.n}/{a.smoother}/{a.cycle}{a.nu}/{a.beta2:g}"))
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def run_ours(a):
+    import torch
+    import paper_2308_13476_gb300 as hm
+    import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    hm.load_library()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, k = a.n, a.k
+    h = 1.0 / n
+    N = (n + 1) ** 2
+    rhs_np = np.broadcast_to(synth.point_source(n, n, h), (a.batch, n + 1, n + 1)).copy()
+    rhs = torch.from_numpy(rhs_np).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(precision):
+        t0 = time.perf_counter()
+        s = hm.Solver(n, n, h, k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
+                      precision=precision, batch=a.batch, max_cycles=20000)
+        torch.cuda.synchronize()
+        return s, time.perf_counter() - t0
+
+    def timed_solves(s, steps, e2e=False):
+        st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        cyc = None
+        launches = 0
+        host_in = torch.from_numpy(rhs_np).pin_memory() if e2e else None
+        host_out = torch.empty((a.batch, n + 1, n + 1), dtype=torch.complex128).pin_memory() if e2e else None
+        for q in range(steps):
+            flush.zero_()
+            x = torch.zeros_like(rhs)
+            torch.cuda.synchronize()
+            st_ev[q].record()
+            if e2e:
+                r_dev = torch.empty_like(rhs)
+                r_dev.copy_(host_in, non_blocking=True)
+                x, status, cyc, rr = s.solve(r_dev, x=x, tol=a.tol)
+                host_out.copy_(x, non_blocking=True)
+            else:
+                x, status, cyc, rr = s.solve(rhs, x=x, tol=a.tol)
+            en_ev[q].record()
+            torch.cuda.synchronize()
+            if status != hm.MG_OK:
+                raise RuntimeError(f"solve failed: {hm.STATUS_NAMES[status]} cycles={cyc} relres={rr}")
+            launches += s.counters()[0]
+        ms = [st_ev[q].elapsed_time(en_ev[q]) for q in range(steps)]
+        return ms, cyc, launches, rr
+
+    s, setup_s = make(a.precision)
+    timed_solves(s, a.warmup)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ms, cyc, launches, rr = timed_solves(s, a.steps)
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    my_t = sum(ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([my_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        my_t = float(t.item())
+    units = N * a.batch * a.steps
+    value, tmax = aggregate([my_t], [units * world])
+    # end to end through the public API with host buffers
+    ms_e2e, _, _, _ = timed_solves(s, a.steps, e2e=True)
+    e2e_value = N * a.batch * a.steps * world / (sum(ms_e2e) / 1e3)
+    # roofline of the dominant kernel, timed live with CUDA events on the library's stream
+    what = 0 if a.smoother == "jacobi" else 1
+    kms, kbytes = s.profile(what, 0, reps=50)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None,
+            "kernel": ("level-0 weighted-Jacobi sweep" if what == 0 else "level-0 residual b - A x") +
+                      f" ({'complex64' if a.precision == 'mixed' else 'complex128'}), "
+                      f"{kbytes / 1e6:.1f} MB algorithmic per launch, peak = measured hbm_gbs"}
+    extra = {"setup_s": setup_s, "cycles": cyc, "relres": rr}
+    if not a.no_fp64_line and a.precision == "mixed":
+        s.close()
+        s64, setup64 = make("fp64")
+        timed_solves(s64, 1)
+        ms64, cyc64, _, _ = timed_solves(s64, 1)
+        extra["fp64_path"] = {"value": N * a.batch / (ms64[0] / 1e3), "unit": UNIT, "cycles": cyc64,
+                              "ms_per_solve": ms64[0]}
+        s64.close()
+    else:
+        s.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": sum(ms) / len(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+f64" if a.precision == "mixed" else "c128", "data": "synthetic",
+        "config": workload_config(a), "clocks": clk, "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rhs.numel() * 16),
+                "d2h_bytes_per_step": int(rhs.numel() * 16)},
+        "roofline": roof, "extra": extra,
+    }
+    if rank == 0 and world == 1 and a.cpu_sample_cycles > 0:
+        tc = oracle_cycle_seconds(a, a.cpu_sample_cycles)
+        cyc_needed = max(cyc)
+        line["cpu_baseline"] = {"value": N * a.batch / (tc * cyc_needed), "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{a.cpu_sample_cycles} oracle cycles on the full workload (FP64, one "
+                                          f"core), scaled to the {cyc_needed} cycles of one solve"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/* helmmg -- stand-alone multigrid for the 2D Helmholtz equation on one GPU.
+ *
+ * Method: Dwarka & Vuik, "Stand-alone multigrid for Helmholtz revisited:
+ * towards convergence using standard components" (arXiv 2308.13476).
+ *
+ *   Problem (Sec. 2, MP 2-A / MP 2-B): -Lap u - k(x,y)^2 u = f on a grid of
+ *   nx by ny square cells of side h, with the first-order absorbing condition
+ *   (d/dn - i k) u = 0 on the whole boundary, 5-point second-order finite
+ *   differences.  Every grid node, boundary nodes included, is an unknown.
+ *   Boundary rows come from eliminating a ghost node with the central
+ *   difference of the boundary condition and are scaled by 1/2 on an edge and
+ *   1/4 at a corner; the matrix A is complex symmetric (A^T = A).  The
+ *   right-hand side uses the same row scaling (a point source on an interior
+ *   node is unaffected).
+ *
+ *   Method (Sec. 3-5): multigrid V-cycle (gamma = 1) or W-cycle (gamma = 2)
+ *   used as a stand-alone solver; weighted-Jacobi smoothing with
+ *   X = omega * diag(A) (omega = 4.5 in the paper) or GMRES(3) smoothing;
+ *   the rational-Bezier prolongation of Eq. (xex) and its transpose as
+ *   restriction; Galerkin coarse operators built on the complex-shifted
+ *   Laplacian -Lap - (1 + i beta2) k^2 (the shift enters once, on the fine
+ *   level); coarsening while both interval counts are even and the grid
+ *   still has at least 10 nodes, with a direct solve on the last grid; stop
+ *   at a relative residual ||b - A x||_2 / ||b||_2 <= tol.
+ *
+ * Data layout.  A grid vector is (ny+1) x (nx+1) complex128 values (real,
+ * imaginary interleaved), row-major with x fastest: node (i, j) at
+ * j*(nx+1) + i.  A batch of B right-hand sides is B such grids back to back.
+ * Real grid fields (k, m, gradients) are (ny+1) x (nx+1) doubles.
+ *
+ * Pointers.  Arrays passed to mg_solve, mg_adjoint, mg_apply,
+ * mg_get_stencil and mg_gradient are DEVICE pointers on the current device,
+ * owned by the caller; the library never frees or keeps them.  The k field of
+ * mg_setup may be host or device memory; it is copied.  cycles_out and
+ * relres_out are HOST arrays of B entries.
+ *
+ * Streams.  All work is ordered on options.stream (a cudaStream_t, NULL =
+ * legacy default stream).  mg_solve returns after the stopping decision, with
+ * the stream synchronised.
+ *
+ * Errors.  Every call returns an mg_status.  On failure mg_last_error()
+ * describes the cause; arrays the caller owns are left as they were at the
+ * failing step (x holds the last iterate).  The library never aborts the
+ * process and never traps on the device.
+ *
+ * Threads.  One handle per host thread; handles are independent.
+ */
+#ifndef HELMMG_H
+#define HELMMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx* mg_handle;
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = -1,     /* bad argument, shape or option                          */
+  MG_ENOMEM = -2,     /* device allocation failed                               */
+  MG_ECUDA = -3,      /* CUDA runtime error                                     */
+  MG_EMAXIT = -4,     /* max_cycles reached before tol (x = last iterate)       */
+  MG_EDIVERGED = -5,  /* relative residual above 1e6 or not finite             */
+  MG_ETIMEOUT = -6,   /* reserved: a bounded device wait gave up                */
+  MG_ESTATE = -7      /* call not valid in the handle's state (e.g. singular
+                         coarsest operator)                                      */
+} mg_status;
+
+typedef struct {
+  int cycle;        /* gamma: 1 = V-cycle, 2 = W-cycle (Table cons1)            */
+  int smoother;     /* 0 = weighted Jacobi (Sec. 3), 1 = GMRES(3) (Sec. 5.3)     */
+  int nu_pre;       /* smoothing steps before the coarse correction, per level  */
+  int nu_post;      /* smoothing steps after it, per level                      */
+  double omega;     /* Jacobi: X = omega * diag(A); the paper uses 4.5          */
+  int precision;    /* 0 = complex128 throughout; 1 = complex64 cycles inside a
+                       complex128 iterative-refinement loop (outer residual,
+                       update, setup and coarsest solve in FP64)               */
+  int max_cycles;   /* cap on cycles (refinement steps for precision 1)       */
+  int min_coarse;   /* stop coarsening below this many grid nodes (Sec. 5: 10) */
+  int batch;        /* B: right-hand sides solved together                      */
+  void* stream;     /* cudaStream_t                                             */
+} mg_options;
+
+/* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
+ * min_coarse 10, batch 1, default stream. */
+void mg_default_options(mg_options* opt);
+
+/* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).
+ *   nx, ny    interval counts (>= 2); grids are coarsened while both are even
+ *   h         cell size (> 0)
+ *   k_field   NULL for constant k = k_const (MP 2-A), else (ny+1)*(nx+1)
+ *             positive wavenumbers (MP 2-B), host or device memory, copied
+ *   beta2     complex shift of the CSL used for Galerkin coarsening (>= 0;
+ *             0 coarsens the Helmholtz operator itself)
+ *   levels    0 = as many as the coarsening rule allows; n > 0 caps the count
+ *   opt       NULL = mg_default_options
+ * The coarsest grid must have at most 2048 nodes.  On success *out owns all
+ * device memory of the hierarchy; release it with mg_destroy. */
+mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_field, double k_const, double beta2,
+                   int levels, const mg_options* opt);
+
+/* Solve A x = rhs for the handle's batch, starting from the x passed in.
+ *   rhs        device, B grids complex128 (read only)
+ *   x          device, B grids complex128: initial guess in, iterate out
+ *   tol        relative residual target (> 0)
+ *   cycles_out host int[B] or NULL: cycles done per right-hand side
+ *   relres_out host double[B] or NULL: final relative residual per RHS
+ * Each right-hand side stops on its own: once it meets tol it is no longer
+ * updated.  Returns MG_OK when all met tol, MG_EDIVERGED if any diverged
+ * (checked first), MG_EMAXIT if any hit max_cycles.  An all-zero rhs gives
+ * x = 0 and 0 cycles. */
+mg_status mg_solve(mg_handle h, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out);
+
+/* Solve the adjoint system A^H lam = rhs_adj with the same hierarchy.  Since
+ * A^T = A, A^H lam = g is conj(A) lam = g, i.e. A conj(lam) = conj(g): the
+ * right-hand side is conjugated on the way in and the solution on the way
+ * out.  Arguments and results as for mg_solve (lam in: initial guess). */
+mg_status mg_adjoint(mg_handle h, const void* rhs_adj, void* lam, double tol, int* cycles_out, double* relres_out);
+
+/* Gradient of L(m) = 1/2 sum_s ||S u_s - d_s||^2 with respect to the squared
+ * slowness m, k^2 = omega_f^2 m, given forward fields u_s (A u_s = f_s) and
+ * adjoint fields lam_s (A^H lam_s = S^T (S u_s - d_s)):
+ *   g = -Re sum_s conj(lam_s) * dA_pp/dm_p * u_s,
+ *   dA_pp/dm_p = -w_p omega_f^2 - i b_p omega_f / (2 h sqrt(m_p)),
+ * w_p the boundary row weight (1, 1/2, 1/4), b_p = 1 on the boundary.
+ *   u, lam   device, nsrc grids complex128 of the handle's (nx, ny)
+ *   m        device, (ny+1)*(nx+1) doubles (> 0)
+ *   g        device, (ny+1)*(nx+1) doubles, overwritten */
+mg_status mg_gradient(mg_handle h, const void* u, const void* lam, int nsrc, const double* m, double omega_f,
+                      double* g);
+
+/* Release every resource of the handle.  NULL is accepted. */
+mg_status mg_destroy(mg_handle h);
+
+/* Message for the last failing call on this host thread; never NULL. */
+const char* mg_last_error(void);
+
+/* ---- inspection entry points (same layouts; for tests and tools) ---- */
+
+/* Level geometry: interval counts and stencil radius (1 on level 0, then 2,
+ * then 3) of level `level`; the number of levels via *nlevels. */
+mg_status mg_level_info(mg_handle h, int level, int* nx, int* ny, int* radius, int* nlevels);
+
+/* y = A_level x for B grids of that level (level 0: the Helmholtz operator;
+ * level >= 1: the Galerkin operator, FP64).  x, y device complex128. */
+mg_status mg_apply(mg_handle h, int level, const void* x, void* y);
+
+/* Per-node stencil of A_level: device complex128 array
+ * [ny+1][nx+1][2r+1][2r+1] with entry [j][i][dy+r][dx+r] the coupling of
+ * node (i, j) to node (i+dx, j+dy) (0 off the grid). */
+mg_status mg_get_stencil(mg_handle h, int level, void* out);
+
+/* Relative residual history of the last solve: hist[b * cap + c] is the
+ * relative residual of RHS b after cycle c+1 (c < min(cycles, cap)).
+ * hist: host double[B * cap]. */
+mg_status mg_history(mg_handle h, double* hist, int cap);
+
+/* ---- instrumentation ---- */
+
+/* Time one kernel of the hierarchy in the handle's precision: `what` = 0 one
+ * weighted-Jacobi sweep, 1 a residual b - A x, 2 a restriction, 3 a
+ * prolongation-and-correct, on level `level` for all B right-hand sides.
+ * The kernel runs `reps` times back to back between two CUDA events on the
+ * handle's stream (after one untimed launch); *ms gets the mean time of one
+ * launch and *bytes the algorithmic DRAM bytes of one launch (each input
+ * array read once, each output written once).  It overwrites the handle's
+ * internal work vectors, never caller memory. */
+mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes);
+
+/* Kernel launches issued by the last mg_solve / mg_adjoint (graph kernel
+ * nodes counted once per graph launch) and the number of graph launches. */
+mg_status mg_counters(mg_handle h, long long* kernel_launches, long long* graph_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELMMG_H */

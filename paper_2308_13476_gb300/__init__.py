@@ -1,0 +1,291 @@
+"""Python binding of the helmmg C-ABI (include/helmmg.h): stand-alone
+multigrid for the 2D Helmholtz equation (Dwarka & Vuik, arXiv 2308.13476)
+on one GB300 GPU.
+
+This module only marshals arguments: every step of a solve runs in the
+library's CUDA kernels.  Device arrays are torch CUDA tensors (complex128
+grids of shape (B, ny+1, nx+1) or (ny+1, nx+1), float64 fields); the library
+never keeps references to them.  If the compiled library is missing the
+import of this package still succeeds, but every call raises
+``HelmmgUnavailable``: there is no CPU fallback.
+
+Low-level functions carry the C names (``mg_setup``, ``mg_solve``,
+``mg_adjoint``, ``mg_gradient``, ``mg_destroy`` ...); ``Solver`` wraps them.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhelmmg.so")
+
+MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_EMAXIT, MG_EDIVERGED, MG_ETIMEOUT, MG_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "MG_OK", -1: "MG_EINVAL", -2: "MG_ENOMEM", -3: "MG_ECUDA", -4: "MG_EMAXIT",
+                -5: "MG_EDIVERGED", -6: "MG_ETIMEOUT", -7: "MG_ESTATE"}
+EXPORTED = ["mg_default_options", "mg_setup", "mg_solve", "mg_adjoint", "mg_gradient", "mg_destroy",
+            "mg_last_error", "mg_level_info", "mg_apply", "mg_get_stencil", "mg_history", "mg_profile",
+            "mg_counters"]
+
+
+class HelmmgUnavailable(RuntimeError):
+    """The compiled CUDA library could not be loaded."""
+
+
+class HelmmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MgOptions(ctypes.Structure):
+    _fields_ = [("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("nu_pre", ctypes.c_int),
+                ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libhelmmg.so (built by ``paper_2308_13476_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise HelmmgUnavailable(f"{path} is missing: run paper_2308_13476_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+    lib.mg_default_options.argtypes = [ctypes.POINTER(MgOptions)]
+    lib.mg_default_options.restype = None
+    lib.mg_setup.argtypes = [ctypes.POINTER(vp), i, i, d, vp, d, d, i, ctypes.POINTER(MgOptions)]
+    lib.mg_solve.argtypes = [vp, vp, vp, d, ip, dp]
+    lib.mg_adjoint.argtypes = [vp, vp, vp, d, ip, dp]
+    lib.mg_gradient.argtypes = [vp, vp, vp, i, vp, d, vp]
+    lib.mg_destroy.argtypes = [vp]
+    lib.mg_last_error.argtypes = []
+    lib.mg_last_error.restype = ctypes.c_char_p
+    lib.mg_level_info.argtypes = [vp, i, ip, ip, ip, ip]
+    lib.mg_apply.argtypes = [vp, i, vp, vp]
+    lib.mg_get_stencil.argtypes = [vp, i, vp]
+    lib.mg_history.argtypes = [vp, dp, i]
+    lib.mg_profile.argtypes = [vp, i, i, i, dp, dp]
+    lib.mg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    for name in EXPORTED:
+        if name not in ("mg_default_options", "mg_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, allow=()):
+    if status != MG_OK and status not in allow:
+        raise HelmmgError(status, load_library().mg_last_error().decode())
+    return status
+
+
+def _ptr(t, dtype=None, name="array"):
+    """Device pointer of a contiguous CUDA tensor (checked)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- C-named calls
+
+
+def mg_default_options():
+    o = MgOptions()
+    load_library().mg_default_options(ctypes.byref(o))
+    return o
+
+
+def mg_setup(nx, ny, h, k_field=None, k_const=0.0, beta2=0.0, levels=0, opt=None):
+    """Returns an opaque handle (int).  ``k_field``: float64 tensor
+    (ny+1, nx+1) on the host or the device, or None for constant k."""
+    lib = load_library()
+    opt = opt or mg_default_options()
+    hdl = ctypes.c_void_p()
+    kp = None
+    if k_field is not None:
+        import torch
+        if k_field.dtype != torch.float64 or not k_field.is_contiguous():
+            raise TypeError("k_field must be a contiguous float64 tensor")
+        if tuple(k_field.shape) != (ny + 1, nx + 1):
+            raise ValueError("k_field must have shape (ny+1, nx+1)")
+        kp = ctypes.c_void_p(k_field.data_ptr())
+    _check(lib.mg_setup(ctypes.byref(hdl), int(nx), int(ny), float(h), kp, float(k_const), float(beta2),
+                        int(levels), ctypes.byref(opt)))
+    return hdl.value
+
+
+def _solve_call(fn, hdl, rhs, x, tol, batch):
+    import torch
+    cyc = (ctypes.c_int * batch)()
+    rr = (ctypes.c_double * batch)()
+    st = fn(ctypes.c_void_p(hdl), _ptr(rhs, torch.complex128, "rhs"), _ptr(x, torch.complex128, "x"), float(tol),
+            cyc, rr)
+    _check(st, allow=(MG_EMAXIT, MG_EDIVERGED))
+    return st, list(cyc), list(rr)
+
+
+def mg_solve(hdl, rhs, x, tol, batch=1):
+    """In-place solve; returns (status, cycles per RHS, relres per RHS)."""
+    return _solve_call(load_library().mg_solve, hdl, rhs, x, tol, batch)
+
+
+def mg_adjoint(hdl, rhs_adj, lam, tol, batch=1):
+    """In-place solve of A^H lam = rhs_adj; returns (status, cycles, relres)."""
+    return _solve_call(load_library().mg_adjoint, hdl, rhs_adj, lam, tol, batch)
+
+
+def mg_gradient(hdl, u, lam, m, omega_f, g):
+    import torch
+    nsrc = u.shape[0] if u.dim() == 3 else 1
+    _check(load_library().mg_gradient(ctypes.c_void_p(hdl), _ptr(u, torch.complex128, "u"),
+                                      _ptr(lam, torch.complex128, "lam"), int(nsrc), _ptr(m, torch.float64, "m"),
+                                      float(omega_f), _ptr(g, torch.float64, "g")))
+
+
+def mg_destroy(hdl):
+    if hdl:
+        load_library().mg_destroy(ctypes.c_void_p(hdl))
+
+
+def mg_level_info(hdl, level):
+    a, b, r, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().mg_level_info(ctypes.c_void_p(hdl), int(level), ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(r), ctypes.byref(n)))
+    return a.value, b.value, r.value, n.value
+
+
+def mg_apply(hdl, level, x, y):
+    import torch
+    _check(load_library().mg_apply(ctypes.c_void_p(hdl), int(level), _ptr(x, torch.complex128, "x"),
+                                   _ptr(y, torch.complex128, "y")))
+
+
+def mg_get_stencil(hdl, level, out):
+    import torch
+    _check(load_library().mg_get_stencil(ctypes.c_void_p(hdl), int(level), _ptr(out, torch.complex128, "out")))
+
+
+def mg_history(hdl, batch, cap):
+    buf = (ctypes.c_double * (batch * cap))()
+    _check(load_library().mg_history(ctypes.c_void_p(hdl), buf, int(cap)))
+    return [list(buf[b * cap:(b + 1) * cap]) for b in range(batch)]
+
+
+def mg_profile(hdl, what, level, reps):
+    """(ms per launch, algorithmic bytes per launch) of one kernel kind."""
+    ms, nb = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().mg_profile(ctypes.c_void_p(hdl), int(what), int(level), int(reps), ctypes.byref(ms),
+                                     ctypes.byref(nb)))
+    return ms.value, nb.value
+
+
+def mg_counters(hdl):
+    k, g = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load_library().mg_counters(ctypes.c_void_p(hdl), ctypes.byref(k), ctypes.byref(g)))
+    return k.value, g.value
+
+
+# ------------------------------------------------------------- convenience
+
+
+SMOOTHERS = {"jacobi": 0, "gmres3": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class Solver:
+    """One multigrid hierarchy on the current CUDA device.
+
+    Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
+           nu_pre, nu_post, omega, precision="fp64"|"mixed", batch, levels,
+           max_cycles, min_coarse, stream)
+    ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
+    """
+
+    def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
+                 precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, stream=None):
+        o = mg_default_options()
+        o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
+        o.smoother = SMOOTHERS[smoother]
+        o.nu_pre, o.nu_post, o.omega = int(nu_pre), int(nu_post), float(omega)
+        o.precision = PRECISIONS[precision]
+        o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
+        o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
+        self.nx, self.ny, self.h, self.batch = nx, ny, h, batch
+        if isinstance(k, (int, float)):
+            self.handle = mg_setup(nx, ny, h, None, float(k), beta2, levels, o)
+        else:
+            self.handle = mg_setup(nx, ny, h, k, 0.0, beta2, levels, o)
+        self.nlevels = mg_level_info(self.handle, 0)[3]
+
+    def _grid(self, t):
+        import torch
+        t = t.reshape(self.batch, self.ny + 1, self.nx + 1)
+        return t.to(torch.complex128).contiguous()
+
+    def solve(self, rhs, x=None, tol=1e-6):
+        """Returns (x, status, cycles, relres); x is a new tensor unless given."""
+        import torch
+        rhs = self._grid(rhs)
+        if x is None:
+            x = torch.zeros_like(rhs)
+        st, cyc, rr = mg_solve(self.handle, rhs, x, tol, self.batch)
+        return x, st, cyc, rr
+
+    def adjoint(self, rhs_adj, lam=None, tol=1e-6):
+        import torch
+        rhs_adj = self._grid(rhs_adj)
+        if lam is None:
+            lam = torch.zeros_like(rhs_adj)
+        st, cyc, rr = mg_adjoint(self.handle, rhs_adj, lam, tol, self.batch)
+        return lam, st, cyc, rr
+
+    def gradient(self, u, lam, m, omega_f):
+        import torch
+        g = torch.empty((self.ny + 1, self.nx + 1), dtype=torch.float64, device=u.device)
+        mg_gradient(self.handle, u.contiguous(), lam.contiguous(), m.contiguous(), omega_f, g)
+        return g
+
+    def level_info(self, level):
+        return mg_level_info(self.handle, level)
+
+    def apply(self, level, x):
+        import torch
+        y = torch.empty_like(x)
+        mg_apply(self.handle, level, x.contiguous(), y)
+        return y
+
+    def stencil(self, level):
+        import torch
+        nx, ny, r, _ = mg_level_info(self.handle, level)
+        out = torch.empty((ny + 1, nx + 1, 2 * r + 1, 2 * r + 1), dtype=torch.complex128, device="cuda")
+        mg_get_stencil(self.handle, level, out)
+        return out
+
+    def history(self, cap):
+        return mg_history(self.handle, self.batch, cap)
+
+    def profile(self, what, level=0, reps=20):
+        return mg_profile(self.handle, what, level, reps)
+
+    def counters(self):
+        return mg_counters(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

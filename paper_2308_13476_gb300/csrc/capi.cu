@@ -1,0 +1,658 @@
+// C-ABI of the helmmg library: hierarchy setup, the cycle driver (recursive
+// V/W schedule captured once into a CUDA graph), the FP64 and the mixed
+// (complex64 cycles in FP64 iterative refinement) solve loops, the adjoint
+// solve and the misfit gradient.  See include/helmmg.h for the contract.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/helmmg.h"
+#include "internal.h"
+
+using namespace hmg;
+
+static thread_local std::string g_err;
+
+#define FAIL(code, ...)                                          \
+  do {                                                           \
+    char _b[512];                                                \
+    snprintf(_b, sizeof(_b), __VA_ARGS__);                       \
+    g_err = _b;                                                  \
+    return code;                                                 \
+  } while (0)
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) FAIL(MG_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e)); \
+  } while (0)
+
+namespace {
+
+template <class T> struct LevelVec {
+  cx<T>* x = nullptr;   // iterate / correction
+  cx<T>* b = nullptr;   // right-hand side / restricted residual
+  cx<T>* t = nullptr;   // Jacobi ping-pong partner of x
+  cx<T>* r = nullptr;   // residual before restriction
+  cx<T>* st = nullptr;  // stored stencil planes (levels >= 1)
+  cx<T>* dinv = nullptr;
+  GmresBufs gb{};
+};
+
+struct Level {
+  Grid g;
+  int radius;                 // 1 on level 0 (matrix free), 2, then 3
+  double2* st = nullptr;      // FP64 Galerkin stencil, levels >= 1
+  double2* dinv = nullptr;
+  long long plane = 0;
+};
+
+}  // namespace
+
+struct mg_ctx {
+  mg_options opt;
+  int nx = 0, ny = 0, B = 1, nlev = 0, ncoarse = 0;
+  double h = 0, kconst = 0, beta2 = 0;
+  std::vector<Level> lev;
+  std::vector<LevelVec<double>> v64;
+  std::vector<LevelVec<float>> v32;
+  Op0Consts<double>* c0d = nullptr;
+  Op0Consts<float>* c0f = nullptr;
+  double* kf64 = nullptr;
+  float* kf32 = nullptr;
+  double2* cinv = nullptr;
+  double* partial = nullptr;
+  double* gst = nullptr;   // GMRES scalars
+  int* active = nullptr;
+  int* state = nullptr;
+  int* cycles = nullptr;
+  double* relres = nullptr;
+  double* hist = nullptr;
+  int hist_len = 0;
+  double* bnorm = nullptr;
+  double* tolp = nullptr;  // {tol, divergence threshold}
+  int* n_active = nullptr;
+  int* h_n_active = nullptr;  // pinned
+  int* status = nullptr;
+  cudaStream_t cap = nullptr;        // capture stream
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::vector<void*> allocs;
+  long long graph_kernels = 0;     // kernel nodes in the cycle graph
+  long long last_launches = 0, last_graphs = 0;
+
+  ~mg_ctx() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    for (void* p : allocs) cudaFree(p);
+    if (h_n_active) cudaFreeHost(h_n_active);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+static cudaError_t dalloc(mg_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back(*p);
+  return cudaMemset(*p, 0, bytes);
+}
+
+static Grid make_grid(int nx, int ny, int B) {
+  Grid g;
+  g.nx = nx;
+  g.ny = ny;
+  g.pitch = ((nx + 1 + 2 * HALO) + 3) / 4 * 4;
+  g.rows = ny + 1 + 2 * HALO;
+  g.vstride = (long long)g.pitch * g.rows;
+  (void)B;
+  return g;
+}
+
+static OpView<double> op64(const mg_ctx* c, int l) {
+  OpView<double> v{};
+  if (l == 0) {
+    v.kind = 1;
+    v.c0 = c->c0d;
+    v.kf = c->kf64;
+  } else {
+    v.kind = c->lev[l].radius;
+    v.st = c->lev[l].st;
+    v.dinv = c->lev[l].dinv;
+    v.plane = c->lev[l].plane;
+  }
+  return v;
+}
+
+static OpView<float> op32(const mg_ctx* c, int l) {
+  OpView<float> v{};
+  if (l == 0) {
+    v.kind = 1;
+    v.c0 = c->c0f;
+    v.kf = c->kf32;
+  } else {
+    v.kind = c->lev[l].radius;
+    v.st = c->v32[l].st;
+    v.dinv = c->v32[l].dinv;
+    v.plane = c->lev[l].plane;
+  }
+  return v;
+}
+
+template <class T> static OpView<T> opT(const mg_ctx* c, int l);
+template <> OpView<double> opT<double>(const mg_ctx* c, int l) { return op64(c, l); }
+template <> OpView<float> opT<float>(const mg_ctx* c, int l) { return op32(c, l); }
+template <class T> static std::vector<LevelVec<T>>& vecs(mg_ctx* c);
+template <> std::vector<LevelVec<double>>& vecs<double>(mg_ctx* c) { return c->v64; }
+template <> std::vector<LevelVec<float>>& vecs<float>(mg_ctx* c) { return c->v32; }
+
+template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, const Grid& g, bool gmres) {
+  const size_t bytes = sizeof(cx<T>) * (size_t)g.vstride * c->B;
+  cudaError_t e;
+  if ((e = dalloc(c, (void**)&v.x, bytes))) return e;
+  if ((e = dalloc(c, (void**)&v.b, bytes))) return e;
+  if ((e = dalloc(c, (void**)&v.t, bytes))) return e;
+  if ((e = dalloc(c, (void**)&v.r, bytes))) return e;
+  if (gmres) {
+    for (int q = 0; q < 4; ++q)
+      if ((e = dalloc(c, &v.gb.u[q], bytes))) return e;
+    if ((e = dalloc(c, &v.gb.w, bytes))) return e;
+    v.gb.partial = c->partial;
+    v.gb.st = c->gst;
+  }
+  return cudaSuccess;
+}
+
+// ----------------------------------------------------------------- cycle emission
+
+template <class T> struct Emit {
+  mg_ctx* c;
+  cudaStream_t s;
+  std::vector<cx<T>*> cur, oth;
+
+  void smooth(int l, int nu) {
+    if (nu <= 0) return;
+    auto& V = vecs<T>(c)[l];
+    const Grid& g = c->lev[l].g;
+    const OpView<T> op = opT<T>(c, l);
+    if (c->opt.smoother == 0) {
+      for (int q = 0; q < nu; ++q) {
+        launch_jacobi<T>(g, op, cur[l], V.b, oth[l], c->B, c->active, s);
+        std::swap(cur[l], oth[l]);
+      }
+    } else {
+      gmres_smooth<T>(g, op, cur[l], V.b, nu, c->B, c->active, V.gb, s);
+    }
+  }
+
+  void coarse_solve(int l) {
+    auto& V = vecs<T>(c)[l];
+    launch_coarse_solve<T>(c->lev[l].g, c->cinv, c->ncoarse, V.b, cur[l], c->B, c->active, s);
+  }
+
+  void cycle(int l) {
+    const int L = c->nlev;
+    if (l == L - 1) {
+      coarse_solve(l);
+      return;
+    }
+    auto& V = vecs<T>(c);
+    const Grid& g = c->lev[l].g;
+    const Grid& gc = c->lev[l + 1].g;
+    smooth(l, c->opt.nu_pre);
+    launch_residual<T>(g, opT<T>(c, l), cur[l], V[l].b, V[l].r, c->B, c->active, s);
+    launch_restrict<T>(g, gc, V[l].r, V[l + 1].b, c->B, c->active, s);
+    if (l + 1 == L - 1) {
+      coarse_solve(l + 1);
+    } else {
+      cudaMemsetAsync(cur[l + 1], 0, sizeof(cx<T>) * (size_t)gc.vstride * c->B, s);
+      for (int q = 0; q < c->opt.cycle; ++q) cycle(l + 1);
+    }
+    launch_prolong_add<T>(g, gc, cur[l + 1], cur[l], c->B, c->active, s);
+    smooth(l, c->opt.nu_post);
+  }
+
+  void init() {
+    auto& V = vecs<T>(c);
+    cur.resize(c->nlev);
+    oth.resize(c->nlev);
+    for (int l = 0; l < c->nlev; ++l) {
+      cur[l] = V[l].x;
+      oth[l] = V[l].t;
+    }
+  }
+};
+
+// One FP64 cycle followed by the stopping test (graph body of the FP64 path).
+static void emit_fp64_iteration(mg_ctx* c, cudaStream_t s) {
+  Emit<double> e{c, s};
+  e.init();
+  e.cycle(0);
+  if (e.cur[0] != c->v64[0].x) launch_copy_masked<double>(c->lev[0].g, e.cur[0], c->v64[0].x, c->B, c->active, s);
+  const int nblk = launch_resnorm<double>(c->lev[0].g, op64(c, 0), c->v64[0].x, c->v64[0].b, c->partial, c->B,
+                                          c->active, s);
+  launch_stop(c->partial, nblk, c->B, c->bnorm, c->tolp, c->active, c->state, c->cycles, c->relres, c->hist,
+              c->hist_len, c->n_active, 1, s);
+}
+
+// One refinement step of the mixed path: e = 0, one complex64 cycle on the
+// float residual, x += e in FP64, new FP64 residual (cast to float) and the
+// stopping test.
+static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
+  Emit<float> e{c, s};
+  e.init();
+  const Grid& g0 = c->lev[0].g;
+  cudaMemsetAsync(c->v32[0].x, 0, sizeof(float2) * (size_t)g0.vstride * c->B, s);
+  e.cycle(0);
+  launch_update_mixed(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
+  const int nblk = launch_resid_cast_norm(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->partial, c->B,
+                                          c->active, s);
+  launch_stop(c->partial, nblk, c->B, c->bnorm, c->tolp, c->active, c->state, c->cycles, c->relres, c->hist,
+              c->hist_len, c->n_active, 1, s);
+}
+
+template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, int reps, double* ms, double* bytes) {
+  cudaStream_t s = (cudaStream_t)h->opt.stream;
+  auto& V = vecs<T>(h);
+  if (level < 0 || level >= (int)V.size() || (what >= 2 && level + 1 >= h->nlev)) FAIL(MG_EINVAL, "bad level");
+  const Grid& g = h->lev[level].g;
+  const OpView<T> op = opT<T>(h, level);
+  const double nodes = (double)(g.nx + 1) * (g.ny + 1) * h->B;
+  const double e = sizeof(cx<T>);
+  double opbytes = 0;   // per node: stored stencil and inverse diagonal, or the k field
+  if (level > 0) {
+    const int r = h->lev[level].radius;
+    opbytes = e * ((2 * r + 1) * (2 * r + 1) + 1) / h->B;
+  } else if (op.kf) {
+    opbytes = sizeof(T) / (double)h->B;
+  }
+  auto launch = [&]() {
+    switch (what) {
+      case 0: launch_jacobi<T>(g, op, V[level].x, V[level].b, V[level].t, h->B, nullptr, s); break;
+      case 1: launch_residual<T>(g, op, V[level].x, V[level].b, V[level].r, h->B, nullptr, s); break;
+      case 2: launch_restrict<T>(g, h->lev[level + 1].g, V[level].r, V[level + 1].b, h->B, nullptr, s); break;
+      default: launch_prolong_add<T>(g, h->lev[level + 1].g, V[level + 1].x, V[level].x, h->B, nullptr, s); break;
+    }
+  };
+  if (what == 0 || what == 1) *bytes = nodes * (3 * e + opbytes);
+  else if (what == 2) *bytes = nodes * e * 1.25;     // read fine r, write coarse r
+  else *bytes = nodes * e * 2.25;                     // read+write fine x, read coarse e
+  launch();
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, s));
+  for (int q = 0; q < reps; ++q) launch();
+  CK(cudaEventRecord(b, s));
+  CK(cudaEventSynchronize(b));
+  float t = 0;
+  CK(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  CK(cudaGetLastError());
+  *ms = t / reps;
+  return MG_OK;
+}
+
+// ----------------------------------------------------------------- C ABI
+
+extern "C" {
+
+void mg_default_options(mg_options* o) {
+  if (!o) return;
+  o->cycle = 1;
+  o->smoother = 0;
+  o->nu_pre = 1;
+  o->nu_post = 1;
+  o->omega = 4.5;
+  o->precision = 0;
+  o->max_cycles = 10000;
+  o->min_coarse = 10;
+  o->batch = 1;
+  o->stream = nullptr;
+}
+
+const char* mg_last_error(void) { return g_err.c_str(); }
+
+mg_status mg_destroy(mg_handle h) {
+  delete h;
+  return MG_OK;
+}
+
+static mg_status setup_impl(mg_ctx* c, const double* k_field) {
+  const mg_options& o = c->opt;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  // level list: halve while both counts are even and the grid has >= min_coarse nodes
+  std::vector<std::pair<int, int>> sizes{{c->nx, c->ny}};
+  while (true) {
+    auto [cx_, cy_] = sizes.back();
+    if (c->nlev > 0 && (int)sizes.size() >= c->nlev) break;
+    if (cx_ % 2 || cy_ % 2 || (long long)(cx_ + 1) * (cy_ + 1) < o.min_coarse) break;
+    sizes.push_back({cx_ / 2, cy_ / 2});
+  }
+  c->nlev = (int)sizes.size();
+  c->ncoarse = (sizes.back().first + 1) * (sizes.back().second + 1);
+  if (c->ncoarse > 2048) FAIL(MG_EINVAL, "coarsest grid has %d nodes (> 2048); use more levels", c->ncoarse);
+  c->lev.resize(c->nlev);
+  for (int l = 0; l < c->nlev; ++l) {
+    c->lev[l].g = make_grid(sizes[l].first, sizes[l].second, c->B);
+    c->lev[l].radius = l == 0 ? 1 : (l == 1 ? 2 : 3);
+    c->lev[l].plane = (long long)(sizes[l].first + 1) * (sizes[l].second + 1);
+  }
+  const bool mixed = o.precision == 1;
+  const bool gm = o.smoother == 1;
+  const Grid& g0 = c->lev[0].g;
+  CK(dalloc(c, (void**)&c->c0d, sizeof(Op0Consts<double>)));
+  if (mixed) CK(dalloc(c, (void**)&c->c0f, sizeof(Op0Consts<float>)));
+  const long long N0 = c->lev[0].plane;
+  if (k_field) {
+    CK(dalloc(c, (void**)&c->kf64, sizeof(double) * N0));
+    CK(cudaMemcpyAsync(c->kf64, k_field, sizeof(double) * N0, cudaMemcpyDefault, s));
+    if (mixed) {
+      CK(dalloc(c, (void**)&c->kf32, sizeof(float) * N0));
+      launch_to_float_real(c->kf64, c->kf32, N0, s);
+    }
+  }
+  launch_op0consts(c->c0d, c->c0f, c->h, c->kconst, o.omega, c->beta2, s);
+  // Galerkin operators A_{l+1} = R_l C_l P_l
+  for (int l = 1; l < c->nlev; ++l) {
+    Level& L = c->lev[l];
+    const int r = L.radius;
+    const long long S = (long long)(2 * r + 1) * (2 * r + 1);
+    CK(dalloc(c, (void**)&L.st, sizeof(double2) * S * L.plane));
+    CK(dalloc(c, (void**)&L.dinv, sizeof(double2) * L.plane));
+    launch_galerkin(op64(c, l - 1), c->lev[l - 1].g.nx, c->lev[l - 1].g.ny, L.st, L.g.nx, L.g.ny, r, c->beta2, s);
+    launch_diaginv(L.st, r, L.plane, o.omega, L.dinv, s);
+  }
+  CK(cudaGetLastError());
+  // coarsest direct solver
+  {
+    const int N = c->ncoarse;
+    double2* M;
+    CK(dalloc(c, (void**)&M, sizeof(double2) * (size_t)N * N));
+    CK(dalloc(c, (void**)&c->cinv, sizeof(double2) * (size_t)N * N));
+    CK(dalloc(c, (void**)&c->status, sizeof(int) * 4));
+    const int lc = c->nlev - 1;
+    launch_dense(op64(c, lc), c->lev[lc].g.nx, c->lev[lc].g.ny, M, s);
+    launch_gauss_jordan(M, c->cinv, N, c->status, s);
+    CK(cudaGetLastError());
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st) FAIL(MG_ESTATE, "coarsest operator is singular");
+  }
+  // work arrays
+  const int nblk0 = cdiv(g0.nx + 1, BX) * cdiv(g0.ny + 1, BY);
+  CK(dalloc(c, (void**)&c->partial, sizeof(double) * (size_t)nblk0 * c->B * 8));
+  CK(dalloc(c, (void**)&c->gst, sizeof(double) * 96 * c->B));
+  CK(dalloc(c, (void**)&c->active, sizeof(int) * c->B));
+  CK(dalloc(c, (void**)&c->state, sizeof(int) * c->B));
+  CK(dalloc(c, (void**)&c->cycles, sizeof(int) * c->B));
+  CK(dalloc(c, (void**)&c->relres, sizeof(double) * c->B));
+  CK(dalloc(c, (void**)&c->bnorm, sizeof(double) * c->B));
+  CK(dalloc(c, (void**)&c->tolp, sizeof(double) * 2));
+  CK(dalloc(c, (void**)&c->n_active, sizeof(int)));
+  c->hist_len = std::min(o.max_cycles, 4096);
+  CK(dalloc(c, (void**)&c->hist, sizeof(double) * (size_t)c->hist_len * c->B));
+  CK(cudaMallocHost((void**)&c->h_n_active, sizeof(int)));
+  // vectors
+  if (!mixed) {
+    c->v64.resize(c->nlev);
+    for (int l = 0; l < c->nlev; ++l) CK(alloc_vectors<double>(c, c->v64[l], c->lev[l].g, gm));
+  } else {
+    c->v64.resize(1);
+    const size_t bytes = sizeof(double2) * (size_t)g0.vstride * c->B;
+    CK(dalloc(c, (void**)&c->v64[0].x, bytes));
+    CK(dalloc(c, (void**)&c->v64[0].b, bytes));
+    c->v32.resize(c->nlev);
+    for (int l = 0; l < c->nlev; ++l) {
+      CK(alloc_vectors<float>(c, c->v32[l], c->lev[l].g, gm));
+      if (l > 0) {
+        const Level& L = c->lev[l];
+        const long long S = (long long)(2 * L.radius + 1) * (2 * L.radius + 1);
+        CK(dalloc(c, (void**)&c->v32[l].st, sizeof(float2) * S * L.plane));
+        CK(dalloc(c, (void**)&c->v32[l].dinv, sizeof(float2) * L.plane));
+        launch_to_float(L.st, c->v32[l].st, S * L.plane, s);
+        launch_to_float(L.dinv, c->v32[l].dinv, L.plane, s);
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  return MG_OK;
+}
+
+mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_field, double k_const, double beta2,
+                   int levels, const mg_options* opt) {
+  if (!out) FAIL(MG_EINVAL, "out is NULL");
+  *out = nullptr;
+  mg_options o;
+  if (opt) o = *opt; else mg_default_options(&o);
+  if (nx < 2 || ny < 2) FAIL(MG_EINVAL, "grid needs nx, ny >= 2 (got %d, %d)", nx, ny);
+  if (!(h > 0) || !(beta2 >= 0) || levels < 0) FAIL(MG_EINVAL, "need h > 0, beta2 >= 0, levels >= 0");
+  if (!k_field && !(k_const >= 0)) FAIL(MG_EINVAL, "k_const must be >= 0");
+  if (o.cycle != 1 && o.cycle != 2) FAIL(MG_EINVAL, "cycle must be 1 (V) or 2 (W)");
+  if (o.smoother != 0 && o.smoother != 1) FAIL(MG_EINVAL, "smoother must be 0 (Jacobi) or 1 (GMRES(3))");
+  if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post > 64) FAIL(MG_EINVAL, "bad nu_pre / nu_post");
+  if (!(o.omega > 0)) FAIL(MG_EINVAL, "omega must be > 0");
+  if (o.precision != 0 && o.precision != 1) FAIL(MG_EINVAL, "precision must be 0 or 1");
+  if (o.max_cycles < 1 || o.min_coarse < 1) FAIL(MG_EINVAL, "max_cycles and min_coarse must be >= 1");
+  if (o.batch < 1 || o.batch > 65535) FAIL(MG_EINVAL, "batch must be in 1..65535");
+  if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
+  mg_ctx* c = new mg_ctx();
+  c->opt = o;
+  c->nx = nx;
+  c->ny = ny;
+  c->h = h;
+  c->kconst = k_field ? 0.0 : k_const;
+  c->beta2 = beta2;
+  c->B = o.batch;
+  c->nlev = levels;
+  mg_status st = setup_impl(c, k_field);
+  if (st != MG_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+static mg_status capture(mg_ctx* c) {
+  if (c->gexec) return MG_OK;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  if (c->opt.precision == 0) emit_fp64_iteration(c, c->cap);
+  else emit_mixed_iteration(c, c->cap);
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (e != cudaSuccess) FAIL(MG_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  c->graph = g;
+  CK(cudaGraphInstantiate(&c->gexec, g, 0));
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  c->graph_kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    c->graph_kernels += t == cudaGraphNodeTypeKernel;
+  }
+  return MG_OK;
+}
+
+static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out,
+                            int conj) {
+  if (!rhs || !x) FAIL(MG_EINVAL, "rhs and x must be device pointers");
+  if (!(tol > 0)) FAIL(MG_EINVAL, "tol must be > 0");
+  cudaStream_t s = (cudaStream_t)c->opt.stream;
+  const Grid& g0 = c->lev[0].g;
+  const int B = c->B;
+  const bool mixed = c->opt.precision == 1;
+  mg_status st = capture(c);
+  if (st != MG_OK) return st;
+  launch_pack<double>(g0, (const double2*)rhs, c->v64[0].b, B, conj, s);
+  launch_pack<double>(g0, (const double2*)x, c->v64[0].x, B, conj, s);
+  int nblk = launch_vecnorm<double>(g0, c->v64[0].b, c->partial, B, s);
+  launch_norm_finish(c->partial, nblk, B, c->bnorm, s);
+  std::vector<double> bn(B);
+  CK(cudaMemcpyAsync(bn.data(), c->bnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // control arrays
+  std::vector<int> act(B), zero(B, 0);
+  std::vector<double> bsafe(B);
+  const double tolv[2] = {tol, 1e6};
+  int nact = 0;
+  for (int b = 0; b < B; ++b) {
+    act[b] = bn[b] > 0.0;
+    nact += act[b];
+    bsafe[b] = bn[b] > 0 ? bn[b] : 1.0;
+    if (bn[b] == 0.0) CK(cudaMemsetAsync(c->v64[0].x + (size_t)b * g0.vstride, 0, sizeof(double2) * g0.vstride, s));
+  }
+  std::vector<int> stt(B);
+  for (int b = 0; b < B; ++b) stt[b] = act[b] ? 0 : 1;
+  CK(cudaMemcpyAsync(c->active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->state, stt.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->cycles, zero.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->bnorm, bsafe.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->tolp, tolv, sizeof(double) * 2, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->n_active, &nact, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(c->relres, 0, sizeof(double) * B, s));
+  CK(cudaMemsetAsync(c->hist, 0, sizeof(double) * (size_t)c->hist_len * B, s));
+  // initial test on x0
+  if (mixed)
+    nblk = launch_resid_cast_norm(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->partial, B, c->active, s);
+  else
+    nblk = launch_resnorm<double>(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->partial, B, c->active, s);
+  launch_stop(c->partial, nblk, B, c->bnorm, c->tolp, c->active, c->state, c->cycles, c->relres, c->hist,
+              c->hist_len, c->n_active, 0, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int done = 0;
+  // direct launches: 2 pack + norm + finish + initial residual + stop + unpack
+  c->last_launches = 7;
+  c->last_graphs = 0;
+  while (*c->h_n_active > 0 && done < c->opt.max_cycles) {
+    CK(cudaGraphLaunch(c->gexec, s));
+    ++done;
+    c->last_graphs += 1;
+    c->last_launches += c->graph_kernels;
+    CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
+  std::vector<int> cyc(B);
+  std::vector<double> rr(B);
+  CK(cudaMemcpyAsync(stt.data(), c->state, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(cyc.data(), c->cycles, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rr.data(), c->relres, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  bool div = false, maxit = false;
+  for (int b = 0; b < B; ++b) {
+    if (cycles_out) cycles_out[b] = cyc[b];
+    if (relres_out) relres_out[b] = rr[b];
+    div |= stt[b] == 2;
+    maxit |= stt[b] == 0;
+  }
+  if (div) FAIL(MG_EDIVERGED, "relative residual diverged (> 1e6 or not finite)");
+  if (maxit) FAIL(MG_EMAXIT, "max_cycles (%d) reached before tol", c->opt.max_cycles);
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_handle h, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  return solve_impl(h, rhs, x, tol, cycles_out, relres_out, 0);
+}
+
+mg_status mg_adjoint(mg_handle h, const void* rhs_adj, void* lam, double tol, int* cycles_out, double* relres_out) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  return solve_impl(h, rhs_adj, lam, tol, cycles_out, relres_out, 1);
+}
+
+mg_status mg_gradient(mg_handle h, const void* u, const void* lam, int nsrc, const double* m, double omega_f,
+                      double* g) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  if (!u || !lam || !m || !g || nsrc < 1 || !(omega_f > 0)) FAIL(MG_EINVAL, "bad gradient arguments");
+  cudaStream_t s = (cudaStream_t)h->opt.stream;
+  launch_gradient(h->nx, h->ny, h->h, m, omega_f, (const double2*)u, (const double2*)lam, nsrc, g, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+mg_status mg_level_info(mg_handle h, int level, int* nx, int* ny, int* radius, int* nlevels) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  if (nlevels) *nlevels = h->nlev;
+  if (level < 0 || level >= h->nlev) FAIL(MG_EINVAL, "level %d out of range", level);
+  if (nx) *nx = h->lev[level].g.nx;
+  if (ny) *ny = h->lev[level].g.ny;
+  if (radius) *radius = h->lev[level].radius;
+  return MG_OK;
+}
+
+mg_status mg_apply(mg_handle h, int level, const void* x, void* y) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  if (level < 0 || level >= h->nlev || !x || !y) FAIL(MG_EINVAL, "bad mg_apply arguments");
+  cudaStream_t s = (cudaStream_t)h->opt.stream;
+  const Grid& g = h->lev[level].g;
+  const size_t bytes = sizeof(double2) * (size_t)g.vstride * h->B;
+  double2 *a = nullptr, *b = nullptr;
+  CK(cudaMalloc(&a, bytes));
+  cudaError_t e = cudaMalloc(&b, bytes);
+  if (e != cudaSuccess) { cudaFree(a); FAIL(MG_ENOMEM, "mg_apply scratch allocation failed"); }
+  cudaMemsetAsync(a, 0, bytes, s);
+  cudaMemsetAsync(b, 0, bytes, s);
+  launch_pack<double>(g, (const double2*)x, a, h->B, 0, s);
+  launch_apply<double>(g, op64(h, level), a, b, h->B, nullptr, s);
+  launch_unpack<double>(g, b, (double2*)y, h->B, 0, s);
+  e = cudaStreamSynchronize(s);
+  cudaFree(a);
+  cudaFree(b);
+  if (e != cudaSuccess) FAIL(MG_ECUDA, "mg_apply: %s", cudaGetErrorString(e));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_get_stencil(mg_handle h, int level, void* out) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  if (level < 0 || level >= h->nlev || !out) FAIL(MG_EINVAL, "bad mg_get_stencil arguments");
+  cudaStream_t s = (cudaStream_t)h->opt.stream;
+  launch_export_stencil(op64(h, level), h->lev[level].g.nx, h->lev[level].g.ny, h->lev[level].radius, (double2*)out,
+                        s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+mg_status mg_counters(mg_handle h, long long* kernel_launches, long long* graph_launches) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  if (kernel_launches) *kernel_launches = h->last_launches;
+  if (graph_launches) *graph_launches = h->last_graphs;
+  return MG_OK;
+}
+
+mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  if (what < 0 || what > 3 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
+  if (h->opt.precision == 1) return profile_t<float>(h, what, level, reps, ms, bytes);
+  return profile_t<double>(h, what, level, reps, ms, bytes);
+}
+
+mg_status mg_history(mg_handle h, double* hist, int cap) {
+  if (!h) FAIL(MG_EINVAL, "NULL handle");
+  if (!hist || cap < 1) FAIL(MG_EINVAL, "bad history buffer");
+  cudaStream_t s = (cudaStream_t)h->opt.stream;
+  std::vector<double> tmp((size_t)h->hist_len * h->B);
+  CK(cudaMemcpyAsync(tmp.data(), h->hist, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int b = 0; b < h->B; ++b)
+    for (int q = 0; q < cap; ++q) hist[(size_t)b * cap + q] = q < h->hist_len ? tmp[(size_t)b * h->hist_len + q] : 0.0;
+  return MG_OK;
+}
+
+}  // extern "C"

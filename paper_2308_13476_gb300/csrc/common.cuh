@@ -1,0 +1,170 @@
+// Shared device definitions of the helmmg library: padded grid layout,
+// complex arithmetic, the two operator kinds (matrix-free fine level, stored
+// Galerkin stencils) and deterministic block reductions.
+//
+// Layout of every grid vector: one (ny+1) x (nx+1) grid per right-hand side,
+// stored row-major with a zero halo of HALO nodes on every side, rows of
+// `pitch` elements (nx+1+2*HALO rounded up to a multiple of 4), RHS after RHS
+// `vstride` elements apart.  The halo is zero-filled at allocation and never
+// written, so stencils and transfers read neighbours without bounds tests.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hmg {
+
+constexpr int HALO = 4;
+constexpr int BX = 32;   // block shape of the node-parallel kernels
+constexpr int BY = 8;
+constexpr int MAXR = 3;  // largest Galerkin stencil radius (7 x 7)
+
+template <class T> struct cvec;
+template <> struct cvec<double> { using type = double2; };
+template <> struct cvec<float> { using type = float2; };
+template <class T> using cx = typename cvec<T>::type;
+
+template <class T> __host__ __device__ __forceinline__ cx<T> mk(T re, T im) {
+  cx<T> r; r.x = re; r.y = im; return r;
+}
+template <class T> __device__ __forceinline__ cx<T> add(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <class T> __device__ __forceinline__ cx<T> sub(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <class T> __device__ __forceinline__ cx<T> scl(T s, cx<T> a) { return mk<T>(s * a.x, s * a.y); }
+template <class T> __device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a + b*c
+template <class T> __device__ __forceinline__ cx<T> fma_c(cx<T> b, cx<T> c, cx<T> a) {
+  return mk<T>(fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y)));
+}
+// conj(a) * b
+template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <class T> __device__ __forceinline__ T abs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
+template <class T> __device__ __forceinline__ cx<T> cinv(cx<T> a) {
+  T d = a.x * a.x + a.y * a.y;
+  return mk<T>(a.x / d, -a.y / d);
+}
+template <class T, class U> __device__ __forceinline__ cx<T> cvt(cx<U> a) {
+  return mk<T>((T)a.x, (T)a.y);
+}
+
+// Geometry of one level's padded vectors.
+struct Grid {
+  int nx, ny;          // interval counts; nodes 0..nx, 0..ny
+  int pitch;           // padded row length (elements)
+  int rows;            // padded row count
+  long long vstride;   // elements per right-hand side
+  __host__ __device__ __forceinline__ long long at(int i, int j) const {
+    return (long long)(j + HALO) * pitch + (i + HALO);
+  }
+};
+
+// Fine-level (level 0) constants, written on the device by the setup kernel.
+// dinv[by*2+bx] = 1/(omega * A_PP) for constant k and the four boundary
+// classes (bx = node on a vertical boundary line, by = on a horizontal one).
+template <class T> struct Op0Consts {
+  T inv_h2, inv_h, k, k2, omega, beta2;
+  cx<T> dinv[4];
+};
+
+// Matrix-free fine-level operator: ghost-eliminated Sommerfeld rows scaled
+// by 1/2 (edge) and 1/4 (corner), Sec. 2 of the paper.  With wx = 1/2 on a
+// vertical boundary line (else 1) and wy likewise,
+//   (A x)_P = [4 wx wy x_P - wy (x_E + x_W) - wx (x_N + x_S)] / h^2
+//             - wx wy k_P^2 x_P - i (k_P / h)(bx wy + wx by) x_P
+// and halo nodes read as zero.
+template <class T> struct Op0 {
+  const Op0Consts<T>* c;
+  const T* kf;     // per-node k, dense (ny+1)*(nx+1), or null for constant k
+  int nx, ny;
+
+  __device__ __forceinline__ void geom(int i, int j, T& wx, T& wy, int& bx, int& by) const {
+    bx = (i == 0 || i == nx);
+    by = (j == 0 || j == ny);
+    wx = bx ? T(0.5) : T(1);
+    wy = by ? T(0.5) : T(1);
+  }
+  __device__ __forceinline__ T kval(int i, int j) const {
+    return kf ? kf[(long long)j * (nx + 1) + i] : c->k;
+  }
+  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, long long p, int pitch, int i, int j) const {
+    T wx, wy; int bx, by;
+    geom(i, j, wx, wy, bx, by);
+    const cx<T> xp = x[p];
+    const cx<T> xe = x[p + 1], xw = x[p - 1], xn = x[p + pitch], xs = x[p - pitch];
+    const T k = kval(i, j);
+    const T w = wx * wy;
+    cx<T> s = add<T>(scl<T>(wy, add<T>(xe, xw)), scl<T>(wx, add<T>(xn, xs)));
+    cx<T> lap = sub<T>(scl<T>(T(4) * w, xp), s);
+    T re = lap.x * c->inv_h2 - (w * (k * k)) * xp.x;
+    T im = lap.y * c->inv_h2 - (w * (k * k)) * xp.y;
+    const T sb = (k * c->inv_h) * (T(bx) * wy + wx * T(by));
+    // - i sb x_P = (sb x.im, -sb x.re)
+    return mk<T>(re + sb * xp.y, im - sb * xp.x);
+  }
+  __device__ __forceinline__ cx<T> diag_inv(int i, int j) const {
+    T wx, wy; int bx, by;
+    geom(i, j, wx, wy, bx, by);
+    if (!kf) return c->dinv[by * 2 + bx];
+    const T k = kval(i, j);
+    const T w = wx * wy;
+    const T dr = (T(4) * w) * c->inv_h2 - w * (k * k);
+    const T di = -(k * c->inv_h) * (T(bx) * wy + wx * T(by));
+    return cinv<T>(mk<T>(c->omega * dr, c->omega * di));
+  }
+};
+
+// Stored Galerkin stencil of radius R: st[e][j][i] (dense planes of
+// (ny+1)*(nx+1) nodes) with e = (dy+R)*(2R+1) + (dx+R) the coupling of node
+// (i,j) to node (i+dx, j+dy); dinv[j][i] = 1/(omega * centre entry).
+template <class T, int R> struct OpS {
+  const cx<T>* st;
+  const cx<T>* dinvp;
+  long long plane;
+  int nx, ny;
+  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, long long p, int pitch, int i, int j) const {
+    const long long q = (long long)j * (nx + 1) + i;
+    cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx) {
+        const int e = (dy + R) * (2 * R + 1) + (dx + R);
+        acc = fma_c<T>(st[e * plane + q], x[p + (long long)dy * pitch + dx], acc);
+      }
+    }
+    return acc;
+  }
+  __device__ __forceinline__ cx<T> diag_inv(int i, int j) const {
+    return dinvp[(long long)j * (nx + 1) + i];
+  }
+};
+
+// Block-wide sum of NV doubles; result valid in thread 0.  Fixed shape and
+// order, so results are bitwise reproducible run to run.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32] */) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[k * 32 + warp] = t;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = 0;
+      for (int w = 0; w < nwarps; ++w) t += sh[k * 32 + w];
+      v[k] = t;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace hmg

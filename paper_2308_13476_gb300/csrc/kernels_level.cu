@@ -1,0 +1,381 @@
+// Node-parallel kernels of one multigrid level: operator apply, residual,
+// weighted-Jacobi sweep, residual norms, Bezier restriction / prolongation,
+// layout conversion and the stopping test.
+//
+// Paper references: the operator is the 5-point discretisation of Sec. 2
+// (matrix-free on the fine level, Galerkin stencils below, Sec. 3); the
+// Jacobi sweep is S = I - X^{-1} A with X = omega * diag(A) (Sec. 3); the
+// transfers are Eq. (xex) and its transpose; the stopping test is the
+// relative residual of Sec. 5.
+#include <math.h>
+
+#include "internal.h"
+
+namespace hmg {
+
+// ------------------------------------------------------------------ helpers
+
+template <class T, class F>
+static void with_op(const OpView<T>& v, int nx, int ny, F&& f) {
+  if (v.kind == 1) {
+    Op0<T> op{v.c0, v.kf, nx, ny};
+    f(op);
+  } else if (v.kind == 2) {
+    OpS<T, 2> op{v.st, v.dinv, v.plane, nx, ny};
+    f(op);
+  } else {
+    OpS<T, 3> op{v.st, v.dinv, v.plane, nx, ny};
+    f(op);
+  }
+}
+
+static inline dim3 node_grid(const Grid& g, int B) {
+  return dim3(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY), B);
+}
+
+#define NODE_INDEX                                       \
+  const int rhs = blockIdx.z;                            \
+  const int i = blockIdx.x * BX + threadIdx.x;           \
+  const int j = blockIdx.y * BY + threadIdx.y;           \
+  const long long off = (long long)rhs * g.vstride;
+
+// ------------------------------------------------------------------ operator kernels
+
+template <class T, class Op>
+__global__ void __launch_bounds__(BX * BY) k_residual(Grid g, Op op, const cx<T>* __restrict__ x,
+                                                      const cx<T>* __restrict__ b, cx<T>* __restrict__ r,
+                                                      const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx || j > g.ny) return;
+  const long long p = g.at(i, j);
+  r[off + p] = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+}
+
+template <class T, class Op>
+__global__ void __launch_bounds__(BX * BY) k_apply(Grid g, Op op, const cx<T>* __restrict__ x,
+                                                   cx<T>* __restrict__ y, const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx || j > g.ny) return;
+  const long long p = g.at(i, j);
+  y[off + p] = op.apply(x + off, p, g.pitch, i, j);
+}
+
+// x_out = x + (omega diag A)^{-1} (b - A x)   (one weighted-Jacobi sweep)
+template <class T, class Op>
+__global__ void __launch_bounds__(BX * BY) k_jacobi(Grid g, Op op, const cx<T>* __restrict__ x,
+                                                    const cx<T>* __restrict__ b, cx<T>* __restrict__ xo,
+                                                    const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx || j > g.ny) return;
+  const long long p = g.at(i, j);
+  const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+  xo[off + p] = fma_c<T>(op.diag_inv(i, j), r, x[off + p]);
+}
+
+template <class T, class Op>
+__global__ void __launch_bounds__(BX * BY) k_resnorm(Grid g, Op op, const cx<T>* __restrict__ x,
+                                                     const cx<T>* __restrict__ b, double* __restrict__ partial,
+                                                     const int* __restrict__ active) {
+  __shared__ double sh[32];
+  NODE_INDEX
+  if (active && !active[rhs]) return;   // block-uniform
+  double v[1] = {0.0};
+  if (i <= g.nx && j <= g.ny) {
+    const long long p = g.at(i, j);
+    const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+    v[0] = (double)abs2<T>(r);
+  }
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0)
+    partial[(long long)rhs * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+}
+
+__global__ void __launch_bounds__(BX * BY) k_resid_cast_norm(Grid g, Op0<double> op, const double2* __restrict__ x,
+                                                             const double2* __restrict__ b, float2* __restrict__ r32,
+                                                             Grid g32, double* __restrict__ partial,
+                                                             const int* __restrict__ active) {
+  __shared__ double sh[32];
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  double v[1] = {0.0};
+  if (i <= g.nx && j <= g.ny) {
+    const long long p = g.at(i, j);
+    const double2 r = sub<double>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+    r32[(long long)rhs * g32.vstride + g32.at(i, j)] = make_float2((float)r.x, (float)r.y);
+    v[0] = abs2<double>(r);
+  }
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0)
+    partial[(long long)rhs * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+}
+
+__global__ void __launch_bounds__(BX * BY) k_update_mixed(Grid g, Grid g32, double2* __restrict__ x,
+                                                          const float2* __restrict__ e,
+                                                          const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx || j > g.ny) return;
+  const long long p = off + g.at(i, j);
+  const float2 d = e[(long long)rhs * g32.vstride + g32.at(i, j)];
+  double2 xv = x[p];
+  xv.x += (double)d.x;
+  xv.y += (double)d.y;
+  x[p] = xv;
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_vecnorm(Grid g, const cx<T>* __restrict__ v_, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  NODE_INDEX
+  double v[1] = {0.0};
+  if (i <= g.nx && j <= g.ny) v[0] = (double)abs2<T>(v_[off + g.at(i, j)]);
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0)
+    partial[(long long)rhs * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+}
+
+// ------------------------------------------------------------------ transfers
+
+// 1D weights of Eq. (xex) as a column stencil: fine offset a - 2J in -2..2.
+template <class T> __device__ __forceinline__ T bw(int d) {
+  return d == 0 ? T(0.75) : (d == 1 || d == -1) ? T(0.5) : T(0.125);
+}
+
+// r_c(I,J) = 1/4 sum_{a,b=-2..2} w(a) w(b) r_f(2I+a, 2J+b)   (R = P^T / 4)
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<T>* __restrict__ rf,
+                                                      cx<T>* __restrict__ rc, const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx || j > g.ny) return;
+  const cx<T>* f = rf + (long long)rhs * gf.vstride;
+  const long long pc = gf.at(2 * i, 2 * j);
+  cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+  for (int b = -2; b <= 2; ++b) {
+    const cx<T>* row = f + pc + (long long)b * gf.pitch;
+    cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
+    t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
+    t = add<T>(t, scl<T>(T(0.75), row[0]));
+    acc = add<T>(acc, scl<T>(bw<T>(b), t));
+  }
+  rc[off + g.at(i, j)] = scl<T>(T(0.25), acc);
+}
+
+// x_f(i,j) += sum_{I,J} P(i,I) P(j,J) e_c(I,J)   (Eq. (xex) in each direction)
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const cx<T>* __restrict__ ec,
+                                                         cx<T>* __restrict__ xf, const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx || j > g.ny) return;
+  const cx<T>* c = ec + (long long)rhs * gc.vstride;
+  const int I = i >> 1, J = j >> 1;
+  auto rowval = [&](int JJ) -> cx<T> {
+    const cx<T>* row = c + gc.at(I, JJ);
+    if (i & 1) return scl<T>(T(0.5), add<T>(row[0], row[1]));
+    return add<T>(scl<T>(T(0.125), add<T>(row[-1], row[1])), scl<T>(T(0.75), row[0]));
+  };
+  cx<T> v;
+  if (j & 1) {
+    v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
+  } else {
+    v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+  }
+  const long long p = off + g.at(i, j);
+  xf[p] = add<T>(xf[p], v);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_copy_masked(Grid g, const cx<T>* __restrict__ src, cx<T>* __restrict__ dst,
+                                                         const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx || j > g.ny) return;
+  const long long p = off + g.at(i, j);
+  dst[p] = src[p];
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_pack(Grid g, const double2* __restrict__ user, cx<T>* __restrict__ v, int conj) {
+  NODE_INDEX
+  if (i > g.nx || j > g.ny) return;
+  double2 u = user[((long long)rhs * (g.ny + 1) + j) * (g.nx + 1) + i];
+  if (conj) u.y = -u.y;
+  v[off + g.at(i, j)] = mk<T>((T)u.x, (T)u.y);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_unpack(Grid g, const cx<T>* __restrict__ v, double2* __restrict__ user, int conj) {
+  NODE_INDEX
+  if (i > g.nx || j > g.ny) return;
+  const cx<T> a = v[off + g.at(i, j)];
+  user[((long long)rhs * (g.ny + 1) + j) * (g.nx + 1) + i] = make_double2((double)a.x, conj ? -(double)a.y : (double)a.y);
+}
+
+// ------------------------------------------------------------------ stopping test
+
+__global__ void __launch_bounds__(256) k_stop(const double* __restrict__ partial, int nblk, const double* __restrict__ bnorm,
+                                              const double* __restrict__ tolp, int* active, int* state, int* cycles,
+                                              double* relres, double* hist, int hist_len, int* n_active, int count) {
+  __shared__ double sh[32];
+  const int rhs = blockIdx.x;
+  if (!active[rhs]) return;   // block-uniform
+  double v[1] = {0.0};
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) v[0] += partial[(long long)rhs * nblk + k];
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0) {
+    const double tol = tolp[0], diverge = tolp[1];
+    const double rr = sqrt(v[0]) / bnorm[rhs];
+    relres[rhs] = rr;
+    if (count) {
+      const int c = ++cycles[rhs];
+      if (c <= hist_len) hist[(long long)rhs * hist_len + c - 1] = rr;
+    }
+    int st = 0;
+    if (!(rr == rr) || rr > diverge) st = 2;      // NaN or divergence
+    else if (rr <= tol) st = 1;
+    if (st) {
+      state[rhs] = st;
+      active[rhs] = 0;
+      atomicSub(n_active, 1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_norm_finish(const double* __restrict__ partial, int nblk, double* out) {
+  __shared__ double sh[32];
+  const int rhs = blockIdx.x;
+  double v[1] = {0.0};
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) v[0] += partial[(long long)rhs * nblk + k];
+  block_sum<1>(v, sh);
+  if (threadIdx.x == 0) out[rhs] = sqrt(v[0]);
+}
+
+// ------------------------------------------------------------------ gradient
+
+// g = -Re sum_s conj(lam_s) (dA_pp/dm_p) u_s with
+// dA_pp/dm_p = -w_p omega_f^2 - i b_p omega_f / (2 h sqrt(m_p)).
+__global__ void k_gradient(int nx, int ny, double h, const double* __restrict__ m, double omega_f,
+                           const double2* __restrict__ u, const double2* __restrict__ lam, int nsrc,
+                           double* __restrict__ g) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i > nx || j > ny) return;
+  const long long q = (long long)j * (nx + 1) + i;
+  const long long N = (long long)(nx + 1) * (ny + 1);
+  const int bx = (i == 0 || i == nx), by = (j == 0 || j == ny);
+  const double wx = bx ? 0.5 : 1.0, wy = by ? 0.5 : 1.0;
+  const double bnd = bx * wy + wx * by;
+  const double2 da = make_double2(-wx * wy * omega_f * omega_f, -bnd * omega_f / (2.0 * h * sqrt(m[q])));
+  double acc = 0.0;
+  for (int s = 0; s < nsrc; ++s) {
+    const double2 t = cmul<double>(lam[s * N + q], mul<double>(da, u[s * N + q]));
+    acc += t.x;
+  }
+  g[q] = -acc;
+}
+
+// ------------------------------------------------------------------ launch wrappers
+
+template <class T>
+void launch_residual(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, cx<T>* r, int B,
+                     const int* active, cudaStream_t s) {
+  with_op<T>(v, g.nx, g.ny, [&](auto op) {
+    k_residual<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, r, active);
+  });
+}
+template <class T>
+void launch_apply(const Grid& g, const OpView<T>& v, const cx<T>* x, cx<T>* y, int B, const int* active,
+                  cudaStream_t s) {
+  with_op<T>(v, g.nx, g.ny, [&](auto op) { k_apply<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, y, active); });
+}
+template <class T>
+void launch_jacobi(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, cx<T>* xo, int B,
+                   const int* active, cudaStream_t s) {
+  with_op<T>(v, g.nx, g.ny, [&](auto op) {
+    k_jacobi<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, xo, active);
+  });
+}
+template <class T>
+int launch_resnorm(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, double* partial, int B,
+                   const int* active, cudaStream_t s) {
+  dim3 grd = node_grid(g, B);
+  with_op<T>(v, g.nx, g.ny, [&](auto op) {
+    k_resnorm<T, decltype(op)><<<grd, dim3(BX, BY), 0, s>>>(g, op, x, b, partial, active);
+  });
+  return grd.x * grd.y;
+}
+int launch_resid_cast_norm(const Grid& g, const OpView<double>& v, const double2* x, const double2* b, float2* r32,
+                           double* partial, int B, const int* active, cudaStream_t s) {
+  // r32 uses the same geometry as the FP64 level-0 vectors except the pitch
+  // may differ; the caller passes vectors of identical Grid, so reuse g.
+  dim3 grd = node_grid(g, B);
+  Op0<double> op{v.c0, v.kf, g.nx, g.ny};
+  k_resid_cast_norm<<<grd, dim3(BX, BY), 0, s>>>(g, op, x, b, r32, g, partial, active);
+  return grd.x * grd.y;
+}
+void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s) {
+  k_update_mixed<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, g, x, e, active);
+}
+template <class T>
+void launch_restrict(const Grid& gf, const Grid& gc, const cx<T>* rf, cx<T>* rc, int B, const int* active,
+                     cudaStream_t s) {
+  k_restrict<T><<<node_grid(gc, B), dim3(BX, BY), 0, s>>>(gf, gc, rf, rc, active);
+}
+template <class T>
+void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<T>* ec, cx<T>* xf, int B, const int* active,
+                        cudaStream_t s) {
+  k_prolong_add<T><<<node_grid(gf, B), dim3(BX, BY), 0, s>>>(gf, gc, ec, xf, active);
+}
+template <class T>
+void launch_copy_masked(const Grid& g, const cx<T>* src, cx<T>* dst, int B, const int* active, cudaStream_t s) {
+  k_copy_masked<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, src, dst, active);
+}
+template <class T> void launch_pack(const Grid& g, const double2* user, cx<T>* v, int B, int conj, cudaStream_t s) {
+  k_pack<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, user, v, conj);
+}
+template <class T> void launch_unpack(const Grid& g, const cx<T>* v, double2* user, int B, int conj, cudaStream_t s) {
+  k_unpack<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, v, user, conj);
+}
+template <class T> int launch_vecnorm(const Grid& g, const cx<T>* v, double* partial, int B, cudaStream_t s) {
+  dim3 grd = node_grid(g, B);
+  k_vecnorm<T><<<grd, dim3(BX, BY), 0, s>>>(g, v, partial);
+  return grd.x * grd.y;
+}
+void launch_stop(const double* partial, int nblk, int B, const double* bnorm, const double* tolp, int* active,
+                 int* state, int* cycles, double* relres, double* hist, int hist_len, int* n_active, int count,
+                 cudaStream_t s) {
+  k_stop<<<B, 256, 0, s>>>(partial, nblk, bnorm, tolp, active, state, cycles, relres, hist, hist_len, n_active,
+                           count);
+}
+void launch_norm_finish(const double* partial, int nblk, int B, double* out, cudaStream_t s) {
+  k_norm_finish<<<B, 256, 0, s>>>(partial, nblk, out);
+}
+void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u, const double2* lam,
+                     int nsrc, double* g, cudaStream_t s) {
+  k_gradient<<<dim3(cdiv(nx + 1, BX), cdiv(ny + 1, BY)), dim3(BX, BY), 0, s>>>(nx, ny, h, m, omega_f, u, lam, nsrc, g);
+}
+
+#define INST(T)                                                                                                   \
+  template void launch_residual<T>(const Grid&, const OpView<T>&, const cx<T>*, const cx<T>*, cx<T>*, int,         \
+                                   const int*, cudaStream_t);                                                      \
+  template void launch_apply<T>(const Grid&, const OpView<T>&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t); \
+  template void launch_jacobi<T>(const Grid&, const OpView<T>&, const cx<T>*, const cx<T>*, cx<T>*, int,           \
+                                 const int*, cudaStream_t);                                                        \
+  template int launch_resnorm<T>(const Grid&, const OpView<T>&, const cx<T>*, const cx<T>*, double*, int,          \
+                                 const int*, cudaStream_t);                                                        \
+  template void launch_restrict<T>(const Grid&, const Grid&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t); \
+  template void launch_prolong_add<T>(const Grid&, const Grid&, const cx<T>*, cx<T>*, int, const int*,            \
+                                      cudaStream_t);                                                               \
+  template void launch_copy_masked<T>(const Grid&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t);          \
+  template void launch_pack<T>(const Grid&, const double2*, cx<T>*, int, int, cudaStream_t);                      \
+  template void launch_unpack<T>(const Grid&, const cx<T>*, double2*, int, int, cudaStream_t);                    \
+  template int launch_vecnorm<T>(const Grid&, const cx<T>*, double*, int, cudaStream_t);
+INST(double)
+INST(float)
+
+}  // namespace hmg

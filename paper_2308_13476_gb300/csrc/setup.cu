@@ -1,0 +1,277 @@
+// Setup kernels: fine-level constants, Galerkin coarse operators
+// A_{l+1} = R_l C_l P_l (Sec. 3; coarsening on the CSL, Sec. 4), Jacobi
+// inverse diagonals, and the coarsest-grid direct solver (Sec. 5: coarsen
+// until fewer than 10 unknowns remain, solve there exactly).  All FP64.
+#include <math.h>
+
+#include "internal.h"
+
+namespace hmg {
+
+__device__ __forceinline__ double bwd(int d) {
+  return d == 0 ? 0.75 : (d == 1 || d == -1) ? 0.5 : (d == 2 || d == -2) ? 0.125 : 0.0;
+}
+
+// Coupling of node (i, j) to node (i+dx, j+dy) in a level operator; for the
+// matrix-free fine operator the mass term carries the shift (1 + i beta2).
+__device__ double2 op_coef(const OpView<double>& v, int nx, int ny, int i, int j, int dy, int dx, double beta2) {
+  const int i2 = i + dx, j2 = j + dy;
+  if (i2 < 0 || i2 > nx || j2 < 0 || j2 > ny) return make_double2(0, 0);
+  if (v.kind != 1) {
+    const int r = v.kind;
+    if (dx < -r || dx > r || dy < -r || dy > r) return make_double2(0, 0);
+    const int e = (dy + r) * (2 * r + 1) + (dx + r);
+    return v.st[e * v.plane + (long long)j * (nx + 1) + i];
+  }
+  const Op0Consts<double>* c = v.c0;
+  const int bx = (i == 0 || i == nx), by = (j == 0 || j == ny);
+  const double wx = bx ? 0.5 : 1.0, wy = by ? 0.5 : 1.0, w = wx * wy;
+  const double k = v.kf ? v.kf[(long long)j * (nx + 1) + i] : c->k;
+  if (dx == 0 && dy == 0) {
+    const double k2 = k * k;
+    return make_double2(4.0 * w * c->inv_h2 - w * k2, -w * (beta2 * k2) - (k * c->inv_h) * (bx * wy + wx * by));
+  }
+  if (dy == 0 && (dx == 1 || dx == -1)) return make_double2(-wy * c->inv_h2, 0);
+  if (dx == 0 && (dy == 1 || dy == -1)) return make_double2(-wx * c->inv_h2, 0);
+  return make_double2(0, 0);
+}
+
+__global__ void s_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, double k, double omega,
+                            double beta2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Op0Consts<double> c;
+  c.inv_h2 = 1.0 / (h * h);
+  c.inv_h = 1.0 / h;
+  c.k = k;
+  c.k2 = k * k;
+  c.omega = omega;
+  c.beta2 = beta2;
+  for (int by = 0; by < 2; ++by)
+    for (int bx = 0; bx < 2; ++bx) {
+      const double wx = bx ? 0.5 : 1.0, wy = by ? 0.5 : 1.0, w = wx * wy;
+      const double dr = 4.0 * w * c.inv_h2 - w * (k * k);
+      const double di = -(k * c.inv_h) * (bx * wy + wx * by);
+      const double2 d = make_double2(omega * dr, omega * di);
+      const double dd = d.x * d.x + d.y * d.y;
+      c.dinv[by * 2 + bx] = make_double2(d.x / dd, -d.y / dd);
+    }
+  *c64 = c;
+  if (c32) {
+    Op0Consts<float> f;
+    f.inv_h2 = (float)c.inv_h2;
+    f.inv_h = (float)c.inv_h;
+    f.k = (float)c.k;
+    f.k2 = (float)c.k2;
+    f.omega = (float)c.omega;
+    f.beta2 = (float)c.beta2;
+    for (int q = 0; q < 4; ++q) f.dinv[q] = make_float2((float)c.dinv[q].x, (float)c.dinv[q].y);
+    *c32 = f;
+  }
+}
+
+// One thread per (coarse node, stencil entry):
+// A_c[(I,J),(I2,J2)] = sum 1/4 w(fa-2I) w(fb-2J) * A_f[(fa,fb),(fa2,fb2)] * w(fa2-2I2) w(fb2-2J2)
+__global__ void s_galerkin(OpView<double> fine, int fnx, int fny, int rf, double2* __restrict__ cst, int cnx, int cny,
+                           int rc, double beta2) {
+  const int S = (2 * rc + 1) * (2 * rc + 1);
+  const long long plane = (long long)(cnx + 1) * (cny + 1);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= plane * S) return;
+  const int e = (int)(idx % S);
+  const long long q = idx / S;
+  const int I = (int)(q % (cnx + 1)), J = (int)(q / (cnx + 1));
+  const int dy = e / (2 * rc + 1) - rc, dx = e % (2 * rc + 1) - rc;
+  const int I2 = I + dx, J2 = J + dy;
+  double2 acc = make_double2(0, 0);
+  if (I2 >= 0 && I2 <= cnx && J2 >= 0 && J2 <= cny) {
+    for (int b = -2; b <= 2; ++b) {
+      const int fb = 2 * J + b;
+      if (fb < 0 || fb > fny) continue;
+      for (int a = -2; a <= 2; ++a) {
+        const int fa = 2 * I + a;
+        if (fa < 0 || fa > fnx) continue;
+        const double wr = 0.25 * bwd(a) * bwd(b);
+        for (int b2 = -2; b2 <= 2; ++b2) {
+          const int fb2 = 2 * J2 + b2;
+          const int ey = fb2 - fb;
+          if (fb2 < 0 || fb2 > fny || ey < -rf || ey > rf) continue;
+          for (int a2 = -2; a2 <= 2; ++a2) {
+            const int fa2 = 2 * I2 + a2;
+            const int ex = fa2 - fa;
+            if (fa2 < 0 || fa2 > fnx || ex < -rf || ex > rf) continue;
+            const double2 cf = op_coef(fine, fnx, fny, fa, fb, ey, ex, beta2);
+            const double wgt = wr * bwd(a2) * bwd(b2);
+            acc.x += wgt * cf.x;
+            acc.y += wgt * cf.y;
+          }
+        }
+      }
+    }
+  }
+  cst[e * plane + q] = acc;
+}
+
+__global__ void s_diaginv(const double2* __restrict__ st, int rc, long long plane, double omega, double2* __restrict__ dinv) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= plane) return;
+  const int ec = rc * (2 * rc + 1) + rc;
+  const double2 d = st[ec * plane + q];
+  const double2 x = make_double2(omega * d.x, omega * d.y);
+  const double dd = x.x * x.x + x.y * x.y;
+  dinv[q] = make_double2(x.x / dd, -x.y / dd);
+}
+
+__global__ void s_to_float(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) b[q] = make_float2((float)a[q].x, (float)a[q].y);
+}
+__global__ void s_to_float_real(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) b[q] = (float)a[q];
+}
+
+__global__ void s_dense(OpView<double> v, int nx, int ny, double2* __restrict__ M) {
+  const long long N = (long long)(nx + 1) * (ny + 1);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * N) return;
+  const long long r = idx / N, c = idx % N;
+  const int i = (int)(r % (nx + 1)), j = (int)(r / (nx + 1));
+  const int i2 = (int)(c % (nx + 1)), j2 = (int)(c / (nx + 1));
+  const int R = v.kind == 1 ? 1 : v.kind;
+  const int dx = i2 - i, dy = j2 - j;
+  double2 val = make_double2(0, 0);
+  if (dx >= -R && dx <= R && dy >= -R && dy <= R) val = op_coef(v, nx, ny, i, j, dy, dx, 0.0);
+  M[idx] = val;
+}
+
+__global__ void s_export(OpView<double> v, int nx, int ny, int r, double2* __restrict__ out) {
+  const int S = (2 * r + 1) * (2 * r + 1);
+  const long long plane = (long long)(nx + 1) * (ny + 1);
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= plane * S) return;
+  const long long q = idx / S;
+  const int e = (int)(idx % S);
+  const int i = (int)(q % (nx + 1)), j = (int)(q / (nx + 1));
+  const int dy = e / (2 * r + 1) - r, dx = e % (2 * r + 1) - r;
+  out[idx] = op_coef(v, nx, ny, i, j, dy, dx, 0.0);
+}
+
+// In-place Gauss-Jordan with partial pivoting, one block: inv = M^{-1}.
+// fac: dynamic shared memory, N double2.  status[0] = 1 on a zero pivot.
+__global__ void s_gauss_jordan(double2* __restrict__ M, double2* __restrict__ inv, int N, int* status) {
+  extern __shared__ double2 fac[];
+  __shared__ int piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (long long q = tid; q < (long long)N * N; q += nt) {
+    const long long r = q / N, c = q % N;
+    inv[q] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    if (tid == 0) {
+      int p = k;
+      double best = -1.0;
+      for (int r = k; r < N; ++r) {
+        const double2 a = M[(long long)r * N + k];
+        const double m = a.x * a.x + a.y * a.y;
+        if (m > best) { best = m; p = r; }
+      }
+      piv = p;
+      if (best == 0.0) status[0] = 1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k) {
+      for (int c = tid; c < N; c += nt) {
+        double2 t = M[(long long)k * N + c]; M[(long long)k * N + c] = M[(long long)p * N + c]; M[(long long)p * N + c] = t;
+        t = inv[(long long)k * N + c]; inv[(long long)k * N + c] = inv[(long long)p * N + c]; inv[(long long)p * N + c] = t;
+      }
+    }
+    __syncthreads();
+    const double2 d = M[(long long)k * N + k];
+    const double dd = d.x * d.x + d.y * d.y;
+    const double2 di = dd > 0 ? make_double2(d.x / dd, -d.y / dd) : make_double2(0, 0);
+    __syncthreads();
+    for (int c = tid; c < N; c += nt) {
+      M[(long long)k * N + c] = mul<double>(di, M[(long long)k * N + c]);
+      inv[(long long)k * N + c] = mul<double>(di, inv[(long long)k * N + c]);
+    }
+    for (int r = tid; r < N; r += nt) fac[r] = M[(long long)r * N + k];
+    __syncthreads();
+    for (long long q = tid; q < (long long)N * N; q += nt) {
+      const int r = (int)(q / N), c = (int)(q % N);
+      if (r == k) continue;
+      const double2 f = fac[r];
+      M[q] = sub<double>(M[q], mul<double>(f, M[(long long)k * N + c]));
+      inv[q] = sub<double>(inv[q], mul<double>(f, inv[(long long)k * N + c]));
+    }
+    __syncthreads();
+  }
+}
+
+// e = A_coarsest^{-1} r, one block per RHS, FP64 arithmetic.
+template <class T>
+__global__ void s_coarse_solve(Grid g, const double2* __restrict__ inv, int N, const cx<T>* __restrict__ r,
+                               cx<T>* __restrict__ e, const int* __restrict__ active) {
+  extern __shared__ double2 rs[];
+  const int rhs = blockIdx.x;
+  if (active && !active[rhs]) return;
+  const long long off = (long long)rhs * g.vstride;
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    const int i = q % (g.nx + 1), j = q / (g.nx + 1);
+    const cx<T> a = r[off + g.at(i, j)];
+    rs[q] = make_double2((double)a.x, (double)a.y);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    double2 acc = make_double2(0, 0);
+    const double2* row = inv + (long long)q * N;
+    for (int c = 0; c < N; ++c) acc = fma_c<double>(row[c], rs[c], acc);
+    const int i = q % (g.nx + 1), j = q / (g.nx + 1);
+    e[off + g.at(i, j)] = mk<T>((T)acc.x, (T)acc.y);
+  }
+}
+
+// ------------------------------------------------------------------ wrappers
+
+void launch_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, double k, double omega, double beta2,
+                      cudaStream_t s) {
+  s_op0consts<<<1, 32, 0, s>>>(c64, c32, h, k, omega, beta2);
+}
+void launch_galerkin(const OpView<double>& fine, int fnx, int fny, double2* cst, int cnx, int cny, int rc, double beta2,
+                     cudaStream_t s) {
+  const int rf = fine.kind == 1 ? 1 : fine.kind;
+  const long long n = (long long)(cnx + 1) * (cny + 1) * (2 * rc + 1) * (2 * rc + 1);
+  s_galerkin<<<cdiv(n, 128), 128, 0, s>>>(fine, fnx, fny, rf, cst, cnx, cny, rc, beta2);
+}
+void launch_diaginv(const double2* st, int rc, long long plane, double omega, double2* dinv, cudaStream_t s) {
+  s_diaginv<<<cdiv(plane, 256), 256, 0, s>>>(st, rc, plane, omega, dinv);
+}
+void launch_to_float(const double2* src, float2* dst, long long n, cudaStream_t s) {
+  if (n > 0) s_to_float<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+}
+void launch_to_float_real(const double* src, float* dst, long long n, cudaStream_t s) {
+  if (n > 0) s_to_float_real<<<cdiv(n, 256), 256, 0, s>>>(src, dst, n);
+}
+void launch_dense(const OpView<double>& op, int nx, int ny, double2* M, cudaStream_t s) {
+  const long long N = (long long)(nx + 1) * (ny + 1);
+  s_dense<<<cdiv(N * N, 256), 256, 0, s>>>(op, nx, ny, M);
+}
+void launch_gauss_jordan(double2* M, double2* inv, int N, int* status, cudaStream_t s) {
+  s_gauss_jordan<<<1, 256, (size_t)N * sizeof(double2), s>>>(M, inv, N, status);
+}
+void launch_export_stencil(const OpView<double>& op, int nx, int ny, int r, double2* out, cudaStream_t s) {
+  const long long n = (long long)(nx + 1) * (ny + 1) * (2 * r + 1) * (2 * r + 1);
+  s_export<<<cdiv(n, 256), 256, 0, s>>>(op, nx, ny, r, out);
+}
+template <class T>
+void launch_coarse_solve(const Grid& g, const double2* inv, int N, const cx<T>* r, cx<T>* e, int B, const int* active,
+                         cudaStream_t s) {
+  s_coarse_solve<T><<<B, 128, (size_t)N * sizeof(double2), s>>>(g, inv, N, r, e, active);
+}
+template void launch_coarse_solve<double>(const Grid&, const double2*, int, const double2*, double2*, int, const int*,
+                                          cudaStream_t);
+template void launch_coarse_solve<float>(const Grid&, const double2*, int, const float2*, float2*, int, const int*,
+                                         cudaStream_t);
+
+}  // namespace hmg

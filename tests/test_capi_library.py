@@ -1,0 +1,54 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads,
+and exports every entry point that include/helmmg.h declares.  No compute
+calls are made (no GPU here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "helmmg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2308_13476_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mg_setup", "mg_solve", "mg_adjoint", "mg_gradient", "mg_destroy", "mg_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    import paper_2308_13476_gb300 as hm
+    assert sorted(hm.EXPORTED) == declared_functions()
+
+
+def test_default_options_and_error_paths_without_gpu(lib_path):
+    import paper_2308_13476_gb300 as hm
+    o = hm.mg_default_options()
+    assert (o.cycle, o.smoother, o.nu_pre, o.nu_post, o.omega, o.precision) == (1, 0, 1, 1, 4.5, 0)
+    assert (o.max_cycles, o.min_coarse, o.batch) == (10000, 10, 1)
+    lib = hm.load_library()
+    h = ctypes.c_void_p()
+    # argument validation happens before any device call
+    st = lib.mg_setup(ctypes.byref(h), 1, 8, 0.1, None, 5.0, 0.7, 0, ctypes.byref(o))
+    assert st == hm.MG_EINVAL and h.value is None
+    assert b"nx, ny >= 2" in lib.mg_last_error()
+    assert lib.mg_destroy(None) == hm.MG_OK

@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Bars: FP64 operators and Galerkin stencils to 1e-13 relative (max norm),
+FP64 iterates to 1e-10 relative at every checked cycle with identical cycle
+counts, the mixed path to 1e-6 relative of the FP64 oracle solution.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cycle as ocycle
+from oracle import gradient as ograd
+from oracle import hierarchy as ohier
+from oracle import problem as oprob
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU runner deselects -m gpu anyway
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2308_13476_gb300 as hm  # noqa: E402
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def opts(smoother):
+    return hm.SMOOTHERS[smoother]
+
+
+# ------------------------------------------------------------------ operators
+
+
+@pytest.mark.parametrize("nx,ny,kvar", [(32, 32, False), (40, 24, True), (10, 6, False)])
+def test_operators_and_galerkin_stencils(nx, ny, kvar):
+    h = 1.0 / 32
+    k = synth.k_field(synth.chi_sharp(nx, ny, 7), 10.0, 20.0) if kvar else 20.0
+    H = ohier.build_hierarchy(nx, ny, h, k, 0.7)
+    s = hm.Solver(nx, ny, h, dev(k, torch.float64) if kvar else k, 0.7)
+    assert s.nlevels == H.nlevels
+    for l, (cx_, cy_) in enumerate(H.sizes):
+        gnx, gny, r, _ = s.level_info(l)
+        assert (gnx, gny) == (cx_, cy_)
+        x = synth.random_complex((cy_ + 1, cx_ + 1), 100 + l)
+        y = host(s.apply(l, dev(x)[None]))[0]
+        ref = (H.A[l] @ x.ravel()).reshape(x.shape)
+        assert rel(y, ref) <= 1e-13, l
+        S = host(s.stencil(l))
+        So = ohier.stencil_of(H.A[l], cx_, cy_, r)
+        assert np.abs(S - So).max() <= 1e-13 * np.abs(So).max(), l
+    s.close()
+
+
+# ------------------------------------------------------------------ iterates
+
+
+def _oracle_run(nx, ny, h, k, beta2, opt, b, tol, keep=True, levels=0, max_cycles=10000):
+    H = ohier.build_hierarchy(nx, ny, h, k, beta2, levels=levels)
+    return ocycle.mg_solve(H, b.ravel(), tol, opt, keep_iterates=keep, max_cycles=max_cycles)
+
+
+CASES = [
+    # (name, nx, ny, k, beta2, smoother, gamma, nu_pre, nu_post, tol)
+    ("cfg1_jacobi_V11", 32, 32, 20.0, 0.7, "jacobi", 1, 1, 1, 1e-6),
+    ("jacobi_W22", 32, 32, 20.0, 0.7, "jacobi", 2, 2, 2, 1e-6),
+    ("jacobi_V21_odd", 40, 40, 25.0, 0.7, "jacobi", 1, 2, 1, 1e-6),
+    ("gmres_V11_shift1k", 64, 64, 40.0, 1 / 40.0, "gmres3", 1, 1, 1, 1e-6),
+    ("gmres_W22", 48, 48, 30.0, 1 / 30.0, "gmres3", 2, 2, 2, 1e-8),
+    ("gmres_V11_shift0", 32, 32, 20.0, 0.0, "gmres3", 1, 1, 1, 1e-6),
+    ("rect_jacobi", 56, 24, 20.0, 0.7, "jacobi", 1, 2, 2, 1e-6),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp64_iterates_and_cycle_counts(case):
+    name, nx, ny, k, beta2, sm, gamma, n1, n2, tol = case
+    h = 1.0 / max(nx, ny)
+    b = synth.point_source(nx, ny, h)
+    opt = ocycle.CycleOptions(gamma, sm, n1, n2, 4.5)
+    ref = _oracle_run(nx, ny, h, k, beta2, opt, b, tol)
+    assert ref.converged
+    s = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2)
+    x, st, cyc, rr = s.solve(dev(b), tol=tol)
+    assert st == hm.MG_OK
+    assert cyc[0] == ref.cycles
+    assert rel(host(x)[0], ref.x) <= 1e-10
+    hist = np.array(s.history(ref.cycles)[0])
+    assert np.allclose(hist, ref.history, rtol=1e-9, atol=0)
+    # iterates after a few intermediate cycle counts
+    for m in sorted({1, 2, ref.cycles // 2}):
+        s2 = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, max_cycles=m)
+        xm, st2, cm, _ = s2.solve(dev(b), tol=tol)
+        assert st2 == hm.MG_EMAXIT and cm[0] == m
+        assert rel(host(xm)[0], ref.iterates[m - 1]) <= 1e-10, m
+        s2.close()
+    s.close()
+
+
+def test_variable_k_iterates():
+    nx = ny = 40
+    h = 1.0 / 40
+    k = synth.k_field(synth.chi_smooth(nx, ny, 3), 10.0, 25.0)
+    b = synth.point_source(nx, ny, h)
+    opt = ocycle.CycleOptions(1, "gmres3", 1, 1, 4.5)
+    ref = _oracle_run(nx, ny, h, k, 1 / 25.0, opt, b, 1e-7)
+    s = hm.Solver(nx, ny, h, dev(k, torch.float64), 1 / 25.0, smoother="gmres3")
+    x, st, cyc, _ = s.solve(dev(b), tol=1e-7)
+    assert st == hm.MG_OK and cyc[0] == ref.cycles
+    assert rel(host(x)[0], ref.x) <= 1e-10
+
+
+def test_batch_each_rhs_matches_oracle():
+    nx = ny = 32
+    h = 1.0 / 32
+    srcs = synth.source_row(nx, ny, h, 3)
+    srcs[2] = synth.random_complex((ny + 1, nx + 1), 5)
+    H = ohier.build_hierarchy(nx, ny, h, 20.0, 0.7)
+    opt = ocycle.CycleOptions(1, "jacobi", 1, 1, 4.5)
+    refs = [ocycle.mg_solve(H, srcs[q].ravel(), 1e-6, opt) for q in range(3)]
+    s = hm.Solver(nx, ny, h, 20.0, 0.7, batch=3)
+    x, st, cyc, rr = s.solve(dev(srcs), tol=1e-6)
+    assert st == hm.MG_OK
+    for q in range(3):
+        assert cyc[q] == refs[q].cycles
+        assert rel(host(x)[q], refs[q].x) <= 1e-10
+
+
+def test_mixed_precision_against_fp64_oracle():
+    # complex64 cycles inside FP64 refinement: the FP64 residual of the
+    # returned x meets tol, and driven to 1e-10 the solution agrees with the
+    # FP64 oracle's to 1e-6 relative.
+    nx = ny = 64
+    h = 1.0 / 64
+    k = 40.0
+    b = synth.point_source(nx, ny, h)
+    opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
+    H = ohier.build_hierarchy(nx, ny, h, k, 1 / k)
+    ref = ocycle.mg_solve(H, b.ravel(), 1e-12, opt)
+    for sm, beta2 in (("gmres3", 1 / k), ("jacobi", 0.7)):
+        s = hm.Solver(nx, ny, h, k, beta2, smoother=sm, nu_pre=2, nu_post=2, precision="mixed")
+        x, st, cyc, rr = s.solve(dev(b), tol=1e-6)
+        assert st == hm.MG_OK and rr[0] <= 1e-6
+        r = b.ravel() - H.A[0] @ host(x)[0].ravel()
+        assert abs(np.linalg.norm(r) / np.linalg.norm(b) - rr[0]) <= 1e-3 * rr[0]
+        x, st, cyc, rr = s.solve(dev(b), tol=1e-10)
+        assert st == hm.MG_OK
+        assert rel(host(x)[0], ref.x) <= 1e-6
+        s.close()
+
+
+def test_adjoint_solves_hermitian_system():
+    nx = ny = 32
+    h = 1.0 / 32
+    g = synth.random_complex((ny + 1, nx + 1), 11)
+    A = oprob.helmholtz_matrix(nx, ny, h, 20.0)
+    s = hm.Solver(nx, ny, h, 20.0, 1 / 20.0, smoother="gmres3", nu_pre=2, nu_post=2)
+    lam, st, cyc, rr = s.adjoint(dev(g), tol=1e-10)
+    assert st == hm.MG_OK
+    lam = host(lam)[0].ravel()
+    r = g.ravel() - A.conj().T @ lam
+    assert np.linalg.norm(r) / np.linalg.norm(g) <= 1e-10
+
+
+def test_gradient_kernel_matches_oracle_formula():
+    nx = ny = 24
+    h = 20.0
+    omega_f = 2 * np.pi * 4.0
+    m = (1.0 / 2000.0**2) * (1 + 0.1 * synth.smooth_perturbation(nx, ny, 2, 4.0))
+    u = synth.random_complex((3, ny + 1, nx + 1), 1)
+    lam = synth.random_complex((3, ny + 1, nx + 1), 2)
+    dA = ograd.diag_derivative(nx, ny, h, m, omega_f)
+    ref = -np.real(np.sum(np.conj(lam) * dA[None] * u, axis=0))
+    s = hm.Solver(nx, ny, h, dev(omega_f * np.sqrt(m), torch.float64), 0.0)
+    g = host(s.gradient(dev(u), dev(lam), dev(m, torch.float64), omega_f))
+    assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ edge cases
+
+
+def test_zero_rhs_and_direct_levels():
+    nx = ny = 8
+    h = 1.0 / 8
+    s = hm.Solver(nx, ny, h, 5.0, 0.7)
+    x0 = dev(synth.random_complex((1, ny + 1, nx + 1), 3))
+    x, st, cyc, rr = s.solve(dev(np.zeros((1, ny + 1, nx + 1))), x=x0, tol=1e-6)
+    assert st == hm.MG_OK and cyc[0] == 0 and np.abs(host(x)).max() == 0.0
+    # one level: the cycle is the direct solve, one cycle reaches any tol
+    b = synth.point_source(nx, ny, h)
+    s1 = hm.Solver(nx, ny, h, 5.0, 0.7, levels=1)
+    x, st, cyc, rr = s1.solve(dev(b), tol=1e-12)
+    A = oprob.helmholtz_matrix(nx, ny, h, 5.0).toarray()
+    assert st == hm.MG_OK and cyc[0] == 1
+    assert rel(host(x)[0].ravel(), np.linalg.solve(A, b.ravel())) <= 1e-12
+
+
+def test_divergence_reported_not_hung():
+    # kh > 0.625 with Jacobi (excluded in Table tabhind): the oracle diverges,
+    # the library must return MG_EDIVERGED after the same number of cycles.
+    nx = ny = 16
+    h = 1.0 / 16
+    k = 30.0
+    b = synth.point_source(nx, ny, h)
+    opt = ocycle.CycleOptions(1, "jacobi", 1, 1, 4.5)
+    ref = _oracle_run(nx, ny, h, k, 0.7, opt, b, 1e-6, keep=False, max_cycles=5000)
+    s = hm.Solver(nx, ny, h, k, 0.7, max_cycles=5000)
+    x, st, cyc, rr = s.solve(dev(b), tol=1e-6)
+    if ref.diverged:
+        assert st == hm.MG_EDIVERGED and cyc[0] == ref.cycles
+    else:
+        assert st in (hm.MG_OK, hm.MG_EMAXIT) and cyc[0] == ref.cycles
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(hm.HelmmgError):
+        hm.Solver(7, 8, 0.1, 5.0, 0.7, levels=0, cycle=1, nu_pre=-1)
+    with pytest.raises(hm.HelmmgError):
+        hm.Solver(1, 8, 0.1, 5.0, 0.7)
+    with pytest.raises(hm.HelmmgError):
+        hm.Solver(8, 8, -0.1, 5.0, 0.7)
+    # coarsest grid too large for the direct solver
+    with pytest.raises(hm.HelmmgError):
+        hm.Solver(63, 63, 0.1, 5.0, 0.7)
