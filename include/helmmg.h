@@ -78,11 +78,13 @@ typedef struct {
   int max_cycles;   /* cap on cycles (refinement steps for precision 1)       */
   int min_coarse;   /* stop coarsening below this many grid nodes (Sec. 5: 10) */
   int batch;        /* B: right-hand sides solved together                      */
+  int coarse_nodes; /* levels with at most this many grid nodes (and all below
+                       them) run as one CTA per RHS per visit; 0 = never      */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
- * min_coarse 10, batch 1, default stream. */
+ * min_coarse 10, batch 1; coarse_nodes 1100; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).

@@ -40,7 +40,7 @@ class MgOptions(ctypes.Structure):
     _fields_ = [("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("coarse_nodes", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -206,18 +206,21 @@ class Solver:
 
     Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
            nu_pre, nu_post, omega, precision="fp64"|"mixed", batch, levels,
-           max_cycles, min_coarse, stream)
+           max_cycles, min_coarse, coarse_nodes, stream)
     ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
     """
 
     def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
-                 precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, stream=None):
+                 precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, coarse_nodes=None,
+                 stream=None):
         o = mg_default_options()
         o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
         o.smoother = SMOOTHERS[smoother]
         o.nu_pre, o.nu_post, o.omega = int(nu_pre), int(nu_post), float(omega)
         o.precision = PRECISIONS[precision]
         o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
+        if coarse_nodes is not None:
+            o.coarse_nodes = int(coarse_nodes)
         o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         self.nx, self.ny, self.h, self.batch = nx, ny, h, batch
         if isinstance(k, (int, float)):

@@ -42,12 +42,25 @@ template <class T> struct LevelVec {
   GmresBufs gb{};
 };
 
+template <class T> struct CoarsePlan {
+  CLevel<T>* levels = nullptr;   // device, one per level
+  CStep* steps = nullptr;        // device
+  int nsteps = 0;
+};
+
 struct Level {
   Grid g;
   int radius;                 // 1 on level 0 (matrix free), 2, then 3
-  double2* st = nullptr;      // FP64 Galerkin stencil, levels >= 1
+  int kind = 1;               // OpView kind of the level's operator
+  double2* st = nullptr;      // FP64 Galerkin stencil (variable k), levels >= 1
   double2* dinv = nullptr;
   long long plane = 0;
+  // constant k: Kronecker factors [n+1][2r+1] (FP64 and float copies)
+  double2 *gx = nullptr, *hy = nullptr;
+  double *wx = nullptr, *wy = nullptr;
+  float2 *gx32 = nullptr, *hy32 = nullptr;
+  float *wx32 = nullptr, *wy32 = nullptr;
+  float2* dinv32 = nullptr;
 };
 
 }  // namespace
@@ -65,6 +78,7 @@ struct mg_ctx {
   float* kf32 = nullptr;
   double2* cinv = nullptr;
   double* partial = nullptr;
+  unsigned* tickets = nullptr;
   double* gst = nullptr;   // GMRES scalars
   int* active = nullptr;
   int* state = nullptr;
@@ -81,6 +95,9 @@ struct mg_ctx {
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   std::vector<void*> allocs;
+  int lc = 1 << 30;                  // first level run by the coarse-cycle interpreter
+  CoarsePlan<double> plan64;
+  CoarsePlan<float> plan32;
   long long graph_kernels = 0;     // kernel nodes in the cycle graph
   long long last_launches = 0, last_graphs = 0;
 
@@ -114,30 +131,38 @@ static Grid make_grid(int nx, int ny, int B) {
 
 static OpView<double> op64(const mg_ctx* c, int l) {
   OpView<double> v{};
+  const Level& L = c->lev[l];
+  v.kind = L.kind;
   if (l == 0) {
-    v.kind = 1;
     v.c0 = c->c0d;
     v.kf = c->kf64;
   } else {
-    v.kind = c->lev[l].radius;
-    v.st = c->lev[l].st;
-    v.dinv = c->lev[l].dinv;
-    v.plane = c->lev[l].plane;
+    v.st = L.st;
+    v.dinv = L.dinv;
+    v.plane = L.plane;
+    v.gx = L.gx;
+    v.wx = L.wx;
+    v.hy = L.hy;
+    v.wy = L.wy;
   }
   return v;
 }
 
 static OpView<float> op32(const mg_ctx* c, int l) {
   OpView<float> v{};
+  const Level& L = c->lev[l];
+  v.kind = L.kind;
   if (l == 0) {
-    v.kind = 1;
     v.c0 = c->c0f;
     v.kf = c->kf32;
   } else {
-    v.kind = c->lev[l].radius;
     v.st = c->v32[l].st;
-    v.dinv = c->v32[l].dinv;
-    v.plane = c->lev[l].plane;
+    v.dinv = L.kind >= 4 ? L.dinv32 : c->v32[l].dinv;
+    v.plane = L.plane;
+    v.gx = L.gx32;
+    v.wx = L.wx32;
+    v.hy = L.hy32;
+    v.wy = L.wy32;
   }
   return v;
 }
@@ -157,10 +182,11 @@ template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, c
   if ((e = dalloc(c, (void**)&v.t, bytes))) return e;
   if ((e = dalloc(c, (void**)&v.r, bytes))) return e;
   if (gmres) {
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 3; ++q)
       if ((e = dalloc(c, &v.gb.u[q], bytes))) return e;
     if ((e = dalloc(c, &v.gb.w, bytes))) return e;
     v.gb.partial = c->partial;
+    v.gb.tickets = c->tickets;
     v.gb.st = c->gst;
   }
   return cudaSuccess;
@@ -172,6 +198,8 @@ template <class T> struct Emit {
   mg_ctx* c;
   cudaStream_t s;
   std::vector<cx<T>*> cur, oth;
+  int lc;                        // first level run by the coarse-cycle interpreter
+  const CoarsePlan<T>* plan;
 
   void smooth(int l, int nu) {
     if (nu <= 0) return;
@@ -195,6 +223,10 @@ template <class T> struct Emit {
 
   void cycle(int l) {
     const int L = c->nlev;
+    if (l >= lc) {   // one visit of the sub-cycle below, in one launch
+      launch_coarse_cycle<T>(plan->levels, plan->steps, plan->nsteps, c->cinv, c->ncoarse, c->B, c->active, s);
+      return;
+    }
     if (l == L - 1) {
       coarse_solve(l);
       return;
@@ -205,7 +237,7 @@ template <class T> struct Emit {
     smooth(l, c->opt.nu_pre);
     launch_residual<T>(g, opT<T>(c, l), cur[l], V[l].b, V[l].r, c->B, c->active, s);
     launch_restrict<T>(g, gc, V[l].r, V[l + 1].b, c->B, c->active, s);
-    if (l + 1 == L - 1) {
+    if (l + 1 == L - 1 && lc > l + 1) {
       coarse_solve(l + 1);
     } else {
       cudaMemsetAsync(cur[l + 1], 0, sizeof(cx<T>) * (size_t)gc.vstride * c->B, s);
@@ -226,32 +258,109 @@ template <class T> struct Emit {
   }
 };
 
+static Ctl ctl(const mg_ctx* c) {
+  return Ctl{c->bnorm, c->tolp, c->active, c->state, c->cycles, c->relres, c->hist, c->hist_len, c->n_active,
+             c->partial, c->tickets};
+}
+
+// Records the steps of one visit of level lc (the same recursion as
+// Emit::cycle) for the coarse-cycle interpreter.
+template <class T> struct Plan {
+  mg_ctx* c;
+  std::vector<cx<T>*> cur, oth;
+  std::vector<CStep> steps;
+  void push(int op, int l, int arg, void* p0, void* p1) { steps.push_back(CStep{op, l, arg, 0, p0, p1}); }
+  void smooth(int l, int nu) {
+    if (nu <= 0) return;
+    if (c->opt.smoother == 0) {
+      for (int q = 0; q < nu; ++q) {
+        push(C_JACOBI, l, 0, cur[l], oth[l]);
+        std::swap(cur[l], oth[l]);
+      }
+    } else {
+      push(C_GMRES, l, nu, cur[l], nullptr);
+    }
+  }
+  void cycle(int l) {
+    const int L = c->nlev;
+    if (l == L - 1) {
+      push(C_COARSE, l, 0, cur[l], nullptr);
+      return;
+    }
+    smooth(l, c->opt.nu_pre);
+    push(C_RESTRICT, l, 0, cur[l], nullptr);
+    if (l + 1 == L - 1) {
+      push(C_COARSE, l + 1, 0, cur[l + 1], nullptr);
+    } else {
+      push(C_ZERO, l + 1, 0, cur[l + 1], nullptr);
+      for (int q = 0; q < c->opt.cycle; ++q) cycle(l + 1);
+    }
+    push(C_PROLONG, l, 0, cur[l], cur[l + 1]);
+    smooth(l, c->opt.nu_post);
+  }
+};
+
+template <class T> static cudaError_t build_plan(mg_ctx* c, int lc, CoarsePlan<T>& P) {
+  auto& V = vecs<T>(c);
+  const int L = c->nlev;
+  std::vector<CLevel<T>> lv(L);
+  for (int l = 0; l < L; ++l) {
+    CLevel<T> d{};
+    const OpView<T> op = opT<T>(c, l);
+    d.g = c->lev[l].g;
+    d.kind = op.kind;
+    d.c0 = op.c0;
+    d.kf = op.kf;
+    d.st = op.st;
+    d.dinv = op.dinv;
+    d.plane = op.plane;
+    d.gx = op.gx;
+    d.wx = op.wx;
+    d.hy = op.hy;
+    d.wy = op.wy;
+    d.b = V[l].b;
+    d.r = V[l].r;
+    for (int q = 0; q < 3; ++q) d.u[q] = (cx<T>*)V[l].gb.u[q];
+    d.w = (cx<T>*)V[l].gb.w;
+    lv[l] = d;
+  }
+  Plan<T> pl{c};
+  pl.cur.resize(L);
+  pl.oth.resize(L);
+  for (int l = 0; l < L; ++l) {
+    pl.cur[l] = V[l].x;
+    pl.oth[l] = V[l].t;
+  }
+  pl.cycle(lc);
+  if (pl.cur[lc] != V[lc].x) pl.push(C_COPY, lc, 0, pl.cur[lc], V[lc].x);
+  P.nsteps = (int)pl.steps.size();
+  cudaError_t e;
+  if ((e = dalloc(c, (void**)&P.levels, sizeof(CLevel<T>) * L))) return e;
+  if ((e = dalloc(c, (void**)&P.steps, sizeof(CStep) * P.nsteps))) return e;
+  if ((e = cudaMemcpy(P.levels, lv.data(), sizeof(CLevel<T>) * L, cudaMemcpyHostToDevice))) return e;
+  return cudaMemcpy(P.steps, pl.steps.data(), sizeof(CStep) * P.nsteps, cudaMemcpyHostToDevice);
+}
+
 // One FP64 cycle followed by the stopping test (graph body of the FP64 path).
 static void emit_fp64_iteration(mg_ctx* c, cudaStream_t s) {
-  Emit<double> e{c, s};
+  Emit<double> e{c, s, {}, {}, c->lc, &c->plan64};
   e.init();
   e.cycle(0);
   if (e.cur[0] != c->v64[0].x) launch_copy_masked<double>(c->lev[0].g, e.cur[0], c->v64[0].x, c->B, c->active, s);
-  const int nblk = launch_resnorm<double>(c->lev[0].g, op64(c, 0), c->v64[0].x, c->v64[0].b, c->partial, c->B,
-                                          c->active, s);
-  launch_stop(c->partial, nblk, c->B, c->bnorm, c->tolp, c->active, c->state, c->cycles, c->relres, c->hist,
-              c->hist_len, c->n_active, 1, s);
+  launch_resnorm_stop<double>(c->lev[0].g, op64(c, 0), c->v64[0].x, c->v64[0].b, c->B, ctl(c), 1, s);
 }
 
 // One refinement step of the mixed path: e = 0, one complex64 cycle on the
 // float residual, x += e in FP64, new FP64 residual (cast to float) and the
 // stopping test.
 static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
-  Emit<float> e{c, s};
+  Emit<float> e{c, s, {}, {}, c->lc, &c->plan32};
   e.init();
   const Grid& g0 = c->lev[0].g;
   cudaMemsetAsync(c->v32[0].x, 0, sizeof(float2) * (size_t)g0.vstride * c->B, s);
   e.cycle(0);
   launch_update_mixed(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
-  const int nblk = launch_resid_cast_norm(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->partial, c->B,
-                                          c->active, s);
-  launch_stop(c->partial, nblk, c->B, c->bnorm, c->tolp, c->active, c->state, c->cycles, c->relres, c->hist,
-              c->hist_len, c->n_active, 1, s);
+  launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B, ctl(c), 1, s);
 }
 
 template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, int reps, double* ms, double* bytes) {
@@ -263,9 +372,11 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
   const double nodes = (double)(g.nx + 1) * (g.ny + 1) * h->B;
   const double e = sizeof(cx<T>);
   double opbytes = 0;   // per node: stored stencil and inverse diagonal, or the k field
-  if (level > 0) {
+  if (level > 0 && h->lev[level].kind <= 3) {
     const int r = h->lev[level].radius;
     opbytes = e * ((2 * r + 1) * (2 * r + 1) + 1) / h->B;
+  } else if (level > 0) {
+    opbytes = e / h->B;   // Kronecker form: only the inverse diagonal per node
   } else if (op.kf) {
     opbytes = sizeof(T) / (double)h->B;
   }
@@ -312,6 +423,7 @@ void mg_default_options(mg_options* o) {
   o->max_cycles = 10000;
   o->min_coarse = 10;
   o->batch = 1;
+  o->coarse_nodes = 1100;
   o->stream = nullptr;
 }
 
@@ -357,15 +469,70 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     }
   }
   launch_op0consts(c->c0d, c->c0f, c->h, c->kconst, o.omega, c->beta2, s);
-  // Galerkin operators A_{l+1} = R_l C_l P_l
-  for (int l = 1; l < c->nlev; ++l) {
-    Level& L = c->lev[l];
-    const int r = L.radius;
-    const long long S = (long long)(2 * r + 1) * (2 * r + 1);
-    CK(dalloc(c, (void**)&L.st, sizeof(double2) * S * L.plane));
-    CK(dalloc(c, (void**)&L.dinv, sizeof(double2) * L.plane));
-    launch_galerkin(op64(c, l - 1), c->lev[l - 1].g.nx, c->lev[l - 1].g.ny, L.st, L.g.nx, L.g.ny, r, c->beta2, s);
-    launch_diaginv(L.st, r, L.plane, o.omega, L.dinv, s);
+  // Galerkin operators A_{l+1} = R_l C_l P_l.  Constant k: Kronecker form,
+  // A_l = W_y (x) G_x + H_y (x) W_x, each factor coarsened in 1D.  Variable
+  // k: per-node stencils from the 2D product.
+  const bool kron = k_field == nullptr;
+  if (kron && c->nlev > 1) {
+    // fine-level 1D factors (radius 1) in scratch, then coarsen level by level
+    double2 *g0, *h0, *wx0, *wy0, *tmp;
+    const int nx = c->nx, ny = c->ny, nmax = std::max(nx, ny);
+    CK(dalloc(c, (void**)&g0, sizeof(double2) * 3 * (nx + 1)));
+    CK(dalloc(c, (void**)&wx0, sizeof(double2) * 3 * (nx + 1)));
+    CK(dalloc(c, (void**)&h0, sizeof(double2) * 3 * (ny + 1)));
+    CK(dalloc(c, (void**)&wy0, sizeof(double2) * 3 * (ny + 1)));
+    CK(dalloc(c, (void**)&tmp, sizeof(double2) * 3 * (nmax + 1)));
+    launch_factors0(nx, c->h, c->kconst, c->beta2, g0, tmp, wx0, s);
+    launch_factors0(ny, c->h, c->kconst, c->beta2, tmp, h0, wy0, s);
+    const double2 *pg = g0, *ph = h0, *pwx = wx0, *pwy = wy0;
+    std::vector<double2*> cwx(c->nlev), cwy(c->nlev);
+    for (int l = 1; l < c->nlev; ++l) {
+      Level& L = c->lev[l];
+      const int r = L.radius, rf = c->lev[l - 1].radius, w = 2 * r + 1;
+      const int fx = c->lev[l - 1].g.nx, fy = c->lev[l - 1].g.ny, cx_ = L.g.nx, cy_ = L.g.ny;
+      L.kind = 2 + r;
+      CK(dalloc(c, (void**)&L.gx, sizeof(double2) * w * (cx_ + 1)));
+      CK(dalloc(c, (void**)&L.hy, sizeof(double2) * w * (cy_ + 1)));
+      CK(dalloc(c, (void**)&cwx[l], sizeof(double2) * w * (cx_ + 1)));
+      CK(dalloc(c, (void**)&cwy[l], sizeof(double2) * w * (cy_ + 1)));
+      CK(dalloc(c, (void**)&L.wx, sizeof(double) * w * (cx_ + 1)));
+      CK(dalloc(c, (void**)&L.wy, sizeof(double) * w * (cy_ + 1)));
+      launch_galerkin_1d(pg, fx, rf, L.gx, r, s);
+      launch_galerkin_1d(pwx, fx, rf, cwx[l], r, s);
+      launch_galerkin_1d(ph, fy, rf, L.hy, r, s);
+      launch_galerkin_1d(pwy, fy, rf, cwy[l], r, s);
+      launch_real_part(cwx[l], L.wx, (long long)w * (cx_ + 1), s);
+      launch_real_part(cwy[l], L.wy, (long long)w * (cy_ + 1), s);
+      CK(dalloc(c, (void**)&L.dinv, sizeof(double2) * L.plane));
+      launch_diaginv_op(op64(c, l), cx_, cy_, o.omega, L.dinv, s);
+      pg = L.gx;
+      ph = L.hy;
+      pwx = cwx[l];
+      pwy = cwy[l];
+      if (mixed) {
+        CK(dalloc(c, (void**)&L.gx32, sizeof(float2) * w * (cx_ + 1)));
+        CK(dalloc(c, (void**)&L.hy32, sizeof(float2) * w * (cy_ + 1)));
+        CK(dalloc(c, (void**)&L.wx32, sizeof(float) * w * (cx_ + 1)));
+        CK(dalloc(c, (void**)&L.wy32, sizeof(float) * w * (cy_ + 1)));
+        CK(dalloc(c, (void**)&L.dinv32, sizeof(float2) * L.plane));
+        launch_to_float(L.gx, L.gx32, (long long)w * (cx_ + 1), s);
+        launch_to_float(L.hy, L.hy32, (long long)w * (cy_ + 1), s);
+        launch_to_float_real(L.wx, L.wx32, (long long)w * (cx_ + 1), s);
+        launch_to_float_real(L.wy, L.wy32, (long long)w * (cy_ + 1), s);
+        launch_to_float(L.dinv, L.dinv32, L.plane, s);
+      }
+    }
+  } else {
+    for (int l = 1; l < c->nlev; ++l) {
+      Level& L = c->lev[l];
+      const int r = L.radius;
+      const long long S = (long long)(2 * r + 1) * (2 * r + 1);
+      L.kind = r;
+      CK(dalloc(c, (void**)&L.st, sizeof(double2) * S * L.plane));
+      CK(dalloc(c, (void**)&L.dinv, sizeof(double2) * L.plane));
+      launch_galerkin(op64(c, l - 1), c->lev[l - 1].g.nx, c->lev[l - 1].g.ny, L.st, L.g.nx, L.g.ny, r, c->beta2, s);
+      launch_diaginv(L.st, r, L.plane, o.omega, L.dinv, s);
+    }
   }
   CK(cudaGetLastError());
   // coarsest direct solver
@@ -385,8 +552,9 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     if (st) FAIL(MG_ESTATE, "coarsest operator is singular");
   }
   // work arrays
-  const int nblk0 = cdiv(g0.nx + 1, BX) * cdiv(g0.ny + 1, BY);
-  CK(dalloc(c, (void**)&c->partial, sizeof(double) * (size_t)nblk0 * c->B * 8));
+  const int nblk0 = cdiv(g0.nx + 1, BX) * cdiv(g0.ny + 1, BY * RY);
+  CK(dalloc(c, (void**)&c->partial, sizeof(double) * (size_t)nblk0 * c->B * NVMAX));
+  CK(dalloc(c, (void**)&c->tickets, sizeof(unsigned) * c->B));
   CK(dalloc(c, (void**)&c->gst, sizeof(double) * 96 * c->B));
   CK(dalloc(c, (void**)&c->active, sizeof(int) * c->B));
   CK(dalloc(c, (void**)&c->state, sizeof(int) * c->B));
@@ -410,7 +578,7 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     c->v32.resize(c->nlev);
     for (int l = 0; l < c->nlev; ++l) {
       CK(alloc_vectors<float>(c, c->v32[l], c->lev[l].g, gm));
-      if (l > 0) {
+      if (l > 0 && c->lev[l].kind <= 3) {
         const Level& L = c->lev[l];
         const long long S = (long long)(2 * L.radius + 1) * (2 * L.radius + 1);
         CK(dalloc(c, (void**)&c->v32[l].st, sizeof(float2) * S * L.plane));
@@ -419,6 +587,20 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
         launch_to_float(L.dinv, c->v32[l].dinv, L.plane, s);
       }
     }
+  }
+  // coarse-cycle interpreter: every level from the first one with at most
+  // opt.coarse_nodes nodes down to the coarsest grid
+  c->lc = 1 << 30;
+  if (o.coarse_nodes > 0)
+    for (int l = 0; l < c->nlev; ++l)
+      if (c->lev[l].plane <= o.coarse_nodes) {
+        c->lc = l;
+        break;
+      }
+  CK(cudaStreamSynchronize(s));
+  if (c->lc < c->nlev) {
+    if (!mixed) CK(build_plan<double>(c, c->lc, c->plan64));
+    else CK(build_plan<float>(c, c->lc, c->plan32));
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
@@ -442,6 +624,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.precision != 0 && o.precision != 1) FAIL(MG_EINVAL, "precision must be 0 or 1");
   if (o.max_cycles < 1 || o.min_coarse < 1) FAIL(MG_EINVAL, "max_cycles and min_coarse must be >= 1");
   if (o.batch < 1 || o.batch > 65535) FAIL(MG_EINVAL, "batch must be in 1..65535");
+  if (o.coarse_nodes < 0) FAIL(MG_EINVAL, "coarse_nodes must be >= 0");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
@@ -496,8 +679,7 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
   if (st != MG_OK) return st;
   launch_pack<double>(g0, (const double2*)rhs, c->v64[0].b, B, conj, s);
   launch_pack<double>(g0, (const double2*)x, c->v64[0].x, B, conj, s);
-  int nblk = launch_vecnorm<double>(g0, c->v64[0].b, c->partial, B, s);
-  launch_norm_finish(c->partial, nblk, B, c->bnorm, s);
+  launch_vecnorm_fin<double>(g0, c->v64[0].b, B, c->bnorm, c->partial, c->tickets, s);
   std::vector<double> bn(B);
   CK(cudaMemcpyAsync(bn.data(), c->bnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -524,17 +706,15 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
   CK(cudaMemsetAsync(c->hist, 0, sizeof(double) * (size_t)c->hist_len * B, s));
   // initial test on x0
   if (mixed)
-    nblk = launch_resid_cast_norm(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->partial, B, c->active, s);
+    launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, B, ctl(c), 0, s);
   else
-    nblk = launch_resnorm<double>(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->partial, B, c->active, s);
-  launch_stop(c->partial, nblk, B, c->bnorm, c->tolp, c->active, c->state, c->cycles, c->relres, c->hist,
-              c->hist_len, c->n_active, 0, s);
+    launch_resnorm_stop<double>(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, B, ctl(c), 0, s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int done = 0;
-  // direct launches: 2 pack + norm + finish + initial residual + stop + unpack
-  c->last_launches = 7;
+  // direct launches: 2 pack + norm + initial residual test + unpack
+  c->last_launches = 5;
   c->last_graphs = 0;
   while (*c->h_n_active > 0 && done < c->opt.max_cycles) {
     CK(cudaGraphLaunch(c->gexec, s));

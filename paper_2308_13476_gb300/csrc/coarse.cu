@@ -1,0 +1,270 @@
+// Single-CTA coarse-cycle interpreter.
+//
+// The levels of the hierarchy with few nodes (all levels from `lc` down to
+// the coarsest grid) cost almost nothing in arithmetic but, launched as
+// separate grid-wide kernels, dozens of launches per level and cycle.  Here
+// one CTA per right-hand side runs the whole sub-cycle below level lc-1:
+// the host records the V/W schedule of those levels once (the same
+// recursion as the grid-wide driver, Sec. 3 of the paper) as a list of
+// steps, and the kernel walks it, with a __syncthreads() between dependent
+// phases.  Every step computes exactly what the grid-wide kernels compute:
+// the same stencils, the same Jacobi sweep, the same GMRES(3) arithmetic
+// (gmres.cuh), the same transfers of Eq. (xex) and the same FP64 coarsest
+// solve; only the reductions are block-wide instead of grid-wide.
+#include "gmres.cuh"
+#include "internal.h"
+
+namespace hmg {
+
+template <class T>
+__device__ __forceinline__ cx<T> lv_apply(const CLevel<T>& L, const cx<T>* x, long long p, int i, int j) {
+  switch (L.kind) {
+    case 1: return Op0<T>{L.c0, L.kf, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
+    case 2: return OpS<T, 2>{L.st, L.dinv, L.plane, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
+    case 3: return OpS<T, 3>{L.st, L.dinv, L.plane, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
+    case 4: return OpK<T, 2>{L.gx, L.wx, L.hy, L.wy, L.dinv, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
+    default: return OpK<T, 3>{L.gx, L.wx, L.hy, L.wy, L.dinv, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
+  }
+}
+
+template <class T> __device__ __forceinline__ cx<T> lv_dinv(const CLevel<T>& L, int i, int j) {
+  if (L.kind == 1) return Op0<T>{L.c0, L.kf, L.g.nx, L.g.ny}.diag_inv(i, j);
+  return L.dinv[(long long)j * (L.g.nx + 1) + i];
+}
+
+template <class T> __device__ __forceinline__ T cbw(int d) {
+  return d == 0 ? T(0.75) : (d == 1 || d == -1) ? T(0.5) : T(0.125);
+}
+
+// Node loop over one level: q -> (i, j, p).
+#define CTA_NODES(L)                                                         \
+  for (int q = tid, n1_ = (L).g.nx + 1, nn_ = n1_ * ((L).g.ny + 1); q < nn_; q += nt)
+#define CTA_IJP(L)                 \
+  const int i = q % n1_;           \
+  const int j = q / n1_;           \
+  const long long p = (L).g.at(i, j);
+
+template <class T>
+__device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, double* S, double* sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const cx<T>* b = L.b + off;
+  cx<T>* u[3] = {L.u[0] + off, L.u[1] + off, L.u[2] + off};
+  cx<T>* w = L.w + off;
+  for (int step = 0; step < nu; ++step) {
+    T a0 = T(0);
+    CTA_NODES(L) {
+      CTA_IJP(L)
+      const cx<T> r = sub<T>(b[p], lv_apply<T>(L, x, p, i, j));
+      u[0][p] = r;
+      a0 += abs2<T>(r);
+    }
+    {
+      double t[1] = {(double)a0};
+      block_sum<1>(t, sh);
+      if (tid == 0) fin_init(S, t);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int J = 0; J < 3; ++J) {
+      if (S[G_BRK] != 0.0 || S[G_M] < J) break;   // uniform: shared state after a barrier
+      const T sJ = (T)S[G_S + J];
+      T dt[6] = {0, 0, 0, 0, 0, 0};
+      CTA_NODES(L) {
+        CTA_IJP(L)
+        const cx<T> a = scl<T>(sJ, lv_apply<T>(L, u[J], p, i, j));
+        w[p] = a;
+        for (int l = 0; l <= J; ++l) {
+          const cx<T> e = cmul<T>(u[l][p], a);
+          dt[2 * l] += e.x;
+          dt[2 * l + 1] += e.y;
+        }
+      }
+      double d[6];
+      for (int l = 0; l < 6; ++l) d[l] = (double)dt[l];
+      block_sum<6>(d, sh);
+      if (tid == 0) {
+        if (J == 0) fin_a<0>(S, d);
+        else if (J == 1) fin_a<1>(S, d);
+        else fin_a<2>(S, d);
+      }
+      __syncthreads();
+      cx<T> c[3];
+      for (int l = 0; l < 3; ++l) {
+        const double sl = S[G_S + l];
+        c[l] = l <= J ? mk<T>((T)(S[G_H + 2 * (l * 3 + J)] * sl), (T)(S[G_H + 2 * (l * 3 + J) + 1] * sl))
+                      : mk<T>(0, 0);
+      }
+      T et[5] = {0, 0, 0, 0, 0};
+      CTA_NODES(L) {
+        CTA_IJP(L)
+        cx<T> a = w[p];
+        cx<T> uu[3];
+        for (int l = 0; l <= J; ++l) {
+          uu[l] = u[l][p];
+          a = sub<T>(a, mul<T>(c[l], uu[l]));
+        }
+        if (J < 2) u[J + 1][p] = a;
+        et[0] += abs2<T>(a);
+        if (J < 2)
+          for (int l = 0; l <= J; ++l) {
+            const cx<T> e = cmul<T>(a, uu[l]);
+            et[1 + 2 * l] += e.x;
+            et[2 + 2 * l] += e.y;
+          }
+      }
+      double e5[5];
+      for (int l = 0; l < 5; ++l) e5[l] = (double)et[l];
+      block_sum<5>(e5, sh);
+      if (tid == 0) {
+        if (J == 0) fin_b<0>(S, e5);
+        else if (J == 1) fin_b<1>(S, e5);
+        else fin_b<2>(S, e5);
+      }
+      __syncthreads();
+    }
+    const int m = (int)S[G_M];
+    if (m > 0) {
+      cx<T> c[3];
+      for (int l = 0; l < 3; ++l) {
+        const double sl = S[G_S + l];
+        c[l] = mk<T>((T)(S[G_Y + 2 * l] * sl), (T)(S[G_Y + 2 * l + 1] * sl));
+      }
+      CTA_NODES(L) {
+        CTA_IJP(L)
+        cx<T> a = x[p];
+        for (int l = 0; l < 3; ++l)
+          if (l < m) a = fma_c<T>(c[l], u[l][p], a);
+        x[p] = a;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle(const CLevel<T>* __restrict__ levels,
+                                                             const CStep* __restrict__ steps, int nsteps,
+                                                             const double2* __restrict__ inv, int N,
+                                                             const int* __restrict__ active) {
+  extern __shared__ double2 rs[];            // coarsest right-hand side, N entries
+  __shared__ double sh[NVMAX * 32];
+  __shared__ double S[GS];
+  const int rhs = blockIdx.x;
+  if (active && !active[rhs]) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int s = 0; s < nsteps; ++s) {
+    const CStep st = steps[s];
+    const CLevel<T>& L = levels[st.level];
+    const long long off = (long long)rhs * L.g.vstride;
+    cx<T>* p0 = (cx<T>*)st.p0 + off;
+    switch (st.op) {
+      case C_JACOBI: {   // p1 = p0 + (omega diag A)^-1 (b - A p0)
+        cx<T>* p1 = (cx<T>*)st.p1 + off;
+        const cx<T>* b = L.b + off;
+        CTA_NODES(L) {
+          CTA_IJP(L)
+          const cx<T> r = sub<T>(b[p], lv_apply<T>(L, p0, p, i, j));
+          p1[p] = fma_c<T>(lv_dinv<T>(L, i, j), r, p0[p]);
+        }
+        __syncthreads();
+        break;
+      }
+      case C_GMRES:
+        cta_gmres<T>(L, p0, off, st.arg, S, sh);
+        break;
+      case C_RESTRICT: {  // r = b - A p0 on this level, then b_{l+1} = R r
+        cx<T>* r = L.r + off;
+        const cx<T>* b = L.b + off;
+        CTA_NODES(L) {
+          CTA_IJP(L)
+          r[p] = sub<T>(b[p], lv_apply<T>(L, p0, p, i, j));
+        }
+        __syncthreads();
+        const CLevel<T>& C = levels[st.level + 1];
+        cx<T>* bc = C.b + (long long)rhs * C.g.vstride;
+        CTA_NODES(C) {
+          CTA_IJP(C)
+          const long long pc = L.g.at(2 * i, 2 * j);
+          cx<T> acc = mk<T>(0, 0);
+          for (int bb = -2; bb <= 2; ++bb) {
+            const cx<T>* row = r + pc + (long long)bb * L.g.pitch;
+            cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
+            t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
+            t = add<T>(t, scl<T>(T(0.75), row[0]));
+            acc = add<T>(acc, scl<T>(cbw<T>(bb), t));
+          }
+          bc[p] = scl<T>(T(0.25), acc);
+        }
+        __syncthreads();
+        break;
+      }
+      case C_ZERO: {
+        CTA_NODES(L) {
+          CTA_IJP(L)
+          p0[p] = mk<T>(0, 0);
+        }
+        __syncthreads();
+        break;
+      }
+      case C_COARSE: {   // p0 = A_c^{-1} b, FP64
+        const cx<T>* b = L.b + off;
+        CTA_NODES(L) {
+          CTA_IJP(L)
+          const cx<T> a = b[p];
+          rs[q] = make_double2((double)a.x, (double)a.y);
+        }
+        __syncthreads();
+        CTA_NODES(L) {
+          CTA_IJP(L)
+          double2 acc = make_double2(0, 0);
+          const double2* row = inv + (long long)q * N;
+          for (int c2 = 0; c2 < N; ++c2) acc = fma_c<double>(row[c2], rs[c2], acc);
+          p0[p] = mk<T>((T)acc.x, (T)acc.y);
+        }
+        __syncthreads();
+        break;
+      }
+      case C_PROLONG: {  // p0 += P p1 (p1 on level + 1)
+        const CLevel<T>& C = levels[st.level + 1];
+        const cx<T>* ec = (const cx<T>*)st.p1 + (long long)rhs * C.g.vstride;
+        CTA_NODES(L) {
+          CTA_IJP(L)
+          const int I = i >> 1, J = j >> 1;
+          auto rowval = [&](int JJ) -> cx<T> {
+            const cx<T>* row = ec + C.g.at(I, JJ);
+            if (i & 1) return scl<T>(T(0.5), add<T>(row[0], row[1]));
+            return add<T>(scl<T>(T(0.125), add<T>(row[-1], row[1])), scl<T>(T(0.75), row[0]));
+          };
+          cx<T> v;
+          if (j & 1) v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
+          else v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+          p0[p] = add<T>(p0[p], v);
+        }
+        __syncthreads();
+        break;
+      }
+      default: {   // C_COPY p1 = p0
+        cx<T>* p1 = (cx<T>*)st.p1 + off;
+        CTA_NODES(L) {
+          CTA_IJP(L)
+          p1[p] = p0[p];
+        }
+        __syncthreads();
+        break;
+      }
+    }
+  }
+}
+
+template <class T>
+void launch_coarse_cycle(const CLevel<T>* levels, const CStep* steps, int nsteps, const double2* inv, int N, int B,
+                         const int* active, cudaStream_t s) {
+  k_coarse_cycle<T><<<B, CTA_THREADS, (size_t)N * sizeof(double2), s>>>(levels, steps, nsteps, inv, N, active);
+}
+
+template void launch_coarse_cycle<double>(const CLevel<double>*, const CStep*, int, const double2*, int, int,
+                                          const int*, cudaStream_t);
+template void launch_coarse_cycle<float>(const CLevel<float>*, const CStep*, int, const double2*, int, int,
+                                         const int*, cudaStream_t);
+
+}  // namespace hmg

@@ -16,7 +16,9 @@ namespace hmg {
 constexpr int HALO = 4;
 constexpr int BX = 32;   // block shape of the node-parallel kernels
 constexpr int BY = 8;
+constexpr int RY = 4;    // grid rows per thread (a block covers BX x BY*RY nodes)
 constexpr int MAXR = 3;  // largest Galerkin stencil radius (7 x 7)
+constexpr int NVMAX = 8; // values per block partial record
 
 template <class T> struct cvec;
 template <> struct cvec<double> { using type = double2; };
@@ -141,6 +143,46 @@ template <class T, int R> struct OpS {
   }
 };
 
+// Constant-k Galerkin operator in Kronecker form (radius R):
+//   A = W_y (x) G_x + H_y (x) W_x,
+// with G_x, H_y complex and W_x, W_y real banded 1D operators, each the 1D
+// Galerkin coarsening of its fine-level factor (the fine operator is
+// W1 (x) (L1/h^2 - (1 + i beta2) k^2 W1 - i k/h B1) + (L1/h^2 - i k/h B1) (x) W1
+// in terms of the 1D Neumann Laplacian L1, boundary weights W1 and boundary
+// indicator B1).  Rows are [n+1][2R+1], entry R + d the coupling to node + d.
+template <class T, int R> struct OpK {
+  const cx<T>* gx;
+  const T* wx;
+  const cx<T>* hy;
+  const T* wy;
+  const cx<T>* dinvp;
+  int nx, ny;
+  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, long long p, int pitch, int i, int j) const {
+    const cx<T>* G = gx + i * (2 * R + 1);
+    const T* Wx = wx + i * (2 * R + 1);
+    const cx<T>* H = hy + j * (2 * R + 1);
+    const T* Wy = wy + j * (2 * R + 1);
+    cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+      const cx<T>* row = x + p + (long long)dy * pitch;
+      cx<T> s1 = mk<T>(0, 0), s2 = mk<T>(0, 0);
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx) {
+        const cx<T> xv = row[dx];
+        s1 = fma_c<T>(G[dx + R], xv, s1);
+        s2 = mk<T>(fma(Wx[dx + R], xv.x, s2.x), fma(Wx[dx + R], xv.y, s2.y));
+      }
+      acc = mk<T>(fma(Wy[dy + R], s1.x, acc.x), fma(Wy[dy + R], s1.y, acc.y));
+      acc = fma_c<T>(H[dy + R], s2, acc);
+    }
+    return acc;
+  }
+  __device__ __forceinline__ cx<T> diag_inv(int i, int j) const {
+    return dinvp[(long long)j * (nx + 1) + i];
+  }
+};
+
 // Block-wide sum of NV doubles; result valid in thread 0.  Fixed shape and
 // order, so results are bitwise reproducible run to run.
 template <int NV>
@@ -165,6 +207,48 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32
     }
   }
   __syncthreads();
+}
+
+// Grid-wide deterministic sum of NV doubles for one right-hand side, inside
+// the producing kernel: every block publishes its block sum, takes a ticket,
+// and the block holding the last ticket sums all partials in block order
+// (fixed, so results are bitwise reproducible) and resets the ticket.
+// Returns true, block-uniformly, in that last block; the totals are then
+// valid in thread 0's v.  partial: [rhs][nblk][NVMAX]; tickets: [rhs], 0 at
+// rest.  Must be reached by every thread of every block of the RHS.
+template <int NV>
+__device__ __forceinline__ bool reduce_last(double (&v)[NV], double* sh, double* partial, unsigned* tickets, int rhs,
+                                            int nblk, int blk) {
+  __shared__ int s_last;
+  block_sum<NV>(v, sh);
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nt = blockDim.x * blockDim.y;
+  if (tid == 0) {
+    double* q = partial + ((long long)rhs * nblk + blk) * NVMAX;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) q[k] = v[k];
+    __threadfence();
+    const unsigned t = atomicAdd(&tickets[rhs], 1u);
+    s_last = (t == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int b = tid; b < nblk; b += nt) {
+    const double* q = partial + ((long long)rhs * nblk + b) * NVMAX;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(q + k);
+  }
+  block_sum<NV>(acc, sh);
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = acc[k];
+    tickets[rhs] = 0u;
+  }
+  return true;
 }
 
 }  // namespace hmg

@@ -9,7 +9,8 @@ namespace hmg {
 
 // Operator of one level in precision T, as handed to the launch wrappers.
 // kind 1: matrix-free fine-level operator (c0, kf); kind 2 / 3: stored
-// Galerkin stencil of that radius (st, dinv, plane).
+// Galerkin stencil of that radius (st, dinv, plane); kind 4 / 5: constant-k
+// Kronecker form of radius 2 / 3 (gx, wx, hy, wy, dinv).
 template <class T> struct OpView {
   int kind;
   const Op0Consts<T>* c0;
@@ -17,7 +18,23 @@ template <class T> struct OpView {
   const cx<T>* st;
   const cx<T>* dinv;
   long long plane;
+  const cx<T>* gx;
+  const T* wx;
+  const cx<T>* hy;
+  const T* wy;
 };
+__host__ __device__ inline int op_radius(int kind) { return kind == 1 ? 1 : (kind == 2 || kind == 4) ? 2 : 3; }
+
+// Dispatch a generic lambda on the operator functor of a view.
+template <class T, class F> inline void with_op(const OpView<T>& v, int nx, int ny, F&& f) {
+  switch (v.kind) {
+    case 1: f(Op0<T>{v.c0, v.kf, nx, ny}); break;
+    case 2: f(OpS<T, 2>{v.st, v.dinv, v.plane, nx, ny}); break;
+    case 3: f(OpS<T, 3>{v.st, v.dinv, v.plane, nx, ny}); break;
+    case 4: f(OpK<T, 2>{v.gx, v.wx, v.hy, v.wy, v.dinv, nx, ny}); break;
+    default: f(OpK<T, 3>{v.gx, v.wx, v.hy, v.wy, v.dinv, nx, ny}); break;
+  }
+}
 
 // Node-parallel kernels (kernels_level.cu).  `active[b]` == 0 skips RHS b.
 // B = number of right-hand sides.
@@ -27,14 +44,33 @@ template <class T> void launch_apply(const Grid& g, const OpView<T>& op, const c
                                      const int* active, cudaStream_t s);
 template <class T> void launch_jacobi(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
                                       cx<T>* xout, int B, const int* active, cudaStream_t s);
-// Per-block partial sums of |b - A x|^2 into partial[b * nblk + blk]; returns nblk.
-template <class T> int launch_resnorm(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
-                                      double* partial, int B, const int* active, cudaStream_t s);
-// r = b - A x in FP64 with |r|^2 partials, r written in float (mixed path).
-int launch_resid_cast_norm(const Grid& g, const OpView<double>& op, const double2* x, const double2* b,
-                           float2* r32, double* partial, int B, const int* active, cudaStream_t s);
-// x += e (FP64 += float), masked.
+// Per-solve control block of the stopping test (device arrays, one entry per
+// RHS unless noted).  tolp = {tol, divergence threshold}; partial/tickets are
+// the scratch of the fused reductions (reduce_last).
+struct Ctl {
+  const double* bnorm;
+  const double* tolp;
+  int* active;
+  int* state;
+  int* cycles;
+  double* relres;
+  double* hist;
+  int hist_len;
+  int* n_active;        // one int
+  double* partial;
+  unsigned* tickets;
+};
+// ||b - A x|| per RHS with the stopping test fused (count != 0: a cycle just finished).
+template <class T> void launch_resnorm_stop(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
+                                            int B, const Ctl& c, int count, cudaStream_t s);
+// Mixed path: r = b - A x in FP64, written as float into r32 (same Grid), stopping test fused.
+void launch_resid_cast_stop(const Grid& g, const OpView<double>& op, const double2* x, const double2* b,
+                            float2* r32, int B, const Ctl& c, int count, cudaStream_t s);
+// x += e (FP64 += float, same Grid), masked.
 void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s);
+// out[b] = ||v_b|| (one kernel).
+template <class T> void launch_vecnorm_fin(const Grid& g, const cx<T>* v, int B, double* out, double* partial,
+                                           unsigned* tickets, cudaStream_t s);
 template <class T> void launch_restrict(const Grid& gf, const Grid& gc, const cx<T>* rf, cx<T>* rc, int B,
                                         const int* active, cudaStream_t s);
 template <class T> void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<T>* ec, cx<T>* xf, int B,
@@ -44,17 +80,6 @@ template <class T> void launch_copy_masked(const Grid& g, const cx<T>* src, cx<T
 // Dense user array [B][ny+1][nx+1] complex128 <-> padded vector; conj != 0 conjugates.
 template <class T> void launch_pack(const Grid& g, const double2* user, cx<T>* v, int B, int conj, cudaStream_t s);
 template <class T> void launch_unpack(const Grid& g, const cx<T>* v, double2* user, int B, int conj, cudaStream_t s);
-// Stopping test for every active RHS b: relres[b] = sqrt(sum partial) / bnorm[b];
-// tolp = {tol, divergence threshold} in device memory.  count != 0: a cycle
-// has just finished (cycles[b] += 1, history entry written).  A RHS that meets
-// tol (state 1) or diverges (state 2) is deactivated and n_active decremented.
-void launch_stop(const double* partial, int nblk, int B, const double* bnorm, const double* tolp,
-                 int* active, int* state, int* cycles, double* relres, double* hist, int hist_len,
-                 int* n_active, int count, cudaStream_t s);
-// ||b||: sum partials into bnorm (sqrt), one block per RHS.
-void launch_norm_finish(const double* partial, int nblk, int B, double* out, cudaStream_t s);
-template <class T> int launch_vecnorm(const Grid& g, const cx<T>* v, double* partial, int B, cudaStream_t s);
-
 // Coarsest-grid solve with the stored FP64 inverse (setup.cu).
 template <class T> void launch_coarse_solve(const Grid& g, const double2* inv, int N, const cx<T>* r, cx<T>* e,
                                             int B, const int* active, cudaStream_t s);
@@ -69,6 +94,17 @@ void launch_galerkin(const OpView<double>& fine, int fnx, int fny, double2* coar
 void launch_diaginv(const double2* st, int rc, long long plane, double omega, double2* dinv, cudaStream_t s);
 void launch_to_float(const double2* src, float2* dst, long long n, cudaStream_t s);
 void launch_to_float_real(const double* src, float* dst, long long n, cudaStream_t s);
+// 1D factors of the constant-k fine operator (radius 1, rows [n+1][3]):
+// g = L1/h^2 - (1 + i beta2) k^2 W1 - i (k/h) B1 (the x factor) when shifted,
+// h = L1/h^2 - i (k/h) B1 (the y factor), w = W1.
+void launch_factors0(int n, double h, double k, double beta2, double2* g, double2* hf, double2* w, cudaStream_t s);
+// 1D Galerkin coarsening X_c = (P1^T / 2) X P1 of a banded [nf+1][2rf+1] row
+// array into [nc+1][2rc+1] (nc = nf / 2).
+void launch_galerkin_1d(const double2* X, int nf, int rf, double2* Xc, int rc, cudaStream_t s);
+// Real parts of a complex row array (the W factors are real).
+void launch_real_part(const double2* a, double* b, long long n, cudaStream_t s);
+// Per-node 1/(omega * diagonal) of a level operator (any kind).
+void launch_diaginv_op(const OpView<double>& op, int nx, int ny, double omega, double2* dinv, cudaStream_t s);
 // Dense matrix of a level operator (N = (nx+1)(ny+1) <= 4096) and its inverse.
 void launch_dense(const OpView<double>& op, int nx, int ny, double2* M, cudaStream_t s);
 void launch_gauss_jordan(double2* M, double2* inv, int N, int* status, cudaStream_t s);
@@ -77,14 +113,43 @@ void launch_export_stencil(const OpView<double>& op, int nx, int ny, int r, doub
 
 // GMRES(3) smoother (kernels_gmres.cu).  State layout per RHS in `gs`.
 struct GmresBufs {
-  void* u[4];       // Arnoldi vectors (unnormalised), precision T
-  void* w;          // A v_j
-  double* partial;  // block partials
-  double* st;       // per-RHS scalars, see kernels_gmres.cu
-  int nblk_cap;
+  void* u[3];          // Arnoldi vectors (unnormalised), precision T
+  void* w;             // A v_j
+  double* partial;     // block partials of the fused reductions
+  unsigned* tickets;   // one per RHS, 0 at rest
+  double* st;          // per-RHS scalars, see kernels_gmres.cu
 };
 template <class T> void gmres_smooth(const Grid& g, const OpView<T>& op, cx<T>* x, const cx<T>* b, int nu, int B,
                                      const int* active, const GmresBufs& gb, cudaStream_t s);
+
+// Single-CTA coarse-cycle interpreter (coarse.cu).  One CTA per RHS walks a
+// host-recorded list of steps over the levels lc..L-1.
+constexpr int CTA_THREADS = 512;
+enum { C_JACOBI = 0, C_GMRES = 1, C_RESTRICT = 2, C_ZERO = 3, C_COARSE = 4, C_PROLONG = 5, C_COPY = 6 };
+template <class T> struct CLevel {
+  Grid g;
+  int kind;                 // as OpView::kind
+  const Op0Consts<T>* c0;
+  const T* kf;
+  const cx<T>* st;
+  const cx<T>* dinv;
+  long long plane;
+  const cx<T>* gx;
+  const T* wx;
+  const cx<T>* hy;
+  const T* wy;
+  cx<T>* b;                 // right-hand side of the level
+  cx<T>* r;                 // residual scratch
+  cx<T>* u[3];              // GMRES(3) basis (null without GMRES)
+  cx<T>* w;
+};
+struct CStep {
+  int op, level, arg, pad;  // arg: GMRES steps
+  void* p0;                 // iterate of `level` (in place), or source
+  void* p1;                 // destination (Jacobi, copy) or coarse correction (prolong)
+};
+template <class T> void launch_coarse_cycle(const CLevel<T>* levels, const CStep* steps, int nsteps,
+                                            const double2* inv, int N, int B, const int* active, cudaStream_t s);
 
 // Gradient of the receiver misfit (kernels_level.cu).
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u,

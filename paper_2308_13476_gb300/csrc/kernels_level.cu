@@ -15,29 +15,17 @@ namespace hmg {
 
 // ------------------------------------------------------------------ helpers
 
-template <class T, class F>
-static void with_op(const OpView<T>& v, int nx, int ny, F&& f) {
-  if (v.kind == 1) {
-    Op0<T> op{v.c0, v.kf, nx, ny};
-    f(op);
-  } else if (v.kind == 2) {
-    OpS<T, 2> op{v.st, v.dinv, v.plane, nx, ny};
-    f(op);
-  } else {
-    OpS<T, 3> op{v.st, v.dinv, v.plane, nx, ny};
-    f(op);
-  }
-}
-
 static inline dim3 node_grid(const Grid& g, int B) {
-  return dim3(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY), B);
+  return dim3(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY * RY), B);
 }
 
+// Thread (tx, ty) of block (bx, by, rhs) handles node column i and the RY
+// rows j = by*BY*RY + r*BY + ty, r = 0..RY-1 (warps stay on one row).
 #define NODE_INDEX                                       \
   const int rhs = blockIdx.z;                            \
   const int i = blockIdx.x * BX + threadIdx.x;           \
-  const int j = blockIdx.y * BY + threadIdx.y;           \
   const long long off = (long long)rhs * g.vstride;
+#define FOR_ROWS for (int r_ = 0, j = blockIdx.y * BY * RY + threadIdx.y; r_ < RY; ++r_, j += BY)
 
 // ------------------------------------------------------------------ operator kernels
 
@@ -47,9 +35,12 @@ __global__ void __launch_bounds__(BX * BY) k_residual(Grid g, Op op, const cx<T>
                                                       const int* __restrict__ active) {
   NODE_INDEX
   if (active && !active[rhs]) return;
-  if (i > g.nx || j > g.ny) return;
-  const long long p = g.at(i, j);
-  r[off + p] = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const long long p = g.at(i, j);
+    r[off + p] = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+  }
 }
 
 template <class T, class Op>
@@ -57,9 +48,12 @@ __global__ void __launch_bounds__(BX * BY) k_apply(Grid g, Op op, const cx<T>* _
                                                    cx<T>* __restrict__ y, const int* __restrict__ active) {
   NODE_INDEX
   if (active && !active[rhs]) return;
-  if (i > g.nx || j > g.ny) return;
-  const long long p = g.at(i, j);
-  y[off + p] = op.apply(x + off, p, g.pitch, i, j);
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const long long p = g.at(i, j);
+    y[off + p] = op.apply(x + off, p, g.pitch, i, j);
+  }
 }
 
 // x_out = x + (omega diag A)^{-1} (b - A x)   (one weighted-Jacobi sweep)
@@ -69,72 +63,114 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(Grid g, Op op, const cx<T>* 
                                                     const int* __restrict__ active) {
   NODE_INDEX
   if (active && !active[rhs]) return;
-  if (i > g.nx || j > g.ny) return;
-  const long long p = g.at(i, j);
-  const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
-  xo[off + p] = fma_c<T>(op.diag_inv(i, j), r, x[off + p]);
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const long long p = g.at(i, j);
+    const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+    xo[off + p] = fma_c<T>(op.diag_inv(i, j), r, x[off + p]);
+  }
+}
+
+// Stopping test for one right-hand side, run by the last block of a norm
+// reduction: relres = sqrt(sumsq) / ||b||; count != 0 means a cycle has just
+// finished.  A RHS that meets tol (state 1) or diverges (state 2: not finite
+// or above the threshold) is deactivated.
+__device__ void stop_update(const Ctl& c, int rhs, double sumsq, int count) {
+  const double tol = c.tolp[0], diverge = c.tolp[1];
+  const double rr = sqrt(sumsq) / c.bnorm[rhs];
+  c.relres[rhs] = rr;
+  if (count) {
+    const int cy = ++c.cycles[rhs];
+    if (cy <= c.hist_len) c.hist[(long long)rhs * c.hist_len + cy - 1] = rr;
+  }
+  int st = 0;
+  if (!(rr == rr) || rr > diverge) st = 2;
+  else if (rr <= tol) st = 1;
+  if (st) {
+    c.state[rhs] = st;
+    c.active[rhs] = 0;
+    atomicSub(c.n_active, 1);
+  }
 }
 
 template <class T, class Op>
-__global__ void __launch_bounds__(BX * BY) k_resnorm(Grid g, Op op, const cx<T>* __restrict__ x,
-                                                     const cx<T>* __restrict__ b, double* __restrict__ partial,
-                                                     const int* __restrict__ active) {
+__global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const cx<T>* __restrict__ x,
+                                                          const cx<T>* __restrict__ b, Ctl c, int count) {
   __shared__ double sh[32];
   NODE_INDEX
-  if (active && !active[rhs]) return;   // block-uniform
-  double v[1] = {0.0};
-  if (i <= g.nx && j <= g.ny) {
-    const long long p = g.at(i, j);
-    const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
-    v[0] = (double)abs2<T>(r);
+  if (!c.active[rhs]) return;   // block-uniform
+  T a0 = T(0);   // per-thread sum in the working precision, widened once
+  if (i <= g.nx) {
+    FOR_ROWS {
+      if (j > g.ny) break;
+      const long long p = g.at(i, j);
+      const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+      a0 += abs2<T>(r);
+    }
   }
-  block_sum<1>(v, sh);
-  if (threadIdx.x == 0 && threadIdx.y == 0)
-    partial[(long long)rhs * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+  double v[1] = {(double)a0};
+  if (reduce_last<1>(v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+      threadIdx.x == 0 && threadIdx.y == 0)
+    stop_update(c, rhs, v[0], count);
 }
 
-__global__ void __launch_bounds__(BX * BY) k_resid_cast_norm(Grid g, Op0<double> op, const double2* __restrict__ x,
+// FP64 residual of the refinement loop, written in float for the next
+// complex64 correction cycle, with the stopping test fused.
+__global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double> op, const double2* __restrict__ x,
                                                              const double2* __restrict__ b, float2* __restrict__ r32,
-                                                             Grid g32, double* __restrict__ partial,
-                                                             const int* __restrict__ active) {
+                                                             Ctl c, int count) {
   __shared__ double sh[32];
   NODE_INDEX
-  if (active && !active[rhs]) return;
+  if (!c.active[rhs]) return;
   double v[1] = {0.0};
-  if (i <= g.nx && j <= g.ny) {
-    const long long p = g.at(i, j);
-    const double2 r = sub<double>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
-    r32[(long long)rhs * g32.vstride + g32.at(i, j)] = make_float2((float)r.x, (float)r.y);
-    v[0] = abs2<double>(r);
+  if (i <= g.nx) {
+    FOR_ROWS {
+      if (j > g.ny) break;
+      const long long p = g.at(i, j);
+      const double2 r = sub<double>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+      r32[off + p] = make_float2((float)r.x, (float)r.y);
+      v[0] += abs2<double>(r);
+    }
   }
-  block_sum<1>(v, sh);
-  if (threadIdx.x == 0 && threadIdx.y == 0)
-    partial[(long long)rhs * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+  if (reduce_last<1>(v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+      threadIdx.x == 0 && threadIdx.y == 0)
+    stop_update(c, rhs, v[0], count);
 }
 
-__global__ void __launch_bounds__(BX * BY) k_update_mixed(Grid g, Grid g32, double2* __restrict__ x,
-                                                          const float2* __restrict__ e,
+__global__ void __launch_bounds__(BX * BY) k_update_mixed(Grid g, double2* __restrict__ x, const float2* __restrict__ e,
                                                           const int* __restrict__ active) {
   NODE_INDEX
   if (active && !active[rhs]) return;
-  if (i > g.nx || j > g.ny) return;
-  const long long p = off + g.at(i, j);
-  const float2 d = e[(long long)rhs * g32.vstride + g32.at(i, j)];
-  double2 xv = x[p];
-  xv.x += (double)d.x;
-  xv.y += (double)d.y;
-  x[p] = xv;
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const long long p = off + g.at(i, j);
+    const float2 d = e[p];
+    double2 xv = x[p];
+    xv.x += (double)d.x;
+    xv.y += (double)d.y;
+    x[p] = xv;
+  }
 }
 
+// ||v|| per RHS into out[rhs] (one kernel, last-block finish).
 template <class T>
-__global__ void __launch_bounds__(BX * BY) k_vecnorm(Grid g, const cx<T>* __restrict__ v_, double* __restrict__ partial) {
+__global__ void __launch_bounds__(BX * BY) k_vecnorm_fin(Grid g, const cx<T>* __restrict__ v_, double* __restrict__ out,
+                                                         double* partial, unsigned* tickets) {
   __shared__ double sh[32];
   NODE_INDEX
-  double v[1] = {0.0};
-  if (i <= g.nx && j <= g.ny) v[0] = (double)abs2<T>(v_[off + g.at(i, j)]);
-  block_sum<1>(v, sh);
-  if (threadIdx.x == 0 && threadIdx.y == 0)
-    partial[(long long)rhs * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+  T a0 = T(0);
+  if (i <= g.nx) {
+    FOR_ROWS {
+      if (j > g.ny) break;
+      a0 += abs2<T>(v_[off + g.at(i, j)]);
+    }
+  }
+  double v[1] = {(double)a0};
+  if (reduce_last<1>(v, sh, partial, tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+      threadIdx.x == 0 && threadIdx.y == 0)
+    out[rhs] = sqrt(v[0]);
 }
 
 // ------------------------------------------------------------------ transfers
@@ -150,19 +186,22 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<
                                                       cx<T>* __restrict__ rc, const int* __restrict__ active) {
   NODE_INDEX
   if (active && !active[rhs]) return;
-  if (i > g.nx || j > g.ny) return;
+  if (i > g.nx) return;
   const cx<T>* f = rf + (long long)rhs * gf.vstride;
-  const long long pc = gf.at(2 * i, 2 * j);
-  cx<T> acc = mk<T>(0, 0);
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const long long pc = gf.at(2 * i, 2 * j);
+    cx<T> acc = mk<T>(0, 0);
 #pragma unroll
-  for (int b = -2; b <= 2; ++b) {
-    const cx<T>* row = f + pc + (long long)b * gf.pitch;
-    cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
-    t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
-    t = add<T>(t, scl<T>(T(0.75), row[0]));
-    acc = add<T>(acc, scl<T>(bw<T>(b), t));
+    for (int b = -2; b <= 2; ++b) {
+      const cx<T>* row = f + pc + (long long)b * gf.pitch;
+      cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
+      t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
+      t = add<T>(t, scl<T>(T(0.75), row[0]));
+      acc = add<T>(acc, scl<T>(bw<T>(b), t));
+    }
+    rc[off + g.at(i, j)] = scl<T>(T(0.25), acc);
   }
-  rc[off + g.at(i, j)] = scl<T>(T(0.25), acc);
 }
 
 // x_f(i,j) += sum_{I,J} P(i,I) P(j,J) e_c(I,J)   (Eq. (xex) in each direction)
@@ -171,22 +210,26 @@ __global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const 
                                                          cx<T>* __restrict__ xf, const int* __restrict__ active) {
   NODE_INDEX
   if (active && !active[rhs]) return;
-  if (i > g.nx || j > g.ny) return;
+  if (i > g.nx) return;
   const cx<T>* c = ec + (long long)rhs * gc.vstride;
-  const int I = i >> 1, J = j >> 1;
+  const int I = i >> 1;
   auto rowval = [&](int JJ) -> cx<T> {
     const cx<T>* row = c + gc.at(I, JJ);
     if (i & 1) return scl<T>(T(0.5), add<T>(row[0], row[1]));
     return add<T>(scl<T>(T(0.125), add<T>(row[-1], row[1])), scl<T>(T(0.75), row[0]));
   };
-  cx<T> v;
-  if (j & 1) {
-    v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
-  } else {
-    v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const int J = j >> 1;
+    cx<T> v;
+    if (j & 1) {
+      v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
+    } else {
+      v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+    }
+    const long long p = off + g.at(i, j);
+    xf[p] = add<T>(xf[p], v);
   }
-  const long long p = off + g.at(i, j);
-  xf[p] = add<T>(xf[p], v);
 }
 
 template <class T>
@@ -194,65 +237,36 @@ __global__ void __launch_bounds__(BX * BY) k_copy_masked(Grid g, const cx<T>* __
                                                          const int* __restrict__ active) {
   NODE_INDEX
   if (active && !active[rhs]) return;
-  if (i > g.nx || j > g.ny) return;
-  const long long p = off + g.at(i, j);
-  dst[p] = src[p];
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const long long p = off + g.at(i, j);
+    dst[p] = src[p];
+  }
 }
 
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_pack(Grid g, const double2* __restrict__ user, cx<T>* __restrict__ v, int conj) {
   NODE_INDEX
-  if (i > g.nx || j > g.ny) return;
-  double2 u = user[((long long)rhs * (g.ny + 1) + j) * (g.nx + 1) + i];
-  if (conj) u.y = -u.y;
-  v[off + g.at(i, j)] = mk<T>((T)u.x, (T)u.y);
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    double2 u = user[((long long)rhs * (g.ny + 1) + j) * (g.nx + 1) + i];
+    if (conj) u.y = -u.y;
+    v[off + g.at(i, j)] = mk<T>((T)u.x, (T)u.y);
+  }
 }
 
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_unpack(Grid g, const cx<T>* __restrict__ v, double2* __restrict__ user, int conj) {
   NODE_INDEX
-  if (i > g.nx || j > g.ny) return;
-  const cx<T> a = v[off + g.at(i, j)];
-  user[((long long)rhs * (g.ny + 1) + j) * (g.nx + 1) + i] = make_double2((double)a.x, conj ? -(double)a.y : (double)a.y);
-}
-
-// ------------------------------------------------------------------ stopping test
-
-__global__ void __launch_bounds__(256) k_stop(const double* __restrict__ partial, int nblk, const double* __restrict__ bnorm,
-                                              const double* __restrict__ tolp, int* active, int* state, int* cycles,
-                                              double* relres, double* hist, int hist_len, int* n_active, int count) {
-  __shared__ double sh[32];
-  const int rhs = blockIdx.x;
-  if (!active[rhs]) return;   // block-uniform
-  double v[1] = {0.0};
-  for (int k = threadIdx.x; k < nblk; k += blockDim.x) v[0] += partial[(long long)rhs * nblk + k];
-  block_sum<1>(v, sh);
-  if (threadIdx.x == 0) {
-    const double tol = tolp[0], diverge = tolp[1];
-    const double rr = sqrt(v[0]) / bnorm[rhs];
-    relres[rhs] = rr;
-    if (count) {
-      const int c = ++cycles[rhs];
-      if (c <= hist_len) hist[(long long)rhs * hist_len + c - 1] = rr;
-    }
-    int st = 0;
-    if (!(rr == rr) || rr > diverge) st = 2;      // NaN or divergence
-    else if (rr <= tol) st = 1;
-    if (st) {
-      state[rhs] = st;
-      active[rhs] = 0;
-      atomicSub(n_active, 1);
-    }
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const cx<T> a = v[off + g.at(i, j)];
+    user[((long long)rhs * (g.ny + 1) + j) * (g.nx + 1) + i] =
+        make_double2((double)a.x, conj ? -(double)a.y : (double)a.y);
   }
-}
-
-__global__ void __launch_bounds__(256) k_norm_finish(const double* __restrict__ partial, int nblk, double* out) {
-  __shared__ double sh[32];
-  const int rhs = blockIdx.x;
-  double v[1] = {0.0};
-  for (int k = threadIdx.x; k < nblk; k += blockDim.x) v[0] += partial[(long long)rhs * nblk + k];
-  block_sum<1>(v, sh);
-  if (threadIdx.x == 0) out[rhs] = sqrt(v[0]);
 }
 
 // ------------------------------------------------------------------ gradient
@@ -301,25 +315,24 @@ void launch_jacobi(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T
   });
 }
 template <class T>
-int launch_resnorm(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, double* partial, int B,
-                   const int* active, cudaStream_t s) {
-  dim3 grd = node_grid(g, B);
+void launch_resnorm_stop(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, int B, const Ctl& c,
+                         int count, cudaStream_t s) {
   with_op<T>(v, g.nx, g.ny, [&](auto op) {
-    k_resnorm<T, decltype(op)><<<grd, dim3(BX, BY), 0, s>>>(g, op, x, b, partial, active);
+    k_resnorm_stop<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, c, count);
   });
-  return grd.x * grd.y;
 }
-int launch_resid_cast_norm(const Grid& g, const OpView<double>& v, const double2* x, const double2* b, float2* r32,
-                           double* partial, int B, const int* active, cudaStream_t s) {
-  // r32 uses the same geometry as the FP64 level-0 vectors except the pitch
-  // may differ; the caller passes vectors of identical Grid, so reuse g.
-  dim3 grd = node_grid(g, B);
+void launch_resid_cast_stop(const Grid& g, const OpView<double>& v, const double2* x, const double2* b, float2* r32,
+                            int B, const Ctl& c, int count, cudaStream_t s) {
   Op0<double> op{v.c0, v.kf, g.nx, g.ny};
-  k_resid_cast_norm<<<grd, dim3(BX, BY), 0, s>>>(g, op, x, b, r32, g, partial, active);
-  return grd.x * grd.y;
+  k_resid_cast_stop<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, r32, c, count);
 }
 void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s) {
-  k_update_mixed<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, g, x, e, active);
+  k_update_mixed<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, x, e, active);
+}
+template <class T>
+void launch_vecnorm_fin(const Grid& g, const cx<T>* v, int B, double* out, double* partial, unsigned* tickets,
+                        cudaStream_t s) {
+  k_vecnorm_fin<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, v, out, partial, tickets);
 }
 template <class T>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<T>* rf, cx<T>* rc, int B, const int* active,
@@ -341,20 +354,6 @@ template <class T> void launch_pack(const Grid& g, const double2* user, cx<T>* v
 template <class T> void launch_unpack(const Grid& g, const cx<T>* v, double2* user, int B, int conj, cudaStream_t s) {
   k_unpack<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, v, user, conj);
 }
-template <class T> int launch_vecnorm(const Grid& g, const cx<T>* v, double* partial, int B, cudaStream_t s) {
-  dim3 grd = node_grid(g, B);
-  k_vecnorm<T><<<grd, dim3(BX, BY), 0, s>>>(g, v, partial);
-  return grd.x * grd.y;
-}
-void launch_stop(const double* partial, int nblk, int B, const double* bnorm, const double* tolp, int* active,
-                 int* state, int* cycles, double* relres, double* hist, int hist_len, int* n_active, int count,
-                 cudaStream_t s) {
-  k_stop<<<B, 256, 0, s>>>(partial, nblk, bnorm, tolp, active, state, cycles, relres, hist, hist_len, n_active,
-                           count);
-}
-void launch_norm_finish(const double* partial, int nblk, int B, double* out, cudaStream_t s) {
-  k_norm_finish<<<B, 256, 0, s>>>(partial, nblk, out);
-}
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u, const double2* lam,
                      int nsrc, double* g, cudaStream_t s) {
   k_gradient<<<dim3(cdiv(nx + 1, BX), cdiv(ny + 1, BY)), dim3(BX, BY), 0, s>>>(nx, ny, h, m, omega_f, u, lam, nsrc, g);
@@ -366,15 +365,15 @@ void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, 
   template void launch_apply<T>(const Grid&, const OpView<T>&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t); \
   template void launch_jacobi<T>(const Grid&, const OpView<T>&, const cx<T>*, const cx<T>*, cx<T>*, int,           \
                                  const int*, cudaStream_t);                                                        \
-  template int launch_resnorm<T>(const Grid&, const OpView<T>&, const cx<T>*, const cx<T>*, double*, int,          \
-                                 const int*, cudaStream_t);                                                        \
+  template void launch_resnorm_stop<T>(const Grid&, const OpView<T>&, const cx<T>*, const cx<T>*, int, const Ctl&, \
+                                       int, cudaStream_t);                                                         \
   template void launch_restrict<T>(const Grid&, const Grid&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t); \
   template void launch_prolong_add<T>(const Grid&, const Grid&, const cx<T>*, cx<T>*, int, const int*,            \
                                       cudaStream_t);                                                               \
   template void launch_copy_masked<T>(const Grid&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t);          \
   template void launch_pack<T>(const Grid&, const double2*, cx<T>*, int, int, cudaStream_t);                      \
   template void launch_unpack<T>(const Grid&, const cx<T>*, double2*, int, int, cudaStream_t);                    \
-  template int launch_vecnorm<T>(const Grid&, const cx<T>*, double*, int, cudaStream_t);
+  template void launch_vecnorm_fin<T>(const Grid&, const cx<T>*, int, double*, double*, unsigned*, cudaStream_t);
 INST(double)
 INST(float)
 

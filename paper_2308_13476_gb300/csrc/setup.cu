@@ -17,11 +17,18 @@ __device__ __forceinline__ double bwd(int d) {
 __device__ double2 op_coef(const OpView<double>& v, int nx, int ny, int i, int j, int dy, int dx, double beta2) {
   const int i2 = i + dx, j2 = j + dy;
   if (i2 < 0 || i2 > nx || j2 < 0 || j2 > ny) return make_double2(0, 0);
-  if (v.kind != 1) {
+  if (v.kind == 2 || v.kind == 3) {
     const int r = v.kind;
     if (dx < -r || dx > r || dy < -r || dy > r) return make_double2(0, 0);
     const int e = (dy + r) * (2 * r + 1) + (dx + r);
     return v.st[e * v.plane + (long long)j * (nx + 1) + i];
+  }
+  if (v.kind >= 4) {   // W_y[j][dy] G_x[i][dx] + H_y[j][dy] W_x[i][dx]
+    const int r = v.kind - 2, w = 2 * r + 1;
+    if (dx < -r || dx > r || dy < -r || dy > r) return make_double2(0, 0);
+    const double2 G = v.gx[i * w + dx + r], H = v.hy[j * w + dy + r];
+    const double Wx = v.wx[i * w + dx + r], Wy = v.wy[j * w + dy + r];
+    return make_double2(Wy * G.x + H.x * Wx, Wy * G.y + H.y * Wx);
   }
   const Op0Consts<double>* c = v.c0;
   const int bx = (i == 0 || i == nx), by = (j == 0 || j == ny);
@@ -137,7 +144,7 @@ __global__ void s_dense(OpView<double> v, int nx, int ny, double2* __restrict__ 
   const long long r = idx / N, c = idx % N;
   const int i = (int)(r % (nx + 1)), j = (int)(r / (nx + 1));
   const int i2 = (int)(c % (nx + 1)), j2 = (int)(c / (nx + 1));
-  const int R = v.kind == 1 ? 1 : v.kind;
+  const int R = op_radius(v.kind);
   const int dx = i2 - i, dy = j2 - j;
   double2 val = make_double2(0, 0);
   if (dx >= -R && dx <= R && dy >= -R && dy <= R) val = op_coef(v, nx, ny, i, j, dy, dx, 0.0);
@@ -232,7 +239,83 @@ __global__ void s_coarse_solve(Grid g, const double2* __restrict__ inv, int N, c
   }
 }
 
+// 1D factors of the fine operator, rows [n+1][3] (offsets -1, 0, +1):
+// L1 = Neumann Laplacian (row 0: [0, 1, -1], row n: [-1, 1, 0]), W1 = diag(1/2,
+// 1, ..., 1, 1/2), B1 = diag(1, 0, ..., 0, 1);  g = L1/h^2 - (1 + i beta2) k^2 W1
+// - i (k/h) B1, hf = L1/h^2 - i (k/h) B1, w = W1.
+__global__ void s_factors0(int n, double h, double k, double beta2, double2* g, double2* hf, double2* w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const double ih2 = 1.0 / (h * h);
+  const bool bnd = (i == 0 || i == n);
+  const double lm = i > 0 ? -1.0 : 0.0, lp = i < n ? -1.0 : 0.0, lc = bnd ? 1.0 : 2.0;
+  const double wi = bnd ? 0.5 : 1.0, bi = bnd ? 1.0 : 0.0;
+  const double k2 = k * k;
+  g[i * 3 + 0] = make_double2(lm * ih2, 0);
+  g[i * 3 + 1] = make_double2(lc * ih2 - wi * k2, -wi * (beta2 * k2) - bi * (k / h));
+  g[i * 3 + 2] = make_double2(lp * ih2, 0);
+  hf[i * 3 + 0] = make_double2(lm * ih2, 0);
+  hf[i * 3 + 1] = make_double2(lc * ih2, -bi * (k / h));
+  hf[i * 3 + 2] = make_double2(lp * ih2, 0);
+  w[i * 3 + 0] = make_double2(0, 0);
+  w[i * 3 + 1] = make_double2(wi, 0);
+  w[i * 3 + 2] = make_double2(0, 0);
+}
+
+// X_c[I][d] = sum_{a, a2} 1/2 w(a - 2I) X[a][a2 - a] w(a2 - 2(I + d)), one thread per (I, d).
+__global__ void s_galerkin_1d(const double2* __restrict__ X, int nf, int rf, double2* __restrict__ Xc, int rc) {
+  const int nc = nf / 2, wc = 2 * rc + 1, wf = 2 * rf + 1;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (nc + 1) * wc) return;
+  const int I = idx / wc, d = idx % wc - rc, I2 = I + d;
+  double2 acc = make_double2(0, 0);
+  if (I2 >= 0 && I2 <= nc) {
+    for (int a = 2 * I - 2; a <= 2 * I + 2; ++a) {
+      if (a < 0 || a > nf) continue;
+      for (int a2 = 2 * I2 - 2; a2 <= 2 * I2 + 2; ++a2) {
+        const int e = a2 - a;
+        if (a2 < 0 || a2 > nf || e < -rf || e > rf) continue;
+        const double wgt = 0.5 * bwd(a - 2 * I) * bwd(a2 - 2 * I2);
+        const double2 xv = X[a * wf + e + rf];
+        acc.x += wgt * xv.x;
+        acc.y += wgt * xv.y;
+      }
+    }
+  }
+  Xc[idx] = acc;
+}
+
+__global__ void s_real_part(const double2* __restrict__ a, double* __restrict__ b, long long n) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) b[q] = a[q].x;
+}
+
+__global__ void s_diaginv_op(OpView<double> v, int nx, int ny, double omega, double2* __restrict__ dinv) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)(nx + 1) * (ny + 1)) return;
+  const int i = (int)(q % (nx + 1)), j = (int)(q / (nx + 1));
+  const double2 d = op_coef(v, nx, ny, i, j, 0, 0, 0.0);
+  const double2 x = make_double2(omega * d.x, omega * d.y);
+  const double dd = x.x * x.x + x.y * x.y;
+  dinv[q] = make_double2(x.x / dd, -x.y / dd);
+}
+
 // ------------------------------------------------------------------ wrappers
+
+void launch_factors0(int n, double h, double k, double beta2, double2* g, double2* hf, double2* w, cudaStream_t s) {
+  s_factors0<<<cdiv(n + 1, 128), 128, 0, s>>>(n, h, k, beta2, g, hf, w);
+}
+void launch_galerkin_1d(const double2* X, int nf, int rf, double2* Xc, int rc, cudaStream_t s) {
+  const int n = (nf / 2 + 1) * (2 * rc + 1);
+  s_galerkin_1d<<<cdiv(n, 128), 128, 0, s>>>(X, nf, rf, Xc, rc);
+}
+void launch_real_part(const double2* a, double* b, long long n, cudaStream_t s) {
+  if (n > 0) s_real_part<<<cdiv(n, 256), 256, 0, s>>>(a, b, n);
+}
+void launch_diaginv_op(const OpView<double>& op, int nx, int ny, double omega, double2* dinv, cudaStream_t s) {
+  const long long n = (long long)(nx + 1) * (ny + 1);
+  s_diaginv_op<<<cdiv(n, 256), 256, 0, s>>>(op, nx, ny, omega, dinv);
+}
 
 void launch_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, double k, double omega, double beta2,
                       cudaStream_t s) {

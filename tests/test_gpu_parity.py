@@ -81,29 +81,44 @@ CASES = [
 ]
 
 
+# coarse_nodes: 0 = every level as grid-wide kernels; None = library default;
+# 10**6 = the whole cycle inside the single-CTA interpreter
+COARSE = [0, None, 10**6]
+
+
+@pytest.mark.parametrize("cn", COARSE, ids=["grid", "default", "cta"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_fp64_iterates_and_cycle_counts(case):
+def test_fp64_iterates_and_cycle_counts(case, cn):
+    """Jacobi cycles are a fixed affine map, so whole-solve iterates must agree
+    to 1e-10.  GMRES(3)-smoothed cycles are a nonlinear map that amplifies
+    rounding differences (the oracle's own MGS and Gram-matrix MGS forms
+    drift apart to ~1e-8 by cycle 12 on these grids), so for GMRES the 1e-10
+    bar applies to one cycle started from the oracle's previous iterate, and
+    whole-solve iterates are compared at 1e-6."""
     name, nx, ny, k, beta2, sm, gamma, n1, n2, tol = case
     h = 1.0 / max(nx, ny)
     b = synth.point_source(nx, ny, h)
     opt = ocycle.CycleOptions(gamma, sm, n1, n2, 4.5)
     ref = _oracle_run(nx, ny, h, k, beta2, opt, b, tol)
     assert ref.converged
-    s = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2)
+    whole = 1e-10 if sm == "jacobi" else 1e-6
+    s = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, coarse_nodes=cn)
     x, st, cyc, rr = s.solve(dev(b), tol=tol)
     assert st == hm.MG_OK
     assert cyc[0] == ref.cycles
-    assert rel(host(x)[0], ref.x) <= 1e-10
+    assert rel(host(x)[0], ref.x) <= whole
     hist = np.array(s.history(ref.cycles)[0])
-    assert np.allclose(hist, ref.history, rtol=1e-9, atol=0)
-    # iterates after a few intermediate cycle counts
-    for m in sorted({1, 2, ref.cycles // 2}):
-        s2 = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, max_cycles=m)
-        xm, st2, cm, _ = s2.solve(dev(b), tol=tol)
-        assert st2 == hm.MG_EMAXIT and cm[0] == m
-        assert rel(host(xm)[0], ref.iterates[m - 1]) <= 1e-10, m
-        s2.close()
+    assert np.allclose(hist, ref.history, rtol=1e-9 if sm == "jacobi" else 1e-3, atol=0)
     s.close()
+    # one cycle from the same input iterate, at several points of the solve
+    s1 = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, max_cycles=1,
+                   coarse_nodes=cn)
+    for m in sorted({1, 2, ref.cycles // 2, ref.cycles}):
+        x0 = np.zeros_like(b) if m == 1 else ref.iterates[m - 2].reshape(b.shape)
+        xm, st1, cm, _ = s1.solve(dev(b), x=dev(x0)[None].contiguous(), tol=1e-300)
+        assert st1 == hm.MG_EMAXIT and cm[0] == 1
+        assert rel(host(xm)[0], ref.iterates[m - 1]) <= 1e-10, m
+    s1.close()
 
 
 def test_variable_k_iterates():
@@ -116,10 +131,22 @@ def test_variable_k_iterates():
     s = hm.Solver(nx, ny, h, dev(k, torch.float64), 1 / 25.0, smoother="gmres3")
     x, st, cyc, _ = s.solve(dev(b), tol=1e-7)
     assert st == hm.MG_OK and cyc[0] == ref.cycles
-    assert rel(host(x)[0], ref.x) <= 1e-10
+    assert rel(host(x)[0], ref.x) <= 1e-6
+    s1 = hm.Solver(nx, ny, h, dev(k, torch.float64), 1 / 25.0, smoother="gmres3", max_cycles=1)
+    x0 = ref.iterates[ref.cycles // 2 - 1].reshape(b.shape)
+    xm, _, _, _ = s1.solve(dev(b), x=dev(x0)[None].contiguous(), tol=1e-300)
+    assert rel(host(xm)[0], ref.iterates[ref.cycles // 2]) <= 1e-10
+    # Jacobi on the same variable-k problem: whole-solve iterates at 1e-10
+    optj = ocycle.CycleOptions(1, "jacobi", 2, 2, 4.5)
+    refj = _oracle_run(nx, ny, h, k, 0.7, optj, b, 1e-6)
+    sj = hm.Solver(nx, ny, h, dev(k, torch.float64), 0.7, nu_pre=2, nu_post=2)
+    x, st, cyc, _ = sj.solve(dev(b), tol=1e-6)
+    assert st == hm.MG_OK and cyc[0] == refj.cycles
+    assert rel(host(x)[0], refj.x) <= 1e-10
 
 
-def test_batch_each_rhs_matches_oracle():
+@pytest.mark.parametrize("cn", COARSE, ids=["grid", "default", "cta"])
+def test_batch_each_rhs_matches_oracle(cn):
     nx = ny = 32
     h = 1.0 / 32
     srcs = synth.source_row(nx, ny, h, 3)
@@ -127,7 +154,7 @@ def test_batch_each_rhs_matches_oracle():
     H = ohier.build_hierarchy(nx, ny, h, 20.0, 0.7)
     opt = ocycle.CycleOptions(1, "jacobi", 1, 1, 4.5)
     refs = [ocycle.mg_solve(H, srcs[q].ravel(), 1e-6, opt) for q in range(3)]
-    s = hm.Solver(nx, ny, h, 20.0, 0.7, batch=3)
+    s = hm.Solver(nx, ny, h, 20.0, 0.7, batch=3, coarse_nodes=cn)
     x, st, cyc, rr = s.solve(dev(srcs), tol=1e-6)
     assert st == hm.MG_OK
     for q in range(3):
@@ -146,8 +173,8 @@ def test_mixed_precision_against_fp64_oracle():
     opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
     H = ohier.build_hierarchy(nx, ny, h, k, 1 / k)
     ref = ocycle.mg_solve(H, b.ravel(), 1e-12, opt)
-    for sm, beta2 in (("gmres3", 1 / k), ("jacobi", 0.7)):
-        s = hm.Solver(nx, ny, h, k, beta2, smoother=sm, nu_pre=2, nu_post=2, precision="mixed")
+    for sm, beta2, cn in (("gmres3", 1 / k, None), ("jacobi", 0.7, None), ("gmres3", 1 / k, 0), ("gmres3", 1 / k, 10**6)):
+        s = hm.Solver(nx, ny, h, k, beta2, smoother=sm, nu_pre=2, nu_post=2, precision="mixed", coarse_nodes=cn)
         x, st, cyc, rr = s.solve(dev(b), tol=1e-6)
         assert st == hm.MG_OK and rr[0] <= 1e-6
         r = b.ravel() - H.A[0] @ host(x)[0].ravel()
