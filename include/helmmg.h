@@ -173,6 +173,32 @@ mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, dou
  * nodes counted once per graph launch) and the number of graph launches. */
 mg_status mg_counters(mg_handle h, long long* kernel_launches, long long* graph_launches);
 
+/* ---- allocation-free call ---- */
+
+/* ||b - A x||_2 and ||b||_2 for the fine-level Helmholtz operator of
+ * mg_setup (same discretisation) on an nx by ny grid of cell size h, without
+ * any handle and without allocating device memory.  The paper has no
+ * counterpart; this is a service for callers that cannot allocate when they
+ * need a residual: code running while another framework's memory pool owns
+ * the device, latency-critical loops that cannot absorb the device-wide
+ * synchronisation of an allocation, or contexts where allocation is not
+ * permitted at all.
+ *   k_field  NULL for constant k = k_const, else a DEVICE array of
+ *            (ny+1)*(nx+1) wavenumbers
+ *   x, b     DEVICE, (ny+1)*(nx+1) complex128, dense rows (read only)
+ *   out      DEVICE double[2]: out[0] = ||b - A x||, out[1] = ||b||
+ *   stream   cudaStream_t (NULL = legacy default stream); the call only
+ *            enqueues work, the results are ready when the stream reaches them
+ * Scratch: one file-scope device array of 256 KiB + 256 B per device
+ * (partial sums of at most 16384 thread blocks of 32 x 32 nodes), held until
+ * the process exits.  Grids needing more blocks (about 16.7 M nodes) are
+ * rejected with MG_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  All calls share the array: calls whose kernels overlap on the GPU
+ * race and must be serialised by the caller. */
+mg_status mg_residual_norm_static(int nx, int ny, double h, const double* k_field, double k_const, const void* x,
+                                  const void* b, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "MG_OK", -1: "MG_EINVAL", -2: "MG_ENOMEM", -3: "MG_ECUDA", -4
                 -5: "MG_EDIVERGED", -6: "MG_ETIMEOUT", -7: "MG_ESTATE"}
 EXPORTED = ["mg_default_options", "mg_setup", "mg_solve", "mg_adjoint", "mg_gradient", "mg_destroy",
             "mg_last_error", "mg_level_info", "mg_apply", "mg_get_stencil", "mg_history", "mg_profile",
-            "mg_counters"]
+            "mg_counters", "mg_residual_norm_static"]
 
 
 class HelmmgUnavailable(RuntimeError):
@@ -70,6 +70,7 @@ def load_library(path=LIB_PATH):
     lib.mg_history.argtypes = [vp, dp, i]
     lib.mg_profile.argtypes = [vp, i, i, i, dp, dp]
     lib.mg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.mg_residual_norm_static.argtypes = [i, i, d, vp, d, vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("mg_default_options", "mg_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -192,6 +193,19 @@ def mg_counters(hdl):
     k, g = ctypes.c_longlong(), ctypes.c_longlong()
     _check(load_library().mg_counters(ctypes.c_void_p(hdl), ctypes.byref(k), ctypes.byref(g)))
     return k.value, g.value
+
+
+def mg_residual_norm_static(nx, ny, h, k, x, b, out, stream=None):
+    """out[0] = ||b - A x||, out[1] = ||b|| on the device, without any device
+    allocation by the library (see include/helmmg.h).  ``k``: float or a
+    float64 CUDA tensor (ny+1, nx+1); x, b: complex128 CUDA grids; out: a
+    float64 CUDA tensor of 2 entries."""
+    import torch
+    kp, kc = (None, float(k)) if isinstance(k, (int, float)) else (_ptr(k, torch.float64, "k"), 0.0)
+    st = stream.cuda_stream if stream is not None else None
+    _check(load_library().mg_residual_norm_static(int(nx), int(ny), float(h), kp, kc, _ptr(x, torch.complex128, "x"),
+                                                  _ptr(b, torch.complex128, "b"), _ptr(out, torch.float64, "out"),
+                                                  ctypes.c_void_p(st)))
 
 
 # ------------------------------------------------------------- convenience

@@ -16,6 +16,10 @@ using namespace hmg;
 
 static thread_local std::string g_err;
 
+namespace hmg {
+void hmg_set_error(const char* msg) { g_err = msg; }
+}  // namespace hmg
+
 #define FAIL(code, ...)                                          \
   do {                                                           \
     char _b[512];                                                \

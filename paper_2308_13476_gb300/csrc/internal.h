@@ -157,4 +157,7 @@ void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, 
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Sets the message mg_last_error() returns on this host thread (capi.cu).
+void hmg_set_error(const char* msg);
+
 }  // namespace hmg
