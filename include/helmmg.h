@@ -61,7 +61,7 @@ typedef enum {
   MG_ECUDA = -3,      /* CUDA runtime error                                     */
   MG_EMAXIT = -4,     /* max_cycles reached before tol (x = last iterate)       */
   MG_EDIVERGED = -5,  /* relative residual above 1e6 or not finite             */
-  MG_ETIMEOUT = -6,   /* reserved: a bounded device wait gave up                */
+  MG_ETIMEOUT = -6,   /* a bounded device wait (grid-wide barrier) gave up      */
   MG_ESTATE = -7      /* call not valid in the handle's state (e.g. singular
                          coarsest operator)                                      */
 } mg_status;
@@ -79,12 +79,16 @@ typedef struct {
   int min_coarse;   /* stop coarsening below this many grid nodes (Sec. 5: 10) */
   int batch;        /* B: right-hand sides solved together                      */
   int coarse_nodes; /* levels with at most this many grid nodes (and all below
-                       them) run as one CTA per RHS per visit; 0 = never      */
+                       them) run inside one launch per visit; 0 = never       */
+  int coarse_mode;  /* that launch: 0 = one CTA per right-hand side,
+                       1 = a cooperative grid of all co-resident CTAs with
+                       bounded grid-wide barriers (MG_ETIMEOUT if one gives up) */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
- * min_coarse 10, batch 1; coarse_nodes 1100; default stream. */
+ * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0; default
+ * stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).

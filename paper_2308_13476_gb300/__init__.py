@@ -40,7 +40,7 @@ class MgOptions(ctypes.Structure):
     _fields_ = [("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
-                ("coarse_nodes", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -226,7 +226,7 @@ class Solver:
 
     def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
                  precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, coarse_nodes=None,
-                 stream=None):
+                 coarse_mode=None, stream=None):
         o = mg_default_options()
         o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
         o.smoother = SMOOTHERS[smoother]
@@ -235,6 +235,8 @@ class Solver:
         o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
         if coarse_nodes is not None:
             o.coarse_nodes = int(coarse_nodes)
+        if coarse_mode is not None:
+            o.coarse_mode = int(coarse_mode)
         o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         self.nx, self.ny, self.h, self.batch = nx, ny, h, batch
         if isinstance(k, (int, float)):

@@ -100,6 +100,8 @@ struct mg_ctx {
   cudaGraph_t graph = nullptr;
   std::vector<void*> allocs;
   int lc = 1 << 30;                  // first level run by the coarse-cycle interpreter
+  int coop_grid = 0;                 // > 0: cooperative interpreter with this many blocks
+  CoopCtl coop{};
   CoarsePlan<double> plan64;
   CoarsePlan<float> plan32;
   long long graph_kernels = 0;     // kernel nodes in the cycle graph
@@ -122,6 +124,8 @@ static cudaError_t dalloc(mg_ctx* c, void** p, size_t bytes) {
   return cudaMemset(*p, 0, bytes);
 }
 
+// Rows per thread: several on big grids (fewer, fuller blocks and fewer
+// reduction partials), one on small grids (more threads to hide latency).
 static Grid make_grid(int nx, int ny, int B) {
   Grid g;
   g.nx = nx;
@@ -129,9 +133,12 @@ static Grid make_grid(int nx, int ny, int B) {
   g.pitch = ((nx + 1 + 2 * HALO) + 3) / 4 * 4;
   g.rows = ny + 1 + 2 * HALO;
   g.vstride = (long long)g.pitch * g.rows;
-  (void)B;
+  const long long nodes = (long long)(nx + 1) * (ny + 1) * B;
+  g.ry = nodes >= (1LL << 20) ? 4 : (nodes >= (1LL << 18) ? 2 : 1);
   return g;
 }
+
+static long long node_blocks(const Grid& g) { return (long long)cdiv(g.nx + 1, BX) * cdiv(g.ny + 1, BY * g.ry); }
 
 static OpView<double> op64(const mg_ctx* c, int l) {
   OpView<double> v{};
@@ -228,7 +235,11 @@ template <class T> struct Emit {
   void cycle(int l) {
     const int L = c->nlev;
     if (l >= lc) {   // one visit of the sub-cycle below, in one launch
-      launch_coarse_cycle<T>(plan->levels, plan->steps, plan->nsteps, c->cinv, c->ncoarse, c->B, c->active, s);
+      if (c->coop_grid > 0)
+        launch_cycle_coop<T>(plan->levels, c->nlev, plan->steps, plan->nsteps, c->cinv, c->ncoarse, c->active,
+                             c->B, c->coop_grid, c->coop, s);
+      else
+        launch_coarse_cycle<T>(plan->levels, plan->steps, plan->nsteps, c->cinv, c->ncoarse, c->B, c->active, s);
       return;
     }
     if (l == L - 1) {
@@ -428,6 +439,7 @@ void mg_default_options(mg_options* o) {
   o->min_coarse = 10;
   o->batch = 1;
   o->coarse_nodes = 1100;
+  o->coarse_mode = 0;
   o->stream = nullptr;
 }
 
@@ -556,8 +568,9 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     if (st) FAIL(MG_ESTATE, "coarsest operator is singular");
   }
   // work arrays
-  const int nblk0 = cdiv(g0.nx + 1, BX) * cdiv(g0.ny + 1, BY * RY);
-  CK(dalloc(c, (void**)&c->partial, sizeof(double) * (size_t)nblk0 * c->B * NVMAX));
+  long long nblk_max = 0;   // reduction partials: the most blocks of any level
+  for (int l = 0; l < c->nlev; ++l) nblk_max = std::max(nblk_max, node_blocks(c->lev[l].g));
+  CK(dalloc(c, (void**)&c->partial, sizeof(double) * (size_t)nblk_max * c->B * NVMAX));
   CK(dalloc(c, (void**)&c->tickets, sizeof(unsigned) * c->B));
   CK(dalloc(c, (void**)&c->gst, sizeof(double) * 96 * c->B));
   CK(dalloc(c, (void**)&c->active, sizeof(int) * c->B));
@@ -566,10 +579,10 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   CK(dalloc(c, (void**)&c->relres, sizeof(double) * c->B));
   CK(dalloc(c, (void**)&c->bnorm, sizeof(double) * c->B));
   CK(dalloc(c, (void**)&c->tolp, sizeof(double) * 2));
-  CK(dalloc(c, (void**)&c->n_active, sizeof(int)));
+  CK(dalloc(c, (void**)&c->n_active, sizeof(int) * 2));   // {active count, cooperative-barrier error}
   c->hist_len = std::min(o.max_cycles, 4096);
   CK(dalloc(c, (void**)&c->hist, sizeof(double) * (size_t)c->hist_len * c->B));
-  CK(cudaMallocHost((void**)&c->h_n_active, sizeof(int)));
+  CK(cudaMallocHost((void**)&c->h_n_active, sizeof(int) * 2));
   // vectors
   if (!mixed) {
     c->v64.resize(c->nlev);
@@ -605,6 +618,16 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   if (c->lc < c->nlev) {
     if (!mixed) CK(build_plan<double>(c, c->lc, c->plan64));
     else CK(build_plan<float>(c, c->lc, c->plan32));
+    if (o.coarse_mode == 1 && c->nlev <= COOP_MAXLEV) {   // cooperative grid: all co-resident blocks, split evenly over the RHS
+      const int gmax = mixed ? coop_max_blocks<float>(c->ncoarse) : coop_max_blocks<double>(c->ncoarse);
+      if (gmax >= c->B) {
+        c->coop_grid = (gmax / c->B) * c->B;
+        CK(dalloc(c, (void**)&c->coop.bar, sizeof(unsigned) * 2));
+        CK(dalloc(c, (void**)&c->coop.partial, sizeof(double) * (size_t)c->coop_grid * NVMAX));
+        c->coop.err = c->n_active + 1;
+        c->coop.spin_limit = 1LL << 22;
+      }
+    }
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
@@ -629,6 +652,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.max_cycles < 1 || o.min_coarse < 1) FAIL(MG_EINVAL, "max_cycles and min_coarse must be >= 1");
   if (o.batch < 1 || o.batch > 65535) FAIL(MG_EINVAL, "batch must be in 1..65535");
   if (o.coarse_nodes < 0) FAIL(MG_EINVAL, "coarse_nodes must be >= 0");
+  if (o.coarse_mode != 0 && o.coarse_mode != 1) FAIL(MG_EINVAL, "coarse_mode must be 0 or 1");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
@@ -705,7 +729,9 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
   CK(cudaMemcpyAsync(c->cycles, zero.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->bnorm, bsafe.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->tolp, tolv, sizeof(double) * 2, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c->n_active, &nact, sizeof(int), cudaMemcpyHostToDevice, s));
+  const int ctl2[2] = {nact, 0};
+  CK(cudaMemcpyAsync(c->n_active, ctl2, sizeof(int) * 2, cudaMemcpyHostToDevice, s));
+  if (c->coop.bar) CK(cudaMemsetAsync(c->coop.bar, 0, sizeof(unsigned) * 2, s));
   CK(cudaMemsetAsync(c->relres, 0, sizeof(double) * B, s));
   CK(cudaMemsetAsync(c->hist, 0, sizeof(double) * (size_t)c->hist_len * B, s));
   // initial test on x0
@@ -714,19 +740,24 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
   else
     launch_resnorm_stop<double>(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, B, ctl(c), 0, s);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int done = 0;
   // direct launches: 2 pack + norm + initial residual test + unpack
   c->last_launches = 5;
   c->last_graphs = 0;
-  while (*c->h_n_active > 0 && done < c->opt.max_cycles) {
+  while (c->h_n_active[0] > 0 && c->h_n_active[1] == 0 && done < c->opt.max_cycles) {
     CK(cudaGraphLaunch(c->gexec, s));
     ++done;
     c->last_graphs += 1;
     c->last_launches += c->graph_kernels;
-    CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+  }
+  if (c->h_n_active[1] != 0) {
+    launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
+    cudaStreamSynchronize(s);
+    FAIL(MG_ETIMEOUT, "a grid-wide barrier of the cooperative cycle kernel timed out");
   }
   launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
   std::vector<int> cyc(B);

@@ -13,28 +13,9 @@
 // solve; only the reductions are block-wide instead of grid-wide.
 #include "gmres.cuh"
 #include "internal.h"
+#include "levelops.cuh"
 
 namespace hmg {
-
-template <class T>
-__device__ __forceinline__ cx<T> lv_apply(const CLevel<T>& L, const cx<T>* x, long long p, int i, int j) {
-  switch (L.kind) {
-    case 1: return Op0<T>{L.c0, L.kf, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
-    case 2: return OpS<T, 2>{L.st, L.dinv, L.plane, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
-    case 3: return OpS<T, 3>{L.st, L.dinv, L.plane, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
-    case 4: return OpK<T, 2>{L.gx, L.wx, L.hy, L.wy, L.dinv, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
-    default: return OpK<T, 3>{L.gx, L.wx, L.hy, L.wy, L.dinv, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
-  }
-}
-
-template <class T> __device__ __forceinline__ cx<T> lv_dinv(const CLevel<T>& L, int i, int j) {
-  if (L.kind == 1) return Op0<T>{L.c0, L.kf, L.g.nx, L.g.ny}.diag_inv(i, j);
-  return L.dinv[(long long)j * (L.g.nx + 1) + i];
-}
-
-template <class T> __device__ __forceinline__ T cbw(int d) {
-  return d == 0 ? T(0.75) : (d == 1 || d == -1) ? T(0.5) : T(0.125);
-}
 
 // Node loop over one level: q -> (i, j, p).
 #define CTA_NODES(L)                                                         \
@@ -61,7 +42,7 @@ __device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, d
     {
       double t[1] = {(double)a0};
       block_sum<1>(t, sh);
-      if (tid == 0) fin_init(S, t);
+      if (tid == 0) fin_init<T>(S, t);
       __syncthreads();
     }
 #pragma unroll
@@ -83,9 +64,9 @@ __device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, d
       for (int l = 0; l < 6; ++l) d[l] = (double)dt[l];
       block_sum<6>(d, sh);
       if (tid == 0) {
-        if (J == 0) fin_a<0>(S, d);
-        else if (J == 1) fin_a<1>(S, d);
-        else fin_a<2>(S, d);
+        if (J == 0) fin_a<0, T>(S, d);
+        else if (J == 1) fin_a<1, T>(S, d);
+        else fin_a<2, T>(S, d);
       }
       __syncthreads();
       cx<T> c[3];
@@ -116,9 +97,9 @@ __device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, d
       for (int l = 0; l < 5; ++l) e5[l] = (double)et[l];
       block_sum<5>(e5, sh);
       if (tid == 0) {
-        if (J == 0) fin_b<0>(S, e5);
-        else if (J == 1) fin_b<1>(S, e5);
-        else fin_b<2>(S, e5);
+        if (J == 0) fin_b<0, T>(S, e5);
+        else if (J == 1) fin_b<1, T>(S, e5);
+        else fin_b<2, T>(S, e5);
       }
       __syncthreads();
     }

@@ -16,7 +16,7 @@ namespace hmg {
 constexpr int HALO = 4;
 constexpr int BX = 32;   // block shape of the node-parallel kernels
 constexpr int BY = 8;
-constexpr int RY = 4;    // grid rows per thread (a block covers BX x BY*RY nodes)
+constexpr int RYMAX = 4; // largest number of grid rows per thread (Grid::ry)
 constexpr int MAXR = 3;  // largest Galerkin stencil radius (7 x 7)
 constexpr int NVMAX = 8; // values per block partial record
 
@@ -57,6 +57,8 @@ struct Grid {
   int pitch;           // padded row length (elements)
   int rows;            // padded row count
   long long vstride;   // elements per right-hand side
+  int ry;              // grid rows per thread of the node kernels (1..RYMAX):
+                       // a block covers BX x (BY * ry) nodes
   __host__ __device__ __forceinline__ long long at(int i, int j) const {
     return (long long)(j + HALO) * pitch + (i + HALO);
   }

@@ -19,119 +19,119 @@ constexpr int G_M = 70;     // number of Arnoldi columns
 constexpr int G_BRK = 71;   // 1 = stop (breakdown or beta == 0)
 
 
-// min || beta e1 - Hbar y || by Givens rotations; Hbar is (m+1) x m.
-__device__ __forceinline__ void lsq(double* S) {
+// min || beta e1 - Hbar y || by Givens rotations; Hbar is (m+1) x m.  The
+// arithmetic runs in Ts (FP64 for the complex128 path, FP32 for the
+// complex64 cycles of the mixed path); the state S is stored in FP64.
+template <class Ts> __device__ __forceinline__ void lsq(double* S) {
   const int m = (int)S[G_M];
   if (m <= 0) return;
-  double Hr[4][3], Hi[4][3], gr[4], gi[4];
+  Ts Hr[4][3], Hi[4][3], gr[4], gi[4];
   for (int a = 0; a < 4; ++a) {
-    gr[a] = gi[a] = 0.0;
+    gr[a] = gi[a] = Ts(0);
     for (int c = 0; c < 3; ++c) {
-      Hr[a][c] = S[G_H + 2 * (a * 3 + c)];
-      Hi[a][c] = S[G_H + 2 * (a * 3 + c) + 1];
+      Hr[a][c] = (Ts)S[G_H + 2 * (a * 3 + c)];
+      Hi[a][c] = (Ts)S[G_H + 2 * (a * 3 + c) + 1];
     }
   }
-  gr[0] = S[G_BETA];
+  gr[0] = (Ts)S[G_BETA];
   for (int c = 0; c < m; ++c) {
-    // rotation zeroing Hbar[c+1][c] against Hbar[c][c]
-    const double ar = Hr[c][c], ai = Hi[c][c], br = Hr[c + 1][c], bi = Hi[c + 1][c];
-    const double na = sqrt(ar * ar + ai * ai), nb = sqrt(br * br + bi * bi);
-    const double nr = sqrt(na * na + nb * nb);
-    if (nr == 0.0) continue;
-    // G = [[cs, sn], [-conj(sn), cs]] with cs = |a|/r real, sn = (a/|a|) conj(b) / r
-    double cs, snr, sni;
-    if (na == 0.0) {
-      cs = 0.0; snr = 1.0; sni = 0.0;
-      // rows swap up to phase: sn = conj(b)/|b|
-      snr = br / nb; sni = -bi / nb;
+    // rotation zeroing Hbar[c+1][c] against Hbar[c][c]:
+    // G = [[cs, sn], [-conj(sn), cs]], cs = |a|/r real, sn = (a/|a|) conj(b) / r
+    const Ts ar = Hr[c][c], ai = Hi[c][c], br = Hr[c + 1][c], bi = Hi[c + 1][c];
+    const Ts na = sqrt(ar * ar + ai * ai), nb = sqrt(br * br + bi * bi);
+    const Ts nr = sqrt(na * na + nb * nb);
+    if (nr == Ts(0)) continue;
+    Ts cs, snr, sni;
+    if (na == Ts(0)) {
+      cs = Ts(0);
+      snr = br / nb;
+      sni = -bi / nb;
     } else {
       cs = na / nr;
-      const double pr = ar / na, pi = ai / na;     // a/|a|
-      snr = (pr * br + pi * bi) / nr;              // (a/|a|) * conj(b) / r
+      const Ts pr = ar / na, pi = ai / na;
+      snr = (pr * br + pi * bi) / nr;
       sni = (pi * br - pr * bi) / nr;
     }
     for (int col = c; col < m; ++col) {
-      const double xr = Hr[c][col], xi = Hi[c][col], yr = Hr[c + 1][col], yi = Hi[c + 1][col];
-      // new_c = cs x + sn y ; new_{c+1} = -conj(sn) x + cs y
+      const Ts xr = Hr[c][col], xi = Hi[c][col], yr = Hr[c + 1][col], yi = Hi[c + 1][col];
       Hr[c][col] = cs * xr + (snr * yr - sni * yi);
       Hi[c][col] = cs * xi + (snr * yi + sni * yr);
       Hr[c + 1][col] = -(snr * xr + sni * xi) + cs * yr;
       Hi[c + 1][col] = -(snr * xi - sni * xr) + cs * yi;
     }
-    const double xr = gr[c], xi = gi[c], yr = gr[c + 1], yi = gi[c + 1];
+    const Ts xr = gr[c], xi = gi[c], yr = gr[c + 1], yi = gi[c + 1];
     gr[c] = cs * xr + (snr * yr - sni * yi);
     gi[c] = cs * xi + (snr * yi + sni * yr);
     gr[c + 1] = -(snr * xr + sni * xi) + cs * yr;
     gi[c + 1] = -(snr * xi - sni * xr) + cs * yi;
   }
-  double yr[3] = {0, 0, 0}, yi[3] = {0, 0, 0};
+  Ts yr[3] = {0, 0, 0}, yi[3] = {0, 0, 0};
   for (int c = m - 1; c >= 0; --c) {
-    double tr = gr[c], ti = gi[c];
+    Ts tr = gr[c], ti = gi[c];
     for (int q = c + 1; q < m; ++q) {
       tr -= Hr[c][q] * yr[q] - Hi[c][q] * yi[q];
       ti -= Hr[c][q] * yi[q] + Hi[c][q] * yr[q];
     }
-    const double dr = Hr[c][c], di = Hi[c][c], dd = dr * dr + di * di;
+    const Ts dr = Hr[c][c], di = Hi[c][c], dd = dr * dr + di * di;
     yr[c] = (tr * dr + ti * di) / dd;
     yi[c] = (ti * dr - tr * di) / dd;
   }
   for (int c = 0; c < 3; ++c) {
-    S[G_Y + 2 * c] = c < m ? yr[c] : 0.0;
-    S[G_Y + 2 * c + 1] = c < m ? yi[c] : 0.0;
+    S[G_Y + 2 * c] = c < m ? (double)yr[c] : 0.0;
+    S[G_Y + 2 * c + 1] = c < m ? (double)yi[c] : 0.0;
   }
 }
 
+// ---- scalar steps of one Arnoldi pass, run by one thread ----
 
-// ---- scalar steps, run by thread 0 of the last block of each reduction ----
-
-__device__ __forceinline__ void fin_init(double* S, const double* v) {
+template <class Ts> __device__ __forceinline__ void fin_init(double* S, const double* v) {
   for (int k = 0; k < GS; ++k) S[k] = 0.0;
-  const double beta = sqrt(v[0]);
-  S[G_BETA] = beta;
+  const Ts beta = sqrt((Ts)v[0]);
+  S[G_BETA] = (double)beta;
   S[G_M] = 0;
-  if (beta == 0.0) S[G_BRK] = 1.0;
-  else S[G_S + 0] = 1.0 / beta;
+  if (beta == Ts(0)) S[G_BRK] = 1.0;
+  else S[G_S + 0] = (double)(Ts(1) / beta);
 }
 
 // h_lJ = <v_l, w> - sum_{q<l} h_qJ <v_l, v_q>, with <v_l, w> = s_l <u_l, w>
-template <int J> __device__ __forceinline__ void fin_a(double* S, const double* v) {
-  double hr[J + 1], hi[J + 1];
+template <int J, class Ts> __device__ __forceinline__ void fin_a(double* S, const double* v) {
+  Ts hr[J + 1], hi[J + 1];
   for (int l = 0; l <= J; ++l) {
-    double dr = S[G_S + l] * v[2 * l], di = S[G_S + l] * v[2 * l + 1];
+    const Ts sl = (Ts)S[G_S + l];
+    Ts dr = sl * (Ts)v[2 * l], di = sl * (Ts)v[2 * l + 1];
     for (int q = 0; q < l; ++q) {
-      const double gr = S[G_G + 2 * (l * 4 + q)], gi = S[G_G + 2 * (l * 4 + q) + 1];
+      const Ts gr = (Ts)S[G_G + 2 * (l * 4 + q)], gi = (Ts)S[G_G + 2 * (l * 4 + q) + 1];
       dr -= hr[q] * gr - hi[q] * gi;
       di -= hr[q] * gi + hi[q] * gr;
     }
     hr[l] = dr;
     hi[l] = di;
-    S[G_H + 2 * (l * 3 + J)] = dr;
-    S[G_H + 2 * (l * 3 + J) + 1] = di;
+    S[G_H + 2 * (l * 3 + J)] = (double)dr;
+    S[G_H + 2 * (l * 3 + J) + 1] = (double)di;
   }
 }
-
 
 // h_{J+1,J} = ||u_{J+1}||, breakdown test, Gram entries of v_{J+1}; the least
 // squares problem is solved once the Arnoldi process stops.
-template <int J> __device__ __forceinline__ void fin_b(double* S, const double* v) {
-  const double hn = sqrt(v[0]);
-  S[G_H + 2 * ((J + 1) * 3 + J)] = hn;
+template <int J, class Ts> __device__ __forceinline__ void fin_b(double* S, const double* v) {
+  const Ts hn = sqrt((Ts)v[0]);
+  S[G_H + 2 * ((J + 1) * 3 + J)] = (double)hn;
   S[G_H + 2 * ((J + 1) * 3 + J) + 1] = 0.0;
   S[G_M] = J + 1;
-  if (hn <= 1e-14 * S[G_BETA]) {
+  if (hn <= Ts(1e-14) * (Ts)S[G_BETA]) {
     S[G_BRK] = 1.0;
   } else {
-    const double sn = 1.0 / hn;
-    S[G_S + J + 1] = sn;
+    const Ts sn = Ts(1) / hn;
+    S[G_S + J + 1] = (double)sn;
     if (J < 2) {
       for (int l = 0; l <= J; ++l) {   // <v_{J+1}, v_l> = s_{J+1} s_l <u_{J+1}, u_l>
-        S[G_G + 2 * ((J + 1) * 4 + l)] = sn * S[G_S + l] * v[1 + 2 * l];
-        S[G_G + 2 * ((J + 1) * 4 + l) + 1] = sn * S[G_S + l] * v[2 + 2 * l];
+        const Ts f = sn * (Ts)S[G_S + l];
+        S[G_G + 2 * ((J + 1) * 4 + l)] = (double)(f * (Ts)v[1 + 2 * l]);
+        S[G_G + 2 * ((J + 1) * 4 + l) + 1] = (double)(f * (Ts)v[2 + 2 * l]);
       }
     }
   }
-  if (J == 2 || S[G_BRK] != 0.0) lsq(S);
+  if (J == 2 || S[G_BRK] != 0.0) lsq<Ts>(S);
 }
-
 
 }  // namespace hmg

@@ -151,6 +151,21 @@ struct CStep {
 template <class T> void launch_coarse_cycle(const CLevel<T>* levels, const CStep* steps, int nsteps,
                                             const double2* inv, int N, int B, const int* active, cudaStream_t s);
 
+// Cooperative multi-CTA interpreter (coop.cu): the same steps, all blocks of
+// the GPU, grid-wide barriers between phases.
+constexpr int COOP_THREADS = 256;
+constexpr int COOP_MAXLEV = 16;
+struct CoopCtl {
+  unsigned* bar;          // {arrival count, generation}, zero at rest
+  int* err;               // set to 1 when a barrier wait gave up
+  long long spin_limit;   // polls per barrier wait
+  double* partial;        // [B * bpr][NVMAX] block sums
+};
+template <class T> int coop_max_blocks(int N);
+template <class T> cudaError_t launch_cycle_coop(const CLevel<T>* levels, int nlev, const CStep* steps, int nsteps,
+                                                 const double2* inv, int N, const int* active, int B, int grid,
+                                                 const CoopCtl& c, cudaStream_t s);
+
 // Gradient of the receiver misfit (kernels_level.cu).
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u,
                      const double2* lam, int nsrc, double* g, cudaStream_t s);

@@ -26,7 +26,21 @@ namespace hmg {
   const int nblk = gridDim.x * gridDim.y;                \
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;   \
   const bool t0 = threadIdx.x == 0 && threadIdx.y == 0;
-#define GROWS for (int r_ = 0, j = blockIdx.y * BY * RY + threadIdx.y; r_ < RY; ++r_, j += BY)
+// Runs a scalar step on the RHS state in shared memory (all threads of the
+// block copy it in and out; thread 0 computes), so its many dependent reads
+// and writes stay on chip.
+template <class T, class F>
+__device__ __forceinline__ void staged(double* S, const double* v, F f) {
+  __shared__ double Ssh[GS];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x, nt = blockDim.x * blockDim.y;
+  for (int k = tid; k < GS; k += nt) Ssh[k] = S[k];
+  __syncthreads();
+  if (tid == 0) f(Ssh, v);
+  __syncthreads();
+  for (int k = tid; k < GS; k += nt) S[k] = Ssh[k];
+}
+
+#define GROWS for (int r_ = 0, j = blockIdx.y * BY * g.ry + threadIdx.y; r_ < g.ry; ++r_, j += BY)
 
 // u0 = b - A x, partial |u0|^2
 template <class T, class Op>
@@ -47,7 +61,7 @@ __global__ void __launch_bounds__(BX * BY) g_init(Grid g, Op op, const cx<T>* __
     }
   }
   double v[1] = {(double)a0};
-  if (reduce_last<1>(v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init(st + (long long)rhs * GS, v);
+  if (reduce_last<1>(v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(st + (long long)rhs * GS, v);
 }
 
 // w = A v_J (v_J = s_J u_J); partial dots <u_i, w> for i <= J
@@ -84,7 +98,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
   double v[2 * (J + 1)];
 #pragma unroll
   for (int k = 0; k < 2 * (J + 1); ++k) v[k] = (double)acc[k];
-  if (reduce_last<2 * (J + 1)>(v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_a<J>(S, v);
+  if (reduce_last<2 * (J + 1)>(v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
 }
 
 // u_{J+1} = w - sum_{i<=J} h_iJ s_i u_i ; partials |u_{J+1}|^2 and <u_{J+1}, u_l>, l <= J (J < 2)
@@ -136,7 +150,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restri
   double v[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = (double)acc[k];
-  if (reduce_last<NV>(v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_b<J>(S, v);
+  if (reduce_last<NV>(v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_b<J, T>(s, q); });
 }
 
 // x += sum_{i<m} y_i s_i u_i
@@ -173,7 +187,7 @@ __global__ void __launch_bounds__(BX * BY) g_update(Grid g, cx<T>* __restrict__ 
 template <class T>
 void gmres_smooth(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T>* b, int nu, int B, const int* active,
                   const GmresBufs& gb, cudaStream_t s) {
-  dim3 grd(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY * RY), B);
+  dim3 grd(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY * g.ry), B);
   cx<T>* u0 = (cx<T>*)gb.u[0];
   cx<T>* u1 = (cx<T>*)gb.u[1];
   cx<T>* u2 = (cx<T>*)gb.u[2];

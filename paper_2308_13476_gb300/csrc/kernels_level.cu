@@ -16,16 +16,16 @@ namespace hmg {
 // ------------------------------------------------------------------ helpers
 
 static inline dim3 node_grid(const Grid& g, int B) {
-  return dim3(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY * RY), B);
+  return dim3(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY * g.ry), B);
 }
 
-// Thread (tx, ty) of block (bx, by, rhs) handles node column i and the RY
-// rows j = by*BY*RY + r*BY + ty, r = 0..RY-1 (warps stay on one row).
+// Thread (tx, ty) of block (bx, by, rhs) handles node column i and the g.ry
+// rows j = by*BY*ry + r*BY + ty, r = 0..ry-1 (warps stay on one row).
 #define NODE_INDEX                                       \
   const int rhs = blockIdx.z;                            \
   const int i = blockIdx.x * BX + threadIdx.x;           \
   const long long off = (long long)rhs * g.vstride;
-#define FOR_ROWS for (int r_ = 0, j = blockIdx.y * BY * RY + threadIdx.y; r_ < RY; ++r_, j += BY)
+#define FOR_ROWS for (int r_ = 0, j = blockIdx.y * BY * g.ry + threadIdx.y; r_ < g.ry; ++r_, j += BY)
 
 // ------------------------------------------------------------------ operator kernels
 

@@ -81,12 +81,16 @@ CASES = [
 ]
 
 
-# coarse_nodes: 0 = every level as grid-wide kernels; None = library default;
-# 10**6 = the whole cycle inside the single-CTA interpreter
-COARSE = [0, None, 10**6]
+# execution modes: every level as grid-wide kernels; the library default
+# (small levels in one CTA per RHS); level 0 as grid-wide kernels and the rest
+# in one cooperative launch; the whole cycle in one CTA per RHS; the whole
+# cycle in one cooperative launch
+COARSE = [dict(coarse_nodes=0), dict(), dict(coarse_nodes=1200, coarse_mode=1),
+          dict(coarse_nodes=10**6, coarse_mode=0), dict(coarse_nodes=10**6, coarse_mode=1)]
+COARSE_IDS = ["grid", "default", "hybrid", "cta", "coop"]
 
 
-@pytest.mark.parametrize("cn", COARSE, ids=["grid", "default", "cta"])
+@pytest.mark.parametrize("cn", COARSE, ids=COARSE_IDS)
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_fp64_iterates_and_cycle_counts(case, cn):
     """Jacobi cycles are a fixed affine map, so whole-solve iterates must agree
@@ -102,7 +106,7 @@ def test_fp64_iterates_and_cycle_counts(case, cn):
     ref = _oracle_run(nx, ny, h, k, beta2, opt, b, tol)
     assert ref.converged
     whole = 1e-10 if sm == "jacobi" else 1e-6
-    s = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, coarse_nodes=cn)
+    s = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, **cn)
     x, st, cyc, rr = s.solve(dev(b), tol=tol)
     assert st == hm.MG_OK
     assert cyc[0] == ref.cycles
@@ -111,8 +115,7 @@ def test_fp64_iterates_and_cycle_counts(case, cn):
     assert np.allclose(hist, ref.history, rtol=1e-9 if sm == "jacobi" else 1e-3, atol=0)
     s.close()
     # one cycle from the same input iterate, at several points of the solve
-    s1 = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, max_cycles=1,
-                   coarse_nodes=cn)
+    s1 = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, max_cycles=1, **cn)
     for m in sorted({1, 2, ref.cycles // 2, ref.cycles}):
         x0 = np.zeros_like(b) if m == 1 else ref.iterates[m - 2].reshape(b.shape)
         xm, st1, cm, _ = s1.solve(dev(b), x=dev(x0)[None].contiguous(), tol=1e-300)
@@ -145,7 +148,7 @@ def test_variable_k_iterates():
     assert rel(host(x)[0], refj.x) <= 1e-10
 
 
-@pytest.mark.parametrize("cn", COARSE, ids=["grid", "default", "cta"])
+@pytest.mark.parametrize("cn", COARSE, ids=COARSE_IDS)
 def test_batch_each_rhs_matches_oracle(cn):
     nx = ny = 32
     h = 1.0 / 32
@@ -154,7 +157,7 @@ def test_batch_each_rhs_matches_oracle(cn):
     H = ohier.build_hierarchy(nx, ny, h, 20.0, 0.7)
     opt = ocycle.CycleOptions(1, "jacobi", 1, 1, 4.5)
     refs = [ocycle.mg_solve(H, srcs[q].ravel(), 1e-6, opt) for q in range(3)]
-    s = hm.Solver(nx, ny, h, 20.0, 0.7, batch=3, coarse_nodes=cn)
+    s = hm.Solver(nx, ny, h, 20.0, 0.7, batch=3, **cn)
     x, st, cyc, rr = s.solve(dev(srcs), tol=1e-6)
     assert st == hm.MG_OK
     for q in range(3):
@@ -173,8 +176,9 @@ def test_mixed_precision_against_fp64_oracle():
     opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
     H = ohier.build_hierarchy(nx, ny, h, k, 1 / k)
     ref = ocycle.mg_solve(H, b.ravel(), 1e-12, opt)
-    for sm, beta2, cn in (("gmres3", 1 / k, None), ("jacobi", 0.7, None), ("gmres3", 1 / k, 0), ("gmres3", 1 / k, 10**6)):
-        s = hm.Solver(nx, ny, h, k, beta2, smoother=sm, nu_pre=2, nu_post=2, precision="mixed", coarse_nodes=cn)
+    for sm, beta2, cn in (("gmres3", 1 / k, COARSE[1]), ("jacobi", 0.7, COARSE[1]), ("gmres3", 1 / k, COARSE[0]),
+                          ("gmres3", 1 / k, COARSE[2]), ("gmres3", 1 / k, COARSE[4])):
+        s = hm.Solver(nx, ny, h, k, beta2, smoother=sm, nu_pre=2, nu_post=2, precision="mixed", **cn)
         x, st, cyc, rr = s.solve(dev(b), tol=1e-6)
         assert st == hm.MG_OK and rr[0] <= 1e-6
         r = b.ravel() - H.A[0] @ host(x)[0].ravel()
