@@ -48,6 +48,11 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-fp64-line", action="store_true", help="skip the FP64 comparison solve")
     p.add_argument("--cpu-sample-cycles", type=int, default=2)
+    p.add_argument("--probe", action="store_true",
+                   help="profiling probe: set up the workload and run two solves capped at --max-cycles; no timing")
+    p.add_argument("--max-cycles", type=int, default=2)
+    p.add_argument("--coarse-nodes", type=int, default=-1)
+    p.add_argument("--coarse-mode", type=int, default=-1)
     a = p.parse_args()
     if a.warmup < 3:
         p.error("--warmup must be >= 3")
@@ -327,8 +332,34 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_probe(a):
+    """Two solves of the workload capped at a.max_cycles cycles (for ncu captures)."""
+    import torch
+    import paper_2308_13476_gb300 as hm
+    import synth
+    torch.cuda.set_device(0)
+    h = 1.0 / a.n
+    src = synth.source_row(a.n, a.n, h, a.batch) if a.batch > 1 else synth.point_source(a.n, a.n, h)[None]
+    rhs = torch.from_numpy(src).cuda()
+    kw = {}
+    if a.coarse_nodes >= 0:
+        kw["coarse_nodes"] = a.coarse_nodes
+    if a.coarse_mode >= 0:
+        kw["coarse_mode"] = a.coarse_mode
+    s = hm.Solver(a.n, a.n, h, a.k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
+                  precision=a.precision, batch=a.batch, max_cycles=a.max_cycles, **kw)
+    for _ in range(2):
+        s.solve(rhs, tol=a.tol)
+        torch.cuda.synchronize()
+    print(json.dumps({"probe": "ok", "kernel_launches": s.counters()[0]}))
+    s.close()
+
+
 def main():
     a = parse()
+    if a.probe:
+        run_probe(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:
