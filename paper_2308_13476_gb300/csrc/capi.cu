@@ -76,8 +76,10 @@ struct mg_ctx {
   std::vector<Level> lev;
   std::vector<LevelVec<double>> v64;
   std::vector<LevelVec<float>> v32;
-  Op0Consts<double>* c0d = nullptr;
+  Op0Consts<double>* c0d = nullptr;   // device copies (written by the setup kernel)
   Op0Consts<float>* c0f = nullptr;
+  Op0Consts<double> hc0d{};            // host copies, passed to the kernels by value
+  Op0Consts<float> hc0f{};
   double* kf64 = nullptr;
   float* kf32 = nullptr;
   double2* cinv = nullptr;
@@ -145,7 +147,7 @@ static OpView<double> op64(const mg_ctx* c, int l) {
   const Level& L = c->lev[l];
   v.kind = L.kind;
   if (l == 0) {
-    v.c0 = c->c0d;
+    v.c0 = c->hc0d;
     v.kf = c->kf64;
   } else {
     v.st = L.st;
@@ -164,7 +166,7 @@ static OpView<float> op32(const mg_ctx* c, int l) {
   const Level& L = c->lev[l];
   v.kind = L.kind;
   if (l == 0) {
-    v.c0 = c->c0f;
+    v.c0 = c->hc0f;
     v.kf = c->kf32;
   } else {
     v.st = c->v32[l].st;
@@ -485,6 +487,9 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     }
   }
   launch_op0consts(c->c0d, c->c0f, c->h, c->kconst, o.omega, c->beta2, s);
+  CK(cudaMemcpyAsync(&c->hc0d, c->c0d, sizeof(Op0Consts<double>), cudaMemcpyDeviceToHost, s));
+  if (mixed) CK(cudaMemcpyAsync(&c->hc0f, c->c0f, sizeof(Op0Consts<float>), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   // Galerkin operators A_{l+1} = R_l C_l P_l.  Constant k: Kronecker form,
   // A_l = W_y (x) G_x + H_y (x) W_x, each factor coarsened in 1D.  Variable
   // k: per-node stencils from the 2D product.

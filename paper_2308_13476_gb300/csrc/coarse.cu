@@ -23,7 +23,7 @@ namespace hmg {
 #define CTA_IJP(L)                 \
   const int i = q % n1_;           \
   const int j = q / n1_;           \
-  const long long p = (L).g.at(i, j);
+  const int p = (L).g.at(i, j);
 
 template <class T>
 __device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, double* S, double* sh) {
@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle(const CLevel<T>* _
         cx<T>* bc = C.b + (long long)rhs * C.g.vstride;
         CTA_NODES(C) {
           CTA_IJP(C)
-          const long long pc = L.g.at(2 * i, 2 * j);
+          const int pc = L.g.at(2 * i, 2 * j);
           cx<T> acc = mk<T>(0, 0);
           for (int bb = -2; bb <= 2; ++bb) {
-            const cx<T>* row = r + pc + (long long)bb * L.g.pitch;
+            const cx<T>* row = r + pc + bb * L.g.pitch;
             cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
             t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
             t = add<T>(t, scl<T>(T(0.75), row[0]));

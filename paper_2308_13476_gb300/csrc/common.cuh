@@ -59,12 +59,12 @@ struct Grid {
   long long vstride;   // elements per right-hand side
   int ry;              // grid rows per thread of the node kernels (1..RYMAX):
                        // a block covers BX x (BY * ry) nodes
-  __host__ __device__ __forceinline__ long long at(int i, int j) const {
-    return (long long)(j + HALO) * pitch + (i + HALO);
-  }
+  // offset of node (i, j) inside one right-hand side's slice (< 2^31)
+  __host__ __device__ __forceinline__ int at(int i, int j) const { return (j + HALO) * pitch + (i + HALO); }
 };
 
-// Fine-level (level 0) constants, written on the device by the setup kernel.
+// Fine-level (level 0) constants, computed on the device by the setup kernel
+// and passed to the kernels by value (copied back once at setup).
 // dinv[by*2+bx] = 1/(omega * A_PP) for constant k and the four boundary
 // classes (bx = node on a vertical boundary line, by = on a horizontal one).
 template <class T> struct Op0Consts {
@@ -79,7 +79,7 @@ template <class T> struct Op0Consts {
 //             - wx wy k_P^2 x_P - i (k_P / h)(bx wy + wx by) x_P
 // and halo nodes read as zero.
 template <class T> struct Op0 {
-  const Op0Consts<T>* c;
+  Op0Consts<T> c;
   const T* kf;     // per-node k, dense (ny+1)*(nx+1), or null for constant k
   int nx, ny;
 
@@ -90,9 +90,9 @@ template <class T> struct Op0 {
     wy = by ? T(0.5) : T(1);
   }
   __device__ __forceinline__ T kval(int i, int j) const {
-    return kf ? kf[(long long)j * (nx + 1) + i] : c->k;
+    return kf ? kf[j * (nx + 1) + i] : c.k;
   }
-  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, long long p, int pitch, int i, int j) const {
+  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, int p, int pitch, int i, int j) const {
     T wx, wy; int bx, by;
     geom(i, j, wx, wy, bx, by);
     const cx<T> xp = x[p];
@@ -101,21 +101,21 @@ template <class T> struct Op0 {
     const T w = wx * wy;
     cx<T> s = add<T>(scl<T>(wy, add<T>(xe, xw)), scl<T>(wx, add<T>(xn, xs)));
     cx<T> lap = sub<T>(scl<T>(T(4) * w, xp), s);
-    T re = lap.x * c->inv_h2 - (w * (k * k)) * xp.x;
-    T im = lap.y * c->inv_h2 - (w * (k * k)) * xp.y;
-    const T sb = (k * c->inv_h) * (T(bx) * wy + wx * T(by));
+    T re = lap.x * c.inv_h2 - (w * (k * k)) * xp.x;
+    T im = lap.y * c.inv_h2 - (w * (k * k)) * xp.y;
+    const T sb = (k * c.inv_h) * (T(bx) * wy + wx * T(by));
     // - i sb x_P = (sb x.im, -sb x.re)
     return mk<T>(re + sb * xp.y, im - sb * xp.x);
   }
   __device__ __forceinline__ cx<T> diag_inv(int i, int j) const {
     T wx, wy; int bx, by;
     geom(i, j, wx, wy, bx, by);
-    if (!kf) return c->dinv[by * 2 + bx];
+    if (!kf) return c.dinv[by * 2 + bx];
     const T k = kval(i, j);
     const T w = wx * wy;
-    const T dr = (T(4) * w) * c->inv_h2 - w * (k * k);
-    const T di = -(k * c->inv_h) * (T(bx) * wy + wx * T(by));
-    return cinv<T>(mk<T>(c->omega * dr, c->omega * di));
+    const T dr = (T(4) * w) * c.inv_h2 - w * (k * k);
+    const T di = -(k * c.inv_h) * (T(bx) * wy + wx * T(by));
+    return cinv<T>(mk<T>(c.omega * dr, c.omega * di));
   }
 };
 
@@ -127,7 +127,7 @@ template <class T, int R> struct OpS {
   const cx<T>* dinvp;
   long long plane;
   int nx, ny;
-  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, long long p, int pitch, int i, int j) const {
+  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, int p, int pitch, int i, int j) const {
     const long long q = (long long)j * (nx + 1) + i;
     cx<T> acc = mk<T>(0, 0);
 #pragma unroll
@@ -135,7 +135,7 @@ template <class T, int R> struct OpS {
 #pragma unroll
       for (int dx = -R; dx <= R; ++dx) {
         const int e = (dy + R) * (2 * R + 1) + (dx + R);
-        acc = fma_c<T>(st[e * plane + q], x[p + (long long)dy * pitch + dx], acc);
+        acc = fma_c<T>(st[e * plane + q], x[p + dy * pitch + dx], acc);
       }
     }
     return acc;
@@ -159,7 +159,7 @@ template <class T, int R> struct OpK {
   const T* wy;
   const cx<T>* dinvp;
   int nx, ny;
-  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, long long p, int pitch, int i, int j) const {
+  __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, int p, int pitch, int i, int j) const {
     const cx<T>* G = gx + i * (2 * R + 1);
     const T* Wx = wx + i * (2 * R + 1);
     const cx<T>* H = hy + j * (2 * R + 1);
@@ -167,7 +167,7 @@ template <class T, int R> struct OpK {
     cx<T> acc = mk<T>(0, 0);
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy) {
-      const cx<T>* row = x + p + (long long)dy * pitch;
+      const cx<T>* row = x + p + dy * pitch;
       cx<T> s1 = mk<T>(0, 0), s2 = mk<T>(0, 0);
 #pragma unroll
       for (int dx = -R; dx <= R; ++dx) {
@@ -211,18 +211,46 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32
   __syncthreads();
 }
 
+// Block-wide sum of NV values of the working precision T: the warp stage runs
+// in T (shuffles), each warp's sum is widened to double once, and thread 0
+// adds the warps in double.  Fixed shape and order (reproducible).
+template <int NV, class T>
+__device__ __forceinline__ void block_sum_t(const T (&v)[NV], double* sh /* [NV][32] */, double (&out)[NV]) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T t = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[k * 32 + warp] = (double)t;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = 0;
+      for (int w = 0; w < nwarps; ++w) t += sh[k * 32 + w];
+      out[k] = t;
+    }
+  }
+  __syncthreads();
+}
+
 // Grid-wide deterministic sum of NV doubles for one right-hand side, inside
 // the producing kernel: every block publishes its block sum, takes a ticket,
 // and the block holding the last ticket sums all partials in block order
 // (fixed, so results are bitwise reproducible) and resets the ticket.
-// Returns true, block-uniformly, in that last block; the totals are then
-// valid in thread 0's v.  partial: [rhs][nblk][NVMAX]; tickets: [rhs], 0 at
-// rest.  Must be reached by every thread of every block of the RHS.
-template <int NV>
-__device__ __forceinline__ bool reduce_last(double (&v)[NV], double* sh, double* partial, unsigned* tickets, int rhs,
-                                            int nblk, int blk) {
+// vin: this thread's sums in the working precision.  Returns true,
+// block-uniformly, in that last block; the totals are then valid in thread
+// 0's v.  partial: [rhs][nblk][NVMAX]; tickets: [rhs], 0 at rest.  Must be
+// reached by every thread of every block of the RHS.
+template <int NV, class T>
+__device__ __forceinline__ bool reduce_last(const T (&vin)[NV], double (&v)[NV], double* sh, double* partial,
+                                            unsigned* tickets, int rhs, int nblk, int blk) {
   __shared__ int s_last;
-  block_sum<NV>(v, sh);
+  block_sum_t<NV, T>(vin, sh, v);
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nt = blockDim.x * blockDim.y;
   if (tid == 0) {

@@ -87,7 +87,7 @@ __device__ __forceinline__ bool coop_reduce(double (&v)[NV], double* sh, double*
 #define COOP_IJP(L)     \
   const int i = q % n1_;\
   const int j = q / n1_;\
-  const long long p = (L).g.at(i, j);
+  const int p = (L).g.at(i, j);
 
 template <class T>
 __device__ bool coop_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, double* S, double* sh, double* tot,
@@ -251,10 +251,10 @@ __global__ void __launch_bounds__(COOP_THREADS) k_cycle_coop(const CLevel<T>* __
           cx<T>* bc = C.b + (long long)rhs * C.g.vstride;
           COOP_NODES(C) {
             COOP_IJP(C)
-            const long long pc = L.g.at(2 * i, 2 * j);
+            const int pc = L.g.at(2 * i, 2 * j);
             cx<T> acc = mk<T>(0, 0);
             for (int bb = -2; bb <= 2; ++bb) {
-              const cx<T>* row = r + pc + (long long)bb * L.g.pitch;
+              const cx<T>* row = r + pc + bb * L.g.pitch;
               cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
               t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
               t = add<T>(t, scl<T>(T(0.75), row[0]));

@@ -13,7 +13,7 @@ namespace hmg {
 // Kronecker form of radius 2 / 3 (gx, wx, hy, wy, dinv).
 template <class T> struct OpView {
   int kind;
-  const Op0Consts<T>* c0;
+  Op0Consts<T> c0;
   const T* kf;
   const cx<T>* st;
   const cx<T>* dinv;
@@ -129,7 +129,7 @@ enum { C_JACOBI = 0, C_GMRES = 1, C_RESTRICT = 2, C_ZERO = 3, C_COARSE = 4, C_PR
 template <class T> struct CLevel {
   Grid g;
   int kind;                 // as OpView::kind
-  const Op0Consts<T>* c0;
+  Op0Consts<T> c0;
   const T* kf;
   const cx<T>* st;
   const cx<T>* dinv;

@@ -50,18 +50,18 @@ __global__ void __launch_bounds__(BX * BY) g_init(Grid g, Op op, const cx<T>* __
   __shared__ double sh[NVMAX * 32];
   GNODE
   if (active && !active[rhs]) return;
-  T a0 = T(0);   // per-thread sums in the working precision, widened once
+  T a0[1] = {T(0)};   // per-thread sums in the working precision
   if (i <= g.nx) {
     GROWS {
       if (j > g.ny) break;
-      const long long p = g.at(i, j);
+      const int p = g.at(i, j);
       const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
       u0[off + p] = r;
-      a0 += abs2<T>(r);
+      a0[0] += abs2<T>(r);
     }
   }
-  double v[1] = {(double)a0};
-  if (reduce_last<1>(v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(st + (long long)rhs * GS, v);
+  double v[1];
+  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(st + (long long)rhs * GS, v);
 }
 
 // w = A v_J (v_J = s_J u_J); partial dots <u_i, w> for i <= J
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
     const cx<T>* us[3] = {u0, u1, u2};
     GROWS {
       if (j > g.ny) break;
-      const long long p = g.at(i, j);
+      const int p = g.at(i, j);
       const cx<T> a = scl<T>(sJ, op.apply(uJ + off, p, g.pitch, i, j));
       w[off + p] = a;
 #pragma unroll
@@ -96,9 +96,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
     }
   }
   double v[2 * (J + 1)];
-#pragma unroll
-  for (int k = 0; k < 2 * (J + 1); ++k) v[k] = (double)acc[k];
-  if (reduce_last<2 * (J + 1)>(v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
+  if (reduce_last<2 * (J + 1), T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
 }
 
 // u_{J+1} = w - sum_{i<=J} h_iJ s_i u_i ; partials |u_{J+1}|^2 and <u_{J+1}, u_l>, l <= J (J < 2)
@@ -127,7 +125,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restri
     }
     GROWS {
       if (j > g.ny) break;
-      const long long p = g.at(i, j);
+      const int p = g.at(i, j);
       cx<T> a = w[off + p];
       cx<T> uu[J + 1];
 #pragma unroll
@@ -148,9 +146,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restri
     }
   }
   double v[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = (double)acc[k];
-  if (reduce_last<NV>(v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_b<J, T>(s, q); });
+  if (reduce_last<NV, T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_b<J, T>(s, q); });
 }
 
 // x += sum_{i<m} y_i s_i u_i

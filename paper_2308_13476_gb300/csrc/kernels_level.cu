@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual(Grid g, Op op, const cx<T>
   if (i > g.nx) return;
   FOR_ROWS {
     if (j > g.ny) break;
-    const long long p = g.at(i, j);
+    const int p = g.at(i, j);
     r[off + p] = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
   }
 }
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(BX * BY) k_apply(Grid g, Op op, const cx<T>* _
   if (i > g.nx) return;
   FOR_ROWS {
     if (j > g.ny) break;
-    const long long p = g.at(i, j);
+    const int p = g.at(i, j);
     y[off + p] = op.apply(x + off, p, g.pitch, i, j);
   }
 }
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(Grid g, Op op, const cx<T>* 
   if (i > g.nx) return;
   FOR_ROWS {
     if (j > g.ny) break;
-    const long long p = g.at(i, j);
+    const int p = g.at(i, j);
     const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
     xo[off + p] = fma_c<T>(op.diag_inv(i, j), r, x[off + p]);
   }
@@ -100,17 +100,17 @@ __global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const c
   __shared__ double sh[32];
   NODE_INDEX
   if (!c.active[rhs]) return;   // block-uniform
-  T a0 = T(0);   // per-thread sum in the working precision, widened once
+  T a0[1] = {T(0)};   // per-thread sum in the working precision
   if (i <= g.nx) {
     FOR_ROWS {
       if (j > g.ny) break;
-      const long long p = g.at(i, j);
+      const int p = g.at(i, j);
       const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
-      a0 += abs2<T>(r);
+      a0[0] += abs2<T>(r);
     }
   }
-  double v[1] = {(double)a0};
-  if (reduce_last<1>(v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+  double v[1];
+  if (reduce_last<1, T>(a0, v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
       threadIdx.x == 0 && threadIdx.y == 0)
     stop_update(c, rhs, v[0], count);
 }
@@ -123,17 +123,18 @@ __global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double>
   __shared__ double sh[32];
   NODE_INDEX
   if (!c.active[rhs]) return;
-  double v[1] = {0.0};
+  double a0[1] = {0.0};
   if (i <= g.nx) {
     FOR_ROWS {
       if (j > g.ny) break;
-      const long long p = g.at(i, j);
+      const int p = g.at(i, j);
       const double2 r = sub<double>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
       r32[off + p] = make_float2((float)r.x, (float)r.y);
-      v[0] += abs2<double>(r);
+      a0[0] += abs2<double>(r);
     }
   }
-  if (reduce_last<1>(v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+  double v[1];
+  if (reduce_last<1, double>(a0, v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
       threadIdx.x == 0 && threadIdx.y == 0)
     stop_update(c, rhs, v[0], count);
 }
@@ -160,15 +161,15 @@ __global__ void __launch_bounds__(BX * BY) k_vecnorm_fin(Grid g, const cx<T>* __
                                                          double* partial, unsigned* tickets) {
   __shared__ double sh[32];
   NODE_INDEX
-  T a0 = T(0);
+  T a0[1] = {T(0)};
   if (i <= g.nx) {
     FOR_ROWS {
       if (j > g.ny) break;
-      a0 += abs2<T>(v_[off + g.at(i, j)]);
+      a0[0] += abs2<T>(v_[off + g.at(i, j)]);
     }
   }
-  double v[1] = {(double)a0};
-  if (reduce_last<1>(v, sh, partial, tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+  double v[1];
+  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
       threadIdx.x == 0 && threadIdx.y == 0)
     out[rhs] = sqrt(v[0]);
 }
@@ -190,11 +191,11 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<
   const cx<T>* f = rf + (long long)rhs * gf.vstride;
   FOR_ROWS {
     if (j > g.ny) break;
-    const long long pc = gf.at(2 * i, 2 * j);
+    const int pc = gf.at(2 * i, 2 * j);
     cx<T> acc = mk<T>(0, 0);
 #pragma unroll
     for (int b = -2; b <= 2; ++b) {
-      const cx<T>* row = f + pc + (long long)b * gf.pitch;
+      const cx<T>* row = f + pc + b * gf.pitch;
       cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
       t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
       t = add<T>(t, scl<T>(T(0.75), row[0]));
@@ -323,7 +324,7 @@ void launch_resnorm_stop(const Grid& g, const OpView<T>& v, const cx<T>* x, cons
 }
 void launch_resid_cast_stop(const Grid& g, const OpView<double>& v, const double2* x, const double2* b, float2* r32,
                             int B, const Ctl& c, int count, cudaStream_t s) {
-  Op0<double> op{v.c0, v.kf, g.nx, g.ny};
+  Op0<double> op{v.c0, v.kf, g.nx, g.ny};  // constants by value
   k_resid_cast_stop<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, r32, c, count);
 }
 void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s) {

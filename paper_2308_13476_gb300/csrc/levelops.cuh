@@ -7,7 +7,7 @@
 namespace hmg {
 
 template <class T>
-__device__ __forceinline__ cx<T> lv_apply(const CLevel<T>& L, const cx<T>* x, long long p, int i, int j) {
+__device__ __forceinline__ cx<T> lv_apply(const CLevel<T>& L, const cx<T>* x, int p, int i, int j) {
   switch (L.kind) {
     case 1: return Op0<T>{L.c0, L.kf, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);
     case 2: return OpS<T, 2>{L.st, L.dinv, L.plane, L.g.nx, L.g.ny}.apply(x, p, L.g.pitch, i, j);

@@ -30,7 +30,7 @@ __device__ double2 op_coef(const OpView<double>& v, int nx, int ny, int i, int j
     const double Wx = v.wx[i * w + dx + r], Wy = v.wy[j * w + dy + r];
     return make_double2(Wy * G.x + H.x * Wx, Wy * G.y + H.y * Wx);
   }
-  const Op0Consts<double>* c = v.c0;
+  const Op0Consts<double>* c = &v.c0;
   const int bx = (i == 0 || i == nx), by = (j == 0 || j == ny);
   const double wx = bx ? 0.5 : 1.0, wy = by ? 0.5 : 1.0, w = wx * wy;
   const double k = v.kf ? v.kf[(long long)j * (nx + 1) + i] : c->k;
