@@ -93,19 +93,25 @@ template <class T> struct Op0 {
     return kf ? kf[j * (nx + 1) + i] : c.k;
   }
   __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, int p, int pitch, int i, int j) const {
-    T wx, wy; int bx, by;
-    geom(i, j, wx, wy, bx, by);
-    const cx<T> xp = x[p];
-    const cx<T> xe = x[p + 1], xw = x[p - 1], xn = x[p + pitch], xs = x[p - pitch];
+    return apply5(x[p], x[p + 1], x[p - 1], x[p + pitch], x[p - pitch], i, j);
+  }
+  // the stencil given the node's value and its E, W, N, S neighbours:
+  // A x = d x_P - (wy (x_E + x_W) + wx (x_N + x_S)) / h^2 - i sb x_P with the
+  // diagonal coefficient d = w (4 / h^2 - k^2); interior nodes (w = 1, no
+  // boundary term) take the short path
+  __device__ __forceinline__ cx<T> apply5(cx<T> xp, cx<T> xe, cx<T> xw, cx<T> xn, cx<T> xs, int i, int j) const {
     const T k = kval(i, j);
-    const T w = wx * wy;
-    cx<T> s = add<T>(scl<T>(wy, add<T>(xe, xw)), scl<T>(wx, add<T>(xn, xs)));
-    cx<T> lap = sub<T>(scl<T>(T(4) * w, xp), s);
-    T re = lap.x * c.inv_h2 - (w * (k * k)) * xp.x;
-    T im = lap.y * c.inv_h2 - (w * (k * k)) * xp.y;
+    const bool bx = (i == 0 || i == nx), by = (j == 0 || j == ny);
+    if (!(bx || by)) {
+      const T sr = (xe.x + xw.x) + (xn.x + xs.x), si = (xe.y + xw.y) + (xn.y + xs.y);
+      const T d = fma(-k, k, T(4) * c.inv_h2);
+      return mk<T>(fma(d, xp.x, -c.inv_h2 * sr), fma(d, xp.y, -c.inv_h2 * si));
+    }
+    const T wx = bx ? T(0.5) : T(1), wy = by ? T(0.5) : T(1), w = wx * wy;
+    const T sr = wy * (xe.x + xw.x) + wx * (xn.x + xs.x), si = wy * (xe.y + xw.y) + wx * (xn.y + xs.y);
+    const T d = w * fma(-k, k, T(4) * c.inv_h2);
     const T sb = (k * c.inv_h) * (T(bx) * wy + wx * T(by));
-    // - i sb x_P = (sb x.im, -sb x.re)
-    return mk<T>(re + sb * xp.y, im - sb * xp.x);
+    return mk<T>(fma(d, xp.x, fma(sb, xp.y, -c.inv_h2 * sr)), fma(d, xp.y, fma(-sb, xp.x, -c.inv_h2 * si)));
   }
   __device__ __forceinline__ cx<T> diag_inv(int i, int j) const {
     T wx, wy; int bx, by;

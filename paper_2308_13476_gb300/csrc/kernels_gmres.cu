@@ -16,12 +16,16 @@
 
 #include "gmres.cuh"
 #include "internal.h"
+#include "pack.cuh"
 
 namespace hmg {
 
+// The thread's pack starts at column i0 and holds nv nodes inside the grid.
 #define GNODE                                            \
+  constexpr int NP = PK<T>::NP;                          \
   const int rhs = blockIdx.z;                            \
-  const int i = blockIdx.x * BX + threadIdx.x;           \
+  const int i0 = (blockIdx.x * BX + threadIdx.x) * NP;   \
+  const int nv = min(NP, g.nx + 1 - i0);                 \
   const long long off = (long long)rhs * g.vstride;      \
   const int nblk = gridDim.x * gridDim.y;                \
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;   \
@@ -51,13 +55,18 @@ __global__ void __launch_bounds__(BX * BY) g_init(Grid g, Op op, const cx<T>* __
   GNODE
   if (active && !active[rhs]) return;
   T a0[1] = {T(0)};   // per-thread sums in the working precision
-  if (i <= g.nx) {
+  if (nv > 0) {
     GROWS {
       if (j > g.ny) break;
-      const int p = g.at(i, j);
-      const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
-      u0[off + p] = r;
-      a0[0] += abs2<T>(r);
+      const int p = g.at(i0, j);
+      const Pack<T> ax = apply_pack<T>(op, x + off, p, g.pitch, i0, j);
+      Pack<T> r = load_pack(b + off, p);
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        r.v[n] = sub<T>(r.v[n], ax.v[n]);
+        if (n < nv) a0[0] += abs2<T>(r.v[n]);
+      }
+      store_pack(u0 + off, p, r, nv);
     }
   }
   double v[1];
@@ -79,19 +88,27 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
   T acc[2 * (J + 1)];
 #pragma unroll
   for (int k = 0; k < 2 * (J + 1); ++k) acc[k] = T(0);
-  if (i <= g.nx) {
+  if (nv > 0) {
     const T sJ = (T)S[G_S + J];
     const cx<T>* us[3] = {u0, u1, u2};
     GROWS {
       if (j > g.ny) break;
-      const int p = g.at(i, j);
-      const cx<T> a = scl<T>(sJ, op.apply(uJ + off, p, g.pitch, i, j));
-      w[off + p] = a;
+      const int p = g.at(i0, j);
+      Pack<T> a = apply_pack<T>(op, uJ + off, p, g.pitch, i0, j);
+#pragma unroll
+      for (int n = 0; n < NP; ++n) a.v[n] = scl<T>(sJ, a.v[n]);
+      store_pack(w + off, p, a, nv);
 #pragma unroll
       for (int l = 0; l <= J; ++l) {
-        const cx<T> d = cmul<T>(us[l][off + p], a);
-        acc[2 * l] += d.x;
-        acc[2 * l + 1] += d.y;
+        const Pack<T> ul = load_pack(us[l] + off, p);
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          if (n < nv) {
+            const cx<T> d = cmul<T>(ul.v[n], a.v[n]);
+            acc[2 * l] += d.x;
+            acc[2 * l + 1] += d.y;
+          }
+        }
       }
     }
   }
@@ -114,7 +131,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restri
   T acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = T(0);
-  if (i <= g.nx) {
+  if (nv > 0) {
     const cx<T>* us[3] = {u0, u1, u2};
     cx<T> c[J + 1];
 #pragma unroll
@@ -125,22 +142,27 @@ __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restri
     }
     GROWS {
       if (j > g.ny) break;
-      const int p = g.at(i, j);
-      cx<T> a = w[off + p];
-      cx<T> uu[J + 1];
+      const int p = g.at(i0, j);
+      Pack<T> a = load_pack(w + off, p);
+      Pack<T> uu[J + 1];
 #pragma unroll
       for (int l = 0; l <= J; ++l) {
-        uu[l] = us[l][off + p];
-        a = sub<T>(a, mul<T>(c[l], uu[l]));
-      }
-      if (un) un[off + p] = a;
-      acc[0] += abs2<T>(a);
-      if (J < 2) {
+        uu[l] = load_pack(us[l] + off, p);
 #pragma unroll
-        for (int l = 0; l <= J && 1 + 2 * l + 1 < NV; ++l) {
-          const cx<T> d = cmul<T>(a, uu[l]);
-          acc[1 + 2 * l] += d.x;
-          acc[2 + 2 * l] += d.y;
+        for (int n = 0; n < NP; ++n) a.v[n] = sub<T>(a.v[n], mul<T>(c[l], uu[l].v[n]));
+      }
+      if (un) store_pack(un + off, p, a, nv);
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        if (n >= nv) continue;
+        acc[0] += abs2<T>(a.v[n]);
+        if (J < 2) {
+#pragma unroll
+          for (int l = 0; l <= J && 1 + 2 * l + 1 < NV; ++l) {
+            const cx<T> d = cmul<T>(a.v[n], uu[l].v[n]);
+            acc[1 + 2 * l] += d.x;
+            acc[2 + 2 * l] += d.y;
+          }
         }
       }
     }
@@ -154,11 +176,13 @@ template <class T>
 __global__ void __launch_bounds__(BX * BY) g_update(Grid g, cx<T>* __restrict__ x, const cx<T>* __restrict__ u0,
                                                     const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
                                                     const double* __restrict__ st, const int* __restrict__ active) {
+  constexpr int NP = PK<T>::NP;
   const int rhs = blockIdx.z;
-  const int i = blockIdx.x * BX + threadIdx.x;
+  const int i0 = (blockIdx.x * BX + threadIdx.x) * NP;
+  const int nv = min(NP, g.nx + 1 - i0);
   const long long off = (long long)rhs * g.vstride;
   if (active && !active[rhs]) return;
-  if (i > g.nx) return;
+  if (nv <= 0) return;
   const double* S = st + (long long)rhs * GS;
   const int m = (int)S[G_M];
   if (m <= 0) return;
@@ -171,19 +195,24 @@ __global__ void __launch_bounds__(BX * BY) g_update(Grid g, cx<T>* __restrict__ 
   }
   GROWS {
     if (j > g.ny) break;
-    const long long p = off + g.at(i, j);
-    cx<T> a = x[p];
+    const int p = g.at(i0, j);
+    Pack<T> a = load_pack(x + off, p);
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
-      if (l < m) a = fma_c<T>(c[l], us[l][p], a);
-    x[p] = a;
+    for (int l = 0; l < 3; ++l) {
+      if (l < m) {
+        const Pack<T> ul = load_pack(us[l] + off, p);
+#pragma unroll
+        for (int n = 0; n < NP; ++n) a.v[n] = fma_c<T>(c[l], ul.v[n], a.v[n]);
+      }
+    }
+    store_pack(x + off, p, a, nv);
   }
 }
 
 template <class T>
 void gmres_smooth(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T>* b, int nu, int B, const int* active,
                   const GmresBufs& gb, cudaStream_t s) {
-  dim3 grd(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY * g.ry), B);
+  dim3 grd(cdiv(g.nx + 1, BX * PK<T>::NP), cdiv(g.ny + 1, BY * g.ry), B);
   cx<T>* u0 = (cx<T>*)gb.u[0];
   cx<T>* u1 = (cx<T>*)gb.u[1];
   cx<T>* u2 = (cx<T>*)gb.u[2];

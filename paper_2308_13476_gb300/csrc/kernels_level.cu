@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "pack.cuh"
 
 namespace hmg {
 
@@ -17,6 +18,9 @@ namespace hmg {
 
 static inline dim3 node_grid(const Grid& g, int B) {
   return dim3(cdiv(g.nx + 1, BX), cdiv(g.ny + 1, BY * g.ry), B);
+}
+static inline dim3 pack_grid(const Grid& g, int B, int np) {
+  return dim3(cdiv(g.nx + 1, BX * np), cdiv(g.ny + 1, BY * g.ry), B);
 }
 
 // Thread (tx, ty) of block (bx, by, rhs) handles node column i and the g.ry
@@ -26,6 +30,14 @@ static inline dim3 node_grid(const Grid& g, int B) {
   const int i = blockIdx.x * BX + threadIdx.x;           \
   const long long off = (long long)rhs * g.vstride;
 #define FOR_ROWS for (int r_ = 0, j = blockIdx.y * BY * g.ry + threadIdx.y; r_ < g.ry; ++r_, j += BY)
+// Pack kernels: the thread's pack starts at column i0 and holds nv nodes
+// inside the grid.
+#define PACK_INDEX(T)                                          \
+  constexpr int NP = PK<T>::NP;                                \
+  const int rhs = blockIdx.z;                                  \
+  const int i0 = (blockIdx.x * BX + threadIdx.x) * NP;         \
+  const int nv = min(NP, g.nx + 1 - i0);                       \
+  const long long off = (long long)rhs * g.vstride;
 
 // ------------------------------------------------------------------ operator kernels
 
@@ -33,26 +45,30 @@ template <class T, class Op>
 __global__ void __launch_bounds__(BX * BY) k_residual(Grid g, Op op, const cx<T>* __restrict__ x,
                                                       const cx<T>* __restrict__ b, cx<T>* __restrict__ r,
                                                       const int* __restrict__ active) {
-  NODE_INDEX
+  PACK_INDEX(T)
   if (active && !active[rhs]) return;
-  if (i > g.nx) return;
+  if (nv <= 0) return;
   FOR_ROWS {
     if (j > g.ny) break;
-    const int p = g.at(i, j);
-    r[off + p] = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+    const int p = g.at(i0, j);
+    const Pack<T> ax = apply_pack<T>(op, x + off, p, g.pitch, i0, j);
+    Pack<T> bb = load_pack(b + off, p);
+#pragma unroll
+    for (int n = 0; n < NP; ++n) bb.v[n] = sub<T>(bb.v[n], ax.v[n]);
+    store_pack(r + off, p, bb, nv);
   }
 }
 
 template <class T, class Op>
 __global__ void __launch_bounds__(BX * BY) k_apply(Grid g, Op op, const cx<T>* __restrict__ x,
                                                    cx<T>* __restrict__ y, const int* __restrict__ active) {
-  NODE_INDEX
+  PACK_INDEX(T)
   if (active && !active[rhs]) return;
-  if (i > g.nx) return;
+  if (nv <= 0) return;
   FOR_ROWS {
     if (j > g.ny) break;
-    const int p = g.at(i, j);
-    y[off + p] = op.apply(x + off, p, g.pitch, i, j);
+    const int p = g.at(i0, j);
+    store_pack(y + off, p, apply_pack<T>(op, x + off, p, g.pitch, i0, j), nv);
   }
 }
 
@@ -61,14 +77,19 @@ template <class T, class Op>
 __global__ void __launch_bounds__(BX * BY) k_jacobi(Grid g, Op op, const cx<T>* __restrict__ x,
                                                     const cx<T>* __restrict__ b, cx<T>* __restrict__ xo,
                                                     const int* __restrict__ active) {
-  NODE_INDEX
+  PACK_INDEX(T)
   if (active && !active[rhs]) return;
-  if (i > g.nx) return;
+  if (nv <= 0) return;
   FOR_ROWS {
     if (j > g.ny) break;
-    const int p = g.at(i, j);
-    const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
-    xo[off + p] = fma_c<T>(op.diag_inv(i, j), r, x[off + p]);
+    const int p = g.at(i0, j);
+    const Pack<T> ax = apply_pack<T>(op, x + off, p, g.pitch, i0, j);
+    const Pack<T> bb = load_pack(b + off, p);
+    Pack<T> xv = load_pack(x + off, p);
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+      xv.v[n] = fma_c<T>(op.diag_inv(min(i0 + n, g.nx), j), sub<T>(bb.v[n], ax.v[n]), xv.v[n]);
+    store_pack(xo + off, p, xv, nv);
   }
 }
 
@@ -98,15 +119,18 @@ template <class T, class Op>
 __global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const cx<T>* __restrict__ x,
                                                           const cx<T>* __restrict__ b, Ctl c, int count) {
   __shared__ double sh[32];
-  NODE_INDEX
+  PACK_INDEX(T)
   if (!c.active[rhs]) return;   // block-uniform
   T a0[1] = {T(0)};   // per-thread sum in the working precision
-  if (i <= g.nx) {
+  if (nv > 0) {
     FOR_ROWS {
       if (j > g.ny) break;
-      const int p = g.at(i, j);
-      const cx<T> r = sub<T>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
-      a0[0] += abs2<T>(r);
+      const int p = g.at(i0, j);
+      const Pack<T> ax = apply_pack<T>(op, x + off, p, g.pitch, i0, j);
+      const Pack<T> bb = load_pack(b + off, p);
+#pragma unroll
+      for (int n = 0; n < NP; ++n)
+        if (n < nv) a0[0] += abs2<T>(sub<T>(bb.v[n], ax.v[n]));
     }
   }
   double v[1];
@@ -209,40 +233,45 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const cx<T>* __restrict__ ec,
                                                          cx<T>* __restrict__ xf, const int* __restrict__ active) {
-  NODE_INDEX
+  PACK_INDEX(T)
   if (active && !active[rhs]) return;
-  if (i > g.nx) return;
+  if (nv <= 0) return;
   const cx<T>* c = ec + (long long)rhs * gc.vstride;
-  const int I = i >> 1;
-  auto rowval = [&](int JJ) -> cx<T> {
-    const cx<T>* row = c + gc.at(I, JJ);
-    if (i & 1) return scl<T>(T(0.5), add<T>(row[0], row[1]));
-    return add<T>(scl<T>(T(0.125), add<T>(row[-1], row[1])), scl<T>(T(0.75), row[0]));
-  };
   FOR_ROWS {
     if (j > g.ny) break;
     const int J = j >> 1;
-    cx<T> v;
-    if (j & 1) {
-      v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
-    } else {
-      v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+    const int p = g.at(i0, j);
+    Pack<T> xv = load_pack(xf + off, p);
+#pragma unroll
+    for (int n = 0; n < NP; ++n) {
+      const int i = i0 + n, I = i >> 1;
+      auto rowval = [&](int JJ) -> cx<T> {
+        const cx<T>* row = c + gc.at(I, JJ);
+        if (i & 1) return scl<T>(T(0.5), add<T>(row[0], row[1]));
+        return add<T>(scl<T>(T(0.125), add<T>(row[-1], row[1])), scl<T>(T(0.75), row[0]));
+      };
+      cx<T> v;
+      if (j & 1) {
+        v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
+      } else {
+        v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+      }
+      xv.v[n] = add<T>(xv.v[n], v);
     }
-    const long long p = off + g.at(i, j);
-    xf[p] = add<T>(xf[p], v);
+    store_pack(xf + off, p, xv, nv);
   }
 }
 
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_copy_masked(Grid g, const cx<T>* __restrict__ src, cx<T>* __restrict__ dst,
                                                          const int* __restrict__ active) {
-  NODE_INDEX
+  PACK_INDEX(T)
   if (active && !active[rhs]) return;
-  if (i > g.nx) return;
+  if (nv <= 0) return;
   FOR_ROWS {
     if (j > g.ny) break;
-    const long long p = off + g.at(i, j);
-    dst[p] = src[p];
+    const int p = g.at(i0, j);
+    store_pack(dst + off, p, load_pack(src + off, p), nv);
   }
 }
 
@@ -300,26 +329,28 @@ template <class T>
 void launch_residual(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, cx<T>* r, int B,
                      const int* active, cudaStream_t s) {
   with_op<T>(v, g.nx, g.ny, [&](auto op) {
-    k_residual<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, r, active);
+    k_residual<T, decltype(op)><<<pack_grid(g, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(g, op, x, b, r, active);
   });
 }
 template <class T>
 void launch_apply(const Grid& g, const OpView<T>& v, const cx<T>* x, cx<T>* y, int B, const int* active,
                   cudaStream_t s) {
-  with_op<T>(v, g.nx, g.ny, [&](auto op) { k_apply<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, y, active); });
+  with_op<T>(v, g.nx, g.ny, [&](auto op) {
+    k_apply<T, decltype(op)><<<pack_grid(g, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(g, op, x, y, active);
+  });
 }
 template <class T>
 void launch_jacobi(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, cx<T>* xo, int B,
                    const int* active, cudaStream_t s) {
   with_op<T>(v, g.nx, g.ny, [&](auto op) {
-    k_jacobi<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, xo, active);
+    k_jacobi<T, decltype(op)><<<pack_grid(g, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(g, op, x, b, xo, active);
   });
 }
 template <class T>
 void launch_resnorm_stop(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, int B, const Ctl& c,
                          int count, cudaStream_t s) {
   with_op<T>(v, g.nx, g.ny, [&](auto op) {
-    k_resnorm_stop<T, decltype(op)><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, c, count);
+    k_resnorm_stop<T, decltype(op)><<<pack_grid(g, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(g, op, x, b, c, count);
   });
 }
 void launch_resid_cast_stop(const Grid& g, const OpView<double>& v, const double2* x, const double2* b, float2* r32,
@@ -343,11 +374,11 @@ void launch_restrict(const Grid& gf, const Grid& gc, const cx<T>* rf, cx<T>* rc,
 template <class T>
 void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<T>* ec, cx<T>* xf, int B, const int* active,
                         cudaStream_t s) {
-  k_prolong_add<T><<<node_grid(gf, B), dim3(BX, BY), 0, s>>>(gf, gc, ec, xf, active);
+  k_prolong_add<T><<<pack_grid(gf, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(gf, gc, ec, xf, active);
 }
 template <class T>
 void launch_copy_masked(const Grid& g, const cx<T>* src, cx<T>* dst, int B, const int* active, cudaStream_t s) {
-  k_copy_masked<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, src, dst, active);
+  k_copy_masked<T><<<pack_grid(g, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(g, src, dst, active);
 }
 template <class T> void launch_pack(const Grid& g, const double2* user, cx<T>* v, int B, int conj, cudaStream_t s) {
   k_pack<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, user, v, conj);
