@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--max-cycles", type=int, default=2)
     p.add_argument("--coarse-nodes", type=int, default=-1)
     p.add_argument("--coarse-mode", type=int, default=-1)
+    p.add_argument("--no-autotune", action="store_true", help="library default launch shapes instead of the autotuner's")
     a = p.parse_args()
     if a.warmup < 3:
         p.error("--warmup must be >= 3")
@@ -243,10 +244,17 @@ def run_ours(a):
     rhs = torch.from_numpy(rhs_np).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def make(precision):
+    tuned = {}
+    if not a.no_autotune:   # launch shapes from the autotuner (cached per GPU and problem shape)
+        from paper_2308_13476_gb300 import autotune
+        tuned, _ = autotune.tune(n, n, h, k, a.beta2, rhs, smoother=a.smoother, cycle=a.cycle, nu=a.nu,
+                                 precision=a.precision, cache_path=os.path.join(ROOT, "paper_2308_13476_gb300",
+                                                                                "autotune_cache.json"))
+
+    def make(precision, shapes=None):
         t0 = time.perf_counter()
         s = hm.Solver(n, n, h, k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
-                      precision=precision, batch=a.batch, max_cycles=20000)
+                      precision=precision, batch=a.batch, max_cycles=20000, **(shapes or {}))
         torch.cuda.synchronize()
         return s, time.perf_counter() - t0
 
@@ -277,7 +285,7 @@ def run_ours(a):
         ms = [st_ev[q].elapsed_time(en_ev[q]) for q in range(steps)]
         return ms, cyc, launches, rr
 
-    s, setup_s = make(a.precision)
+    s, setup_s = make(a.precision, tuned)
     timed_solves(s, a.warmup)
     if world > 1:
         import torch.distributed as dist
@@ -320,7 +328,8 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": tmax * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f64" if a.precision == "mixed" else "c128", "data": "synthetic",
-        "config": workload_config(a), "clocks": clk, "gpu_launches": launches,
+        "config": dict(workload_config(a), launch_shapes=tuned or "library defaults"), "clocks": clk,
+        "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rhs.numel() * 16),
                 "d2h_bytes_per_step": int(rhs.numel() * 16)},
         "roofline": roof, "extra": extra,

@@ -83,12 +83,17 @@ typedef struct {
   int coarse_mode;  /* that launch: 0 = one CTA per right-hand side,
                        1 = a cooperative grid of all co-resident CTAs with
                        bounded grid-wide barriers (MG_ETIMEOUT if one gives up) */
+  int fuse;         /* 1 = fused halo-tile kernels: residual + restriction in
+                       one pass, fine-level Jacobi sweeps up to 4 per pass;
+                       0 = one kernel per step (same results)                  */
+  int tile_rows;    /* grid rows per thread of the node kernels: 0 = chosen
+                       from each level's size, 1..4 = forced (autotuner knob) */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
- * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0; default
- * stream. */
+ * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0, fuse 1,
+ * tile_rows 0; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).

@@ -40,7 +40,8 @@ class MgOptions(ctypes.Structure):
     _fields_ = [("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("nu_pre", ctypes.c_int),
                 ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
-                ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("fuse", ctypes.c_int),
+                ("tile_rows", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -220,13 +221,13 @@ class Solver:
 
     Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
            nu_pre, nu_post, omega, precision="fp64"|"mixed", batch, levels,
-           max_cycles, min_coarse, coarse_nodes, stream)
+           max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, stream)
     ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
     """
 
     def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
                  precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, coarse_nodes=None,
-                 coarse_mode=None, stream=None):
+                 coarse_mode=None, fuse=None, tile_rows=None, stream=None):
         o = mg_default_options()
         o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
         o.smoother = SMOOTHERS[smoother]
@@ -237,6 +238,10 @@ class Solver:
             o.coarse_nodes = int(coarse_nodes)
         if coarse_mode is not None:
             o.coarse_mode = int(coarse_mode)
+        if fuse is not None:
+            o.fuse = int(fuse)
+        if tile_rows is not None:
+            o.tile_rows = int(tile_rows)
         o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         self.nx, self.ny, self.h, self.batch = nx, ny, h, batch
         if isinstance(k, (int, float)):

@@ -127,8 +127,9 @@ static cudaError_t dalloc(mg_ctx* c, void** p, size_t bytes) {
 }
 
 // Rows per thread: several on big grids (fewer, fuller blocks and fewer
-// reduction partials), one on small grids (more threads to hide latency).
-static Grid make_grid(int nx, int ny, int B) {
+// reduction partials), one on small grids (more threads to hide latency);
+// tile_rows > 0 forces the value (the autotuner's knob).
+static Grid make_grid(int nx, int ny, int B, int tile_rows = 0) {
   Grid g;
   g.nx = nx;
   g.ny = ny;
@@ -137,6 +138,7 @@ static Grid make_grid(int nx, int ny, int B) {
   g.vstride = (long long)g.pitch * g.rows;
   const long long nodes = (long long)(nx + 1) * (ny + 1) * B;
   g.ry = nodes >= (1LL << 20) ? 4 : (nodes >= (1LL << 18) ? 2 : 1);
+  if (tile_rows > 0) g.ry = std::min(tile_rows, RYMAX);
   return g;
 }
 
@@ -219,7 +221,13 @@ template <class T> struct Emit {
     auto& V = vecs<T>(c)[l];
     const Grid& g = c->lev[l].g;
     const OpView<T> op = opT<T>(c, l);
-    if (c->opt.smoother == 0) {
+    if (c->opt.smoother == 0 && l == 0 && c->opt.fuse && nu > 1) {   // temporal blocking on the fine level
+      for (int q = 0; q < nu; q += jacobi_fused_max_nu()) {
+        const int m = std::min(nu - q, jacobi_fused_max_nu());
+        launch_jacobi_fused<T>(g, op, cur[l], V.b, oth[l], m, c->B, c->active, s);
+        std::swap(cur[l], oth[l]);
+      }
+    } else if (c->opt.smoother == 0) {
       for (int q = 0; q < nu; ++q) {
         launch_jacobi<T>(g, op, cur[l], V.b, oth[l], c->B, c->active, s);
         std::swap(cur[l], oth[l]);
@@ -252,8 +260,12 @@ template <class T> struct Emit {
     const Grid& g = c->lev[l].g;
     const Grid& gc = c->lev[l + 1].g;
     smooth(l, c->opt.nu_pre);
-    launch_residual<T>(g, opT<T>(c, l), cur[l], V[l].b, V[l].r, c->B, c->active, s);
-    launch_restrict<T>(g, gc, V[l].r, V[l + 1].b, c->B, c->active, s);
+    if (c->opt.fuse) {
+      launch_resid_restrict<T>(g, gc, opT<T>(c, l), cur[l], V[l].b, V[l + 1].b, c->B, c->active, s);
+    } else {
+      launch_residual<T>(g, opT<T>(c, l), cur[l], V[l].b, V[l].r, c->B, c->active, s);
+      launch_restrict<T>(g, gc, V[l].r, V[l + 1].b, c->B, c->active, s);
+    }
     if (l + 1 == L - 1 && lc > l + 1) {
       coarse_solve(l + 1);
     } else {
@@ -442,6 +454,8 @@ void mg_default_options(mg_options* o) {
   o->batch = 1;
   o->coarse_nodes = 1100;
   o->coarse_mode = 0;
+  o->fuse = 1;
+  o->tile_rows = 0;
   o->stream = nullptr;
 }
 
@@ -468,13 +482,14 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   if (c->ncoarse > 2048) FAIL(MG_EINVAL, "coarsest grid has %d nodes (> 2048); use more levels", c->ncoarse);
   c->lev.resize(c->nlev);
   for (int l = 0; l < c->nlev; ++l) {
-    c->lev[l].g = make_grid(sizes[l].first, sizes[l].second, c->B);
+    c->lev[l].g = make_grid(sizes[l].first, sizes[l].second, c->B, o.tile_rows);
     c->lev[l].radius = l == 0 ? 1 : (l == 1 ? 2 : 3);
     c->lev[l].plane = (long long)(sizes[l].first + 1) * (sizes[l].second + 1);
   }
   const bool mixed = o.precision == 1;
   const bool gm = o.smoother == 1;
   const Grid& g0 = c->lev[0].g;
+  CK(configure_fused_kernels());
   CK(dalloc(c, (void**)&c->c0d, sizeof(Op0Consts<double>)));
   if (mixed) CK(dalloc(c, (void**)&c->c0f, sizeof(Op0Consts<float>)));
   const long long N0 = c->lev[0].plane;
@@ -658,6 +673,8 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.batch < 1 || o.batch > 65535) FAIL(MG_EINVAL, "batch must be in 1..65535");
   if (o.coarse_nodes < 0) FAIL(MG_EINVAL, "coarse_nodes must be >= 0");
   if (o.coarse_mode != 0 && o.coarse_mode != 1) FAIL(MG_EINVAL, "coarse_mode must be 0 or 1");
+  if (o.fuse != 0 && o.fuse != 1) FAIL(MG_EINVAL, "fuse must be 0 or 1");
+  if (o.tile_rows < 0 || o.tile_rows > RYMAX) FAIL(MG_EINVAL, "tile_rows must be in 0..4");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;

@@ -1,0 +1,161 @@
+// Shared-memory halo-tile kernels that fuse steps of the cycle:
+//
+//  * k_resid_restrict: r_c = R (b - A x) in one pass.  A block owns a tile
+//    of CTX x CTY coarse nodes; it computes the fine residual on the tile's
+//    fine footprint plus the 2-node halo the restriction needs (Eq. (xex)
+//    transposed: fine offsets -2..2 around node 2I) into shared memory, then
+//    every thread restricts one coarse node from it.  The fine residual never
+//    goes to HBM.
+//  * k_jacobi_fused: nu weighted-Jacobi sweeps (Sec. 3) of the fine level in
+//    one pass.  A block loads its tile of x with a nu-node halo and of b
+//    with a (nu-1)-node halo once, runs the sweeps in shared memory on a
+//    region that shrinks by one node per sweep, and writes the tile.  Nodes
+//    outside the grid stay zero (they are not unknowns); nodes computed in
+//    two tiles' halos get identical values, so the result equals nu separate
+//    sweeps node for node.
+#include "internal.h"
+
+namespace hmg {
+
+constexpr int CTX = 32, CTY = 8;                  // coarse tile of k_resid_restrict
+constexpr int RFX = 2 * CTX + 3, RFY = 2 * CTY + 3;  // fine footprint incl. restriction halo
+
+template <class T> __device__ __forceinline__ T rw(int d) {
+  return d == 0 ? T(0.75) : (d == 1 || d == -1) ? T(0.5) : T(0.125);
+}
+
+template <class T, class Op>
+__global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, Op op, const cx<T>* __restrict__ x,
+                                                              const cx<T>* __restrict__ b, cx<T>* __restrict__ rc,
+                                                              const int* __restrict__ active) {
+  __shared__ cx<T> rt[RFY][RFX];
+  const int rhs = blockIdx.z;
+  if (active && !active[rhs]) return;
+  const cx<T>* xs = x + (long long)rhs * gf.vstride;
+  const cx<T>* bs = b + (long long)rhs * gf.vstride;
+  const int I0 = blockIdx.x * CTX, J0 = blockIdx.y * CTY;
+  const int fx0 = 2 * I0 - 2, fy0 = 2 * J0 - 2;   // fine origin of the footprint
+  const int tid = threadIdx.y * CTX + threadIdx.x;
+  for (int q = tid; q < RFX * RFY; q += CTX * CTY) {
+    const int li = q % RFX, lj = q / RFX;
+    const int i = fx0 + li, j = fy0 + lj;
+    cx<T> r = mk<T>(0, 0);   // outside the grid the fine residual is zero
+    if (i >= 0 && i <= gf.nx && j >= 0 && j <= gf.ny) {
+      const int p = gf.at(i, j);
+      r = sub<T>(bs[p], op.apply(xs, p, gf.pitch, i, j));
+    }
+    rt[lj][li] = r;
+  }
+  __syncthreads();
+  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  if (I > gc.nx || J > gc.ny) return;
+  const int ci = 2 * threadIdx.x + 2, cj = 2 * threadIdx.y + 2;   // fine node 2I in the tile
+  cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+  for (int bb = -2; bb <= 2; ++bb) {
+    const cx<T>* row = &rt[cj + bb][ci];
+    cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
+    t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
+    t = add<T>(t, scl<T>(T(0.75), row[0]));
+    acc = add<T>(acc, scl<T>(rw<T>(bb), t));
+  }
+  rc[(long long)rhs * gc.vstride + gc.at(I, J)] = scl<T>(T(0.25), acc);
+}
+
+constexpr int JTX = 64, JTY = 16;        // output tile of k_jacobi_fused
+constexpr int JMAXNU = 4;                // sweeps fused in one launch (more: several launches)
+
+template <class T>
+__global__ void __launch_bounds__(256) k_jacobi_fused(Grid g, Op0<T> op, const cx<T>* __restrict__ x,
+                                                      const cx<T>* __restrict__ b, cx<T>* __restrict__ xo, int nu,
+                                                      const int* __restrict__ active) {
+  extern __shared__ unsigned char smem_raw[];
+  const int rhs = blockIdx.z;
+  if (active && !active[rhs]) return;
+  const int H = nu;                                 // halo of x
+  const int WX = JTX + 2 * H, WY = JTY + 2 * H;
+  cx<T>* A = reinterpret_cast<cx<T>*>(smem_raw);   // x, ping
+  cx<T>* Bf = A + WX * WY;                          // x, pong
+  cx<T>* Bt = Bf + WX * WY;                         // b on the same window
+  const cx<T>* xs = x + (long long)rhs * g.vstride;
+  const cx<T>* bs = b + (long long)rhs * g.vstride;
+  const int i0 = blockIdx.x * JTX - H, j0 = blockIdx.y * JTY - H;   // window origin
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = tid; q < WX * WY; q += nt) {
+    const int li = q % WX, lj = q / WX, i = i0 + li, j = j0 + lj;
+    const bool in = i >= 0 && i <= g.nx && j >= 0 && j <= g.ny;
+    const int p = in ? g.at(i, j) : 0;
+    A[q] = in ? xs[p] : mk<T>(0, 0);
+    Bt[q] = in ? bs[p] : mk<T>(0, 0);
+    Bf[q] = mk<T>(0, 0);
+  }
+  __syncthreads();
+  cx<T>* src = A;
+  cx<T>* dst = Bf;
+  for (int s = 1; s <= nu; ++s) {
+    // sweep s is valid on the window shrunk by s nodes
+    const int lo = s, hix = WX - 1 - s, hiy = WY - 1 - s;
+    const int w = hix - lo + 1, hgt = hiy - lo + 1;
+    for (int q = tid; q < w * hgt; q += nt) {
+      const int li = lo + q % w, lj = lo + q / w, i = i0 + li, j = j0 + lj;
+      const int c = lj * WX + li;
+      if (i < 0 || i > g.nx || j < 0 || j > g.ny) {
+        dst[c] = mk<T>(0, 0);
+        continue;
+      }
+      const cx<T> ax = op.apply5(src[c], src[c + 1], src[c - 1], src[c + WX], src[c - WX], i, j);
+      dst[c] = fma_c<T>(op.diag_inv(i, j), sub<T>(Bt[c], ax), src[c]);
+    }
+    __syncthreads();
+    cx<T>* t = src;
+    src = dst;
+    dst = t;
+  }
+  cx<T>* xd = xo + (long long)rhs * g.vstride;
+  for (int q = tid; q < JTX * JTY; q += nt) {
+    const int li = H + q % JTX, lj = H + q / JTX, i = i0 + li, j = j0 + lj;
+    if (i <= g.nx && j <= g.ny) xd[g.at(i, j)] = src[lj * WX + li];
+  }
+}
+
+template <class T>
+void launch_resid_restrict(const Grid& gf, const Grid& gc, const OpView<T>& v, const cx<T>* x, const cx<T>* b,
+                           cx<T>* rc, int B, const int* active, cudaStream_t s) {
+  const dim3 grd(cdiv(gc.nx + 1, CTX), cdiv(gc.ny + 1, CTY), B);
+  with_op<T>(v, gf.nx, gf.ny, [&](auto op) {
+    k_resid_restrict<T, decltype(op)><<<grd, dim3(CTX, CTY), 0, s>>>(gf, gc, op, x, b, rc, active);
+  });
+}
+
+template <class T> size_t jacobi_fused_smem(int nu) {
+  return sizeof(cx<T>) * 3 * (size_t)(JTX + 2 * nu) * (JTY + 2 * nu);
+}
+
+template <class T>
+void launch_jacobi_fused(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, cx<T>* xo, int nu, int B,
+                         const int* active, cudaStream_t s) {
+  Op0<T> op{v.c0, v.kf, g.nx, g.ny};
+  const dim3 grd(cdiv(g.nx + 1, JTX), cdiv(g.ny + 1, JTY), B);
+  k_jacobi_fused<T><<<grd, 256, jacobi_fused_smem<T>(nu), s>>>(g, op, x, b, xo, nu, active);
+}
+
+int jacobi_fused_max_nu() { return JMAXNU; }
+
+cudaError_t configure_fused_kernels() {   // allow the complex128 window (> 48 KiB) on the current device
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)jacobi_fused_smem<double>(JMAXNU));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_jacobi_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)jacobi_fused_smem<float>(JMAXNU));
+}
+
+template void launch_resid_restrict<double>(const Grid&, const Grid&, const OpView<double>&, const double2*,
+                                            const double2*, double2*, int, const int*, cudaStream_t);
+template void launch_resid_restrict<float>(const Grid&, const Grid&, const OpView<float>&, const float2*,
+                                           const float2*, float2*, int, const int*, cudaStream_t);
+template void launch_jacobi_fused<double>(const Grid&, const OpView<double>&, const double2*, const double2*,
+                                          double2*, int, int, const int*, cudaStream_t);
+template void launch_jacobi_fused<float>(const Grid&, const OpView<float>&, const float2*, const float2*, float2*,
+                                         int, int, const int*, cudaStream_t);
+
+}  // namespace hmg

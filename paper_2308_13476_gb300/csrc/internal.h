@@ -166,6 +166,15 @@ template <class T> cudaError_t launch_cycle_coop(const CLevel<T>* levels, int nl
                                                  const double2* inv, int N, const int* active, int B, int grid,
                                                  const CoopCtl& c, cudaStream_t s);
 
+// Fused halo-tile kernels (fused.cu): r_c = R (b - A x) in one pass (any
+// level), and up to jacobi_fused_max_nu() fine-level Jacobi sweeps in one pass.
+template <class T> void launch_resid_restrict(const Grid& gf, const Grid& gc, const OpView<T>& op, const cx<T>* x,
+                                              const cx<T>* b, cx<T>* rc, int B, const int* active, cudaStream_t s);
+template <class T> void launch_jacobi_fused(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
+                                            cx<T>* xo, int nu, int B, const int* active, cudaStream_t s);
+int jacobi_fused_max_nu();
+cudaError_t configure_fused_kernels();
+
 // Gradient of the receiver misfit (kernels_level.cu).
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u,
                      const double2* lam, int nsrc, double* g, cudaStream_t s);

@@ -1,0 +1,36 @@
+"""The autotuner on the GPU: it returns one of its candidates, caches it, and
+a solver built with the tuned launch shapes reproduces the default solver's
+iterate and cycle count (launch shapes do not change the arithmetic)."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2308_13476_gb300 as hm  # noqa: E402
+from paper_2308_13476_gb300 import autotune  # noqa: E402
+
+
+def test_tuned_shapes_reproduce_default(tmp_path):
+    n, k = 96, 60.0
+    h = 1.0 / n
+    rhs = torch.from_numpy(synth.source_row(n, n, h, 3)).cuda()
+    space = {"tile_rows": [0, 1, 4], "coarse_nodes": [0, 1100], "coarse_mode": [0, 1]}
+    path = os.path.join(tmp_path, "tune.json")
+    best, results = autotune.tune(n, n, h, k, 1 / k, rhs, nu=1, space=space, cache_path=path, cycles=2, reps=1)
+    assert len(results) == 12 and best in [{kk: r[kk] for kk in space} for r in results]
+    assert autotune.tune(n, n, h, k, 1 / k, rhs, nu=1, space=space, cache_path=path)[0] == best   # cached
+    ref = hm.Solver(n, n, h, k, 1 / k, smoother="gmres3", precision="fp64", batch=3, nu_pre=1, nu_post=1)
+    tun = hm.Solver(n, n, h, k, 1 / k, smoother="gmres3", precision="fp64", batch=3, nu_pre=1, nu_post=1, **best)
+    x1, s1, c1, _ = ref.solve(rhs, tol=1e-8)
+    x2, s2, c2, _ = tun.solve(rhs, tol=1e-8)
+    assert s1 == s2 == hm.MG_OK and c1 == c2
+    a, b = x1.cpu().numpy(), x2.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)

@@ -86,8 +86,9 @@ CASES = [
 # in one cooperative launch; the whole cycle in one CTA per RHS; the whole
 # cycle in one cooperative launch
 COARSE = [dict(coarse_nodes=0), dict(), dict(coarse_nodes=1200, coarse_mode=1),
-          dict(coarse_nodes=10**6, coarse_mode=0), dict(coarse_nodes=10**6, coarse_mode=1)]
-COARSE_IDS = ["grid", "default", "hybrid", "cta", "coop"]
+          dict(coarse_nodes=10**6, coarse_mode=0), dict(coarse_nodes=10**6, coarse_mode=1),
+          dict(coarse_nodes=0, fuse=0)]
+COARSE_IDS = ["grid", "default", "hybrid", "cta", "coop", "grid_unfused"]
 
 
 @pytest.mark.parametrize("cn", COARSE, ids=COARSE_IDS)
