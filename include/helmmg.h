@@ -110,6 +110,19 @@ void mg_default_options(mg_options* opt);
 mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_field, double k_const, double beta2,
                    int levels, const mg_options* opt);
 
+/* Ragged batch: nprob independent constant-k problems of different sizes in
+ * one handle (problem p: nx[p] x ny[p] cells of side h[p], wavenumber
+ * k_const[p]; the same shift and options, one right-hand side each, so
+ * opt->batch must be 1).  mg_solve / mg_adjoint on this handle take rhs and x
+ * as the problems' grids packed back to back (problem p starts after
+ * sum_{q<p} (nx[q]+1)(ny[q]+1) complex128 values) and report cycles and
+ * relative residuals per problem.  Every problem has its own hierarchy and
+ * stream; each round launches one cycle of every unconverged problem, so the
+ * problems run side by side on the GPU.  Inspection calls return MG_ESTATE
+ * on a ragged handle. */
+mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* ny, const double* h,
+                          const double* k_const, double beta2, const mg_options* opt);
+
 /* Solve A x = rhs for the handle's batch, starting from the x passed in.
  *   rhs        device, B grids complex128 (read only)
  *   x          device, B grids complex128: initial guess in, iterate out

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "MG_OK", -1: "MG_EINVAL", -2: "MG_ENOMEM", -3: "MG_ECUDA", -4
                 -5: "MG_EDIVERGED", -6: "MG_ETIMEOUT", -7: "MG_ESTATE"}
 EXPORTED = ["mg_default_options", "mg_setup", "mg_solve", "mg_adjoint", "mg_gradient", "mg_destroy",
             "mg_last_error", "mg_level_info", "mg_apply", "mg_get_stencil", "mg_history", "mg_profile",
-            "mg_counters", "mg_residual_norm_static"]
+            "mg_counters", "mg_residual_norm_static", "mg_setup_ragged"]
 
 
 class HelmmgUnavailable(RuntimeError):
@@ -72,6 +72,7 @@ def load_library(path=LIB_PATH):
     lib.mg_profile.argtypes = [vp, i, i, i, dp, dp]
     lib.mg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.mg_residual_norm_static.argtypes = [i, i, d, vp, d, vp, vp, vp, vp]
+    lib.mg_setup_ragged.argtypes = [ctypes.POINTER(vp), i, ip, ip, dp, dp, d, ctypes.POINTER(MgOptions)]
     for name in EXPORTED:
         if name not in ("mg_default_options", "mg_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -209,11 +210,78 @@ def mg_residual_norm_static(nx, ny, h, k, x, b, out, stream=None):
                                                   ctypes.c_void_p(st)))
 
 
+def mg_setup_ragged(nx, ny, h, k_const, beta2=0.0, opt=None):
+    """Handle of a ragged batch (lists of per-problem sizes, cell sizes and wavenumbers)."""
+    lib = load_library()
+    opt = opt or mg_default_options()
+    n = len(nx)
+    hdl = ctypes.c_void_p()
+    ia = lambda v: (ctypes.c_int * n)(*[int(q) for q in v])
+    da = lambda v: (ctypes.c_double * n)(*[float(q) for q in v])
+    _check(lib.mg_setup_ragged(ctypes.byref(hdl), n, ia(nx), ia(ny), da(h), da(k_const), float(beta2),
+                               ctypes.byref(opt)))
+    return hdl.value
+
+
 # ------------------------------------------------------------- convenience
 
 
 SMOOTHERS = {"jacobi": 0, "gmres3": 1}
+
+
+def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, precision="fp64", batch=1,
+             max_cycles=10000, min_coarse=10, coarse_nodes=None, coarse_mode=None, fuse=None, tile_rows=None,
+             stream=None):
+    o = mg_default_options()
+    o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
+    o.smoother = SMOOTHERS[smoother]
+    o.nu_pre, o.nu_post, o.omega = int(nu_pre), int(nu_post), float(omega)
+    o.precision = PRECISIONS[precision]
+    o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
+    for name, val in (("coarse_nodes", coarse_nodes), ("coarse_mode", coarse_mode), ("fuse", fuse),
+                      ("tile_rows", tile_rows)):
+        if val is not None:
+            setattr(o, name, int(val))
+    o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
+    return o
 PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class RaggedSolver:
+    """Independent constant-k problems of different sizes solved together.
+
+    RaggedSolver(sizes=[(nx, ny, h, k), ...], beta2, **options).  solve()
+    takes and returns a list of complex128 CUDA grids (ny+1, nx+1)."""
+
+    def __init__(self, sizes, beta2, **options):
+        self.sizes = [(int(a), int(b), float(c), float(d)) for a, b, c, d in sizes]
+        o = _options(**options)
+        self.handle = mg_setup_ragged([s[0] for s in self.sizes], [s[1] for s in self.sizes],
+                                      [s[2] for s in self.sizes], [s[3] for s in self.sizes], beta2, o)
+
+    def solve(self, rhs_list, tol=1e-6):
+        import torch
+        flat = torch.cat([r.reshape(-1).to(torch.complex128) for r in rhs_list]).contiguous()
+        x = torch.zeros_like(flat)
+        n = len(self.sizes)
+        st, cyc, rr = mg_solve(self.handle, flat, x, tol, n)
+        out, o = [], 0
+        for nx, ny, _, _ in self.sizes:
+            m = (nx + 1) * (ny + 1)
+            out.append(x[o:o + m].reshape(ny + 1, nx + 1))
+            o += m
+        return out, st, cyc, rr
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -108,13 +108,18 @@ struct mg_ctx {
   CoarsePlan<float> plan32;
   long long graph_kernels = 0;     // kernel nodes in the cycle graph
   long long last_launches = 0, last_graphs = 0;
+  int done = 0;                    // cycles of the current solve
+  std::vector<mg_ctx*> sub;        // ragged batch: one handle per problem
+  cudaStream_t own_stream = nullptr;
 
   ~mg_ctx() {
+    for (mg_ctx* p : sub) delete p;
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     for (void* p : allocs) cudaFree(p);
     if (h_n_active) cudaFreeHost(h_n_active);
     if (cap) cudaStreamDestroy(cap);
+    if (own_stream) cudaStreamDestroy(own_stream);
   }
 };
 
@@ -694,6 +699,42 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   return MG_OK;
 }
 
+mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* ny, const double* h,
+                          const double* k_const, double beta2, const mg_options* opt) {
+  if (!out) FAIL(MG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || !nx || !ny || !h || !k_const) FAIL(MG_EINVAL, "ragged batch needs nprob >= 1 and its arrays");
+  mg_options o;
+  if (opt) o = *opt; else mg_default_options(&o);
+  if (o.batch != 1) FAIL(MG_EINVAL, "a ragged batch solves one right-hand side per problem (batch must be 1)");
+  mg_ctx* c = new mg_ctx();
+  c->opt = o;
+  for (int p = 0; p < nprob; ++p) {
+    cudaStream_t sp;
+    if (cudaStreamCreateWithFlags(&sp, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      FAIL(MG_ECUDA, "stream creation failed");
+    }
+    mg_options op = o;
+    op.stream = sp;
+    mg_handle hp = nullptr;
+    mg_status st = mg_setup(&hp, nx[p], ny[p], h[p], nullptr, k_const[p], beta2, 0, &op);
+    if (st != MG_OK) {
+      cudaStreamDestroy(sp);
+      std::string m = g_err;
+      delete c;
+      FAIL(st, "problem %d of the ragged batch: %s", p, m.c_str());
+    }
+    hp->own_stream = sp;
+    c->sub.push_back(hp);
+  }
+  c->nx = c->sub[0]->nx;
+  c->ny = c->sub[0]->ny;
+  c->nlev = c->sub[0]->nlev;
+  *out = c;
+  return MG_OK;
+}
+
 static mg_status capture(mg_ctx* c) {
   if (c->gexec) return MG_OK;
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -717,8 +758,14 @@ static mg_status capture(mg_ctx* c) {
   return MG_OK;
 }
 
-static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out,
-                            int conj) {
+// A solve in four phases, so that several handles (the problems of a ragged
+// batch) can run their cycles side by side on their own streams:
+// solve_begin packs the inputs, sets up the per-RHS control arrays and runs
+// the initial stopping test; solve_launch issues one cycle (graph) and the
+// asynchronous read-back of the active count; solve_more says, after the
+// stream is synchronised, whether another cycle is needed; solve_end
+// unpacks x and reports.
+static mg_status solve_begin(mg_ctx* c, const void* rhs, void* x, double tol, int conj) {
   if (!rhs || !x) FAIL(MG_EINVAL, "rhs and x must be device pointers");
   if (!(tol > 0)) FAIL(MG_EINVAL, "tol must be > 0");
   cudaStream_t s = (cudaStream_t)c->opt.stream;
@@ -733,8 +780,7 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
   std::vector<double> bn(B);
   CK(cudaMemcpyAsync(bn.data(), c->bnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  // control arrays
-  std::vector<int> act(B), zero(B, 0);
+  std::vector<int> act(B), zero(B, 0), stt(B);
   std::vector<double> bsafe(B);
   const double tolv[2] = {tol, 1e6};
   int nact = 0;
@@ -742,10 +788,9 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
     act[b] = bn[b] > 0.0;
     nact += act[b];
     bsafe[b] = bn[b] > 0 ? bn[b] : 1.0;
+    stt[b] = act[b] ? 0 : 1;
     if (bn[b] == 0.0) CK(cudaMemsetAsync(c->v64[0].x + (size_t)b * g0.vstride, 0, sizeof(double2) * g0.vstride, s));
   }
-  std::vector<int> stt(B);
-  for (int b = 0; b < B; ++b) stt[b] = act[b] ? 0 : 1;
   CK(cudaMemcpyAsync(c->active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->state, stt.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->cycles, zero.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
@@ -756,33 +801,42 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
   if (c->coop.bar) CK(cudaMemsetAsync(c->coop.bar, 0, sizeof(unsigned) * 2, s));
   CK(cudaMemsetAsync(c->relres, 0, sizeof(double) * B, s));
   CK(cudaMemsetAsync(c->hist, 0, sizeof(double) * (size_t)c->hist_len * B, s));
-  // initial test on x0
-  if (mixed)
+  if (mixed)   // initial test on x0
     launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, B, ctl(c), 0, s);
   else
     launch_resnorm_stop<double>(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, B, ctl(c), 0, s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  int done = 0;
-  // direct launches: 2 pack + norm + initial residual test + unpack
-  c->last_launches = 5;
+  c->done = 0;
+  c->last_launches = 5;   // 2 pack + norm + initial residual test + unpack
   c->last_graphs = 0;
-  while (c->h_n_active[0] > 0 && c->h_n_active[1] == 0 && done < c->opt.max_cycles) {
-    CK(cudaGraphLaunch(c->gexec, s));
-    ++done;
-    c->last_graphs += 1;
-    c->last_launches += c->graph_kernels;
-    CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-  }
+  return MG_OK;
+}
+
+static bool solve_more(const mg_ctx* c) {
+  return c->h_n_active[0] > 0 && c->h_n_active[1] == 0 && c->done < c->opt.max_cycles;
+}
+
+static mg_status solve_launch(mg_ctx* c) {
+  cudaStream_t s = (cudaStream_t)c->opt.stream;
+  CK(cudaGraphLaunch(c->gexec, s));
+  ++c->done;
+  c->last_graphs += 1;
+  c->last_launches += c->graph_kernels;
+  CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  return MG_OK;
+}
+
+static mg_status solve_end(mg_ctx* c, void* x, int conj, int* cycles_out, double* relres_out) {
+  cudaStream_t s = (cudaStream_t)c->opt.stream;
+  const Grid& g0 = c->lev[0].g;
+  const int B = c->B;
+  launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
   if (c->h_n_active[1] != 0) {
-    launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
     cudaStreamSynchronize(s);
     FAIL(MG_ETIMEOUT, "a grid-wide barrier of the cooperative cycle kernel timed out");
   }
-  launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
-  std::vector<int> cyc(B);
+  std::vector<int> cyc(B), stt(B);
   std::vector<double> rr(B);
   CK(cudaMemcpyAsync(stt.data(), c->state, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(cyc.data(), c->cycles, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
@@ -801,6 +855,62 @@ static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int
   return MG_OK;
 }
 
+// Ragged batch: every problem on its own stream, one cycle graph per
+// unconverged problem per round, all problems polled after each round.
+static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out,
+                              int conj) {
+  if (!rhs || !x) FAIL(MG_EINVAL, "rhs and x must be device pointers");
+  CK(cudaStreamSynchronize((cudaStream_t)c->opt.stream));   // the caller's inputs are ready
+  const int P = (int)c->sub.size();
+  std::vector<size_t> off(P + 1, 0);
+  for (int p = 0; p < P; ++p) off[p + 1] = off[p] + (size_t)(c->sub[p]->nx + 1) * (c->sub[p]->ny + 1);
+  for (int p = 0; p < P; ++p) {
+    mg_status st = solve_begin(c->sub[p], (const double2*)rhs + off[p], (double2*)x + off[p], tol, conj);
+    if (st != MG_OK) return st;
+  }
+  long long launches = 0;
+  while (true) {
+    for (int p = 0; p < P; ++p) CK(cudaStreamSynchronize((cudaStream_t)c->sub[p]->opt.stream));
+    bool any = false;
+    for (int p = 0; p < P; ++p)
+      if (solve_more(c->sub[p])) {
+        mg_status st = solve_launch(c->sub[p]);
+        if (st != MG_OK) return st;
+        any = true;
+      }
+    if (!any) break;
+  }
+  mg_status worst = MG_OK;
+  std::string msg;
+  for (int p = 0; p < P; ++p) {
+    mg_status st = solve_end(c->sub[p], (double2*)x + off[p], conj, cycles_out ? cycles_out + p : nullptr,
+                             relres_out ? relres_out + p : nullptr);
+    launches += c->sub[p]->last_launches;
+    if (st != MG_OK && (worst == MG_OK || st == MG_EDIVERGED)) {
+      worst = st;
+      msg = g_err;
+    }
+  }
+  c->last_launches = launches;
+  if (worst != MG_OK) FAIL(worst, "problem(s) of the ragged batch: %s", msg.c_str());
+  return MG_OK;
+}
+
+static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out,
+                            int conj) {
+  if (!c->sub.empty()) return solve_ragged(c, rhs, x, tol, cycles_out, relres_out, conj);
+  mg_status st = solve_begin(c, rhs, x, tol, conj);
+  if (st != MG_OK) return st;
+  cudaStream_t s = (cudaStream_t)c->opt.stream;
+  CK(cudaStreamSynchronize(s));
+  while (solve_more(c)) {
+    st = solve_launch(c);
+    if (st != MG_OK) return st;
+    CK(cudaStreamSynchronize(s));
+  }
+  return solve_end(c, x, conj, cycles_out, relres_out);
+}
+
 mg_status mg_solve(mg_handle h, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out) {
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   return solve_impl(h, rhs, x, tol, cycles_out, relres_out, 0);
@@ -813,6 +923,7 @@ mg_status mg_adjoint(mg_handle h, const void* rhs_adj, void* lam, double tol, in
 
 mg_status mg_gradient(mg_handle h, const void* u, const void* lam, int nsrc, const double* m, double omega_f,
                       double* g) {
+  if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (!u || !lam || !m || !g || nsrc < 1 || !(omega_f > 0)) FAIL(MG_EINVAL, "bad gradient arguments");
   cudaStream_t s = (cudaStream_t)h->opt.stream;
@@ -823,6 +934,7 @@ mg_status mg_gradient(mg_handle h, const void* u, const void* lam, int nsrc, con
 }
 
 mg_status mg_level_info(mg_handle h, int level, int* nx, int* ny, int* radius, int* nlevels) {
+  if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (nlevels) *nlevels = h->nlev;
   if (level < 0 || level >= h->nlev) FAIL(MG_EINVAL, "level %d out of range", level);
@@ -833,6 +945,7 @@ mg_status mg_level_info(mg_handle h, int level, int* nx, int* ny, int* radius, i
 }
 
 mg_status mg_apply(mg_handle h, int level, const void* x, void* y) {
+  if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (level < 0 || level >= h->nlev || !x || !y) FAIL(MG_EINVAL, "bad mg_apply arguments");
   cudaStream_t s = (cudaStream_t)h->opt.stream;
@@ -856,6 +969,7 @@ mg_status mg_apply(mg_handle h, int level, const void* x, void* y) {
 }
 
 mg_status mg_get_stencil(mg_handle h, int level, void* out) {
+  if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (level < 0 || level >= h->nlev || !out) FAIL(MG_EINVAL, "bad mg_get_stencil arguments");
   cudaStream_t s = (cudaStream_t)h->opt.stream;
@@ -874,6 +988,7 @@ mg_status mg_counters(mg_handle h, long long* kernel_launches, long long* graph_
 }
 
 mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes) {
+  if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (what < 0 || what > 3 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
   if (h->opt.precision == 1) return profile_t<float>(h, what, level, reps, ms, bytes);
@@ -881,6 +996,7 @@ mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, dou
 }
 
 mg_status mg_history(mg_handle h, double* hist, int cap) {
+  if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (!hist || cap < 1) FAIL(MG_EINVAL, "bad history buffer");
   cudaStream_t s = (cudaStream_t)h->opt.stream;
