@@ -237,6 +237,10 @@ template <class T> struct Emit {
         launch_jacobi<T>(g, op, cur[l], V.b, oth[l], c->B, c->active, s);
         std::swap(cur[l], oth[l]);
       }
+    } else if (c->opt.fuse && op.kind == 1) {
+      gmres_smooth_march<T>(g, op, cur[l], V.b, nu, c->B, c->active, V.gb, s);
+    } else if (c->opt.fuse && op.kind >= 4) {
+      gmres_smooth_kron<T>(g, op, cur[l], V.b, nu, c->B, c->active, V.gb, s);
     } else {
       gmres_smooth<T>(g, op, cur[l], V.b, nu, c->B, c->active, V.gb, s);
     }
@@ -594,7 +598,13 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   }
   // work arrays
   long long nblk_max = 0;   // reduction partials: the most blocks of any level
-  for (int l = 0; l < c->nlev; ++l) nblk_max = std::max(nblk_max, node_blocks(c->lev[l].g));
+  for (int l = 0; l < c->nlev; ++l) {
+    nblk_max = std::max(nblk_max, node_blocks(c->lev[l].g));
+    if (c->lev[l].kind == 1)
+      nblk_max = std::max({nblk_max, gmres_march_blocks(c->lev[l].g, true, c->B),
+                           gmres_march_blocks(c->lev[l].g, false, c->B)});
+    if (c->lev[l].kind >= 4) nblk_max = std::max(nblk_max, kron_march_blocks(c->lev[l].g, c->B));
+  }
   CK(dalloc(c, (void**)&c->partial, sizeof(double) * (size_t)nblk_max * c->B * NVMAX));
   CK(dalloc(c, (void**)&c->tickets, sizeof(unsigned) * c->B));
   CK(dalloc(c, (void**)&c->gst, sizeof(double) * 96 * c->B));

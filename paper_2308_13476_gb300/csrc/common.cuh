@@ -18,7 +18,7 @@ constexpr int BX = 32;   // block shape of the node-parallel kernels
 constexpr int BY = 8;
 constexpr int RYMAX = 4; // largest number of grid rows per thread (Grid::ry)
 constexpr int MAXR = 3;  // largest Galerkin stencil radius (7 x 7)
-constexpr int NVMAX = 8; // values per block partial record
+constexpr int NVMAX = 12; // values per block partial record
 
 template <class T> struct cvec;
 template <> struct cvec<double> { using type = double2; };

@@ -134,4 +134,18 @@ template <int J, class Ts> __device__ __forceinline__ void fin_b(double* S, cons
   if (J == 2 || S[G_BRK] != 0.0) lsq<Ts>(S);
 }
 
+// Runs a scalar step on the RHS state in shared memory (all threads of the
+// block copy it in and out; thread 0 computes), so its many dependent reads
+// and writes stay on chip.
+template <class T, class F>
+__device__ __forceinline__ void staged(double* S, const double* v, F f) {
+  __shared__ double Ssh[GS];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x, nt = blockDim.x * blockDim.y;
+  for (int k = tid; k < GS; k += nt) Ssh[k] = S[k];
+  __syncthreads();
+  if (tid == 0) f(Ssh, v);
+  __syncthreads();
+  for (int k = tid; k < GS; k += nt) S[k] = Ssh[k];
+}
+
 }  // namespace hmg

@@ -122,6 +122,20 @@ struct GmresBufs {
 template <class T> void gmres_smooth(const Grid& g, const OpView<T>& op, cx<T>* x, const cx<T>* b, int nu, int B,
                                      const int* active, const GmresBufs& gb, cudaStream_t s);
 
+// The same smoother on the fine level (kind 1) in four row-marching passes
+// plus the update (gmres_march.cu); the partial buffer must hold
+// gmres_march_blocks() records per RHS.
+long long gmres_march_blocks(const Grid& g, bool fp64, int B);
+template <class T> void gmres_smooth_march(const Grid& g, const OpView<T>& op, cx<T>* x, const cx<T>* b, int nu,
+                                           int B, const int* active, const GmresBufs& gb, cudaStream_t s);
+
+// The same smoother on a Kronecker-form level (kinds 4, 5) with the kernels
+// that apply A written as column marches (kron_march.cu); the partial buffer
+// must hold kron_march_blocks() records per RHS.
+long long kron_march_blocks(const Grid& g, int B);
+template <class T> void gmres_smooth_kron(const Grid& g, const OpView<T>& op, cx<T>* x, const cx<T>* b, int nu, int B,
+                                          const int* active, const GmresBufs& gb, cudaStream_t s);
+
 // Single-CTA coarse-cycle interpreter (coarse.cu).  One CTA per RHS walks a
 // host-recorded list of steps over the levels lc..L-1.
 constexpr int CTA_THREADS = 512;

@@ -30,20 +30,6 @@ namespace hmg {
   const int nblk = gridDim.x * gridDim.y;                \
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;   \
   const bool t0 = threadIdx.x == 0 && threadIdx.y == 0;
-// Runs a scalar step on the RHS state in shared memory (all threads of the
-// block copy it in and out; thread 0 computes), so its many dependent reads
-// and writes stay on chip.
-template <class T, class F>
-__device__ __forceinline__ void staged(double* S, const double* v, F f) {
-  __shared__ double Ssh[GS];
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x, nt = blockDim.x * blockDim.y;
-  for (int k = tid; k < GS; k += nt) Ssh[k] = S[k];
-  __syncthreads();
-  if (tid == 0) f(Ssh, v);
-  __syncthreads();
-  for (int k = tid; k < GS; k += nt) S[k] = Ssh[k];
-}
-
 #define GROWS for (int r_ = 0, j = blockIdx.y * BY * g.ry + threadIdx.y; r_ < g.ry; ++r_, j += BY)
 
 // u0 = b - A x, partial |u0|^2
@@ -236,6 +222,28 @@ void gmres_smooth(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T>* b,
   });
 }
 
+template <class T>
+void launch_gmres_update(const Grid& g, cx<T>* x, const GmresBufs& gb, int B, const int* active, cudaStream_t s) {
+  dim3 grd(cdiv(g.nx + 1, BX * PK<T>::NP), cdiv(g.ny + 1, BY * g.ry), B);
+  g_update<T><<<grd, dim3(BX, BY), 0, s>>>(g, x, (const cx<T>*)gb.u[0], (const cx<T>*)gb.u[1],
+                                          (const cx<T>*)gb.u[2], gb.st, active);
+}
+
+template <class T, int J>
+void launch_arn_b(const Grid& g, const GmresBufs& gb, cx<T>* un, int B, const int* active, cudaStream_t s) {
+  dim3 grd(cdiv(g.nx + 1, BX * PK<T>::NP), cdiv(g.ny + 1, BY * g.ry), B);
+  g_arn_b<T, J><<<grd, dim3(BX, BY), 0, s>>>(g, (const cx<T>*)gb.u[0], (const cx<T>*)gb.u[1], (const cx<T>*)gb.u[2],
+                                            un, (const cx<T>*)gb.w, gb.st, gb.partial, gb.tickets, active);
+}
+
+template void launch_arn_b<double, 0>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t);
+template void launch_arn_b<double, 1>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t);
+template void launch_arn_b<double, 2>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t);
+template void launch_arn_b<float, 0>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t);
+template void launch_arn_b<float, 1>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t);
+template void launch_arn_b<float, 2>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t);
+template void launch_gmres_update<double>(const Grid&, double2*, const GmresBufs&, int, const int*, cudaStream_t);
+template void launch_gmres_update<float>(const Grid&, float2*, const GmresBufs&, int, const int*, cudaStream_t);
 template void gmres_smooth<double>(const Grid&, const OpView<double>&, double2*, const double2*, int, int, const int*,
                                    const GmresBufs&, cudaStream_t);
 template void gmres_smooth<float>(const Grid&, const OpView<float>&, float2*, const float2*, int, int, const int*,
