@@ -82,6 +82,9 @@ struct mg_ctx {
   Op0Consts<float> hc0f{};
   double* kf64 = nullptr;
   float* kf32 = nullptr;
+  FFConsts* ffc = nullptr;   // mixed path: float-float constants (device) and host copy
+  FFConsts hffc{};
+  float2* ffdiag = nullptr;  // mixed path, variable k: per-node float-float diagonal
   double2* cinv = nullptr;
   double* partial = nullptr;
   unsigned* tickets = nullptr;
@@ -389,16 +392,17 @@ static void emit_fp64_iteration(mg_ctx* c, cudaStream_t s) {
 }
 
 // One refinement step of the mixed path: e = 0, one complex64 cycle on the
-// float residual, x += e in FP64, new FP64 residual (cast to float) and the
-// stopping test.
+// float residual, x += e in float-float, the new float-float residual (cast
+// to float) and the stopping test.
 static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
   Emit<float> e{c, s, {}, {}, c->lc, &c->plan32};
   e.init();
   const Grid& g0 = c->lev[0].g;
   cudaMemsetAsync(c->v32[0].x, 0, sizeof(float2) * (size_t)g0.vstride * c->B, s);
   e.cycle(0);
-  launch_update_mixed(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
-  launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B, ctl(c), 1, s);
+  launch_ff_update(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
+  launch_ff_resid_cast_stop(g0, c->hffc, c->kf64, c->h, c->ffdiag, c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B,
+                            ctl(c), 1, s);
 }
 
 template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, int reps, double* ms, double* bytes) {
@@ -512,7 +516,13 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   }
   launch_op0consts(c->c0d, c->c0f, c->h, c->kconst, o.omega, c->beta2, s);
   CK(cudaMemcpyAsync(&c->hc0d, c->c0d, sizeof(Op0Consts<double>), cudaMemcpyDeviceToHost, s));
-  if (mixed) CK(cudaMemcpyAsync(&c->hc0f, c->c0f, sizeof(Op0Consts<float>), cudaMemcpyDeviceToHost, s));
+  if (mixed) {
+    CK(cudaMemcpyAsync(&c->hc0f, c->c0f, sizeof(Op0Consts<float>), cudaMemcpyDeviceToHost, s));
+    CK(dalloc(c, (void**)&c->ffc, sizeof(FFConsts)));
+    if (k_field) CK(dalloc(c, (void**)&c->ffdiag, sizeof(float2) * N0));
+    launch_ff_setup(c->h, c->kconst, c->kf64, g0.nx, g0.ny, c->ffc, c->ffdiag, s);
+    CK(cudaMemcpyAsync(&c->hffc, c->ffc, sizeof(FFConsts), cudaMemcpyDeviceToHost, s));
+  }
   CK(cudaStreamSynchronize(s));
   // Galerkin operators A_{l+1} = R_l C_l P_l.  Constant k: Kronecker form,
   // A_l = W_y (x) G_x + H_y (x) W_x, each factor coarsened in 1D.  Variable
@@ -784,9 +794,15 @@ static mg_status solve_begin(mg_ctx* c, const void* rhs, void* x, double tol, in
   const bool mixed = c->opt.precision == 1;
   mg_status st = capture(c);
   if (st != MG_OK) return st;
-  launch_pack<double>(g0, (const double2*)rhs, c->v64[0].b, B, conj, s);
-  launch_pack<double>(g0, (const double2*)x, c->v64[0].x, B, conj, s);
-  launch_vecnorm_fin<double>(g0, c->v64[0].b, B, c->bnorm, c->partial, c->tickets, s);
+  if (mixed) {   // level-0 outer vectors in float-float
+    launch_ff_pack(g0, (const double2*)rhs, c->v64[0].b, B, conj, s);
+    launch_ff_pack(g0, (const double2*)x, c->v64[0].x, B, conj, s);
+    launch_ff_norm(g0, c->v64[0].b, B, c->bnorm, c->partial, c->tickets, s);
+  } else {
+    launch_pack<double>(g0, (const double2*)rhs, c->v64[0].b, B, conj, s);
+    launch_pack<double>(g0, (const double2*)x, c->v64[0].x, B, conj, s);
+    launch_vecnorm_fin<double>(g0, c->v64[0].b, B, c->bnorm, c->partial, c->tickets, s);
+  }
   std::vector<double> bn(B);
   CK(cudaMemcpyAsync(bn.data(), c->bnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -812,7 +828,8 @@ static mg_status solve_begin(mg_ctx* c, const void* rhs, void* x, double tol, in
   CK(cudaMemsetAsync(c->relres, 0, sizeof(double) * B, s));
   CK(cudaMemsetAsync(c->hist, 0, sizeof(double) * (size_t)c->hist_len * B, s));
   if (mixed)   // initial test on x0
-    launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, B, ctl(c), 0, s);
+    launch_ff_resid_cast_stop(g0, c->hffc, c->kf64, c->h, c->ffdiag, c->v64[0].x, c->v64[0].b, c->v32[0].b, B,
+                              ctl(c), 0, s);
   else
     launch_resnorm_stop<double>(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, B, ctl(c), 0, s);
   CK(cudaGetLastError());
@@ -841,7 +858,10 @@ static mg_status solve_end(mg_ctx* c, void* x, int conj, int* cycles_out, double
   cudaStream_t s = (cudaStream_t)c->opt.stream;
   const Grid& g0 = c->lev[0].g;
   const int B = c->B;
-  launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
+  if (c->opt.precision == 1)
+    launch_ff_unpack(g0, c->v64[0].x, (double2*)x, B, conj, s);
+  else
+    launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
   if (c->h_n_active[1] != 0) {
     cudaStreamSynchronize(s);
     FAIL(MG_ETIMEOUT, "a grid-wide barrier of the cooperative cycle kernel timed out");

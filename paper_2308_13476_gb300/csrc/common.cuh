@@ -287,4 +287,54 @@ __device__ __forceinline__ bool reduce_last(const T (&vin)[NV], double (&v)[NV],
   return true;
 }
 
+// The same sum split over two launches on one stream: the first launch's
+// blocks only publish their block sums (publish, records 0 .. rec0-1); the
+// second launch's blocks publish after them (records rec0 + blk) and take
+// tickets, and its last block sums all nrec records in record order.
+// partial: [rhs][nrec][NVMAX].
+template <int NV, class T>
+__device__ __forceinline__ void publish(const T (&vin)[NV], double* sh, double* partial, int rhs, int nrec, int rec) {
+  double v[NV];
+  block_sum_t<NV, T>(vin, sh, v);
+  if (threadIdx.x + threadIdx.y * blockDim.x == 0) {
+    double* q = partial + ((long long)rhs * nrec + rec) * NVMAX;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) q[k] = v[k];
+  }
+}
+template <int NV, class T>
+__device__ __forceinline__ bool reduce_last_at(const T (&vin)[NV], double (&v)[NV], double* sh, double* partial,
+                                               unsigned* tickets, int rhs, int nblk, int blk, int rec0, int nrec) {
+  __shared__ int s_last;
+  block_sum_t<NV, T>(vin, sh, v);
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nt = blockDim.x * blockDim.y;
+  if (tid == 0) {
+    double* q = partial + ((long long)rhs * nrec + rec0 + blk) * NVMAX;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) q[k] = v[k];
+    __threadfence();
+    const unsigned t = atomicAdd(&tickets[rhs], 1u);
+    s_last = (t == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int b = tid; b < nrec; b += nt) {
+    const double* q = partial + ((long long)rhs * nrec + b) * NVMAX;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(q + k);
+  }
+  block_sum<NV>(acc, sh);
+  if (tid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = acc[k];
+    tickets[rhs] = 0u;
+  }
+  return true;
+}
+
 }  // namespace hmg

@@ -4,12 +4,12 @@
 // The node-parallel version (kernels_gmres.cu) stores w = A v_j and needs
 // eight grid passes, about 28 vector reads and writes per step.  Here each
 // warp owns a strip of columns and walks down a chunk of rows, keeping the
-// last three rows of every field it needs in registers (horizontal
-// neighbours come from the adjacent lanes by shuffles).  Row m of the next
-// Arnoldi vector is formed as soon as rows m-1..m+1 of its input are in
-// registers (w = A v_j is recomputed, never stored), and A is applied to
-// the new vector one row behind, so the dots of Arnoldi step j+1 come out of
-// the pass that creates u_{j+1}:
+// rows it needs of every field in registers (horizontal neighbours come from
+// the adjacent lanes by shuffles).  Row m of the next Arnoldi vector is
+// formed as soon as rows m-1..m+1 of its input are in registers (w = A v_j is
+// recomputed, never stored), and A is applied to the new vector one row
+// behind, so the dots of Arnoldi step j+1 come out of the pass that creates
+// u_{j+1}:
 //   M0: u0 = b - A x                      |u0|^2, <u0, A u0>
 //   M1: u1 = s0 A u0 - c00 u0             |u1|^2, <u1, u0>, <u_l, A u1>
 //   M2: u2 = s1 A u1 - sum c_l1 u_l       |u2|^2, <u2, u_l>, <u_l, A u2>
@@ -25,8 +25,20 @@
 // its strip; after the two stencil applications of a pass the outer two
 // columns on each side are invalid, so a strip is 32 NP - 4 columns wide and
 // neighbouring strips overlap by four loaded columns.  Rows: a warp covers a
-// chunk of CH rows and reads two rows above and below it.  Nodes outside the
+// chunk of rows (see MGeo) and reads two rows above and below it.  Nodes outside the
 // grid are zero in every produced vector (they are not unknowns).
+//
+// Rows arrive through a per-lane ring of four 16-byte shared-memory slots
+// filled by cp.async three rows ahead of use (each lane reads back only what
+// it copied, so no barrier is needed), and every field keeps the rows it
+// uses in a ring of four registers.  Row r sits in slot (r - j0 + 2) mod 4 of
+// both rings, and the march is unrolled by four so that the slots are
+// compile-time names (no copies as the rings advance).  A warp whose loaded
+// columns and computed rows hold no boundary node takes the interior path:
+// the stencil without boundary tests (the same arithmetic as Op0::apply5's
+// interior case).
+#include <algorithm>
+
 #include "gmres.cuh"
 #include "internal.h"
 
@@ -34,7 +46,7 @@ namespace hmg {
 
 namespace {
 
-constexpr int MW = 4;   // warps per block
+constexpr int MD = 3;   // rows in flight ahead of use
 
 template <class T> struct MNP { static constexpr int NP = 1; };
 template <> struct MNP<float> { static constexpr int NP = 2; };
@@ -49,22 +61,33 @@ template <class T> __device__ __forceinline__ Row<T> zrow() {
   return r;
 }
 
-// Row j of a slice at this lane's nodes i.. (zero right of the grid; the
-// padded layout makes the two columns left of the grid and the rows
-// -2..ny+2 readable zeros).
-__device__ __forceinline__ Row<float> mload(const float2* __restrict__ s, const Grid& g, int i, int j) {
+// Asynchronous copy of this lane's 16 bytes of row j (nodes i..) into a
+// shared-memory slot; columns right of the grid are zero-filled (the padded
+// layout makes the two columns left of the grid and the rows -2..ny+2
+// readable zeros).
+template <class T>
+__device__ __forceinline__ void stage_row(uint32_t dst, const cx<T>* __restrict__ s, const Grid& g, int i, int j) {
+  const bool ok = i <= g.nx;
+  const cx<T>* src = s + g.at(ok ? i : 0, j);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(MD) : "memory"); }
+__device__ __forceinline__ Row<float> stage_read(const float4* p) {
+  const float4 q = *p;
   Row<float> r;
-  if (i > g.nx) return zrow<float>();
-  const float4 q = __ldg(reinterpret_cast<const float4*>(s + g.at(i, j)));
   r.v[0] = make_float2(q.x, q.y);
   r.v[1] = make_float2(q.z, q.w);
   return r;
 }
-__device__ __forceinline__ Row<double> mload(const double2* __restrict__ s, const Grid& g, int i, int j) {
+__device__ __forceinline__ Row<double> stage_read(const double2* p) {
   Row<double> r;
-  r.v[0] = i > g.nx ? zc<double>() : __ldg(s + g.at(i, j));
+  r.v[0] = *p;
   return r;
 }
+template <class T> struct SlotT { using type = double2; };
+template <> struct SlotT<float> { using type = float4; };
+
 __device__ __forceinline__ void mstore(float2* __restrict__ d, const Grid& g, int i, int j, const Row<float>& r) {
   if (i + 1 <= g.nx)
     *reinterpret_cast<float4*>(d + g.at(i, j)) = make_float4(r.v[0].x, r.v[0].y, r.v[1].x, r.v[1].y);
@@ -82,34 +105,296 @@ template <class T> __device__ __forceinline__ cx<T> shfl_dn1(cx<T> a) {
   return mk<T>(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
 }
 
-// (A v) on row m at this lane's nodes from rows m-1, m, m+1 of v; zero for
-// nodes outside the grid.  All lanes must call it (shuffles).
-template <class T>
-__device__ __forceinline__ Row<T> mapply(const Op0<T>& op, const Row<T>& dn, const Row<T>& c, const Row<T>& up,
-                                         int i, int m) {
-  constexpr int NP = MNP<T>::NP;
-  const cx<T> west = shfl_up1<T>(c.v[NP - 1]);
-  const cx<T> east = shfl_dn1<T>(c.v[0]);
-  Row<T> r;
-  const bool rowin = m >= 0 && m <= op.ny;
+// Per-warp march context.  IN: interior path (see the file comment).
+template <class T, bool IN> struct MCtx {
+  static constexpr int NP = MNP<T>::NP;
+  Op0<T> op;
+  Grid g;
+  int i;       // first node of this lane
+  int j0, j1;  // chunk rows [j0, j1)
+  bool outl;   // the lane's nodes are in the strip's output columns
+
+  // (A v) on row m from rows m-1, m, m+1 of v; zero for nodes outside the
+  // grid.  All lanes must call it (shuffles).
+  __device__ __forceinline__ Row<T> apply(const Row<T>& dn, const Row<T>& c, const Row<T>& up, int m) const {
+    const cx<T> west = shfl_up1<T>(c.v[NP - 1]);
+    const cx<T> east = shfl_dn1<T>(c.v[0]);
+    Row<T> r;
 #pragma unroll
-  for (int n = 0; n < NP; ++n) {
-    const int in = i + n;
-    const cx<T> xe = n + 1 < NP ? c.v[n + 1 < NP ? n + 1 : 0] : east;
-    const cx<T> xw = n > 0 ? c.v[n > 0 ? n - 1 : 0] : west;
-    r.v[n] = (rowin && in >= 0 && in <= op.nx) ? op.apply5(c.v[n], xe, xw, up.v[n], dn.v[n], in, m) : zc<T>();
+    for (int n = 0; n < NP; ++n) {
+      const cx<T> xe = n + 1 < NP ? c.v[n + 1 < NP ? n + 1 : 0] : east;
+      const cx<T> xw = n > 0 ? c.v[n > 0 ? n - 1 : 0] : west;
+      const int in = i + n;
+      if (IN) {   // Op0::apply5, interior case
+        const cx<T> xn = up.v[n], xs = dn.v[n], xp = c.v[n];
+        const T k = op.kf ? op.kf[m * (op.nx + 1) + in] : op.c.k;
+        const T sr = (xe.x + xw.x) + (xn.x + xs.x), si = (xe.y + xw.y) + (xn.y + xs.y);
+        const T d = fma(-k, k, T(4) * op.c.inv_h2);
+        r.v[n] = mk<T>(fma(d, xp.x, -op.c.inv_h2 * sr), fma(d, xp.y, -op.c.inv_h2 * si));
+      } else {
+        r.v[n] = (m >= 0 && m <= op.ny && in >= 0 && in <= op.nx)
+                     ? op.apply5(c.v[n], xe, xw, up.v[n], dn.v[n], in, m)
+                     : zc<T>();
+      }
+    }
+    return r;
   }
-  return r;
+  // node n of the lane counts in the dots of row m
+  __device__ __forceinline__ bool cnt(int n, int m) const {
+    return outl && (IN || i + n <= g.nx) && m >= j0 && m < j1;
+  }
+  __device__ __forceinline__ bool own_row(int m) const { return outl && m >= j0 && m < j1; }
+};
+
+// Slot of row t + d at unroll phase S (the march starts at t0 = j0 - 2 with
+// phase 0, so row r sits in slot (r - j0 + 2) mod 4).
+template <int S, int D> struct Sl { static constexpr int v = (S + D + 8) & 3; };
+
+// The NF input fields of a pass: shared-memory staging and register rings.
+template <class T, bool IN, int NF> struct MIn {
+  MCtx<T, IN> c;
+  const cx<T>* src[NF];
+  uint32_t sbase[NF];   // shared address of this lane's slot 0 of each field
+  Row<T> F[NF][4];      // register ring: row r in slot (r - j0 + 2) mod 4
+  int t1;               // last row the march reads
+
+  __device__ __forceinline__ void issue(int r, int slot) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) stage_row<T>(sbase[f] + slot * 32 * 16, src[f], c.g, c.i, r);
+  }
+  // rows t0 .. t0 + MD - 1 in flight
+  __device__ __forceinline__ void prime(int t0) {
+#pragma unroll
+    for (int d = 0; d < MD; ++d) {
+      if (t0 + d <= t1) issue(t0 + d, d);
+      stage_commit();
+    }
+  }
+  // row t + MD in flight, row t into the register ring
+  template <int S> __device__ __forceinline__ void fetch(int t) {
+    if (t + MD <= t1) issue(t + MD, Sl<S, MD>::v);
+    stage_commit();
+    stage_wait();
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      F[f][Sl<S, 0>::v] = stage_read(reinterpret_cast<const typename SlotT<T>::type*>(
+          __cvta_shared_to_generic(sbase[f] + Sl<S, 0>::v * 32 * 16)));
+  }
+};
+
+// Runs p.step<S>(t) for t = t0..t1, S = (t - t0) mod 4.
+template <class P> __device__ __forceinline__ void march(P& p, int t0, int t1) {
+#pragma unroll 1
+  for (int t = t0; t <= t1; t += 4) {
+    p.template step<0>(t);
+    if (t + 1 > t1) break;
+    p.template step<1>(t + 1);
+    if (t + 2 > t1) break;
+    p.template step<2>(t + 2);
+    if (t + 3 > t1) break;
+    p.template step<3>(t + 3);
+  }
 }
 
-// Per-warp geometry inside one right-hand side.
+// M0 at iteration t: x and b rows t arrive; u0 row t-1 = b - A x formed from
+// x rows t-2..t; A u0 on row t-2.
+template <class T, bool IN> struct P0 {
+  static constexpr int NP = MNP<T>::NP;
+  MIn<T, IN, 2> m;   // 0: x, 1: b
+  cx<T>* us;
+  Row<T> U[4];
+  T acc[3];
+  template <int S> __device__ __forceinline__ void step(int t) {
+    m.template fetch<S>(t);
+    const MCtx<T, IN>& c = m.c;
+    if (t < c.j0) return;
+    const Row<T> ax = c.apply(m.F[0][Sl<S, -2>::v], m.F[0][Sl<S, -1>::v], m.F[0][Sl<S, 0>::v], t - 1);
+    Row<T> u;
+#pragma unroll
+    for (int n = 0; n < NP; ++n) u.v[n] = sub<T>(m.F[1][Sl<S, -1>::v].v[n], ax.v[n]);   // both zero outside the grid
+    U[Sl<S, -1>::v] = u;
+    if (c.own_row(t - 1)) mstore(us, c.g, c.i, t - 1, u);
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+      if (c.cnt(n, t - 1)) acc[0] += abs2<T>(u.v[n]);
+    if (t - 2 >= c.j0) {
+      const Row<T> au = c.apply(U[Sl<S, -3>::v], U[Sl<S, -2>::v], U[Sl<S, -1>::v], t - 2);
+#pragma unroll
+      for (int n = 0; n < NP; ++n)
+        if (c.cnt(n, t - 2)) {
+          const cx<T> d = cmul<T>(U[Sl<S, -2>::v].v[n], au.v[n]);
+          acc[1] += d.x;
+          acc[2] += d.y;
+        }
+    }
+  }
+};
+
+// M1 at iteration t: u0 row t arrives; u1 row t-1 formed; A u1 on row t-2.
+template <class T, bool IN> struct P1 {
+  static constexpr int NP = MNP<T>::NP;
+  MIn<T, IN, 1> m;   // 0: u0
+  cx<T>* ws;
+  T s0;
+  cx<T> c0;
+  Row<T> U[4];
+  T acc[7];
+  template <int S> __device__ __forceinline__ void step(int t) {
+    m.template fetch<S>(t);
+    const MCtx<T, IN>& c = m.c;
+    if (t < c.j0) return;
+    const Row<T>(&V)[4] = m.F[0];
+    const Row<T> av = c.apply(V[Sl<S, -2>::v], V[Sl<S, -1>::v], V[Sl<S, 0>::v], t - 1);
+    Row<T> u;
+#pragma unroll
+    for (int n = 0; n < NP; ++n) u.v[n] = sub<T>(scl<T>(s0, av.v[n]), mul<T>(c0, V[Sl<S, -1>::v].v[n]));
+    U[Sl<S, -1>::v] = u;
+    if (c.own_row(t - 1)) mstore(ws, c.g, c.i, t - 1, u);
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+      if (c.cnt(n, t - 1)) {
+        acc[0] += abs2<T>(u.v[n]);
+        const cx<T> d = cmul<T>(u.v[n], V[Sl<S, -1>::v].v[n]);
+        acc[1] += d.x;
+        acc[2] += d.y;
+      }
+    if (t - 2 >= c.j0) {
+      const Row<T> au = c.apply(U[Sl<S, -3>::v], U[Sl<S, -2>::v], U[Sl<S, -1>::v], t - 2);
+#pragma unroll
+      for (int n = 0; n < NP; ++n)
+        if (c.cnt(n, t - 2)) {
+          const cx<T> d0 = cmul<T>(V[Sl<S, -2>::v].v[n], au.v[n]), d1 = cmul<T>(U[Sl<S, -2>::v].v[n], au.v[n]);
+          acc[3] += d0.x;
+          acc[4] += d0.y;
+          acc[5] += d1.x;
+          acc[6] += d1.y;
+        }
+    }
+  }
+};
+
+// M2 at iteration t: u1 and u0 rows t arrive; u2 row t-1 formed; A u2 on
+// row t-2.
+template <class T, bool IN> struct P2 {
+  static constexpr int NP = MNP<T>::NP;
+  MIn<T, IN, 2> m;   // 0: u1, 1: u0
+  cx<T>* ws;
+  T s1;
+  cx<T> c0, c1;
+  Row<T> U[4];
+  T acc[11];
+  template <int S> __device__ __forceinline__ void step(int t) {
+    m.template fetch<S>(t);
+    const MCtx<T, IN>& c = m.c;
+    if (t < c.j0) return;
+    const Row<T>(&V)[4] = m.F[0];
+    const Row<T>(&Z)[4] = m.F[1];
+    const Row<T> av = c.apply(V[Sl<S, -2>::v], V[Sl<S, -1>::v], V[Sl<S, 0>::v], t - 1);
+    Row<T> u;
+#pragma unroll
+    for (int n = 0; n < NP; ++n) {
+      u.v[n] = sub<T>(scl<T>(s1, av.v[n]), mul<T>(c0, Z[Sl<S, -1>::v].v[n]));
+      u.v[n] = sub<T>(u.v[n], mul<T>(c1, V[Sl<S, -1>::v].v[n]));
+    }
+    U[Sl<S, -1>::v] = u;
+    if (c.own_row(t - 1)) mstore(ws, c.g, c.i, t - 1, u);
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+      if (c.cnt(n, t - 1)) {
+        acc[0] += abs2<T>(u.v[n]);
+        const cx<T> d0 = cmul<T>(u.v[n], Z[Sl<S, -1>::v].v[n]), d1 = cmul<T>(u.v[n], V[Sl<S, -1>::v].v[n]);
+        acc[1] += d0.x;
+        acc[2] += d0.y;
+        acc[3] += d1.x;
+        acc[4] += d1.y;
+      }
+    if (t - 2 >= c.j0) {
+      const Row<T> au = c.apply(U[Sl<S, -3>::v], U[Sl<S, -2>::v], U[Sl<S, -1>::v], t - 2);
+#pragma unroll
+      for (int n = 0; n < NP; ++n)
+        if (c.cnt(n, t - 2)) {
+          const cx<T> d0 = cmul<T>(Z[Sl<S, -2>::v].v[n], au.v[n]), d1 = cmul<T>(V[Sl<S, -2>::v].v[n], au.v[n]),
+                      d2 = cmul<T>(U[Sl<S, -2>::v].v[n], au.v[n]);
+          acc[5] += d0.x;
+          acc[6] += d0.y;
+          acc[7] += d1.x;
+          acc[8] += d1.y;
+          acc[9] += d2.x;
+          acc[10] += d2.y;
+        }
+    }
+  }
+};
+
+// M3 at iteration t: u2, u0 and u1 rows t arrive; u3 on row t-1.
+template <class T, bool IN> struct P3 {
+  static constexpr int NP = MNP<T>::NP;
+  MIn<T, IN, 3> m;   // 0: u2, 1: u0, 2: u1
+  T s2;
+  cx<T> cl[3];
+  T acc[1];
+  template <int S> __device__ __forceinline__ void step(int t) {
+    m.template fetch<S>(t);
+    const MCtx<T, IN>& c = m.c;
+    if (t < c.j0 + 1) return;
+    const Row<T>(&V)[4] = m.F[0];
+    const Row<T> av = c.apply(V[Sl<S, -2>::v], V[Sl<S, -1>::v], V[Sl<S, 0>::v], t - 1);
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+      if (c.cnt(n, t - 1)) {
+        cx<T> u = sub<T>(scl<T>(s2, av.v[n]), mul<T>(cl[0], m.F[1][Sl<S, -1>::v].v[n]));
+        u = sub<T>(u, mul<T>(cl[1], m.F[2][Sl<S, -1>::v].v[n]));
+        u = sub<T>(u, mul<T>(cl[2], V[Sl<S, -1>::v].v[n]));
+        acc[0] += abs2<T>(u);
+      }
+  }
+};
+
+// Per-warp geometry inside one right-hand side.  With band = 1 (grids of at
+// least 7 rows) the interior set is strips [s_lo, s_hi) x rows [3, ny-2) in
+// chunks of ch rows; the boundary set is the 3-row bands at the top (rows
+// 0..2) and bottom (rows ny-2..ny) of every strip plus the other strips over
+// rows [3, ny-2) in chunks of chb rows (short, so that the few boundary strips
+// still give many warps).  With band = 0 every warp is a boundary warp, in
+// chunks of chb rows from row 0.
 struct MGeo {
-  int nstrips, ch, nchunks;
+  int nstrips, ny, band, ch, chb;
+  int s_lo, s_hi;   // interior strips
+  int nci;          // interior chunks
+  int nsub;         // chunks of a boundary strip (band: over rows [3, ny-2))
+  int ni, nb;       // warps in the interior and boundary sets
+  // strip and rows [j0, j1) of warp w of the set
+  template <bool IN> __host__ __device__ __forceinline__ void map(int w, int& strip, int& j0, int& j1) const {
+    if (IN) {
+      const int nsi = s_hi - s_lo;
+      strip = s_lo + w % nsi;
+      j0 = 3 + (w / nsi) * ch;
+      j1 = j0 + ch < ny - 2 ? j0 + ch : ny - 2;
+      return;
+    }
+    if (!band) {
+      strip = w % nstrips;
+      j0 = (w / nstrips) * chb;
+      j1 = j0 + chb < ny + 1 ? j0 + chb : ny + 1;
+      return;
+    }
+    if (w < 2 * nstrips) {
+      strip = w % nstrips;
+      j0 = w < nstrips ? 0 : ny - 2;
+      j1 = j0 + 3;
+      return;
+    }
+    const int q = w - 2 * nstrips, nside = nstrips - (s_hi - s_lo);
+    const int sidx = q % nside;
+    strip = sidx < s_lo ? sidx : s_hi + (sidx - s_lo);
+    j0 = 3 + (q / nside) * chb;
+    j1 = j0 + chb < ny - 2 ? j0 + chb : ny - 2;
+  }
 };
 template <class T> __host__ __device__ constexpr int strip_w() { return 32 * MNP<T>::NP - 4; }
 
-// Common prologue.  `has`: the warp owns a (strip, chunk); i: first node of
-// this lane; outl: the lane's nodes are in the strip's output columns.
+// Common prologue (one warp per block).  i: first node of this lane; outl:
+// the lane's nodes are in the strip's output columns.
 #define MPRO                                                                  \
   constexpr int NP = MNP<T>::NP;                                              \
   __shared__ double sh[NVMAX * 32];                                           \
@@ -117,233 +402,138 @@ template <class T> __host__ __device__ constexpr int strip_w() { return 32 * MNP
   if (active && !active[rhs]) return;                                         \
   const long long off = (long long)rhs * g.vstride;                           \
   const int lane = threadIdx.x & 31;                                          \
-  const int gw = blockIdx.x * MW + (threadIdx.x >> 5);                        \
-  const bool has = gw < mg.nstrips * mg.nchunks;                              \
-  const int strip = has ? gw % mg.nstrips : 0, chunk = has ? gw / mg.nstrips : 0; \
-  const int i = strip * strip_w<T>() - 2 + NP * lane;                         \
+  int strip, j0, j1;                                                          \
+  mg.template map<IN>(blockIdx.x, strip, j0, j1);                             \
+  const int cs = strip * strip_w<T>() - 2;                                    \
+  const int i = cs + NP * lane;                                               \
   const bool outl = NP * lane >= 2 && NP * lane + NP <= 32 * NP - 2;          \
-  const int j0 = chunk * mg.ch, j1 = min(j0 + mg.ch, g.ny + 1);               \
-  const int nblk = gridDim.x, blk = blockIdx.x;                               \
-  double* S = st + (long long)rhs * GS;
+  double* S = st + (long long)rhs * GS;                                       \
+  const MCtx<T, IN> ctx{op, g, i, j0, j1, outl};
 
-// node n of the lane counts in the dots of row m
-#define MCOUNT(n, m) (outl && i + (n) <= g.nx && (m) >= j0 && (m) < j1)
+// Runs pass P on the warp's strip and chunk (rows j0-2 .. t1 read) and
+// returns its sums in acc.  stg: the warp's staging area, [NF][4 slots][32
+// lanes] of 16 bytes.
+template <template <class, bool> class P, class T, bool IN, int NV, class Init>
+__device__ __forceinline__ void run_pass(const MCtx<T, IN>& c, int t1, const void* stg, T (&acc)[NV], Init&& init) {
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(stg) + (threadIdx.x & 31) * 16;
+  P<T, IN> p;
+  p.m.c = c;
+  constexpr int NF = sizeof(p.m.src) / sizeof(p.m.src[0]);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) p.m.sbase[f] = s0 + f * 4 * 32 * 16;
+  p.m.t1 = t1;
+  init(p);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) p.acc[k] = T(0);
+  p.m.prime(c.j0 - 2);
+  march(p, c.j0 - 2, t1);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = p.acc[k];
+}
+
+// The interior launch runs first and only publishes its block sums (records
+// 0 .. ni-1); the boundary launch publishes after them, and its last block
+// sums all records and runs the scalar step F.
+template <bool IN, int NV, class T, class F>
+__device__ __forceinline__ void finish(const T (&acc)[NV], double* sh, double* partial, unsigned* tickets, int rhs,
+                                       const MGeo& mg, double* S, F f) {
+  double v[NV];
+  const int nrec = mg.ni + mg.nb;
+  if (IN) {
+    publish<NV, T>(acc, sh, partial, rhs, nrec, blockIdx.x);
+  } else if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, gridDim.x, blockIdx.x, mg.ni, nrec)) {
+    staged<T>(S, v, f);
+  }
+}
 
 // M0: u0 = b - A x; |u0|^2 and <u0, A u0>.
-template <class T>
-__global__ void __launch_bounds__(MW * 32) gm_init(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
-                                                   const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
-                                                   double* partial, unsigned* tickets,
-                                                   const int* __restrict__ active) {
+template <class T, bool IN>
+__global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
+                                              const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
+                                              double* partial, unsigned* tickets, const int* __restrict__ active) {
   MPRO
-  T acc[3] = {T(0), T(0), T(0)};
-  if (has) {
-    const cx<T>* xs = x + off;
-    const cx<T>* bs = b + off;
-    cx<T>* us = u0 + off;
-    // x rows t-2..t, b row t-1 (prefetched one row ahead); u0 rows t-3..t-1
-    Row<T> x0, x1 = mload(xs, g, i, j0 - 2), x2 = mload(xs, g, i, j0 - 1);
-    Row<T> xq = mload(xs, g, i, j0), bq = mload(bs, g, i, j0 - 1);
-    Row<T> a0 = zrow<T>(), a1 = zrow<T>(), a2 = zrow<T>();
-    for (int t = j0; t <= j1 + 1; ++t) {
-      x0 = x1;
-      x1 = x2;
-      x2 = xq;
-      const Row<T> bt = bq;
-      if (t + 1 <= j1 + 1) {
-        xq = mload(xs, g, i, t + 1);
-        bq = mload(bs, g, i, t);
-      }
-      const Row<T> ax = mapply<T>(op, x0, x1, x2, i, t - 1);
-      Row<T> u;
-#pragma unroll
-      for (int n = 0; n < NP; ++n) u.v[n] = sub<T>(bt.v[n], ax.v[n]);   // b and A x are zero outside the grid
-      if (t - 1 >= j0 && t - 1 < j1 && outl) mstore(us, g, i, t - 1, u);
-#pragma unroll
-      for (int n = 0; n < NP; ++n)
-        if (MCOUNT(n, t - 1)) acc[0] += abs2<T>(u.v[n]);
-      a0 = a1;
-      a1 = a2;
-      a2 = u;
-      if (t - 2 >= j0) {
-        const Row<T> au = mapply<T>(op, a0, a1, a2, i, t - 2);
-#pragma unroll
-        for (int n = 0; n < NP; ++n)
-          if (MCOUNT(n, t - 2)) {
-            const cx<T> d = cmul<T>(a1.v[n], au.v[n]);
-            acc[1] += d.x;
-            acc[2] += d.y;
-          }
-      }
+  T acc[3];
+  __shared__ typename SlotT<T>::type stg[2][4][32];
+  run_pass<P0>(ctx, j1 + 1, stg, acc, [&](auto& p) {
+    p.m.src[0] = x + off;
+    p.m.src[1] = b + off;
+    p.us = u0 + off;
+  });
+  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+    fin_init<T>(s, q);
+    if (s[G_BRK] == 0.0) {   // <u0, w> with w = s0 A u0
+      const double d[2] = {q[1] * s[G_S], q[2] * s[G_S]};
+      fin_a<0, T>(s, d);
     }
-  }
-  double v[3];
-  if (reduce_last<3, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
-    staged<T>(S, v, [](double* s, const double* q) {
-      fin_init<T>(s, q);
-      if (s[G_BRK] == 0.0) {   // <u0, w> with w = s0 A u0
-        const double d[2] = {q[1] * s[G_S], q[2] * s[G_S]};
-        fin_a<0, T>(s, d);
-      }
-    });
+  });
 }
 
 // M1: u1 = s0 A u0 - c00 u0; |u1|^2, <u1, u0>, then <u0, A u1>, <u1, A u1>.
-template <class T>
-__global__ void __launch_bounds__(MW * 32) gm_step1(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
-                                                    cx<T>* __restrict__ u1, double* st, double* partial,
-                                                    unsigned* tickets, const int* __restrict__ active) {
+template <class T, bool IN>
+__global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+                                               cx<T>* __restrict__ u1, double* st, double* partial,
+                                               unsigned* tickets, const int* __restrict__ active) {
   MPRO
   if (S[G_BRK] != 0.0) return;   // uniform per RHS
   const T s0 = (T)S[G_S];
   const cx<T> c0 = mk<T>((T)(S[G_H] * S[G_S]), (T)(S[G_H + 1] * S[G_S]));
   T acc[7];
-#pragma unroll
-  for (int k = 0; k < 7; ++k) acc[k] = T(0);
-  if (has) {
-    const cx<T>* vs = u0 + off;
-    cx<T>* ws = u1 + off;
-    Row<T> a0, a1 = mload(vs, g, i, j0 - 2), a2 = mload(vs, g, i, j0 - 1), aq = mload(vs, g, i, j0);
-    Row<T> b0 = zrow<T>(), b1 = zrow<T>(), b2 = zrow<T>();
-    for (int t = j0; t <= j1 + 1; ++t) {
-      a0 = a1;
-      a1 = a2;
-      a2 = aq;
-      if (t + 1 <= j1 + 1) aq = mload(vs, g, i, t + 1);
-      const Row<T> av = mapply<T>(op, a0, a1, a2, i, t - 1);
-      Row<T> u;
-#pragma unroll
-      for (int n = 0; n < NP; ++n) u.v[n] = sub<T>(scl<T>(s0, av.v[n]), mul<T>(c0, a1.v[n]));
-      if (t - 1 < 0 || t - 1 > g.ny) u = zrow<T>();
-      else if (t - 1 >= j0 && t - 1 < j1 && outl) mstore(ws, g, i, t - 1, u);
-#pragma unroll
-      for (int n = 0; n < NP; ++n)
-        if (MCOUNT(n, t - 1)) {
-          acc[0] += abs2<T>(u.v[n]);
-          const cx<T> d = cmul<T>(u.v[n], a1.v[n]);
-          acc[1] += d.x;
-          acc[2] += d.y;
-        }
-      b0 = b1;
-      b1 = b2;
-      b2 = u;
-      if (t - 2 >= j0) {
-        const Row<T> au = mapply<T>(op, b0, b1, b2, i, t - 2);
-#pragma unroll
-        for (int n = 0; n < NP; ++n)
-          if (MCOUNT(n, t - 2)) {
-            const cx<T> d0 = cmul<T>(a0.v[n], au.v[n]), d1 = cmul<T>(b1.v[n], au.v[n]);
-            acc[3] += d0.x;
-            acc[4] += d0.y;
-            acc[5] += d1.x;
-            acc[6] += d1.y;
-          }
-      }
+  __shared__ typename SlotT<T>::type stg[1][4][32];
+  run_pass<P1>(ctx, j1 + 1, stg, acc, [&](auto& p) {
+    p.m.src[0] = u0 + off;
+    p.ws = u1 + off;
+    p.s0 = s0;
+    p.c0 = c0;
+  });
+  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+    fin_b<0, T>(s, q);
+    if (s[G_BRK] == 0.0) {
+      const double s1 = s[G_S + 1];
+      const double d[4] = {q[3] * s1, q[4] * s1, q[5] * s1, q[6] * s1};
+      fin_a<1, T>(s, d);
     }
-  }
-  double v[7];
-  if (reduce_last<7, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
-    staged<T>(S, v, [](double* s, const double* q) {
-      fin_b<0, T>(s, q);
-      if (s[G_BRK] == 0.0) {
-        const double s1 = s[G_S + 1];
-        const double d[4] = {q[3] * s1, q[4] * s1, q[5] * s1, q[6] * s1};
-        fin_a<1, T>(s, d);
-      }
-    });
+  });
 }
 
 // M2: u2 = s1 A u1 - c01 u0 - c11 u1; |u2|^2, <u2, u0>, <u2, u1>, then
 // <u_l, A u2> for l = 0, 1, 2.
-template <class T>
-__global__ void __launch_bounds__(MW * 32) gm_step2(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
-                                                    const cx<T>* __restrict__ u1, cx<T>* __restrict__ u2, double* st,
-                                                    double* partial, unsigned* tickets,
-                                                    const int* __restrict__ active) {
+template <class T, bool IN>
+__global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+                                               const cx<T>* __restrict__ u1, cx<T>* __restrict__ u2, double* st,
+                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
   MPRO
   if (S[G_BRK] != 0.0 || S[G_M] < 1) return;
   const T s1 = (T)S[G_S + 1];
   const cx<T> c0 = mk<T>((T)(S[G_H + 2 * 1] * S[G_S]), (T)(S[G_H + 2 * 1 + 1] * S[G_S]));
   const cx<T> c1 = mk<T>((T)(S[G_H + 2 * 4] * S[G_S + 1]), (T)(S[G_H + 2 * 4 + 1] * S[G_S + 1]));
   T acc[11];
-#pragma unroll
-  for (int k = 0; k < 11; ++k) acc[k] = T(0);
-  if (has) {
-    const cx<T>* zs = u0 + off;
-    const cx<T>* vs = u1 + off;
-    cx<T>* ws = u2 + off;
-    // u1 rows t-2..t, u0 rows t-2..t-1 (+ prefetch), u2 rows t-3..t-1
-    Row<T> a0, a1 = mload(vs, g, i, j0 - 2), a2 = mload(vs, g, i, j0 - 1), aq = mload(vs, g, i, j0);
-    Row<T> z0, z1 = mload(zs, g, i, j0 - 2), zq = mload(zs, g, i, j0 - 1);
-    Row<T> b0 = zrow<T>(), b1 = zrow<T>(), b2 = zrow<T>();
-    for (int t = j0; t <= j1 + 1; ++t) {
-      a0 = a1;
-      a1 = a2;
-      a2 = aq;
-      z0 = z1;
-      z1 = zq;
-      if (t + 1 <= j1 + 1) {
-        aq = mload(vs, g, i, t + 1);
-        zq = mload(zs, g, i, t);
-      }
-      const Row<T> av = mapply<T>(op, a0, a1, a2, i, t - 1);
-      Row<T> u;
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        u.v[n] = sub<T>(scl<T>(s1, av.v[n]), mul<T>(c0, z1.v[n]));
-        u.v[n] = sub<T>(u.v[n], mul<T>(c1, a1.v[n]));
-      }
-      if (t - 1 < 0 || t - 1 > g.ny) u = zrow<T>();
-      else if (t - 1 >= j0 && t - 1 < j1 && outl) mstore(ws, g, i, t - 1, u);
-#pragma unroll
-      for (int n = 0; n < NP; ++n)
-        if (MCOUNT(n, t - 1)) {
-          acc[0] += abs2<T>(u.v[n]);
-          const cx<T> d0 = cmul<T>(u.v[n], z1.v[n]), d1 = cmul<T>(u.v[n], a1.v[n]);
-          acc[1] += d0.x;
-          acc[2] += d0.y;
-          acc[3] += d1.x;
-          acc[4] += d1.y;
-        }
-      b0 = b1;
-      b1 = b2;
-      b2 = u;
-      if (t - 2 >= j0) {
-        const Row<T> au = mapply<T>(op, b0, b1, b2, i, t - 2);
-#pragma unroll
-        for (int n = 0; n < NP; ++n)
-          if (MCOUNT(n, t - 2)) {
-            const cx<T> d0 = cmul<T>(z0.v[n], au.v[n]), d1 = cmul<T>(a0.v[n], au.v[n]),
-                        d2 = cmul<T>(b1.v[n], au.v[n]);
-            acc[5] += d0.x;
-            acc[6] += d0.y;
-            acc[7] += d1.x;
-            acc[8] += d1.y;
-            acc[9] += d2.x;
-            acc[10] += d2.y;
-          }
-      }
+  __shared__ typename SlotT<T>::type stg[2][4][32];
+  run_pass<P2>(ctx, j1 + 1, stg, acc, [&](auto& p) {
+    p.m.src[0] = u1 + off;
+    p.m.src[1] = u0 + off;
+    p.ws = u2 + off;
+    p.s1 = s1;
+    p.c0 = c0;
+    p.c1 = c1;
+  });
+  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+    fin_b<1, T>(s, q);
+    if (s[G_BRK] == 0.0) {
+      const double s2 = s[G_S + 2];
+      const double d[6] = {q[5] * s2, q[6] * s2, q[7] * s2, q[8] * s2, q[9] * s2, q[10] * s2};
+      fin_a<2, T>(s, d);
     }
-  }
-  double v[11];
-  if (reduce_last<11, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
-    staged<T>(S, v, [](double* s, const double* q) {
-      fin_b<1, T>(s, q);
-      if (s[G_BRK] == 0.0) {
-        const double s2 = s[G_S + 2];
-        const double d[6] = {q[5] * s2, q[6] * s2, q[7] * s2, q[8] * s2, q[9] * s2, q[10] * s2};
-        fin_a<2, T>(s, d);
-      }
-    });
+  });
 }
 
 // M3: |u3|^2 with u3 = s2 A u2 - sum_l c_l2 u_l; then the least-squares
 // solve (fin_b<2>).
-template <class T>
-__global__ void __launch_bounds__(MW * 32) gm_step3(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
-                                                    const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
-                                                    double* st, double* partial, unsigned* tickets,
-                                                    const int* __restrict__ active) {
+template <class T, bool IN>
+__global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+                                               const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
+                                               double* st, double* partial, unsigned* tickets,
+                                               const int* __restrict__ active) {
   MPRO
   if (S[G_BRK] != 0.0 || S[G_M] < 2) return;
   const T s2 = (T)S[G_S + 2];
@@ -351,50 +541,53 @@ __global__ void __launch_bounds__(MW * 32) gm_step3(Grid g, MGeo mg, Op0<T> op, 
 #pragma unroll
   for (int l = 0; l < 3; ++l)
     cl[l] = mk<T>((T)(S[G_H + 2 * (l * 3 + 2)] * S[G_S + l]), (T)(S[G_H + 2 * (l * 3 + 2) + 1] * S[G_S + l]));
-  T acc[1] = {T(0)};
-  if (has) {
-    const cx<T>* zs = u0 + off;
-    const cx<T>* ys = u1 + off;
-    const cx<T>* vs = u2 + off;
-    // u2 rows t-2..t; u0, u1 row t-1 (all prefetched one row ahead)
-    Row<T> a0, a1 = mload(vs, g, i, j0 - 1), a2 = mload(vs, g, i, j0), aq = mload(vs, g, i, j0 + 1);
-    Row<T> zq = mload(zs, g, i, j0), yq = mload(ys, g, i, j0);
-    for (int t = j0 + 1; t <= j1; ++t) {
-      a0 = a1;
-      a1 = a2;
-      a2 = aq;
-      const Row<T> z = zq, y = yq;
-      if (t + 1 <= j1) {
-        aq = mload(vs, g, i, t + 1);
-        zq = mload(zs, g, i, t);
-        yq = mload(ys, g, i, t);
-      }
-      const Row<T> av = mapply<T>(op, a0, a1, a2, i, t - 1);
-#pragma unroll
-      for (int n = 0; n < NP; ++n)
-        if (MCOUNT(n, t - 1)) {
-          cx<T> u = sub<T>(scl<T>(s2, av.v[n]), mul<T>(cl[0], z.v[n]));
-          u = sub<T>(u, mul<T>(cl[1], y.v[n]));
-          u = sub<T>(u, mul<T>(cl[2], a1.v[n]));
-          acc[0] += abs2<T>(u);
-        }
-    }
-  }
-  double v[1];
-  if (reduce_last<1, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
-    staged<T>(S, v, [](double* s, const double* q) { fin_b<2, T>(s, q); });
+  T acc[1];
+  __shared__ typename SlotT<T>::type stg[3][4][32];
+  run_pass<P3>(ctx, j1, stg, acc, [&](auto& p) {
+    p.m.src[0] = u2 + off;
+    p.m.src[1] = u0 + off;
+    p.m.src[2] = u1 + off;
+    p.s2 = s2;
+    p.cl[0] = cl[0];
+    p.cl[1] = cl[1];
+    p.cl[2] = cl[2];
+  });
+  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) { fin_b<2, T>(s, q); });
 }
 
-// Rows per warp: tall chunks (few halo rows) unless the grid has too few
-// strips to give every SM several warps.
+// Interior chunks are tall (few halo rows) unless the grid has too few
+// strips to give every SM several warps.  Interior strips: loaded columns in
+// 1..nx-1.
 template <class T> MGeo march_geo(const Grid& g, int B) {
+  constexpr int NP = MNP<T>::NP, SW = strip_w<T>();
   MGeo m;
-  m.nstrips = cdiv(g.nx + 1, strip_w<T>());
+  m.nstrips = cdiv(g.nx + 1, SW);
+  m.ny = g.ny;
+  m.band = g.ny >= 6;
+  m.chb = 16;
+  m.s_lo = m.s_hi = 0;
+  for (int s = 0; s < m.nstrips; ++s) {
+    const int cs = s * SW - 2;
+    if (cs >= 1 && cs + 32 * NP - 1 <= g.nx - 1) {
+      if (m.s_hi == 0) m.s_lo = s;
+      m.s_hi = s + 1;
+    }
+  }
+  if (!m.band) m.s_lo = m.s_hi = 0;
+  const int nsi = m.s_hi - m.s_lo, inner_rows = g.ny - 5;
   const long long want = 152LL * 48;   // warps to fill the GPU a few times over
   int ch = 64;
-  while (ch > 8 && (long long)m.nstrips * cdiv(g.ny + 1, ch) * B < want) ch /= 2;
+  while (ch > 8 && (long long)nsi * cdiv(inner_rows, ch) * B < want) ch /= 2;
   m.ch = ch;
-  m.nchunks = cdiv(g.ny + 1, ch);
+  m.nci = nsi > 0 ? cdiv(inner_rows, ch) : 0;
+  m.ni = nsi * m.nci;
+  if (m.band) {
+    m.nsub = cdiv(inner_rows, m.chb);
+    m.nb = 2 * m.nstrips + (m.nstrips - nsi) * m.nsub;
+  } else {
+    m.nsub = cdiv(g.ny + 1, m.chb);
+    m.nb = m.nstrips * m.nsub;
+  }
   return m;
 }
 
@@ -406,7 +599,7 @@ template <class T> void launch_gmres_update(const Grid& g, cx<T>* x, const Gmres
 
 long long gmres_march_blocks(const Grid& g, bool fp64, int B) {
   const MGeo m = fp64 ? march_geo<double>(g, B) : march_geo<float>(g, B);
-  return cdiv((long long)m.nstrips * m.nchunks, MW);
+  return (long long)m.ni + m.nb;
 }
 
 template <class T>
@@ -420,12 +613,16 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
   double* st = gb.st;
   const Op0<T> op{opv.c0, opv.kf, g.nx, g.ny};
   const MGeo mg = march_geo<T>(g, B);
-  const dim3 grd(cdiv((long long)mg.nstrips * mg.nchunks, MW), 1, B);
+  const dim3 gi(mg.ni, 1, B), gbd(mg.nb, 1, B);
   for (int step = 0; step < nu; ++step) {
-    gm_init<T><<<grd, MW * 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active);
-    gm_step1<T><<<grd, MW * 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active);
-    gm_step2<T><<<grd, MW * 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
-    gm_step3<T><<<grd, MW * 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
+    if (mg.ni) gm_init<T, true><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active);
+    gm_init<T, false><<<gbd, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active);
+    if (mg.ni) gm_step1<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active);
+    gm_step1<T, false><<<gbd, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active);
+    if (mg.ni) gm_step2<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
+    gm_step2<T, false><<<gbd, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
+    if (mg.ni) gm_step3<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
+    gm_step3<T, false><<<gbd, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
     launch_gmres_update<T>(g, x, gb, B, active, s);
   }
 }

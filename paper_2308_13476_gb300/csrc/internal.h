@@ -60,14 +60,31 @@ struct Ctl {
   double* partial;
   unsigned* tickets;
 };
+// Stopping test for one right-hand side, run by the last block of a norm
+// reduction: relres = sqrt(sumsq) / ||b||; count != 0 means a cycle has just
+// finished.  A RHS that meets tol (state 1) or diverges (state 2: not finite
+// or above the threshold) is deactivated.
+__device__ __forceinline__ void stop_update(const Ctl& c, int rhs, double sumsq, int count) {
+  const double tol = c.tolp[0], diverge = c.tolp[1];
+  const double rr = sqrt(sumsq) / c.bnorm[rhs];
+  c.relres[rhs] = rr;
+  if (count) {
+    const int cy = ++c.cycles[rhs];
+    if (cy <= c.hist_len) c.hist[(long long)rhs * c.hist_len + cy - 1] = rr;
+  }
+  int st = 0;
+  if (!(rr == rr) || rr > diverge) st = 2;
+  else if (rr <= tol) st = 1;
+  if (st) {
+    c.state[rhs] = st;
+    c.active[rhs] = 0;
+    atomicSub(c.n_active, 1);
+  }
+}
+
 // ||b - A x|| per RHS with the stopping test fused (count != 0: a cycle just finished).
 template <class T> void launch_resnorm_stop(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
                                             int B, const Ctl& c, int count, cudaStream_t s);
-// Mixed path: r = b - A x in FP64, written as float into r32 (same Grid), stopping test fused.
-void launch_resid_cast_stop(const Grid& g, const OpView<double>& op, const double2* x, const double2* b,
-                            float2* r32, int B, const Ctl& c, int count, cudaStream_t s);
-// x += e (FP64 += float, same Grid), masked.
-void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s);
 // out[b] = ||v_b|| (one kernel).
 template <class T> void launch_vecnorm_fin(const Grid& g, const cx<T>* v, int B, double* out, double* partial,
                                            unsigned* tickets, cudaStream_t s);
@@ -188,6 +205,29 @@ template <class T> void launch_jacobi_fused(const Grid& g, const OpView<T>& op, 
                                             cx<T>* xo, int nu, int B, const int* active, cudaStream_t s);
 int jacobi_fused_max_nu();
 cudaError_t configure_fused_kernels();
+
+// Outer iterate of the mixed path in float-float arithmetic (mixed_ff.cu):
+// level-0 vectors hold each node as the float4 {re.hi, im.hi, re.lo, im.lo}
+// in the space of a complex128 vector.
+struct FF {
+  float h, l;
+};
+struct FFConsts {
+  FF d, ih2, sb;   // 4/h^2 - k^2, 1/h^2, k/h (constant k)
+};
+// Constants, and for variable k the per-node diagonal w (4/h^2 - k^2) into dP.
+void launch_ff_setup(double h, double k, const double* kf, int nx, int ny, FFConsts* consts, float2* dP,
+                     cudaStream_t s);
+// r = b - A x in float-float, written as float into r32, stopping test fused.
+void launch_ff_resid_cast_stop(const Grid& g, const FFConsts& K, const double* kf, double h, const float2* dP,
+                               const void* x, const void* b, float2* r32, int B, const Ctl& c, int count,
+                               cudaStream_t s);
+// x += e (float-float += float), masked.
+void launch_ff_update(const Grid& g, void* x, const float2* e, int B, const int* active, cudaStream_t s);
+void launch_ff_pack(const Grid& g, const double2* user, void* v, int B, int conj, cudaStream_t s);
+void launch_ff_unpack(const Grid& g, const void* v, double2* user, int B, int conj, cudaStream_t s);
+void launch_ff_norm(const Grid& g, const void* v, int B, double* out, double* partial, unsigned* tickets,
+                    cudaStream_t s);
 
 // Gradient of the receiver misfit (kernels_level.cu).
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u,

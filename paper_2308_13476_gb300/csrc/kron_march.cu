@@ -31,7 +31,8 @@ struct KGeo {
 
 // A v down column i: sums() forms the two row sums of one input row,
 // shift_in() appends them to the ring of the last 2R+1 rows, and combine()
-// returns (A v)(i, m) once the ring holds rows m-R..m+R.
+// returns (A v)(i, m) once the ring holds rows m-R..m+R.  The next input row
+// is fetched one iteration ahead (prime / advance).
 template <class T, int R> struct KRing {
   static constexpr int K = 2 * R + 1;
   cx<T> G[K];
@@ -47,16 +48,44 @@ template <class T, int R> struct KRing {
       s2[k] = mk<T>(T(0), T(0));
     }
   }
-  // row sums of row `row` of v (slice pointer vs, node offset p of (i, row))
-  __device__ __forceinline__ void sums(const cx<T>* __restrict__ vs, int p, cx<T>& a, cx<T>& c) const {
+  // the 2R+1 values of one input row around column i (slice pointer vs,
+  // node offset p of (i, row))
+  __device__ __forceinline__ static void fetch(const cx<T>* __restrict__ vs, int p, cx<T> (&xv)[K]) {
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) xv[dx + R] = __ldg(vs + p + dx);
+  }
+  // row sums of one input row
+  __device__ __forceinline__ void sums(const cx<T> (&xv)[K], cx<T>& a, cx<T>& c) const {
     a = mk<T>(T(0), T(0));
     c = mk<T>(T(0), T(0));
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
-      const cx<T> xv = __ldg(vs + p + dx);
-      a = fma_c<T>(G[dx + R], xv, a);
-      c = mk<T>(fma(Wx[dx + R], xv.x, c.x), fma(Wx[dx + R], xv.y, c.y));
+      a = fma_c<T>(G[dx + R], xv[dx + R], a);
+      c = mk<T>(fma(Wx[dx + R], xv[dx + R].x, c.x), fma(Wx[dx + R], xv[dx + R].y, c.y));
     }
+  }
+  // march prologue: rows j0-R .. j0+R-1 into the ring, row j0+R fetched into nx
+  __device__ __forceinline__ void prime(const cx<T>* __restrict__ vs, const Grid& g, int i, int j0, cx<T> (&nx)[K]) {
+    cx<T> a, c;
+#pragma unroll 1
+    for (int r = j0 - R; r < j0 + R; ++r) {
+      fetch(vs, g.at(i, r), nx);
+      sums(nx, a, c);
+      shift_in(a, c);
+    }
+    fetch(vs, g.at(i, j0 + R), nx);
+  }
+  // ring advance for output row m: uses the fetched row m+R, fetches row
+  // m+R+1 (the next iteration's) before the arithmetic
+  __device__ __forceinline__ void advance(const cx<T>* __restrict__ vs, const Grid& g, int i, int m, int j1,
+                                          cx<T> (&nx)[K]) {
+    cx<T> cur[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) cur[k] = nx[k];
+    if (m + 1 < j1) fetch(vs, g.at(i, m + R + 1), nx);
+    cx<T> a, c;
+    sums(cur, a, c);
+    shift_in(a, c);
   }
   __device__ __forceinline__ void shift_in(cx<T> a, cx<T> c) {
 #pragma unroll
@@ -106,16 +135,11 @@ __global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op
     const cx<T>* xs = x + off;
     KRing<T, R> ring;
     ring.init(op, i);
-    cx<T> p1, p2;
-#pragma unroll 1
-    for (int r = j0 - R; r < j0 + R; ++r) {
-      ring.sums(xs, g.at(i, r), p1, p2);
-      ring.shift_in(p1, p2);
-    }
+    cx<T> nx[KRing<T, R>::K];
+    ring.prime(xs, g, i, j0, nx);
 #pragma unroll 1
     for (int m = j0; m < j1; ++m) {
-      ring.sums(xs, g.at(i, m + R), p1, p2);
-      ring.shift_in(p1, p2);
+      ring.advance(xs, g, i, m, j1, nx);
       const int p = g.at(i, m);
       const cx<T> r = sub<T>(b[off + p], ring.combine(op, m));
       u0[off + p] = r;
@@ -145,16 +169,11 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
     const cx<T>* vs = uJ + off;
     KRing<T, R> ring;
     ring.init(op, i);
-    cx<T> p1, p2;
-#pragma unroll 1
-    for (int r = j0 - R; r < j0 + R; ++r) {
-      ring.sums(vs, g.at(i, r), p1, p2);
-      ring.shift_in(p1, p2);
-    }
+    cx<T> nx[KRing<T, R>::K];
+    ring.prime(vs, g, i, j0, nx);
 #pragma unroll 1
     for (int m = j0; m < j1; ++m) {
-      ring.sums(vs, g.at(i, m + R), p1, p2);
-      ring.shift_in(p1, p2);
+      ring.advance(vs, g, i, m, j1, nx);
       const int p = g.at(i, m);
       const cx<T> a = scl<T>(sJ, ring.combine(op, m));
       w[off + p] = a;
