@@ -183,12 +183,15 @@ mg_status mg_history(mg_handle h, double* hist, int cap);
 
 /* Time one kernel of the hierarchy in the handle's precision: `what` = 0 one
  * weighted-Jacobi sweep, 1 a residual b - A x, 2 a restriction, 3 a
- * prolongation-and-correct, on level `level` for all B right-hand sides.
- * The kernel runs `reps` times back to back between two CUDA events on the
- * handle's stream (after one untimed launch); *ms gets the mean time of one
- * launch and *bytes the algorithmic DRAM bytes of one launch (each input
- * array read once, each output written once).  It overwrites the handle's
- * internal work vectors, never caller memory. */
+ * prolongation-and-correct, 4 one GMRES(3) smoothing step (Sec. 5.3; the
+ * kernels the cycle runs for that level: on level 0 with fuse = 1 four
+ * row-march passes and the update, 16 vector reads and writes per node;
+ * otherwise eight node-parallel passes, 28; needs smoother = 1), on level
+ * `level` for all B right-hand sides.  The work runs `reps` times back to
+ * back between two CUDA events on the handle's stream (after one untimed
+ * run); *ms gets the mean time of one run and *bytes its algorithmic DRAM
+ * bytes (each input array read once, each output written once).  It
+ * overwrites the handle's internal work vectors, never caller memory. */
 mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes);
 
 /* Kernel launches issued by the last mg_solve / mg_adjoint (graph kernel

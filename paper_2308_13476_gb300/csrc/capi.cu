@@ -217,6 +217,19 @@ template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, c
 
 // ----------------------------------------------------------------- cycle emission
 
+// nu GMRES(3) smoothing steps on level l: the fine level as row marches, the
+// Kronecker-form levels with column-march operator kernels (both with
+// fuse = 1), stored stencils (or fuse = 0) with the node-parallel kernels.
+template <class T>
+static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, const int* active, cudaStream_t s) {
+  const Grid& g = c->lev[l].g;
+  const OpView<T> op = opT<T>(c, l);
+  const GmresBufs& gb = vecs<T>(c)[l].gb;
+  if (c->opt.fuse && op.kind == 1) gmres_smooth_march<T>(g, op, x, b, nu, c->B, active, gb, s);
+  else if (c->opt.fuse && op.kind >= 4) gmres_smooth_kron<T>(g, op, x, b, nu, c->B, active, gb, s);
+  else gmres_smooth<T>(g, op, x, b, nu, c->B, active, gb, s);
+}
+
 template <class T> struct Emit {
   mg_ctx* c;
   cudaStream_t s;
@@ -240,12 +253,8 @@ template <class T> struct Emit {
         launch_jacobi<T>(g, op, cur[l], V.b, oth[l], c->B, c->active, s);
         std::swap(cur[l], oth[l]);
       }
-    } else if (c->opt.fuse && op.kind == 1) {
-      gmres_smooth_march<T>(g, op, cur[l], V.b, nu, c->B, c->active, V.gb, s);
-    } else if (c->opt.fuse && op.kind >= 4) {
-      gmres_smooth_kron<T>(g, op, cur[l], V.b, nu, c->B, c->active, V.gb, s);
     } else {
-      gmres_smooth<T>(g, op, cur[l], V.b, nu, c->B, c->active, V.gb, s);
+      gmres_level<T>(c, l, cur[l], V.b, nu, c->active, s);
     }
   }
 
@@ -408,7 +417,9 @@ static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
 template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, int reps, double* ms, double* bytes) {
   cudaStream_t s = (cudaStream_t)h->opt.stream;
   auto& V = vecs<T>(h);
-  if (level < 0 || level >= (int)V.size() || (what >= 2 && level + 1 >= h->nlev)) FAIL(MG_EINVAL, "bad level");
+  if (level < 0 || level >= (int)V.size() || ((what == 2 || what == 3) && level + 1 >= h->nlev))
+    FAIL(MG_EINVAL, "bad level");
+  if (what == 4 && h->opt.smoother != 1) FAIL(MG_EINVAL, "what = 4 needs the GMRES(3) smoother");
   const Grid& g = h->lev[level].g;
   const OpView<T> op = opT<T>(h, level);
   const double nodes = (double)(g.nx + 1) * (g.ny + 1) * h->B;
@@ -427,12 +438,20 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
       case 0: launch_jacobi<T>(g, op, V[level].x, V[level].b, V[level].t, h->B, nullptr, s); break;
       case 1: launch_residual<T>(g, op, V[level].x, V[level].b, V[level].r, h->B, nullptr, s); break;
       case 2: launch_restrict<T>(g, h->lev[level + 1].g, V[level].r, V[level + 1].b, h->B, nullptr, s); break;
-      default: launch_prolong_add<T>(g, h->lev[level + 1].g, V[level + 1].x, V[level].x, h->B, nullptr, s); break;
+      case 3: launch_prolong_add<T>(g, h->lev[level + 1].g, V[level + 1].x, V[level].x, h->B, nullptr, s); break;
+      default: gmres_level<T>(h, level, V[level].x, V[level].b, 1, nullptr, s); break;
     }
   };
   if (what == 0 || what == 1) *bytes = nodes * (3 * e + opbytes);
   else if (what == 2) *bytes = nodes * e * 1.25;     // read fine r, write coarse r
-  else *bytes = nodes * e * 2.25;                     // read+write fine x, read coarse e
+  else if (what == 3) *bytes = nodes * e * 2.25;     // read+write fine x, read coarse e
+  else {   // GMRES(3) step: four passes that read the operator, plus vectors
+    double gop = 0;   // operator bytes per node and RHS read by one pass
+    if (level == 0) gop = op.kf ? sizeof(T) / (double)h->B : 0.0;
+    else if (h->lev[level].kind <= 3) gop = opbytes - e / h->B;   // stencil without the inverse diagonal
+    const int vec = (h->opt.fuse && h->lev[level].kind == 1) ? 16 : 28;   // row marches + update, or 8 passes
+    *bytes = nodes * (vec * e + 4 * gop);
+  }
   launch();
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
@@ -1020,7 +1039,7 @@ mg_status mg_counters(mg_handle h, long long* kernel_launches, long long* graph_
 mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes) {
   if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
-  if (what < 0 || what > 3 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
+  if (what < 0 || what > 4 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
   if (h->opt.precision == 1) return profile_t<float>(h, what, level, reps, ms, bytes);
   return profile_t<double>(h, what, level, reps, ms, bytes);
 }
