@@ -45,10 +45,11 @@ def parse():
     p.add_argument("--cycle", default="V", choices=["V", "W"])
     p.add_argument("--nu", type=int, default=2, help="pre = post smoothing steps")
     p.add_argument("--beta2", type=float, default=-1.0, help="complex shift (default 1/k for GMRES, 0.7 Jacobi)")
-    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed-ff"])
     p.add_argument("--batch", type=int, default=64)
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-fp64-line", action="store_true", help="skip the FP64 comparison solve")
+    p.add_argument("--no-ff-line", action="store_true", help="skip the float-float outer-loop variant")
     p.add_argument("--cpu-sample-cycles", type=int, default=2)
     p.add_argument("--probe", action="store_true",
                    help="profiling probe: set up the workload and run two solves capped at --max-cycles; no timing")
@@ -313,11 +314,19 @@ def run_ours(a):
             "traffic": step_traffic(a, what),
             "kernel": ("level-0 weighted-Jacobi sweep" if what == 0 else
                        "level-0 GMRES(3) smoothing step: 4 row-march passes + update, 16 vector passes") +
-                      f" ({'complex64' if a.precision == 'mixed' else 'complex128'}), "
+                      f" ({'complex128' if a.precision == 'fp64' else 'complex64'}), "
                       f"{kbytes / 1e6:.1f} MB algorithmic per step, {kms * 1e3:.0f} us per step, "
                       f"peak = measured hbm_gbs"}
     extra = {"setup_s": setup_s, "cycles": cyc, "relres": rr}
-    if not a.no_fp64_line and a.precision == "mixed":
+    if not a.no_ff_line and a.precision == "mixed":   # the float-float outer loop, same launch shapes
+        s.close()
+        sff, _ = make("mixed-ff", tuned)
+        timed_solves(sff, 1)
+        msff, cycff, _, rrff = timed_solves(sff, a.steps)
+        extra["mixed_ff_path"] = {"value": N * a.batch * a.steps / (sum(msff) / 1e3), "unit": UNIT,
+                                  "cycles": cycff, "max_relres": max(rrff), "ms_per_solve": sum(msff) / a.steps}
+        s = sff
+    if not a.no_fp64_line and a.precision in ("mixed", "mixed-ff"):
         s.close()
         s64, setup64 = make("fp64")
         ms64, cyc64, _, _ = timed_solves(s64, 1)   # one solve (its first cycle includes the graph capture)
@@ -329,7 +338,7 @@ def run_ours(a):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": tmax * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64+ff" if a.precision == "mixed" else "c128", "data": "synthetic",
+        "dtype": {"mixed": "c64+f64", "mixed-ff": "c64+ff"}.get(a.precision, "c128"), "data": "synthetic",
         "config": dict(workload_config(a), launch_shapes=tuned or "library defaults"), "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rhs.numel() * 16),
@@ -357,7 +366,7 @@ def step_traffic(a, what):
     is the captured one and the hashed kernel sources are unchanged."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic_gmres_step_level0.json")
-    if what != 4 or a.n != 1024 or a.precision != "mixed" or not os.path.exists(path):
+    if what != 4 or a.n != 1024 or a.precision == "fp64" or not os.path.exists(path):
         return None
     rec = json.load(open(path))
     h = hashlib.sha256()

@@ -74,8 +74,10 @@ typedef struct {
   double omega;     /* Jacobi: X = omega * diag(A); the paper uses 4.5          */
   int precision;    /* 0 = complex128 throughout; 1 = complex64 cycles inside a
                        complex128 iterative-refinement loop (outer residual,
-                       update, setup and coarsest solve in FP64)               */
-  int max_cycles;   /* cap on cycles (refinement steps for precision 1)       */
+                       update, setup and coarsest solve in FP64); 2 = the same
+                       with the outer x, b, residual and update held as
+                       float-float pairs (48-bit significand, FP32 pipes)      */
+  int max_cycles;   /* cap on cycles (refinement steps for precision 1, 2)    */
   int min_coarse;   /* stop coarsening below this many grid nodes (Sec. 5: 10) */
   int batch;        /* B: right-hand sides solved together                      */
   int coarse_nodes; /* levels with at most this many grid nodes (and all below

@@ -244,7 +244,7 @@ def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, preci
             setattr(o, name, int(val))
     o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
     return o
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed-ff": 2}
 
 
 class RaggedSolver:
@@ -288,7 +288,7 @@ class Solver:
     """One multigrid hierarchy on the current CUDA device.
 
     Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
-           nu_pre, nu_post, omega, precision="fp64"|"mixed", batch, levels,
+           nu_pre, nu_post, omega, precision="fp64"|"mixed"|"mixed-ff", batch, levels,
            max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, stream)
     ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
     """

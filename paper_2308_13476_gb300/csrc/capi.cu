@@ -401,17 +401,22 @@ static void emit_fp64_iteration(mg_ctx* c, cudaStream_t s) {
 }
 
 // One refinement step of the mixed path: e = 0, one complex64 cycle on the
-// float residual, x += e in float-float, the new float-float residual (cast
-// to float) and the stopping test.
+// float residual, x += e and the new outer residual (cast to float) with the
+// stopping test -- in FP64 (precision 1) or float-float (precision 2).
 static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
   Emit<float> e{c, s, {}, {}, c->lc, &c->plan32};
   e.init();
   const Grid& g0 = c->lev[0].g;
   cudaMemsetAsync(c->v32[0].x, 0, sizeof(float2) * (size_t)g0.vstride * c->B, s);
   e.cycle(0);
-  launch_ff_update(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
-  launch_ff_resid_cast_stop(g0, c->hffc, c->kf64, c->h, c->ffdiag, c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B,
-                            ctl(c), 1, s);
+  if (c->opt.precision == 2) {
+    launch_ff_update(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
+    launch_ff_resid_cast_stop(g0, c->hffc, c->kf64, c->h, c->ffdiag, c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B,
+                              ctl(c), 1, s);
+  } else {
+    launch_update_mixed(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
+    launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B, ctl(c), 1, s);
+  }
 }
 
 template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, int reps, double* ms, double* bytes) {
@@ -518,7 +523,8 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     c->lev[l].radius = l == 0 ? 1 : (l == 1 ? 2 : 3);
     c->lev[l].plane = (long long)(sizes[l].first + 1) * (sizes[l].second + 1);
   }
-  const bool mixed = o.precision == 1;
+  const bool mixed = o.precision >= 1;
+  const bool ffo = o.precision == 2;   // float-float outer loop
   const bool gm = o.smoother == 1;
   const Grid& g0 = c->lev[0].g;
   CK(configure_fused_kernels());
@@ -535,8 +541,8 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   }
   launch_op0consts(c->c0d, c->c0f, c->h, c->kconst, o.omega, c->beta2, s);
   CK(cudaMemcpyAsync(&c->hc0d, c->c0d, sizeof(Op0Consts<double>), cudaMemcpyDeviceToHost, s));
-  if (mixed) {
-    CK(cudaMemcpyAsync(&c->hc0f, c->c0f, sizeof(Op0Consts<float>), cudaMemcpyDeviceToHost, s));
+  if (mixed) CK(cudaMemcpyAsync(&c->hc0f, c->c0f, sizeof(Op0Consts<float>), cudaMemcpyDeviceToHost, s));
+  if (ffo) {
     CK(dalloc(c, (void**)&c->ffc, sizeof(FFConsts)));
     if (k_field) CK(dalloc(c, (void**)&c->ffdiag, sizeof(float2) * N0));
     launch_ff_setup(c->h, c->kconst, c->kf64, g0.nx, g0.ny, c->ffc, c->ffdiag, s);
@@ -712,7 +718,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.smoother != 0 && o.smoother != 1) FAIL(MG_EINVAL, "smoother must be 0 (Jacobi) or 1 (GMRES(3))");
   if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post > 64) FAIL(MG_EINVAL, "bad nu_pre / nu_post");
   if (!(o.omega > 0)) FAIL(MG_EINVAL, "omega must be > 0");
-  if (o.precision != 0 && o.precision != 1) FAIL(MG_EINVAL, "precision must be 0 or 1");
+  if (o.precision < 0 || o.precision > 2) FAIL(MG_EINVAL, "precision must be 0, 1 or 2");
   if (o.max_cycles < 1 || o.min_coarse < 1) FAIL(MG_EINVAL, "max_cycles and min_coarse must be >= 1");
   if (o.batch < 1 || o.batch > 65535) FAIL(MG_EINVAL, "batch must be in 1..65535");
   if (o.coarse_nodes < 0) FAIL(MG_EINVAL, "coarse_nodes must be >= 0");
@@ -810,10 +816,10 @@ static mg_status solve_begin(mg_ctx* c, const void* rhs, void* x, double tol, in
   cudaStream_t s = (cudaStream_t)c->opt.stream;
   const Grid& g0 = c->lev[0].g;
   const int B = c->B;
-  const bool mixed = c->opt.precision == 1;
+  const bool mixed = c->opt.precision >= 1, ffo = c->opt.precision == 2;
   mg_status st = capture(c);
   if (st != MG_OK) return st;
-  if (mixed) {   // level-0 outer vectors in float-float
+  if (ffo) {   // level-0 outer vectors in float-float
     launch_ff_pack(g0, (const double2*)rhs, c->v64[0].b, B, conj, s);
     launch_ff_pack(g0, (const double2*)x, c->v64[0].x, B, conj, s);
     launch_ff_norm(g0, c->v64[0].b, B, c->bnorm, c->partial, c->tickets, s);
@@ -846,9 +852,11 @@ static mg_status solve_begin(mg_ctx* c, const void* rhs, void* x, double tol, in
   if (c->coop.bar) CK(cudaMemsetAsync(c->coop.bar, 0, sizeof(unsigned) * 2, s));
   CK(cudaMemsetAsync(c->relres, 0, sizeof(double) * B, s));
   CK(cudaMemsetAsync(c->hist, 0, sizeof(double) * (size_t)c->hist_len * B, s));
-  if (mixed)   // initial test on x0
+  if (ffo)   // initial test on x0
     launch_ff_resid_cast_stop(g0, c->hffc, c->kf64, c->h, c->ffdiag, c->v64[0].x, c->v64[0].b, c->v32[0].b, B,
                               ctl(c), 0, s);
+  else if (mixed)
+    launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, B, ctl(c), 0, s);
   else
     launch_resnorm_stop<double>(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, B, ctl(c), 0, s);
   CK(cudaGetLastError());
@@ -877,7 +885,7 @@ static mg_status solve_end(mg_ctx* c, void* x, int conj, int* cycles_out, double
   cudaStream_t s = (cudaStream_t)c->opt.stream;
   const Grid& g0 = c->lev[0].g;
   const int B = c->B;
-  if (c->opt.precision == 1)
+  if (c->opt.precision == 2)
     launch_ff_unpack(g0, c->v64[0].x, (double2*)x, B, conj, s);
   else
     launch_unpack<double>(g0, c->v64[0].x, (double2*)x, B, conj, s);
@@ -1040,7 +1048,7 @@ mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, dou
   if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (what < 0 || what > 4 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
-  if (h->opt.precision == 1) return profile_t<float>(h, what, level, reps, ms, bytes);
+  if (h->opt.precision >= 1) return profile_t<float>(h, what, level, reps, ms, bytes);
   return profile_t<double>(h, what, level, reps, ms, bytes);
 }
 

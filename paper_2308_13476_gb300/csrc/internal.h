@@ -85,6 +85,11 @@ __device__ __forceinline__ void stop_update(const Ctl& c, int rhs, double sumsq,
 // ||b - A x|| per RHS with the stopping test fused (count != 0: a cycle just finished).
 template <class T> void launch_resnorm_stop(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
                                             int B, const Ctl& c, int count, cudaStream_t s);
+// Mixed path, FP64 outer loop: r = b - A x in FP64, written as float into r32
+// (same Grid), stopping test fused; and x += e (FP64 += float), masked.
+void launch_resid_cast_stop(const Grid& g, const OpView<double>& op, const double2* x, const double2* b,
+                            float2* r32, int B, const Ctl& c, int count, cudaStream_t s);
+void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s);
 // out[b] = ||v_b|| (one kernel).
 template <class T> void launch_vecnorm_fin(const Grid& g, const cx<T>* v, int B, double* out, double* partial,
                                            unsigned* tickets, cudaStream_t s);

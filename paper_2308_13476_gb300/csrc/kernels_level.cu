@@ -118,6 +118,46 @@ __global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const c
     stop_update(c, rhs, v[0], count);
 }
 
+// FP64 residual of the refinement loop, written in float for the next
+// complex64 correction cycle, with the stopping test fused.
+__global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double> op, const double2* __restrict__ x,
+                                                             const double2* __restrict__ b, float2* __restrict__ r32,
+                                                             Ctl c, int count) {
+  __shared__ double sh[32];
+  NODE_INDEX
+  if (!c.active[rhs]) return;
+  double a0[1] = {0.0};
+  if (i <= g.nx) {
+    FOR_ROWS {
+      if (j > g.ny) break;
+      const int p = g.at(i, j);
+      const double2 r = sub<double>(b[off + p], op.apply(x + off, p, g.pitch, i, j));
+      r32[off + p] = make_float2((float)r.x, (float)r.y);
+      a0[0] += abs2<double>(r);
+    }
+  }
+  double v[1];
+  if (reduce_last<1, double>(a0, v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+      threadIdx.x == 0 && threadIdx.y == 0)
+    stop_update(c, rhs, v[0], count);
+}
+
+__global__ void __launch_bounds__(BX * BY) k_update_mixed(Grid g, double2* __restrict__ x, const float2* __restrict__ e,
+                                                          const int* __restrict__ active) {
+  NODE_INDEX
+  if (active && !active[rhs]) return;
+  if (i > g.nx) return;
+  FOR_ROWS {
+    if (j > g.ny) break;
+    const long long p = off + g.at(i, j);
+    const float2 d = e[p];
+    double2 xv = x[p];
+    xv.x += (double)d.x;
+    xv.y += (double)d.y;
+    x[p] = xv;
+  }
+}
+
 // ||v|| per RHS into out[rhs] (one kernel, last-block finish).
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_vecnorm_fin(Grid g, const cx<T>* __restrict__ v_, double* __restrict__ out,
@@ -291,6 +331,14 @@ void launch_resnorm_stop(const Grid& g, const OpView<T>& v, const cx<T>* x, cons
   with_op<T>(v, g.nx, g.ny, [&](auto op) {
     k_resnorm_stop<T, decltype(op)><<<pack_grid(g, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(g, op, x, b, c, count);
   });
+}
+void launch_resid_cast_stop(const Grid& g, const OpView<double>& v, const double2* x, const double2* b, float2* r32,
+                            int B, const Ctl& c, int count, cudaStream_t s) {
+  Op0<double> op{v.c0, v.kf, g.nx, g.ny};  // constants by value
+  k_resid_cast_stop<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, r32, c, count);
+}
+void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s) {
+  k_update_mixed<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, x, e, active);
 }
 template <class T>
 void launch_vecnorm_fin(const Grid& g, const cx<T>* v, int B, double* out, double* partial, unsigned* tickets,

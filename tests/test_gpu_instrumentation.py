@@ -17,7 +17,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 import paper_2308_13476_gb300 as hm  # noqa: E402
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed-ff"])
 def test_profile_all_kinds_then_solve(precision):
     n, B, k = 64, 2, 20.0
     h = 1.0 / n

@@ -33,12 +33,13 @@ def test_layered_model_mixed_and_fp64():
     kd = torch.from_numpy(k).cuda()
     bd = torch.from_numpy(b).cuda()
     A = oprob.helmholtz_matrix(nx, nz, h, k)
-    s = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision="mixed")
-    x, st, cyc, rr = s.solve(bd, tol=1e-6)
-    assert st == hm.MG_OK and rr[0] <= 1e-6
-    r = b.ravel() - A @ x.cpu().numpy().ravel()
-    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-6
-    s.close()
+    for precision in ("mixed", "mixed-ff"):
+        s = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision=precision)
+        x, st, cyc, rr = s.solve(bd, tol=1e-6)
+        assert st == hm.MG_OK and rr[0] <= 1e-6
+        r = b.ravel() - A @ x.cpu().numpy().ravel()
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-6
+        s.close()
     s64 = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, max_cycles=3)
     H = ohier.build_hierarchy(nx, nz, h, k, beta2)
     ref = ocycle.mg_solve(H, b.ravel(), 1e-6, ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5), max_cycles=3)

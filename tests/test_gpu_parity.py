@@ -166,10 +166,12 @@ def test_batch_each_rhs_matches_oracle(cn):
         assert rel(host(x)[q], refs[q].x) <= 1e-10
 
 
-def test_mixed_precision_against_fp64_oracle():
-    # complex64 cycles inside FP64 refinement: the FP64 residual of the
-    # returned x meets tol, and driven to 1e-10 the solution agrees with the
-    # FP64 oracle's to 1e-6 relative.
+@pytest.mark.parametrize("precision", ["mixed", "mixed-ff"])
+def test_mixed_precision_against_fp64_oracle(precision):
+    # complex64 cycles inside the refinement loop (outer values in FP64, or
+    # float-float for mixed-ff): the FP64 residual of the returned x meets
+    # tol and equals the reported one, and driven to 1e-10 the solution
+    # agrees with the FP64 oracle's to 1e-6 relative.
     nx = ny = 64
     h = 1.0 / 64
     k = 40.0
@@ -179,7 +181,7 @@ def test_mixed_precision_against_fp64_oracle():
     ref = ocycle.mg_solve(H, b.ravel(), 1e-12, opt)
     for sm, beta2, cn in (("gmres3", 1 / k, COARSE[1]), ("jacobi", 0.7, COARSE[1]), ("gmres3", 1 / k, COARSE[0]),
                           ("gmres3", 1 / k, COARSE[2]), ("gmres3", 1 / k, COARSE[4])):
-        s = hm.Solver(nx, ny, h, k, beta2, smoother=sm, nu_pre=2, nu_post=2, precision="mixed", **cn)
+        s = hm.Solver(nx, ny, h, k, beta2, smoother=sm, nu_pre=2, nu_post=2, precision=precision, **cn)
         x, st, cyc, rr = s.solve(dev(b), tol=1e-6)
         assert st == hm.MG_OK and rr[0] <= 1e-6
         r = b.ravel() - H.A[0] @ host(x)[0].ravel()
