@@ -51,6 +51,13 @@ def parse():
     p.add_argument("--no-fp64-line", action="store_true", help="skip the FP64 comparison solve")
     p.add_argument("--no-ff-line", action="store_true", help="skip the float-float outer-loop variant")
     p.add_argument("--cpu-sample-cycles", type=int, default=2)
+    p.add_argument("--workload", default="batched", choices=["batched", "layered", "ragged", "gradient"],
+                   help="batched: the bench line (default); the others print one JSON line for the other "
+                        "workloads: layered velocity model at --freq Hz, a ragged batch of 32 problems, the "
+                        "adjoint gradient of a receiver misfit")
+    p.add_argument("--freq", type=float, default=10.0, help="layered workload: frequency in Hz (10, 20, 40)")
+    p.add_argument("--march", type=int, default=-1, choices=[-1, 0, 1],
+                   help="GMRES(3) as row/column marches: 1 always, 0 never, -1 by level size (library default)")
     p.add_argument("--probe", action="store_true",
                    help="profiling probe: set up the workload and run two solves capped at --max-cycles; no timing")
     p.add_argument("--max-cycles", type=int, default=2)
@@ -197,8 +204,8 @@ def run_reference(a):
     N = (a.n + 1) ** 2 * a.batch
     value = N / (tc * a.batch * cycles_needed) if cycles_needed else None
     sample = (f"{a.steps} timed oracle cycles (after {a.warmup} untimed) of one right-hand side of the workload, "
-              f"one core, scaled to {a.batch} right-hand sides x {cycles_needed} cycles per solve "
-              f"(profiles/bench_cycles.json)")
+              f"one core, scaled to {a.batch} right-hand sides x the oracle's {cycles_needed} cycles per solve "
+              f"(oracle/bench_cycles.json)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": tc * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -210,7 +217,9 @@ def run_reference(a):
 
 
 def _cycles_from_cache(a):
-    p = os.path.join(ROOT, "profiles", "bench_cycles.json")
+    """Cycles of one solve of the workload by the oracle (written by
+    oracle/bench_cycles.py), or None."""
+    p = os.path.join(ROOT, "oracle", "bench_cycles.json")
     try:
         d = json.load(open(p))
         return int(d.get(f"{a.k:g}/{a.n}/{a.smoother}/{a.cycle}{a.nu}/{a.beta2:g}"))
@@ -255,7 +264,7 @@ def run_ours(a):
     def make(precision, shapes=None):
         t0 = time.perf_counter()
         s = hm.Solver(n, n, h, k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
-                      precision=precision, batch=a.batch, max_cycles=20000, **(shapes or {}))
+                      precision=precision, batch=a.batch, max_cycles=20000, march=a.march, **(shapes or {}))
         torch.cuda.synchronize()
         return s, time.perf_counter() - t0
 
@@ -347,12 +356,14 @@ def run_ours(a):
     }
     if rank == 0 and world == 1 and a.cpu_sample_cycles > 0:
         tc = oracle_cycle_seconds(a, a.cpu_sample_cycles)
-        cyc_needed = max(cyc)
+        cyc_oracle = _cycles_from_cache(a)
+        cyc_needed = cyc_oracle or max(cyc)
+        src = "the oracle's" if cyc_oracle else "the GPU path's (no oracle count stored)"
         line["cpu_baseline"] = {"value": N * a.batch / (tc * a.batch * cyc_needed), "unit": UNIT, "cores": 1,
                                 "kind": "oracle",
                                 "sample": f"{a.cpu_sample_cycles} oracle cycles (FP64, one core) of one right-hand "
-                                          f"side of the workload, scaled to {a.batch} right-hand sides x the "
-                                          f"{cyc_needed} cycles of one solve"}
+                                          f"side of the workload, scaled to {a.batch} right-hand sides x "
+                                          f"{src} {cyc_needed} cycles of one solve"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -401,10 +412,136 @@ def run_probe(a):
     s.close()
 
 
+def _event_ms(fn, steps):
+    """Mean CUDA-event time of fn() over `steps` calls (device synchronised around each)."""
+    import torch
+    tot = 0.0
+    out = None
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps, out
+
+
+def run_layered(a):
+    """Variable-k workload: the seeded layered model (stand-in for the 9.2 x
+    3.0 km benchmark model), h = 1500 / (10 f) m, grid 640 x 224 cells at
+    10 Hz scaled with f, source at (centre, 2h), GMRES(3) V(2,2),
+    beta2 = 1/(k_max L), one right-hand side, mixed and FP64 paths."""
+    import torch
+    import paper_2308_13476_gb300 as hm
+    import synth
+    torch.cuda.set_device(0)
+    f = a.freq
+    h = 1500.0 / (10.0 * f)
+    nx, nz = int(round(640 * f / 10)), int(round(224 * f / 10))
+    v = synth.layered_velocity(nx, nz, h, seed=11)
+    k = 2 * np.pi * f / v
+    b = torch.from_numpy(synth.point_source(nx, nz, h, nx // 2, 2)).cuda()
+    kd = torch.from_numpy(k).cuda()
+    beta2 = 1.0 / (k.max() * nx * h)
+    N = (nx + 1) * (nz + 1)
+    out = {"workload": f"layered velocity model, {f:g} Hz, {nx} x {nz} cells, h = {h:g} m", "unit": "DOF-solves/s",
+           "data": "synthetic", "smoother": "gmres3", "cycle": "V(2,2)", "beta2": beta2, "tol": a.tol}
+    for prec in ([a.precision, "fp64"] if not a.no_fp64_line and a.precision != "fp64" else [a.precision]):
+        s = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision=prec,
+                      max_cycles=20000, march=a.march)
+        s.solve(b, tol=a.tol)   # warm-up (graph capture)
+        ms, (x, st, cyc, rr) = _event_ms(lambda: s.solve(b, tol=a.tol), a.steps)
+        if st != hm.MG_OK:
+            raise RuntimeError(f"layered solve failed: {hm.STATUS_NAMES[st]}")
+        out[prec] = {"value": N / (ms / 1e3), "cycles": int(cyc[0]), "relres": float(rr[0]), "ms_per_solve": ms}
+        s.close()
+    out["value"] = out[a.precision]["value"]
+    print(json.dumps(out))
+
+
+def run_ragged(a):
+    """Ragged batch: 32 square constant-k problems with interval counts drawn
+    in [127, 1023] and rounded to c * 2^m (synth.ragged_sizes, seed 3),
+    h = 1/n, k = 0.625 n (kh = 0.625), beta2 = 1/k each, centre source,
+    GMRES(3) V(2,2) in one handle; value = all problems' unknowns / time."""
+    import torch
+    import paper_2308_13476_gb300 as hm
+    import synth
+    torch.cuda.set_device(0)
+    ns = synth.ragged_sizes(32, 3)
+    probs = [(n, n, 1.0 / n, 0.625 * n) for n in ns]
+    rhs = [torch.from_numpy(synth.point_source(n, n, 1.0 / n)).cuda() for n in ns]
+    rs = hm.RaggedSolver(probs, [1.0 / p[3] for p in probs], smoother="gmres3", nu_pre=2, nu_post=2,
+                         precision=a.precision, max_cycles=20000, march=a.march)
+    rs.solve(rhs, tol=a.tol)
+    ms, (xs, st, cyc, rr) = _event_ms(lambda: rs.solve(rhs, tol=a.tol), a.steps)
+    if st != hm.MG_OK:
+        raise RuntimeError(f"ragged solve failed: {hm.STATUS_NAMES[st]}")
+    rs.close()
+    N = sum((n + 1) ** 2 for n in ns)
+    print(json.dumps({"workload": "ragged batch of 32 constant-k problems, kh = 0.625", "unit": "DOF-solves/s",
+                      "value": N / (ms / 1e3), "ms_per_solve": ms, "unknowns_total": N, "sizes": ns,
+                      "cycles": [int(c) for c in cyc], "max_relres": float(max(rr)), "precision": a.precision,
+                      "data": "synthetic", "smoother": "gmres3", "cycle": "V(2,2)", "tol": a.tol}))
+
+
+def run_gradient(a):
+    """Adjoint gradient: L = 1/2 sum_s ||P u_s - d_s||^2, 16 sources and 256
+    receivers on the first interior row of a 1025^2 grid, 15 Hz, squared
+    slowness m = m0 (1 + 0.1 rho) with m0 = 1/2000^2 and rho a smooth seeded
+    field, h = 0.625 * 1800 / (2 pi 15) m; data from the unperturbed model;
+    one evaluation = batched forward solve + batched adjoint solve + gradient
+    kernel through torch.autograd."""
+    import torch
+    import synth
+    from paper_2308_13476_gb300 import autograd as hag
+    torch.cuda.set_device(0)
+    n, nsrc, nrec = 1024, 16, 256
+    omega = 2 * np.pi * 15.0
+    h = 0.625 * 1800.0 / omega
+    m0 = np.full((n + 1, n + 1), 1.0 / 2000.0**2)
+    m = m0 * (1 + 0.1 * synth.smooth_perturbation(n, n, 7, sigma_nodes=20.0))
+    src = torch.from_numpy(synth.source_row(n, n, h, nsrc)).cuda()
+    cols = np.linspace(1, n - 1, nrec).round().astype(np.int64)
+    rec = torch.from_numpy((n - 1) * (n + 1) + cols).cuda()
+    grid = (n, n, h, omega)
+    kw = dict(tol=a.tol, smoother="gmres3", nu_pre=2, nu_post=2, precision=a.precision, march=a.march)
+    # data: the unperturbed model's receiver traces (the misfit with zero data returns them)
+    m0t = torch.from_numpy(m0).cuda()
+    from paper_2308_13476_gb300 import Solver
+    k0 = (omega * torch.sqrt(m0t)).contiguous()
+    s0 = Solver(n, n, h, k0, 1.0 / (float(k0.max()) * n * h), batch=nsrc, smoother="gmres3", nu_pre=2, nu_post=2,
+                precision=a.precision)
+    u0, st, _, _ = s0.solve(src, tol=1e-8)
+    s0.close()
+    data = u0.reshape(nsrc, -1)[:, rec].contiguous()
+    mt = torch.from_numpy(m).cuda()
+
+    def evaluate():
+        mm = mt.clone().requires_grad_(True)
+        L = hag.misfit(mm, src, rec, data, grid, **kw)
+        L.backward()
+        return float(L.detach()), mm.grad
+
+    evaluate()
+    ms, (L, g) = _event_ms(evaluate, a.steps)
+    N = (n + 1) ** 2
+    print(json.dumps({"workload": "adjoint gradient, 16 sources, 256 receivers, 1025^2, 15 Hz",
+                      "unit": "gradient evaluations/s", "value": 1e3 / ms, "ms_per_evaluation": ms,
+                      "dof_solves_per_s": 2 * nsrc * N / (ms / 1e3), "misfit": L,
+                      "grad_norm": float(g.norm()), "precision": a.precision, "data": "synthetic",
+                      "smoother": "gmres3", "cycle": "V(2,2)", "tol": a.tol}))
+
+
 def main():
     a = parse()
     if a.probe:
         run_probe(a)
+        return
+    if a.workload != "batched":
+        {"layered": run_layered, "ragged": run_ragged, "gradient": run_gradient}[a.workload](a)
         return
     if a.impl == "reference":
         run_reference(a)

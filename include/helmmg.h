@@ -90,12 +90,21 @@ typedef struct {
                        0 = one kernel per step (same results)                  */
   int tile_rows;    /* grid rows per thread of the node kernels: 0 = chosen
                        from each level's size, 1..4 = forced (autotuner knob) */
+  int march;        /* GMRES(3) on the fine level as row marches and on
+                       Kronecker-form levels with column-march operator
+                       kernels (needs fuse = 1): 1 = always, 0 = never (the
+                       node-parallel kernels; same results to rounding),
+                       -1 = the Kronecker-form levels always, the fine level
+                       when it holds at least 4 M nodes over all right-hand
+                       sides and the other problems of a ragged batch (a row
+                       march keeps each warp on one strip, which needs that
+                       much work to fill the GPU)                           */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
  * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0, fuse 1,
- * tile_rows 0; default stream. */
+ * tile_rows 0; march -1; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).
@@ -114,8 +123,8 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
 
 /* Ragged batch: nprob independent constant-k problems of different sizes in
  * one handle (problem p: nx[p] x ny[p] cells of side h[p], wavenumber
- * k_const[p]; the same shift and options, one right-hand side each, so
- * opt->batch must be 1).  mg_solve / mg_adjoint on this handle take rhs and x
+ * k_const[p], complex shift beta2[p]; host arrays of nprob entries, copied;
+ * the same options and one right-hand side each, so opt->batch must be 1).  mg_solve / mg_adjoint on this handle take rhs and x
  * as the problems' grids packed back to back (problem p starts after
  * sum_{q<p} (nx[q]+1)(ny[q]+1) complex128 values) and report cycles and
  * relative residuals per problem.  Every problem has its own hierarchy and
@@ -123,7 +132,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
  * problems run side by side on the GPU.  Inspection calls return MG_ESTATE
  * on a ragged handle. */
 mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* ny, const double* h,
-                          const double* k_const, double beta2, const mg_options* opt);
+                          const double* k_const, const double* beta2, const mg_options* opt);
 
 /* Solve A x = rhs for the handle's batch, starting from the x passed in.
  *   rhs        device, B grids complex128 (read only)
@@ -186,9 +195,10 @@ mg_status mg_history(mg_handle h, double* hist, int cap);
 /* Time one kernel of the hierarchy in the handle's precision: `what` = 0 one
  * weighted-Jacobi sweep, 1 a residual b - A x, 2 a restriction, 3 a
  * prolongation-and-correct, 4 one GMRES(3) smoothing step (Sec. 5.3; the
- * kernels the cycle runs for that level: on level 0 with fuse = 1 four
- * row-march passes and the update, 16 vector reads and writes per node;
- * otherwise eight node-parallel passes, 28; needs smoother = 1), on level
+ * kernels the cycle runs for that level: on level 0, when it runs as row
+ * marches (option march), four row-march passes and the update, 16 vector
+ * reads and writes per node; otherwise eight passes, 28; needs
+ * smoother = 1), on level
  * `level` for all B right-hand sides.  The work runs `reps` times back to
  * back between two CUDA events on the handle's stream (after one untimed
  * run); *ms gets the mean time of one run and *bytes its algorithmic DRAM

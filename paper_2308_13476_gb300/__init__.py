@@ -41,7 +41,7 @@ class MgOptions(ctypes.Structure):
                 ("nu_post", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
                 ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("fuse", ctypes.c_int),
-                ("tile_rows", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("tile_rows", ctypes.c_int), ("march", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -72,7 +72,7 @@ def load_library(path=LIB_PATH):
     lib.mg_profile.argtypes = [vp, i, i, i, dp, dp]
     lib.mg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.mg_residual_norm_static.argtypes = [i, i, d, vp, d, vp, vp, vp, vp]
-    lib.mg_setup_ragged.argtypes = [ctypes.POINTER(vp), i, ip, ip, dp, dp, d, ctypes.POINTER(MgOptions)]
+    lib.mg_setup_ragged.argtypes = [ctypes.POINTER(vp), i, ip, ip, dp, dp, dp, ctypes.POINTER(MgOptions)]
     for name in EXPORTED:
         if name not in ("mg_default_options", "mg_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -211,14 +211,16 @@ def mg_residual_norm_static(nx, ny, h, k, x, b, out, stream=None):
 
 
 def mg_setup_ragged(nx, ny, h, k_const, beta2=0.0, opt=None):
-    """Handle of a ragged batch (lists of per-problem sizes, cell sizes and wavenumbers)."""
+    """Handle of a ragged batch (lists of per-problem sizes, cell sizes,
+    wavenumbers and shifts; a scalar beta2 applies to every problem)."""
     lib = load_library()
     opt = opt or mg_default_options()
     n = len(nx)
     hdl = ctypes.c_void_p()
     ia = lambda v: (ctypes.c_int * n)(*[int(q) for q in v])
     da = lambda v: (ctypes.c_double * n)(*[float(q) for q in v])
-    _check(lib.mg_setup_ragged(ctypes.byref(hdl), n, ia(nx), ia(ny), da(h), da(k_const), float(beta2),
+    b2 = [float(beta2)] * n if isinstance(beta2, (int, float)) else list(beta2)
+    _check(lib.mg_setup_ragged(ctypes.byref(hdl), n, ia(nx), ia(ny), da(h), da(k_const), da(b2),
                                ctypes.byref(opt)))
     return hdl.value
 
@@ -231,7 +233,7 @@ SMOOTHERS = {"jacobi": 0, "gmres3": 1}
 
 def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, precision="fp64", batch=1,
              max_cycles=10000, min_coarse=10, coarse_nodes=None, coarse_mode=None, fuse=None, tile_rows=None,
-             stream=None):
+             march=None, stream=None):
     o = mg_default_options()
     o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
     o.smoother = SMOOTHERS[smoother]
@@ -239,7 +241,7 @@ def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, preci
     o.precision = PRECISIONS[precision]
     o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
     for name, val in (("coarse_nodes", coarse_nodes), ("coarse_mode", coarse_mode), ("fuse", fuse),
-                      ("tile_rows", tile_rows)):
+                      ("tile_rows", tile_rows), ("march", march)):
         if val is not None:
             setattr(o, name, int(val))
     o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
@@ -250,8 +252,9 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "mixed-ff": 2}
 class RaggedSolver:
     """Independent constant-k problems of different sizes solved together.
 
-    RaggedSolver(sizes=[(nx, ny, h, k), ...], beta2, **options).  solve()
-    takes and returns a list of complex128 CUDA grids (ny+1, nx+1)."""
+    RaggedSolver(sizes=[(nx, ny, h, k), ...], beta2, **options), beta2 a
+    scalar or one shift per problem.  solve() takes and returns a list of
+    complex128 CUDA grids (ny+1, nx+1)."""
 
     def __init__(self, sizes, beta2, **options):
         self.sizes = [(int(a), int(b), float(c), float(d)) for a, b, c, d in sizes]
@@ -289,13 +292,13 @@ class Solver:
 
     Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
            nu_pre, nu_post, omega, precision="fp64"|"mixed"|"mixed-ff", batch, levels,
-           max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, stream)
+           max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, march, stream)
     ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
     """
 
     def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
                  precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, coarse_nodes=None,
-                 coarse_mode=None, fuse=None, tile_rows=None, stream=None):
+                 coarse_mode=None, fuse=None, tile_rows=None, march=None, stream=None):
         o = mg_default_options()
         o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
         o.smoother = SMOOTHERS[smoother]
@@ -310,6 +313,8 @@ class Solver:
             o.fuse = int(fuse)
         if tile_rows is not None:
             o.tile_rows = int(tile_rows)
+        if march is not None:
+            o.march = int(march)
         o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         self.nx, self.ny, self.h, self.batch = nx, ny, h, batch
         if isinstance(k, (int, float)):

@@ -71,6 +71,7 @@ struct Level {
 
 struct mg_ctx {
   mg_options opt;
+  long long peer_nodes = 0;   // ragged sub-handle: fine-level nodes of the problems solved beside it
   int nx = 0, ny = 0, B = 1, nlev = 0, ncoarse = 0;
   double h = 0, kconst = 0, beta2 = 0;
   std::vector<Level> lev;
@@ -220,13 +221,27 @@ template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, c
 // nu GMRES(3) smoothing steps on level l: the fine level as row marches, the
 // Kronecker-form levels with column-march operator kernels (both with
 // fuse = 1), stored stencils (or fuse = 0) with the node-parallel kernels.
+// Whether level l runs its GMRES(3) kernels as marches (option march).
+// Automatic: the Kronecker-form levels always (their column marches cut the
+// arithmetic of every apply); the fine level when it holds at least 4 M nodes
+// over all right-hand sides, counting those of the other problems of a
+// ragged batch, which run beside it (a row march keeps each warp on one
+// strip, and less work leaves the GPU under-filled).
+static bool use_march(const mg_ctx* c, int l) {
+  if (!c->opt.fuse || c->opt.march == 0) return false;
+  if (c->opt.march == 1 || c->lev[l].kind >= 4) return true;
+  const Grid& g = c->lev[l].g;
+  return (long long)(g.nx + 1) * (g.ny + 1) * c->B + c->peer_nodes >= (4LL << 20);
+}
+
 template <class T>
 static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, const int* active, cudaStream_t s) {
   const Grid& g = c->lev[l].g;
   const OpView<T> op = opT<T>(c, l);
   const GmresBufs& gb = vecs<T>(c)[l].gb;
-  if (c->opt.fuse && op.kind == 1) gmres_smooth_march<T>(g, op, x, b, nu, c->B, active, gb, s);
-  else if (c->opt.fuse && op.kind >= 4) gmres_smooth_kron<T>(g, op, x, b, nu, c->B, active, gb, s);
+  const bool m = use_march(c, l);
+  if (m && op.kind == 1) gmres_smooth_march<T>(g, op, x, b, nu, c->B, active, gb, s);
+  else if (m && op.kind >= 4) gmres_smooth_kron<T>(g, op, x, b, nu, c->B, active, gb, s);
   else gmres_smooth<T>(g, op, x, b, nu, c->B, active, gb, s);
 }
 
@@ -454,7 +469,7 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
     double gop = 0;   // operator bytes per node and RHS read by one pass
     if (level == 0) gop = op.kf ? sizeof(T) / (double)h->B : 0.0;
     else if (h->lev[level].kind <= 3) gop = opbytes - e / h->B;   // stencil without the inverse diagonal
-    const int vec = (h->opt.fuse && h->lev[level].kind == 1) ? 16 : 28;   // row marches + update, or 8 passes
+    const int vec = (use_march(h, level) && h->lev[level].kind == 1) ? 16 : 28;   // row marches + update, or 8 passes
     *bytes = nodes * (vec * e + 4 * gop);
   }
   launch();
@@ -493,6 +508,7 @@ void mg_default_options(mg_options* o) {
   o->coarse_mode = 0;
   o->fuse = 1;
   o->tile_rows = 0;
+  o->march = -1;
   o->stream = nullptr;
 }
 
@@ -725,6 +741,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.coarse_mode != 0 && o.coarse_mode != 1) FAIL(MG_EINVAL, "coarse_mode must be 0 or 1");
   if (o.fuse != 0 && o.fuse != 1) FAIL(MG_EINVAL, "fuse must be 0 or 1");
   if (o.tile_rows < 0 || o.tile_rows > RYMAX) FAIL(MG_EINVAL, "tile_rows must be in 0..4");
+  if (o.march < -1 || o.march > 1) FAIL(MG_EINVAL, "march must be -1, 0 or 1");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
@@ -745,10 +762,11 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
 }
 
 mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* ny, const double* h,
-                          const double* k_const, double beta2, const mg_options* opt) {
+                          const double* k_const, const double* beta2, const mg_options* opt) {
   if (!out) FAIL(MG_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nprob < 1 || !nx || !ny || !h || !k_const) FAIL(MG_EINVAL, "ragged batch needs nprob >= 1 and its arrays");
+  if (nprob < 1 || !nx || !ny || !h || !k_const || !beta2)
+    FAIL(MG_EINVAL, "ragged batch needs nprob >= 1 and its arrays");
   mg_options o;
   if (opt) o = *opt; else mg_default_options(&o);
   if (o.batch != 1) FAIL(MG_EINVAL, "a ragged batch solves one right-hand side per problem (batch must be 1)");
@@ -763,7 +781,7 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
     mg_options op = o;
     op.stream = sp;
     mg_handle hp = nullptr;
-    mg_status st = mg_setup(&hp, nx[p], ny[p], h[p], nullptr, k_const[p], beta2, 0, &op);
+    mg_status st = mg_setup(&hp, nx[p], ny[p], h[p], nullptr, k_const[p], beta2[p], 0, &op);
     if (st != MG_OK) {
       cudaStreamDestroy(sp);
       std::string m = g_err;
@@ -773,6 +791,9 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
     hp->own_stream = sp;
     c->sub.push_back(hp);
   }
+  long long total = 0;
+  for (mg_ctx* q : c->sub) total += (long long)(q->nx + 1) * (q->ny + 1);
+  for (mg_ctx* q : c->sub) q->peer_nodes = total - (long long)(q->nx + 1) * (q->ny + 1);
   c->nx = c->sub[0]->nx;
   c->ny = c->sub[0]->ny;
   c->nlev = c->sub[0]->nlev;

@@ -21,7 +21,8 @@ import paper_2308_13476_gb300 as hm  # noqa: E402
 def test_profile_all_kinds_then_solve(precision):
     n, B, k = 64, 2, 20.0
     h = 1.0 / n
-    s = hm.Solver(n, n, h, k, 0.05, smoother="gmres3", nu_pre=2, nu_post=2, precision=precision, batch=B)
+    s = hm.Solver(n, n, h, k, 0.05, smoother="gmres3", nu_pre=2, nu_post=2, precision=precision, batch=B,
+                  march=1)
     e = 16 if precision == "fp64" else 8
     nodes = (n + 1) ** 2 * B
     expect = {0: 3 * e, 1: 3 * e, 2: 1.25 * e, 3: 2.25 * e, 4: 16 * e}

@@ -33,8 +33,9 @@ def test_layered_model_mixed_and_fp64():
     kd = torch.from_numpy(k).cuda()
     bd = torch.from_numpy(b).cuda()
     A = oprob.helmholtz_matrix(nx, nz, h, k)
-    for precision in ("mixed", "mixed-ff"):
-        s = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision=precision)
+    for precision, march in (("mixed", -1), ("mixed-ff", 1)):
+        s = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision=precision,
+                      march=march)
         x, st, cyc, rr = s.solve(bd, tol=1e-6)
         assert st == hm.MG_OK and rr[0] <= 1e-6
         r = b.ravel() - A @ x.cpu().numpy().ravel()

@@ -84,11 +84,13 @@ CASES = [
 # execution modes: every level as grid-wide kernels; the library default
 # (small levels in one CTA per RHS); level 0 as grid-wide kernels and the rest
 # in one cooperative launch; the whole cycle in one CTA per RHS; the whole
-# cycle in one cooperative launch
+# cycle in one cooperative launch; grid-wide kernels without fusion; grid-wide
+# kernels with the GMRES(3) marches forced on (small grids run them on the
+# boundary path only)
 COARSE = [dict(coarse_nodes=0), dict(), dict(coarse_nodes=1200, coarse_mode=1),
           dict(coarse_nodes=10**6, coarse_mode=0), dict(coarse_nodes=10**6, coarse_mode=1),
-          dict(coarse_nodes=0, fuse=0)]
-COARSE_IDS = ["grid", "default", "hybrid", "cta", "coop", "grid_unfused"]
+          dict(coarse_nodes=0, fuse=0), dict(coarse_nodes=0, march=1)]
+COARSE_IDS = ["grid", "default", "hybrid", "cta", "coop", "grid_unfused", "grid_march"]
 
 
 @pytest.mark.parametrize("cn", COARSE, ids=COARSE_IDS)
@@ -265,3 +267,33 @@ def test_invalid_arguments_rejected():
     # coarsest grid too large for the direct solver
     with pytest.raises(hm.HelmmgError):
         hm.Solver(63, 63, 0.1, 5.0, 0.7)
+
+
+def test_interior_row_march_path_on_a_larger_grid():
+    """On 257^2 the fine level's row marches (forced on) run most warps on
+    the interior path (no boundary tests); the small cases above only reach
+    the boundary path.  The node-parallel kernels are checked on the same
+    grid.  FP64: one cycle from the oracle's iterate equals the oracle's next
+    iterate to 1e-10 at cycles 1, 2 and 3; mixed and mixed-ff: the oracle's
+    FP64 residual of the returned x meets tol."""
+    n, k = 256, 100.0
+    h = 1.0 / n
+    b = synth.point_source(n, n, h) + 1e-2 * synth.random_complex((n + 1, n + 1), 5) / h**2
+    opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
+    ref = _oracle_run(n, n, h, k, 1 / k, opt, b, 1e-300, max_cycles=3)
+    for march in (1, 0):
+        s1 = hm.Solver(n, n, h, k, 1 / k, smoother="gmres3", nu_pre=2, nu_post=2, max_cycles=1, march=march)
+        for m in (1, 2, 3):
+            x0 = np.zeros_like(b) if m == 1 else ref.iterates[m - 2].reshape(b.shape)
+            xm, st1, cm, _ = s1.solve(dev(b), x=dev(x0)[None].contiguous(), tol=1e-300)
+            assert cm[0] == 1
+            assert rel(host(xm)[0], ref.iterates[m - 1]) <= 1e-10, (march, m)
+        s1.close()
+    A = oprob.helmholtz_matrix(n, n, h, k)
+    for precision in ("mixed", "mixed-ff"):
+        s = hm.Solver(n, n, h, k, 1 / k, smoother="gmres3", nu_pre=2, nu_post=2, precision=precision, march=1)
+        x, st, cyc, rr = s.solve(dev(b), tol=1e-6)
+        assert st == hm.MG_OK and rr[0] <= 1e-6
+        r = b.ravel() - A @ host(x)[0].ravel()
+        assert abs(np.linalg.norm(r) / np.linalg.norm(b) - rr[0]) <= 1e-3 * rr[0], precision
+        s.close()
