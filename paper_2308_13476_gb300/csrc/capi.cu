@@ -102,6 +102,8 @@ struct mg_ctx {
   int* h_n_active = nullptr;  // pinned
   int* status = nullptr;
   cudaStream_t cap = nullptr;        // capture stream
+  cudaStream_t side = nullptr;       // second stream of the fine-level row marches
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   std::vector<void*> allocs;
@@ -123,6 +125,9 @@ struct mg_ctx {
     for (void* p : allocs) cudaFree(p);
     if (h_n_active) cudaFreeHost(h_n_active);
     if (cap) cudaStreamDestroy(cap);
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     if (own_stream) cudaStreamDestroy(own_stream);
   }
 };
@@ -238,7 +243,10 @@ template <class T>
 static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, const int* active, cudaStream_t s) {
   const Grid& g = c->lev[l].g;
   const OpView<T> op = opT<T>(c, l);
-  const GmresBufs& gb = vecs<T>(c)[l].gb;
+  GmresBufs gb = vecs<T>(c)[l].gb;
+  gb.side = c->side;
+  gb.ev_fork = c->ev_fork;
+  gb.ev_join = c->ev_join;
   const bool m = use_march(c, l);
   if (m && op.kind == 1) gmres_smooth_march<T>(g, op, x, b, nu, c->B, active, gb, s);
   else if (m && op.kind >= 4) gmres_smooth_kron<T>(g, op, x, b, nu, c->B, active, gb, s);
@@ -718,6 +726,11 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  if (o.smoother == 1) {
+    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
   return MG_OK;
 }
 

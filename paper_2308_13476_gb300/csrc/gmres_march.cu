@@ -432,19 +432,18 @@ __device__ __forceinline__ void run_pass(const MCtx<T, IN>& c, int t1, const voi
   for (int k = 0; k < NV; ++k) acc[k] = p.acc[k];
 }
 
-// The interior launch runs first and only publishes its block sums (records
-// 0 .. ni-1); the boundary launch publishes after them, and its last block
-// sums all records and runs the scalar step F.
+// The interior and boundary launches of a pass may run one after the other
+// or side by side: every block publishes its sums (interior blocks in
+// records 0 .. ni-1, boundary blocks after them) and takes a ticket counted
+// over both launches; the block holding the last ticket sums all records in
+// record order and runs the scalar step F.
 template <bool IN, int NV, class T, class F>
 __device__ __forceinline__ void finish(const T (&acc)[NV], double* sh, double* partial, unsigned* tickets, int rhs,
                                        const MGeo& mg, double* S, F f) {
   double v[NV];
   const int nrec = mg.ni + mg.nb;
-  if (IN) {
-    publish<NV, T>(acc, sh, partial, rhs, nrec, blockIdx.x);
-  } else if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, gridDim.x, blockIdx.x, mg.ni, nrec)) {
+  if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blockIdx.x, IN ? 0 : mg.ni, nrec))
     staged<T>(S, v, f);
-  }
 }
 
 // M0: u0 = b - A x; |u0|^2 and <u0, A u0>.
@@ -614,15 +613,31 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
   const Op0<T> op{opv.c0, opv.kf, g.nx, g.ny};
   const MGeo mg = march_geo<T>(g, B);
   const dim3 gi(mg.ni, 1, B), gbd(mg.nb, 1, B);
+  // the boundary launch of each pass on the side stream, beside the interior
+  // one (its few long-lived warps then overlap the interior launch)
+  const bool fork = gb.side && mg.ni;
+  cudaStream_t sb = fork ? gb.side : s;
+  auto pass = [&](auto interior, auto boundary) {
+    if (fork) {
+      cudaEventRecord(gb.ev_fork, s);
+      cudaStreamWaitEvent(gb.side, gb.ev_fork, 0);
+    }
+    boundary();
+    if (mg.ni) interior();
+    if (fork) {
+      cudaEventRecord(gb.ev_join, gb.side);
+      cudaStreamWaitEvent(s, gb.ev_join, 0);
+    }
+  };
   for (int step = 0; step < nu; ++step) {
-    if (mg.ni) gm_init<T, true><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active);
-    gm_init<T, false><<<gbd, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active);
-    if (mg.ni) gm_step1<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active);
-    gm_step1<T, false><<<gbd, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active);
-    if (mg.ni) gm_step2<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
-    gm_step2<T, false><<<gbd, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
-    if (mg.ni) gm_step3<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
-    gm_step3<T, false><<<gbd, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active);
+    pass([&] { gm_init<T, true><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active); },
+         [&] { gm_init<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); });
+    pass([&] { gm_step1<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active); },
+         [&] { gm_step1<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, st, P, tk, active); });
+    pass([&] { gm_step2<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
+         [&] { gm_step2<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
+    pass([&] { gm_step3<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
+         [&] { gm_step3<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
     launch_gmres_update<T>(g, x, gb, B, active, s);
   }
 }

@@ -140,6 +140,9 @@ struct GmresBufs {
   double* partial;     // block partials of the fused reductions
   unsigned* tickets;   // one per RHS, 0 at rest
   double* st;          // per-RHS scalars, see kernels_gmres.cu
+  cudaStream_t side;   // optional second stream (with the two events) on
+  cudaEvent_t ev_fork; // which the fine level's boundary launches run beside
+  cudaEvent_t ev_join; // the interior ones; null: one stream
 };
 template <class T> void gmres_smooth(const Grid& g, const OpView<T>& op, cx<T>* x, const cx<T>* b, int nu, int B,
                                      const int* active, const GmresBufs& gb, cudaStream_t s);
