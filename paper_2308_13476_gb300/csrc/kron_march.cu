@@ -29,65 +29,79 @@ struct KGeo {
   int nchunks;
 };
 
-// A v down column i: sums() forms the two row sums of one input row,
-// shift_in() appends them to the ring of the last 2R+1 rows, and combine()
-// returns (A v)(i, m) once the ring holds rows m-R..m+R.  The next input row
-// is fetched one iteration ahead (prime / advance).
+// A v down column i: the input rows arrive in order through a per-warp
+// shared-memory ring (each row's 32 + 2R columns around the warp's columns,
+// copied by cp.async KD rows ahead of use, so the 2R+1 neighbours of a lane
+// are read from shared memory instead of being loaded from L2 2R+1 times);
+// advance() forms the two row sums of the lane's column and appends them to
+// the register ring of the last 2R+1 rows, and combine() returns (A v)(i, m)
+// once that ring holds rows m-R..m+R.
+constexpr int KD = 4;    // rows in flight ahead of use
+constexpr int KSL = 8;   // ring slots (a power of two > KD)
+
 template <class T, int R> struct KRing {
   static constexpr int K = 2 * R + 1;
+  static constexpr int WD = 32 + 2 * R;   // staged row width
   cx<T> G[K];
   T Wx[K];
   cx<T> s1[K], s2[K];
+  const cx<T>* vs;   // slice of the applied vector
+  Grid g;
+  int cw0, lane;     // the warp's first column, the lane
+  cx<T>* sm;         // the warp's ring, [KSL][WD]
+  int r0;            // first row of the march (slot 0)
 
-  __device__ __forceinline__ void init(const OpK<T, R>& op, int i) {
+  __device__ __forceinline__ void init(const OpK<T, R>& op, int i, bool col) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      G[k] = op.gx[i * K + k];
-      Wx[k] = op.wx[i * K + k];
+      G[k] = col ? op.gx[i * K + k] : mk<T>(T(0), T(0));
+      Wx[k] = col ? op.wx[i * K + k] : T(0);
       s1[k] = mk<T>(T(0), T(0));
       s2[k] = mk<T>(T(0), T(0));
     }
   }
-  // the 2R+1 values of one input row around column i (slice pointer vs,
-  // node offset p of (i, row))
-  __device__ __forceinline__ static void fetch(const cx<T>* __restrict__ vs, int p, cx<T> (&xv)[K]) {
+  // copy row r's staged columns into its slot; columns past nx are
+  // zero-filled (the padded layout covers the R columns left of the grid and
+  // the R rows past either edge)
+  __device__ __forceinline__ void issue(int r) {
+    cx<T>* dst = sm + ((r - r0) & (KSL - 1)) * WD;
 #pragma unroll
-    for (int dx = -R; dx <= R; ++dx) xv[dx + R] = __ldg(vs + p + dx);
+    for (int e = lane; e < WD; e += 32) {
+      const int col = cw0 - R + e;
+      const bool ok = col <= g.nx;
+      const cx<T>* src = vs + g.at(ok ? col : 0, r);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + e);
+      if (sizeof(cx<T>) == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+    }
   }
-  // row sums of one input row
-  __device__ __forceinline__ void sums(const cx<T> (&xv)[K], cx<T>& a, cx<T>& c) const {
-    a = mk<T>(T(0), T(0));
-    c = mk<T>(T(0), T(0));
+  __device__ __forceinline__ static void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+  // rows r0 .. r0 + KD - 1 in flight
+  __device__ __forceinline__ void prime(int last) {
+#pragma unroll
+    for (int d = 0; d < KD; ++d) {
+      if (r0 + d <= last) issue(r0 + d);
+      commit();
+    }
+  }
+  // take input row r (rows up to `last` exist): row r + KD in flight, row r's
+  // sums into the register ring.  All lanes of the warp call it.
+  __device__ __forceinline__ void advance(int r, int last) {
+    __syncwarp();   // every lane is done with the slot row r + KD reuses
+    if (r + KD <= last) issue(r + KD);
+    commit();
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(KD) : "memory");
+    __syncwarp();   // row r, copied by all lanes, is visible to all
+    const cx<T>* row = sm + ((r - r0) & (KSL - 1)) * WD + lane + R;
+    cx<T> a = mk<T>(T(0), T(0)), c = mk<T>(T(0), T(0));
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
-      a = fma_c<T>(G[dx + R], xv[dx + R], a);
-      c = mk<T>(fma(Wx[dx + R], xv[dx + R].x, c.x), fma(Wx[dx + R], xv[dx + R].y, c.y));
+      const cx<T> xv = row[dx];
+      a = fma_c<T>(G[dx + R], xv, a);
+      c = mk<T>(fma(Wx[dx + R], xv.x, c.x), fma(Wx[dx + R], xv.y, c.y));
     }
-  }
-  // march prologue: rows j0-R .. j0+R-1 into the ring, row j0+R fetched into nx
-  __device__ __forceinline__ void prime(const cx<T>* __restrict__ vs, const Grid& g, int i, int j0, cx<T> (&nx)[K]) {
-    cx<T> a, c;
-#pragma unroll 1
-    for (int r = j0 - R; r < j0 + R; ++r) {
-      fetch(vs, g.at(i, r), nx);
-      sums(nx, a, c);
-      shift_in(a, c);
-    }
-    fetch(vs, g.at(i, j0 + R), nx);
-  }
-  // ring advance for output row m: uses the fetched row m+R, fetches row
-  // m+R+1 (the next iteration's) before the arithmetic
-  __device__ __forceinline__ void advance(const cx<T>* __restrict__ vs, const Grid& g, int i, int m, int j1,
-                                          cx<T> (&nx)[K]) {
-    cx<T> cur[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) cur[k] = nx[k];
-    if (m + 1 < j1) fetch(vs, g.at(i, m + R + 1), nx);
-    cx<T> a, c;
-    sums(cur, a, c);
-    shift_in(a, c);
-  }
-  __device__ __forceinline__ void shift_in(cx<T> a, cx<T> c) {
 #pragma unroll
     for (int k = 0; k < K - 1; ++k) {
       s1[k] = s1[k + 1];
@@ -111,18 +125,33 @@ template <class T, int R> struct KRing {
   }
 };
 
+// Common prologue.  A warp owns 32 columns of one chunk of rows; `has`: the
+// warp has work; `col`: the lane's column is inside the grid.
 #define KPRO                                                                  \
   __shared__ double sh[NVMAX * 32];                                           \
+  __shared__ __align__(16) cx<T> ksm[KW][KSL][32 + 2 * R];                    \
   const int rhs = blockIdx.z;                                                 \
   if (active && !active[rhs]) return;                                         \
   const long long off = (long long)rhs * g.vstride;                           \
-  const int gw = blockIdx.x * KW + (threadIdx.x >> 5);                       \
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;                  \
+  const int gw = blockIdx.x * KW + wib;                                       \
   const bool has = gw < kg.ncw * kg.nchunks;                                  \
-  const int i = (has ? gw % kg.ncw : 0) * 32 + (threadIdx.x & 31);            \
+  const int cw0 = (has ? gw % kg.ncw : 0) * 32, i = cw0 + lane;               \
   const int j0 = (has ? gw / kg.ncw : 0) * kg.ch, j1 = min(j0 + kg.ch, g.ny + 1); \
   const bool col = has && i <= g.nx;                                          \
-  const int nblk = gridDim.x, blk = blockIdx.x;                               \
-  const bool t0 = threadIdx.x == 0;
+  const int nblk = gridDim.x, blk = blockIdx.x;
+
+#define KMARCH_SETUP(vsrc)                                                    \
+  KRing<T, R> ring;                                                           \
+  ring.init(op, i, col);                                                      \
+  ring.vs = (vsrc);                                                           \
+  ring.g = g;                                                                 \
+  ring.cw0 = cw0;                                                             \
+  ring.lane = lane;                                                           \
+  ring.sm = &ksm[wib][0][0];                                                  \
+  ring.r0 = j0 - R;                                                           \
+  const int last = j1 + R - 1;                                                \
+  ring.prime(last);
 
 // u0 = b - A x, partial |u0|^2 (as g_init)
 template <class T, int R>
@@ -131,23 +160,24 @@ __global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op
                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
   KPRO
   T a0[1] = {T(0)};
-  if (col) {
-    const cx<T>* xs = x + off;
-    KRing<T, R> ring;
-    ring.init(op, i);
-    cx<T> nx[KRing<T, R>::K];
-    ring.prime(xs, g, i, j0, nx);
+  if (has) {
+    KMARCH_SETUP(x + off)
 #pragma unroll 1
-    for (int m = j0; m < j1; ++m) {
-      ring.advance(xs, g, i, m, j1, nx);
-      const int p = g.at(i, m);
-      const cx<T> r = sub<T>(b[off + p], ring.combine(op, m));
-      u0[off + p] = r;
-      a0[0] += abs2<T>(r);
+    for (int r = j0 - R; r <= last; ++r) {
+      ring.advance(r, last);
+      const int m = r - R;
+      if (m >= j0 && col) {
+        const int p = g.at(i, m);
+        const cx<T> res = sub<T>(b[off + p], ring.combine(op, m));
+        u0[off + p] = res;
+        a0[0] += abs2<T>(res);
+      }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   double v[1];
-  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(st + (long long)rhs * GS, v);
+  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && threadIdx.x == 0)
+    fin_init<T>(st + (long long)rhs * GS, v);
 }
 
 // w = s_J A u_J; partial dots <u_l, w>, l <= J (as g_arn_a)
@@ -163,27 +193,27 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
   T acc[2 * (J + 1)];
 #pragma unroll
   for (int k = 0; k < 2 * (J + 1); ++k) acc[k] = T(0);
-  if (col) {
+  if (has) {
     const T sJ = (T)S[G_S + J];
     const cx<T>* us[3] = {u0 + off, u1 + off, u2 + off};
-    const cx<T>* vs = uJ + off;
-    KRing<T, R> ring;
-    ring.init(op, i);
-    cx<T> nx[KRing<T, R>::K];
-    ring.prime(vs, g, i, j0, nx);
+    KMARCH_SETUP(uJ + off)
 #pragma unroll 1
-    for (int m = j0; m < j1; ++m) {
-      ring.advance(vs, g, i, m, j1, nx);
-      const int p = g.at(i, m);
-      const cx<T> a = scl<T>(sJ, ring.combine(op, m));
-      w[off + p] = a;
+    for (int r = j0 - R; r <= last; ++r) {
+      ring.advance(r, last);
+      const int m = r - R;
+      if (m >= j0 && col) {
+        const int p = g.at(i, m);
+        const cx<T> a = scl<T>(sJ, ring.combine(op, m));
+        w[off + p] = a;
 #pragma unroll
-      for (int l = 0; l <= J; ++l) {
-        const cx<T> d = cmul<T>(us[l][p], a);
-        acc[2 * l] += d.x;
-        acc[2 * l + 1] += d.y;
+        for (int l = 0; l <= J; ++l) {
+          const cx<T> d = cmul<T>(us[l][p], a);
+          acc[2 * l] += d.x;
+          acc[2 * l + 1] += d.y;
+        }
       }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   double v[2 * (J + 1)];
   if (reduce_last<2 * (J + 1), T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
