@@ -21,8 +21,10 @@ matrices with scipy, and follows the paper's definitions step by step:
                    (Definition def2s) for the Table conv1 / opt1 checks.
 * ``gradient``  -- adjoint-state gradient of a receiver misfit with respect
                    to squared slowness, by direct sparse solves.
+* ``krylov``    -- the cycle as the right preconditioner of a restarted
+                   flexible GMRES (the Krylov use recalled in Sec. 1).
 
 Readings of passages the paper leaves open are documented at each function
 (shift sign, boundary rows, edge rule of Eq. (xex), pre/post smoothing split).
 """
-from . import problem, transfer, hierarchy, smoothers, cycle, analysis, gradient  # noqa: F401
+from . import problem, transfer, hierarchy, smoothers, cycle, analysis, gradient, krylov  # noqa: F401

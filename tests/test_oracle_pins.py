@@ -347,3 +347,68 @@ def test_adjoint_gradient_matches_central_differences():
         fd = (Lp - Lm) / (2 * eps)
         ad = float(np.sum(g * d))
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+# ---------------------------------------------------------------- Krylov acceleration (FGMRES with the cycle)
+
+
+def test_fgmres_cycle_minimises_over_the_preconditioned_space():
+    """One FGMRES(5) restart cycle: the result is the least-squares minimiser
+    of ||b - A (x0 + Z y)|| over the preconditioned vectors Z it built (checked
+    with lstsq, no Arnoldi), and the Givens residual estimate equals the true
+    residual norm."""
+    from oracle import krylov
+    n = 12
+    A = problem.helmholtz_matrix(n, n, 1 / n, 7.5, 0.0).tocsr()
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(169) + 1j * rng.standard_normal(169)
+    x0 = rng.standard_normal(169) + 1j * rng.standard_normal(169)
+    D = sp.diags(1.0 / A.diagonal())           # a fixed preconditioner (diagonal scaling)
+    x1, k, hist, Z = krylov.fgmres_cycle(A, lambda v: D @ v, x0, b, 5, 1e-300, np.linalg.norm(b))
+    assert k == 5 and Z.shape == (169, 5)
+    r0 = b - A @ x0
+    y = np.linalg.lstsq(A @ Z, r0, rcond=None)[0]
+    best = np.linalg.norm(r0 - A @ (Z @ y))
+    got = np.linalg.norm(b - A @ x1)
+    assert abs(got - best) <= 1e-10 * np.linalg.norm(r0)
+    assert abs(hist[-1] * np.linalg.norm(b) - got) <= 1e-10 * np.linalg.norm(r0)
+    assert all(hist[q + 1] <= hist[q] * (1 + 1e-12) for q in range(len(hist) - 1))
+
+
+def test_fgmres_special_preconditioners():
+    """Identity preconditioner: one FGMRES(3) cycle is GMRES(3) (the Sec. 5.3
+    smoother step, computed by lstsq-free Arnoldi there).  Exact inverse as
+    preconditioner: one step solves the system."""
+    from oracle import krylov
+    n = 12
+    A = problem.helmholtz_matrix(n, n, 1 / n, 7.5, 0.0).tocsr()
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal(169) + 1j * rng.standard_normal(169)
+    x0 = rng.standard_normal(169) + 1j * rng.standard_normal(169)
+    x1, k, _, _ = krylov.fgmres_cycle(A, lambda v: v, x0, b, 3, 1e-300, np.linalg.norm(b))
+    assert k == 3
+    ref = smoothers.gmres_step(A, x0, b, 3)
+    assert np.linalg.norm(x1 - ref) <= 1e-10 * np.linalg.norm(ref)
+    lu = spla.splu(A.tocsc())
+    x2, k2, hist, _ = krylov.fgmres_cycle(A, lu.solve, x0, b, 5, 1e-12, np.linalg.norm(b))
+    assert k2 == 1 and hist[0] <= 1e-12
+    assert np.linalg.norm(b - A @ x2) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_fgmres_with_the_cycle_needs_fewer_cycles():
+    """The cycle as a preconditioner (FGMRES(10), GMRES(3) V(1,1), beta2 = 1/k)
+    reaches the tolerance with fewer cycles than the stand-alone method, and
+    its true relative residual meets the tolerance."""
+    from oracle import krylov
+    n, k = 48, 30.0
+    H = hierarchy.build_hierarchy(n, n, 1 / n, k, 1 / k)
+    b = np.zeros((n + 1) ** 2, dtype=complex)
+    b[(n // 2) * (n + 1) + n // 2] = n * n
+    opt = cycle.CycleOptions(1, "gmres3", 1, 1, 4.5)
+    alone = cycle.mg_solve(H, b, 1e-6, opt)
+    fg = krylov.fgmres_solve(H, b, 1e-6, opt, 10)
+    assert alone.converged and fg.converged
+    assert fg.relres <= 1e-6
+    assert np.linalg.norm(b - H.A[0] @ fg.x) / np.linalg.norm(b) <= 1e-6
+    assert fg.cycles < alone.cycles
+    assert len(fg.history) == fg.cycles
