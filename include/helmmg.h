@@ -99,12 +99,24 @@ typedef struct {
                        sides and the other problems of a ragged batch (a row
                        march keeps each warp on one strip, which needs that
                        much work to fill the GPU)                           */
+  int krylov;       /* 0 = the stand-alone cycle iteration (the paper's method);
+                       m in 1..32 = restarted flexible GMRES(m) on the fine
+                       operator with one cycle (from zero) as the right
+                       preconditioner, the Krylov use recalled in Sec. 1
+                       (precision 0 or 1: FP64 Arnoldi basis, rotations and
+                       update; the preconditioned vectors in the cycle's
+                       precision).  max_cycles then caps preconditioner
+                       applications, the cycle counts report them, mg_history
+                       holds the residual estimate after each one, and the
+                       stopping test is the true relative residual at a
+                       restart.  Memory: m+1 FP64 and m cycle-precision fine
+                       grids per right-hand side.                           */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
  * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0, fuse 1,
- * tile_rows 0; march -1; default stream. */
+ * tile_rows 0; march -1; krylov 0; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).

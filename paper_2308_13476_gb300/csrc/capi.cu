@@ -117,11 +117,18 @@ struct mg_ctx {
   int done = 0;                    // cycles of the current solve
   std::vector<mg_ctx*> sub;        // ragged batch: one handle per problem
   cudaStream_t own_stream = nullptr;
+  // FGMRES(m) outer loop (opt.krylov = m > 0)
+  FgArgs fg{};                     // buffers and geometry; per-solve fields set in solve_fgmres
+  cudaGraph_t pgraph = nullptr;    // one preconditioning cycle (no test, no update)
+  cudaGraphExec_t pexec = nullptr;
+  long long pgraph_kernels = 0;
 
   ~mg_ctx() {
     for (mg_ctx* p : sub) delete p;
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
+    if (pexec) cudaGraphExecDestroy(pexec);
+    if (pgraph) cudaGraphDestroy(pgraph);
     for (void* p : allocs) cudaFree(p);
     if (h_n_active) cudaFreeHost(h_n_active);
     if (cap) cudaStreamDestroy(cap);
@@ -517,6 +524,7 @@ void mg_default_options(mg_options* o) {
   o->fuse = 1;
   o->tile_rows = 0;
   o->march = -1;
+  o->krylov = 0;
   o->stream = nullptr;
 }
 
@@ -725,6 +733,25 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  if (o.krylov > 0) {   // FGMRES(m) basis, preconditioned vectors and scalars
+    FgArgs& a = c->fg;
+    const int m = o.krylov;
+    a.g = g0;
+    a.B = c->B;
+    a.m = m;
+    a.vlen = g0.vstride * c->B;
+    fg_geometry(g0, c->B, !mixed, a);
+    const size_t zb = mixed ? sizeof(float2) : sizeof(double2);
+    CK(dalloc(c, (void**)&a.V, sizeof(double2) * (size_t)a.vlen * (m + 1)));
+    CK(dalloc(c, &a.Z, zb * (size_t)a.vlen * m));
+    CK(dalloc(c, (void**)&a.X, sizeof(double2) * (size_t)a.vlen));
+    CK(dalloc(c, (void**)&a.b, sizeof(double2) * (size_t)a.vlen));
+    a.sd = FgLayout{m}.size();
+    CK(dalloc(c, (void**)&a.S, sizeof(double) * (size_t)a.sd * c->B));
+    CK(dalloc(c, (void**)&a.kst, sizeof(int) * 2 * c->B));
+    CK(dalloc(c, (void**)&a.partial, sizeof(double) * (size_t)a.nvp * a.nbr * c->B));
+    CK(dalloc(c, (void**)&a.tickets, sizeof(unsigned) * c->B));
+  }
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   if (o.smoother == 1) {
     CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
@@ -755,6 +782,8 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.fuse != 0 && o.fuse != 1) FAIL(MG_EINVAL, "fuse must be 0 or 1");
   if (o.tile_rows < 0 || o.tile_rows > RYMAX) FAIL(MG_EINVAL, "tile_rows must be in 0..4");
   if (o.march < -1 || o.march > 1) FAIL(MG_EINVAL, "march must be -1, 0 or 1");
+  if (o.krylov < 0 || o.krylov > FG_MAXM) FAIL(MG_EINVAL, "krylov must be in 0..%d", FG_MAXM);
+  if (o.krylov > 0 && o.precision == 2) FAIL(MG_EINVAL, "the FGMRES outer loop needs precision 0 or 1");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
@@ -834,6 +863,149 @@ static mg_status capture(mg_ctx* c) {
     CK(cudaGraphNodeGetType(nd, &t));
     c->graph_kernels += t == cudaGraphNodeTypeKernel;
   }
+  return MG_OK;
+}
+
+// Graph of one preconditioning cycle for the FGMRES outer loop: the cycle
+// from the level-0 iterate (zeroed by the prep kernel) on the level-0
+// right-hand side, the result left in the level-0 iterate.
+static mg_status capture_precond(mg_ctx* c) {
+  if (c->pexec) return MG_OK;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  if (c->opt.precision == 0) {
+    Emit<double> e{c, c->cap, {}, {}, c->lc, &c->plan64};
+    e.init();
+    e.cycle(0);
+    if (e.cur[0] != c->v64[0].x) launch_copy_masked<double>(c->lev[0].g, e.cur[0], c->v64[0].x, c->B, c->active, c->cap);
+  } else {
+    Emit<float> e{c, c->cap, {}, {}, c->lc, &c->plan32};
+    e.init();
+    e.cycle(0);
+    if (e.cur[0] != c->v32[0].x) launch_copy_masked<float>(c->lev[0].g, e.cur[0], c->v32[0].x, c->B, c->active, c->cap);
+  }
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (e != cudaSuccess) FAIL(MG_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  c->pgraph = g;
+  CK(cudaGraphInstantiate(&c->pexec, g, 0));
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  c->pgraph_kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    c->pgraph_kernels += t == cudaGraphNodeTypeKernel;
+  }
+  return MG_OK;
+}
+
+// FGMRES(m) with the cycle as the right preconditioner (fgmres.cu): every
+// right-hand side runs its own restart cycles; the steps of one restart
+// cycle run in lockstep over the batch, a RHS leaving it (residual estimate
+// at tol, breakdown, or its step allowance used) is masked out of the
+// remaining steps, and all of them take the update and the restart test
+// together.  The host polls the count of RHS still inside the restart cycle
+// after every step.
+static mg_status solve_fgmres(mg_ctx* c, const void* rhs, void* x, double tol, int conj, int* cycles_out,
+                              double* relres_out) {
+  if (!rhs || !x) FAIL(MG_EINVAL, "rhs and x must be device pointers");
+  if (!(tol > 0)) FAIL(MG_EINVAL, "tol must be > 0");
+  cudaStream_t s = (cudaStream_t)c->opt.stream;
+  const Grid& g0 = c->lev[0].g;
+  const int B = c->B, m = c->opt.krylov;
+  const bool mixed = c->opt.precision == 1;
+  mg_status st = capture_precond(c);
+  if (st != MG_OK) return st;
+  FgArgs a = c->fg;
+  a.c0 = c->hc0d;
+  a.kf = c->kf64;
+  a.active = c->active;
+  a.state = c->state;
+  a.cycles = c->cycles;
+  a.relres = c->relres;
+  a.hist = c->hist;
+  a.hist_len = c->hist_len;
+  a.n_active = c->n_active;
+  a.bnorm = c->bnorm;
+  a.tol = tol;
+  a.max_cycles = c->opt.max_cycles;
+  launch_pack<double>(g0, (const double2*)rhs, (double2*)a.b, B, conj, s);
+  launch_pack<double>(g0, (const double2*)x, a.X, B, conj, s);
+  launch_vecnorm_fin<double>(g0, a.b, B, c->bnorm, c->partial, c->tickets, s);
+  std::vector<double> bn(B);
+  CK(cudaMemcpyAsync(bn.data(), c->bnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<int> zero(B, 0), stt(B);
+  std::vector<double> bsafe(B);
+  for (int b = 0; b < B; ++b) {
+    bsafe[b] = bn[b] > 0 ? bn[b] : 1.0;
+    stt[b] = bn[b] > 0 ? 0 : 1;
+    if (bn[b] == 0.0) CK(cudaMemsetAsync(a.X + (size_t)b * g0.vstride, 0, sizeof(double2) * g0.vstride, s));
+  }
+  CK(cudaMemcpyAsync(c->active, zero.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->state, stt.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->cycles, zero.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->bnorm, bsafe.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(a.kst, 0, sizeof(int) * 2 * B, s));
+  if (c->coop.bar) CK(cudaMemsetAsync(c->coop.bar, 0, sizeof(unsigned) * 2, s));
+  CK(cudaMemsetAsync(c->relres, 0, sizeof(double) * B, s));
+  CK(cudaMemsetAsync(c->hist, 0, sizeof(double) * (size_t)c->hist_len * B, s));
+  long long launches = 3, graphs = 0;   // 2 pack + norm
+  cx<float>* cb32 = mixed ? c->v32[0].b : nullptr;
+  cx<float>* cx32 = mixed ? c->v32[0].x : nullptr;
+  while (true) {
+    CK(cudaMemsetAsync(c->n_active, 0, sizeof(int) * 2, s));
+    launch_fg_restart(a, s);
+    ++launches;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->h_n_active[0] == 0) break;
+    for (int j = 0; j < m; ++j) {
+      if (mixed) launch_fg_prep<float>(a, j, cb32, cx32, s);
+      else launch_fg_prep<double>(a, j, c->v64[0].b, c->v64[0].x, s);
+      CK(cudaGraphLaunch(c->pexec, s));
+      if (mixed) {
+        launch_fg_dots<float>(a, j, cx32, s);
+        launch_fg_orth<float>(a, j, s);
+      } else {
+        launch_fg_dots<double>(a, j, c->v64[0].x, s);
+        launch_fg_orth<double>(a, j, s);
+      }
+      launches += 3 + c->pgraph_kernels;
+      ++graphs;
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (c->h_n_active[1] != 0) FAIL(MG_ETIMEOUT, "a grid-wide barrier of the cooperative cycle kernel timed out");
+      if (c->h_n_active[0] == 0) break;
+    }
+    if (mixed) launch_fg_update<float>(a, s);
+    else launch_fg_update<double>(a, s);
+    ++launches;
+  }
+  launch_unpack<double>(g0, a.X, (double2*)x, B, conj, s);
+  ++launches;
+  c->last_launches = launches;
+  c->last_graphs = graphs;
+  std::vector<int> cyc(B);
+  std::vector<double> rr(B);
+  CK(cudaMemcpyAsync(stt.data(), c->state, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(cyc.data(), c->cycles, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rr.data(), c->relres, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  bool div = false, maxit = false;
+  for (int b = 0; b < B; ++b) {
+    if (cycles_out) cycles_out[b] = cyc[b];
+    if (relres_out) relres_out[b] = rr[b];
+    div |= stt[b] == 2;
+    maxit |= stt[b] == 0;
+  }
+  if (div) FAIL(MG_EDIVERGED, "relative residual not finite");
+  if (maxit) FAIL(MG_EMAXIT, "max_cycles (%d) reached before tol", c->opt.max_cycles);
   return MG_OK;
 }
 
@@ -955,6 +1127,24 @@ static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, i
   const int P = (int)c->sub.size();
   std::vector<size_t> off(P + 1, 0);
   for (int p = 0; p < P; ++p) off[p + 1] = off[p] + (size_t)(c->sub[p]->nx + 1) * (c->sub[p]->ny + 1);
+  if (c->opt.krylov > 0) {   // FGMRES: the problems one after the other
+    mg_status worst = MG_OK;
+    std::string msg;
+    long long launches = 0;
+    for (int p = 0; p < P; ++p) {
+      mg_status st = solve_fgmres(c->sub[p], (const double2*)rhs + off[p], (double2*)x + off[p], tol, conj,
+                                  cycles_out ? cycles_out + p : nullptr, relres_out ? relres_out + p : nullptr);
+      launches += c->sub[p]->last_launches;
+      if (st != MG_OK && (worst == MG_OK || st == MG_EDIVERGED)) {
+        worst = st;
+        msg = g_err;
+      }
+      if (st != MG_OK && st != MG_EMAXIT && st != MG_EDIVERGED) return st;
+    }
+    c->last_launches = launches;
+    if (worst != MG_OK) FAIL(worst, "problem(s) of the ragged batch: %s", msg.c_str());
+    return MG_OK;
+  }
   for (int p = 0; p < P; ++p) {
     mg_status st = solve_begin(c->sub[p], (const double2*)rhs + off[p], (double2*)x + off[p], tol, conj);
     if (st != MG_OK) return st;
@@ -990,6 +1180,7 @@ static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, i
 static mg_status solve_impl(mg_ctx* c, const void* rhs, void* x, double tol, int* cycles_out, double* relres_out,
                             int conj) {
   if (!c->sub.empty()) return solve_ragged(c, rhs, x, tol, cycles_out, relres_out, conj);
+  if (c->opt.krylov > 0) return solve_fgmres(c, rhs, x, tol, conj, cycles_out, relres_out);
   mg_status st = solve_begin(c, rhs, x, tol, conj);
   if (st != MG_OK) return st;
   cudaStream_t s = (cudaStream_t)c->opt.stream;

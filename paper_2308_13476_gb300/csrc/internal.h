@@ -237,6 +237,61 @@ void launch_ff_unpack(const Grid& g, const void* v, double2* user, int B, int co
 void launch_ff_norm(const Grid& g, const void* v, int B, double* out, double* partial, unsigned* tickets,
                     cudaStream_t s);
 
+// Flexible GMRES(m) outer loop with one cycle as the right preconditioner
+// (fgmres.cu).  V: m+1 FP64 basis vectors, Z: m preconditioned vectors in the
+// cycle's precision, vector q of RHS b at base + q * vlen + b * vstride.
+constexpr int FG_MAXM = 32;
+// Per-RHS FP64 scalars of the restart cycle: the rotated Hessenberg columns
+// (column j, row i), the Gram matrix of V (row a, column b: <v_a, v_b>), the
+// rotations (cs real, sn complex), g, y, beta and the divisor of the next
+// basis vector (h_{j+1,j}, or beta at a restart); complex values as (re, im).
+struct FgLayout {
+  int m;
+  __host__ __device__ int h(int j, int i) const { return 2 * (j * (m + 1) + i); }
+  __host__ __device__ int gram(int a, int b) const { return 2 * m * (m + 1) + 2 * (a * (m + 1) + b); }
+  __host__ __device__ int cs(int i) const { return 2 * m * (m + 1) + 2 * (m + 1) * (m + 1) + i; }
+  __host__ __device__ int sn(int i) const { return cs(m) + 2 * i; }
+  __host__ __device__ int g(int i) const { return sn(m) + 2 * i; }
+  __host__ __device__ int y(int i) const { return g(m + 1) + 2 * i; }
+  __host__ __device__ int beta() const { return y(m); }
+  __host__ __device__ int div() const { return beta() + 1; }
+  __host__ __device__ int size() const { return beta() + 2; }
+};
+struct FgArgs {
+  Grid g;                  // fine level
+  Op0Consts<double> c0;    // fine operator (FP64)
+  const double* kf;
+  int B, m;
+  int nbr, ncx, ns, nvp;   // blocks per RHS, strip columns, strips, values per partial record
+  long long vlen;          // g.vstride * B
+  double2* V;
+  void* Z;
+  double2* X;
+  const double2* b;
+  double* S;               // [B][sd] scalars (FgLayout)
+  int sd;
+  int* kst;                // [B][2]: steps of the current restart cycle, steps allowed in it
+  int* active;             // 1 while the RHS is inside a restart cycle
+  int* state;              // 0 running, 1 converged, 2 not finite
+  int* cycles;             // preconditioner applications
+  double* relres;          // true relative residual at the last restart
+  double* hist;            // residual estimate after every application
+  int hist_len;
+  int* n_active;
+  const double* bnorm;
+  double tol;
+  int max_cycles;
+  double* partial;         // [B][nvp][nbr]
+  unsigned* tickets;       // [B], 0 at rest
+};
+// Strip geometry and blocks per RHS (nbr, ncx, ns, nvp) for a fine grid.
+void fg_geometry(const Grid& g, int B, bool fp64z, FgArgs& a);
+void launch_fg_restart(const FgArgs& a, cudaStream_t s);
+template <class T> void launch_fg_prep(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s);
+template <class T> void launch_fg_dots(const FgArgs& a, int j, const cx<T>* z, cudaStream_t s);
+template <class T> void launch_fg_orth(const FgArgs& a, int j, cudaStream_t s);
+template <class T> void launch_fg_update(const FgArgs& a, cudaStream_t s);
+
 // Gradient of the receiver misfit (kernels_level.cu).
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u,
                      const double2* lam, int nsrc, double* g, cudaStream_t s);

@@ -52,3 +52,28 @@ def test_default_options_and_error_paths_without_gpu(lib_path):
     assert st == hm.MG_EINVAL and h.value is None
     assert b"nx, ny >= 2" in lib.mg_last_error()
     assert lib.mg_destroy(None) == hm.MG_OK
+
+
+def test_options_struct_matches_the_header():
+    """The ctypes mirror of mg_options lists the header's fields in order."""
+    import paper_2308_13476_gb300 as hm
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct \{(.*?)\} mg_options;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(?:int|double|void\s*\*)\s*\**\s*([a-z_0-9]+)\s*;", body)
+    assert fields == [f[0] for f in hm.MgOptions._fields_]
+
+
+def test_krylov_option_validated_without_gpu(lib_path):
+    import paper_2308_13476_gb300 as hm
+    lib = hm.load_library()
+    o = hm.mg_default_options()
+    assert o.krylov == 0
+    h = ctypes.c_void_p()
+    o.krylov = 33
+    assert lib.mg_setup(ctypes.byref(h), 8, 8, 0.1, None, 5.0, 0.7, 0, ctypes.byref(o)) == hm.MG_EINVAL
+    assert b"krylov" in lib.mg_last_error()
+    o.krylov, o.precision = 4, 2
+    assert lib.mg_setup(ctypes.byref(h), 8, 8, 0.1, None, 5.0, 0.7, 0, ctypes.byref(o)) == hm.MG_EINVAL
+    assert b"precision 0 or 1" in lib.mg_last_error()
+    assert h.value is None
