@@ -56,6 +56,10 @@ def parse():
                         "workloads: layered velocity model at --freq Hz, a ragged batch of 32 problems, the "
                         "adjoint gradient of a receiver misfit")
     p.add_argument("--freq", type=float, default=10.0, help="layered workload: frequency in Hz (10, 20, 40)")
+    p.add_argument("--transfer", default="bezier", choices=["bezier", "linear"],
+                   help="inter-grid transfers: Eq. (xex) or linear interpolation (ablation)")
+    p.add_argument("--krylov", type=int, default=0,
+                   help="m > 0: restarted FGMRES(m) with one cycle as the right preconditioner")
     p.add_argument("--march", type=int, default=-1, choices=[-1, 0, 1],
                    help="GMRES(3) as row/column marches: 1 always, 0 never, -1 by level size (library default)")
     p.add_argument("--probe", action="store_true",
@@ -106,6 +110,9 @@ def workload_config(a):
         "rhs_per_gpu": a.batch,
         "smoother": a.smoother,
         "cycle": f"{a.cycle}({a.nu},{a.nu})",
+        "transfer": "Eq. (xex) higher-order" if a.transfer == "bezier" else "linear interpolation (ablation)",
+        "outer": (f"FGMRES({a.krylov}), one cycle from zero as the right preconditioner; cycles = "
+                  f"preconditioner applications" if a.krylov else "stand-alone cycle iteration"),
         "beta2": a.beta2,
         "precision": a.precision,
         "tol": a.tol,
@@ -161,15 +168,23 @@ class ClockSampler:
 
 
 def oracle_cycle_seconds(a, ncycles):  # noqa: D401
-    """Time ``ncycles`` oracle cycles on the full workload (setup excluded)."""
+    """Time ``ncycles`` oracle cycles on the full workload (setup excluded);
+    with --krylov, ``ncycles`` FGMRES steps (each one preconditioning cycle
+    plus its Arnoldi work) of one restart cycle."""
     import synth
     from oracle import cycle as oc
     from oracle import hierarchy as oh
     h = 1.0 / a.n
     b = (synth.source_row(a.n, a.n, h, a.batch)[0] if a.batch > 1 else synth.point_source(a.n, a.n, h)).ravel()
-    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2)
+    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2, kind=a.transfer)
     opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
     x = np.zeros_like(b)
+    if a.krylov:
+        from oracle import krylov as okr
+        t0 = time.perf_counter()
+        okr.fgmres_cycle(H.A[0], lambda v: oc.mg_cycle(H, 0, np.zeros_like(v), v, opt), x, b, ncycles, 0.0,
+                         np.linalg.norm(b))
+        return (time.perf_counter() - t0) / ncycles
     t0 = time.perf_counter()
     for _ in range(ncycles):
         x = oc.mg_cycle(H, 0, x, b, opt)
@@ -189,17 +204,25 @@ def run_reference(a):
     from oracle import hierarchy as oh
     h = 1.0 / a.n
     b = (synth.source_row(a.n, a.n, h, a.batch)[0] if a.batch > 1 else synth.point_source(a.n, a.n, h)).ravel()
-    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2)
+    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2, kind=a.transfer)
     opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
     x = np.zeros_like(b)
-    for _ in range(a.warmup):
-        x = oc.mg_cycle(H, 0, x, b, opt)
-        _ = np.linalg.norm(b - H.A[0] @ x)
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        x = oc.mg_cycle(H, 0, x, b, opt)
-        _ = np.linalg.norm(b - H.A[0] @ x)
-    tc = (time.perf_counter() - t0) / a.steps
+    if a.krylov:   # one FGMRES step (a preconditioning cycle and its Arnoldi work) per step
+        from oracle import krylov as okr
+        M = lambda v: oc.mg_cycle(H, 0, np.zeros_like(v), v, opt)  # noqa: E731
+        okr.fgmres_cycle(H.A[0], M, x, b, a.warmup, 0.0, np.linalg.norm(b))
+        t0 = time.perf_counter()
+        okr.fgmres_cycle(H.A[0], M, x, b, a.steps, 0.0, np.linalg.norm(b))
+        tc = (time.perf_counter() - t0) / a.steps
+    else:
+        for _ in range(a.warmup):
+            x = oc.mg_cycle(H, 0, x, b, opt)
+            _ = np.linalg.norm(b - H.A[0] @ x)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            x = oc.mg_cycle(H, 0, x, b, opt)
+            _ = np.linalg.norm(b - H.A[0] @ x)
+        tc = (time.perf_counter() - t0) / a.steps
     cycles_needed = _cycles_from_cache(a)
     N = (a.n + 1) ** 2 * a.batch
     value = N / (tc * a.batch * cycles_needed) if cycles_needed else None
@@ -222,7 +245,8 @@ def _cycles_from_cache(a):
     p = os.path.join(ROOT, "oracle", "bench_cycles.json")
     try:
         d = json.load(open(p))
-        return int(d.get(f"{a.k:g}/{a.n}/{a.smoother}/{a.cycle}{a.nu}/{a.beta2:g}"))
+        return int(d.get(f"{a.k:g}/{a.n}/{a.smoother}/{a.cycle}{a.nu}/{a.beta2:g}" +
+                         (f"/fgmres{a.krylov}" if a.krylov else "") + ("/linear" if a.transfer == "linear" else "")))
     except Exception:
         return None
 
@@ -264,7 +288,8 @@ def run_ours(a):
     def make(precision, shapes=None):
         t0 = time.perf_counter()
         s = hm.Solver(n, n, h, k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
-                      precision=precision, batch=a.batch, max_cycles=20000, march=a.march, **(shapes or {}))
+                      precision=precision, batch=a.batch, max_cycles=20000, march=a.march, krylov=a.krylov,
+                      transfer=a.transfer, **(shapes or {}))
         torch.cuda.synchronize()
         return s, time.perf_counter() - t0
 
@@ -313,7 +338,7 @@ def run_ours(a):
     ms_e2e, _, _, _ = timed_solves(s, a.steps, e2e=True)
     e2e_value, _ = job_throughput(sum(ms_e2e) / 1e3, N * a.batch * a.steps)
     # roofline of the dominant kernel, timed live with CUDA events on the library's stream
-    what = 0 if a.smoother == "jacobi" else 4
+    what = 5 if a.krylov else (0 if a.smoother == "jacobi" else 4)
     kms, kbytes = s.profile(what, 0, reps=20)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -321,13 +346,15 @@ def run_ours(a):
     achieved = kbytes / (kms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": step_traffic(a, what),
-            "kernel": ("level-0 weighted-Jacobi sweep" if what == 0 else
-                       "level-0 GMRES(3) smoothing step: 4 row-march passes + update, 16 vector passes") +
+            "kernel": ({0: "level-0 weighted-Jacobi sweep",
+                        4: "level-0 GMRES(3) smoothing step: 4 row-march passes + update, 16 vector passes",
+                        5: f"last FGMRES({a.krylov}) Arnoldi step (MGS-coefficient pass + new-vector pass, "
+                           f"{2 * a.krylov + 1} FP64 and 3 cycle-precision vector passes)"}[what]) +
                       f" ({'complex128' if a.precision == 'fp64' else 'complex64'}), "
                       f"{kbytes / 1e6:.1f} MB algorithmic per step, {kms * 1e3:.0f} us per step, "
                       f"peak = measured hbm_gbs"}
     extra = {"setup_s": setup_s, "cycles": cyc, "relres": rr}
-    if not a.no_ff_line and a.precision == "mixed":   # the float-float outer loop, same launch shapes
+    if not a.no_ff_line and a.precision == "mixed" and not a.krylov:   # float-float outer loop, same shapes
         s.close()
         sff, _ = make("mixed-ff", tuned)
         timed_solves(sff, 1)

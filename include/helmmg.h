@@ -103,20 +103,27 @@ typedef struct {
                        m in 1..32 = restarted flexible GMRES(m) on the fine
                        operator with one cycle (from zero) as the right
                        preconditioner, the Krylov use recalled in Sec. 1
-                       (precision 0 or 1: FP64 Arnoldi basis, rotations and
-                       update; the preconditioned vectors in the cycle's
-                       precision).  max_cycles then caps preconditioner
+                       (precision 0 or 1).  The restart residual, x, the
+                       update and all scalars are FP64; the basis, the
+                       preconditioned vectors and the Arnoldi passes take the
+                       cycle's precision (precision 1: each restart cycle is
+                       an FP32 FGMRES correction of the FP64 residual).  max_cycles then caps preconditioner
                        applications, the cycle counts report them, mg_history
                        holds the residual estimate after each one, and the
                        stopping test is the true relative residual at a
-                       restart.  Memory: m+1 FP64 and m cycle-precision fine
-                       grids per right-hand side.                           */
+                       restart.  Memory: 2m+1 fine grids in the cycle's
+                       precision and 2 FP64 ones per right-hand side.      */
+  int transfer;     /* inter-grid transfers, both directions (R = P^T / 4) and
+                       the Galerkin coarsening: 0 = the higher-order Eq. (xex)
+                       (paper default); 1 = linear interpolation, the
+                       "Linear" column of Table conv1 (an ablation: the paper
+                       finds the two-grid map no longer contracting)      */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
  * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0, fuse 1,
- * tile_rows 0; march -1; krylov 0; default stream. */
+ * tile_rows 0; march -1; krylov 0; transfer 0; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).
@@ -198,8 +205,9 @@ mg_status mg_apply(mg_handle h, int level, const void* x, void* y);
 mg_status mg_get_stencil(mg_handle h, int level, void* out);
 
 /* Relative residual history of the last solve: hist[b * cap + c] is the
- * relative residual of RHS b after cycle c+1 (c < min(cycles, cap)).
- * hist: host double[B * cap]. */
+ * relative residual of RHS b after cycle c+1 (c < min(cycles, cap)); with
+ * krylov > 0, the FGMRES residual estimate after preconditioner
+ * application c+1.  hist: host double[B * cap]. */
 mg_status mg_history(mg_handle h, double* hist, int cap);
 
 /* ---- instrumentation ---- */
@@ -210,7 +218,11 @@ mg_status mg_history(mg_handle h, double* hist, int cap);
  * kernels the cycle runs for that level: on level 0, when it runs as row
  * marches (option march), four row-march passes and the update, 16 vector
  * reads and writes per node; otherwise eight passes, 28; needs
- * smoother = 1), on level
+ * smoother = 1), 5 the last Arnoldi step of an FGMRES(m) restart cycle
+ * (j = m - 1: the pass for the m MGS coefficients and the pass for the new
+ * basis vector, 2m + 4 vector reads and writes per node in the cycle's
+ * precision; needs krylov > 0 and level 0; it marks every right-hand side
+ * active), on level
  * `level` for all B right-hand sides.  The work runs `reps` times back to
  * back between two CUDA events on the handle's stream (after one untimed
  * run); *ms gets the mean time of one run and *bytes its algorithmic DRAM

@@ -5,9 +5,13 @@ the CPU baseline of ``bench.py`` time a few oracle cycles and scale them to a
 whole solve; the number of cycles a solve takes comes from here: the oracle's
 own solve of the workload's first right-hand side to the bench tolerance,
 written to ``oracle/bench_cycles.json`` under the key
-``"{k:g}/{n}/{smoother}/{cycle}{nu}/{beta2:g}"``.
+``"{k:g}/{n}/{smoother}/{cycle}{nu}/{beta2:g}"``, with ``"/fgmres{m}"``
+appended for the FGMRES(m) outer loop (``oracle.krylov``; the count is then
+preconditioner applications) and ``"/linear"`` for linear-interpolation
+transfers.
 
     python -m oracle.bench_cycles --k 300 --n 1024 --batch 64
+    python -m oracle.bench_cycles --k 300 --n 1024 --smoother jacobi --nu 1 --krylov 20
 
 This module only calls ``oracle/`` and the seeded generators in ``synth/``.
 """
@@ -18,25 +22,27 @@ import time
 
 from . import cycle as oc
 from . import hierarchy as oh
+from . import krylov as okr
 
 PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "bench_cycles.json")
 
 
-def key(k, n, smoother, cycle, nu, beta2):
-    return f"{k:g}/{n}/{smoother}/{cycle}{nu}/{beta2:g}"
+def key(k, n, smoother, cycle, nu, beta2, krylov=0, transfer="bezier"):
+    return (f"{k:g}/{n}/{smoother}/{cycle}{nu}/{beta2:g}" + (f"/fgmres{krylov}" if krylov else "") +
+            ("/linear" if transfer == "linear" else ""))
 
 
-def count(k, n, smoother="gmres3", cycle="V", nu=2, beta2=None, batch=64, tol=1e-6):
+def count(k, n, smoother="gmres3", cycle="V", nu=2, beta2=None, batch=64, tol=1e-6, krylov=0, transfer="bezier"):
     """Cycles the oracle needs for the first right-hand side of the workload."""
     import synth
     if beta2 is None:
         beta2 = 1.0 / k if smoother == "gmres3" else 0.7
     h = 1.0 / n
     b = (synth.source_row(n, n, h, batch)[0] if batch > 1 else synth.point_source(n, n, h)).ravel()
-    H = oh.build_hierarchy(n, n, h, k, beta2)
+    H = oh.build_hierarchy(n, n, h, k, beta2, kind=transfer)
     opt = oc.CycleOptions(1 if cycle == "V" else 2, smoother, nu, nu, 4.5)
-    res = oc.mg_solve(H, b, tol, opt)
-    return key(k, n, smoother, cycle, nu, beta2), res.cycles, res.converged
+    res = okr.fgmres_solve(H, b, tol, opt, krylov) if krylov else oc.mg_solve(H, b, tol, opt)
+    return key(k, n, smoother, cycle, nu, beta2, krylov, transfer), res.cycles, res.converged
 
 
 def main():
@@ -49,9 +55,11 @@ def main():
     p.add_argument("--beta2", type=float, default=None)
     p.add_argument("--batch", type=int, default=64)
     p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--krylov", type=int, default=0, help="m > 0: FGMRES(m) around the cycle")
+    p.add_argument("--transfer", default="bezier", choices=["bezier", "linear"])
     a = p.parse_args()
     t0 = time.perf_counter()
-    kk, cyc, ok = count(a.k, a.n, a.smoother, a.cycle, a.nu, a.beta2, a.batch, a.tol)
+    kk, cyc, ok = count(a.k, a.n, a.smoother, a.cycle, a.nu, a.beta2, a.batch, a.tol, a.krylov, a.transfer)
     if not ok:
         raise SystemExit(f"oracle did not converge for {kk}")
     table = {}

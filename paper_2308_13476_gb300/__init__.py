@@ -42,7 +42,7 @@ class MgOptions(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
                 ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("fuse", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("march", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("transfer", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -230,11 +230,12 @@ def mg_setup_ragged(nx, ny, h, k_const, beta2=0.0, opt=None):
 
 
 SMOOTHERS = {"jacobi": 0, "gmres3": 1}
+TRANSFERS = {"bezier": 0, "linear": 1}
 
 
 def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, precision="fp64", batch=1,
              max_cycles=10000, min_coarse=10, coarse_nodes=None, coarse_mode=None, fuse=None, tile_rows=None,
-             march=None, krylov=None, stream=None):
+             march=None, krylov=None, transfer="bezier", stream=None):
     o = mg_default_options()
     o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
     o.smoother = SMOOTHERS[smoother]
@@ -245,6 +246,7 @@ def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, preci
                       ("tile_rows", tile_rows), ("march", march), ("krylov", krylov)):
         if val is not None:
             setattr(o, name, int(val))
+    o.transfer = TRANSFERS[transfer]
     o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
     return o
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed-ff": 2}
@@ -293,15 +295,19 @@ class Solver:
 
     Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
            nu_pre, nu_post, omega, precision="fp64"|"mixed"|"mixed-ff", batch, levels,
-           max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, march, krylov, stream)
+           max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, march, krylov,
+           transfer="bezier"|"linear", stream)
     ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
     ``krylov`` = m > 0 wraps the cycle in restarted FGMRES(m) as its right
     preconditioner (cycles then count preconditioner applications).
+    ``transfer="linear"`` replaces the higher-order transfers of Eq. (xex) by
+    linear interpolation (an ablation).
     """
 
     def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
                  precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, coarse_nodes=None,
-                 coarse_mode=None, fuse=None, tile_rows=None, march=None, krylov=0, stream=None):
+                 coarse_mode=None, fuse=None, tile_rows=None, march=None, krylov=0, transfer="bezier",
+                 stream=None):
         o = mg_default_options()
         o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
         o.smoother = SMOOTHERS[smoother]
@@ -319,6 +325,7 @@ class Solver:
         if march is not None:
             o.march = int(march)
         o.krylov = int(krylov)
+        o.transfer = TRANSFERS[transfer]
         o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         self.nx, self.ny, self.h, self.batch = nx, ny, h, batch
         if isinstance(k, (int, float)):

@@ -74,6 +74,7 @@ struct mg_ctx {
   long long peer_nodes = 0;   // ragged sub-handle: fine-level nodes of the problems solved beside it
   int nx = 0, ny = 0, B = 1, nlev = 0, ncoarse = 0;
   double h = 0, kconst = 0, beta2 = 0;
+  Xfer xw = xfer_of(0);   // inter-grid transfer weights (opt.transfer)
   std::vector<Level> lev;
   std::vector<LevelVec<double>> v64;
   std::vector<LevelVec<float>> v32;
@@ -312,10 +313,10 @@ template <class T> struct Emit {
     const Grid& gc = c->lev[l + 1].g;
     smooth(l, c->opt.nu_pre);
     if (c->opt.fuse) {
-      launch_resid_restrict<T>(g, gc, opT<T>(c, l), cur[l], V[l].b, V[l + 1].b, c->B, c->active, s);
+      launch_resid_restrict<T>(g, gc, opT<T>(c, l), cur[l], V[l].b, V[l + 1].b, c->B, c->active, c->xw, s);
     } else {
       launch_residual<T>(g, opT<T>(c, l), cur[l], V[l].b, V[l].r, c->B, c->active, s);
-      launch_restrict<T>(g, gc, V[l].r, V[l + 1].b, c->B, c->active, s);
+      launch_restrict<T>(g, gc, V[l].r, V[l + 1].b, c->B, c->active, c->xw, s);
     }
     if (l + 1 == L - 1 && lc > l + 1) {
       coarse_solve(l + 1);
@@ -323,7 +324,7 @@ template <class T> struct Emit {
       cudaMemsetAsync(cur[l + 1], 0, sizeof(cx<T>) * (size_t)gc.vstride * c->B, s);
       for (int q = 0; q < c->opt.cycle; ++q) cycle(l + 1);
     }
-    launch_prolong_add<T>(g, gc, cur[l + 1], cur[l], c->B, c->active, s);
+    launch_prolong_add<T>(g, gc, cur[l + 1], cur[l], c->B, c->active, c->xw, s);
     smooth(l, c->opt.nu_post);
   }
 
@@ -388,6 +389,7 @@ template <class T> static cudaError_t build_plan(mg_ctx* c, int lc, CoarsePlan<T
     CLevel<T> d{};
     const OpView<T> op = opT<T>(c, l);
     d.g = c->lev[l].g;
+    d.xw = c->xw;
     d.kind = op.kind;
     d.c0 = op.c0;
     d.kf = op.kf;
@@ -449,12 +451,33 @@ static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
   }
 }
 
+// The FGMRES kernels' arguments: the handle's buffers and control arrays.
+static FgArgs fg_args(const mg_ctx* c, double tol) {
+  FgArgs a = c->fg;
+  a.c0 = c->hc0d;
+  a.kf = c->kf64;
+  a.c0f = c->hc0f;
+  a.kf32 = c->kf32;
+  a.active = c->active;
+  a.state = c->state;
+  a.cycles = c->cycles;
+  a.relres = c->relres;
+  a.hist = c->hist;
+  a.hist_len = c->hist_len;
+  a.n_active = c->n_active;
+  a.bnorm = c->bnorm;
+  a.tol = tol;
+  a.max_cycles = c->opt.max_cycles;
+  return a;
+}
+
 template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, int reps, double* ms, double* bytes) {
   cudaStream_t s = (cudaStream_t)h->opt.stream;
   auto& V = vecs<T>(h);
   if (level < 0 || level >= (int)V.size() || ((what == 2 || what == 3) && level + 1 >= h->nlev))
     FAIL(MG_EINVAL, "bad level");
   if (what == 4 && h->opt.smoother != 1) FAIL(MG_EINVAL, "what = 4 needs the GMRES(3) smoother");
+  if (what == 5 && (h->opt.krylov < 1 || level != 0)) FAIL(MG_EINVAL, "what = 5 needs krylov > 0 and level 0");
   const Grid& g = h->lev[level].g;
   const OpView<T> op = opT<T>(h, level);
   const double nodes = (double)(g.nx + 1) * (g.ny + 1) * h->B;
@@ -468,18 +491,29 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
   } else if (op.kf) {
     opbytes = sizeof(T) / (double)h->B;
   }
+  const std::vector<int> ones(h->B, 1);
+  const FgArgs fa = what == 5 ? fg_args(h, 0.0) : FgArgs{};
   auto launch = [&]() {
     switch (what) {
       case 0: launch_jacobi<T>(g, op, V[level].x, V[level].b, V[level].t, h->B, nullptr, s); break;
       case 1: launch_residual<T>(g, op, V[level].x, V[level].b, V[level].r, h->B, nullptr, s); break;
-      case 2: launch_restrict<T>(g, h->lev[level + 1].g, V[level].r, V[level + 1].b, h->B, nullptr, s); break;
-      case 3: launch_prolong_add<T>(g, h->lev[level + 1].g, V[level + 1].x, V[level].x, h->B, nullptr, s); break;
-      default: gmres_level<T>(h, level, V[level].x, V[level].b, 1, nullptr, s); break;
+      case 2: launch_restrict<T>(g, h->lev[level + 1].g, V[level].r, V[level + 1].b, h->B, nullptr, h->xw, s); break;
+      case 3: launch_prolong_add<T>(g, h->lev[level + 1].g, V[level + 1].x, V[level].x, h->B, nullptr, h->xw, s); break;
+      case 4: gmres_level<T>(h, level, V[level].x, V[level].b, 1, nullptr, s); break;
+      default: {   // the last Arnoldi step of a restart cycle (j = m - 1): both passes, every RHS active
+        const int j = h->opt.krylov - 1;
+        cudaMemcpyAsync(h->active, ones.data(), sizeof(int) * h->B, cudaMemcpyHostToDevice, s);
+        launch_fg_dots<T>(fa, j, V[0].x, s);
+        launch_fg_orth<T>(fa, j, s);
+        break;
+      }
     }
   };
   if (what == 0 || what == 1) *bytes = nodes * (3 * e + opbytes);
   else if (what == 2) *bytes = nodes * e * 1.25;     // read fine r, write coarse r
   else if (what == 3) *bytes = nodes * e * 2.25;     // read+write fine x, read coarse e
+  else if (what == 5)   // z, Z_j twice; v_0..v_j twice, v_{j+1} once (all in the cycle's precision); k field twice
+    *bytes = nodes * (e * (2.0 * h->opt.krylov + 4.0) + (op.kf ? 2 * sizeof(T) / (double)h->B : 0.0));
   else {   // GMRES(3) step: four passes that read the operator, plus vectors
     double gop = 0;   // operator bytes per node and RHS read by one pass
     if (level == 0) gop = op.kf ? sizeof(T) / (double)h->B : 0.0;
@@ -525,6 +559,7 @@ void mg_default_options(mg_options* o) {
   o->tile_rows = 0;
   o->march = -1;
   o->krylov = 0;
+  o->transfer = 0;
   o->stream = nullptr;
 }
 
@@ -538,6 +573,7 @@ mg_status mg_destroy(mg_handle h) {
 static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   const mg_options& o = c->opt;
   cudaStream_t s = (cudaStream_t)o.stream;
+  c->xw = xfer_of(o.transfer);
   // level list: halve while both counts are even and the grid has >= min_coarse nodes
   std::vector<std::pair<int, int>> sizes{{c->nx, c->ny}};
   while (true) {
@@ -609,10 +645,10 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
       CK(dalloc(c, (void**)&cwy[l], sizeof(double2) * w * (cy_ + 1)));
       CK(dalloc(c, (void**)&L.wx, sizeof(double) * w * (cx_ + 1)));
       CK(dalloc(c, (void**)&L.wy, sizeof(double) * w * (cy_ + 1)));
-      launch_galerkin_1d(pg, fx, rf, L.gx, r, s);
-      launch_galerkin_1d(pwx, fx, rf, cwx[l], r, s);
-      launch_galerkin_1d(ph, fy, rf, L.hy, r, s);
-      launch_galerkin_1d(pwy, fy, rf, cwy[l], r, s);
+      launch_galerkin_1d(pg, fx, rf, L.gx, r, c->xw, s);
+      launch_galerkin_1d(pwx, fx, rf, cwx[l], r, c->xw, s);
+      launch_galerkin_1d(ph, fy, rf, L.hy, r, c->xw, s);
+      launch_galerkin_1d(pwy, fy, rf, cwy[l], r, c->xw, s);
       launch_real_part(cwx[l], L.wx, (long long)w * (cx_ + 1), s);
       launch_real_part(cwy[l], L.wy, (long long)w * (cy_ + 1), s);
       CK(dalloc(c, (void**)&L.dinv, sizeof(double2) * L.plane));
@@ -642,7 +678,8 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
       L.kind = r;
       CK(dalloc(c, (void**)&L.st, sizeof(double2) * S * L.plane));
       CK(dalloc(c, (void**)&L.dinv, sizeof(double2) * L.plane));
-      launch_galerkin(op64(c, l - 1), c->lev[l - 1].g.nx, c->lev[l - 1].g.ny, L.st, L.g.nx, L.g.ny, r, c->beta2, s);
+      launch_galerkin(op64(c, l - 1), c->lev[l - 1].g.nx, c->lev[l - 1].g.ny, L.st, L.g.nx, L.g.ny, r, c->beta2, c->xw,
+                      s);
       launch_diaginv(L.st, r, L.plane, o.omega, L.dinv, s);
     }
   }
@@ -742,7 +779,7 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     a.vlen = g0.vstride * c->B;
     fg_geometry(g0, c->B, !mixed, a);
     const size_t zb = mixed ? sizeof(float2) : sizeof(double2);
-    CK(dalloc(c, (void**)&a.V, sizeof(double2) * (size_t)a.vlen * (m + 1)));
+    CK(dalloc(c, &a.V, zb * (size_t)a.vlen * (m + 1)));
     CK(dalloc(c, &a.Z, zb * (size_t)a.vlen * m));
     CK(dalloc(c, (void**)&a.X, sizeof(double2) * (size_t)a.vlen));
     CK(dalloc(c, (void**)&a.b, sizeof(double2) * (size_t)a.vlen));
@@ -784,6 +821,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.march < -1 || o.march > 1) FAIL(MG_EINVAL, "march must be -1, 0 or 1");
   if (o.krylov < 0 || o.krylov > FG_MAXM) FAIL(MG_EINVAL, "krylov must be in 0..%d", FG_MAXM);
   if (o.krylov > 0 && o.precision == 2) FAIL(MG_EINVAL, "the FGMRES outer loop needs precision 0 or 1");
+  if (o.transfer != 0 && o.transfer != 1) FAIL(MG_EINVAL, "transfer must be 0 (Eq. (xex)) or 1 (linear)");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
@@ -918,19 +956,7 @@ static mg_status solve_fgmres(mg_ctx* c, const void* rhs, void* x, double tol, i
   const bool mixed = c->opt.precision == 1;
   mg_status st = capture_precond(c);
   if (st != MG_OK) return st;
-  FgArgs a = c->fg;
-  a.c0 = c->hc0d;
-  a.kf = c->kf64;
-  a.active = c->active;
-  a.state = c->state;
-  a.cycles = c->cycles;
-  a.relres = c->relres;
-  a.hist = c->hist;
-  a.hist_len = c->hist_len;
-  a.n_active = c->n_active;
-  a.bnorm = c->bnorm;
-  a.tol = tol;
-  a.max_cycles = c->opt.max_cycles;
+  const FgArgs a = fg_args(c, tol);
   launch_pack<double>(g0, (const double2*)rhs, (double2*)a.b, B, conj, s);
   launch_pack<double>(g0, (const double2*)x, a.X, B, conj, s);
   launch_vecnorm_fin<double>(g0, a.b, B, c->bnorm, c->partial, c->tickets, s);
@@ -957,7 +983,8 @@ static mg_status solve_fgmres(mg_ctx* c, const void* rhs, void* x, double tol, i
   cx<float>* cx32 = mixed ? c->v32[0].x : nullptr;
   while (true) {
     CK(cudaMemsetAsync(c->n_active, 0, sizeof(int) * 2, s));
-    launch_fg_restart(a, s);
+    if (mixed) launch_fg_restart<float>(a, s);
+    else launch_fg_restart<double>(a, s);
     ++launches;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
@@ -1272,7 +1299,7 @@ mg_status mg_counters(mg_handle h, long long* kernel_launches, long long* graph_
 mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes) {
   if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
-  if (what < 0 || what > 4 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
+  if (what < 0 || what > 5 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
   if (h->opt.precision >= 1) return profile_t<float>(h, what, level, reps, ms, bytes);
   return profile_t<double>(h, what, level, reps, ms, bytes);
 }

@@ -169,10 +169,10 @@ __global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle(const CLevel<T>* _
           cx<T> acc = mk<T>(0, 0);
           for (int bb = -2; bb <= 2; ++bb) {
             const cx<T>* row = r + pc + bb * L.g.pitch;
-            cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
-            t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
-            t = add<T>(t, scl<T>(T(0.75), row[0]));
-            acc = add<T>(acc, scl<T>(cbw<T>(bb), t));
+            cx<T> t = scl<T>(T(L.xw.w2), add<T>(row[-2], row[2]));
+            t = add<T>(t, scl<T>(T(L.xw.w1), add<T>(row[-1], row[1])));
+            t = add<T>(t, scl<T>(T(L.xw.w0), row[0]));
+            acc = add<T>(acc, scl<T>(L.xw.template w<T>(bb), t));
           }
           bc[p] = scl<T>(T(0.25), acc);
         }
@@ -213,12 +213,12 @@ __global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle(const CLevel<T>* _
           const int I = i >> 1, J = j >> 1;
           auto rowval = [&](int JJ) -> cx<T> {
             const cx<T>* row = ec + C.g.at(I, JJ);
-            if (i & 1) return scl<T>(T(0.5), add<T>(row[0], row[1]));
-            return add<T>(scl<T>(T(0.125), add<T>(row[-1], row[1])), scl<T>(T(0.75), row[0]));
+            if (i & 1) return scl<T>(T(L.xw.w1), add<T>(row[0], row[1]));
+            return add<T>(scl<T>(T(L.xw.w2), add<T>(row[-1], row[1])), scl<T>(T(L.xw.w0), row[0]));
           };
           cx<T> v;
-          if (j & 1) v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
-          else v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+          if (j & 1) v = scl<T>(T(L.xw.w1), add<T>(rowval(J), rowval(J + 1)));
+          else v = add<T>(scl<T>(T(L.xw.w2), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(L.xw.w0), rowval(J)));
           p0[p] = add<T>(p0[p], v);
         }
         __syncthreads();

@@ -63,6 +63,20 @@ struct Grid {
   __host__ __device__ __forceinline__ int at(int i, int j) const { return (j + HALO) * pitch + (i + HALO); }
 };
 
+// Inter-grid transfer in one direction as the column stencil of P: coarse
+// node I reaches fine node 2I + d with weight w(d).  Eq. (xex) (the paper's
+// higher-order transfer) gives w(0) = 3/4, w(+-1) = 1/2, w(+-2) = 1/8;
+// linear interpolation (the "Linear" column of Table conv1) gives 1, 1/2, 0.
+// 2D transfers are the tensor product, and R = P^T / 4.
+struct Xfer {
+  double w0, w1, w2;
+  template <class T> __host__ __device__ __forceinline__ T w(int d) const {
+    return d == 0 ? T(w0) : (d == 1 || d == -1) ? T(w1) : (d == 2 || d == -2) ? T(w2) : T(0);
+  }
+};
+// kind 0: Eq. (xex); kind 1: linear interpolation.
+inline Xfer xfer_of(int kind) { return kind == 1 ? Xfer{1.0, 0.5, 0.0} : Xfer{0.75, 0.5, 0.125}; }
+
 // Fine-level (level 0) constants, computed on the device by the setup kernel
 // and passed to the kernels by value (copied back once at setup).
 // dinv[by*2+bx] = 1/(omega * A_PP) for constant k and the four boundary

@@ -9,13 +9,18 @@
 //           v_{j+1} = w' / h_{j+1,j}, Givens rotations on column j and on g;
 //           |g_{j+1}| is the residual norm of x + Z_{j+1} y
 //   x += Z_k y (triangular solve)
-// The fine operator A, the Arnoldi vectors V, the rotations and x are FP64;
-// Z is kept in the cycle's precision (complex64 in the mixed path: the
-// Arnoldi relation A Z_k = V_{k+1} Hbar holds for the Z actually stored, so
-// the outer residual still reaches FP64 accuracy).
+// Precision: x, b, the restart residual r = b - A x, the update and every
+// scalar (Hessenberg, Gram matrix, rotations, y) are FP64.  The basis V,
+// the preconditioned vectors Z and the arithmetic of the Arnoldi passes
+// (w = A z, the dots, v_{j+1}) take the cycle's precision T: FP64 for the
+// complex128 path; FP32 for the mixed path, where each restart cycle is then
+// an FP32 FGMRES correction of the FP64 residual (iterative refinement with
+// FGMRES as the inner solver), and the true FP64 residual at the restart
+// decides convergence.  GB300's FP64 pipe runs at about 1/58 of FP32, and an
+// FP64 Arnoldi step costs ~180 FP64 FMAs per node, which made it ALU-bound.
 //
 // Kernels (the cycle between prep and dots is the captured cycle graph):
-//   restart  r = b - A x into v_0, ||r||, restart test            (last block)
+//   restart  r = b - A x (FP64) into v_0, ||r||, restart test    (last block)
 //   prep     v_j /= h_{j,j-1} (or beta) in place, cycle rhs = v_j, cycle x = 0
 //   dots     Z_j = z, w = A z_j, <v_i, w> (i <= j) and <v_i, v_j> (i < j);
 //            the last block turns them into the MGS coefficients (Gram form:
@@ -24,11 +29,12 @@
 //   orth     v_{j+1} = w - sum_i h_i v_i (w recomputed from z_j), ||v_{j+1}||;
 //            the last block finishes the Arnoldi step, the rotations and the
 //            per-RHS exit test
-//   update   x += sum_i y_i z_i
+//   update   x += sum_i y_i z_i (FP64)
 // Every kernel walks strips of 32 columns x 64 rows (8 rows per thread,
 // warps along rows) with a fixed number of blocks per right-hand side;
-// block sums go to a value-major partial array and the block holding the
-// last ticket adds them in block order (bitwise reproducible).
+// per-strip sums in T are widened to FP64 per warp, block sums go to a
+// value-major partial array and the block holding the last ticket adds them
+// in block order (bitwise reproducible).
 #include <math.h>
 
 #include <algorithm>
@@ -55,11 +61,19 @@ __device__ __forceinline__ double warp_sum(double t) {
   return t;
 }
 
-// A z at node (i, j) from a padded vector of precision T (FP64 arithmetic).
-template <class T>
-__device__ __forceinline__ double2 apply_d(const Op0<double>& op, const cx<T>* __restrict__ z, int p, int pitch, int i,
-                                           int j) {
-  return op.apply5(to_d(z[p]), to_d(z[p + 1]), to_d(z[p - 1]), to_d(z[p + pitch]), to_d(z[p - pitch]), i, j);
+// The fine operator in precision T (the cycle's level-0 operator).
+template <class T> __device__ __forceinline__ Op0<T> op_t(const FgArgs& a);
+template <> __device__ __forceinline__ Op0<double> op_t<double>(const FgArgs& a) {
+  return Op0<double>{a.c0, a.kf, a.g.nx, a.g.ny};
+}
+template <> __device__ __forceinline__ Op0<float> op_t<float>(const FgArgs& a) {
+  return Op0<float>{a.c0f, a.kf32, a.g.nx, a.g.ny};
+}
+
+template <class T> __device__ __forceinline__ T warp_sum_t(T t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  return t;
 }
 
 struct StripPos {
@@ -96,7 +110,7 @@ __device__ bool fg_reduce(const FgArgs& a, int rhs, int nval, const double* mine
 
 // ------------------------------------------------------------------ restart
 
-__global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> op) {
+template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> op) {
   __shared__ double red[FBY], tot[1], mine[1];
   const int rhs = blockIdx.z;
   if (a.state[rhs] != 0) return;   // block-uniform
@@ -104,7 +118,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> o
   const long long off = (long long)rhs * g.vstride;
   const double2* x = a.X + off;
   const double2* b = a.b + off;
-  double2* v0 = a.V + off;
+  cx<T>* v0 = (cx<T>*)a.V + off;
   double acc = 0.0;
   for (int s = blockIdx.x; s < a.ns; s += a.nbr) {
     const StripPos sp = strip_pos(a, s);
@@ -115,7 +129,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> o
       if (j > g.ny) break;
       const int p = g.at(sp.i, j);
       const double2 rr = sub<double>(b[p], op.apply(x, p, g.pitch, sp.i, j));
-      v0[p] = rr;
+      v0[p] = from_d<T>(rr);
       acc += abs2<double>(rr);
     }
   }
@@ -161,8 +175,8 @@ __global__ void __launch_bounds__(FTHREADS) k_fg_prep(FgArgs a, int jj, cx<T>* _
   if (!a.active[rhs]) return;
   const Grid& g = a.g;
   const long long off = (long long)rhs * g.vstride;
-  const double dv = a.S[(long long)rhs * a.sd + FgLayout{a.m}.div()];
-  double2* vj = a.V + jj * a.vlen + off;
+  const T dv = (T)a.S[(long long)rhs * a.sd + FgLayout{a.m}.div()];
+  cx<T>* vj = (cx<T>*)a.V + jj * a.vlen + off;
   for (int s = blockIdx.x; s < a.ns; s += a.nbr) {
     const StripPos sp = strip_pos(a, s);
     if (sp.i > g.nx) continue;
@@ -171,10 +185,10 @@ __global__ void __launch_bounds__(FTHREADS) k_fg_prep(FgArgs a, int jj, cx<T>* _
       const int j = sp.j0 + r * FBY;
       if (j > g.ny) break;
       const int p = g.at(sp.i, j);
-      const double2 u = vj[p];
-      const double2 v = make_double2(u.x / dv, u.y / dv);
+      const cx<T> u = vj[p];
+      const cx<T> v = mk<T>(u.x / dv, u.y / dv);
       vj[p] = v;
-      cb[off + p] = from_d<T>(v);
+      cb[off + p] = v;
       cxv[off + p] = mk<T>(T(0), T(0));
     }
   }
@@ -183,8 +197,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fg_prep(FgArgs a, int jj, cx<T>* _
 // ------------------------------------------------------------------ dots (MGS coefficients)
 
 template <class T>
-__global__ void __launch_bounds__(FTHREADS, 2) k_fg_dots(FgArgs a, Op0<double> op, const cx<T>* __restrict__ z,
-                                                         int jj) {
+__global__ void __launch_bounds__(FTHREADS, 2) k_fg_dots(FgArgs a, const cx<T>* __restrict__ z, int jj) {
   __shared__ double red[FNV][FBY];
   __shared__ double mine[FNV], tot[FNV];
   const int rhs = blockIdx.z;
@@ -195,50 +208,51 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_fg_dots(FgArgs a, Op0<double> o
   __syncthreads();
   const Grid& g = a.g;
   const long long off = (long long)rhs * g.vstride;
+  const Op0<T> op = op_t<T>(a);
   const cx<T>* zs = z + off;
   cx<T>* zj = (cx<T>*)a.Z + jj * a.vlen + off;
-  const double2* vj = a.V + jj * a.vlen + off;
+  const cx<T>* vj = (const cx<T>*)a.V + jj * a.vlen + off;
   for (int s = blockIdx.x; s < a.ns; s += a.nbr) {
     const StripPos sp = strip_pos(a, s);
-    double2 w[FR], u[FR];
+    cx<T> w[FR], u[FR];
     int pr[FR];
 #pragma unroll
     for (int r = 0; r < FR; ++r) {
       const int j = sp.j0 + r * FBY;
       pr[r] = -1;
-      w[r] = u[r] = make_double2(0.0, 0.0);
+      w[r] = u[r] = mk<T>(T(0), T(0));
       if (sp.i <= g.nx && j <= g.ny) {
         const int p = g.at(sp.i, j);
         pr[r] = p;
         zj[p] = zs[p];
-        w[r] = apply_d<T>(op, zs, p, g.pitch, sp.i, j);
+        w[r] = op.apply(zs, p, g.pitch, sp.i, j);
         u[r] = vj[p];
       }
     }
     for (int q = 0; q <= jj; ++q) {
-      const double2* vq = a.V + q * a.vlen + off;
-      double dr = 0.0, di = 0.0, gr = 0.0, gi = 0.0;
+      const cx<T>* vq = (const cx<T>*)a.V + q * a.vlen + off;
+      T dr = T(0), di = T(0), gr = T(0), gi = T(0);
 #pragma unroll
       for (int r = 0; r < FR; ++r) {
         if (pr[r] < 0) continue;
-        const double2 v = vq[pr[r]];
+        const cx<T> v = vq[pr[r]];
         dr = fma(v.x, w[r].x, fma(v.y, w[r].y, dr));
         di = fma(v.x, w[r].y, fma(-v.y, w[r].x, di));
         gr = fma(v.x, u[r].x, fma(v.y, u[r].y, gr));
         gi = fma(v.x, u[r].y, fma(-v.y, u[r].x, gi));
       }
-      dr = warp_sum(dr);
-      di = warp_sum(di);
+      dr = warp_sum_t<T>(dr);
+      di = warp_sum_t<T>(di);
       if (q < jj) {
-        gr = warp_sum(gr);
-        gi = warp_sum(gi);
+        gr = warp_sum_t<T>(gr);
+        gi = warp_sum_t<T>(gi);
       }
-      if (lane == 0) {
-        red[2 * q][warp] += dr;
-        red[2 * q + 1][warp] += di;
+      if (lane == 0) {   // each warp's strip sums widened to FP64
+        red[2 * q][warp] += (double)dr;
+        red[2 * q + 1][warp] += (double)di;
         if (q < jj) {
-          red[2 * (jj + 1) + 2 * q][warp] += gr;
-          red[2 * (jj + 1) + 2 * q + 1][warp] += gi;
+          red[2 * (jj + 1) + 2 * q][warp] += (double)gr;
+          red[2 * (jj + 1) + 2 * q + 1][warp] += (double)gi;
         }
       }
     }
@@ -354,52 +368,55 @@ __device__ void fg_finish_step(const FgArgs& a, int rhs, int jj, double sumsq) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(FTHREADS, 2) k_fg_orth(FgArgs a, Op0<double> op, int jj) {
-  __shared__ double2 hs[FG_MAXM + 1];
+__global__ void __launch_bounds__(FTHREADS, 2) k_fg_orth(FgArgs a, int jj) {
+  __shared__ cx<T> hs[FG_MAXM + 1];
   __shared__ double red[FBY], mine[1], tot[1];
   const int rhs = blockIdx.z;
   if (!a.active[rhs]) return;
   const int tid = threadIdx.x + threadIdx.y * FBX;
   const FgLayout L{a.m};
   const double* S = a.S + (long long)rhs * a.sd;
-  if (tid <= jj) hs[tid] = make_double2(S[L.h(jj, tid)], S[L.h(jj, tid) + 1]);
+  if (tid <= jj) hs[tid] = mk<T>((T)S[L.h(jj, tid)], (T)S[L.h(jj, tid) + 1]);
   __syncthreads();
+  const Op0<T> op = op_t<T>(a);
   const Grid& g = a.g;
   const long long off = (long long)rhs * g.vstride;
   const cx<T>* zj = (const cx<T>*)a.Z + jj * a.vlen + off;
-  double2* vn = a.V + (jj + 1) * a.vlen + off;
+  cx<T>* vn = (cx<T>*)a.V + (jj + 1) * a.vlen + off;
   double acc = 0.0;
   for (int s = blockIdx.x; s < a.ns; s += a.nbr) {
     const StripPos sp = strip_pos(a, s);
-    double2 w[FR];
+    cx<T> w[FR];
     int pr[FR];
 #pragma unroll
     for (int r = 0; r < FR; ++r) {
       const int j = sp.j0 + r * FBY;
       pr[r] = -1;
-      w[r] = make_double2(0.0, 0.0);
+      w[r] = mk<T>(T(0), T(0));
       if (sp.i <= g.nx && j <= g.ny) {
         pr[r] = g.at(sp.i, j);
-        w[r] = apply_d<T>(op, zj, pr[r], g.pitch, sp.i, j);
+        w[r] = op.apply(zj, pr[r], g.pitch, sp.i, j);
       }
     }
     for (int q = 0; q <= jj; ++q) {
-      const double2* vq = a.V + q * a.vlen + off;
-      const double2 h = hs[q];
+      const cx<T>* vq = (const cx<T>*)a.V + q * a.vlen + off;
+      const cx<T> h = hs[q];
 #pragma unroll
       for (int r = 0; r < FR; ++r) {
         if (pr[r] < 0) continue;
-        const double2 v = vq[pr[r]];
+        const cx<T> v = vq[pr[r]];
         w[r].x -= h.x * v.x - h.y * v.y;
         w[r].y -= h.x * v.y + h.y * v.x;
       }
     }
+    T part = T(0);   // this strip's sum in T, widened once
 #pragma unroll
     for (int r = 0; r < FR; ++r) {
       if (pr[r] < 0) continue;
       vn[pr[r]] = w[r];
-      acc += abs2<double>(w[r]);
+      part += abs2<T>(w[r]);
     }
+    acc += (double)part;
   }
   acc = warp_sum(acc);
   if (threadIdx.x == 0) red[threadIdx.y] = acc;
@@ -455,7 +472,7 @@ template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_update(FgArg
   }
 }
 
-inline Op0<double> fine_op(const FgArgs& a) { return Op0<double>{a.c0, a.kf, a.g.nx, a.g.ny}; }
+inline Op0<double> fine_op64(const FgArgs& a) { return Op0<double>{a.c0, a.kf, a.g.nx, a.g.ny}; }
 inline dim3 fg_grid(const FgArgs& a) { return dim3(a.nbr, 1, a.B); }
 
 }  // namespace
@@ -476,23 +493,24 @@ void fg_geometry(const Grid& g, int B, bool fp64z, FgArgs& a) {
   a.nvp = FNV;
 }
 
-void launch_fg_restart(const FgArgs& a, cudaStream_t s) {
-  k_fg_restart<<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, fine_op(a));
+template <class T> void launch_fg_restart(const FgArgs& a, cudaStream_t s) {
+  k_fg_restart<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, fine_op64(a));
 }
 template <class T> void launch_fg_prep(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s) {
   k_fg_prep<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j, cb, cxv);
 }
 template <class T> void launch_fg_dots(const FgArgs& a, int j, const cx<T>* z, cudaStream_t s) {
-  k_fg_dots<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, fine_op(a), z, j);
+  k_fg_dots<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, z, j);
 }
 template <class T> void launch_fg_orth(const FgArgs& a, int j, cudaStream_t s) {
-  k_fg_orth<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, fine_op(a), j);
+  k_fg_orth<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j);
 }
 template <class T> void launch_fg_update(const FgArgs& a, cudaStream_t s) {
   k_fg_update<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a);
 }
 
 #define INST(T)                                                                                  \
+  template void launch_fg_restart<T>(const FgArgs&, cudaStream_t);                               \
   template void launch_fg_prep<T>(const FgArgs&, int, cx<T>*, cx<T>*, cudaStream_t);             \
   template void launch_fg_dots<T>(const FgArgs&, int, const cx<T>*, cudaStream_t);               \
   template void launch_fg_orth<T>(const FgArgs&, int, cudaStream_t);                             \

@@ -20,14 +20,10 @@ namespace hmg {
 constexpr int CTX = 32, CTY = 8;                  // coarse tile of k_resid_restrict
 constexpr int RFX = 2 * CTX + 3, RFY = 2 * CTY + 3;  // fine footprint incl. restriction halo
 
-template <class T> __device__ __forceinline__ T rw(int d) {
-  return d == 0 ? T(0.75) : (d == 1 || d == -1) ? T(0.5) : T(0.125);
-}
-
 template <class T, class Op>
 __global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, Op op, const cx<T>* __restrict__ x,
                                                               const cx<T>* __restrict__ b, cx<T>* __restrict__ rc,
-                                                              const int* __restrict__ active) {
+                                                              const int* __restrict__ active, Xfer xw) {
   __shared__ cx<T> rt[RFY][RFX];
   const int rhs = blockIdx.z;
   if (active && !active[rhs]) return;
@@ -54,10 +50,10 @@ __global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, 
 #pragma unroll
   for (int bb = -2; bb <= 2; ++bb) {
     const cx<T>* row = &rt[cj + bb][ci];
-    cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
-    t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
-    t = add<T>(t, scl<T>(T(0.75), row[0]));
-    acc = add<T>(acc, scl<T>(rw<T>(bb), t));
+    cx<T> t = scl<T>(T(xw.w2), add<T>(row[-2], row[2]));
+    t = add<T>(t, scl<T>(T(xw.w1), add<T>(row[-1], row[1])));
+    t = add<T>(t, scl<T>(T(xw.w0), row[0]));
+    acc = add<T>(acc, scl<T>(xw.w<T>(bb), t));
   }
   rc[(long long)rhs * gc.vstride + gc.at(I, J)] = scl<T>(T(0.25), acc);
 }
@@ -120,10 +116,10 @@ __global__ void __launch_bounds__(256) k_jacobi_fused(Grid g, Op0<T> op, const c
 
 template <class T>
 void launch_resid_restrict(const Grid& gf, const Grid& gc, const OpView<T>& v, const cx<T>* x, const cx<T>* b,
-                           cx<T>* rc, int B, const int* active, cudaStream_t s) {
+                           cx<T>* rc, int B, const int* active, const Xfer& xw, cudaStream_t s) {
   const dim3 grd(cdiv(gc.nx + 1, CTX), cdiv(gc.ny + 1, CTY), B);
   with_op<T>(v, gf.nx, gf.ny, [&](auto op) {
-    k_resid_restrict<T, decltype(op)><<<grd, dim3(CTX, CTY), 0, s>>>(gf, gc, op, x, b, rc, active);
+    k_resid_restrict<T, decltype(op)><<<grd, dim3(CTX, CTY), 0, s>>>(gf, gc, op, x, b, rc, active, xw);
   });
 }
 
@@ -150,9 +146,9 @@ cudaError_t configure_fused_kernels() {   // allow the complex128 window (> 48 K
 }
 
 template void launch_resid_restrict<double>(const Grid&, const Grid&, const OpView<double>&, const double2*,
-                                            const double2*, double2*, int, const int*, cudaStream_t);
+                                            const double2*, double2*, int, const int*, const Xfer&, cudaStream_t);
 template void launch_resid_restrict<float>(const Grid&, const Grid&, const OpView<float>&, const float2*,
-                                           const float2*, float2*, int, const int*, cudaStream_t);
+                                           const float2*, float2*, int, const int*, const Xfer&, cudaStream_t);
 template void launch_jacobi_fused<double>(const Grid&, const OpView<double>&, const double2*, const double2*,
                                           double2*, int, int, const int*, cudaStream_t);
 template void launch_jacobi_fused<float>(const Grid&, const OpView<float>&, const float2*, const float2*, float2*,

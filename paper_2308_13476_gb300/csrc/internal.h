@@ -93,10 +93,11 @@ void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, cons
 // out[b] = ||v_b|| (one kernel).
 template <class T> void launch_vecnorm_fin(const Grid& g, const cx<T>* v, int B, double* out, double* partial,
                                            unsigned* tickets, cudaStream_t s);
+// Transfers (weights xw, Eq. (xex) or linear): r_c = R r_f and x_f += P e_c.
 template <class T> void launch_restrict(const Grid& gf, const Grid& gc, const cx<T>* rf, cx<T>* rc, int B,
-                                        const int* active, cudaStream_t s);
+                                        const int* active, const Xfer& xw, cudaStream_t s);
 template <class T> void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<T>* ec, cx<T>* xf, int B,
-                                           const int* active, cudaStream_t s);
+                                           const int* active, const Xfer& xw, cudaStream_t s);
 template <class T> void launch_copy_masked(const Grid& g, const cx<T>* src, cx<T>* dst, int B, const int* active,
                                            cudaStream_t s);
 // Dense user array [B][ny+1][nx+1] complex128 <-> padded vector; conj != 0 conjugates.
@@ -112,7 +113,7 @@ void launch_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, d
 // Galerkin coarse stencil (radius rc) from the fine operator: fine kind 1 uses
 // the matrix-free definition with the CSL shift beta2; kind 2/3 a stored stencil.
 void launch_galerkin(const OpView<double>& fine, int fnx, int fny, double2* coarse_st, int cnx, int cny, int rc,
-                     double beta2, cudaStream_t s);
+                     double beta2, const Xfer& xw, cudaStream_t s);
 void launch_diaginv(const double2* st, int rc, long long plane, double omega, double2* dinv, cudaStream_t s);
 void launch_to_float(const double2* src, float2* dst, long long n, cudaStream_t s);
 void launch_to_float_real(const double* src, float* dst, long long n, cudaStream_t s);
@@ -122,7 +123,7 @@ void launch_to_float_real(const double* src, float* dst, long long n, cudaStream
 void launch_factors0(int n, double h, double k, double beta2, double2* g, double2* hf, double2* w, cudaStream_t s);
 // 1D Galerkin coarsening X_c = (P1^T / 2) X P1 of a banded [nf+1][2rf+1] row
 // array into [nc+1][2rc+1] (nc = nf / 2).
-void launch_galerkin_1d(const double2* X, int nf, int rf, double2* Xc, int rc, cudaStream_t s);
+void launch_galerkin_1d(const double2* X, int nf, int rf, double2* Xc, int rc, const Xfer& xw, cudaStream_t s);
 // Real parts of a complex row array (the W factors are real).
 void launch_real_part(const double2* a, double* b, long long n, cudaStream_t s);
 // Per-node 1/(omega * diagonal) of a level operator (any kind).
@@ -167,6 +168,7 @@ constexpr int CTA_THREADS = 512;
 enum { C_JACOBI = 0, C_GMRES = 1, C_RESTRICT = 2, C_ZERO = 3, C_COARSE = 4, C_PROLONG = 5, C_COPY = 6 };
 template <class T> struct CLevel {
   Grid g;
+  Xfer xw;                  // transfers between this level and the next
   int kind;                 // as OpView::kind
   Op0Consts<T> c0;
   const T* kf;
@@ -208,7 +210,8 @@ template <class T> cudaError_t launch_cycle_coop(const CLevel<T>* levels, int nl
 // Fused halo-tile kernels (fused.cu): r_c = R (b - A x) in one pass (any
 // level), and up to jacobi_fused_max_nu() fine-level Jacobi sweeps in one pass.
 template <class T> void launch_resid_restrict(const Grid& gf, const Grid& gc, const OpView<T>& op, const cx<T>* x,
-                                              const cx<T>* b, cx<T>* rc, int B, const int* active, cudaStream_t s);
+                                              const cx<T>* b, cx<T>* rc, int B, const int* active, const Xfer& xw,
+                                              cudaStream_t s);
 template <class T> void launch_jacobi_fused(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
                                             cx<T>* xo, int nu, int B, const int* active, cudaStream_t s);
 int jacobi_fused_max_nu();
@@ -238,8 +241,8 @@ void launch_ff_norm(const Grid& g, const void* v, int B, double* out, double* pa
                     cudaStream_t s);
 
 // Flexible GMRES(m) outer loop with one cycle as the right preconditioner
-// (fgmres.cu).  V: m+1 FP64 basis vectors, Z: m preconditioned vectors in the
-// cycle's precision, vector q of RHS b at base + q * vlen + b * vstride.
+// (fgmres.cu).  V: m+1 basis vectors and Z: m preconditioned vectors, both
+// in the cycle's precision; vector q of RHS b at base + q * vlen + b * vstride.
 constexpr int FG_MAXM = 32;
 // Per-RHS FP64 scalars of the restart cycle: the rotated Hessenberg columns
 // (column j, row i), the Gram matrix of V (row a, column b: <v_a, v_b>), the
@@ -259,12 +262,14 @@ struct FgLayout {
 };
 struct FgArgs {
   Grid g;                  // fine level
-  Op0Consts<double> c0;    // fine operator (FP64)
+  Op0Consts<double> c0;    // fine operator (FP64: restart residual)
   const double* kf;
+  Op0Consts<float> c0f;    // and in FP32 (Arnoldi passes of the mixed path)
+  const float* kf32;
   int B, m;
   int nbr, ncx, ns, nvp;   // blocks per RHS, strip columns, strips, values per partial record
   long long vlen;          // g.vstride * B
-  double2* V;
+  void* V;
   void* Z;
   double2* X;
   const double2* b;
@@ -286,7 +291,7 @@ struct FgArgs {
 };
 // Strip geometry and blocks per RHS (nbr, ncx, ns, nvp) for a fine grid.
 void fg_geometry(const Grid& g, int B, bool fp64z, FgArgs& a);
-void launch_fg_restart(const FgArgs& a, cudaStream_t s);
+template <class T> void launch_fg_restart(const FgArgs& a, cudaStream_t s);
 template <class T> void launch_fg_prep(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s);
 template <class T> void launch_fg_dots(const FgArgs& a, int j, const cx<T>* z, cudaStream_t s);
 template <class T> void launch_fg_orth(const FgArgs& a, int j, cudaStream_t s);

@@ -203,16 +203,13 @@ __global__ void __launch_bounds__(BX * BY) k_vecnorm_fin(Grid g, const cx<T>* __
 
 // ------------------------------------------------------------------ transfers
 
-// 1D weights of Eq. (xex) as a column stencil: fine offset a - 2J in -2..2.
-template <class T> __device__ __forceinline__ T bw(int d) {
-  return d == 0 ? T(0.75) : (d == 1 || d == -1) ? T(0.5) : T(0.125);
-}
-
 // r_c(I,J) = 1/4 sum_{a,b=-2..2} w(a) w(b) r_f(2I+a, 2J+b)   (R = P^T / 4)
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<T>* __restrict__ rf,
-                                                      cx<T>* __restrict__ rc, const int* __restrict__ active) {
+                                                      cx<T>* __restrict__ rc, const int* __restrict__ active,
+                                                      Xfer xw) {
   NODE_INDEX
+  const T c0 = T(xw.w0), c1 = T(xw.w1), c2 = T(xw.w2);
   if (active && !active[rhs]) return;
   if (i > g.nx) return;
   const cx<T>* f = rf + (long long)rhs * gf.vstride;
@@ -223,10 +220,10 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<
 #pragma unroll
     for (int b = -2; b <= 2; ++b) {
       const cx<T>* row = f + pc + b * gf.pitch;
-      cx<T> t = scl<T>(T(0.125), add<T>(row[-2], row[2]));
-      t = add<T>(t, scl<T>(T(0.5), add<T>(row[-1], row[1])));
-      t = add<T>(t, scl<T>(T(0.75), row[0]));
-      acc = add<T>(acc, scl<T>(bw<T>(b), t));
+      cx<T> t = scl<T>(c2, add<T>(row[-2], row[2]));
+      t = add<T>(t, scl<T>(c1, add<T>(row[-1], row[1])));
+      t = add<T>(t, scl<T>(c0, row[0]));
+      acc = add<T>(acc, scl<T>(xw.w<T>(b), t));
     }
     rc[off + g.at(i, j)] = scl<T>(T(0.25), acc);
   }
@@ -235,8 +232,10 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<
 // x_f(i,j) += sum_{I,J} P(i,I) P(j,J) e_c(I,J)   (Eq. (xex) in each direction)
 template <class T>
 __global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const cx<T>* __restrict__ ec,
-                                                         cx<T>* __restrict__ xf, const int* __restrict__ active) {
+                                                         cx<T>* __restrict__ xf, const int* __restrict__ active,
+                                                         Xfer xw) {
   PACK_INDEX(T)
+  const T c0 = T(xw.w0), c1 = T(xw.w1), c2 = T(xw.w2);
   if (active && !active[rhs]) return;
   if (nv <= 0) return;
   const cx<T>* c = ec + (long long)rhs * gc.vstride;
@@ -250,14 +249,14 @@ __global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const 
       const int i = i0 + n, I = i >> 1;
       auto rowval = [&](int JJ) -> cx<T> {
         const cx<T>* row = c + gc.at(I, JJ);
-        if (i & 1) return scl<T>(T(0.5), add<T>(row[0], row[1]));
-        return add<T>(scl<T>(T(0.125), add<T>(row[-1], row[1])), scl<T>(T(0.75), row[0]));
+        if (i & 1) return scl<T>(c1, add<T>(row[0], row[1]));
+        return add<T>(scl<T>(c2, add<T>(row[-1], row[1])), scl<T>(c0, row[0]));
       };
       cx<T> v;
       if (j & 1) {
-        v = scl<T>(T(0.5), add<T>(rowval(J), rowval(J + 1)));
+        v = scl<T>(c1, add<T>(rowval(J), rowval(J + 1)));
       } else {
-        v = add<T>(scl<T>(T(0.125), add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(T(0.75), rowval(J)));
+        v = add<T>(scl<T>(c2, add<T>(rowval(J - 1), rowval(J + 1))), scl<T>(c0, rowval(J)));
       }
       xv.v[n] = add<T>(xv.v[n], v);
     }
@@ -371,13 +370,13 @@ void launch_vecnorm_fin(const Grid& g, const cx<T>* v, int B, double* out, doubl
 }
 template <class T>
 void launch_restrict(const Grid& gf, const Grid& gc, const cx<T>* rf, cx<T>* rc, int B, const int* active,
-                     cudaStream_t s) {
-  k_restrict<T><<<node_grid(gc, B), dim3(BX, BY), 0, s>>>(gf, gc, rf, rc, active);
+                     const Xfer& xw, cudaStream_t s) {
+  k_restrict<T><<<node_grid(gc, B), dim3(BX, BY), 0, s>>>(gf, gc, rf, rc, active, xw);
 }
 template <class T>
 void launch_prolong_add(const Grid& gf, const Grid& gc, const cx<T>* ec, cx<T>* xf, int B, const int* active,
-                        cudaStream_t s) {
-  k_prolong_add<T><<<pack_grid(gf, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(gf, gc, ec, xf, active);
+                        const Xfer& xw, cudaStream_t s) {
+  k_prolong_add<T><<<pack_grid(gf, B, PK<T>::NP), dim3(BX, BY), 0, s>>>(gf, gc, ec, xf, active, xw);
 }
 template <class T>
 void launch_copy_masked(const Grid& g, const cx<T>* src, cx<T>* dst, int B, const int* active, cudaStream_t s) {
@@ -402,9 +401,10 @@ void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, 
                                  const int*, cudaStream_t);                                                        \
   template void launch_resnorm_stop<T>(const Grid&, const OpView<T>&, const cx<T>*, const cx<T>*, int, const Ctl&, \
                                        int, cudaStream_t);                                                         \
-  template void launch_restrict<T>(const Grid&, const Grid&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t); \
+  template void launch_restrict<T>(const Grid&, const Grid&, const cx<T>*, cx<T>*, int, const int*, const Xfer&,   \
+                                   cudaStream_t);                                                                  \
   template void launch_prolong_add<T>(const Grid&, const Grid&, const cx<T>*, cx<T>*, int, const int*,            \
-                                      cudaStream_t);                                                               \
+                                      const Xfer&, cudaStream_t);                                                  \
   template void launch_copy_masked<T>(const Grid&, const cx<T>*, cx<T>*, int, const int*, cudaStream_t);          \
   template void launch_pack<T>(const Grid&, const double2*, cx<T>*, int, int, cudaStream_t);                      \
   template void launch_unpack<T>(const Grid&, const cx<T>*, double2*, int, int, cudaStream_t);                    \

@@ -1,6 +1,6 @@
 // Device helpers shared by the coarse-cycle interpreters (coarse.cu and
 // coop.cu): operator apply and inverse diagonal of a level described by a
-// CLevel, and the 1D weights of Eq. (xex).
+// CLevel.
 #pragma once
 #include "internal.h"
 
@@ -20,10 +20,6 @@ __device__ __forceinline__ cx<T> lv_apply(const CLevel<T>& L, const cx<T>* x, in
 template <class T> __device__ __forceinline__ cx<T> lv_dinv(const CLevel<T>& L, int i, int j) {
   if (L.kind == 1) return Op0<T>{L.c0, L.kf, L.g.nx, L.g.ny}.diag_inv(i, j);
   return L.dinv[(long long)j * (L.g.nx + 1) + i];
-}
-
-template <class T> __device__ __forceinline__ T cbw(int d) {
-  return d == 0 ? T(0.75) : (d == 1 || d == -1) ? T(0.5) : T(0.125);
 }
 
 }  // namespace hmg

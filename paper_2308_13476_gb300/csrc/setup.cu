@@ -8,9 +8,6 @@
 
 namespace hmg {
 
-__device__ __forceinline__ double bwd(int d) {
-  return d == 0 ? 0.75 : (d == 1 || d == -1) ? 0.5 : (d == 2 || d == -2) ? 0.125 : 0.0;
-}
 
 // Coupling of node (i, j) to node (i+dx, j+dy) in a level operator; for the
 // matrix-free fine operator the mass term carries the shift (1 + i beta2).
@@ -79,7 +76,7 @@ __global__ void s_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, doubl
 // One thread per (coarse node, stencil entry):
 // A_c[(I,J),(I2,J2)] = sum 1/4 w(fa-2I) w(fb-2J) * A_f[(fa,fb),(fa2,fb2)] * w(fa2-2I2) w(fb2-2J2)
 __global__ void s_galerkin(OpView<double> fine, int fnx, int fny, int rf, double2* __restrict__ cst, int cnx, int cny,
-                           int rc, double beta2) {
+                           int rc, double beta2, Xfer xw) {
   const int S = (2 * rc + 1) * (2 * rc + 1);
   const long long plane = (long long)(cnx + 1) * (cny + 1);
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,7 +94,7 @@ __global__ void s_galerkin(OpView<double> fine, int fnx, int fny, int rf, double
       for (int a = -2; a <= 2; ++a) {
         const int fa = 2 * I + a;
         if (fa < 0 || fa > fnx) continue;
-        const double wr = 0.25 * bwd(a) * bwd(b);
+        const double wr = 0.25 * xw.w<double>(a) * xw.w<double>(b);
         for (int b2 = -2; b2 <= 2; ++b2) {
           const int fb2 = 2 * J2 + b2;
           const int ey = fb2 - fb;
@@ -107,7 +104,7 @@ __global__ void s_galerkin(OpView<double> fine, int fnx, int fny, int rf, double
             const int ex = fa2 - fa;
             if (fa2 < 0 || fa2 > fnx || ex < -rf || ex > rf) continue;
             const double2 cf = op_coef(fine, fnx, fny, fa, fb, ey, ex, beta2);
-            const double wgt = wr * bwd(a2) * bwd(b2);
+            const double wgt = wr * xw.w<double>(a2) * xw.w<double>(b2);
             acc.x += wgt * cf.x;
             acc.y += wgt * cf.y;
           }
@@ -263,7 +260,8 @@ __global__ void s_factors0(int n, double h, double k, double beta2, double2* g, 
 }
 
 // X_c[I][d] = sum_{a, a2} 1/2 w(a - 2I) X[a][a2 - a] w(a2 - 2(I + d)), one thread per (I, d).
-__global__ void s_galerkin_1d(const double2* __restrict__ X, int nf, int rf, double2* __restrict__ Xc, int rc) {
+__global__ void s_galerkin_1d(const double2* __restrict__ X, int nf, int rf, double2* __restrict__ Xc, int rc,
+                              Xfer xw) {
   const int nc = nf / 2, wc = 2 * rc + 1, wf = 2 * rf + 1;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (nc + 1) * wc) return;
@@ -275,7 +273,7 @@ __global__ void s_galerkin_1d(const double2* __restrict__ X, int nf, int rf, dou
       for (int a2 = 2 * I2 - 2; a2 <= 2 * I2 + 2; ++a2) {
         const int e = a2 - a;
         if (a2 < 0 || a2 > nf || e < -rf || e > rf) continue;
-        const double wgt = 0.5 * bwd(a - 2 * I) * bwd(a2 - 2 * I2);
+        const double wgt = 0.5 * xw.w<double>(a - 2 * I) * xw.w<double>(a2 - 2 * I2);
         const double2 xv = X[a * wf + e + rf];
         acc.x += wgt * xv.x;
         acc.y += wgt * xv.y;
@@ -305,9 +303,9 @@ __global__ void s_diaginv_op(OpView<double> v, int nx, int ny, double omega, dou
 void launch_factors0(int n, double h, double k, double beta2, double2* g, double2* hf, double2* w, cudaStream_t s) {
   s_factors0<<<cdiv(n + 1, 128), 128, 0, s>>>(n, h, k, beta2, g, hf, w);
 }
-void launch_galerkin_1d(const double2* X, int nf, int rf, double2* Xc, int rc, cudaStream_t s) {
+void launch_galerkin_1d(const double2* X, int nf, int rf, double2* Xc, int rc, const Xfer& xw, cudaStream_t s) {
   const int n = (nf / 2 + 1) * (2 * rc + 1);
-  s_galerkin_1d<<<cdiv(n, 128), 128, 0, s>>>(X, nf, rf, Xc, rc);
+  s_galerkin_1d<<<cdiv(n, 128), 128, 0, s>>>(X, nf, rf, Xc, rc, xw);
 }
 void launch_real_part(const double2* a, double* b, long long n, cudaStream_t s) {
   if (n > 0) s_real_part<<<cdiv(n, 256), 256, 0, s>>>(a, b, n);
@@ -322,10 +320,10 @@ void launch_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, d
   s_op0consts<<<1, 32, 0, s>>>(c64, c32, h, k, omega, beta2);
 }
 void launch_galerkin(const OpView<double>& fine, int fnx, int fny, double2* cst, int cnx, int cny, int rc, double beta2,
-                     cudaStream_t s) {
+                     const Xfer& xw, cudaStream_t s) {
   const int rf = fine.kind == 1 ? 1 : fine.kind;
   const long long n = (long long)(cnx + 1) * (cny + 1) * (2 * rc + 1) * (2 * rc + 1);
-  s_galerkin<<<cdiv(n, 128), 128, 0, s>>>(fine, fnx, fny, rf, cst, cnx, cny, rc, beta2);
+  s_galerkin<<<cdiv(n, 128), 128, 0, s>>>(fine, fnx, fny, rf, cst, cnx, cny, rc, beta2, xw);
 }
 void launch_diaginv(const double2* st, int rc, long long plane, double omega, double2* dinv, cudaStream_t s) {
   s_diaginv<<<cdiv(plane, 256), 256, 0, s>>>(st, rc, plane, omega, dinv);

@@ -77,3 +77,15 @@ def test_krylov_option_validated_without_gpu(lib_path):
     assert lib.mg_setup(ctypes.byref(h), 8, 8, 0.1, None, 5.0, 0.7, 0, ctypes.byref(o)) == hm.MG_EINVAL
     assert b"precision 0 or 1" in lib.mg_last_error()
     assert h.value is None
+
+
+def test_transfer_option_validated_without_gpu(lib_path):
+    import paper_2308_13476_gb300 as hm
+    lib = hm.load_library()
+    o = hm.mg_default_options()
+    assert o.transfer == 0
+    h = ctypes.c_void_p()
+    o.transfer = 2
+    assert lib.mg_setup(ctypes.byref(h), 8, 8, 0.1, None, 5.0, 0.7, 0, ctypes.byref(o)) == hm.MG_EINVAL
+    assert b"transfer" in lib.mg_last_error()
+    assert h.value is None
