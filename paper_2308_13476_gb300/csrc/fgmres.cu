@@ -70,10 +70,32 @@ template <> __device__ __forceinline__ Op0<float> op_t<float>(const FgArgs& a) {
   return Op0<float>{a.c0f, a.kf32, a.g.nx, a.g.ny};
 }
 
-template <class T> __device__ __forceinline__ T warp_sum_t(T t) {
+// Sums four values over a warp in six shuffles: the first two rounds halve
+// the values each lane carries (lanes 0-15 keep a, b and 16-31 keep c, d;
+// then lanes with bit 3 clear keep the first of their pair), the last three
+// are plain butterflies.  Lane 8w + u (u < 8) returns the total of value w
+// (a, b, c, d for w = 0..3).  Fixed order: bitwise reproducible.
+template <class T> __device__ __forceinline__ T warp_sum4(T a, T b, T c, T d, int lane) {
+  const bool hi16 = lane & 16;
+  T k0 = hi16 ? c : a, k1 = hi16 ? d : b;
+  const T s0 = hi16 ? a : c, s1 = hi16 ? b : d;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool hi8 = lane & 8;
+  T k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  return t;
+  for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  return k;
+}
+
+template <class T> constexpr bool PREFETCH = sizeof(T) == 4;
+
+// The thread's FR rows of one vector (zero where pr < 0: outside the grid).
+template <class T>
+__device__ __forceinline__ void load_rows(const cx<T>* __restrict__ v, const int (&pr)[FR], cx<T> (&out)[FR]) {
+#pragma unroll
+  for (int r = 0; r < FR; ++r) out[r] = pr[r] >= 0 ? v[pr[r]] : mk<T>(T(0), T(0));
 }
 
 struct StripPos {
@@ -229,31 +251,34 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_fg_dots(FgArgs a, const cx<T>* 
         u[r] = vj[p];
       }
     }
+    // v_q at the thread's rows; FP32 fetches v_{q+1} before v_q is used
+    // (FP64 is bound by its arithmetic and has no registers to spare)
+    cx<T> cur[FR], nxt[FR];
+    load_rows<T>((const cx<T>*)a.V + off, pr, cur);
     for (int q = 0; q <= jj; ++q) {
-      const cx<T>* vq = (const cx<T>*)a.V + q * a.vlen + off;
+      if (PREFETCH<T> && q < jj) load_rows<T>((const cx<T>*)a.V + (q + 1) * a.vlen + off, pr, nxt);
       T dr = T(0), di = T(0), gr = T(0), gi = T(0);
 #pragma unroll
       for (int r = 0; r < FR; ++r) {
-        if (pr[r] < 0) continue;
-        const cx<T> v = vq[pr[r]];
+        const cx<T> v = cur[r];   // zero outside the grid
         dr = fma(v.x, w[r].x, fma(v.y, w[r].y, dr));
         di = fma(v.x, w[r].y, fma(-v.y, w[r].x, di));
         gr = fma(v.x, u[r].x, fma(v.y, u[r].y, gr));
         gi = fma(v.x, u[r].y, fma(-v.y, u[r].x, gi));
       }
-      dr = warp_sum_t<T>(dr);
-      di = warp_sum_t<T>(di);
-      if (q < jj) {
-        gr = warp_sum_t<T>(gr);
-        gi = warp_sum_t<T>(gi);
+      // the warp's four sums; lanes 0, 8, 16, 24 then hold dr, di, gr, gi,
+      // widened to FP64 into the warp's column of red
+      const T t = warp_sum4<T>(dr, di, gr, gi, lane);
+      if ((lane & 7) == 0) {
+        const int which = lane >> 3;   // 0 dr, 1 di, 2 gr, 3 gi
+        if (which < 2) red[2 * q + which][warp] += (double)t;
+        else if (q < jj) red[2 * (jj + 1) + 2 * q + which - 2][warp] += (double)t;
       }
-      if (lane == 0) {   // each warp's strip sums widened to FP64
-        red[2 * q][warp] += (double)dr;
-        red[2 * q + 1][warp] += (double)di;
-        if (q < jj) {
-          red[2 * (jj + 1) + 2 * q][warp] += (double)gr;
-          red[2 * (jj + 1) + 2 * q + 1][warp] += (double)gi;
-        }
+      if (PREFETCH<T>) {
+#pragma unroll
+        for (int r = 0; r < FR; ++r) cur[r] = nxt[r];
+      } else if (q < jj) {
+        load_rows<T>((const cx<T>*)a.V + (q + 1) * a.vlen + off, pr, cur);
       }
     }
   }
@@ -398,15 +423,21 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_fg_orth(FgArgs a, int jj) {
         w[r] = op.apply(zj, pr[r], g.pitch, sp.i, j);
       }
     }
+    cx<T> cur[FR], nxt[FR];
+    load_rows<T>((const cx<T>*)a.V + off, pr, cur);
     for (int q = 0; q <= jj; ++q) {
-      const cx<T>* vq = (const cx<T>*)a.V + q * a.vlen + off;
+      if (PREFETCH<T> && q < jj) load_rows<T>((const cx<T>*)a.V + (q + 1) * a.vlen + off, pr, nxt);
       const cx<T> h = hs[q];
 #pragma unroll
       for (int r = 0; r < FR; ++r) {
-        if (pr[r] < 0) continue;
-        const cx<T> v = vq[pr[r]];
-        w[r].x -= h.x * v.x - h.y * v.y;
-        w[r].y -= h.x * v.y + h.y * v.x;
+        w[r].x -= h.x * cur[r].x - h.y * cur[r].y;
+        w[r].y -= h.x * cur[r].y + h.y * cur[r].x;
+      }
+      if (PREFETCH<T>) {
+#pragma unroll
+        for (int r = 0; r < FR; ++r) cur[r] = nxt[r];
+      } else if (q < jj) {
+        load_rows<T>((const cx<T>*)a.V + (q + 1) * a.vlen + off, pr, cur);
       }
     }
     T part = T(0);   // this strip's sum in T, widened once
@@ -433,15 +464,17 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_fg_orth(FgArgs a, int jj) {
 
 // ------------------------------------------------------------------ update
 
+// x += sum_q y_q z_q: the correction is summed in T (for the mixed path an
+// FP32 correction, like the refinement loop's x += e) and added to x in FP64.
 template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_update(FgArgs a) {
-  __shared__ double2 ys[FG_MAXM];
+  __shared__ cx<T> ys[FG_MAXM];
   const int rhs = blockIdx.z;
   const int k = a.kst[2 * rhs];
   if (k == 0) return;   // block-uniform
   const int tid = threadIdx.x + threadIdx.y * FBX;
   const FgLayout L{a.m};
   const double* S = a.S + (long long)rhs * a.sd;
-  if (tid < k) ys[tid] = make_double2(S[L.y(tid)], S[L.y(tid) + 1]);
+  if (tid < k) ys[tid] = mk<T>((T)S[L.y(tid)], (T)S[L.y(tid) + 1]);
   __syncthreads();
   const Grid& g = a.g;
   const long long off = (long long)rhs * g.vstride;
@@ -449,26 +482,26 @@ template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_update(FgArg
   for (int s = blockIdx.x; s < a.ns; s += a.nbr) {
     const StripPos sp = strip_pos(a, s);
     if (sp.i > g.nx) continue;
-    double2 acc[FR];
+    cx<T> acc[FR];
     int pr[FR];
 #pragma unroll
     for (int r = 0; r < FR; ++r) {
       const int j = sp.j0 + r * FBY;
       pr[r] = j <= g.ny ? g.at(sp.i, j) : -1;
-      acc[r] = make_double2(0.0, 0.0);
+      acc[r] = mk<T>(T(0), T(0));
     }
     for (int q = 0; q < k; ++q) {
       const cx<T>* zq = (const cx<T>*)a.Z + q * a.vlen + off;
-      const double2 y = ys[q];
+      const cx<T> y = ys[q];
 #pragma unroll
       for (int r = 0; r < FR; ++r) {
         if (pr[r] < 0) continue;
-        acc[r] = fma_c<double>(to_d(zq[pr[r]]), y, acc[r]);
+        acc[r] = fma_c<T>(zq[pr[r]], y, acc[r]);
       }
     }
 #pragma unroll
     for (int r = 0; r < FR; ++r)
-      if (pr[r] >= 0) x[pr[r]] = add<double>(x[pr[r]], acc[r]);
+      if (pr[r] >= 0) x[pr[r]] = add<double>(x[pr[r]], to_d(acc[r]));
   }
 }
 
