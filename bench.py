@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--no-fp64-line", action="store_true", help="skip the FP64 comparison solve")
     p.add_argument("--no-ff-line", action="store_true", help="skip the float-float outer-loop variant")
     p.add_argument("--cpu-sample-cycles", type=int, default=2)
-    p.add_argument("--workload", default="batched", choices=["batched", "layered", "ragged", "gradient"],
+    p.add_argument("--workload", default="batched", choices=["batched", "layered", "ragged", "gradient", "two-grid"],
                    help="batched: the bench line (default); the others print one JSON line for the other "
                         "workloads: layered velocity model at --freq Hz, a ragged batch of 32 problems, the "
                         "adjoint gradient of a receiver misfit")
@@ -488,6 +488,65 @@ def run_layered(a):
     print(json.dumps(out))
 
 
+def run_two_grid(a):
+    """Dense two-grid analysis (mg_two_grid): the four columns of Table conv1
+    (Linear / Bezier transfers, A_c on A or on the CSL with beta2 = 0.7) at
+    k = 30, kh = 0.625 (49 x 49 grid, N = 2401), one post-smoothing Jacobi
+    step, omega = 4.5.  FP64 on CUDA cores; the roofline is the FP64 FMA rate
+    (FLOPs of the dense products, the two Gauss-Jordan inverses, the Cholesky
+    and the power method)."""
+    import torch
+    import paper_2308_13476_gb300 as hm
+    torch.cuda.set_device(0)
+    k = 30.0
+    n = int(round(k / 0.625))
+    N, Nc = (n + 1) ** 2, (n // 2 + 1) ** 2
+    variants = [("linear", 0.0), ("linear", 0.7), ("bezier", 0.0), ("bezier", 0.7)]
+    results, ms_all, flops_all = {}, [], 0.0
+    for kind, beta2 in variants:
+        s = hm.Solver(n, n, 1.0 / n, k, beta2, transfer=kind)
+        r = s.two_grid()   # warm-up
+        for _ in range(max(0, a.warmup - 1)):
+            s.two_grid()
+        ms, r = _event_ms(lambda: s.two_grid(), a.steps)
+        s.close()
+        # complex MACs: Y = A1^-1 R (Nc^2 N), P Y (N^2 Nc), CG (N^3), T0 (N^3), T0^H T0 (N^3), E^H E (N^3),
+        # two Gauss-Jordan inverses (2 Nc^3, 2 N^3), Cholesky (N^3 / 6), power method (N^2 per iteration)
+        cmac = Nc * Nc * N + N * N * Nc + 4.0 * N ** 3 + 2.0 * Nc ** 3 + 2.0 * N ** 3 + N ** 3 / 6.0 + \
+            r["iterations"] * N * N
+        flops_all += 8.0 * cmac * a.steps
+        ms_all.append(ms)
+        results[f"{kind}/{'C' if beta2 else 'A'}"] = {"norm_t0": r["norm_t0"], "hpd": r["hpd"],
+                                                       "gamma_ratio": r["gamma_ratio"],
+                                                       "power_iterations": r["iterations"], "ms": ms}
+    t = sum(ms_all) * a.steps / 1e3
+    peak = 1194.0   # measured FP64 FMA rate of this pool's GB300 (GFLOP/s)
+    line = {"metric": "two-grid analyses/s (dense T0, ||T0||_2, Gamma~ HPD test and kappa_1; Table conv1, k = 30)",
+            "value": len(variants) * a.steps / t, "unit": "analyses/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": sum(ms_all), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"MP 2-A, k = {k:g}, {n + 1} x {n + 1} grid (N = {N}), two finest levels",
+                       "variants": [f"{kk}/{'C' if b else 'A'}" for kk, b in variants], "nu": 1, "omega": 4.5},
+            "roofline": {"bound": "alu", "achieved": flops_all / t / 1e9, "peak": peak, "unit": "GFLOP/s",
+                         "frac": flops_all / t / 1e9 / peak, "traffic": None,
+                         "kernel": "all kernels of one analysis (FP64 complex GEMM, Gauss-Jordan, Cholesky, power "
+                                   "method); peak = FP64 FMA rate measured on this pool"},
+            "results": results}
+    if a.cpu_sample_cycles > 0:   # the oracle's dense analysis of one variant (Bezier / CSL)
+        from oracle import analysis as oan
+        t0 = time.perf_counter()
+        A, P, R, Ac = oan.two_grid_parts(n, n, 1.0 / n, k, 0.7, coarsen_on="C")
+        np.linalg.norm(oan.two_grid_matrix(A, P, R, Ac, 4.5, 1), 2)
+        G = oan.gamma_tilde(A, P, R, Ac, 4.5)
+        oan.is_hpd(G)
+        np.linalg.norm(G, 1) / np.linalg.cond(G, 1)
+        tc = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / tc, "unit": "analyses/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "one oracle analysis (numpy dense SVD, inverse, Cholesky) of the Bezier/CSL "
+                                          "variant; numpy's BLAS threads over the host cores"}
+    print(json.dumps(line))
+
+
 def run_ragged(a):
     """Ragged batch: 32 square constant-k problems with interval counts drawn
     in [127, 1023] and rounded to c * 2^m (synth.ragged_sizes, seed 3),
@@ -568,7 +627,8 @@ def main():
         run_probe(a)
         return
     if a.workload != "batched":
-        {"layered": run_layered, "ragged": run_ragged, "gradient": run_gradient}[a.workload](a)
+        {"layered": run_layered, "ragged": run_ragged, "gradient": run_gradient,
+         "two-grid": run_two_grid}[a.workload](a)
         return
     if a.impl == "reference":
         run_reference(a)

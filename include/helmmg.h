@@ -210,6 +210,30 @@ mg_status mg_get_stencil(mg_handle h, int level, void* out);
  * application c+1.  hist: host double[B * cap]. */
 mg_status mg_history(mg_handle h, double* hist, int cap);
 
+/* ---- analysis ---- */
+
+/* Dense two-grid analysis of the handle's two finest levels (Sec. 3), for
+ * small grids (at most 4096 fine nodes):
+ *   T0 = (I - P A_1^{-1} R A)(I - X^{-1} A)^nu  (Eq. (tgi1), X = omega diag(A):
+ *        nu weighted-Jacobi sweeps, then the coarse-grid correction),
+ *   Gamma~ = A^H D~^H + D~ A - A^H D~^H D~ A, D~ = X^{-1} + P A_1^{-1} R
+ *        (Definition def2s),
+ * with A the fine operator, A_1 the handle's level-1 Galerkin operator (built
+ * on the CSL with the handle's beta2; beta2 = 0 builds it on A), P and
+ * R = P^T / 4 the handle's transfers (option transfer) and omega the handle's.
+ * out (host, 6 doubles): [0] ||T0||_2 (Table conv1; power method on
+ * T0^H T0, stopped when the Rayleigh quotient moves by at most 1e-14 of
+ * itself over 100 iterations, or after max_iter), [1] 1.0 if Gamma~ is
+ * Hermitian (to 1e-10 of its largest entry) and its Cholesky factorisation
+ * succeeds, else 0.0 (the HPD test of Sec. 3), [2] ||Gamma~||_1 /
+ * kappa_1(Gamma~) (Cor. mgc2, Table opt1; NaN if Gamma~ is singular), [3]
+ * power iterations run, [4] 1.0 if the power method met its stopping test,
+ * [5] 1.0 if A_1 was singular.  1 <= nu <= 8, 200 <= max_iter <= 1e6.
+ * Device scratch (about 5 N^2 complex128 for N fine nodes) is allocated and
+ * freed inside the call; MG_ENOMEM if it does not fit.  MG_EINVAL for grids
+ * above 4096 nodes or a one-level hierarchy; MG_ESTATE on a ragged handle. */
+mg_status mg_two_grid(mg_handle h, int nu, int max_iter, double* out);
+
 /* ---- instrumentation ---- */
 
 /* Time one kernel of the hierarchy in the handle's precision: `what` = 0 one

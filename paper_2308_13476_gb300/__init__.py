@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "MG_OK", -1: "MG_EINVAL", -2: "MG_ENOMEM", -3: "MG_ECUDA", -4
                 -5: "MG_EDIVERGED", -6: "MG_ETIMEOUT", -7: "MG_ESTATE"}
 EXPORTED = ["mg_default_options", "mg_setup", "mg_solve", "mg_adjoint", "mg_gradient", "mg_destroy",
             "mg_last_error", "mg_level_info", "mg_apply", "mg_get_stencil", "mg_history", "mg_profile",
-            "mg_counters", "mg_residual_norm_static", "mg_setup_ragged"]
+            "mg_counters", "mg_residual_norm_static", "mg_setup_ragged", "mg_two_grid"]
 
 
 class HelmmgUnavailable(RuntimeError):
@@ -74,6 +74,7 @@ def load_library(path=LIB_PATH):
     lib.mg_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
     lib.mg_residual_norm_static.argtypes = [i, i, d, vp, d, vp, vp, vp, vp]
     lib.mg_setup_ragged.argtypes = [ctypes.POINTER(vp), i, ip, ip, dp, dp, dp, ctypes.POINTER(MgOptions)]
+    lib.mg_two_grid.argtypes = [vp, i, i, dp]
     for name in EXPORTED:
         if name not in ("mg_default_options", "mg_last_error"):
             getattr(lib, name).restype = ctypes.c_int
@@ -182,6 +183,16 @@ def mg_history(hdl, batch, cap):
     buf = (ctypes.c_double * (batch * cap))()
     _check(load_library().mg_history(ctypes.c_void_p(hdl), buf, int(cap)))
     return [list(buf[b * cap:(b + 1) * cap]) for b in range(batch)]
+
+
+def mg_two_grid(hdl, nu=1, max_iter=20000):
+    """Dense two-grid analysis of the two finest levels: a dict with the
+    spectral norm of T0, whether Gamma~ is HPD, ||Gamma~||_1 / kappa_1 and
+    the power-method bookkeeping (see include/helmmg.h)."""
+    out = (ctypes.c_double * 6)()
+    _check(load_library().mg_two_grid(ctypes.c_void_p(hdl), int(nu), int(max_iter), out))
+    return {"norm_t0": out[0], "hpd": out[1] == 1.0, "gamma_ratio": out[2], "iterations": int(out[3]),
+            "converged": out[4] == 1.0, "coarse_singular": out[5] == 1.0}
 
 
 def mg_profile(hdl, what, level, reps):
@@ -380,6 +391,9 @@ class Solver:
 
     def history(self, cap):
         return mg_history(self.handle, self.batch, cap)
+
+    def two_grid(self, nu=1, max_iter=20000):
+        return mg_two_grid(self.handle, nu, max_iter)
 
     def profile(self, what, level=0, reps=20):
         return mg_profile(self.handle, what, level, reps)

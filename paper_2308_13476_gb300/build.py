@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhelmmg.so")
-SOURCES = ["capi.cu", "kernels_level.cu", "kernels_gmres.cu", "setup.cu", "coarse.cu", "coop.cu", "fused.cu", "noalloc.cu", "gmres_march.cu", "kron_march.cu", "mixed_ff.cu", "fgmres.cu"]
+SOURCES = ["capi.cu", "kernels_level.cu", "kernels_gmres.cu", "setup.cu", "coarse.cu", "coop.cu", "fused.cu", "noalloc.cu", "gmres_march.cu", "kron_march.cu", "mixed_ff.cu", "fgmres.cu", "analysis.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

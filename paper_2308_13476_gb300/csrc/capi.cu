@@ -1304,6 +1304,21 @@ mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, dou
   return profile_t<double>(h, what, level, reps, ms, bytes);
 }
 
+mg_status mg_two_grid(mg_handle h, int nu, int max_iter, double* out) {
+  if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
+  if (!h || !out) FAIL(MG_EINVAL, "NULL handle or output");
+  if (nu < 1 || nu > 8 || max_iter < 200 || max_iter > 1000000) FAIL(MG_EINVAL, "need 1 <= nu <= 8 and 200 <= max_iter <= 1e6");
+  if (h->nlev < 2) FAIL(MG_EINVAL, "the two-grid analysis needs a hierarchy with two levels");
+  const Grid& g0 = h->lev[0].g;
+  const Grid& g1 = h->lev[1].g;
+  if ((long long)(g0.nx + 1) * (g0.ny + 1) > 4096) FAIL(MG_EINVAL, "the two-grid analysis is dense: at most 4096 fine nodes");
+  cudaError_t e = two_grid_analysis(op64(h, 0), op64(h, 1), g0.nx, g0.ny, g1.nx, g1.ny, h->opt.omega, h->xw, nu,
+                                    max_iter, out, (cudaStream_t)h->opt.stream);
+  if (e == cudaErrorMemoryAllocation) FAIL(MG_ENOMEM, "two-grid analysis: device allocation failed");
+  if (e != cudaSuccess) FAIL(MG_ECUDA, "two-grid analysis: %s", cudaGetErrorString(e));
+  return MG_OK;
+}
+
 mg_status mg_history(mg_handle h, double* hist, int cap) {
   if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");

@@ -297,6 +297,14 @@ template <class T> void launch_fg_dots(const FgArgs& a, int j, const cx<T>* z, c
 template <class T> void launch_fg_orth(const FgArgs& a, int j, cudaStream_t s);
 template <class T> void launch_fg_update(const FgArgs& a, cudaStream_t s);
 
+// Dense two-grid analysis of the two finest levels (analysis.cu).  out[0] =
+// ||T0||_2, out[1] = 1 if Gamma~ is Hermitian positive definite, out[2] =
+// ||Gamma~||_1 / kappa_1(Gamma~), out[3] = power iterations, out[4] = 1 if
+// the power method met its stopping test, out[5] = 1 if A_1 was singular.
+cudaError_t two_grid_analysis(const OpView<double>& fine, const OpView<double>& coarse, int fnx, int fny, int cnx,
+                              int cny, double omega, const Xfer& xw, int nu, int max_iter, double* out,
+                              cudaStream_t s);
+
 // Gradient of the receiver misfit (kernels_level.cu).
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u,
                      const double2* lam, int nsrc, double* g, cudaStream_t s);
