@@ -90,6 +90,8 @@ template <class T> __device__ __forceinline__ T warp_sum4(T a, T b, T c, T d, in
 }
 
 template <class T> constexpr bool PREFETCH = sizeof(T) == 4;
+// resident blocks per SM the Arnoldi passes are compiled for (FP32: 24 warps)
+template <class T> constexpr int FG_MINB = sizeof(T) == 4 ? 3 : 2;
 
 // The thread's FR rows of one vector (zero where pr < 0: outside the grid).
 template <class T>
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fg_prep(FgArgs a, int jj, cx<T>* _
 // ------------------------------------------------------------------ dots (MGS coefficients)
 
 template <class T>
-__global__ void __launch_bounds__(FTHREADS, 2) k_fg_dots(FgArgs a, const cx<T>* __restrict__ z, int jj) {
+__global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_dots(FgArgs a, const cx<T>* __restrict__ z, int jj) {
   __shared__ double red[FNV][FBY];
   __shared__ double mine[FNV], tot[FNV];
   const int rhs = blockIdx.z;
@@ -393,7 +395,7 @@ __device__ void fg_finish_step(const FgArgs& a, int rhs, int jj, double sumsq) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(FTHREADS, 2) k_fg_orth(FgArgs a, int jj) {
+__global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_orth(FgArgs a, int jj) {
   __shared__ cx<T> hs[FG_MAXM + 1];
   __shared__ double red[FBY], mine[1], tot[1];
   const int rhs = blockIdx.z;
