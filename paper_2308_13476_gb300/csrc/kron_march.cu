@@ -12,6 +12,7 @@
 // bandwidth-bound.  Outputs, reductions and scalar steps are those of
 // g_init and g_arn_a (kernels_gmres.cu); g_arn_b and g_update, which do not
 // apply A, are shared.
+#include <algorithm>
 #include <type_traits>
 
 #include "gmres.cuh"
@@ -220,15 +221,42 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
     staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
 }
 
-KGeo kron_geo(const Grid& g, int B) {
+constexpr int KCH[] = {64, 48, 32, 24, 16, 12, 8};   // candidate rows per chunk
+
+// Rows per chunk for a level: each warp marches ch + 2R rows, and the
+// launch runs in ceil(blocks / cap) rounds of the cap blocks the GPU holds
+// at once, so the chunk height minimising rounds x (ch + 2R) is taken (the
+// tallest on ties).  A fixed height can leave a last round of a few blocks:
+// 64-row chunks of a 513^2 level with 64 right-hand sides give 2.05 rounds.
+KGeo kron_geo(const Grid& g, int B, int R, long long cap) {
   KGeo k;
   k.ncw = cdiv(g.nx + 1, 32);
-  const long long want = 152LL * 64;   // warps to fill the GPU a few times over
-  int ch = 64;
-  while (ch > 8 && (long long)k.ncw * cdiv(g.ny + 1, ch) * B < want) ch /= 2;
-  k.ch = ch;
-  k.nchunks = cdiv(g.ny + 1, ch);
+  long long best = -1;
+  for (int ch : KCH) {
+    const long long blocks = (long long)cdiv((long long)k.ncw * cdiv(g.ny + 1, ch), KW) * B;
+    const long long cost = (long long)cdiv(blocks, cap) * (ch + 2 * R);
+    if (best < 0 || cost < best) {
+      best = cost;
+      k.ch = ch;
+    }
+  }
+  k.nchunks = cdiv(g.ny + 1, k.ch);
   return k;
+}
+
+// Blocks of km_arn_a<T, R, 2> (the kernel with the most state) resident on
+// the device at once.
+template <class T, int R> long long kron_capacity() {
+  static long long cap = 0;
+  if (!cap) {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, km_arn_a<T, R, 2>, KW * 32, 0);
+    cudaGetLastError();
+    cap = (long long)std::max(per, 1) * std::max(sms, 1);
+  }
+  return cap;
 }
 
 }  // namespace
@@ -238,9 +266,9 @@ template <class T> void launch_gmres_update(const Grid& g, cx<T>* x, const Gmres
 template <class T, int J> void launch_arn_b(const Grid& g, const GmresBufs& gb, cx<T>* un, int B, const int* active,
                                             cudaStream_t s);
 
-long long kron_march_blocks(const Grid& g, int B) {
-  const KGeo k = kron_geo(g, B);
-  return cdiv((long long)k.ncw * k.nchunks, KW);
+long long kron_march_blocks(const Grid& g, int B) {   // the most for any chunk height: the shortest
+  (void)B;
+  return cdiv((long long)cdiv(g.nx + 1, 32) * cdiv(g.ny + 1, KCH[sizeof(KCH) / sizeof(KCH[0]) - 1]), KW);
 }
 
 template <class T>
@@ -253,10 +281,10 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
   double* P = gb.partial;
   unsigned* tk = gb.tickets;
   double* st = gb.st;
-  const KGeo kg = kron_geo(g, B);
-  const dim3 grd(cdiv((long long)kg.ncw * kg.nchunks, KW), 1, B);
   auto run = [&](auto op, auto rad) {
     constexpr int R = decltype(rad)::value;
+    const KGeo kg = kron_geo(g, B, R, kron_capacity<T, R>());
+    const dim3 grd(cdiv((long long)kg.ncw * kg.nchunks, KW), 1, B);
     for (int step = 0; step < nu; ++step) {
       km_init<T, R><<<grd, KW * 32, 0, s>>>(g, kg, op, x, b, u0, st, P, tk, active);
       km_arn_a<T, R, 0><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
