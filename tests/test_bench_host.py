@@ -51,3 +51,36 @@ def test_job_throughput_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.job_throughput(2.0, 10.0) == (5.0, 2.0)
+
+
+def _args(argv, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    return bench, bench.parse()
+
+
+def test_oracle_cycle_counts_for_the_bench_lines(monkeypatch):
+    """The CPU baseline of each bench line scales by the oracle's own count
+    for that line (oracle/bench_cycles.json): the stand-alone cycle, FGMRES
+    around Jacobi cycles, FGMRES around the GMRES(3) cycle."""
+    bench, a = _args([], monkeypatch)
+    assert (a.smoother, a.nu, a.krylov, a.transfer) == ("gmres3", 2, 0, "bezier")
+    assert bench._cycles_from_cache(a) == 43
+    bench, a = _args(["--krylov", "20", "--smoother", "jacobi", "--nu", "1"], monkeypatch)
+    assert abs(a.beta2 - 0.7) < 1e-15
+    assert bench._cycles_from_cache(a) == 417
+    bench, a = _args(["--krylov", "10"], monkeypatch)
+    assert bench._cycles_from_cache(a) == 63
+    bench, a = _args(["--transfer", "linear"], monkeypatch)
+    assert bench._cycles_from_cache(a) is None      # no oracle count stored: the line says so
+
+
+def test_workload_config_names_the_outer_loop_and_transfer(monkeypatch):
+    bench, a = _args(["--krylov", "20", "--smoother", "jacobi", "--nu", "1"], monkeypatch)
+    c = bench.workload_config(a)
+    assert "FGMRES(20)" in c["outer"] and c["cycle"] == "V(1,1)" and c["smoother"] == "jacobi"
+    assert c["transfer"].startswith("Eq. (xex)")
+    bench, a = _args(["--transfer", "linear"], monkeypatch)
+    c = bench.workload_config(a)
+    assert c["outer"] == "stand-alone cycle iteration" and "linear" in c["transfer"]
