@@ -399,14 +399,20 @@ def run_ours(a):
 
 
 def step_traffic(a, what):
-    """DRAM bytes of one fine-level GMRES(3) step from the committed ncu
-    capture, scaled to this run's right-hand sides; None unless the workload
-    is the captured one and the hashed kernel sources are unchanged."""
+    """DRAM bytes of the roofline unit (the fine-level GMRES(3) step, or the
+    last FGMRES Arnoldi step) from the committed ncu capture, scaled to this
+    run's right-hand sides; None unless the workload is the captured one and
+    the hashed kernel sources are unchanged."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic_gmres_step_level0.json")
-    if what != 4 or a.n != 1024 or a.precision == "fp64" or not os.path.exists(path):
+    name = {4: "traffic_gmres_step_level0.json", 5: "traffic_fgmres_step_level0.json"}.get(what)
+    if name is None or a.n != 1024 or a.precision == "fp64":
+        return None
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
         return None
     rec = json.load(open(path))
+    if what == 5 and rec.get("m") != a.krylov:
+        return None
     h = hashlib.sha256()
     for f in rec["sources"]:
         with open(os.path.join(ROOT, f), "rb") as fh:
