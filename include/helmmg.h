@@ -244,8 +244,8 @@ mg_status mg_two_grid(mg_handle h, int nu, int max_iter, double* out);
  * reads and writes per node; otherwise eight passes, 28; needs
  * smoother = 1), 5 the last Arnoldi step of an FGMRES(m) restart cycle
  * (j = m - 1: the pass for the m MGS coefficients and the pass for the new
- * basis vector, 2m + 4 vector reads and writes per node in the cycle's
- * precision; needs krylov > 0 and level 0; it marks every right-hand side
+ * basis vector, which also writes the cycle's right-hand side and zeroes its
+ * iterate: 2m + 6 vector reads and writes per node in the cycle's precision; needs krylov > 0 and level 0; it marks every right-hand side
  * active), on level
  * `level` for all B right-hand sides.  The work runs `reps` times back to
  * back between two CUDA events on the handle's stream (after one untimed

@@ -504,7 +504,7 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
         const int j = h->opt.krylov - 1;
         cudaMemcpyAsync(h->active, ones.data(), sizeof(int) * h->B, cudaMemcpyHostToDevice, s);
         launch_fg_dots<T>(fa, j, V[0].x, s);
-        launch_fg_orth<T>(fa, j, s);
+        launch_fg_orth<T>(fa, j, V[0].b, V[0].x, s);
         break;
       }
     }
@@ -512,8 +512,8 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
   if (what == 0 || what == 1) *bytes = nodes * (3 * e + opbytes);
   else if (what == 2) *bytes = nodes * e * 1.25;     // read fine r, write coarse r
   else if (what == 3) *bytes = nodes * e * 2.25;     // read+write fine x, read coarse e
-  else if (what == 5)   // z, Z_j twice; v_0..v_j twice, v_{j+1} once (all in the cycle's precision); k field twice
-    *bytes = nodes * (e * (2.0 * h->opt.krylov + 4.0) + (op.kf ? 2 * sizeof(T) / (double)h->B : 0.0));
+  else if (what == 5)   // z, Z_j twice; u_0..u_j twice; u_{j+1}, cycle rhs, cycle x (all in the cycle's precision); k twice
+    *bytes = nodes * (e * (2.0 * h->opt.krylov + 6.0) + (op.kf ? 2 * sizeof(T) / (double)h->B : 0.0));
   else {   // GMRES(3) step: four passes that read the operator, plus vectors
     double gop = 0;   // operator bytes per node and RHS read by one pass
     if (level == 0) gop = op.kf ? sizeof(T) / (double)h->B : 0.0;
@@ -983,25 +983,23 @@ static mg_status solve_fgmres(mg_ctx* c, const void* rhs, void* x, double tol, i
   cx<float>* cx32 = mixed ? c->v32[0].x : nullptr;
   while (true) {
     CK(cudaMemsetAsync(c->n_active, 0, sizeof(int) * 2, s));
-    if (mixed) launch_fg_restart<float>(a, s);
-    else launch_fg_restart<double>(a, s);
+    if (mixed) launch_fg_restart<float>(a, cb32, cx32, s);
+    else launch_fg_restart<double>(a, c->v64[0].b, c->v64[0].x, s);
     ++launches;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (c->h_n_active[0] == 0) break;
     for (int j = 0; j < m; ++j) {
-      if (mixed) launch_fg_prep<float>(a, j, cb32, cx32, s);
-      else launch_fg_prep<double>(a, j, c->v64[0].b, c->v64[0].x, s);
       CK(cudaGraphLaunch(c->pexec, s));
       if (mixed) {
         launch_fg_dots<float>(a, j, cx32, s);
-        launch_fg_orth<float>(a, j, s);
+        launch_fg_orth<float>(a, j, cb32, cx32, s);
       } else {
         launch_fg_dots<double>(a, j, c->v64[0].x, s);
-        launch_fg_orth<double>(a, j, s);
+        launch_fg_orth<double>(a, j, c->v64[0].b, c->v64[0].x, s);
       }
-      launches += 3 + c->pgraph_kernels;
+      launches += 2 + c->pgraph_kernels;
       ++graphs;
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));

@@ -19,16 +19,22 @@
 // decides convergence.  GB300's FP64 pipe runs at about 1/58 of FP32, and an
 // FP64 Arnoldi step costs ~180 FP64 FMAs per node, which made it ALU-bound.
 //
-// Kernels (the cycle between prep and dots is the captured cycle graph):
-//   restart  r = b - A x (FP64) into v_0, ||r||, restart test    (last block)
-//   prep     v_j /= h_{j,j-1} (or beta) in place, cycle rhs = v_j, cycle x = 0
-//   dots     Z_j = z, w = A z_j, <v_i, w> (i <= j) and <v_i, v_j> (i < j);
-//            the last block turns them into the MGS coefficients (Gram form:
-//            h_i = <v_i, w> - sum_{l<i} h_l <v_i, v_l>, which is MGS in exact
-//            arithmetic for any V) in one pass over the j+1 vectors
-//   orth     v_{j+1} = w - sum_i h_i v_i (w recomputed from z_j), ||v_{j+1}||;
-//            the last block finishes the Arnoldi step, the rotations and the
-//            per-RHS exit test
+// The basis is kept unnormalised: u_j with v_j = s_j u_j, s_0 = 1/beta and
+// s_j = 1/h_{j,j-1} among the scalars.  The cycle from zero is homogeneous
+// (M(u) = M(v)/s), so it runs directly on u_j, which the pass that forms u_j
+// also writes as the cycle's right-hand side, and the dots pass scales its
+// output: z_j = s_j M(u_j).  Kernels (the captured cycle graph runs between
+// the restart or orth pass and the next dots pass):
+//   restart  r = b - A x (FP64) into u_0 and the cycle rhs, cycle x = 0,
+//            ||r||, restart test                                (last block)
+//   dots     Z_j = s_j z', w = A Z_j, <u_i, w> (i <= j) and <u_i, u_j> (i < j);
+//            the last block scales them by the s_i and turns them into the
+//            MGS coefficients (Gram form: h_i = <v_i, w> - sum_{l<i} h_l
+//            <v_i, v_l>, MGS in exact arithmetic for any V) in one pass over
+//            the j+1 vectors
+//   orth     u_{j+1} = w - sum_i h_i s_i u_i (w recomputed from Z_j) into the
+//            basis and the cycle rhs, cycle x = 0, ||u_{j+1}||; the last block
+//            finishes the Arnoldi step, the rotations and the per-RHS exit
 //   update   x += sum_i y_i z_i (FP64)
 // Every kernel walks strips of 32 columns x 64 rows (8 rows per thread,
 // warps along rows) with a fixed number of blocks per right-hand side;
@@ -134,7 +140,9 @@ __device__ bool fg_reduce(const FgArgs& a, int rhs, int nval, const double* mine
 
 // ------------------------------------------------------------------ restart
 
-template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> op) {
+template <class T>
+__global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> op, cx<T>* __restrict__ cb,
+                                                         cx<T>* __restrict__ cxv) {
   __shared__ double red[FBY], tot[1], mine[1];
   const int rhs = blockIdx.z;
   if (a.state[rhs] != 0) return;   // block-uniform
@@ -153,7 +161,10 @@ template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgAr
       if (j > g.ny) break;
       const int p = g.at(sp.i, j);
       const double2 rr = sub<double>(b[p], op.apply(x, p, g.pitch, sp.i, j));
-      v0[p] = from_d<T>(rr);
+      const cx<T> u = from_d<T>(rr);
+      v0[p] = u;
+      cb[off + p] = u;
+      cxv[off + p] = mk<T>(T(0), T(0));
       acc += abs2<double>(rr);
     }
   }
@@ -184,37 +195,9 @@ template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgAr
     for (int q = 0; q <= a.m; ++q) S[L.g(q)] = S[L.g(q) + 1] = 0.0;
     S[L.g(0)] = beta;
     S[L.beta()] = beta;
-    S[L.div()] = beta;
+    S[L.s(0)] = 1.0 / beta;
     a.active[rhs] = 1;
     atomicAdd(a.n_active, 1);
-  }
-}
-
-// ------------------------------------------------------------------ prep
-
-template <class T>
-__global__ void __launch_bounds__(FTHREADS) k_fg_prep(FgArgs a, int jj, cx<T>* __restrict__ cb,
-                                                      cx<T>* __restrict__ cxv) {
-  const int rhs = blockIdx.z;
-  if (!a.active[rhs]) return;
-  const Grid& g = a.g;
-  const long long off = (long long)rhs * g.vstride;
-  const T dv = (T)a.S[(long long)rhs * a.sd + FgLayout{a.m}.div()];
-  cx<T>* vj = (cx<T>*)a.V + jj * a.vlen + off;
-  for (int s = blockIdx.x; s < a.ns; s += a.nbr) {
-    const StripPos sp = strip_pos(a, s);
-    if (sp.i > g.nx) continue;
-#pragma unroll
-    for (int r = 0; r < FR; ++r) {
-      const int j = sp.j0 + r * FBY;
-      if (j > g.ny) break;
-      const int p = g.at(sp.i, j);
-      const cx<T> u = vj[p];
-      const cx<T> v = mk<T>(u.x / dv, u.y / dv);
-      vj[p] = v;
-      cb[off + p] = v;
-      cxv[off + p] = mk<T>(T(0), T(0));
-    }
   }
 }
 
@@ -236,6 +219,7 @@ __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_dots(FgArgs a, cons
   const cx<T>* zs = z + off;
   cx<T>* zj = (cx<T>*)a.Z + jj * a.vlen + off;
   const cx<T>* vj = (const cx<T>*)a.V + jj * a.vlen + off;
+  const T sj = (T)a.S[(long long)rhs * a.sd + FgLayout{a.m}.s(jj)];   // z_j = s_j M(u_j)
   for (int s = blockIdx.x; s < a.ns; s += a.nbr) {
     const StripPos sp = strip_pos(a, s);
     cx<T> w[FR], u[FR];
@@ -248,8 +232,8 @@ __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_dots(FgArgs a, cons
       if (sp.i <= g.nx && j <= g.ny) {
         const int p = g.at(sp.i, j);
         pr[r] = p;
-        zj[p] = zs[p];
-        w[r] = op.apply(zs, p, g.pitch, sp.i, j);
+        zj[p] = scl<T>(sj, zs[p]);
+        w[r] = scl<T>(sj, op.apply(zs, p, g.pitch, sp.i, j));
         u[r] = vj[p];
       }
     }
@@ -293,15 +277,18 @@ __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_dots(FgArgs a, cons
   __syncthreads();
   if (!fg_reduce(a, rhs, nval, mine, tot)) return;
   if (tid) return;
-  // Gram row jj, then the MGS coefficients of column jj
+  // Gram row jj, then the MGS coefficients of column jj (v_i = s_i u_i)
   const FgLayout L{a.m};
   double* S = a.S + (long long)rhs * a.sd;
-  for (int l = 0; l < jj; ++l) {   // <v_jj, v_l> = conj(<v_l, v_jj>)
-    S[L.gram(jj, l)] = tot[2 * (jj + 1) + 2 * l];
-    S[L.gram(jj, l) + 1] = -tot[2 * (jj + 1) + 2 * l + 1];
+  const double sjj = S[L.s(jj)];
+  for (int l = 0; l < jj; ++l) {   // <v_jj, v_l> = s_jj s_l conj(<u_l, u_jj>)
+    const double f = sjj * S[L.s(l)];
+    S[L.gram(jj, l)] = f * tot[2 * (jj + 1) + 2 * l];
+    S[L.gram(jj, l) + 1] = -f * tot[2 * (jj + 1) + 2 * l + 1];
   }
   for (int q = 0; q <= jj; ++q) {
-    double hr = tot[2 * q], hi = tot[2 * q + 1];
+    const double sq = S[L.s(q)];
+    double hr = sq * tot[2 * q], hi = sq * tot[2 * q + 1];
     for (int l = 0; l < q; ++l) {
       const double ar = S[L.h(jj, l)], ai = S[L.h(jj, l) + 1];
       const double gr = S[L.gram(q, l)], gi = S[L.gram(q, l) + 1];
@@ -390,12 +377,13 @@ __device__ void fg_finish_step(const FgArgs& a, int rhs, int jj, double sumsq) {
     a.active[rhs] = 0;
     atomicSub(a.n_active, 1);
   } else {
-    S[L.div()] = nrm;
+    S[L.s(k)] = 1.0 / nrm;
   }
 }
 
 template <class T>
-__global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_orth(FgArgs a, int jj) {
+__global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_orth(FgArgs a, int jj, cx<T>* __restrict__ cb,
+                                                                  cx<T>* __restrict__ cxv) {
   __shared__ cx<T> hs[FG_MAXM + 1];
   __shared__ double red[FBY], mine[1], tot[1];
   const int rhs = blockIdx.z;
@@ -403,7 +391,10 @@ __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_orth(FgArgs a, int 
   const int tid = threadIdx.x + threadIdx.y * FBX;
   const FgLayout L{a.m};
   const double* S = a.S + (long long)rhs * a.sd;
-  if (tid <= jj) hs[tid] = mk<T>((T)S[L.h(jj, tid)], (T)S[L.h(jj, tid) + 1]);
+  if (tid <= jj) {   // h_i s_i: the coefficient of u_i
+    const double si = S[L.s(tid)];
+    hs[tid] = mk<T>((T)(S[L.h(jj, tid)] * si), (T)(S[L.h(jj, tid) + 1] * si));
+  }
   __syncthreads();
   const Op0<T> op = op_t<T>(a);
   const Grid& g = a.g;
@@ -447,6 +438,8 @@ __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_orth(FgArgs a, int 
     for (int r = 0; r < FR; ++r) {
       if (pr[r] < 0) continue;
       vn[pr[r]] = w[r];
+      cb[off + pr[r]] = w[r];
+      cxv[off + pr[r]] = mk<T>(T(0), T(0));
       part += abs2<T>(w[r]);
     }
     acc += (double)part;
@@ -528,27 +521,23 @@ void fg_geometry(const Grid& g, int B, bool fp64z, FgArgs& a) {
   a.nvp = FNV;
 }
 
-template <class T> void launch_fg_restart(const FgArgs& a, cudaStream_t s) {
-  k_fg_restart<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, fine_op64(a));
-}
-template <class T> void launch_fg_prep(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s) {
-  k_fg_prep<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j, cb, cxv);
+template <class T> void launch_fg_restart(const FgArgs& a, cx<T>* cb, cx<T>* cxv, cudaStream_t s) {
+  k_fg_restart<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, fine_op64(a), cb, cxv);
 }
 template <class T> void launch_fg_dots(const FgArgs& a, int j, const cx<T>* z, cudaStream_t s) {
   k_fg_dots<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, z, j);
 }
-template <class T> void launch_fg_orth(const FgArgs& a, int j, cudaStream_t s) {
-  k_fg_orth<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j);
+template <class T> void launch_fg_orth(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s) {
+  k_fg_orth<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j, cb, cxv);
 }
 template <class T> void launch_fg_update(const FgArgs& a, cudaStream_t s) {
   k_fg_update<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a);
 }
 
 #define INST(T)                                                                                  \
-  template void launch_fg_restart<T>(const FgArgs&, cudaStream_t);                               \
-  template void launch_fg_prep<T>(const FgArgs&, int, cx<T>*, cx<T>*, cudaStream_t);             \
+  template void launch_fg_restart<T>(const FgArgs&, cx<T>*, cx<T>*, cudaStream_t);               \
   template void launch_fg_dots<T>(const FgArgs&, int, const cx<T>*, cudaStream_t);               \
-  template void launch_fg_orth<T>(const FgArgs&, int, cudaStream_t);                             \
+  template void launch_fg_orth<T>(const FgArgs&, int, cx<T>*, cx<T>*, cudaStream_t);             \
   template void launch_fg_update<T>(const FgArgs&, cudaStream_t);
 INST(double)
 INST(float)

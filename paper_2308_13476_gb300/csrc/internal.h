@@ -246,8 +246,8 @@ void launch_ff_norm(const Grid& g, const void* v, int B, double* out, double* pa
 constexpr int FG_MAXM = 32;
 // Per-RHS FP64 scalars of the restart cycle: the rotated Hessenberg columns
 // (column j, row i), the Gram matrix of V (row a, column b: <v_a, v_b>), the
-// rotations (cs real, sn complex), g, y, beta and the divisor of the next
-// basis vector (h_{j+1,j}, or beta at a restart); complex values as (re, im).
+// rotations (cs real, sn complex), g, y, beta and the scales s_j of the
+// unnormalised basis (v_j = s_j u_j); complex values as (re, im).
 struct FgLayout {
   int m;
   __host__ __device__ int h(int j, int i) const { return 2 * (j * (m + 1) + i); }
@@ -257,8 +257,8 @@ struct FgLayout {
   __host__ __device__ int g(int i) const { return sn(m) + 2 * i; }
   __host__ __device__ int y(int i) const { return g(m + 1) + 2 * i; }
   __host__ __device__ int beta() const { return y(m); }
-  __host__ __device__ int div() const { return beta() + 1; }
-  __host__ __device__ int size() const { return beta() + 2; }
+  __host__ __device__ int s(int j) const { return beta() + 1 + j; }
+  __host__ __device__ int size() const { return s(m + 1); }
 };
 struct FgArgs {
   Grid g;                  // fine level
@@ -291,10 +291,11 @@ struct FgArgs {
 };
 // Strip geometry and blocks per RHS (nbr, ncx, ns, nvp) for a fine grid.
 void fg_geometry(const Grid& g, int B, bool fp64z, FgArgs& a);
-template <class T> void launch_fg_restart(const FgArgs& a, cudaStream_t s);
-template <class T> void launch_fg_prep(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s);
+// cb, cxv: the cycle's level-0 right-hand side and iterate (the restart and
+// orth passes write the next basis vector into cb and zero cxv).
+template <class T> void launch_fg_restart(const FgArgs& a, cx<T>* cb, cx<T>* cxv, cudaStream_t s);
 template <class T> void launch_fg_dots(const FgArgs& a, int j, const cx<T>* z, cudaStream_t s);
-template <class T> void launch_fg_orth(const FgArgs& a, int j, cudaStream_t s);
+template <class T> void launch_fg_orth(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s);
 template <class T> void launch_fg_update(const FgArgs& a, cudaStream_t s);
 
 // Dense two-grid analysis of the two finest levels (analysis.cu).  out[0] =
