@@ -128,3 +128,23 @@ def test_linear_mixed_and_the_ablation_counts():
     assert st == hm.MG_OK
     assert rel(host(x)[0], ref.x) <= 1e-6
     s.close()
+
+
+def test_linear_transfers_fail_at_scale_where_bezier_converges():
+    """The ablation at scale (8 sources on 513^2, k = 150, GMRES(3) V(2,2),
+    mixed): Eq. (xex) converges in about 20 cycles; with linear
+    interpolation the cycle does not reach 1e-6 (it diverges or stalls)."""
+    n, k = 512, 150.0
+    h = 1.0 / n
+    b = dev(synth.source_row(n, n, h, 8))
+    cyc = {}
+    for kind in ("bezier", "linear"):
+        s = hm.Solver(n, n, h, k, 1 / k, smoother="gmres3", nu_pre=2, nu_post=2, precision="mixed", batch=8,
+                      transfer=kind, max_cycles=400)
+        _, st, c, _ = s.solve(b, tol=1e-6)
+        cyc[kind] = (st, c)
+        s.close()
+    st, c = cyc["bezier"]
+    assert st == hm.MG_OK and max(c) <= 30
+    st, c = cyc["linear"]
+    assert st in (hm.MG_EDIVERGED, hm.MG_EMAXIT)
