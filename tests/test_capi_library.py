@@ -89,3 +89,12 @@ def test_transfer_option_validated_without_gpu(lib_path):
     assert lib.mg_setup(ctypes.byref(h), 8, 8, 0.1, None, 5.0, 0.7, 0, ctypes.byref(o)) == hm.MG_EINVAL
     assert b"transfer" in lib.mg_last_error()
     assert h.value is None
+
+
+def test_two_grid_and_profile_arguments_validated_without_gpu(lib_path):
+    import paper_2308_13476_gb300 as hm
+    lib = hm.load_library()
+    out = (ctypes.c_double * 6)()
+    assert lib.mg_two_grid(None, 1, 1000, out) == hm.MG_EINVAL
+    ms, nb = ctypes.c_double(), ctypes.c_double()
+    assert lib.mg_profile(None, 5, 0, 1, ctypes.byref(ms), ctypes.byref(nb)) == hm.MG_EINVAL
