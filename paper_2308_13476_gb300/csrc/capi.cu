@@ -211,7 +211,7 @@ template <class T> static std::vector<LevelVec<T>>& vecs(mg_ctx* c);
 template <> std::vector<LevelVec<double>>& vecs<double>(mg_ctx* c) { return c->v64; }
 template <> std::vector<LevelVec<float>>& vecs<float>(mg_ctx* c) { return c->v32; }
 
-template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, const Grid& g, bool gmres) {
+template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, const Grid& g, bool gmres, bool kron) {
   const size_t bytes = sizeof(cx<T>) * (size_t)g.vstride * c->B;
   cudaError_t e;
   if ((e = dalloc(c, (void**)&v.x, bytes))) return e;
@@ -222,6 +222,7 @@ template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, c
     for (int q = 0; q < 3; ++q)
       if ((e = dalloc(c, &v.gb.u[q], bytes))) return e;
     if ((e = dalloc(c, &v.gb.w, bytes))) return e;
+    if (kron && sizeof(T) == 4 && (e = dalloc(c, &v.gb.w2, bytes))) return e;   // fused column marches' second w
     v.gb.partial = c->partial;
     v.gb.tickets = c->tickets;
     v.gb.st = c->gst;
@@ -518,7 +519,9 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
     double gop = 0;   // operator bytes per node and RHS read by one pass
     if (level == 0) gop = op.kf ? sizeof(T) / (double)h->B : 0.0;
     else if (h->lev[level].kind <= 3) gop = opbytes - e / h->B;   // stencil without the inverse diagonal
-    const int vec = (use_march(h, level) && h->lev[level].kind == 1) ? 16 : 28;   // row marches + update, or 8 passes
+    // fine-level row marches + update 16; Kronecker column marches, complex64 (two fused passes) 23; else 28
+    const bool mr = use_march(h, level);
+    const int vec = (mr && h->lev[level].kind == 1) ? 16 : (mr && h->lev[level].kind >= 4 && sizeof(T) == 4) ? 23 : 28;
     *bytes = nodes * (vec * e + 4 * gop);
   }
   launch();
@@ -725,7 +728,7 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   // vectors
   if (!mixed) {
     c->v64.resize(c->nlev);
-    for (int l = 0; l < c->nlev; ++l) CK(alloc_vectors<double>(c, c->v64[l], c->lev[l].g, gm));
+    for (int l = 0; l < c->nlev; ++l) CK(alloc_vectors<double>(c, c->v64[l], c->lev[l].g, gm, c->lev[l].kind >= 4));
   } else {
     c->v64.resize(1);
     const size_t bytes = sizeof(double2) * (size_t)g0.vstride * c->B;
@@ -733,7 +736,7 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     CK(dalloc(c, (void**)&c->v64[0].b, bytes));
     c->v32.resize(c->nlev);
     for (int l = 0; l < c->nlev; ++l) {
-      CK(alloc_vectors<float>(c, c->v32[l], c->lev[l].g, gm));
+      CK(alloc_vectors<float>(c, c->v32[l], c->lev[l].g, gm, c->lev[l].kind >= 4));
       if (l > 0 && c->lev[l].kind <= 3) {
         const Level& L = c->lev[l];
         const long long S = (long long)(2 * L.radius + 1) * (2 * L.radius + 1);

@@ -138,6 +138,7 @@ void launch_export_stencil(const OpView<double>& op, int nx, int ny, int r, doub
 struct GmresBufs {
   void* u[3];          // Arnoldi vectors (unnormalised), precision T
   void* w;             // A v_j
+  void* w2;            // second w of the fused Kronecker-level marches (null: unfused)
   double* partial;     // block partials of the fused reductions
   unsigned* tickets;   // one per RHS, 0 at rest
   double* st;          // per-RHS scalars, see kernels_gmres.cu

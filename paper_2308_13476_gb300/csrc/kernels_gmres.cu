@@ -107,7 +107,8 @@ template <class T, int J>
 __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1,
                                                    const cx<T>* __restrict__ u2, cx<T>* __restrict__ un,
                                                    const cx<T>* __restrict__ w, double* __restrict__ st,
-                                                   double* partial, unsigned* tickets, const int* __restrict__ active) {
+                                                   double* partial, unsigned* tickets, const int* __restrict__ active,
+                                                   int ws) {
   constexpr int NV = (J < 2) ? 1 + 2 * (J + 1) : 1;
   __shared__ double sh[NVMAX * 32];
   GNODE
@@ -126,10 +127,16 @@ __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restri
       const double sl = S[G_S + l];
       c[l] = mk<T>((T)(hr * sl), (T)(hi * sl));
     }
+    // ws >= 0: w was stored without its scale s_ws (fused Kronecker marches)
+    const T wsc = ws >= 0 ? (T)S[G_S + ws] : T(1);
     GROWS {
       if (j > g.ny) break;
       const int p = g.at(i0, j);
       Pack<T> a = load_pack(w + off, p);
+      if (ws >= 0) {
+#pragma unroll
+        for (int n = 0; n < NP; ++n) a.v[n] = scl<T>(wsc, a.v[n]);
+      }
       Pack<T> uu[J + 1];
 #pragma unroll
       for (int l = 0; l <= J; ++l) {
@@ -212,11 +219,11 @@ void gmres_smooth(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T>* b,
     for (int step = 0; step < nu; ++step) {
       g_init<T, Op><<<grd, blk, 0, s>>>(g, op, x, b, u0, st, P, tk, active);
       g_arn_a<T, Op, 0><<<grd, blk, 0, s>>>(g, op, u0, u1, u2, w, st, P, tk, active);
-      g_arn_b<T, 0><<<grd, blk, 0, s>>>(g, u0, u1, u2, u1, w, st, P, tk, active);
+      g_arn_b<T, 0><<<grd, blk, 0, s>>>(g, u0, u1, u2, u1, w, st, P, tk, active, -1);
       g_arn_a<T, Op, 1><<<grd, blk, 0, s>>>(g, op, u0, u1, u2, w, st, P, tk, active);
-      g_arn_b<T, 1><<<grd, blk, 0, s>>>(g, u0, u1, u2, u2, w, st, P, tk, active);
+      g_arn_b<T, 1><<<grd, blk, 0, s>>>(g, u0, u1, u2, u2, w, st, P, tk, active, -1);
       g_arn_a<T, Op, 2><<<grd, blk, 0, s>>>(g, op, u0, u1, u2, w, st, P, tk, active);
-      g_arn_b<T, 2><<<grd, blk, 0, s>>>(g, u0, u1, u2, nullptr, w, st, P, tk, active);
+      g_arn_b<T, 2><<<grd, blk, 0, s>>>(g, u0, u1, u2, nullptr, w, st, P, tk, active, -1);
       g_update<T><<<grd, blk, 0, s>>>(g, x, u0, u1, u2, st, active);
     }
   });
@@ -230,18 +237,18 @@ void launch_gmres_update(const Grid& g, cx<T>* x, const GmresBufs& gb, int B, co
 }
 
 template <class T, int J>
-void launch_arn_b(const Grid& g, const GmresBufs& gb, cx<T>* un, int B, const int* active, cudaStream_t s) {
+void launch_arn_b(const Grid& g, const GmresBufs& gb, cx<T>* un, int B, const int* active, cudaStream_t s, int ws) {
   dim3 grd(cdiv(g.nx + 1, BX * PK<T>::NP), cdiv(g.ny + 1, BY * g.ry), B);
   g_arn_b<T, J><<<grd, dim3(BX, BY), 0, s>>>(g, (const cx<T>*)gb.u[0], (const cx<T>*)gb.u[1], (const cx<T>*)gb.u[2],
-                                            un, (const cx<T>*)gb.w, gb.st, gb.partial, gb.tickets, active);
+                                            un, (const cx<T>*)gb.w, gb.st, gb.partial, gb.tickets, active, ws);
 }
 
-template void launch_arn_b<double, 0>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t);
-template void launch_arn_b<double, 1>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t);
-template void launch_arn_b<double, 2>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t);
-template void launch_arn_b<float, 0>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t);
-template void launch_arn_b<float, 1>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t);
-template void launch_arn_b<float, 2>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t);
+template void launch_arn_b<double, 0>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t, int);
+template void launch_arn_b<double, 1>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t, int);
+template void launch_arn_b<double, 2>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t, int);
+template void launch_arn_b<float, 0>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t, int);
+template void launch_arn_b<float, 1>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t, int);
+template void launch_arn_b<float, 2>(const Grid&, const GmresBufs&, float2*, int, const int*, cudaStream_t, int);
 template void launch_gmres_update<double>(const Grid&, double2*, const GmresBufs&, int, const int*, cudaStream_t);
 template void launch_gmres_update<float>(const Grid&, float2*, const GmresBufs&, int, const int*, cudaStream_t);
 template void gmres_smooth<double>(const Grid&, const OpView<double>&, double2*, const double2*, int, int, const int*,

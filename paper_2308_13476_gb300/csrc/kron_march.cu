@@ -221,6 +221,212 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
     staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
 }
 
+// ---------------------------------------------------------------- fused passes
+//
+// km_arn_ab<J> (J = 1, 2) is g_arn_b<J-1> and km_arn_a<J> in one march: the
+// ring stages the rows of w and u_0..u_{J-1}, each lane forms
+// u_J = c_w w - sum_{l<J} (h_{l,J-1} s_l) u_l for its staged columns into a
+// second ring, writes u_J on its own rows and sums |u_J|^2 and <u_J, u_l>
+// there (the inputs of fin_b<J-1>), and the column march applies A to the
+// formed rows: w' = A u_J, stored unscaled (s_J = 1 / |u_J| is known only
+// after this kernel's reduction), with the dots <u_l, w'> of the output rows.
+// The last block runs fin_b<J-1> and, unless it found a breakdown, fin_a<J>
+// on the dots scaled by s_J.  w' cannot overwrite the staged w (neighbouring
+// chunks read its rows as halo), so J = 1 writes w2 and J = 2 reads w2 and
+// writes w; the closing g_arn_b<2> scales w by s_2.  Per smoothing step this
+// saves 7 of 28 vector passes and two launches.
+template <class T, int R, int NS> struct KRingF {
+  static constexpr int K = 2 * R + 1;
+  static constexpr int WD = 32 + 2 * R;
+  cx<T> G[K];
+  T Wx[K];
+  cx<T> s1[K], s2[K];
+  const cx<T>* vs[NS];   // staged slices: w, u_0, .., u_{NS-2}
+  Grid g;
+  int cw0, lane;
+  cx<T>* sm;             // the warp's staged rings, [NS][KSL][WD]
+  cx<T>* fm;             // the warp's ring of formed rows, [KSL][WD]
+  int r0;
+
+  __device__ __forceinline__ void init(const OpK<T, R>& op, int i, bool col) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      G[k] = col ? op.gx[i * K + k] : mk<T>(T(0), T(0));
+      Wx[k] = col ? op.wx[i * K + k] : T(0);
+      s1[k] = mk<T>(T(0), T(0));
+      s2[k] = mk<T>(T(0), T(0));
+    }
+  }
+  __device__ __forceinline__ int slot(int r) const { return (r - r0) & (KSL - 1); }
+  __device__ __forceinline__ void issue(int r) {
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+      cx<T>* dst = sm + (v * KSL + slot(r)) * WD;
+#pragma unroll
+      for (int e = lane; e < WD; e += 32) {
+        const int col = cw0 - R + e;
+        const bool ok = col <= g.nx;
+        const cx<T>* src = vs[v] + g.at(ok ? col : 0, r);
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + e);
+        if (sizeof(cx<T>) == 16)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+        else
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+      }
+    }
+  }
+  __device__ __forceinline__ static void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+  __device__ __forceinline__ void prime(int last) {
+#pragma unroll
+    for (int d = 0; d < KD; ++d) {
+      if (r0 + d <= last) issue(r0 + d);
+      commit();
+    }
+  }
+  // take input row r: form u_J on it (returned for the lane's column), its
+  // two row sums into the register ring.  All lanes of the warp call it.
+  __device__ __forceinline__ cx<T> advance(int r, int last, T cw, const cx<T> (&c)[NS - 1]) {
+    __syncwarp();
+    if (r + KD <= last) issue(r + KD);
+    commit();
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(KD) : "memory");
+    __syncwarp();
+    const int sl = slot(r);
+#pragma unroll
+    for (int e = lane; e < WD; e += 32) {
+      cx<T> u = scl<T>(cw, sm[sl * WD + e]);
+#pragma unroll
+      for (int l = 0; l < NS - 1; ++l) u = sub<T>(u, mul<T>(c[l], sm[((1 + l) * KSL + sl) * WD + e]));
+      fm[sl * WD + e] = u;
+    }
+    __syncwarp();
+    const cx<T>* row = fm + sl * WD + lane + R;
+    cx<T> a = mk<T>(T(0), T(0)), b = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int dx = -R; dx <= R; ++dx) {
+      const cx<T> xv = row[dx];
+      a = fma_c<T>(G[dx + R], xv, a);
+      b = mk<T>(fma(Wx[dx + R], xv.x, b.x), fma(Wx[dx + R], xv.y, b.y));
+    }
+#pragma unroll
+    for (int k = 0; k < K - 1; ++k) {
+      s1[k] = s1[k + 1];
+      s2[k] = s2[k + 1];
+    }
+    s1[K - 1] = a;
+    s2[K - 1] = b;
+    return row[0];
+  }
+  // staged vector v (1 + l for u_l) and the formed u_J at row m, lane's column
+  __device__ __forceinline__ cx<T> staged(int v, int m) const { return sm[(v * KSL + slot(m)) * WD + lane + R]; }
+  __device__ __forceinline__ cx<T> formed(int m) const { return fm[slot(m) * WD + lane + R]; }
+  __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
+    const cx<T>* H = op.hy + m * K;
+    const T* Wy = op.wy + m * K;
+    cx<T> acc = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+      const T wy = __ldg(Wy + dy + R);
+      acc = mk<T>(fma(wy, s1[dy + R].x, acc.x), fma(wy, s1[dy + R].y, acc.y));
+      acc = fma_c<T>(__ldg(H + dy + R), s2[dy + R], acc);
+    }
+    return acc;
+  }
+};
+
+template <class T, int R, int J>
+__global__ void __launch_bounds__(KW * 32) km_arn_ab(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ win,
+                                                const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1,
+                                                cx<T>* __restrict__ uJ, cx<T>* __restrict__ wout,
+                                                double* __restrict__ st, double* partial, unsigned* tickets,
+                                                const int* __restrict__ active) {
+  constexpr int NS = J + 1;             // staged: w, u_0 .. u_{J-1}
+  constexpr int NB = 1 + 2 * J;         // fin_b<J-1>: |u_J|^2, <u_J, u_l> (l < J)
+  constexpr int NA = 2 * (J + 1);       // fin_a<J>: <u_l, w'> (l <= J)
+  __shared__ double sh[NVMAX * 32];
+  __shared__ __align__(16) cx<T> ksm[KW][NS][KSL][32 + 2 * R];
+  __shared__ __align__(16) cx<T> kfm[KW][KSL][32 + 2 * R];
+  const int rhs = blockIdx.z;
+  if (active && !active[rhs]) return;
+  const long long off = (long long)rhs * g.vstride;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * KW + wib;
+  const bool has = gw < kg.ncw * kg.nchunks;
+  const int cw0 = (has ? gw % kg.ncw : 0) * 32, i = cw0 + lane;
+  const int j0 = (has ? gw / kg.ncw : 0) * kg.ch, j1 = min(j0 + kg.ch, g.ny + 1);
+  const bool col = has && i <= g.nx;
+  const int nblk = gridDim.x, blk = blockIdx.x;
+  double* S = st + (long long)rhs * GS;
+  if (S[G_BRK] != 0.0 || S[G_M] < J - 1) return;   // the guard of g_arn_b<J-1>; uniform per RHS
+  T acc[NB + NA];
+#pragma unroll
+  for (int k = 0; k < NB + NA; ++k) acc[k] = T(0);
+  if (has) {
+    // u_J = c_w w - sum_l c_l u_l: w from km_arn_a<0> carries s_0 (c_w = 1);
+    // w2 from km_arn_ab<1> is unscaled (c_w = s_1)
+    const T cw = J == 1 ? T(1) : (T)S[G_S + J - 1];
+    cx<T> c[NS - 1];
+#pragma unroll
+    for (int l = 0; l < J; ++l) {
+      const double sl = S[G_S + l];
+      c[l] = mk<T>((T)(S[G_H + 2 * (l * 3 + J - 1)] * sl), (T)(S[G_H + 2 * (l * 3 + J - 1) + 1] * sl));
+    }
+    KRingF<T, R, NS> ring;
+    ring.init(op, i, col);
+    ring.vs[0] = win + off;
+    ring.vs[1] = u0 + off;
+    if (NS > 2) ring.vs[NS - 1] = u1 + off;
+    ring.g = g;
+    ring.cw0 = cw0;
+    ring.lane = lane;
+    ring.sm = &ksm[wib][0][0][0];
+    ring.fm = &kfm[wib][0][0];
+    ring.r0 = j0 - R;
+    const int last = j1 + R - 1;
+    ring.prime(last);
+#pragma unroll 1
+    for (int r = j0 - R; r <= last; ++r) {
+      const cx<T> u = ring.advance(r, last, cw, c);
+      if (r >= j0 && r < j1 && col) {   // own row: store u_J, the inputs of fin_b<J-1>
+        uJ[off + g.at(i, r)] = u;
+        acc[0] += abs2<T>(u);
+#pragma unroll
+        for (int l = 0; l < J; ++l) {
+          const cx<T> d = cmul<T>(u, ring.staged(1 + l, r));
+          acc[1 + 2 * l] += d.x;
+          acc[2 + 2 * l] += d.y;
+        }
+      }
+      const int m = r - R;
+      if (m >= j0 && col) {
+        const int p = g.at(i, m);
+        const cx<T> a = ring.combine(op, m);
+        wout[off + p] = a;
+#pragma unroll
+        for (int l = 0; l <= J; ++l) {
+          const cx<T> ul = l < J ? ring.staged(1 + l, m) : ring.formed(m);
+          const cx<T> d = cmul<T>(ul, a);
+          acc[NB + 2 * l] += d.x;
+          acc[NB + 2 * l + 1] += d.y;
+        }
+      }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  }
+  double v[NB + NA];
+  if (reduce_last<NB + NA, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
+    staged<T>(S, v, [](double* s, const double* q) {
+      fin_b<J - 1, T>(s, q);
+      if (s[G_BRK] == 0.0) {
+        double d[NA];
+        const double sJ = s[G_S + J];
+#pragma unroll
+        for (int k = 0; k < NA; ++k) d[k] = sJ * q[NB + k];
+        fin_a<J, T>(s, d);
+      }
+    });
+}
+
 constexpr int KCH[] = {64, 48, 32, 24, 16, 12, 8};   // candidate rows per chunk
 
 // Rows per chunk for a level: each warp marches ch + 2R rows, and the
@@ -244,19 +450,29 @@ KGeo kron_geo(const Grid& g, int B, int R, long long cap) {
   return k;
 }
 
-// Blocks of km_arn_a<T, R, 2> (the kernel with the most state) resident on
-// the device at once.
-template <class T, int R> long long kron_capacity() {
-  static long long cap = 0;
-  if (!cap) {
+// The fused marches stage three vectors per row in shared memory; their
+// double variants would need more static shared memory than a block may
+// declare, so only the complex64 path fuses.
+template <class T> constexpr bool KFUSE = sizeof(T) == 4;
+
+// Blocks of the level's heaviest march (km_arn_ab<T, R, 2> when fused, else
+// km_arn_a<T, R, 2>) resident on the device at once.
+template <class T, int R> long long kron_capacity(bool fused) {
+  static long long cap[2] = {0, 0};
+  if (!cap[fused]) {
     int dev = 0, sms = 1, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, km_arn_a<T, R, 2>, KW * 32, 0);
+    if constexpr (KFUSE<T>) {
+      if (fused) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, km_arn_ab<T, R, 2>, KW * 32, 0);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, km_arn_a<T, R, 2>, KW * 32, 0);
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, km_arn_a<T, R, 2>, KW * 32, 0);
+    }
     cudaGetLastError();
-    cap = (long long)std::max(per, 1) * std::max(sms, 1);
+    cap[fused] = (long long)std::max(per, 1) * std::max(sms, 1);
   }
-  return cap;
+  return cap[fused];
 }
 
 }  // namespace
@@ -264,7 +480,7 @@ template <class T, int R> long long kron_capacity() {
 template <class T> void launch_gmres_update(const Grid& g, cx<T>* x, const GmresBufs& gb, int B, const int* active,
                                             cudaStream_t s);
 template <class T, int J> void launch_arn_b(const Grid& g, const GmresBufs& gb, cx<T>* un, int B, const int* active,
-                                            cudaStream_t s);
+                                            cudaStream_t s, int ws);
 
 long long kron_march_blocks(const Grid& g, int B) {   // the most for any chunk height: the shortest
   (void)B;
@@ -278,21 +494,34 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
   cx<T>* u1 = (cx<T>*)gb.u[1];
   cx<T>* u2 = (cx<T>*)gb.u[2];
   cx<T>* w = (cx<T>*)gb.w;
+  cx<T>* w2 = (cx<T>*)gb.w2;
   double* P = gb.partial;
   unsigned* tk = gb.tickets;
   double* st = gb.st;
   auto run = [&](auto op, auto rad) {
     constexpr int R = decltype(rad)::value;
-    const KGeo kg = kron_geo(g, B, R, kron_capacity<T, R>());
+    const bool fused = KFUSE<T> && w2 != nullptr;
+    const KGeo kg = kron_geo(g, B, R, kron_capacity<T, R>(fused));
     const dim3 grd(cdiv((long long)kg.ncw * kg.nchunks, KW), 1, B);
     for (int step = 0; step < nu; ++step) {
       km_init<T, R><<<grd, KW * 32, 0, s>>>(g, kg, op, x, b, u0, st, P, tk, active);
       km_arn_a<T, R, 0><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
-      launch_arn_b<T, 0>(g, gb, u1, B, active, s);
-      km_arn_a<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
-      launch_arn_b<T, 1>(g, gb, u2, B, active, s);
-      km_arn_a<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
-      launch_arn_b<T, 2>(g, gb, nullptr, B, active, s);
+      bool done = false;
+      if constexpr (KFUSE<T>) {
+        if (fused) {   // arn_b<0> + arn_a<1>, arn_b<1> + arn_a<2>
+          km_arn_ab<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, w, u0, u0, u1, w2, st, P, tk, active);
+          km_arn_ab<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, w2, u0, u1, u2, w, st, P, tk, active);
+          launch_arn_b<T, 2>(g, gb, nullptr, B, active, s, 2);
+          done = true;
+        }
+      }
+      if (!done) {
+        launch_arn_b<T, 0>(g, gb, u1, B, active, s, -1);
+        km_arn_a<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
+        launch_arn_b<T, 1>(g, gb, u2, B, active, s, -1);
+        km_arn_a<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
+        launch_arn_b<T, 2>(g, gb, nullptr, B, active, s, -1);
+      }
       launch_gmres_update<T>(g, x, gb, B, active, s);
     }
   };
