@@ -28,12 +28,17 @@
 // chunk of rows (see MGeo) and reads two rows above and below it.  Nodes outside the
 // grid are zero in every produced vector (they are not unknowns).
 //
-// Rows arrive through a per-lane ring of four 16-byte shared-memory slots
-// filled by cp.async three rows ahead of use (each lane reads back only what
-// it copied, so no barrier is needed), and every field keeps the rows it
-// uses in a ring of four registers.  Row r sits in slot (r - j0 + 2) mod 4 of
-// both rings, and the march is unrolled by four so that the slots are
-// compile-time names (no copies as the rings advance).  A warp whose loaded
+// Rows arrive through a per-lane ring of NS 16-byte shared-memory slots per
+// field, filled by cp.async NS - 1 rows ahead of use (each lane reads back
+// only what it copied, so no barrier is needed).  A pass with fewer input
+// fields keeps more rows in flight (NS = 8, 6, 4 for one, two, three fields),
+// so that every pass has about the same bytes in flight per SM: with one warp
+// per block and at most 32 blocks per SM, a one-field pass staging three rows
+// ahead ran at half the bandwidth of the three-field pass.  Every field keeps
+// the rows it uses in a ring of four registers; row r sits in register slot
+// (r - j0 + 2) mod 4, and the march is unrolled by four so that these slots
+// are compile-time names (no copies as the ring advances).  The block's
+// reduction scratch reuses the staging ring once the march has ended.  A warp whose loaded
 // columns and computed rows hold no boundary node takes the interior path:
 // the stencil without boundary tests (the same arithmetic as Op0::apply5's
 // interior case).
@@ -46,7 +51,13 @@ namespace hmg {
 
 namespace {
 
-constexpr int MD = 3;   // rows in flight ahead of use
+// staging slots per field of a pass with NF input fields
+template <int NF> struct Ring { static constexpr int NS = NF == 1 ? 8 : NF == 2 ? 6 : 4; };
+// shared memory of a pass: the staging ring, and afterwards the [NVMAX][32]
+// doubles of the block reduction
+template <int NF> constexpr int ring_bytes() {
+  return NF * Ring<NF>::NS * 32 * 16 > NVMAX * 32 * 8 ? NF * Ring<NF>::NS * 32 * 16 : NVMAX * 32 * 8;
+}
 
 template <class T> struct MNP { static constexpr int NP = 1; };
 template <> struct MNP<float> { static constexpr int NP = 2; };
@@ -72,7 +83,9 @@ __device__ __forceinline__ void stage_row(uint32_t dst, const cx<T>* __restrict_
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
 }
 __device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(MD) : "memory"); }
+template <int N> __device__ __forceinline__ void stage_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ Row<float> stage_read(const float4* p) {
   const float4 q = *p;
   Row<float> r;
@@ -146,39 +159,47 @@ template <class T, bool IN> struct MCtx {
   __device__ __forceinline__ bool own_row(int m) const { return outl && m >= j0 && m < j1; }
 };
 
-// Slot of row t + d at unroll phase S (the march starts at t0 = j0 - 2 with
-// phase 0, so row r sits in slot (r - j0 + 2) mod 4).
+// Register slot of row t + d at unroll phase S (the march starts at t0 = j0 -
+// 2 with phase 0, so row r sits in slot (r - j0 + 2) mod 4).
 template <int S, int D> struct Sl { static constexpr int v = (S + D + 8) & 3; };
 
 // The NF input fields of a pass: shared-memory staging and register rings.
+// Staging slot (f, k) of a lane is at sbase + (f NS + k) 512 bytes.
 template <class T, bool IN, int NF> struct MIn {
+  static constexpr int NS = Ring<NF>::NS, MD = NS - 1;   // MD: rows in flight ahead of use
   MCtx<T, IN> c;
   const cx<T>* src[NF];
-  uint32_t sbase[NF];   // shared address of this lane's slot 0 of each field
-  Row<T> F[NF][4];      // register ring: row r in slot (r - j0 + 2) mod 4
-  int t1;               // last row the march reads
+  uint32_t sbase;   // shared address of this lane's slot 0 of field 0
+  Row<T> F[NF][4];  // register ring: row r in slot (r - j0 + 2) mod 4
+  int t1;           // last row the march reads
+  int sw, sr;       // staging slots of the next row to issue and to read
 
   __device__ __forceinline__ void issue(int r, int slot) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) stage_row<T>(sbase[f] + slot * 32 * 16, src[f], c.g, c.i, r);
+    for (int f = 0; f < NF; ++f) stage_row<T>(sbase + (f * NS + slot) * 32 * 16, src[f], c.g, c.i, r);
   }
-  // rows t0 .. t0 + MD - 1 in flight
+  // rows t0 .. t0 + MD - 1 in flight, in slots 0 .. MD - 1
   __device__ __forceinline__ void prime(int t0) {
 #pragma unroll
     for (int d = 0; d < MD; ++d) {
       if (t0 + d <= t1) issue(t0 + d, d);
       stage_commit();
     }
+    sw = MD;
+    sr = 0;
   }
-  // row t + MD in flight, row t into the register ring
+  // row t + MD in flight (into the slot row t - 1 left), row t into the
+  // register ring
   template <int S> __device__ __forceinline__ void fetch(int t) {
-    if (t + MD <= t1) issue(t + MD, Sl<S, MD>::v);
+    if (t + MD <= t1) issue(t + MD, sw);
+    sw = sw + 1 == NS ? 0 : sw + 1;
     stage_commit();
-    stage_wait();
+    stage_wait<MD>();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
       F[f][Sl<S, 0>::v] = stage_read(reinterpret_cast<const typename SlotT<T>::type*>(
-          __cvta_shared_to_generic(sbase[f] + Sl<S, 0>::v * 32 * 16)));
+          __cvta_shared_to_generic(sbase + (f * NS + sr) * 32 * 16)));
+    sr = sr + 1 == NS ? 0 : sr + 1;
   }
 };
 
@@ -397,7 +418,6 @@ template <class T> __host__ __device__ constexpr int strip_w() { return 32 * MNP
 // the lane's nodes are in the strip's output columns.
 #define MPRO                                                                  \
   constexpr int NP = MNP<T>::NP;                                              \
-  __shared__ double sh[NVMAX * 32];                                           \
   const int rhs = blockIdx.z;                                                 \
   if (active && !active[rhs]) return;                                         \
   const long long off = (long long)rhs * g.vstride;                           \
@@ -411,16 +431,14 @@ template <class T> __host__ __device__ constexpr int strip_w() { return 32 * MNP
   const MCtx<T, IN> ctx{op, g, i, j0, j1, outl};
 
 // Runs pass P on the warp's strip and chunk (rows j0-2 .. t1 read) and
-// returns its sums in acc.  stg: the warp's staging area, [NF][4 slots][32
-// lanes] of 16 bytes.
+// returns its sums in acc.  stg: the warp's staging area, [NF][NS slots][32
+// lanes] of 16 bytes, free again (every copy landed, the warp converged) on
+// return.
 template <template <class, bool> class P, class T, bool IN, int NV, class Init>
 __device__ __forceinline__ void run_pass(const MCtx<T, IN>& c, int t1, const void* stg, T (&acc)[NV], Init&& init) {
-  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(stg) + (threadIdx.x & 31) * 16;
   P<T, IN> p;
   p.m.c = c;
-  constexpr int NF = sizeof(p.m.src) / sizeof(p.m.src[0]);
-#pragma unroll
-  for (int f = 0; f < NF; ++f) p.m.sbase[f] = s0 + f * 4 * 32 * 16;
+  p.m.sbase = (uint32_t)__cvta_generic_to_shared(stg) + (threadIdx.x & 31) * 16;
   p.m.t1 = t1;
   init(p);
 #pragma unroll
@@ -428,6 +446,7 @@ __device__ __forceinline__ void run_pass(const MCtx<T, IN>& c, int t1, const voi
   p.m.prime(c.j0 - 2);
   march(p, c.j0 - 2, t1);
   asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncwarp();
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = p.acc[k];
 }
@@ -453,7 +472,8 @@ __global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const 
                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
   MPRO
   T acc[3];
-  __shared__ typename SlotT<T>::type stg[2][4][32];
+  __shared__ __align__(16) unsigned char stg[ring_bytes<2>()];
+  double* sh = reinterpret_cast<double*>(stg);
   run_pass<P0>(ctx, j1 + 1, stg, acc, [&](auto& p) {
     p.m.src[0] = x + off;
     p.m.src[1] = b + off;
@@ -478,7 +498,8 @@ __global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const
   const T s0 = (T)S[G_S];
   const cx<T> c0 = mk<T>((T)(S[G_H] * S[G_S]), (T)(S[G_H + 1] * S[G_S]));
   T acc[7];
-  __shared__ typename SlotT<T>::type stg[1][4][32];
+  __shared__ __align__(16) unsigned char stg[ring_bytes<1>()];
+  double* sh = reinterpret_cast<double*>(stg);
   run_pass<P1>(ctx, j1 + 1, stg, acc, [&](auto& p) {
     p.m.src[0] = u0 + off;
     p.ws = u1 + off;
@@ -507,7 +528,8 @@ __global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const
   const cx<T> c0 = mk<T>((T)(S[G_H + 2 * 1] * S[G_S]), (T)(S[G_H + 2 * 1 + 1] * S[G_S]));
   const cx<T> c1 = mk<T>((T)(S[G_H + 2 * 4] * S[G_S + 1]), (T)(S[G_H + 2 * 4 + 1] * S[G_S + 1]));
   T acc[11];
-  __shared__ typename SlotT<T>::type stg[2][4][32];
+  __shared__ __align__(16) unsigned char stg[ring_bytes<2>()];
+  double* sh = reinterpret_cast<double*>(stg);
   run_pass<P2>(ctx, j1 + 1, stg, acc, [&](auto& p) {
     p.m.src[0] = u1 + off;
     p.m.src[1] = u0 + off;
@@ -541,7 +563,8 @@ __global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const
   for (int l = 0; l < 3; ++l)
     cl[l] = mk<T>((T)(S[G_H + 2 * (l * 3 + 2)] * S[G_S + l]), (T)(S[G_H + 2 * (l * 3 + 2) + 1] * S[G_S + l]));
   T acc[1];
-  __shared__ typename SlotT<T>::type stg[3][4][32];
+  __shared__ __align__(16) unsigned char stg[ring_bytes<3>()];
+  double* sh = reinterpret_cast<double*>(stg);
   run_pass<P3>(ctx, j1, stg, acc, [&](auto& p) {
     p.m.src[0] = u2 + off;
     p.m.src[1] = u0 + off;
