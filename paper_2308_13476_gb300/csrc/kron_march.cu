@@ -31,8 +31,8 @@ struct KGeo {
 };
 
 // A v down column i: the input rows arrive in order through a per-warp
-// shared-memory ring (each row's 32 + 2R columns around the warp's columns,
-// copied by cp.async KD rows ahead of use, so the 2R+1 neighbours of a lane
+// shared-memory ring (each row's 32 + 2RA columns around the warp's columns,
+// RA >= R, copied by cp.async KD rows ahead of use, so the 2R+1 neighbours of a lane
 // are read from shared memory instead of being loaded from L2 2R+1 times);
 // advance() forms the two row sums of the lane's column and appends them to
 // the register ring of the last 2R+1 rows, and combine() returns (A v)(i, m)
@@ -40,9 +40,45 @@ struct KGeo {
 constexpr int KD = 4;    // rows in flight ahead of use
 constexpr int KSL = 8;   // ring slots (a power of two > KD)
 
+// Staged columns left (and right) of a warp's 32: R, rounded up to even for
+// complex64 so that a staged row starts on a 16-byte boundary (the warp's
+// first column is a multiple of 32, the row pitch a multiple of 4).
+template <class T, int R> constexpr int kron_ra() { return sizeof(T) == 4 ? (R + 1) & ~1 : R; }
+
+// Copy row r's staged columns cw0 - RA .. cw0 + 31 + RA of vs into dst.
+// complex64: one 16-byte copy of a column pair per lane, for the first
+// 16 + RA lanes; a pair that starts at column nx takes the zero halo column
+// nx + 1 with it, a pair right of it is zero-filled.  complex128: one
+// 16-byte element per copy.  The padded layout covers the columns left of
+// the grid and the rows past either edge.
+template <class T, int RA>
+__device__ __forceinline__ void stage_kron_row(cx<T>* dst, const cx<T>* vs, const Grid& g, int cw0, int lane,
+                                               int r) {
+  constexpr int WD = 32 + 2 * RA;
+  if constexpr (sizeof(cx<T>) == 8) {
+    if (lane < WD / 2) {
+      const int col = cw0 - RA + 2 * lane;
+      const bool ok = col <= g.nx;
+      const cx<T>* src = vs + g.at(ok ? col : 0, r);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + 2 * lane);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+    }
+  } else {
+#pragma unroll
+    for (int e = lane; e < WD; e += 32) {
+      const int col = cw0 - RA + e;
+      const bool ok = col <= g.nx;
+      const cx<T>* src = vs + g.at(ok ? col : 0, r);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + e);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+    }
+  }
+}
+
 template <class T, int R> struct KRing {
   static constexpr int K = 2 * R + 1;
-  static constexpr int WD = 32 + 2 * R;   // staged row width
+  static constexpr int RA = kron_ra<T, R>();
+  static constexpr int WD = 32 + 2 * RA;   // staged row width
   cx<T> G[K];
   T Wx[K];
   cx<T> s1[K], s2[K];
@@ -61,22 +97,9 @@ template <class T, int R> struct KRing {
       s2[k] = mk<T>(T(0), T(0));
     }
   }
-  // copy row r's staged columns into its slot; columns past nx are
-  // zero-filled (the padded layout covers the R columns left of the grid and
-  // the R rows past either edge)
+  // copy row r's staged columns into its slot
   __device__ __forceinline__ void issue(int r) {
-    cx<T>* dst = sm + ((r - r0) & (KSL - 1)) * WD;
-#pragma unroll
-    for (int e = lane; e < WD; e += 32) {
-      const int col = cw0 - R + e;
-      const bool ok = col <= g.nx;
-      const cx<T>* src = vs + g.at(ok ? col : 0, r);
-      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + e);
-      if (sizeof(cx<T>) == 16)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
-      else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
-    }
+    stage_kron_row<T, RA>(sm + ((r - r0) & (KSL - 1)) * WD, vs, g, cw0, lane, r);
   }
   __device__ __forceinline__ static void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
   // rows r0 .. r0 + KD - 1 in flight
@@ -95,7 +118,7 @@ template <class T, int R> struct KRing {
     commit();
     asm volatile("cp.async.wait_group %0;\n" ::"n"(KD) : "memory");
     __syncwarp();   // row r, copied by all lanes, is visible to all
-    const cx<T>* row = sm + ((r - r0) & (KSL - 1)) * WD + lane + R;
+    const cx<T>* row = sm + ((r - r0) & (KSL - 1)) * WD + lane + RA;
     cx<T> a = mk<T>(T(0), T(0)), c = mk<T>(T(0), T(0));
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
@@ -130,7 +153,7 @@ template <class T, int R> struct KRing {
 // warp has work; `col`: the lane's column is inside the grid.
 #define KPRO                                                                  \
   __shared__ double sh[NVMAX * 32];                                           \
-  __shared__ __align__(16) cx<T> ksm[KW][KSL][32 + 2 * R];                    \
+  __shared__ __align__(16) cx<T> ksm[KW][KSL][KRing<T, R>::WD];              \
   const int rhs = blockIdx.z;                                                 \
   if (active && !active[rhs]) return;                                         \
   const long long off = (long long)rhs * g.vstride;                           \
@@ -237,7 +260,8 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
 // saves 7 of 28 vector passes and two launches.
 template <class T, int R, int NS> struct KRingF {
   static constexpr int K = 2 * R + 1;
-  static constexpr int WD = 32 + 2 * R;
+  static constexpr int RA = kron_ra<T, R>();
+  static constexpr int WD = 32 + 2 * RA;
   cx<T> G[K];
   T Wx[K];
   cx<T> s1[K], s2[K];
@@ -260,20 +284,7 @@ template <class T, int R, int NS> struct KRingF {
   __device__ __forceinline__ int slot(int r) const { return (r - r0) & (KSL - 1); }
   __device__ __forceinline__ void issue(int r) {
 #pragma unroll
-    for (int v = 0; v < NS; ++v) {
-      cx<T>* dst = sm + (v * KSL + slot(r)) * WD;
-#pragma unroll
-      for (int e = lane; e < WD; e += 32) {
-        const int col = cw0 - R + e;
-        const bool ok = col <= g.nx;
-        const cx<T>* src = vs[v] + g.at(ok ? col : 0, r);
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + e);
-        if (sizeof(cx<T>) == 16)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
-        else
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
-      }
-    }
+    for (int v = 0; v < NS; ++v) stage_kron_row<T, RA>(sm + (v * KSL + slot(r)) * WD, vs[v], g, cw0, lane, r);
   }
   __device__ __forceinline__ static void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
   __device__ __forceinline__ void prime(int last) {
@@ -292,15 +303,30 @@ template <class T, int R, int NS> struct KRingF {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(KD) : "memory");
     __syncwarp();
     const int sl = slot(r);
+    if constexpr (sizeof(cx<T>) == 8) {   // a column pair per lane, 16-byte accesses
+      if (lane < WD / 2) {
+        const int e = 2 * lane;
+        const float4 wv = *reinterpret_cast<const float4*>(sm + sl * WD + e);
+        cx<T> a = scl<T>(cw, mk<T>(wv.x, wv.y)), b = scl<T>(cw, mk<T>(wv.z, wv.w));
 #pragma unroll
-    for (int e = lane; e < WD; e += 32) {
-      cx<T> u = scl<T>(cw, sm[sl * WD + e]);
+        for (int l = 0; l < NS - 1; ++l) {
+          const float4 q = *reinterpret_cast<const float4*>(sm + ((1 + l) * KSL + sl) * WD + e);
+          a = sub<T>(a, mul<T>(c[l], mk<T>(q.x, q.y)));
+          b = sub<T>(b, mul<T>(c[l], mk<T>(q.z, q.w)));
+        }
+        *reinterpret_cast<float4*>(fm + sl * WD + e) = make_float4(a.x, a.y, b.x, b.y);
+      }
+    } else {
 #pragma unroll
-      for (int l = 0; l < NS - 1; ++l) u = sub<T>(u, mul<T>(c[l], sm[((1 + l) * KSL + sl) * WD + e]));
-      fm[sl * WD + e] = u;
+      for (int e = lane; e < WD; e += 32) {
+        cx<T> u = scl<T>(cw, sm[sl * WD + e]);
+#pragma unroll
+        for (int l = 0; l < NS - 1; ++l) u = sub<T>(u, mul<T>(c[l], sm[((1 + l) * KSL + sl) * WD + e]));
+        fm[sl * WD + e] = u;
+      }
     }
     __syncwarp();
-    const cx<T>* row = fm + sl * WD + lane + R;
+    const cx<T>* row = fm + sl * WD + lane + RA;
     cx<T> a = mk<T>(T(0), T(0)), b = mk<T>(T(0), T(0));
 #pragma unroll
     for (int dx = -R; dx <= R; ++dx) {
@@ -318,8 +344,8 @@ template <class T, int R, int NS> struct KRingF {
     return row[0];
   }
   // staged vector v (1 + l for u_l) and the formed u_J at row m, lane's column
-  __device__ __forceinline__ cx<T> staged(int v, int m) const { return sm[(v * KSL + slot(m)) * WD + lane + R]; }
-  __device__ __forceinline__ cx<T> formed(int m) const { return fm[slot(m) * WD + lane + R]; }
+  __device__ __forceinline__ cx<T> staged(int v, int m) const { return sm[(v * KSL + slot(m)) * WD + lane + RA]; }
+  __device__ __forceinline__ cx<T> formed(int m) const { return fm[slot(m) * WD + lane + RA]; }
   __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
     const cx<T>* H = op.hy + m * K;
     const T* Wy = op.wy + m * K;
@@ -344,8 +370,8 @@ __global__ void __launch_bounds__(KW * 32) km_arn_ab(Grid g, KGeo kg, OpK<T, R> 
   constexpr int NB = 1 + 2 * J;         // fin_b<J-1>: |u_J|^2, <u_J, u_l> (l < J)
   constexpr int NA = 2 * (J + 1);       // fin_a<J>: <u_l, w'> (l <= J)
   __shared__ double sh[NVMAX * 32];
-  __shared__ __align__(16) cx<T> ksm[KW][NS][KSL][32 + 2 * R];
-  __shared__ __align__(16) cx<T> kfm[KW][KSL][32 + 2 * R];
+  __shared__ __align__(16) cx<T> ksm[KW][NS][KSL][KRingF<T, R, NS>::WD];
+  __shared__ __align__(16) cx<T> kfm[KW][KSL][KRingF<T, R, NS>::WD];
   const int rhs = blockIdx.z;
   if (active && !active[rhs]) return;
   const long long off = (long long)rhs * g.vstride;
