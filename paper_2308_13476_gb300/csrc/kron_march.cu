@@ -30,13 +30,37 @@ struct KGeo {
   int nchunks;
 };
 
+template <int P, int K, class F> __device__ __forceinline__ void kmarch_phases(int r, int last, F& f) {
+  if constexpr (P < K) {
+    if (r + P > last) return;
+    f(std::integral_constant<int, P>{}, r + P);
+    kmarch_phases<P + 1, K>(r, last, f);
+  }
+}
+// Runs f(phase, r) for r = r0 .. last, phase = (r - r0) mod K as an
+// std::integral_constant.
+template <int K, class F> __device__ __forceinline__ void kmarch(int r0, int last, F&& f) {
+#pragma unroll 1
+  for (int r = r0; r <= last; r += K) kmarch_phases<0, K>(r, last, f);
+}
+
+// Whether the march over a radius-R level is unrolled so that its register
+// ring never moves (KU = 2R+1 phases), or keeps one phase and shifts the ring
+// by a row per step (KU = 1).  Unrolling the radius-3 marches (7 phases)
+// raised the fused passes from 96 to 122-126 registers per thread and cost
+// them a resident block per SM, so only radius 2 unrolls.
+template <int R> constexpr int KU = R == 2 ? 2 * R + 1 : 1;
+
 // A v down column i: the input rows arrive in order through a per-warp
 // shared-memory ring (each row's 32 + 2RA columns around the warp's columns,
 // RA >= R, copied by cp.async KD rows ahead of use, so the 2R+1 neighbours of a lane
 // are read from shared memory instead of being loaded from L2 2R+1 times);
-// advance() forms the two row sums of the lane's column and appends them to
-// the register ring of the last 2R+1 rows, and combine() returns (A v)(i, m)
-// once that ring holds rows m-R..m+R.
+// advance<P>() forms the two row sums of the lane's column and puts them in
+// slot P of the register ring of the last 2R+1 rows, and combine<P>() returns
+// (A v)(i, m) once that ring holds rows m-R..m+R.  With R = 2 the march over
+// rows is unrolled by 2R+1 (kmarch, KU), so that row r sits in the
+// compile-time slot P = (r - r0) mod (2R+1) and the ring never moves; with
+// R = 3 the ring shifts by one row per step.
 constexpr int KD = 4;    // rows in flight ahead of use
 constexpr int KSL = 8;   // ring slots (a power of two > KD)
 
@@ -112,7 +136,7 @@ template <class T, int R> struct KRing {
   }
   // take input row r (rows up to `last` exist): row r + KD in flight, row r's
   // sums into the register ring.  All lanes of the warp call it.
-  __device__ __forceinline__ void advance(int r, int last) {
+  template <int P> __device__ __forceinline__ void advance(int r, int last) {
     __syncwarp();   // every lane is done with the slot row r + KD reuses
     if (r + KD <= last) issue(r + KD);
     commit();
@@ -126,24 +150,29 @@ template <class T, int R> struct KRing {
       a = fma_c<T>(G[dx + R], xv, a);
       c = mk<T>(fma(Wx[dx + R], xv.x, c.x), fma(Wx[dx + R], xv.y, c.y));
     }
+    if constexpr (KU<R> == 1) {
 #pragma unroll
-    for (int k = 0; k < K - 1; ++k) {
-      s1[k] = s1[k + 1];
-      s2[k] = s2[k + 1];
+      for (int k = 0; k < K - 1; ++k) {
+        s1[k] = s1[k + 1];
+        s2[k] = s2[k + 1];
+      }
     }
-    s1[K - 1] = a;
-    s2[K - 1] = c;
+    s1[KU<R> == 1 ? K - 1 : P] = a;
+    s2[KU<R> == 1 ? K - 1 : P] = c;
   }
-  // combination along y for output row m (ring holds rows m-R..m+R)
-  __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
+  // combination along y for output row m = r - R, r the row just taken in
+  // slot P: row m + dy sits in slot (P + 1 + R + dy) mod K, or in slot dy + R
+  // of the shifting ring (KU = 1)
+  template <int P> __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
     const cx<T>* H = op.hy + m * K;
     const T* Wy = op.wy + m * K;
     cx<T> acc = mk<T>(T(0), T(0));
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy) {
+      const int q = KU<R> == 1 ? dy + R : (P + 1 + R + dy) % K;
       const T wy = __ldg(Wy + dy + R);
-      acc = mk<T>(fma(wy, s1[dy + R].x, acc.x), fma(wy, s1[dy + R].y, acc.y));
-      acc = fma_c<T>(__ldg(H + dy + R), s2[dy + R], acc);
+      acc = mk<T>(fma(wy, s1[q].x, acc.x), fma(wy, s1[q].y, acc.y));
+      acc = fma_c<T>(__ldg(H + dy + R), s2[q], acc);
     }
     return acc;
   }
@@ -186,17 +215,17 @@ __global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op
   T a0[1] = {T(0)};
   if (has) {
     KMARCH_SETUP(x + off)
-#pragma unroll 1
-    for (int r = j0 - R; r <= last; ++r) {
-      ring.advance(r, last);
+    kmarch<KU<R>>(j0 - R, last, [&](auto ph, int r) {
+      constexpr int P = decltype(ph)::value;
+      ring.template advance<P>(r, last);
       const int m = r - R;
       if (m >= j0 && col) {
         const int p = g.at(i, m);
-        const cx<T> res = sub<T>(b[off + p], ring.combine(op, m));
+        const cx<T> res = sub<T>(b[off + p], ring.template combine<P>(op, m));
         u0[off + p] = res;
         a0[0] += abs2<T>(res);
       }
-    }
+    });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   double v[1];
@@ -221,13 +250,13 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
     const T sJ = (T)S[G_S + J];
     const cx<T>* us[3] = {u0 + off, u1 + off, u2 + off};
     KMARCH_SETUP(uJ + off)
-#pragma unroll 1
-    for (int r = j0 - R; r <= last; ++r) {
-      ring.advance(r, last);
+    kmarch<KU<R>>(j0 - R, last, [&](auto ph, int r) {
+      constexpr int P = decltype(ph)::value;
+      ring.template advance<P>(r, last);
       const int m = r - R;
       if (m >= j0 && col) {
         const int p = g.at(i, m);
-        const cx<T> a = scl<T>(sJ, ring.combine(op, m));
+        const cx<T> a = scl<T>(sJ, ring.template combine<P>(op, m));
         w[off + p] = a;
 #pragma unroll
         for (int l = 0; l <= J; ++l) {
@@ -236,7 +265,7 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
           acc[2 * l + 1] += d.y;
         }
       }
-    }
+    });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   double v[2 * (J + 1)];
@@ -296,7 +325,7 @@ template <class T, int R, int NS> struct KRingF {
   }
   // take input row r: form u_J on it (returned for the lane's column), its
   // two row sums into the register ring.  All lanes of the warp call it.
-  __device__ __forceinline__ cx<T> advance(int r, int last, T cw, const cx<T> (&c)[NS - 1]) {
+  template <int P> __device__ __forceinline__ cx<T> advance(int r, int last, T cw, const cx<T> (&c)[NS - 1]) {
     __syncwarp();
     if (r + KD <= last) issue(r + KD);
     commit();
@@ -334,34 +363,39 @@ template <class T, int R, int NS> struct KRingF {
       a = fma_c<T>(G[dx + R], xv, a);
       b = mk<T>(fma(Wx[dx + R], xv.x, b.x), fma(Wx[dx + R], xv.y, b.y));
     }
+    if constexpr (KU<R> == 1) {
 #pragma unroll
-    for (int k = 0; k < K - 1; ++k) {
-      s1[k] = s1[k + 1];
-      s2[k] = s2[k + 1];
+      for (int k = 0; k < K - 1; ++k) {
+        s1[k] = s1[k + 1];
+        s2[k] = s2[k + 1];
+      }
     }
-    s1[K - 1] = a;
-    s2[K - 1] = b;
+    s1[KU<R> == 1 ? K - 1 : P] = a;
+    s2[KU<R> == 1 ? K - 1 : P] = b;
     return row[0];
   }
   // staged vector v (1 + l for u_l) and the formed u_J at row m, lane's column
   __device__ __forceinline__ cx<T> staged(int v, int m) const { return sm[(v * KSL + slot(m)) * WD + lane + RA]; }
   __device__ __forceinline__ cx<T> formed(int m) const { return fm[slot(m) * WD + lane + RA]; }
-  __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
+  template <int P> __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
     const cx<T>* H = op.hy + m * K;
     const T* Wy = op.wy + m * K;
     cx<T> acc = mk<T>(T(0), T(0));
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy) {
+      const int q = KU<R> == 1 ? dy + R : (P + 1 + R + dy) % K;
       const T wy = __ldg(Wy + dy + R);
-      acc = mk<T>(fma(wy, s1[dy + R].x, acc.x), fma(wy, s1[dy + R].y, acc.y));
-      acc = fma_c<T>(__ldg(H + dy + R), s2[dy + R], acc);
+      acc = mk<T>(fma(wy, s1[q].x, acc.x), fma(wy, s1[q].y, acc.y));
+      acc = fma_c<T>(__ldg(H + dy + R), s2[q], acc);
     }
     return acc;
   }
 };
 
+// Resident blocks per SM the register budget must allow: as many as the
+// shared memory holds (six for radius 2 with J = 1, five otherwise).
 template <class T, int R, int J>
-__global__ void __launch_bounds__(KW * 32) km_arn_ab(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ win,
+__global__ void __launch_bounds__(KW * 32, R == 2 && J == 1 ? 6 : 5) km_arn_ab(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ win,
                                                 const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1,
                                                 cx<T>* __restrict__ uJ, cx<T>* __restrict__ wout,
                                                 double* __restrict__ st, double* partial, unsigned* tickets,
@@ -410,9 +444,9 @@ __global__ void __launch_bounds__(KW * 32) km_arn_ab(Grid g, KGeo kg, OpK<T, R> 
     ring.r0 = j0 - R;
     const int last = j1 + R - 1;
     ring.prime(last);
-#pragma unroll 1
-    for (int r = j0 - R; r <= last; ++r) {
-      const cx<T> u = ring.advance(r, last, cw, c);
+    kmarch<KU<R>>(j0 - R, last, [&](auto ph, int r) {
+      constexpr int P = decltype(ph)::value;
+      const cx<T> u = ring.template advance<P>(r, last, cw, c);
       if (r >= j0 && r < j1 && col) {   // own row: store u_J, the inputs of fin_b<J-1>
         uJ[off + g.at(i, r)] = u;
         acc[0] += abs2<T>(u);
@@ -426,7 +460,7 @@ __global__ void __launch_bounds__(KW * 32) km_arn_ab(Grid g, KGeo kg, OpK<T, R> 
       const int m = r - R;
       if (m >= j0 && col) {
         const int p = g.at(i, m);
-        const cx<T> a = ring.combine(op, m);
+        const cx<T> a = ring.template combine<P>(op, m);
         wout[off + p] = a;
 #pragma unroll
         for (int l = 0; l <= J; ++l) {
@@ -436,7 +470,7 @@ __global__ void __launch_bounds__(KW * 32) km_arn_ab(Grid g, KGeo kg, OpK<T, R> 
           acc[NB + 2 * l + 1] += d.y;
         }
       }
-    }
+    });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   double v[NB + NA];
