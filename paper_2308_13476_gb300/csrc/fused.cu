@@ -13,6 +13,8 @@
 //    outside the grid stay zero (they are not unknowns); nodes computed in
 //    two tiles' halos get identical values, so the result equals nu separate
 //    sweeps node for node.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace hmg {
@@ -32,15 +34,36 @@ __global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, 
   const int I0 = blockIdx.x * CTX, J0 = blockIdx.y * CTY;
   const int fx0 = 2 * I0 - 2, fy0 = 2 * J0 - 2;   // fine origin of the footprint
   const int tid = threadIdx.y * CTX + threadIdx.x;
-  for (int q = tid; q < RFX * RFY; q += CTX * CTY) {
-    const int li = q % RFX, lj = q / RFX;
-    const int i = fx0 + li, j = fy0 + lj;
-    cx<T> r = mk<T>(0, 0);   // outside the grid the fine residual is zero
-    if (i >= 0 && i <= gf.nx && j >= 0 && j <= gf.ny) {
-      const int p = gf.at(i, j);
-      r = sub<T>(bs[p], op.apply(xs, p, gf.pitch, i, j));
+  if constexpr (std::is_same<Op, Op0<T>>::value) {
+    // matrix-free fine level: a fixed, unrolled count of footprint nodes per
+    // thread, each evaluated at its node clamped into the grid (every load is
+    // in bounds and unconditional, so the loads of all of them can be in
+    // flight together) and replaced by zero outside the grid
+    constexpr int NQ = (RFX * RFY + CTX * CTY - 1) / (CTX * CTY);
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const int q = tid + k * CTX * CTY;
+      if (k + 1 < NQ || q < RFX * RFY) {
+        const int li = q % RFX, lj = q / RFX;
+        const int i = fx0 + li, j = fy0 + lj;
+        const int ic = min(max(i, 0), gf.nx), jc = min(max(j, 0), gf.ny);
+        const int p = gf.at(ic, jc);
+        const cx<T> r = sub<T>(bs[p], op.apply(xs, p, gf.pitch, ic, jc));
+        const bool in = i == ic && j == jc;
+        rt[lj][li] = in ? r : mk<T>(0, 0);   // outside the grid the fine residual is zero
+      }
     }
-    rt[lj][li] = r;
+  } else {
+    for (int q = tid; q < RFX * RFY; q += CTX * CTY) {
+      const int li = q % RFX, lj = q / RFX;
+      const int i = fx0 + li, j = fy0 + lj;
+      cx<T> r = mk<T>(0, 0);   // outside the grid the fine residual is zero
+      if (i >= 0 && i <= gf.nx && j >= 0 && j <= gf.ny) {
+        const int p = gf.at(i, j);
+        r = sub<T>(bs[p], op.apply(xs, p, gf.pitch, i, j));
+      }
+      rt[lj][li] = r;
+    }
   }
   __syncthreads();
   const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
