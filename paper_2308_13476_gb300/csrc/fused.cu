@@ -22,6 +22,10 @@ namespace hmg {
 constexpr int CTX = 32, CTY = 8;                  // coarse tile of k_resid_restrict
 constexpr int RFX = 2 * CTX + 3, RFY = 2 * CTY + 3;  // fine footprint incl. restriction halo
 
+// radius of a Kronecker-form operator, 0 for the others
+template <class Op> struct KronRadius { static constexpr int R = 0; };
+template <class T, int R_> struct KronRadius<OpK<T, R_>> { static constexpr int R = R_; };
+
 template <class T, class Op>
 __global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, Op op, const cx<T>* __restrict__ x,
                                                               const cx<T>* __restrict__ b, cx<T>* __restrict__ rc,
@@ -52,6 +56,53 @@ __global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, 
         const bool in = i == ic && j == jc;
         rt[lj][li] = in ? r : mk<T>(0, 0);   // outside the grid the fine residual is zero
       }
+    }
+  } else if constexpr (KronRadius<Op>::R > 0 && sizeof(T) == 4) {
+    // Kronecker form A = W_y (x) G_x + H_y (x) W_x (complex64): the two row
+    // sums s1 = G_x x and s2 = W_x x of every footprint column are formed
+    // once per row (rows fy0 - R .. fy0 + RFY - 1 + R) into shared memory,
+    // and each footprint node combines the 2R + 1 rows around it along y.
+    // The sums and the combination run in the order of OpK::apply, so every
+    // residual is the same value; the work per node drops from 6 (2R+1)^2
+    // to about 12 (2R+1) FMAs.
+    constexpr int KR = KronRadius<Op>::R, K = 2 * KR + 1, SR = RFY + 2 * KR;
+    __shared__ cx<T> s1t[SR][RFX], s2t[SR][RFX];
+    for (int q = tid; q < SR * RFX; q += CTX * CTY) {
+      const int li = q % RFX, lr = q / RFX;
+      const int i = fx0 + li, j = fy0 - KR + lr;
+      cx<T> a = mk<T>(0, 0), c = mk<T>(0, 0);   // unused outside the grid's columns and their row halo
+      if (i >= 0 && i <= gf.nx && j >= -KR && j <= gf.ny + KR) {
+        const cx<T>* G = op.gx + i * K;
+        const T* Wx = op.wx + i * K;
+        const cx<T>* row = xs + gf.at(i, j);
+#pragma unroll
+        for (int dx = -KR; dx <= KR; ++dx) {
+          const cx<T> xv = row[dx];
+          a = fma_c<T>(G[dx + KR], xv, a);
+          c = mk<T>(fma(Wx[dx + KR], xv.x, c.x), fma(Wx[dx + KR], xv.y, c.y));
+        }
+      }
+      s1t[lr][li] = a;
+      s2t[lr][li] = c;
+    }
+    __syncthreads();
+    for (int q = tid; q < RFX * RFY; q += CTX * CTY) {
+      const int li = q % RFX, lj = q / RFX;
+      const int i = fx0 + li, j = fy0 + lj;
+      cx<T> r = mk<T>(0, 0);   // outside the grid the fine residual is zero
+      if (i >= 0 && i <= gf.nx && j >= 0 && j <= gf.ny) {
+        const cx<T>* H = op.hy + j * K;
+        const T* Wy = op.wy + j * K;
+        cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+        for (int dy = -KR; dy <= KR; ++dy) {
+          const cx<T> a = s1t[lj + KR + dy][li], c = s2t[lj + KR + dy][li];
+          acc = mk<T>(fma(Wy[dy + KR], a.x, acc.x), fma(Wy[dy + KR], a.y, acc.y));
+          acc = fma_c<T>(H[dy + KR], c, acc);
+        }
+        r = sub<T>(bs[gf.at(i, j)], acc);
+      }
+      rt[lj][li] = r;
     }
   } else {
     for (int q = tid; q < RFX * RFY; q += CTX * CTY) {
