@@ -5,7 +5,11 @@
 //    fine footprint plus the 2-node halo the restriction needs (Eq. (xex)
 //    transposed: fine offsets -2..2 around node 2I) into shared memory, then
 //    every thread restricts one coarse node from it.  The fine residual never
-//    goes to HBM.
+//    goes to HBM.  How the footprint residual is formed depends on the
+//    operator: the matrix-free fine level takes a fixed, unrolled set of
+//    nodes per thread; the Kronecker-form levels (complex64) form their row
+//    sums once per footprint row and combine them along y; the stored
+//    stencils (and complex128 Kronecker levels) apply the operator per node.
 //  * k_jacobi_fused: nu weighted-Jacobi sweeps (Sec. 3) of the fine level in
 //    one pass.  A block loads its tile of x with a nu-node halo and of b
 //    with a (nu-1)-node halo once, runs the sweeps in shared memory on a
