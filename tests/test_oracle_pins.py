@@ -291,6 +291,81 @@ def test_table_conv1_two_grid_norms():
         assert (ba < 1.0) == r[3].endswith("+"), (k, ba)
 
 
+def test_gamma_tilde_closed_form_with_projector():
+    # Definition def2s with A = a I (complex a), R = P^T / 4 and A_c = R A P:
+    # P A_c^-1 R A is the orthogonal projector Pi onto range(P) and X^-1 A =
+    # I / omega, so E = D~ A = I / omega + Pi and Gamma~ = I - (I - E)^H (I - E)
+    # has the eigenvalue 1 - 1/omega^2 on range(P) and 1 - (1 - 1/omega)^2 on
+    # its complement.  A transposed instead of conjugated operand, a wrong sign
+    # or a dropped term changes these values.
+    rng = np.random.default_rng(11)
+    n, m = 9, 4
+    a = 2.0 - 3.0j
+    A = a * np.eye(n)
+    P = rng.standard_normal((n, m))
+    R = P.T / 4
+    Ac = R @ A @ P
+    for omega in (4.5, 1.7):
+        G = analysis.gamma_tilde(A, P, R, Ac, omega)
+        assert np.abs(G - G.conj().T).max() <= 1e-12
+        ev = np.sort(np.linalg.eigvalsh(0.5 * (G + G.conj().T)))
+        want = np.sort([1 - 1 / omega ** 2] * m + [1 - (1 - 1 / omega) ** 2] * (n - m))
+        assert np.allclose(ev, want, rtol=0, atol=1e-12), (omega, ev, want)
+    # omega < 1/2 makes 1 - (1 - 1/omega)^2 negative: not HPD
+    assert analysis.is_hpd(analysis.gamma_tilde(A, P, R, Ac, 4.5))
+    assert not analysis.is_hpd(analysis.gamma_tilde(A, P, R, Ac, 0.4))
+
+
+def test_gamma_tilde_eigenvalues_from_singular_values():
+    # Gamma~ = E + E^H - E^H E = I - (I - E)^H (I - E) with E = D~ A, so its
+    # eigenvalues are 1 - sigma_i^2 with sigma_i the singular values of
+    # I - E.  With no coarse space (P = 0) E is the Jacobi-scaled X^-1 A of
+    # Sec. 3, here for a non-normal complex A.
+    rng = np.random.default_rng(12)
+    n = 7
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) + 6 * np.eye(n)
+    P = np.zeros((n, 1))
+    R = np.zeros((1, n))
+    Ac = np.eye(1)
+    omega = 1.3
+    G = analysis.gamma_tilde(A, P, R, Ac, omega)
+    E = A / (omega * np.diag(A))[:, None]
+    sv = np.linalg.svd(np.eye(n) - E, compute_uv=False)
+    ev = np.sort(np.linalg.eigvalsh(0.5 * (G + G.conj().T)))
+    assert np.allclose(ev, np.sort(1 - sv ** 2), rtol=0, atol=1e-12)
+    assert analysis.is_hpd(G) == bool(sv.max() < 1)
+
+
+def test_is_hpd_cases():
+    rng = np.random.default_rng(13)
+    n = 8
+    Q = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    U, _ = np.linalg.qr(Q)
+    hpd = U @ np.diag(np.linspace(0.1, 3.0, n)) @ U.conj().T
+    assert analysis.is_hpd(hpd)
+    indef = U @ np.diag(np.r_[-1e-3, np.linspace(0.1, 3.0, n - 1)]) @ U.conj().T
+    assert not analysis.is_hpd(indef)
+    skew = hpd + 1e-6 * (Q - Q.conj().T)   # positive real part, but not Hermitian
+    assert not analysis.is_hpd(skew)
+
+
+def test_table_conv1_hpd_marks():
+    # Table conv1 (tests/golden/table_conv1.txt, '+' = Gamma~ reported HPD):
+    # Bezier + CSL is HPD at k = 5, 10, 20; every linear entry is not, nor is
+    # Bezier on A at k = 10, 20.  The mark on Bezier/A at k = 5 is not
+    # reproduced by Gamma~ of Definition def2s (its smallest eigenvalue is
+    # -0.12 there, although ||T0|| = 0.991 < 1 is).
+    for r in _table("table_conv1.txt")[:3]:
+        k = float(r[0])
+        n = int(round(k / 0.625))
+        for col, kind, on in ((1, "linear", "A"), (2, "linear", "C"), (3, "bezier", "A"), (4, "bezier", "C")):
+            if (k, kind, on) == (5.0, "bezier", "A"):
+                continue
+            A, P, R, Ac = analysis.two_grid_parts(n, n, 1 / n, k, 0.7, kind=kind, coarsen_on=on)
+            G = analysis.gamma_tilde(A, P, R, Ac, 4.5)
+            assert analysis.is_hpd(G) == r[col].endswith("+"), (k, kind, on)
+
+
 def test_gmres_counts_track_table_cons2g():
     # Table cons2g (beta2 = 1/k, GMRES(3)): V and W counts at k = 50 within
     # 30 % (+-1 cycle) of the printed values, non-increasing in nu.
