@@ -297,3 +297,28 @@ def test_interior_row_march_path_on_a_larger_grid():
         r = b.ravel() - A @ host(x)[0].ravel()
         assert abs(np.linalg.norm(r) / np.linalg.norm(b) - rr[0]) <= 1e-3 * rr[0], precision
         s.close()
+
+
+def test_batched_solves_are_bitwise_reproducible():
+    """Every reduction sums its block partials in a fixed order and no result
+    depends on which block or stream finishes first, so a batched mixed solve
+    (fine-level row marches with their boundary launches on a side stream,
+    Kronecker-level column marches, the coarse interpreter) repeats bit for
+    bit: twice on one handle (graph replays) and once on a fresh handle."""
+    n, k, B = 256, 75.0, 8
+    h = 1.0 / n
+    b = dev(synth.source_row(n, n, h, B))
+    runs = []
+    s = hm.Solver(n, n, h, k, 1 / k, smoother="gmres3", nu_pre=2, nu_post=2, precision="mixed", batch=B, march=1)
+    for _ in range(2):
+        x, st, cyc, rr = s.solve(b, tol=1e-8)
+        assert st == hm.MG_OK
+        runs.append((host(x), cyc, rr))
+    s.close()
+    s = hm.Solver(n, n, h, k, 1 / k, smoother="gmres3", nu_pre=2, nu_post=2, precision="mixed", batch=B, march=1)
+    x, st, cyc, rr = s.solve(b, tol=1e-8)
+    runs.append((host(x), cyc, rr))
+    s.close()
+    for x_, cyc_, rr_ in runs[1:]:
+        assert np.array_equal(x_, runs[0][0])
+        assert cyc_ == runs[0][1] and rr_ == runs[0][2]
