@@ -125,6 +125,27 @@ def test_prolongation_reproduces_linear_functions_inside():
     assert np.allclose(f[1:-1, 1:-1], (1 + ix * iy)[1:-1, 1:-1], atol=1e-12)
 
 
+def test_linear_transfers_are_textbook_interpolation_and_full_weighting():
+    # kind="linear" (the "Linear" column of Table conv1): 1D linear
+    # interpolation reproduces linear functions at every fine node, the
+    # boundary included; in 2D, R = P^T / 4 is the textbook full-weighting
+    # stencil [1 2 1; 2 4 2; 1 2 1] / 16 at interior coarse nodes.
+    n = 12
+    P = transfer.prolongation_1d(n, kind="linear").toarray()
+    J = np.arange(n // 2 + 1)
+    i = np.arange(n + 1)
+    for a, b in [(1.0, 0.0), (0.3, 2.0), (-1.0, 0.25)]:
+        assert np.allclose(P @ (a + b * 2 * J), a + b * i, rtol=0, atol=1e-13)
+    R = transfer.restriction(n, n, kind="linear").toarray()
+    nf, nc = n + 1, n // 2 + 1
+    fw = np.array([[1, 2, 1], [2, 4, 2], [1, 2, 1]]) / 16
+    for I, Jc in [(1, 1), (2, 3), (5, 4)]:
+        row = R[Jc * nc + I].reshape(nf, nf)
+        want = np.zeros((nf, nf))
+        want[2 * Jc - 1:2 * Jc + 2, 2 * I - 1:2 * I + 2] = fw
+        assert np.array_equal(row, want), (I, Jc)
+
+
 def test_restriction_scale_and_cgc_invariance():
     n = 8
     R = transfer.restriction(n, n).toarray()
