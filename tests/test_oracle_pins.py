@@ -285,6 +285,29 @@ def test_two_level_cycle_equals_dense_two_grid_map():
     assert np.linalg.norm(x1 - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_many_coarse_cycles_converge_to_the_two_grid_cycle():
+    # The cycle's recursion (Sec. 3; gamma = 2 is the W-cycle): with gamma
+    # cycles on level 1 of a three-level hierarchy, the level-1 correction
+    # is gamma iterations on A_1 e = r_c from zero.  They converge, so as
+    # gamma grows the three-level cycle tends to the two-level cycle with an
+    # exact solve on the same A_1 = R C P.  A wrong initial guess, residual
+    # or operator in the recursion breaks the limit.
+    n, k = 32, 5.0
+    h = 1 / n
+    H3 = hierarchy.build_hierarchy(n, n, h, k, 0.7, levels=3)
+    H2 = hierarchy.build_hierarchy(n, n, h, k, 0.7, levels=2)
+    rng = np.random.default_rng(5)
+    N = (n + 1) ** 2
+    b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    x0 = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    for sm, gammas, bar in (("gmres3", (1, 2, 10, 40), 1e-12), ("jacobi", (1, 2, 10, 80), 1e-5)):
+        ref = cycle.mg_cycle(H2, 0, x0, b, cycle.CycleOptions(1, sm, 1, 1, 4.5))
+        d = [np.linalg.norm(cycle.mg_cycle(H3, 0, x0, b, cycle.CycleOptions(g, sm, 1, 1, 4.5)) - ref)
+             / np.linalg.norm(ref) for g in gammas]
+        assert all(d[i + 1] < d[i] for i in range(len(d) - 2)), (sm, d)
+        assert d[-1] <= bar and d[0] > 1e-3, (sm, d)
+
+
 def test_converged_cycle_matches_direct_solve():
     n, k = 32, 20.0
     h = 1 / n
