@@ -37,6 +37,26 @@ def test_operator_matches_loop_restatement_and_is_symmetric():
         assert np.abs(A - A.T).max() == 0.0          # complex symmetric
 
 
+def test_variable_wavenumber_field_is_local_and_reduces_to_constant():
+    # MP 2-B takes k(x) node by node: a constant field gives the constant-k
+    # matrix exactly, and changing k at one node changes only that node's
+    # diagonal entry (on a non-square grid, so a transposed field index
+    # moves the change to another row).
+    nx, ny, h = 9, 6, 0.1
+    for b2 in (0.0, 0.7):
+        A = problem.helmholtz_matrix(nx, ny, h, 4.0, b2)
+        F = problem.helmholtz_matrix(nx, ny, h, np.full((ny + 1, nx + 1), 4.0), b2)
+        assert np.array_equal(A.toarray(), F.toarray())
+        for (i, j) in ((3, 2), (0, 4), (nx, ny)):   # interior, edge, corner
+            kf = np.full((ny + 1, nx + 1), 4.0)
+            kf[j, i] = 5.5
+            D = (problem.helmholtz_matrix(nx, ny, h, kf, b2) - A).toarray()
+            p = j * (nx + 1) + i
+            assert D[p, p] != 0
+            D[p, p] = 0
+            assert np.abs(D).max() == 0, (i, j, b2)
+
+
 def test_zero_wavenumber_is_neumann_laplacian():
     # k = 0: the Sommerfeld condition becomes du/dn = 0, so constants are in
     # the kernel (row sums vanish) and the matrix is real, symmetric and
