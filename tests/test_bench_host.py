@@ -84,3 +84,32 @@ def test_workload_config_names_the_outer_loop_and_transfer(monkeypatch):
     bench, a = _args(["--transfer", "linear"], monkeypatch)
     c = bench.workload_config(a)
     assert c["outer"] == "stand-alone cycle iteration" and "linear" in c["transfer"]
+
+
+def test_step_traffic_only_for_the_captured_sources(monkeypatch, tmp_path):
+    """roofline.traffic comes from the committed ncu record only while the
+    kernel sources it hashes are unchanged, and only for the captured
+    workload (n = 1024, cycle precision complex64, FGMRES restart length m)."""
+    import json
+    import shutil
+    bench, a = _args([], monkeypatch)
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic_gmres_step_level0.json")))
+    assert bench.step_traffic(a, 4) == rec["dram_bytes_per_rhs"] * a.batch
+    bench, a64 = _args(["--precision", "fp64"], monkeypatch)
+    assert bench.step_traffic(a64, 4) is None
+    bench, a5 = _args(["--krylov", "20", "--smoother", "jacobi", "--nu", "1"], monkeypatch)
+    fg = json.load(open(os.path.join(ROOT, "profiles", "traffic_fgmres_step_level0.json")))
+    assert fg["m"] == 20 and bench.step_traffic(a5, 5) == fg["dram_bytes_per_rhs"] * a5.batch
+    bench, a10 = _args(["--krylov", "10"], monkeypatch)
+    assert bench.step_traffic(a10, 5) is None      # captured with m = 20
+    # a copy of the tree in which one hashed source differs by a byte
+    for d in ("profiles",):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d)
+    for f in rec["sources"]:
+        os.makedirs(tmp_path / os.path.dirname(f), exist_ok=True)
+        shutil.copy(os.path.join(ROOT, f), tmp_path / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.step_traffic(a, 4) == rec["dram_bytes_per_rhs"] * a.batch
+    with open(tmp_path / rec["sources"][0], "a") as fh:
+        fh.write("\n")
+    assert bench.step_traffic(a, 4) is None
