@@ -28,6 +28,7 @@ class CycleOptions:
     nu_pre: int = 1
     nu_post: int = 1
     omega: float = 4.5        # X = omega * diag(A), Sec. 3 / Sec. 5
+    fine_diag: str = "A"      # "C": fine-level Jacobi with X = omega diag(C) (an alternative reading)
 
 
 def mg_cycle(H, l, x, b, opt):
@@ -35,7 +36,8 @@ def mg_cycle(H, l, x, b, opt):
     A = H.A[l]
     if l == H.nlevels - 1:
         return hierarchy.coarsest_solve(H, b)
-    x = smoothers.smooth(A, x, b, opt.smoother, opt.nu_pre, opt.omega)
+    d = H.C0.diagonal() if (l == 0 and opt.fine_diag == "C") else None
+    x = smoothers.smooth(A, x, b, opt.smoother, opt.nu_pre, opt.omega, d)
     r = b - A @ x
     rc = H.R[l] @ r
     if l + 1 == H.nlevels - 1:
@@ -45,7 +47,7 @@ def mg_cycle(H, l, x, b, opt):
         for _ in range(opt.gamma):
             ec = mg_cycle(H, l + 1, ec, rc, opt)
     x = x + H.P[l] @ ec
-    x = smoothers.smooth(A, x, b, opt.smoother, opt.nu_post, opt.omega)
+    x = smoothers.smooth(A, x, b, opt.smoother, opt.nu_post, opt.omega, d)
     return x
 
 
@@ -61,20 +63,24 @@ class SolveResult:
 
 
 def mg_solve(H, b, tol, opt, max_cycles=10000, x0=None, keep_iterates=False,
-             diverge_at=1e6):
-    """Repeat cycles from x0 (default 0) until ||b - A x|| / ||b|| <= tol."""
+             diverge_at=1e6, norm_w=None):
+    """Repeat cycles from x0 (default 0) until ||b - A x|| / ||b|| <= tol.
+    ``norm_w`` (an alternative reading of the stopping test): the norms are
+    taken of the residual and of b divided node by node by these weights,
+    e.g. the boundary row weights, to test the unscaled rows' residual."""
     A = H.A[0]
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
-    nb = np.linalg.norm(b)
+    wn = (lambda v: np.linalg.norm(v)) if norm_w is None else (lambda v: np.linalg.norm(v / norm_w))
+    nb = wn(b)
     if nb == 0.0:
         return SolveResult(np.zeros_like(b), 0, 0.0, [], [], True, False)
     hist, its = [], []
-    relres = np.linalg.norm(b - A @ x) / nb
+    relres = wn(b - A @ x) / nb
     if relres <= tol:
         return SolveResult(x, 0, relres, hist, its, True, False)
     for c in range(1, max_cycles + 1):
         x = mg_cycle(H, 0, x, b, opt)
-        relres = np.linalg.norm(b - A @ x) / nb
+        relres = wn(b - A @ x) / nb
         hist.append(relres)
         if keep_iterates:
             its.append(x.copy())

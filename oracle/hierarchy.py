@@ -23,17 +23,20 @@ import scipy.linalg as sla
 from . import problem, transfer
 
 
-def level_sizes(nx, ny, levels=0, min_coarse=10):
+def level_sizes(nx, ny, levels=0, min_coarse=10, grid="vertex"):
     """Interval counts [(nx_0, ny_0), (nx_1, ny_1), ...] of the hierarchy.
 
     ``levels = 0`` coarsens as far as the rule allows (Sec. 5); a positive
-    value caps the number of levels (1 = direct solve only)."""
+    value caps the number of levels (1 = direct solve only).  ``grid``
+    ("vertex" or "interior") says whether the boundary nodes are unknowns,
+    which changes the unknown count the rule tests."""
     sizes = [(nx, ny)]
+    nodes = (lambda a, b: (a + 1) * (b + 1)) if grid == "vertex" else (lambda a, b: (a - 1) * (b - 1))
     while True:
         cx, cy = sizes[-1]
         if levels and len(sizes) >= levels:
             break
-        if cx % 2 or cy % 2 or (cx + 1) * (cy + 1) < min_coarse:
+        if cx % 2 or cy % 2 or nodes(cx, cy) < min_coarse:
             break
         sizes.append((cx // 2, cy // 2))
     return sizes
@@ -55,17 +58,33 @@ class Hierarchy:
 
 
 def build_hierarchy(nx, ny, h, k, beta2, levels=0, kind="bezier", edge="zero",
-                    min_coarse=10):
-    """All operators of the cycle.  ``k`` scalar (MP 2-A) or field (MP 2-B)."""
-    sizes = level_sizes(nx, ny, levels, min_coarse)
+                    min_coarse=10, rows="scaled", grid="vertex"):
+    """All operators of the cycle.  ``k`` scalar (MP 2-A) or field (MP 2-B).
+
+    ``rows`` and ``grid`` select alternative readings of the discretisation,
+    kept to compare their cycle counts with the paper's tables: ``rows`` is
+    passed to ``problem.helmholtz_matrix``; ``grid="interior"`` takes only the
+    interior nodes as unknowns (``problem.helmholtz_matrix_interior``) with
+    the transfers of Eq. (xex) restricted to them (a boundary value of a
+    coarse correction is zero)."""
+    sizes = level_sizes(nx, ny, levels, min_coarse, grid)
     H = Hierarchy(sizes=sizes, h=h)
-    H.A.append(problem.helmholtz_matrix(nx, ny, h, k, 0.0))
+    if grid == "interior":
+        op = lambda b2: problem.helmholtz_matrix_interior(nx, ny, h, k, b2)
+    elif grid == "vertex":
+        op = lambda b2: problem.helmholtz_matrix(nx, ny, h, k, b2, rows)
+    else:
+        raise ValueError(grid)
+    H.A.append(op(0.0))
     if len(sizes) > 1:
-        H.C0 = problem.helmholtz_matrix(nx, ny, h, k, beta2)
+        H.C0 = op(beta2)
     for l in range(len(sizes) - 1):
         fx, fy = sizes[l]
         P = transfer.prolongation(fx, fy, kind, edge)
         R = transfer.restriction(fx, fy, kind, edge)
+        if grid == "interior":
+            P = interior_block(P, fx, fy)
+            R = interior_block(R.T.tocsr(), fx, fy).T.tocsr()
         Af = H.C0 if l == 0 else H.A[l]
         Ac = (R @ Af @ P).tocsr()
         Ac.sum_duplicates()
@@ -74,6 +93,15 @@ def build_hierarchy(nx, ny, h, k, beta2, levels=0, kind="bezier", edge="zero",
         H.A.append(Ac)
     H.lu = sla.lu_factor(H.A[-1].toarray())
     return H
+
+
+def interior_block(P, fx, fy):
+    """Rows and columns of a vertex-grid prolongation (fine (fx+1)(fy+1) x
+    coarse (fx/2+1)(fy/2+1)) that belong to interior nodes of both grids."""
+    def inner(nx, ny):
+        j, i = np.meshgrid(np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+        return ((i > 0) & (i < nx) & (j > 0) & (j < ny)).ravel()
+    return P.tocsr()[inner(fx, fy)][:, inner(fx // 2, fy // 2)].tocsr()
 
 
 def coarsest_solve(H, r):

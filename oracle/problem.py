@@ -43,14 +43,25 @@ def _k_field(nx, ny, k):
     return k
 
 
-def helmholtz_matrix(nx, ny, h, k, beta2=0.0):
+def helmholtz_matrix(nx, ny, h, k, beta2=0.0, rows="scaled"):
     """Sparse (CSR, complex128) matrix of -Lap_h - (1 + i beta2) k^2 with
     ghost-eliminated Sommerfeld rows scaled by 1/2 (edge) and 1/4 (corner).
 
     ``beta2 = 0`` gives the Helmholtz operator A of MP 2-A / MP 2-B (Sec. 2);
     ``beta2 > 0`` gives the CSL operator C used for coarsening (Sec. 4, Sec. 5).
     ``k`` is a scalar (MP 2-A) or an (ny+1, nx+1) array (MP 2-B).
+
+    ``rows`` selects the reading of the boundary rows (the paper names only
+    "second-order finite differences"): "scaled" (the default above),
+    "unscaled" (the same ghost-eliminated rows without the 1/2, 1/4 factors;
+    not symmetric), or "bc1" (``helmholtz_matrix_bc1``: the boundary rows are
+    the first-order one-sided absorbing condition itself).
     """
+    if rows == "bc1":
+        return helmholtz_matrix_bc1(nx, ny, h, k, beta2)
+    if rows not in ("scaled", "unscaled"):
+        raise ValueError(rows)
+    scaled = rows == "scaled"
     kf = _k_field(nx, ny, k)
     N = (nx + 1) * (ny + 1)
     inv_h2 = 1.0 / (h * h)
@@ -88,9 +99,77 @@ def helmholtz_matrix(nx, ny, h, k, beta2=0.0):
         shape=(N, N),
     ).tocsr()
     A.sum_duplicates()
+    if not scaled:
+        return A
     # row scaling 1/2 per boundary direction
     w = boundary_weights(nx, ny).ravel()
     return (sp.diags(w) @ A).tocsr()
+
+
+def helmholtz_matrix_bc1(nx, ny, h, k, beta2=0.0):
+    """Alternative reading of the boundary rows (kept for the comparison of
+    readings): interior nodes carry the 5-point rows of -Lap_h - (1 + i
+    beta2) k^2, and each boundary node carries the first-order one-sided
+    difference of the absorbing condition along its outward normal,
+    ((u_P - u_in)/h - i k u_P) / h = 0 (a corner sums its two normals).  The
+    matrix is not symmetric."""
+    kf = _k_field(nx, ny, k)
+    N = (nx + 1) * (ny + 1)
+    rows, cols, vals = [], [], []
+    for j in range(ny + 1):
+        for i in range(nx + 1):
+            p = node_index(nx, i, j)
+            kk = kf[j, i]
+            if 0 < i < nx and 0 < j < ny:
+                rows.append(p)
+                cols.append(p)
+                vals.append(4.0 / h**2 - (1 + 1j * beta2) * kk**2)
+                for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                    rows.append(p)
+                    cols.append(node_index(nx, i + di, j + dj))
+                    vals.append(-1.0 / h**2)
+                continue
+            for on, (qi, qj) in ((i == 0, (1, j)), (i == nx, (nx - 1, j)), (j == 0, (i, 1)), (j == ny, (i, ny - 1))):
+                if on:
+                    rows += [p, p]
+                    cols += [p, node_index(nx, qi, qj)]
+                    vals += [(1.0 / h - 1j * kk) / h, -1.0 / h**2]
+    A = sp.coo_matrix((vals, (rows, cols)), shape=(N, N), dtype=np.complex128).tocsr()
+    A.sum_duplicates()
+    return A
+
+
+def helmholtz_matrix_interior(nx, ny, h, k, beta2=0.0):
+    """Alternative reading of the unknowns (kept for the comparison of
+    readings): only the interior nodes are unknowns, (nx-1)*(ny-1) of them,
+    row-major over i = 1..nx-1, j = 1..ny-1.  A boundary node is eliminated
+    with the first-order one-sided absorbing condition
+    (u_in - u_B)/h = i k u_B, i.e. u_B = u_in / (1 - i k h), which adds
+    -1/(h^2 (1 - i k h)) to the diagonal of each interior row next to the
+    boundary (once per boundary neighbour).  ``k`` is a scalar or an
+    (ny+1, nx+1) field (the boundary node's k is used)."""
+    kf = _k_field(nx, ny, k)
+    mx, my = nx - 1, ny - 1
+    N = mx * my
+    rows, cols, vals = [], [], []
+    for j in range(1, ny):
+        for i in range(1, nx):
+            p = (j - 1) * mx + (i - 1)
+            d = 4.0 / h**2 - (1 + 1j * beta2) * kf[j, i] ** 2
+            for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                qi, qj = i + di, j + dj
+                if 0 < qi < nx and 0 < qj < ny:
+                    rows.append(p)
+                    cols.append((qj - 1) * mx + (qi - 1))
+                    vals.append(-1.0 / h**2)
+                else:
+                    d -= 1.0 / (h**2 * (1.0 - 1j * kf[qj, qi] * h))
+            rows.append(p)
+            cols.append(p)
+            vals.append(d)
+    A = sp.coo_matrix((vals, (rows, cols)), shape=(N, N), dtype=np.complex128).tocsr()
+    A.sum_duplicates()
+    return A
 
 
 def boundary_weights(nx, ny):

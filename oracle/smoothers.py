@@ -15,9 +15,11 @@ ends early when the new Arnoldi vector vanishes (h_{j+1,j} <= 1e-14 beta).
 import numpy as np
 
 
-def jacobi(A, x, b, omega, nu):
-    """``nu`` weighted-Jacobi sweeps x <- x + (omega diag A)^{-1} (b - A x)."""
-    X = omega * A.diagonal()
+def jacobi(A, x, b, omega, nu, diag=None):
+    """``nu`` weighted-Jacobi sweeps x <- x + (omega diag A)^{-1} (b - A x).
+    ``diag`` replaces diag A in X (an alternative reading kept for the
+    comparison of readings: the diagonal of the shifted operator)."""
+    X = omega * (A.diagonal() if diag is None else diag)
     for _ in range(nu):
         x = x + (b - A @ x) / X
     return x
@@ -57,11 +59,11 @@ def gmres(A, x, b, nu, m=3):
     return x
 
 
-def smooth(A, x, b, kind, nu, omega):
+def smooth(A, x, b, kind, nu, omega, diag=None):
     if nu <= 0:
         return x
     if kind == "jacobi":
-        return jacobi(A, x, b, omega, nu)
+        return jacobi(A, x, b, omega, nu, diag)
     if kind == "gmres3":
         return gmres(A, x, b, nu, 3)
     raise ValueError(kind)

@@ -213,10 +213,25 @@ def mg_residual_norm_static(nx, ny, h, k, x, b, out, stream=None):
     """out[0] = ||b - A x||, out[1] = ||b|| on the device, without any device
     allocation by the library (see include/helmmg.h).  ``k``: float or a
     float64 CUDA tensor (ny+1, nx+1); x, b: complex128 CUDA grids; out: a
-    float64 CUDA tensor of 2 entries."""
+    float64 CUDA tensor of 2 entries.  Every tensor must sit on the current
+    CUDA device; the call is enqueued on ``stream`` (default: torch's current
+    stream).  The C side cannot see tensor sizes, so they are checked here:
+    an undersized tensor would otherwise become an out-of-bounds access."""
     import torch
+    nodes = (int(nx) + 1) * (int(ny) + 1)
+    dev = torch.cuda.current_device()
+    named = [("x", x, nodes), ("b", b, nodes), ("out", out, 2)]
+    if not isinstance(k, (int, float)):
+        named.append(("k", k, nodes))
+    for name, t, need in named:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA torch tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if (t.numel() != need) if name != "out" else (t.numel() < need):
+            raise ValueError(f"{name} has {t.numel()} elements, needs {need}")
     kp, kc = (None, float(k)) if isinstance(k, (int, float)) else (_ptr(k, torch.float64, "k"), 0.0)
-    st = stream.cuda_stream if stream is not None else None
+    st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
     _check(load_library().mg_residual_norm_static(int(nx), int(ny), float(h), kp, kc, _ptr(x, torch.complex128, "x"),
                                                   _ptr(b, torch.complex128, "b"), _ptr(out, torch.float64, "out"),
                                                   ctypes.c_void_p(st)))

@@ -1,9 +1,12 @@
 """Variable-k workload: the seeded layered velocity model that stands in
 for the 9.2 km x 3.0 km benchmark model, at 10 Hz (h = v_min / (10 f),
-grid rounded up to 640 x 224 cells), source near the top centre."""
+grid rounded up to 640 x 224 cells), source near the top centre.  The mixed
+paths meet the tolerance in the oracle's FP64 residual; the FP64 path takes
+one cycle from the oracle's iterate to the oracle's next iterate to 1e-10."""
 import numpy as np
 import pytest
 
+import parity_util as pu
 import synth
 from oracle import cycle as ocycle
 from oracle import hierarchy as ohier
@@ -41,11 +44,16 @@ def test_layered_model_mixed_and_fp64():
         r = b.ravel() - A @ x.cpu().numpy().ravel()
         assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-6
         s.close()
-    s64 = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, max_cycles=3)
+    # FP64: one cycle from the oracle's iterate equals the oracle's next
+    # iterate to 1e-10 node by node (boundary ring included), cycles 1..3
     H = ohier.build_hierarchy(nx, nz, h, k, beta2)
-    ref = ocycle.mg_solve(H, b.ravel(), 1e-6, ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5), max_cycles=3)
-    x64, st64, c64, _ = s64.solve(bd, tol=1e-6)
-    assert c64[0] == ref.cycles == 3
-    xv = x64.cpu().numpy().ravel()
-    assert np.linalg.norm(xv - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    ref = ocycle.mg_solve(H, b.ravel(), 1e-300, ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5), max_cycles=3,
+                          keep_iterates=True)
+    s64 = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, max_cycles=1)
+    shape = (nz + 1, nx + 1)
+    for m in (1, 2, 3):
+        x0 = np.zeros_like(b) if m == 1 else ref.iterates[m - 2].reshape(shape)
+        xm, st1, cm, _ = s64.solve(bd, x=torch.from_numpy(x0).cuda()[None].contiguous(), tol=1e-300)
+        assert cm[0] == 1
+        pu.assert_close(xm.cpu().numpy()[0], ref.iterates[m - 1].reshape(shape), 1e-10, shape, f"cycle {m}")
     s64.close()

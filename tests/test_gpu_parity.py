@@ -4,10 +4,13 @@ Bars: FP64 operators and Galerkin stencils to 1e-13 relative (max norm),
 FP64 iterates to 1e-10 relative at every checked cycle with identical cycle
 counts, the mixed path to 1e-6 relative of the FP64 oracle solution.
 """
+import functools
+
 import numpy as np
 import pytest
 
 import synth
+import parity_util as pu
 from oracle import cycle as ocycle
 from oracle import gradient as ograd
 from oracle import hierarchy as ohier
@@ -31,7 +34,8 @@ def host(t):
 
 
 def rel(a, b):
-    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+    """Larger of the 2-norm and the node-wise relative difference."""
+    return max(pu.rel2(a, b), pu.relmax(a, b))
 
 
 def opts(smoother):
@@ -69,16 +73,7 @@ def _oracle_run(nx, ny, h, k, beta2, opt, b, tol, keep=True, levels=0, max_cycle
     return ocycle.mg_solve(H, b.ravel(), tol, opt, keep_iterates=keep, max_cycles=max_cycles)
 
 
-CASES = [
-    # (name, nx, ny, k, beta2, smoother, gamma, nu_pre, nu_post, tol)
-    ("cfg1_jacobi_V11", 32, 32, 20.0, 0.7, "jacobi", 1, 1, 1, 1e-6),
-    ("jacobi_W22", 32, 32, 20.0, 0.7, "jacobi", 2, 2, 2, 1e-6),
-    ("jacobi_V21_odd", 40, 40, 25.0, 0.7, "jacobi", 1, 2, 1, 1e-6),
-    ("gmres_V11_shift1k", 64, 64, 40.0, 1 / 40.0, "gmres3", 1, 1, 1, 1e-6),
-    ("gmres_W22", 48, 48, 30.0, 1 / 30.0, "gmres3", 2, 2, 2, 1e-8),
-    ("gmres_V11_shift0", 32, 32, 20.0, 0.0, "gmres3", 1, 1, 1, 1e-6),
-    ("rect_jacobi", 56, 24, 20.0, 0.7, "jacobi", 1, 2, 2, 1e-6),
-]
+CASES = pu.CASES
 
 
 # execution modes: every level as grid-wide kernels; the library default
@@ -93,29 +88,49 @@ COARSE = [dict(coarse_nodes=0), dict(), dict(coarse_nodes=1200, coarse_mode=1),
 COARSE_IDS = ["grid", "default", "hybrid", "cta", "coop", "grid_unfused", "grid_march"]
 
 
-@pytest.mark.parametrize("cn", COARSE, ids=COARSE_IDS)
-@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_fp64_iterates_and_cycle_counts(case, cn):
-    """Jacobi cycles are a fixed affine map, so whole-solve iterates must agree
-    to 1e-10.  GMRES(3)-smoothed cycles are a nonlinear map that amplifies
-    rounding differences (the oracle's own MGS and Gram-matrix MGS forms
-    drift apart to ~1e-8 by cycle 12 on these grids), so for GMRES the 1e-10
-    bar applies to one cycle started from the oracle's previous iterate, and
-    whole-solve iterates are compared at 1e-6."""
+@functools.lru_cache(maxsize=None)
+def _reference(case):
+    """The oracle's solve of a case, and for GMRES(3) the whole-solve bars
+    derived from the spread between the oracle's MGS and Gram-form steps."""
     name, nx, ny, k, beta2, sm, gamma, n1, n2, tol = case
     h = 1.0 / max(nx, ny)
     b = synth.point_source(nx, ny, h)
     opt = ocycle.CycleOptions(gamma, sm, n1, n2, 4.5)
-    ref = _oracle_run(nx, ny, h, k, beta2, opt, b, tol)
+    H = ohier.build_hierarchy(nx, ny, h, k, beta2)
+    ref = ocycle.mg_solve(H, b.ravel(), tol, opt, keep_iterates=True)
     assert ref.converged
-    whole = 1e-10 if sm == "jacobi" else 1e-6
+    if sm == "jacobi":
+        bars = (1e-10, 1e-9)
+    else:
+        bars = pu.whole_solve_bars(*pu.gram_spread(H, b.ravel(), tol, opt, ref))
+    return b, ref, bars
+
+
+@pytest.mark.parametrize("cn", COARSE, ids=COARSE_IDS)
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp64_iterates_and_cycle_counts(case, cn):
+    """Jacobi cycles are a fixed affine map, so whole-solve iterates must agree
+    to 1e-10 node by node (boundary ring included) and the residual
+    histories to 1e-9.  GMRES(3)-smoothed cycles are a nonlinear map that
+    amplifies rounding differences: the oracle's own MGS and its Gram-matrix
+    form (the CUDA path's), or either on b scaled by 1 + a few ulp, drift
+    apart by up to ~2e-7 mid-solve on gmres_V11_shift1k
+    (tests/test_gmres_drift.py).  For GMRES the 1e-10 bar therefore applies
+    to one cycle started from the oracle's previous iterate, and the whole
+    solve is held to 10x the largest spread between the oracle and those
+    variants on the same case (floored at 1e-10 / 1e-9, capped at 1e-6 /
+    1e-2).  Cycle counts are identical in every case."""
+    name, nx, ny, k, beta2, sm, gamma, n1, n2, tol = case
+    h = 1.0 / max(nx, ny)
+    b, ref, (whole, hist_rtol) = _reference(case)
+    shape = (ny + 1, nx + 1)
     s = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, **cn)
     x, st, cyc, rr = s.solve(dev(b), tol=tol)
     assert st == hm.MG_OK
     assert cyc[0] == ref.cycles
-    assert rel(host(x)[0], ref.x) <= whole
+    pu.assert_close(host(x)[0], ref.x.reshape(shape), whole, shape, "whole solve")
     hist = np.array(s.history(ref.cycles)[0])
-    assert np.allclose(hist, ref.history, rtol=1e-9 if sm == "jacobi" else 1e-3, atol=0)
+    assert np.allclose(hist, ref.history, rtol=hist_rtol, atol=0)
     s.close()
     # one cycle from the same input iterate, at several points of the solve
     s1 = hm.Solver(nx, ny, h, k, beta2, cycle=gamma, smoother=sm, nu_pre=n1, nu_post=n2, max_cycles=1, **cn)
@@ -123,7 +138,7 @@ def test_fp64_iterates_and_cycle_counts(case, cn):
         x0 = np.zeros_like(b) if m == 1 else ref.iterates[m - 2].reshape(b.shape)
         xm, st1, cm, _ = s1.solve(dev(b), x=dev(x0)[None].contiguous(), tol=1e-300)
         assert st1 == hm.MG_EMAXIT and cm[0] == 1
-        assert rel(host(xm)[0], ref.iterates[m - 1]) <= 1e-10, m
+        pu.assert_close(host(xm)[0], ref.iterates[m - 1].reshape(shape), 1e-10, shape, f"one cycle {m}")
     s1.close()
 
 
@@ -141,14 +156,14 @@ def test_variable_k_iterates():
     s1 = hm.Solver(nx, ny, h, dev(k, torch.float64), 1 / 25.0, smoother="gmres3", max_cycles=1)
     x0 = ref.iterates[ref.cycles // 2 - 1].reshape(b.shape)
     xm, _, _, _ = s1.solve(dev(b), x=dev(x0)[None].contiguous(), tol=1e-300)
-    assert rel(host(xm)[0], ref.iterates[ref.cycles // 2]) <= 1e-10
+    pu.assert_close(host(xm)[0], ref.iterates[ref.cycles // 2], 1e-10, (ny + 1, nx + 1), "variable k, one cycle")
     # Jacobi on the same variable-k problem: whole-solve iterates at 1e-10
     optj = ocycle.CycleOptions(1, "jacobi", 2, 2, 4.5)
     refj = _oracle_run(nx, ny, h, k, 0.7, optj, b, 1e-6)
     sj = hm.Solver(nx, ny, h, dev(k, torch.float64), 0.7, nu_pre=2, nu_post=2)
     x, st, cyc, _ = sj.solve(dev(b), tol=1e-6)
     assert st == hm.MG_OK and cyc[0] == refj.cycles
-    assert rel(host(x)[0], refj.x) <= 1e-10
+    pu.assert_close(host(x)[0], refj.x, 1e-10, (ny + 1, nx + 1), "variable k, Jacobi whole solve")
 
 
 @pytest.mark.parametrize("cn", COARSE, ids=COARSE_IDS)
@@ -165,7 +180,7 @@ def test_batch_each_rhs_matches_oracle(cn):
     assert st == hm.MG_OK
     for q in range(3):
         assert cyc[q] == refs[q].cycles
-        assert rel(host(x)[q], refs[q].x) <= 1e-10
+        pu.assert_close(host(x)[q], refs[q].x, 1e-10, (ny + 1, nx + 1), f"rhs {q}")
 
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed-ff"])
@@ -287,7 +302,7 @@ def test_interior_row_march_path_on_a_larger_grid():
             x0 = np.zeros_like(b) if m == 1 else ref.iterates[m - 2].reshape(b.shape)
             xm, st1, cm, _ = s1.solve(dev(b), x=dev(x0)[None].contiguous(), tol=1e-300)
             assert cm[0] == 1
-            assert rel(host(xm)[0], ref.iterates[m - 1]) <= 1e-10, (march, m)
+            pu.assert_close(host(xm)[0], ref.iterates[m - 1], 1e-10, (n + 1, n + 1), f"march {march}, cycle {m}")
         s1.close()
     A = oprob.helmholtz_matrix(n, n, h, k)
     for precision in ("mixed", "mixed-ff"):
