@@ -50,8 +50,16 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-6)
     p.add_argument("--no-fp64-line", action="store_true", help="skip the FP64 comparison solve")
     p.add_argument("--no-ff-line", action="store_true", help="skip the float-float outer-loop variant")
-    p.add_argument("--cpu-sample-cycles", type=int, default=2)
-    p.add_argument("--workload", default="batched", choices=["batched", "layered", "ragged", "gradient", "two-grid"],
+    p.add_argument("--cpu-sample-cycles", type=int, default=10,
+                   help="oracle cycles of the one-core CPU baseline (0: no CPU baseline)")
+    p.add_argument("--cpu-allcore-cycles", type=int, default=4,
+                   help="oracle cycles per host core of the all-core CPU baseline (batched workloads)")
+    p.add_argument("--no-error-vs-oracle", action="store_true",
+                   help="skip the oracle's solve of the first right-hand side (error against the FP64 oracle)")
+    p.add_argument("--error-max-cycles", type=int, default=100,
+                   help="run the oracle's solve for error_vs_oracle only when it needs at most this many cycles")
+    p.add_argument("--workload", default="batched",
+                   choices=["batched", "layered", "ragged", "gradient", "two-grid", "sweep"],
                    help="batched: the bench line (default); the others print one JSON line for the other "
                         "workloads: layered velocity model at --freq Hz, a ragged batch of 32 problems, the "
                         "adjoint gradient of a receiver misfit")
@@ -171,13 +179,9 @@ def oracle_cycle_seconds(a, ncycles):  # noqa: D401
     """Time ``ncycles`` oracle cycles on the full workload (setup excluded);
     with --krylov, ``ncycles`` FGMRES steps (each one preconditioning cycle
     plus its Arnoldi work) of one restart cycle."""
-    import synth
     from oracle import cycle as oc
-    from oracle import hierarchy as oh
-    h = 1.0 / a.n
-    b = (synth.source_row(a.n, a.n, h, a.batch)[0] if a.batch > 1 else synth.point_source(a.n, a.n, h)).ravel()
-    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2, kind=a.transfer)
-    opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
+    b = _oracle_rhs0(a)
+    H, opt = _oracle_setup(a)
     x = np.zeros_like(b)
     if a.krylov:
         from oracle import krylov as okr
@@ -254,12 +258,86 @@ def _cycles_from_cache(a):
 # ------------------------------------------------------------------ GPU arm
 
 
+# FP64 flops per node of one GMRES(3) smoothing step as the method states it
+# (Sec. 5.3; counted on an interior node with complex arithmetic: add 2, real
+# scale 2, conjugated multiply-accumulate 8, |z|^2 accumulate 4): initial
+# residual 14, its norm and scaling 6; Arnoldi step j = 0, 1, 2: apply 12,
+# j + 1 inner products and updates 16 each, norm 4, scaling 2 (none after the
+# last): 34, 50, 64; update of x by three basis vectors 24.  Total 192.
+GMRES_STEP_FLOPS_PER_NODE = 192.0
+
+
+def _oracle_rhs0(a):
+    import synth
+    h = 1.0 / a.n
+    return (synth.source_row(a.n, a.n, h, a.batch)[0] if a.batch > 1 else synth.point_source(a.n, a.n, h)).ravel()
+
+
+def _oracle_setup(a):
+    from oracle import cycle as oc
+    from oracle import hierarchy as oh
+    H = oh.build_hierarchy(a.n, a.n, 1.0 / a.n, a.k, a.beta2, kind=a.transfer)
+    opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
+    return H, opt
+
+
+def _oracle_solution_job(a):
+    """The oracle's solve of the workload's first right-hand side to the
+    bench tolerance (run in a spawned process beside the GPU work)."""
+    from oracle import cycle as oc
+    b = _oracle_rhs0(a)
+    H, opt = _oracle_setup(a)
+    t0 = time.perf_counter()
+    if a.krylov:
+        from oracle import krylov as okr
+        r = okr.fgmres_solve(H, b, a.tol, opt, a.krylov)
+    else:
+        r = oc.mg_solve(H, b, a.tol, opt)
+    return r.x, r.cycles, float(r.relres), bool(r.converged), time.perf_counter() - t0
+
+
+def _oracle_cycles_job(args):
+    """Per-cycle seconds of the oracle on right-hand side ``q`` of the
+    workload (one process per host core for the all-core figure)."""
+    a, q, ncycles = args
+    import synth
+    from oracle import cycle as oc
+    h = 1.0 / a.n
+    src = synth.source_row(a.n, a.n, h, a.batch) if a.batch > 1 else synth.point_source(a.n, a.n, h)[None]
+    b = src[q % len(src)].ravel()
+    H, opt = _oracle_setup(a)
+    x = np.zeros_like(b)
+    t0 = time.perf_counter()
+    for _ in range(ncycles):
+        x = oc.mg_cycle(H, 0, x, b, opt)
+        _ = np.linalg.norm(b - H.A[0] @ x)     # the per-cycle stopping test
+    return (time.perf_counter() - t0) / ncycles
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def run_ours(a):
+    import multiprocessing as mp
+    rank, world, local = dist_env()
+    # the oracle's solution of the first right-hand side, for the error
+    # against the FP64 oracle, runs in a process spawned before any GPU call
+    cyc_oracle = _cycles_from_cache(a)
+    pool, sol_job = None, None
+    want_error = rank == 0 and world == 1 and not a.no_error_vs_oracle and cyc_oracle is not None and \
+        cyc_oracle <= a.error_max_cycles
+    if want_error:
+        pool = mp.get_context("spawn").Pool(1)
+        sol_job = pool.apply_async(_oracle_solution_job, (a,))
+
     import torch
     import paper_2308_13476_gb300 as hm
     import synth
 
-    rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -277,6 +355,9 @@ def run_ours(a):
         rhs_np = synth.point_source(n, n, h)[None].copy()
     rhs = torch.from_numpy(rhs_np).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # the library runs on its own stream; every CUDA event of the timings is
+    # recorded on that stream (the launching stream)
+    S = torch.cuda.Stream(device=dev)
 
     tuned = {}
     if not a.no_autotune:   # launch shapes from the autotuner (cached per GPU and problem shape)
@@ -289,38 +370,86 @@ def run_ours(a):
         t0 = time.perf_counter()
         s = hm.Solver(n, n, h, k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
                       precision=precision, batch=a.batch, max_cycles=20000, march=a.march, krylov=a.krylov,
-                      transfer=a.transfer, **(shapes or {}))
+                      transfer=a.transfer, stream=S, **(shapes or {}))
         torch.cuda.synchronize()
         return s, time.perf_counter() - t0
 
-    def timed_solves(s, steps, e2e=False):
+    def timed_solves(s, steps):
         st_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         en_ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         cyc = None
         launches = 0
-        host_in = torch.from_numpy(rhs_np).pin_memory() if e2e else None
-        host_out = torch.empty((a.batch, n + 1, n + 1), dtype=torch.complex128).pin_memory() if e2e else None
-        # the device input buffer is allocated once, as a serving loop reuses it
-        # (a fresh 1 GB allocation inside the timed region costs tens of ms)
-        r_dev = torch.empty_like(rhs) if e2e else None
+        x = None
         for q in range(steps):
             flush.zero_()
             x = torch.zeros_like(rhs)
             torch.cuda.synchronize()
-            st_ev[q].record()
-            if e2e:
-                r_dev.copy_(host_in, non_blocking=True)
-                x, status, cyc, rr = s.solve(r_dev, x=x, tol=a.tol)
-                host_out.copy_(x, non_blocking=True)
-            else:
-                x, status, cyc, rr = s.solve(rhs, x=x, tol=a.tol)
-            en_ev[q].record()
+            st_ev[q].record(S)
+            x, status, cyc, rr = s.solve(rhs, x=x, tol=a.tol)
+            en_ev[q].record(S)
             torch.cuda.synchronize()
             if status != hm.MG_OK:
                 raise RuntimeError(f"solve failed: {hm.STATUS_NAMES[status]} cycles={cyc} relres={rr}")
             launches += s.counters()[0]
         ms = [st_ev[q].elapsed_time(en_ev[q]) for q in range(steps)]
-        return ms, cyc, launches, rr
+        return ms, cyc, launches, rr, x
+
+    def e2e_pipelined(s, steps):
+        """End to end through the public API with host buffers: every step
+        copies its right-hand sides from pinned host memory and reads its
+        solution back, on a copy stream, double-buffered so that the copies
+        of neighbouring steps overlap the solve (as a serving loop does).
+        Timed from the first copy's start to the last copy's end."""
+        C = torch.cuda.Stream(device=dev)
+        host_in = torch.from_numpy(rhs_np).pin_memory()
+        host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+        r_dev = [torch.empty_like(rhs) for _ in range(2)]
+        x_dev = [torch.empty_like(rhs) for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(steps)]
+        ev_done = [torch.cuda.Event() for _ in range(steps)]
+        ev_out = [torch.cuda.Event() for _ in range(steps)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(C):
+            e0.record(C)
+            r_dev[0].copy_(host_in, non_blocking=True)
+            ev_in[0].record(C)
+        for q in range(steps):
+            if q + 1 < steps:   # next step's input, into the buffer step q-1 read
+                with torch.cuda.stream(C):
+                    if q >= 1:
+                        C.wait_event(ev_done[q - 1])
+                    r_dev[(q + 1) % 2].copy_(host_in, non_blocking=True)
+                    ev_in[q + 1].record(C)
+            S.wait_event(ev_in[q])
+            if q >= 2:          # x buffer of step q-2 read back
+                S.wait_event(ev_out[q - 2])
+            with torch.cuda.stream(S):
+                x_dev[q % 2].zero_()
+            x, status, cyc, rr = s.solve(r_dev[q % 2], x=x_dev[q % 2], tol=a.tol)
+            ev_done[q].record(S)
+            if status != hm.MG_OK:
+                raise RuntimeError(f"solve failed: {hm.STATUS_NAMES[status]}")
+            with torch.cuda.stream(C):
+                C.wait_event(ev_done[q])
+                host_out[q % 2].copy_(x_dev[q % 2], non_blocking=True)
+                ev_out[q].record(C)
+        with torch.cuda.stream(C):
+            e1.record(C)
+        torch.cuda.synchronize()
+        # the copy bandwidths on their own (not overlapped), one copy each way
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        with torch.cuda.stream(C):
+            c0.record(C)
+            r_dev[0].copy_(host_in, non_blocking=True)
+            c1.record(C)
+            host_out[0].copy_(x_dev[0], non_blocking=True)
+            c2.record(C)
+        torch.cuda.synchronize()
+        nbytes = rhs.numel() * 16
+        return e0.elapsed_time(e1), nbytes / (c0.elapsed_time(c1) * 1e-3) / 1e9, \
+            nbytes / (c1.elapsed_time(c2) * 1e-3) / 1e9
 
     s, setup_s = make(a.precision, tuned)
     timed_solves(s, a.warmup)
@@ -329,24 +458,25 @@ def run_ours(a):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    ms, cyc, launches, rr = timed_solves(s, a.steps)
+    ms, cyc, launches, rr, x_last = timed_solves(s, a.steps)
     clk = clocks.stop()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     value, tmax = job_throughput(sum(ms) / 1e3, N * a.batch * a.steps)
-    # end to end through the public API with host buffers (one untimed step
-    # first, like the device-side warm-up)
-    timed_solves(s, 1, e2e=True)
-    ms_e2e, _, _, _ = timed_solves(s, a.steps, e2e=True)
-    e2e_value, _ = job_throughput(sum(ms_e2e) / 1e3, N * a.batch * a.steps)
+    x0_gpu = x_last[0].cpu().numpy().ravel()
+    # end to end through the public API with host buffers (one untimed run first)
+    e2e_pipelined(s, 2)
+    ms_e2e, h2d_gbs, d2h_gbs = e2e_pipelined(s, a.steps)
+    e2e_value, _ = job_throughput(ms_e2e / 1e3, N * a.batch * a.steps)
     # roofline of the dominant kernel, timed live with CUDA events on the library's stream
     what = 5 if a.krylov else (0 if a.smoother == "jacobi" else 4)
     kms, kbytes = s.profile(what, 0, reps=20)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s (no measured peaks file)"
     achieved = kbytes / (kms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": step_traffic(a, what),
@@ -356,22 +486,41 @@ def run_ours(a):
                            f"{2 * a.krylov + 1} FP64 and 3 cycle-precision vector passes)"}[what]) +
                       f" ({'complex128' if a.precision == 'fp64' else 'complex64'}), "
                       f"{kbytes / 1e6:.1f} MB algorithmic per step, {kms * 1e3:.0f} us per step, "
-                      f"peak = measured hbm_gbs"}
+                      f"peak = {peak_src}"}
     extra = {"setup_s": setup_s, "cycles": cyc, "relres": rr}
     if not a.no_ff_line and a.precision == "mixed" and not a.krylov:   # float-float outer loop, same shapes
         s.close()
         sff, _ = make("mixed-ff", tuned)
         timed_solves(sff, 1)
-        msff, cycff, _, rrff = timed_solves(sff, a.steps)
+        msff, cycff, _, rrff, _ = timed_solves(sff, a.steps)
         extra["mixed_ff_path"] = {"value": N * a.batch * a.steps / (sum(msff) / 1e3), "unit": UNIT,
                                   "cycles": cycff, "max_relres": max(rrff), "ms_per_solve": sum(msff) / a.steps}
         s = sff
     if not a.no_fp64_line and a.precision in ("mixed", "mixed-ff"):
         s.close()
         s64, setup64 = make("fp64")
-        ms64, cyc64, _, _ = timed_solves(s64, 1)   # one solve (its first cycle includes the graph capture)
-        extra["fp64_path"] = {"value": N * a.batch / (ms64[0] / 1e3), "unit": UNIT, "cycles": cyc64,
-                              "ms_per_solve": ms64[0]}
+        timed_solves(s64, 1)                      # warm-up: graph capture
+        nfp = max(3, min(a.steps, 5))
+        ms64, cyc64, _, rr64, _ = timed_solves(s64, nfp)
+        fp = {"value": N * a.batch * nfp / (sum(ms64) / 1e3), "unit": UNIT, "cycles": cyc64,
+              "max_relres": max(rr64), "ms_per_solve": sum(ms64) / nfp, "solves_timed": nfp}
+        if a.smoother == "gmres3" and not a.krylov:
+            # FP64 roofline: the fine-level GMRES(3) step against the FP64 FMA
+            # rate measured in this run by the library's probe (mg_profile 6)
+            pms, pflops = s64.profile(6, 0, reps=3)
+            fp64_peak = pflops / (pms * 1e-3) / 1e12
+            sms, sbytes = s64.profile(4, 0, reps=5)
+            flops = GMRES_STEP_FLOPS_PER_NODE * N * a.batch
+            ach = flops / (sms * 1e-3) / 1e12
+            fp["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": ach / fp64_peak, "hbm_frac": sbytes / (sms * 1e-3) / 1e9 / peak,
+                              "kernel": f"level-0 GMRES(3) smoothing step (complex128), "
+                                        f"{GMRES_STEP_FLOPS_PER_NODE:g} algorithmic FP64 flops and "
+                                        f"{sbytes / (N * a.batch):g} B per node, {sms * 1e3:.0f} us per step",
+                              "peak_source": "FP64 FMA throughput probe of the library (mg_profile kind 6: 8 "
+                                             "independent FMA chains per thread, 2048 threads per SM, every SM), "
+                                             "measured in this run"}
+        extra["fp64_path"] = fp
         s64.close()
     else:
         s.close()
@@ -382,19 +531,43 @@ def run_ours(a):
         "config": dict(workload_config(a), launch_shapes=tuned or "library defaults"), "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rhs.numel() * 16),
-                "d2h_bytes_per_step": int(rhs.numel() * 16)},
+                "d2h_bytes_per_step": int(rhs.numel() * 16), "h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs,
+                "how": "double-buffered: the host-to-device copy of the next step's right-hand sides and the "
+                       "device-to-host copy of the last step's solutions run on a copy stream beside the solve; "
+                       "h2d_gbs / d2h_gbs: one 1-way copy timed on its own"},
         "roofline": roof, "extra": extra,
     }
+    if want_error:
+        xo, co, ro, ok, ts = sol_job.get()
+        pool.close()
+        pool.join()
+        line["error_vs_oracle"] = {
+            "rhs": 0, "rel_l2": float(np.linalg.norm(x0_gpu - xo) / np.linalg.norm(xo)),
+            "rel_max": float(np.abs(x0_gpu - xo).max() / np.abs(xo).max()),
+            "gpu_cycles": int(cyc[0]), "oracle_cycles": int(co), "oracle_relres": ro, "oracle_converged": ok,
+            "oracle_seconds": ts,
+            "reference": "the FP64 oracle's solve of the same right-hand side to the same tolerance"}
+    elif pool is not None:
+        pool.terminate()
     if rank == 0 and world == 1 and a.cpu_sample_cycles > 0:
-        tc = oracle_cycle_seconds(a, a.cpu_sample_cycles)
-        cyc_oracle = _cycles_from_cache(a)
         cyc_needed = cyc_oracle or max(cyc)
         src = "the oracle's" if cyc_oracle else "the GPU path's (no oracle count stored)"
-        line["cpu_baseline"] = {"value": N * a.batch / (tc * a.batch * cyc_needed), "unit": UNIT, "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"{a.cpu_sample_cycles} oracle cycles (FP64, one core) of one right-hand "
-                                          f"side of the workload, scaled to {a.batch} right-hand sides x "
-                                          f"{src} {cyc_needed} cycles of one solve"}
+        tc = oracle_cycle_seconds(a, a.cpu_sample_cycles)
+        one = N / (tc * cyc_needed)
+        cb = {"value": one, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{a.cpu_sample_cycles} oracle cycles (FP64, one core) of one right-hand side of the "
+                        f"workload, scaled to a whole solve by {src} {cyc_needed} cycles"}
+        if a.batch > 1 and not a.krylov and a.cpu_allcore_cycles > 0:
+            cores = min(_host_cores(), a.batch)
+            with mp.get_context("spawn").Pool(cores) as p2:
+                secs = p2.map(_oracle_cycles_job, [(a, q, a.cpu_allcore_cycles) for q in range(cores)])
+            allc = sum(N / (t * cyc_needed) for t in secs)
+            cb = {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+                  "sample": f"{cores} processes, one per host core, each timing {a.cpu_allcore_cycles} oracle "
+                            f"cycles (FP64) of its own right-hand side of the workload side by side; the sum of "
+                            f"their rates, each scaled to a whole solve by {src} {cyc_needed} cycles",
+                  "single_core": cb}
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -631,6 +804,53 @@ def run_gradient(a):
                       "smoother": "gmres3", "cycle": "V(2,2)", "tol": a.tol}))
 
 
+def run_sweep(a):
+    """Constant-k sweep (synth.sweep_points): wavenumber at kh = 0.625,
+    h-refinement at k = 100, smoothing steps, V and W, shifts; one centre
+    source per point, relative residual 1e-6 (cap 400 cycles), the mixed and
+    the FP64 path.  Each point: one untimed solve (graph capture), one timed
+    solve (CUDA events on the library's stream).  The oracle's count for
+    each point is read from oracle/sweep_cycles.json (written by
+    python -m oracle.sweep_cycles)."""
+    import torch
+    import paper_2308_13476_gb300 as hm
+    import synth
+    torch.cuda.set_device(0)
+    S = torch.cuda.Stream()
+    try:
+        with open(os.path.join(ROOT, "oracle", "sweep_cycles.json")) as f:
+            oracle_counts = json.load(f)
+    except OSError:
+        oracle_counts = {}
+    rows = []
+    for p in synth.sweep_points():
+        n, k = p["n"], p["k"]
+        h = 1.0 / n
+        b = torch.from_numpy(synth.point_source(n, n, h)).cuda()
+        row = dict(p, oracle_cycles=oracle_counts.get(synth.sweep_key(p)))
+        for prec in ("mixed", "fp64"):
+            s = hm.Solver(n, n, h, k, p["beta2"], cycle=p["cycle"], smoother=p["smoother"], nu_pre=p["nu"],
+                          nu_post=p["nu"], precision=prec, max_cycles=400, stream=S)
+            s.solve(b, tol=a.tol)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(S)
+            x, st, cyc, rr = s.solve(b, tol=a.tol)
+            e1.record(S)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            status = {hm.MG_OK: "ok", hm.MG_EMAXIT: "none", hm.MG_EDIVERGED: "div"}.get(st, str(st))
+            row[prec] = {"cycles": int(cyc[0]), "status": status, "relres": float(rr[0]), "ms": ms,
+                         "dof_solves_per_s": (n + 1) ** 2 / (ms / 1e3) if status == "ok" else None}
+            s.close()
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"workload": "constant-k sweep (MP 2-A, centre source, one right-hand side): k at kh = 0.625, "
+                                  "h-refinement at k = 100, nu, V/W, shifts; mixed and FP64 paths",
+                      "unit": "DOF-solves/s", "tol": a.tol, "max_cycles": 400, "data": "synthetic",
+                      "points": rows}))
+
+
 def main():
     a = parse()
     if a.probe:
@@ -643,7 +863,7 @@ def main():
                                   f"workload (the bench headline), not the {a.workload} line"}))
             return
         {"layered": run_layered, "ragged": run_ragged, "gradient": run_gradient,
-         "two-grid": run_two_grid}[a.workload](a)
+         "two-grid": run_two_grid, "sweep": run_sweep}[a.workload](a)
         return
     if a.impl == "reference":
         run_reference(a)

@@ -252,7 +252,11 @@ mg_status mg_two_grid(mg_handle h, int nu, int max_iter, double* out);
  * `level` for all B right-hand sides.  The work runs `reps` times back to
  * back between two CUDA events on the handle's stream (after one untimed
  * run); *ms gets the mean time of one run and *bytes its algorithmic DRAM
- * bytes (each input array read once, each output written once).  It
+ * bytes (each input array read once, each output written once).  `what` = 6
+ * is a throughput probe of the FP64 FMA pipe, not a step of the method (the
+ * denominator of the FP64 path's roofline): eight independent FMA chains of
+ * 4096 steps per thread, 2048 threads per SM on every SM; *bytes then gets
+ * the FP64 flops of one run instead of bytes, and `level` is ignored.  It
  * overwrites the handle's internal work vectors, never caller memory. */
 mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes);
 

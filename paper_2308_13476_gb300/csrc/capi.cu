@@ -472,6 +472,34 @@ static FgArgs fg_args(const mg_ctx* c, double tol) {
   return a;
 }
 
+// Throughput probe of the FP64 FMA pipe (instrumentation for the FP64
+// roofline, no step of the method).  Every thread runs eight independent
+// FMA chains; the sum is stored only if it equals a value it cannot reach,
+// so nothing is written and nothing can be folded away.
+__global__ void __launch_bounds__(256) k_fp64_fma_probe(int iters, double* __restrict__ sink) {
+  double a[8];
+  const double m = 1.0 + 1e-12 * (threadIdx.x + 1), c = 1e-13;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = 1.0 + 1e-3 * q + 1e-7 * blockIdx.x;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = fma(a[q], m, c);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) t += a[q];
+  if (t == -1.0) sink[0] = t;
+}
+
+static double launch_fp64_fma_probe(int iters, double* sink, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8;
+  k_fp64_fma_probe<<<blocks, 256, 0, s>>>(iters, sink);
+  return 2.0 * 8.0 * (double)iters * blocks * 256.0;   // FP64 flops of one launch
+}
+
 template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, int reps, double* ms, double* bytes) {
   cudaStream_t s = (cudaStream_t)h->opt.stream;
   auto& V = vecs<T>(h);
@@ -494,8 +522,10 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
   }
   const std::vector<int> ones(h->B, 1);
   const FgArgs fa = what == 5 ? fg_args(h, 0.0) : FgArgs{};
+  double probe_flops = 0.0;
   auto launch = [&]() {
     switch (what) {
+      case 6: probe_flops = launch_fp64_fma_probe(4096, reinterpret_cast<double*>(V[0].t), s); break;
       case 0: launch_jacobi<T>(g, op, V[level].x, V[level].b, V[level].t, h->B, nullptr, s); break;
       case 1: launch_residual<T>(g, op, V[level].x, V[level].b, V[level].r, h->B, nullptr, s); break;
       case 2: launch_restrict<T>(g, h->lev[level + 1].g, V[level].r, V[level + 1].b, h->B, nullptr, h->xw, s); break;
@@ -510,7 +540,8 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
       }
     }
   };
-  if (what == 0 || what == 1) *bytes = nodes * (3 * e + opbytes);
+  if (what == 6) *bytes = 0.0;   // set from the probe's flop count below
+  else if (what == 0 || what == 1) *bytes = nodes * (3 * e + opbytes);
   else if (what == 2) *bytes = nodes * e * 1.25;     // read fine r, write coarse r
   else if (what == 3) *bytes = nodes * e * 2.25;     // read+write fine x, read coarse e
   else if (what == 5)   // z, Z_j twice; u_0..u_j twice; u_{j+1}, cycle rhs, cycle x (all in the cycle's precision); k twice
@@ -538,6 +569,7 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
   cudaEventDestroy(b);
   CK(cudaGetLastError());
   *ms = t / reps;
+  if (what == 6) *bytes = probe_flops;
   return MG_OK;
 }
 
@@ -1300,7 +1332,7 @@ mg_status mg_counters(mg_handle h, long long* kernel_launches, long long* graph_
 mg_status mg_profile(mg_handle h, int what, int level, int reps, double* ms, double* bytes) {
   if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
-  if (what < 0 || what > 5 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
+  if (what < 0 || what > 6 || reps < 1 || !ms || !bytes) FAIL(MG_EINVAL, "bad mg_profile arguments");
   if (h->opt.precision >= 1) return profile_t<float>(h, what, level, reps, ms, bytes);
   return profile_t<double>(h, what, level, reps, ms, bytes);
 }

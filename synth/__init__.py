@@ -123,3 +123,43 @@ def ragged_sizes(nprob, seed, lo=127, hi=1023):
     for n in rng.integers(lo, hi + 1, nprob):
         out.append(int(cands[np.argmin(np.abs(cands - (n + 1)))]))
     return out
+
+
+def sweep_points():
+    """The constant-k sweep workloads (MP 2-A, centre point source, one
+    right-hand side, relative residual 1e-6), as dicts with keys k, n,
+    smoother ("gmres3" | "jacobi"), cycle ("V" | "W"), nu (pre = post
+    smoothing steps), beta2 and group:
+
+    * "k": k = 50, 100, 200, 400, 800 at kh = 0.625 (n = k / 0.625), GMRES(3)
+      V(2,2) and W(2,2) with beta2 = 1/k, GMRES(3) V(1,1) without shift, and
+      omega-Jacobi V(4,4) with beta2 = 0.7 up to k = 400;
+    * "h": k = 100 at h = 1/128 .. 1/2048, GMRES(3) V(2,2), beta2 = 1/k;
+    * "nu": k = 50 and 100 at kh = 0.625, GMRES(3) nu = 1..5, V and W, beta2 in
+      {1/k, 0.7} (the settings of Sec. 5.3 Tables cons2g and cons1g), and
+      omega-Jacobi V(nu, nu), nu = 1, 2, 4, beta2 = 0.7.
+    """
+    pts = []
+    for k in (50.0, 100.0, 200.0, 400.0, 800.0):
+        n = int(round(k / 0.625))
+        for cyc in ("V", "W"):
+            pts.append(dict(group="k", k=k, n=n, smoother="gmres3", cycle=cyc, nu=2, beta2=1.0 / k))
+        pts.append(dict(group="k", k=k, n=n, smoother="gmres3", cycle="V", nu=1, beta2=0.0))
+        if k <= 400.0:
+            pts.append(dict(group="k", k=k, n=n, smoother="jacobi", cycle="V", nu=4, beta2=0.7))
+    for n in (128, 256, 512, 1024, 2048):
+        pts.append(dict(group="h", k=100.0, n=n, smoother="gmres3", cycle="V", nu=2, beta2=1.0 / 100.0))
+    for k in (50.0, 100.0):
+        n = int(round(k / 0.625))
+        for nu in (1, 2, 3, 4, 5):
+            for cyc in ("V", "W"):
+                for b2 in (1.0 / k, 0.7):
+                    pts.append(dict(group="nu", k=k, n=n, smoother="gmres3", cycle=cyc, nu=nu, beta2=b2))
+        for nu in (1, 2, 4):
+            pts.append(dict(group="nu", k=k, n=n, smoother="jacobi", cycle="V", nu=nu, beta2=0.7))
+    return pts
+
+
+def sweep_key(p):
+    """Key of a sweep point in the stored tables."""
+    return f"{p['k']:g}/{p['n']}/{p['smoother']}/{p['cycle']}{p['nu']}/{p['beta2']:g}"
