@@ -118,8 +118,12 @@ template <class T> __device__ __forceinline__ cx<T> shfl_dn1(cx<T> a) {
   return mk<T>(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
 }
 
-// Per-warp march context.  IN: interior path (see the file comment).
-template <class T, bool IN> struct MCtx {
+// March modes: MD = 1 interior strips (branch-free stencil), MD = 2 edge
+// strips over interior rows (the same stencil, with the boundary row of
+// Op0::apply5 on columns 0 and nx and zero off the grid), MD = 0 everything
+// else (the 3-row bands; every warp on grids of fewer than 7 rows).
+// Per-warp march context.
+template <class T, int MD> struct MCtx {
   static constexpr int NP = MNP<T>::NP;
   Op0<T> op;
   Grid g;
@@ -138,12 +142,19 @@ template <class T, bool IN> struct MCtx {
       const cx<T> xe = n + 1 < NP ? c.v[n + 1 < NP ? n + 1 : 0] : east;
       const cx<T> xw = n > 0 ? c.v[n > 0 ? n - 1 : 0] : west;
       const int in = i + n;
-      if (IN) {   // Op0::apply5, interior case
+      if (MD != 0) {   // Op0::apply5, interior case
         const cx<T> xn = up.v[n], xs = dn.v[n], xp = c.v[n];
-        const T k = op.kf ? op.kf[m * (op.nx + 1) + in] : op.c.k;
+        const int ik = MD == 2 ? min(max(in, 0), op.nx) : in;   // edge strips: k of an in-grid node
+        const T k = op.kf ? op.kf[m * (op.nx + 1) + ik] : op.c.k;
         const T sr = (xe.x + xw.x) + (xn.x + xs.x), si = (xe.y + xw.y) + (xn.y + xs.y);
         const T d = fma(-k, k, T(4) * op.c.inv_h2);
         r.v[n] = mk<T>(fma(d, xp.x, -op.c.inv_h2 * sr), fma(d, xp.y, -op.c.inv_h2 * si));
+        if (MD == 2) {   // rows are interior here; columns 0 and nx take the
+                         // boundary row of Op0::apply5, columns off the grid zero
+          const bool bcol = in == 0 || in == op.nx, inside = in >= 0 && in <= op.nx;
+          if (bcol) r.v[n] = op.apply5(xp, xe, xw, xn, xs, in, m);
+          if (!inside) r.v[n] = zc<T>();
+        }
       } else {
         r.v[n] = (m >= 0 && m <= op.ny && in >= 0 && in <= op.nx)
                      ? op.apply5(c.v[n], xe, xw, up.v[n], dn.v[n], in, m)
@@ -154,7 +165,7 @@ template <class T, bool IN> struct MCtx {
   }
   // node n of the lane counts in the dots of row m
   __device__ __forceinline__ bool cnt(int n, int m) const {
-    return outl && (IN || i + n <= g.nx) && m >= j0 && m < j1;
+    return outl && (MD == 1 || i + n <= g.nx) && m >= j0 && m < j1;
   }
   __device__ __forceinline__ bool own_row(int m) const { return outl && m >= j0 && m < j1; }
 };
@@ -165,9 +176,9 @@ template <int S, int D> struct Sl { static constexpr int v = (S + D + 8) & 3; };
 
 // The NF input fields of a pass: shared-memory staging and register rings.
 // Staging slot (f, k) of a lane is at sbase + (f NS + k) 512 bytes.
-template <class T, bool IN, int NF> struct MIn {
-  static constexpr int NS = Ring<NF>::NS, MD = NS - 1;   // MD: rows in flight ahead of use
-  MCtx<T, IN> c;
+template <class T, int MD, int NF> struct MIn {
+  static constexpr int NS = Ring<NF>::NS, AH = NS - 1;   // AH: rows in flight ahead of use
+  MCtx<T, MD> c;
   const cx<T>* src[NF];
   uint32_t sbase;   // shared address of this lane's slot 0 of field 0
   Row<T> F[NF][4];  // register ring: row r in slot (r - j0 + 2) mod 4
@@ -178,23 +189,23 @@ template <class T, bool IN, int NF> struct MIn {
 #pragma unroll
     for (int f = 0; f < NF; ++f) stage_row<T>(sbase + (f * NS + slot) * 32 * 16, src[f], c.g, c.i, r);
   }
-  // rows t0 .. t0 + MD - 1 in flight, in slots 0 .. MD - 1
+  // rows t0 .. t0 + AH - 1 in flight, in slots 0 .. AH - 1
   __device__ __forceinline__ void prime(int t0) {
 #pragma unroll
-    for (int d = 0; d < MD; ++d) {
+    for (int d = 0; d < AH; ++d) {
       if (t0 + d <= t1) issue(t0 + d, d);
       stage_commit();
     }
-    sw = MD;
+    sw = AH;
     sr = 0;
   }
-  // row t + MD in flight (into the slot row t - 1 left), row t into the
+  // row t + AH in flight (into the slot row t - 1 left), row t into the
   // register ring
   template <int S> __device__ __forceinline__ void fetch(int t) {
-    if (t + MD <= t1) issue(t + MD, sw);
+    if (t + AH <= t1) issue(t + AH, sw);
     sw = sw + 1 == NS ? 0 : sw + 1;
     stage_commit();
-    stage_wait<MD>();
+    stage_wait<AH>();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
       F[f][Sl<S, 0>::v] = stage_read(reinterpret_cast<const typename SlotT<T>::type*>(
@@ -219,15 +230,15 @@ template <class P> __device__ __forceinline__ void march(P& p, int t0, int t1) {
 
 // M0 at iteration t: x and b rows t arrive; u0 row t-1 = b - A x formed from
 // x rows t-2..t; A u0 on row t-2.
-template <class T, bool IN> struct P0 {
+template <class T, int MD> struct P0 {
   static constexpr int NP = MNP<T>::NP;
-  MIn<T, IN, 2> m;   // 0: x, 1: b
+  MIn<T, MD, 2> m;   // 0: x, 1: b
   cx<T>* us;
   Row<T> U[4];
   T acc[3];
   template <int S> __device__ __forceinline__ void step(int t) {
     m.template fetch<S>(t);
-    const MCtx<T, IN>& c = m.c;
+    const MCtx<T, MD>& c = m.c;
     if (t < c.j0) return;
     const Row<T> ax = c.apply(m.F[0][Sl<S, -2>::v], m.F[0][Sl<S, -1>::v], m.F[0][Sl<S, 0>::v], t - 1);
     Row<T> u;
@@ -252,9 +263,9 @@ template <class T, bool IN> struct P0 {
 };
 
 // M1 at iteration t: u0 row t arrives; u1 row t-1 formed; A u1 on row t-2.
-template <class T, bool IN> struct P1 {
+template <class T, int MD> struct P1 {
   static constexpr int NP = MNP<T>::NP;
-  MIn<T, IN, 1> m;   // 0: u0
+  MIn<T, MD, 1> m;   // 0: u0
   cx<T>* ws;
   T s0;
   cx<T> c0;
@@ -262,7 +273,7 @@ template <class T, bool IN> struct P1 {
   T acc[7];
   template <int S> __device__ __forceinline__ void step(int t) {
     m.template fetch<S>(t);
-    const MCtx<T, IN>& c = m.c;
+    const MCtx<T, MD>& c = m.c;
     if (t < c.j0) return;
     const Row<T>(&V)[4] = m.F[0];
     const Row<T> av = c.apply(V[Sl<S, -2>::v], V[Sl<S, -1>::v], V[Sl<S, 0>::v], t - 1);
@@ -296,9 +307,9 @@ template <class T, bool IN> struct P1 {
 
 // M2 at iteration t: u1 and u0 rows t arrive; u2 row t-1 formed; A u2 on
 // row t-2.
-template <class T, bool IN> struct P2 {
+template <class T, int MD> struct P2 {
   static constexpr int NP = MNP<T>::NP;
-  MIn<T, IN, 2> m;   // 0: u1, 1: u0
+  MIn<T, MD, 2> m;   // 0: u1, 1: u0
   cx<T>* ws;
   T s1;
   cx<T> c0, c1;
@@ -306,7 +317,7 @@ template <class T, bool IN> struct P2 {
   T acc[11];
   template <int S> __device__ __forceinline__ void step(int t) {
     m.template fetch<S>(t);
-    const MCtx<T, IN>& c = m.c;
+    const MCtx<T, MD>& c = m.c;
     if (t < c.j0) return;
     const Row<T>(&V)[4] = m.F[0];
     const Row<T>(&Z)[4] = m.F[1];
@@ -348,15 +359,15 @@ template <class T, bool IN> struct P2 {
 };
 
 // M3 at iteration t: u2, u0 and u1 rows t arrive; u3 on row t-1.
-template <class T, bool IN> struct P3 {
+template <class T, int MD> struct P3 {
   static constexpr int NP = MNP<T>::NP;
-  MIn<T, IN, 3> m;   // 0: u2, 1: u0, 2: u1
+  MIn<T, MD, 3> m;   // 0: u2, 1: u0, 2: u1
   T s2;
   cx<T> cl[3];
   T acc[1];
   template <int S> __device__ __forceinline__ void step(int t) {
     m.template fetch<S>(t);
-    const MCtx<T, IN>& c = m.c;
+    const MCtx<T, MD>& c = m.c;
     if (t < c.j0 + 1) return;
     const Row<T>(&V)[4] = m.F[0];
     const Row<T> av = c.apply(V[Sl<S, -2>::v], V[Sl<S, -1>::v], V[Sl<S, 0>::v], t - 1);
@@ -372,24 +383,29 @@ template <class T, bool IN> struct P3 {
 };
 
 // Per-warp geometry inside one right-hand side.  With band = 1 (grids of at
-// least 7 rows) the interior set is strips [s_lo, s_hi) x rows [3, ny-2) in
-// chunks of ch rows; the boundary set is the 3-row bands at the top (rows
-// 0..2) and bottom (rows ny-2..ny) of every strip plus the other strips over
-// rows [3, ny-2) in chunks of chb rows (short, so that the few boundary strips
-// still give many warps).  With band = 0 every warp is a boundary warp, in
+// least 7 rows) the interior set is every strip over rows [3, ny-2) in chunks
+// of ch rows: strips [e_lo, e_hi), whose loaded columns hold no boundary
+// column, take the branch-free stencil; the others (the edge strips) take it
+// too and replace it by the boundary row of Op0::apply5 on columns 0 and nx
+// and by zero off the grid (lane-constant choices: their rows are interior).
+// The boundary set is the 3-row bands at the top (rows 0..2) and bottom (rows
+// ny-2..ny) of every strip.  With band = 0 every warp is a boundary warp, in
 // chunks of chb rows from row 0.
 struct MGeo {
   int nstrips, ny, band, ch, chb;
-  int s_lo, s_hi;   // interior strips
-  int nci;          // interior chunks
-  int nsub;         // chunks of a boundary strip (band: over rows [3, ny-2))
-  int ni, nb;       // warps in the interior and boundary sets
+  int e_lo, e_hi;   // strips of the interior set without a boundary column
+  int nci;          // chunks per strip over rows [3, ny-2)
+  int ni, nb;       // warps of the interior strips and of the 3-row bands (or of the whole grid)
   // strip and rows [j0, j1) of warp w of the set
-  template <bool IN> __host__ __device__ __forceinline__ void map(int w, int& strip, int& j0, int& j1) const {
-    if (IN) {
-      const int nsi = s_hi - s_lo;
-      strip = s_lo + w % nsi;
-      j0 = 3 + (w / nsi) * ch;
+  // interior strips [e_lo, e_hi), the edge strips outside that range, each
+  // over rows [3, ny-2) in chunks of ch rows
+  __host__ __device__ __forceinline__ int ne() const { return (nstrips - (e_hi - e_lo)) * nci; }
+  template <int MD> __host__ __device__ __forceinline__ void map(int w, int& strip, int& j0, int& j1) const {
+    if (MD != 0) {
+      const int nse = nstrips - (e_hi - e_lo), nsm = MD == 1 ? e_hi - e_lo : nse;
+      const int sidx = w % nsm;
+      strip = MD == 1 ? e_lo + sidx : (sidx < e_lo ? sidx : e_hi + (sidx - e_lo));
+      j0 = 3 + (w / nsm) * ch;
       j1 = j0 + ch < ny - 2 ? j0 + ch : ny - 2;
       return;
     }
@@ -399,19 +415,17 @@ struct MGeo {
       j1 = j0 + chb < ny + 1 ? j0 + chb : ny + 1;
       return;
     }
-    if (w < 2 * nstrips) {
-      strip = w % nstrips;
-      j0 = w < nstrips ? 0 : ny - 2;
-      j1 = j0 + 3;
-      return;
-    }
-    const int q = w - 2 * nstrips, nside = nstrips - (s_hi - s_lo);
-    const int sidx = q % nside;
-    strip = sidx < s_lo ? sidx : s_hi + (sidx - s_lo);
-    j0 = 3 + (q / nside) * chb;
-    j1 = j0 + chb < ny - 2 ? j0 + chb : ny - 2;
+    strip = w % nstrips;
+    j0 = w < nstrips ? 0 : ny - 2;
+    j1 = j0 + 3;
   }
+  // first reduction record of a mode's warps: interior, then edge, then the rest
+  template <int MD> __host__ __device__ __forceinline__ int rec0() const {
+    return MD == 1 ? 0 : (MD == 2 ? ni : ni + ne());
+  }
+  __host__ __device__ __forceinline__ int nrec() const { return ni + ne() + nb; }
 };
+
 template <class T> __host__ __device__ constexpr int strip_w() { return 32 * MNP<T>::NP - 4; }
 
 // Common prologue (one warp per block).  i: first node of this lane; outl:
@@ -423,20 +437,20 @@ template <class T> __host__ __device__ constexpr int strip_w() { return 32 * MNP
   const long long off = (long long)rhs * g.vstride;                           \
   const int lane = threadIdx.x & 31;                                          \
   int strip, j0, j1;                                                          \
-  mg.template map<IN>(blockIdx.x, strip, j0, j1);                             \
+  mg.template map<MD>(blockIdx.x, strip, j0, j1);                             \
   const int cs = strip * strip_w<T>() - 2;                                    \
   const int i = cs + NP * lane;                                               \
   const bool outl = NP * lane >= 2 && NP * lane + NP <= 32 * NP - 2;          \
   double* S = st + (long long)rhs * GS;                                       \
-  const MCtx<T, IN> ctx{op, g, i, j0, j1, outl};
+  const MCtx<T, MD> ctx{op, g, i, j0, j1, outl};
 
 // Runs pass P on the warp's strip and chunk (rows j0-2 .. t1 read) and
 // returns its sums in acc.  stg: the warp's staging area, [NF][NS slots][32
 // lanes] of 16 bytes, free again (every copy landed, the warp converged) on
 // return.
-template <template <class, bool> class P, class T, bool IN, int NV, class Init>
-__device__ __forceinline__ void run_pass(const MCtx<T, IN>& c, int t1, const void* stg, T (&acc)[NV], Init&& init) {
-  P<T, IN> p;
+template <template <class, int> class P, class T, int MD, int NV, class Init>
+__device__ __forceinline__ void run_pass(const MCtx<T, MD>& c, int t1, const void* stg, T (&acc)[NV], Init&& init) {
+  P<T, MD> p;
   p.m.c = c;
   p.m.sbase = (uint32_t)__cvta_generic_to_shared(stg) + (threadIdx.x & 31) * 16;
   p.m.t1 = t1;
@@ -456,17 +470,17 @@ __device__ __forceinline__ void run_pass(const MCtx<T, IN>& c, int t1, const voi
 // records 0 .. ni-1, boundary blocks after them) and takes a ticket counted
 // over both launches; the block holding the last ticket sums all records in
 // record order and runs the scalar step F.
-template <bool IN, int NV, class T, class F>
+template <int MD, int NV, class T, class F>
 __device__ __forceinline__ void finish(const T (&acc)[NV], double* sh, double* partial, unsigned* tickets, int rhs,
                                        const MGeo& mg, double* S, F f) {
   double v[NV];
-  const int nrec = mg.ni + mg.nb;
-  if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blockIdx.x, IN ? 0 : mg.ni, nrec))
+  const int nrec = mg.nrec();
+  if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blockIdx.x, mg.template rec0<MD>(), nrec))
     staged<T>(S, v, f);
 }
 
 // M0: u0 = b - A x; |u0|^2 and <u0, A u0>.
-template <class T, bool IN>
+template <class T, int MD>
 __global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
                                               const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
@@ -479,7 +493,7 @@ __global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const 
     p.m.src[1] = b + off;
     p.us = u0 + off;
   });
-  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
     fin_init<T>(s, q);
     if (s[G_BRK] == 0.0) {   // <u0, w> with w = s0 A u0
       const double d[2] = {q[1] * s[G_S], q[2] * s[G_S]};
@@ -489,7 +503,7 @@ __global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const 
 }
 
 // M1: u1 = s0 A u0 - c00 u0; |u1|^2, <u1, u0>, then <u0, A u1>, <u1, A u1>.
-template <class T, bool IN>
+template <class T, int MD>
 __global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
                                                cx<T>* __restrict__ u1, double* st, double* partial,
                                                unsigned* tickets, const int* __restrict__ active) {
@@ -506,7 +520,7 @@ __global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const
     p.s0 = s0;
     p.c0 = c0;
   });
-  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
     fin_b<0, T>(s, q);
     if (s[G_BRK] == 0.0) {
       const double s1 = s[G_S + 1];
@@ -518,7 +532,7 @@ __global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const
 
 // M2: u2 = s1 A u1 - c01 u0 - c11 u1; |u2|^2, <u2, u0>, <u2, u1>, then
 // <u_l, A u2> for l = 0, 1, 2.
-template <class T, bool IN>
+template <class T, int MD>
 __global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, cx<T>* __restrict__ u2, double* st,
                                                double* partial, unsigned* tickets, const int* __restrict__ active) {
@@ -538,7 +552,7 @@ __global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const
     p.c0 = c0;
     p.c1 = c1;
   });
-  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
     fin_b<1, T>(s, q);
     if (s[G_BRK] == 0.0) {
       const double s2 = s[G_S + 2];
@@ -550,7 +564,7 @@ __global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const
 
 // M3: |u3|^2 with u3 = s2 A u2 - sum_l c_l2 u_l; then the least-squares
 // solve (fin_b<2>).
-template <class T, bool IN>
+template <class T, int MD>
 __global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
                                                double* st, double* partial, unsigned* tickets,
@@ -574,7 +588,7 @@ __global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const
     p.cl[1] = cl[1];
     p.cl[2] = cl[2];
   });
-  finish<IN>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) { fin_b<2, T>(s, q); });
+  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) { fin_b<2, T>(s, q); });
 }
 
 // Interior chunks are tall (few halo rows) unless the grid has too few
@@ -587,28 +601,27 @@ template <class T> MGeo march_geo(const Grid& g, int B) {
   m.ny = g.ny;
   m.band = g.ny >= 6;
   m.chb = 16;
-  m.s_lo = m.s_hi = 0;
+  m.e_lo = m.e_hi = 0;
   for (int s = 0; s < m.nstrips; ++s) {
     const int cs = s * SW - 2;
     if (cs >= 1 && cs + 32 * NP - 1 <= g.nx - 1) {
-      if (m.s_hi == 0) m.s_lo = s;
-      m.s_hi = s + 1;
+      if (m.e_hi == 0) m.e_lo = s;
+      m.e_hi = s + 1;
     }
   }
-  if (!m.band) m.s_lo = m.s_hi = 0;
-  const int nsi = m.s_hi - m.s_lo, inner_rows = g.ny - 5;
+  const int inner_rows = g.ny - 5;
   const long long want = 152LL * 48;   // warps to fill the GPU a few times over
   int ch = 64;
-  while (ch > 8 && (long long)nsi * cdiv(inner_rows, ch) * B < want) ch /= 2;
+  while (ch > 8 && (long long)m.nstrips * cdiv(inner_rows, ch) * B < want) ch /= 2;
   m.ch = ch;
-  m.nci = nsi > 0 ? cdiv(inner_rows, ch) : 0;
-  m.ni = nsi * m.nci;
   if (m.band) {
-    m.nsub = cdiv(inner_rows, m.chb);
-    m.nb = 2 * m.nstrips + (m.nstrips - nsi) * m.nsub;
+    m.nci = cdiv(inner_rows, ch);
+    m.ni = (m.e_hi - m.e_lo) * m.nci;
+    m.nb = 2 * m.nstrips;
   } else {
-    m.nsub = cdiv(g.ny + 1, m.chb);
-    m.nb = m.nstrips * m.nsub;
+    m.e_lo = m.e_hi = 0;
+    m.nci = m.ni = 0;
+    m.nb = m.nstrips * cdiv(g.ny + 1, m.chb);
   }
   return m;
 }
@@ -621,7 +634,7 @@ template <class T> void launch_gmres_update(const Grid& g, cx<T>* x, const Gmres
 
 long long gmres_march_blocks(const Grid& g, bool fp64, int B) {
   const MGeo m = fp64 ? march_geo<double>(g, B) : march_geo<float>(g, B);
-  return (long long)m.ni + m.nb;
+  return (long long)m.nrec();
 }
 
 template <class T>
@@ -635,17 +648,18 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
   double* st = gb.st;
   const Op0<T> op{opv.c0, opv.kf, g.nx, g.ny};
   const MGeo mg = march_geo<T>(g, B);
-  const dim3 gi(mg.ni, 1, B), gbd(mg.nb, 1, B);
-  // the boundary launch of each pass on the side stream, beside the interior
-  // one (its few long-lived warps then overlap the interior launch)
+  const dim3 gi(mg.ni, 1, B), ge(mg.ne(), 1, B), gbd(mg.nb, 1, B);
+  // the edge-strip and band launches of each pass on the side stream, beside
+  // the interior one (their few warps then overlap the interior launch)
   const bool fork = gb.side && mg.ni;
   cudaStream_t sb = fork ? gb.side : s;
-  auto pass = [&](auto interior, auto boundary) {
+  auto pass = [&](auto interior, auto edge, auto bands) {
     if (fork) {
       cudaEventRecord(gb.ev_fork, s);
       cudaStreamWaitEvent(gb.side, gb.ev_fork, 0);
     }
-    boundary();
+    if (mg.ne()) edge();
+    bands();
     if (mg.ni) interior();
     if (fork) {
       cudaEventRecord(gb.ev_join, gb.side);
@@ -653,14 +667,18 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
     }
   };
   for (int step = 0; step < nu; ++step) {
-    pass([&] { gm_init<T, true><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active); },
-         [&] { gm_init<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); });
-    pass([&] { gm_step1<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active); },
-         [&] { gm_step1<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, st, P, tk, active); });
-    pass([&] { gm_step2<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
-         [&] { gm_step2<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
-    pass([&] { gm_step3<T, true><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
-         [&] { gm_step3<T, false><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
+    pass([&] { gm_init<T, 1><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active); },
+         [&] { gm_init<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); },
+         [&] { gm_init<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); });
+    pass([&] { gm_step1<T, 1><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active); },
+         [&] { gm_step1<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, u0, u1, st, P, tk, active); },
+         [&] { gm_step1<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, st, P, tk, active); });
+    pass([&] { gm_step2<T, 1><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
+         [&] { gm_step2<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
+         [&] { gm_step2<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
+    pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
+         [&] { gm_step3<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
+         [&] { gm_step3<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
     launch_gmres_update<T>(g, x, gb, B, active, s);
   }
 }
