@@ -6,7 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/helmmg.h"
@@ -65,6 +67,11 @@ struct Level {
   float2 *gx32 = nullptr, *hy32 = nullptr;
   float *wx32 = nullptr, *wy32 = nullptr;
   float2* dinv32 = nullptr;
+  // constant k: rows [ty0, ty1) whose y-factor rows (hy, wy) all equal the
+  // middle row's, and that row (the translation-invariant interior)
+  int ty0 = 0, ty1 = 0;
+  double2 hyc[7] = {};
+  double wyc[7] = {};
 };
 
 }  // namespace
@@ -181,6 +188,12 @@ static OpView<double> op64(const mg_ctx* c, int l) {
     v.wx = L.wx;
     v.hy = L.hy;
     v.wy = L.wy;
+    v.ty0 = L.ty0;
+    v.ty1 = L.ty1;
+    for (int k = 0; k < 7; ++k) {
+      v.hyc[k] = L.hyc[k];
+      v.wyc[k] = L.wyc[k];
+    }
   }
   return v;
 }
@@ -200,6 +213,12 @@ static OpView<float> op32(const mg_ctx* c, int l) {
     v.wx = L.wx32;
     v.hy = L.hy32;
     v.wy = L.wy32;
+    v.ty0 = L.ty0;   // the float copies round the same FP64 rows: equal rows stay equal
+    v.ty1 = L.ty1;
+    for (int k = 0; k < 7; ++k) {
+      v.hyc[k] = make_float2((float)L.hyc[k].x, (float)L.hyc[k].y);
+      v.wyc[k] = (float)L.wyc[k];
+    }
   }
   return v;
 }
@@ -688,6 +707,31 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
       launch_real_part(cwy[l], L.wy, (long long)w * (cy_ + 1), s);
       CK(dalloc(c, (void**)&L.dinv, sizeof(double2) * L.plane));
       launch_diaginv_op(op64(c, l), cx_, cy_, o.omega, L.dinv, s);
+      // rows of the y-factors equal to the middle row (translation-invariant interior)
+      {
+        const int K = w, ny1 = cy_ + 1, mid = cy_ / 2;
+        std::vector<double2> hh((size_t)K * ny1);
+        std::vector<double> ww((size_t)K * ny1);
+        CK(cudaMemcpyAsync(hh.data(), L.hy, sizeof(double2) * hh.size(), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ww.data(), L.wy, sizeof(double) * ww.size(), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        auto same = [&](int j) {
+          for (int k = 0; k < K; ++k) {
+            const double2 a = hh[(size_t)j * K + k], b = hh[(size_t)mid * K + k];
+            if (a.x != b.x || a.y != b.y || ww[(size_t)j * K + k] != ww[(size_t)mid * K + k]) return false;
+          }
+          return true;
+        };
+        int j0 = mid, j1 = mid + 1;
+        while (j0 > 0 && same(j0 - 1)) --j0;
+        while (j1 < ny1 && same(j1)) ++j1;
+        L.ty0 = j0;
+        L.ty1 = j1;
+        for (int k = 0; k < K; ++k) {
+          L.hyc[k] = hh[(size_t)mid * K + k];
+          L.wyc[k] = ww[(size_t)mid * K + k];
+        }
+      }
       pg = L.gx;
       ph = L.hy;
       pwx = cwx[l];
@@ -825,8 +869,10 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
     CK(dalloc(c, (void**)&a.tickets, sizeof(unsigned) * c->B));
   }
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-  if (o.smoother == 1) {
-    CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  if (o.smoother == 1) {   // the side stream takes the priority of the handle's stream
+    int sprio = 0;
+    if (o.stream) CK(cudaStreamGetPriority((cudaStream_t)o.stream, &sprio));
+    CK(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, sprio));
     CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   }
@@ -887,9 +933,22 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
   if (o.batch != 1) FAIL(MG_EINVAL, "a ragged batch solves one right-hand side per problem (batch must be 1)");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
+  // stream priorities by problem size: the largest problems (the longest
+  // chains of cycles) get the highest priority, so their blocks are
+  // scheduled first whenever the problems compete for the GPU
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  const int nprio = prio_least - prio_greatest + 1;
+  std::vector<int> order(nprob);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)(nx[a] + 1) * (ny[a] + 1) > (long long)(nx[b] + 1) * (ny[b] + 1);
+  });
+  std::vector<int> prio(nprob, prio_least);
+  for (int r = 0; r < nprob; ++r) prio[order[r]] = prio_greatest + (int)((long long)r * nprio / nprob);
   for (int p = 0; p < nprob; ++p) {
     cudaStream_t sp;
-    if (cudaStreamCreateWithFlags(&sp, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithPriority(&sp, cudaStreamNonBlocking, prio[p]) != cudaSuccess) {
       delete c;
       FAIL(MG_ECUDA, "stream creation failed");
     }
@@ -1210,16 +1269,30 @@ static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, i
     if (st != MG_OK) return st;
   }
   long long launches = 0;
-  while (true) {
-    for (int p = 0; p < P; ++p) CK(cudaStreamSynchronize((cudaStream_t)c->sub[p]->opt.stream));
-    bool any = false;
-    for (int p = 0; p < P; ++p)
+  // Each problem runs its own cycles: a problem whose stream has drained
+  // (its active count read back) gets its next cycle at once, without
+  // waiting for the slower problems, so the small problems finish early and
+  // the largest one, on the highest-priority stream, is never held back by a
+  // round barrier.
+  std::vector<char> running(P, 1);
+  int left = P;
+  while (left > 0) {
+    bool progressed = false;
+    for (int p = 0; p < P; ++p) {
+      if (!running[p]) continue;
+      const cudaError_t q = cudaStreamQuery((cudaStream_t)c->sub[p]->opt.stream);
+      if (q == cudaErrorNotReady) continue;
+      CK(q);
+      progressed = true;
       if (solve_more(c->sub[p])) {
         mg_status st = solve_launch(c->sub[p]);
         if (st != MG_OK) return st;
-        any = true;
+      } else {
+        running[p] = 0;
+        --left;
       }
-    if (!any) break;
+    }
+    if (!progressed) std::this_thread::yield();
   }
   mg_status worst = MG_OK;
   std::string msg;

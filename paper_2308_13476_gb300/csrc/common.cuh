@@ -179,6 +179,14 @@ template <class T, int R> struct OpK {
   const T* wy;
   const cx<T>* dinvp;
   int nx, ny;
+  // Rows [ty0, ty1) whose y-factor rows equal hyc / wyc bit for bit (away
+  // from the boundary the constant-k factors are translation invariant):
+  // kernels that take the operator by value read them from the parameter
+  // bank instead of loading the row's coefficients (ty0 = ty1 = 0: none).
+  int ty0, ty1;
+  cx<T> hyc[2 * R + 1];
+  T wyc[2 * R + 1];
+  static constexpr int radius = R;
   __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, int p, int pitch, int i, int j) const {
     const cx<T>* G = gx + i * (2 * R + 1);
     const T* Wx = wx + i * (2 * R + 1);

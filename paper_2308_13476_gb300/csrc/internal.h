@@ -22,6 +22,10 @@ template <class T> struct OpView {
   const T* wx;
   const cx<T>* hy;
   const T* wy;
+  // constant-k levels: rows [ty0, ty1) whose y-factor rows are hyc / wyc
+  int ty0, ty1;
+  cx<T> hyc[7];
+  T wyc[7];
 };
 __host__ __device__ inline int op_radius(int kind) { return kind == 1 ? 1 : (kind == 2 || kind == 4) ? 2 : 3; }
 

@@ -99,6 +99,37 @@ __device__ __forceinline__ void stage_kron_row(cx<T>* dst, const cx<T>* vs, cons
   }
 }
 
+// combination along y for output row m = r - R, r the row just taken in
+// slot P of a ring of the last K = 2R+1 row sums: row m + dy sits in slot
+// (P + 1 + R + dy) mod K, or in slot dy + R of a shifting ring (KU = 1).
+// Rows whose y-factors are the translation-invariant interior ones take the
+// coefficients from the operator's parameter-bank copy (the same values);
+// the others load their row's coefficients.
+template <class T, int R, int K, int KUR, int P>
+__device__ __forceinline__ cx<T> kcombine(const OpK<T, R>& op, int m, const cx<T> (&s1)[K], const cx<T> (&s2)[K]) {
+  cx<T> acc = mk<T>(T(0), T(0));
+  if (m >= op.ty0 && m < op.ty1) {
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+      const int q = KUR == 1 ? dy + R : (P + 1 + R + dy) % K;
+      const T wy = op.wyc[dy + R];
+      acc = mk<T>(fma(wy, s1[q].x, acc.x), fma(wy, s1[q].y, acc.y));
+      acc = fma_c<T>(op.hyc[dy + R], s2[q], acc);
+    }
+    return acc;
+  }
+  const cx<T>* H = op.hy + m * K;
+  const T* Wy = op.wy + m * K;
+#pragma unroll
+  for (int dy = -R; dy <= R; ++dy) {
+    const int q = KUR == 1 ? dy + R : (P + 1 + R + dy) % K;
+    const T wy = __ldg(Wy + dy + R);
+    acc = mk<T>(fma(wy, s1[q].x, acc.x), fma(wy, s1[q].y, acc.y));
+    acc = fma_c<T>(__ldg(H + dy + R), s2[q], acc);
+  }
+  return acc;
+}
+
 template <class T, int R> struct KRing {
   static constexpr int K = 2 * R + 1;
   static constexpr int RA = kron_ra<T, R>();
@@ -164,17 +195,7 @@ template <class T, int R> struct KRing {
   // slot P: row m + dy sits in slot (P + 1 + R + dy) mod K, or in slot dy + R
   // of the shifting ring (KU = 1)
   template <int P> __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
-    const cx<T>* H = op.hy + m * K;
-    const T* Wy = op.wy + m * K;
-    cx<T> acc = mk<T>(T(0), T(0));
-#pragma unroll
-    for (int dy = -R; dy <= R; ++dy) {
-      const int q = KU<R> == 1 ? dy + R : (P + 1 + R + dy) % K;
-      const T wy = __ldg(Wy + dy + R);
-      acc = mk<T>(fma(wy, s1[q].x, acc.x), fma(wy, s1[q].y, acc.y));
-      acc = fma_c<T>(__ldg(H + dy + R), s2[q], acc);
-    }
-    return acc;
+    return kcombine<T, R, K, KU<R>, P>(op, m, s1, s2);
   }
 };
 
@@ -378,17 +399,7 @@ template <class T, int R, int NS> struct KRingF {
   __device__ __forceinline__ cx<T> staged(int v, int m) const { return sm[(v * KSL + slot(m)) * WD + lane + RA]; }
   __device__ __forceinline__ cx<T> formed(int m) const { return fm[slot(m) * WD + lane + RA]; }
   template <int P> __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
-    const cx<T>* H = op.hy + m * K;
-    const T* Wy = op.wy + m * K;
-    cx<T> acc = mk<T>(T(0), T(0));
-#pragma unroll
-    for (int dy = -R; dy <= R; ++dy) {
-      const int q = KU<R> == 1 ? dy + R : (P + 1 + R + dy) % K;
-      const T wy = __ldg(Wy + dy + R);
-      acc = mk<T>(fma(wy, s1[q].x, acc.x), fma(wy, s1[q].y, acc.y));
-      acc = fma_c<T>(__ldg(H + dy + R), s2[q], acc);
-    }
-    return acc;
+    return kcombine<T, R, K, KU<R>, P>(op, m, s1, s2);
   }
 };
 
@@ -585,10 +596,20 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
       launch_gmres_update<T>(g, x, gb, B, active, s);
     }
   };
+  auto with_rows = [&](auto op) {   // the translation-invariant y-factor rows
+    constexpr int K = 2 * decltype(op)::radius + 1;
+    op.ty0 = opv.ty0;
+    op.ty1 = opv.ty1;
+    for (int k = 0; k < K; ++k) {
+      op.hyc[k] = opv.hyc[k];
+      op.wyc[k] = opv.wyc[k];
+    }
+    return op;
+  };
   if (opv.kind == 4)
-    run(OpK<T, 2>{opv.gx, opv.wx, opv.hy, opv.wy, opv.dinv, g.nx, g.ny}, std::integral_constant<int, 2>{});
+    run(with_rows(OpK<T, 2>{opv.gx, opv.wx, opv.hy, opv.wy, opv.dinv, g.nx, g.ny}), std::integral_constant<int, 2>{});
   else
-    run(OpK<T, 3>{opv.gx, opv.wx, opv.hy, opv.wy, opv.dinv, g.nx, g.ny}, std::integral_constant<int, 3>{});
+    run(with_rows(OpK<T, 3>{opv.gx, opv.wx, opv.hy, opv.wy, opv.dinv, g.nx, g.ny}), std::integral_constant<int, 3>{});
 }
 
 template void gmres_smooth_kron<double>(const Grid&, const OpView<double>&, double2*, const double2*, int, int,
