@@ -46,10 +46,11 @@ template <int K, class F> __device__ __forceinline__ void kmarch(int r0, int las
 
 // Whether the march over a radius-R level is unrolled so that its register
 // ring never moves (KU = 2R+1 phases), or keeps one phase and shifts the ring
-// by a row per step (KU = 1).  Unrolling the radius-3 marches (7 phases)
-// raised the fused passes from 96 to 122-126 registers per thread and cost
-// them a resident block per SM, so only radius 2 unrolls.
-template <int R> constexpr int KU = R == 2 ? 2 * R + 1 : 1;
+// by a row per step (KU = 1).  complex64 unrolls both radii (with the y
+// coefficients of the interior rows in the parameter bank the radius-3
+// passes stay within their launch bounds); the complex128 radius-3 marches
+// would spill unrolled and keep the shifting ring.
+template <class T, int R> constexpr int KU = (R == 2 || sizeof(T) == 4) ? 2 * R + 1 : 1;
 
 // A v down column i: the input rows arrive in order through a per-warp
 // shared-memory ring (each row's 32 + 2RA columns around the warp's columns,
@@ -181,21 +182,21 @@ template <class T, int R> struct KRing {
       a = fma_c<T>(G[dx + R], xv, a);
       c = mk<T>(fma(Wx[dx + R], xv.x, c.x), fma(Wx[dx + R], xv.y, c.y));
     }
-    if constexpr (KU<R> == 1) {
+    if constexpr (KU<T, R> == 1) {
 #pragma unroll
       for (int k = 0; k < K - 1; ++k) {
         s1[k] = s1[k + 1];
         s2[k] = s2[k + 1];
       }
     }
-    s1[KU<R> == 1 ? K - 1 : P] = a;
-    s2[KU<R> == 1 ? K - 1 : P] = c;
+    s1[KU<T, R> == 1 ? K - 1 : P] = a;
+    s2[KU<T, R> == 1 ? K - 1 : P] = c;
   }
   // combination along y for output row m = r - R, r the row just taken in
   // slot P: row m + dy sits in slot (P + 1 + R + dy) mod K, or in slot dy + R
   // of the shifting ring (KU = 1)
   template <int P> __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
-    return kcombine<T, R, K, KU<R>, P>(op, m, s1, s2);
+    return kcombine<T, R, K, KU<T, R>, P>(op, m, s1, s2);
   }
 };
 
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op
   T a0[1] = {T(0)};
   if (has) {
     KMARCH_SETUP(x + off)
-    kmarch<KU<R>>(j0 - R, last, [&](auto ph, int r) {
+    kmarch<KU<T, R>>(j0 - R, last, [&](auto ph, int r) {
       constexpr int P = decltype(ph)::value;
       ring.template advance<P>(r, last);
       const int m = r - R;
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
     const T sJ = (T)S[G_S + J];
     const cx<T>* us[3] = {u0 + off, u1 + off, u2 + off};
     KMARCH_SETUP(uJ + off)
-    kmarch<KU<R>>(j0 - R, last, [&](auto ph, int r) {
+    kmarch<KU<T, R>>(j0 - R, last, [&](auto ph, int r) {
       constexpr int P = decltype(ph)::value;
       ring.template advance<P>(r, last);
       const int m = r - R;
@@ -384,22 +385,22 @@ template <class T, int R, int NS> struct KRingF {
       a = fma_c<T>(G[dx + R], xv, a);
       b = mk<T>(fma(Wx[dx + R], xv.x, b.x), fma(Wx[dx + R], xv.y, b.y));
     }
-    if constexpr (KU<R> == 1) {
+    if constexpr (KU<T, R> == 1) {
 #pragma unroll
       for (int k = 0; k < K - 1; ++k) {
         s1[k] = s1[k + 1];
         s2[k] = s2[k + 1];
       }
     }
-    s1[KU<R> == 1 ? K - 1 : P] = a;
-    s2[KU<R> == 1 ? K - 1 : P] = b;
+    s1[KU<T, R> == 1 ? K - 1 : P] = a;
+    s2[KU<T, R> == 1 ? K - 1 : P] = b;
     return row[0];
   }
   // staged vector v (1 + l for u_l) and the formed u_J at row m, lane's column
   __device__ __forceinline__ cx<T> staged(int v, int m) const { return sm[(v * KSL + slot(m)) * WD + lane + RA]; }
   __device__ __forceinline__ cx<T> formed(int m) const { return fm[slot(m) * WD + lane + RA]; }
   template <int P> __device__ __forceinline__ cx<T> combine(const OpK<T, R>& op, int m) const {
-    return kcombine<T, R, K, KU<R>, P>(op, m, s1, s2);
+    return kcombine<T, R, K, KU<T, R>, P>(op, m, s1, s2);
   }
 };
 
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__(KW * 32, R == 2 && J == 1 ? 6 : 5) km_arn_ab(G
     ring.r0 = j0 - R;
     const int last = j1 + R - 1;
     ring.prime(last);
-    kmarch<KU<R>>(j0 - R, last, [&](auto ph, int r) {
+    kmarch<KU<T, R>>(j0 - R, last, [&](auto ph, int r) {
       constexpr int P = decltype(ph)::value;
       const cx<T> u = ring.template advance<P>(r, last, cw, c);
       if (r >= j0 && r < j1 && col) {   // own row: store u_J, the inputs of fin_b<J-1>
