@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--probe", action="store_true",
                    help="profiling probe: set up the workload and run two solves capped at --max-cycles; no timing")
     p.add_argument("--max-cycles", type=int, default=2)
+    p.add_argument("--flat", type=int, default=1, choices=[0, 1],
+                   help="ragged workload: 1 = one flattened launch per kernel over all problems, 0 = a graph per problem")
     p.add_argument("--coarse-nodes", type=int, default=-1)
     p.add_argument("--coarse-mode", type=int, default=-1)
     p.add_argument("--no-autotune", action="store_true", help="library default launch shapes instead of the autotuner's")
@@ -743,7 +745,7 @@ def run_ragged(a):
     probs = [(n, n, 1.0 / n, 0.625 * n) for n in ns]
     rhs = [torch.from_numpy(synth.point_source(n, n, 1.0 / n)).cuda() for n in ns]
     rs = hm.RaggedSolver(probs, [1.0 / p[3] for p in probs], smoother="gmres3", nu_pre=2, nu_post=2,
-                         precision=a.precision, max_cycles=20000, march=a.march)
+                         precision=a.precision, max_cycles=20000, march=a.march, flat=a.flat)
     rs.solve(rhs, tol=a.tol)
     ms, (xs, st, cyc, rr) = _event_ms(lambda: rs.solve(rhs, tol=a.tol), a.steps)
     if st != hm.MG_OK:
@@ -753,6 +755,7 @@ def run_ragged(a):
     print(json.dumps({"workload": "ragged batch of 32 constant-k problems, kh = 0.625", "unit": "DOF-solves/s",
                       "value": N / (ms / 1e3), "ms_per_solve": ms, "unknowns_total": N, "sizes": ns,
                       "cycles": [int(c) for c in cyc], "max_relres": float(max(rr)), "precision": a.precision,
+                      "flat": a.flat,
                       "data": "synthetic", "smoother": "gmres3", "cycle": "V(2,2)", "tol": a.tol}))
 
 

@@ -42,7 +42,7 @@ class MgOptions(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
                 ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("fuse", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("march", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("transfer", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("transfer", ctypes.c_int), ("flat", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -261,7 +261,7 @@ TRANSFERS = {"bezier": 0, "linear": 1}
 
 def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, precision="fp64", batch=1,
              max_cycles=10000, min_coarse=10, coarse_nodes=None, coarse_mode=None, fuse=None, tile_rows=None,
-             march=None, krylov=None, transfer="bezier", stream=None):
+             march=None, krylov=None, transfer="bezier", flat=None, stream=None):
     o = mg_default_options()
     o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
     o.smoother = SMOOTHERS[smoother]
@@ -269,7 +269,7 @@ def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, preci
     o.precision = PRECISIONS[precision]
     o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
     for name, val in (("coarse_nodes", coarse_nodes), ("coarse_mode", coarse_mode), ("fuse", fuse),
-                      ("tile_rows", tile_rows), ("march", march), ("krylov", krylov)):
+                      ("tile_rows", tile_rows), ("march", march), ("krylov", krylov), ("flat", flat)):
         if val is not None:
             setattr(o, name, int(val))
     o.transfer = TRANSFERS[transfer]
@@ -283,7 +283,9 @@ class RaggedSolver:
 
     RaggedSolver(sizes=[(nx, ny, h, k), ...], beta2, **options), beta2 a
     scalar or one shift per problem.  solve() takes and returns a list of
-    complex128 CUDA grids (ny+1, nx+1)."""
+    complex128 CUDA grids (ny+1, nx+1).  ``flat=1`` (the default) runs a
+    cycle of all problems as one launch per kernel when the options allow
+    it, ``flat=0`` one cycle graph per problem."""
 
     def __init__(self, sizes, beta2, **options):
         self.sizes = [(int(a), int(b), float(c), float(d)) for a, b, c, d in sizes]

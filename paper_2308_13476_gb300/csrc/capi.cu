@@ -13,6 +13,7 @@
 
 #include "../../include/helmmg.h"
 #include "internal.h"
+#include "ragged_api.h"
 
 using namespace hmg;
 
@@ -125,6 +126,11 @@ struct mg_ctx {
   int done = 0;                    // cycles of the current solve
   std::vector<mg_ctx*> sub;        // ragged batch: one handle per problem
   cudaStream_t own_stream = nullptr;
+  bool flat = false;               // ragged batch: one flattened launch per kernel over all problems
+  int* d_counts = nullptr;         // ragged flat: [2 P] active counts and barrier flags (device)
+  int* h_counts = nullptr;         // and their pinned host copy
+  std::vector<cudaStream_t> cstreams;  // ragged flat: per level, the stream of the coarse-cycle launches
+  std::vector<cudaEvent_t> cfork, cjoin;
   // FGMRES(m) outer loop (opt.krylov = m > 0)
   FgArgs fg{};                     // buffers and geometry; per-solve fields set in solve_fgmres
   cudaGraph_t pgraph = nullptr;    // one preconditioning cycle (no test, no update)
@@ -139,11 +145,15 @@ struct mg_ctx {
     if (pgraph) cudaGraphDestroy(pgraph);
     for (void* p : allocs) cudaFree(p);
     if (h_n_active) cudaFreeHost(h_n_active);
+    if (h_counts) cudaFreeHost(h_counts);
     if (cap) cudaStreamDestroy(cap);
     if (side) cudaStreamDestroy(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (own_stream) cudaStreamDestroy(own_stream);
+    for (cudaStream_t q : cstreams) cudaStreamDestroy(q);
+    for (cudaEvent_t e : cfork) cudaEventDestroy(e);
+    for (cudaEvent_t e : cjoin) cudaEventDestroy(e);
   }
 };
 
@@ -594,6 +604,139 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
 
 // ----------------------------------------------------------------- C ABI
 
+// ---------------------------------------------------------- ragged, flattened
+//
+// The cycle of every problem of a ragged batch as one graph whose kernels are
+// single launches over all problems (ragged.cuh).  The recursion is the one
+// of Emit::cycle, run on the set of problems that visit a level: problems
+// whose coarse-cycle launch starts at this level take it here (one CTA per
+// problem), the others smooth, restrict, recurse gamma times, prolong and
+// smooth.  Every problem sees its own kernels in the order Emit gives them.
+template <class T> struct EmitR {
+  mg_ctx* c;
+  cudaStream_t s;
+  int P() const { return (int)c->sub.size(); }
+  mg_ctx* q(int p) const { return c->sub[p]; }
+  cx<T>* cur(int p, int l) const { return vecs<T>(c->sub[p])[l].x; }   // GMRES(3) smoothing keeps x in place
+
+  void smooth(int l, const std::vector<int>& G, int nu) {
+    if (nu <= 0 || G.empty()) return;
+    std::vector<RagLevel<T>> v;
+    for (int p : G) {
+      mg_ctx* h = q(p);
+      v.push_back(RagLevel<T>{h->lev[l].g, opT<T>(h, l), cur(p, l), vecs<T>(h)[l].b, vecs<T>(h)[l].gb, h->active});
+    }
+    if (l == 0) gmres_smooth_march_rag<T>(v, nu, s, c->side, c->ev_fork, c->ev_join);
+    else gmres_smooth_kron_rag<T>(v, nu, s);
+  }
+
+  void cycle(int l, const std::vector<int>& S) {
+    std::vector<int> G, I;
+    for (int p : S) (l >= q(p)->lc ? I : G).push_back(p);
+    if (!I.empty()) {   // one visit of each one's coarse sub-cycle, beside the deeper work of the others
+      std::vector<RagCoarse<T>> v;
+      for (int p : I) {
+        mg_ctx* h = q(p);
+        const CoarsePlan<T>* pl = sizeof(T) == 8 ? (const CoarsePlan<T>*)&h->plan64 : (const CoarsePlan<T>*)&h->plan32;
+        v.push_back(RagCoarse<T>{pl->levels, pl->steps, pl->nsteps, h->cinv, h->ncoarse, h->active});
+      }
+      if (G.empty()) {
+        launch_coarse_cycle_rag<T>(v, s);
+      } else {
+        cudaEventRecord(c->cfork[l], s);
+        cudaStreamWaitEvent(c->cstreams[l], c->cfork[l], 0);
+        launch_coarse_cycle_rag<T>(v, c->cstreams[l]);
+        cudaEventRecord(c->cjoin[l], c->cstreams[l]);
+      }
+    }
+    if (G.empty()) return;
+    struct Join {   // the caller's next kernel (a prolongation) reads the coarse launch's result
+      mg_ctx* c;
+      cudaStream_t s;
+      int l;
+      bool on;
+      ~Join() {
+        if (on) cudaStreamWaitEvent(s, c->cjoin[l], 0);
+      }
+    } join{c, s, l, !I.empty()};
+    smooth(l, G, c->opt.nu_pre);
+    std::vector<RagXfer<T>> xf;
+    std::vector<RagVec> zv;
+    for (int p : G) {
+      mg_ctx* h = q(p);
+      auto& V = vecs<T>(h);
+      xf.push_back(RagXfer<T>{h->lev[l].g, h->lev[l + 1].g, opT<T>(h, l), cur(p, l), V[l].b, V[l + 1].b, cur(p, l),
+                              h->active});
+      zv.push_back(RagVec{h->lev[l + 1].g, cur(p, l + 1), h->active});
+    }
+    launch_resid_restrict_rag<T>(xf, c->sub[0]->xw, s);
+    launch_zero_rag<T>(zv, s);
+    for (int g = 0; g < c->opt.cycle; ++g) cycle(l + 1, G);
+    for (size_t k = 0; k < G.size(); ++k) xf[k].rc = cur(G[k], l + 1);   // the coarse correction
+    launch_prolong_add_rag<T>(xf, c->sub[0]->xw, s);
+    smooth(l, G, c->opt.nu_post);
+  }
+
+  std::vector<int> all() const {
+    std::vector<int> v(P());
+    for (int p = 0; p < P(); ++p) v[p] = p;
+    return v;
+  }
+};
+
+// One cycle of every problem and its stopping test, then the active counts
+// gathered into the pinned host array (graph body of the flattened batch).
+static void emit_ragged_iteration(mg_ctx* c, cudaStream_t s) {
+  const int P = (int)c->sub.size();
+  std::vector<RagOuter> outer;
+  std::vector<const int*> counts;
+  for (mg_ctx* h : c->sub) {
+    const Grid& g0 = h->lev[0].g;
+    const OpView<double> o = op64(h, 0);
+    outer.push_back(RagOuter{g0, Op0<double>{o.c0, o.kf, g0.nx, g0.ny}, h->v64[0].x, h->v64[0].b,
+                             h->opt.precision == 1 ? h->v32[0].x : nullptr, h->opt.precision == 1 ? h->v32[0].b : nullptr,
+                             ctl(h)});
+    counts.push_back(h->n_active);
+  }
+  if (c->opt.precision == 1) {
+    std::vector<RagVec> zv;
+    for (mg_ctx* h : c->sub) zv.push_back(RagVec{h->lev[0].g, h->v32[0].x, h->active});
+    launch_zero_rag<float>(zv, s);
+    EmitR<float> e{c, s};
+    e.cycle(0, e.all());
+    launch_update_mixed_rag(outer, s);
+    launch_resid_cast_stop_rag(outer, 1, s);
+  } else {
+    EmitR<double> e{c, s};
+    e.cycle(0, e.all());
+    launch_resnorm_stop_rag(outer, 1, s);
+  }
+  launch_gather_counts(counts, c->d_counts, s);
+  cudaMemcpyAsync(c->h_counts, c->d_counts, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, s);
+}
+
+static mg_status capture_ragged(mg_ctx* c) {
+  if (c->gexec) return MG_OK;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  emit_ragged_iteration(c, c->cap);
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (e != cudaSuccess) FAIL(MG_ECUDA, "graph capture of the flattened ragged cycle failed: %s", cudaGetErrorString(e));
+  c->graph = g;
+  CK(cudaGraphInstantiate(&c->gexec, g, 0));
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  c->graph_kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    c->graph_kernels += t == cudaGraphNodeTypeKernel;
+  }
+  return MG_OK;
+}
+
 extern "C" {
 
 void mg_default_options(mg_options* o) {
@@ -614,6 +757,7 @@ void mg_default_options(mg_options* o) {
   o->march = -1;
   o->krylov = 0;
   o->transfer = 0;
+  o->flat = 1;
   o->stream = nullptr;
 }
 
@@ -903,6 +1047,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.krylov < 0 || o.krylov > FG_MAXM) FAIL(MG_EINVAL, "krylov must be in 0..%d", FG_MAXM);
   if (o.krylov > 0 && o.precision == 2) FAIL(MG_EINVAL, "the FGMRES outer loop needs precision 0 or 1");
   if (o.transfer != 0 && o.transfer != 1) FAIL(MG_EINVAL, "transfer must be 0 (Eq. (xex)) or 1 (linear)");
+  if (o.flat != 0 && o.flat != 1) FAIL(MG_EINVAL, "flat must be 0 or 1");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
@@ -971,6 +1116,39 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
   c->nx = c->sub[0]->nx;
   c->ny = c->sub[0]->ny;
   c->nlev = c->sub[0]->nlev;
+  // one flattened launch per kernel over all problems: GMRES(3) smoothing
+  // with the march kernels, precision 0 or 1, the stand-alone cycle, and
+  // every problem's coarsest grid inside its coarse-cycle launch
+  bool flat = o.flat == 1 && o.smoother == 1 && o.fuse == 1 && o.march != 0 && o.precision <= 1 && o.krylov == 0 &&
+              o.coarse_mode == 0;
+  for (mg_ctx* q : c->sub) flat = flat && q->lc <= q->nlev - 1 && q->coop_grid == 0;
+  if (flat) {
+    mg_status fs = MG_OK;
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        dalloc(c, (void**)&c->d_counts, sizeof(int) * 2 * nprob) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_counts, sizeof(int) * 2 * nprob) != cudaSuccess)
+      fs = MG_ENOMEM;
+    int lmax = 0;
+    for (mg_ctx* q : c->sub) lmax = std::max(lmax, q->nlev);
+    for (int l = 0; l < lmax && fs == MG_OK; ++l) {
+      cudaStream_t cs;
+      cudaEvent_t ef, ej;
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { fs = MG_ECUDA; break; }
+      c->cstreams.push_back(cs);
+      if (cudaEventCreateWithFlags(&ef, cudaEventDisableTiming) != cudaSuccess) { fs = MG_ECUDA; break; }
+      c->cfork.push_back(ef);
+      if (cudaEventCreateWithFlags(&ej, cudaEventDisableTiming) != cudaSuccess) { fs = MG_ECUDA; break; }
+      c->cjoin.push_back(ej);
+    }
+    if (fs != MG_OK) {
+      delete c;
+      FAIL(fs, "ragged batch: allocation of the flattened cycle failed");
+    }
+    c->flat = true;
+  }
   *out = c;
   return MG_OK;
 }
@@ -1269,6 +1447,21 @@ static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, i
     if (st != MG_OK) return st;
   }
   long long launches = 0;
+  if (c->flat) {   // every cycle one graph over all problems (emit_ragged_iteration)
+    for (int p = 0; p < P; ++p) CK(cudaStreamSynchronize((cudaStream_t)c->sub[p]->opt.stream));
+    mg_status st = capture_ragged(c);
+    if (st != MG_OK) return st;
+    cudaStream_t s = (cudaStream_t)c->opt.stream;
+    int left = 0;
+    for (int p = 0; p < P; ++p) left += c->sub[p]->h_n_active[0] > 0;
+    for (int round = 0; left > 0 && round < c->opt.max_cycles; ++round) {
+      CK(cudaGraphLaunch(c->gexec, s));
+      CK(cudaStreamSynchronize(s));
+      launches += c->graph_kernels;
+      left = 0;
+      for (int p = 0; p < P; ++p) left += c->h_counts[p] > 0;
+    }
+  } else {
   // Each problem runs its own cycles: a problem whose stream has drained
   // (its active count read back) gets its next cycle at once, without
   // waiting for the slower problems, so the small problems finish early and
@@ -1293,6 +1486,7 @@ static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, i
       }
     }
     if (!progressed) std::this_thread::yield();
+  }
   }
   mg_status worst = MG_OK;
   std::string msg;

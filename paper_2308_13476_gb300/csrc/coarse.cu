@@ -11,8 +11,12 @@
 // the same stencils, the same Jacobi sweep, the same GMRES(3) arithmetic
 // (gmres.cuh), the same transfers of Eq. (xex) and the same FP64 coarsest
 // solve; only the reductions are block-wide instead of grid-wide.
+#include <algorithm>
+
 #include "gmres.cuh"
 #include "internal.h"
+#include "ragged.cuh"
+#include "ragged_api.h"
 #include "levelops.cuh"
 
 namespace hmg {
@@ -123,10 +127,11 @@ __device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, d
 }
 
 template <class T>
-__global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle(const CLevel<T>* __restrict__ levels,
-                                                             const CStep* __restrict__ steps, int nsteps,
-                                                             const double2* __restrict__ inv, int N,
-                                                             const int* __restrict__ active) {
+__device__ __forceinline__ void k_coarse_cycle_body(uint3 vblk, dim3 vgrid, const CLevel<T>* __restrict__ levels, const CStep* __restrict__ steps, int nsteps, const double2* __restrict__ inv, int N, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   extern __shared__ double2 rs[];            // coarsest right-hand side, N entries
   __shared__ double sh[NVMAX * 32];
   __shared__ double S[GS];
@@ -238,10 +243,37 @@ __global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle(const CLevel<T>* _
 }
 
 template <class T>
+__global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle(const CLevel<T>* __restrict__ levels, const CStep* __restrict__ steps, int nsteps, const double2* __restrict__ inv, int N, const int* __restrict__ active) {
+  k_coarse_cycle_body<T>(blockIdx, gridDim, levels, steps, nsteps, inv, N, active);
+}
+
+template <class T>
+__global__ void __launch_bounds__(CTA_THREADS) k_coarse_cycle_rag(const __grid_constant__ RagLaunch<RagCoarse<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const RagCoarse<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  k_coarse_cycle_body<T>(vb, vg, a.levels, a.steps, a.nsteps, a.inv, a.N, a.active);
+}
+
+template <class T>
 void launch_coarse_cycle(const CLevel<T>* levels, const CStep* steps, int nsteps, const double2* inv, int N, int B,
                          const int* active, cudaStream_t s) {
   k_coarse_cycle<T><<<B, CTA_THREADS, (size_t)N * sizeof(double2), s>>>(levels, steps, nsteps, inv, N, active);
 }
+
+// One CTA per problem of a ragged batch, each walking its own plan.
+template <class T> void launch_coarse_cycle_rag(const std::vector<RagCoarse<T>>& v, cudaStream_t s) {
+  int nmax = 0;
+  for (const auto& c : v) nmax = std::max(nmax, c.N);
+  rag_launch<RagCoarse<T>>((int)v.size(), k_coarse_cycle_rag<T>, dim3(CTA_THREADS), (size_t)nmax * sizeof(double2), s,
+                           [&](int q, RagCoarse<T>& a, int& gx, int&) {
+                             a = v[q];
+                             gx = 1;
+                             return true;
+                           });
+}
+template void launch_coarse_cycle_rag<double>(const std::vector<RagCoarse<double>>&, cudaStream_t);
+template void launch_coarse_cycle_rag<float>(const std::vector<RagCoarse<float>>&, cudaStream_t);
 
 template void launch_coarse_cycle<double>(const CLevel<double>*, const CStep*, int, const double2*, int, int,
                                           const int*, cudaStream_t);

@@ -20,6 +20,8 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "ragged.cuh"
+#include "ragged_api.h"
 
 namespace hmg {
 
@@ -30,10 +32,25 @@ constexpr int RFX = 2 * CTX + 3, RFY = 2 * CTY + 3;  // fine footprint incl. res
 template <class Op> struct KronRadius { static constexpr int R = 0; };
 template <class T, int R_> struct KronRadius<OpK<T, R_>> { static constexpr int R = R_; };
 
+// Arguments of the residual-restriction for one problem (flattened ragged launches).
 template <class T, class Op>
-__global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, Op op, const cx<T>* __restrict__ x,
-                                                              const cx<T>* __restrict__ b, cx<T>* __restrict__ rc,
-                                                              const int* __restrict__ active, Xfer xw) {
+struct RrA {
+  Grid gf;
+  Grid gc;
+  Op op;
+  const cx<T>* x;
+  const cx<T>* b;
+  cx<T>* rc;
+  const int* active;
+  Xfer xw;
+};
+
+template <class T, class Op>
+__device__ __forceinline__ void k_resid_restrict_body(uint3 vblk, dim3 vgrid, Grid gf, Grid gc, Op op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, cx<T>* __restrict__ rc, const int* __restrict__ active, Xfer xw) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   __shared__ cx<T> rt[RFY][RFX];
   const int rhs = blockIdx.z;
   if (active && !active[rhs]) return;
@@ -136,6 +153,19 @@ __global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, 
   rc[(long long)rhs * gc.vstride + gc.at(I, J)] = scl<T>(T(0.25), acc);
 }
 
+template <class T, class Op>
+__global__ void __launch_bounds__(CTX * CTY) k_resid_restrict(Grid gf, Grid gc, Op op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, cx<T>* __restrict__ rc, const int* __restrict__ active, Xfer xw) {
+  k_resid_restrict_body<T, Op>(blockIdx, gridDim, gf, gc, op, x, b, rc, active, xw);
+}
+
+template <class T, class Op>
+__global__ void __launch_bounds__(CTX * CTY) k_resid_restrict_rag(const __grid_constant__ RagLaunch<RrA<T, Op>> L) {
+  uint3 vb;
+  dim3 vg;
+  const RrA<T, Op>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  k_resid_restrict_body<T, Op>(vb, vg, a.gf, a.gc, a.op, a.x, a.b, a.rc, a.active, a.xw);
+}
+
 constexpr int JTX = 64, JTY = 16;        // output tile of k_jacobi_fused
 constexpr int JMAXNU = 4;                // sweeps fused in one launch (more: several launches)
 
@@ -223,6 +253,29 @@ cudaError_t configure_fused_kernels() {   // allow the complex128 window (> 48 K
                               (int)jacobi_fused_smem<float>(JMAXNU));
 }
 
+template <class T>
+void launch_resid_restrict_rag(const std::vector<RagXfer<T>>& v, const Xfer& xw, cudaStream_t s) {
+  if (v.empty()) return;
+  const RagXfer<T>& v0 = v[0];
+  with_op<T>(v0.op, v0.gf.nx, v0.gf.ny, [&](auto op0) {   // the problems' levels at one depth share the operator kind
+    using Op = decltype(op0);
+    rag_launch<RrA<T, Op>>((int)v.size(), k_resid_restrict_rag<T, Op>, dim3(CTX, CTY), 0, s,
+                           [&](int q, RrA<T, Op>& a, int& gx, int& gy) {
+                             const RagXfer<T>& X = v[q];
+                             Op op = op0;
+                             with_op<T>(X.op, X.gf.nx, X.gf.ny, [&](auto o) {
+                               if constexpr (std::is_same<decltype(o), Op>::value) op = o;
+                             });
+                             a = RrA<T, Op>{X.gf, X.gc, op, X.x, X.b, X.rc, X.active, xw};
+                             gx = cdiv(X.gc.nx + 1, CTX);
+                             gy = cdiv(X.gc.ny + 1, CTY);
+                             return true;
+                           });
+  });
+}
+
+template void launch_resid_restrict_rag<double>(const std::vector<RagXfer<double>>&, const Xfer&, cudaStream_t);
+template void launch_resid_restrict_rag<float>(const std::vector<RagXfer<float>>&, const Xfer&, cudaStream_t);
 template void launch_resid_restrict<double>(const Grid&, const Grid&, const OpView<double>&, const double2*,
                                             const double2*, double2*, int, const int*, const Xfer&, cudaStream_t);
 template void launch_resid_restrict<float>(const Grid&, const Grid&, const OpView<float>&, const float2*,

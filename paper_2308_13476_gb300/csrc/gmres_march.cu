@@ -46,6 +46,8 @@
 
 #include "gmres.cuh"
 #include "internal.h"
+#include "ragged.cuh"
+#include "ragged_api.h"
 
 namespace hmg {
 
@@ -428,6 +430,23 @@ struct MGeo {
 
 template <class T> __host__ __device__ constexpr int strip_w() { return 32 * MNP<T>::NP - 4; }
 
+// Arguments of the march kernels for one problem (the flattened launches of a
+// ragged batch carry one per problem).
+template <class T> struct GmA {
+  Grid g;
+  MGeo mg;
+  Op0<T> op;
+  const cx<T>* x;
+  const cx<T>* b;
+  cx<T>* u0;
+  cx<T>* u1;
+  cx<T>* u2;
+  double* st;
+  double* partial;
+  unsigned* tickets;
+  const int* active;
+};
+
 // Common prologue (one warp per block).  i: first node of this lane; outl:
 // the lane's nodes are in the strip's output columns.
 #define MPRO                                                                  \
@@ -470,20 +489,22 @@ __device__ __forceinline__ void run_pass(const MCtx<T, MD>& c, int t1, const voi
 // records 0 .. ni-1, boundary blocks after them) and takes a ticket counted
 // over both launches; the block holding the last ticket sums all records in
 // record order and runs the scalar step F.
+// blk: the block's index inside its own launch (the body's blockIdx.x).
 template <int MD, int NV, class T, class F>
 __device__ __forceinline__ void finish(const T (&acc)[NV], double* sh, double* partial, unsigned* tickets, int rhs,
-                                       const MGeo& mg, double* S, F f) {
+                                       int blk, const MGeo& mg, double* S, F f) {
   double v[NV];
   const int nrec = mg.nrec();
-  if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blockIdx.x, mg.template rec0<MD>(), nrec))
+  if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blk, mg.template rec0<MD>(), nrec))
     staged<T>(S, v, f);
 }
 
 // M0: u0 = b - A x; |u0|^2 and <u0, A u0>.
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
+__device__ __forceinline__ void gm_init_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
                                               const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block index inside this problem's launch
   MPRO
   T acc[3];
   __shared__ __align__(16) unsigned char stg[ring_bytes<2>()];
@@ -493,7 +514,7 @@ __global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const 
     p.m.src[1] = b + off;
     p.us = u0 + off;
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) {
     fin_init<T>(s, q);
     if (s[G_BRK] == 0.0) {   // <u0, w> with w = s0 A u0
       const double d[2] = {q[1] * s[G_S], q[2] * s[G_S]};
@@ -502,11 +523,27 @@ __global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const 
   });
 }
 
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
+                                              const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
+                                              double* partial, unsigned* tickets, const int* __restrict__ active) {
+  gm_init_body<T, MD>(blockIdx, g, mg, op, x, b, u0, st, partial, tickets, active);
+}
+
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_init_rag(const __grid_constant__ RagLaunch<GmA<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const GmA<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  gm_init_body<T, MD>(vb, a.g, a.mg, a.op, a.x, a.b, a.u0, a.st, a.partial, a.tickets, a.active);
+}
+
 // M1: u1 = s0 A u0 - c00 u0; |u1|^2, <u1, u0>, then <u0, A u1>, <u1, A u1>.
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__device__ __forceinline__ void gm_step1_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
                                                cx<T>* __restrict__ u1, double* st, double* partial,
                                                unsigned* tickets, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block index inside this problem's launch
   MPRO
   if (S[G_BRK] != 0.0) return;   // uniform per RHS
   const T s0 = (T)S[G_S];
@@ -520,7 +557,7 @@ __global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const
     p.s0 = s0;
     p.c0 = c0;
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) {
     fin_b<0, T>(s, q);
     if (s[G_BRK] == 0.0) {
       const double s1 = s[G_S + 1];
@@ -530,12 +567,28 @@ __global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const
   });
 }
 
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+                                               cx<T>* __restrict__ u1, double* st, double* partial,
+                                               unsigned* tickets, const int* __restrict__ active) {
+  gm_step1_body<T, MD>(blockIdx, g, mg, op, u0, u1, st, partial, tickets, active);
+}
+
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_step1_rag(const __grid_constant__ RagLaunch<GmA<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const GmA<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  gm_step1_body<T, MD>(vb, a.g, a.mg, a.op, a.u0, a.u1, a.st, a.partial, a.tickets, a.active);
+}
+
 // M2: u2 = s1 A u1 - c01 u0 - c11 u1; |u2|^2, <u2, u0>, <u2, u1>, then
 // <u_l, A u2> for l = 0, 1, 2.
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, cx<T>* __restrict__ u2, double* st,
                                                double* partial, unsigned* tickets, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block index inside this problem's launch
   MPRO
   if (S[G_BRK] != 0.0 || S[G_M] < 1) return;
   const T s1 = (T)S[G_S + 1];
@@ -552,7 +605,7 @@ __global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const
     p.c0 = c0;
     p.c1 = c1;
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) {
     fin_b<1, T>(s, q);
     if (s[G_BRK] == 0.0) {
       const double s2 = s[G_S + 2];
@@ -562,13 +615,29 @@ __global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const
   });
 }
 
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+                                               const cx<T>* __restrict__ u1, cx<T>* __restrict__ u2, double* st,
+                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
+  gm_step2_body<T, MD>(blockIdx, g, mg, op, u0, u1, u2, st, partial, tickets, active);
+}
+
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_step2_rag(const __grid_constant__ RagLaunch<GmA<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const GmA<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  gm_step2_body<T, MD>(vb, a.g, a.mg, a.op, a.u0, a.u1, a.u2, a.st, a.partial, a.tickets, a.active);
+}
+
 // M3: |u3|^2 with u3 = s2 A u2 - sum_l c_l2 u_l; then the least-squares
 // solve (fin_b<2>).
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__device__ __forceinline__ void gm_step3_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
                                                double* st, double* partial, unsigned* tickets,
                                                const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block index inside this problem's launch
   MPRO
   if (S[G_BRK] != 0.0 || S[G_M] < 2) return;
   const T s2 = (T)S[G_S + 2];
@@ -588,7 +657,23 @@ __global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const
     p.cl[1] = cl[1];
     p.cl[2] = cl[2];
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, mg, S, [](double* s, const double* q) { fin_b<2, T>(s, q); });
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) { fin_b<2, T>(s, q); });
+}
+
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+                                               const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
+                                               double* st, double* partial, unsigned* tickets,
+                                               const int* __restrict__ active) {
+  gm_step3_body<T, MD>(blockIdx, g, mg, op, u0, u1, u2, st, partial, tickets, active);
+}
+
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_step3_rag(const __grid_constant__ RagLaunch<GmA<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const GmA<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  gm_step3_body<T, MD>(vb, a.g, a.mg, a.op, a.u0, a.u1, a.u2, a.st, a.partial, a.tickets, a.active);
 }
 
 // Interior chunks are tall (few halo rows) unless the grid has too few
@@ -683,6 +768,57 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
   }
 }
 
+// The same smoothing steps on every problem of a ragged batch: each pass is
+// one flattened launch per kind of warp (interior strips; edge strips and
+// bands on the side stream), over the problems' own geometries.
+template <class T>
+void gmres_smooth_march_rag(const std::vector<RagLevel<T>>& v, int nu, cudaStream_t s, cudaStream_t side,
+                            cudaEvent_t fork, cudaEvent_t join) {
+  const int n = (int)v.size();
+  std::vector<GmA<T>> A(n);
+  bool any_interior = false;
+  for (int q = 0; q < n; ++q) {
+    const RagLevel<T>& L = v[q];
+    const MGeo mg = march_geo<T>(L.g, 1);
+    any_interior |= mg.ni > 0;
+    A[q] = GmA<T>{L.g, mg, Op0<T>{L.op.c0, L.op.kf, L.g.nx, L.g.ny}, L.x, L.b, (cx<T>*)L.gb.u[0],
+                  (cx<T>*)L.gb.u[1], (cx<T>*)L.gb.u[2], L.gb.st, L.gb.partial, L.gb.tickets, L.active};
+  }
+  const bool fk = side && any_interior;
+  cudaStream_t sb = fk ? side : s;
+  auto launch = [&](auto kern, int md, cudaStream_t st) {
+    rag_launch<GmA<T>>(n, kern, dim3(32), 0, st, [&](int q, GmA<T>& a, int& gx, int&) {
+      a = A[q];
+      gx = md == 1 ? a.mg.ni : (md == 2 ? a.mg.ne() : a.mg.nb);
+      return true;
+    });
+  };
+  auto pass = [&](auto ki, auto ke, auto kb) {
+    if (fk) {
+      cudaEventRecord(fork, s);
+      cudaStreamWaitEvent(side, fork, 0);
+    }
+    launch(ke, 2, sb);
+    launch(kb, 0, sb);
+    launch(ki, 1, s);
+    if (fk) {
+      cudaEventRecord(join, side);
+      cudaStreamWaitEvent(s, join, 0);
+    }
+  };
+  for (int step = 0; step < nu; ++step) {
+    pass(gm_init_rag<T, 1>, gm_init_rag<T, 2>, gm_init_rag<T, 0>);
+    pass(gm_step1_rag<T, 1>, gm_step1_rag<T, 2>, gm_step1_rag<T, 0>);
+    pass(gm_step2_rag<T, 1>, gm_step2_rag<T, 2>, gm_step2_rag<T, 0>);
+    pass(gm_step3_rag<T, 1>, gm_step3_rag<T, 2>, gm_step3_rag<T, 0>);
+    launch_gmres_update_rag<T>(v, s);
+  }
+}
+
+template void gmres_smooth_march_rag<double>(const std::vector<RagLevel<double>>&, int, cudaStream_t, cudaStream_t,
+                                             cudaEvent_t, cudaEvent_t);
+template void gmres_smooth_march_rag<float>(const std::vector<RagLevel<float>>&, int, cudaStream_t, cudaStream_t,
+                                            cudaEvent_t, cudaEvent_t);
 template void gmres_smooth_march<double>(const Grid&, const OpView<double>&, double2*, const double2*, int, int,
                                          const int*, const GmresBufs&, cudaStream_t);
 template void gmres_smooth_march<float>(const Grid&, const OpView<float>&, float2*, const float2*, int, int,

@@ -17,8 +17,37 @@
 #include "gmres.cuh"
 #include "internal.h"
 #include "pack.cuh"
+#include "ragged.cuh"
+#include "ragged_api.h"
 
 namespace hmg {
+
+// Arguments of the flattened launches over a ragged batch (one per problem).
+template <class T>
+struct GbA {
+  Grid g;
+  const cx<T>* u0;
+  const cx<T>* u1;
+  const cx<T>* u2;
+  cx<T>* un;
+  const cx<T>* w;
+  double* st;
+  double* partial;
+  unsigned* tickets;
+  const int* active;
+  int ws;
+};
+
+template <class T>
+struct GuA {
+  Grid g;
+  cx<T>* x;
+  const cx<T>* u0;
+  const cx<T>* u1;
+  const cx<T>* u2;
+  const double* st;
+  const int* active;
+};
 
 // The thread's pack starts at column i0 and holds nv nodes inside the grid.
 #define GNODE                                            \
@@ -104,11 +133,11 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
 
 // u_{J+1} = w - sum_{i<=J} h_iJ s_i u_i ; partials |u_{J+1}|^2 and <u_{J+1}, u_l>, l <= J (J < 2)
 template <class T, int J>
-__global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1,
-                                                   const cx<T>* __restrict__ u2, cx<T>* __restrict__ un,
-                                                   const cx<T>* __restrict__ w, double* __restrict__ st,
-                                                   double* partial, unsigned* tickets, const int* __restrict__ active,
-                                                   int ws) {
+__device__ __forceinline__ void g_arn_b_body(uint3 vblk, dim3 vgrid, Grid g, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2, cx<T>* __restrict__ un, const cx<T>* __restrict__ w, double* __restrict__ st, double* partial, unsigned* tickets, const int* __restrict__ active, int ws) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   constexpr int NV = (J < 2) ? 1 + 2 * (J + 1) : 1;
   __shared__ double sh[NVMAX * 32];
   GNODE
@@ -164,11 +193,26 @@ __global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restri
   if (reduce_last<NV, T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_b<J, T>(s, q); });
 }
 
+template <class T, int J>
+__global__ void __launch_bounds__(BX * BY) g_arn_b(Grid g, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2, cx<T>* __restrict__ un, const cx<T>* __restrict__ w, double* __restrict__ st, double* partial, unsigned* tickets, const int* __restrict__ active, int ws) {
+  g_arn_b_body<T, J>(blockIdx, gridDim, g, u0, u1, u2, un, w, st, partial, tickets, active, ws);
+}
+
+template <class T, int J>
+__global__ void __launch_bounds__(BX * BY) g_arn_b_rag(const __grid_constant__ RagLaunch<GbA<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const GbA<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  g_arn_b_body<T, J>(vb, vg, a.g, a.u0, a.u1, a.u2, a.un, a.w, a.st, a.partial, a.tickets, a.active, a.ws);
+}
+
 // x += sum_{i<m} y_i s_i u_i
 template <class T>
-__global__ void __launch_bounds__(BX * BY) g_update(Grid g, cx<T>* __restrict__ x, const cx<T>* __restrict__ u0,
-                                                    const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
-                                                    const double* __restrict__ st, const int* __restrict__ active) {
+__device__ __forceinline__ void g_update_body(uint3 vblk, dim3 vgrid, Grid g, cx<T>* __restrict__ x, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2, const double* __restrict__ st, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   constexpr int NP = PK<T>::NP;
   const int rhs = blockIdx.z;
   const int i0 = (blockIdx.x * BX + threadIdx.x) * NP;
@@ -200,6 +244,19 @@ __global__ void __launch_bounds__(BX * BY) g_update(Grid g, cx<T>* __restrict__ 
     }
     store_pack(x + off, p, a, nv);
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) g_update(Grid g, cx<T>* __restrict__ x, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2, const double* __restrict__ st, const int* __restrict__ active) {
+  g_update_body<T>(blockIdx, gridDim, g, x, u0, u1, u2, st, active);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) g_update_rag(const __grid_constant__ RagLaunch<GuA<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const GuA<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  g_update_body<T>(vb, vg, a.g, a.x, a.u0, a.u1, a.u2, a.st, a.active);
 }
 
 template <class T>
@@ -243,6 +300,37 @@ void launch_arn_b(const Grid& g, const GmresBufs& gb, cx<T>* un, int B, const in
                                             un, (const cx<T>*)gb.w, gb.st, gb.partial, gb.tickets, active, ws);
 }
 
+template <class T> void launch_gmres_update_rag(const std::vector<RagLevel<T>>& v, cudaStream_t s) {
+  rag_launch<GuA<T>>((int)v.size(), g_update_rag<T>, dim3(BX, BY), 0, s, [&](int q, GuA<T>& a, int& gx, int& gy) {
+    const RagLevel<T>& L = v[q];
+    a = GuA<T>{L.g, L.x, (const cx<T>*)L.gb.u[0], (const cx<T>*)L.gb.u[1], (const cx<T>*)L.gb.u[2], L.gb.st, L.active};
+    gx = cdiv(L.g.nx + 1, BX * PK<T>::NP);
+    gy = cdiv(L.g.ny + 1, BY * L.g.ry);
+    return true;
+  });
+}
+
+template <class T, int J>
+void launch_arn_b_rag(const std::vector<RagLevel<T>>& v, bool un_next, int ws, cudaStream_t s) {
+  rag_launch<GbA<T>>((int)v.size(), g_arn_b_rag<T, J>, dim3(BX, BY), 0, s, [&](int q, GbA<T>& a, int& gx, int& gy) {
+    const RagLevel<T>& L = v[q];
+    cx<T>* un = un_next && J < 2 ? (cx<T>*)L.gb.u[J + 1] : nullptr;
+    a = GbA<T>{L.g, (const cx<T>*)L.gb.u[0], (const cx<T>*)L.gb.u[1], (const cx<T>*)L.gb.u[2], un,
+               (const cx<T>*)L.gb.w, L.gb.st, L.gb.partial, L.gb.tickets, L.active, ws};
+    gx = cdiv(L.g.nx + 1, BX * PK<T>::NP);
+    gy = cdiv(L.g.ny + 1, BY * L.g.ry);
+    return true;
+  });
+}
+
+template void launch_gmres_update_rag<double>(const std::vector<RagLevel<double>>&, cudaStream_t);
+template void launch_gmres_update_rag<float>(const std::vector<RagLevel<float>>&, cudaStream_t);
+template void launch_arn_b_rag<double, 0>(const std::vector<RagLevel<double>>&, bool, int, cudaStream_t);
+template void launch_arn_b_rag<double, 1>(const std::vector<RagLevel<double>>&, bool, int, cudaStream_t);
+template void launch_arn_b_rag<double, 2>(const std::vector<RagLevel<double>>&, bool, int, cudaStream_t);
+template void launch_arn_b_rag<float, 0>(const std::vector<RagLevel<float>>&, bool, int, cudaStream_t);
+template void launch_arn_b_rag<float, 1>(const std::vector<RagLevel<float>>&, bool, int, cudaStream_t);
+template void launch_arn_b_rag<float, 2>(const std::vector<RagLevel<float>>&, bool, int, cudaStream_t);
 template void launch_arn_b<double, 0>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t, int);
 template void launch_arn_b<double, 1>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t, int);
 template void launch_arn_b<double, 2>(const Grid&, const GmresBufs&, double2*, int, const int*, cudaStream_t, int);

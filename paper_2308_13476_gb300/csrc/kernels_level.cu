@@ -9,7 +9,11 @@
 // relative residual of Sec. 5.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.h"
+#include "ragged.cuh"
+#include "ragged_api.h"
 #include "pack.cuh"
 
 namespace hmg {
@@ -25,6 +29,46 @@ static inline dim3 pack_grid(const Grid& g, int B, int np) {
 
 // Thread (tx, ty) of block (bx, by, rhs) handles node column i and the g.ry
 // rows j = by*BY*ry + r*BY + ty, r = 0..ry-1 (warps stay on one row).
+// Arguments of the flattened launches over a ragged batch (one per problem).
+template <class T, class Op>
+struct RsA {
+  Grid g;
+  Op op;
+  const cx<T>* x;
+  const cx<T>* b;
+  Ctl c;
+  int count;
+};
+
+
+struct RcA {
+  Grid g;
+  Op0<double> op;
+  const double2* x;
+  const double2* b;
+  float2* r32;
+  Ctl c;
+  int count;
+};
+
+
+struct UmA {
+  Grid g;
+  double2* x;
+  const float2* e;
+  const int* active;
+};
+
+template <class T>
+struct PaA {
+  Grid g;
+  Grid gc;
+  const cx<T>* ec;
+  cx<T>* xf;
+  const int* active;
+  Xfer xw;
+};
+
 #define NODE_INDEX                                       \
   const int rhs = blockIdx.z;                            \
   const int i = blockIdx.x * BX + threadIdx.x;           \
@@ -95,8 +139,11 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(Grid g, Op op, const cx<T>* 
 
 
 template <class T, class Op>
-__global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const cx<T>* __restrict__ x,
-                                                          const cx<T>* __restrict__ b, Ctl c, int count) {
+__device__ __forceinline__ void k_resnorm_stop_body(uint3 vblk, dim3 vgrid, Grid g, Op op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, Ctl c, int count) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   __shared__ double sh[32];
   PACK_INDEX(T)
   if (!c.active[rhs]) return;   // block-uniform
@@ -118,6 +165,19 @@ __global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const c
     stop_update(c, rhs, v[0], count);
 }
 
+template <class T, class Op>
+__global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, Ctl c, int count) {
+  k_resnorm_stop_body<T, Op>(blockIdx, gridDim, g, op, x, b, c, count);
+}
+
+template <class T, class Op>
+__global__ void __launch_bounds__(BX * BY) k_resnorm_stop_rag(const __grid_constant__ RagLaunch<RsA<T, Op>> L) {
+  uint3 vb;
+  dim3 vg;
+  const RsA<T, Op>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  k_resnorm_stop_body<T, Op>(vb, vg, a.g, a.op, a.x, a.b, a.c, a.count);
+}
+
 // FP64 residual of the refinement loop, written in float for the next
 // complex64 correction cycle, with the stopping test fused.  This pass runs
 // at the FP64 rate, so its FP64 work is kept small: on interior nodes
@@ -126,9 +186,11 @@ __global__ void __launch_bounds__(BX * BY) k_resnorm_stop(Grid g, Op op, const c
 // take Op0::apply5); and the norm is summed from the float residual the
 // pass writes anyway (FP32 within a thread, FP64 across threads), which
 // resolves the stopping test's relative residual to about 1e-7 of itself.
-__global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double> op, const double2* __restrict__ x,
-                                                             const double2* __restrict__ b, float2* __restrict__ r32,
-                                                             Ctl c, int count) {
+__device__ __forceinline__ void k_resid_cast_stop_body(uint3 vblk, dim3 vgrid, Grid g, Op0<double> op, const double2* __restrict__ x, const double2* __restrict__ b, float2* __restrict__ r32, Ctl c, int count) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   __shared__ double sh[32];
   NODE_INDEX
   if (!c.active[rhs]) return;
@@ -166,8 +228,22 @@ __global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double>
     stop_update(c, rhs, v[0], count);
 }
 
-__global__ void __launch_bounds__(BX * BY) k_update_mixed(Grid g, double2* __restrict__ x, const float2* __restrict__ e,
-                                                          const int* __restrict__ active) {
+__global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double> op, const double2* __restrict__ x, const double2* __restrict__ b, float2* __restrict__ r32, Ctl c, int count) {
+  k_resid_cast_stop_body(blockIdx, gridDim, g, op, x, b, r32, c, count);
+}
+
+__global__ void __launch_bounds__(BX * BY) k_resid_cast_stop_rag(const __grid_constant__ RagLaunch<RcA> L) {
+  uint3 vb;
+  dim3 vg;
+  const RcA& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  k_resid_cast_stop_body(vb, vg, a.g, a.op, a.x, a.b, a.r32, a.c, a.count);
+}
+
+__device__ __forceinline__ void k_update_mixed_body(uint3 vblk, dim3 vgrid, Grid g, double2* __restrict__ x, const float2* __restrict__ e, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   NODE_INDEX
   if (active && !active[rhs]) return;
   if (i > g.nx) return;
@@ -180,6 +256,17 @@ __global__ void __launch_bounds__(BX * BY) k_update_mixed(Grid g, double2* __res
     xv.y += (double)d.y;
     x[p] = xv;
   }
+}
+
+__global__ void __launch_bounds__(BX * BY) k_update_mixed(Grid g, double2* __restrict__ x, const float2* __restrict__ e, const int* __restrict__ active) {
+  k_update_mixed_body(blockIdx, gridDim, g, x, e, active);
+}
+
+__global__ void __launch_bounds__(BX * BY) k_update_mixed_rag(const __grid_constant__ RagLaunch<UmA> L) {
+  uint3 vb;
+  dim3 vg;
+  const UmA& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  k_update_mixed_body(vb, vg, a.g, a.x, a.e, a.active);
 }
 
 // ||v|| per RHS into out[rhs] (one kernel, last-block finish).
@@ -231,9 +318,11 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(Grid gf, Grid g, const cx<
 
 // x_f(i,j) += sum_{I,J} P(i,I) P(j,J) e_c(I,J)   (Eq. (xex) in each direction)
 template <class T>
-__global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const cx<T>* __restrict__ ec,
-                                                         cx<T>* __restrict__ xf, const int* __restrict__ active,
-                                                         Xfer xw) {
+__device__ __forceinline__ void k_prolong_add_body(uint3 vblk, dim3 vgrid, Grid g, Grid gc, const cx<T>* __restrict__ ec, cx<T>* __restrict__ xf, const int* __restrict__ active, Xfer xw) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   PACK_INDEX(T)
   const T c0 = T(xw.w0), c1 = T(xw.w1), c2 = T(xw.w2);
   if (active && !active[rhs]) return;
@@ -262,6 +351,19 @@ __global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const 
     }
     store_pack(xf + off, p, xv, nv);
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_prolong_add(Grid g, Grid gc, const cx<T>* __restrict__ ec, cx<T>* __restrict__ xf, const int* __restrict__ active, Xfer xw) {
+  k_prolong_add_body<T>(blockIdx, gridDim, g, gc, ec, xf, active, xw);
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX * BY) k_prolong_add_rag(const __grid_constant__ RagLaunch<PaA<T>> L) {
+  uint3 vb;
+  dim3 vg;
+  const PaA<T>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  k_prolong_add_body<T>(vb, vg, a.g, a.gc, a.ec, a.xf, a.active, a.xw);
 }
 
 template <class T>
@@ -388,6 +490,102 @@ template <class T> void launch_pack(const Grid& g, const double2* user, cx<T>* v
 template <class T> void launch_unpack(const Grid& g, const cx<T>* v, double2* user, int B, int conj, cudaStream_t s) {
   k_unpack<T><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, v, user, conj);
 }
+// ---- flattened launches over the problems of a ragged batch (ragged.cuh) ----
+
+template <class T>
+__global__ void __launch_bounds__(256) k_zero_rag(const __grid_constant__ RagLaunch<RagVec> L) {
+  uint3 vb;
+  dim3 vg;
+  const RagVec& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  if (a.active && !a.active[0]) return;
+  cx<T>* v = (cx<T>*)a.v;
+  const long long i0 = (long long)vb.x * 1024 + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const long long i = i0 + 256 * k;
+    if (i < a.g.vstride) v[i] = mk<T>(T(0), T(0));
+  }
+}
+
+template <class T> void launch_zero_rag(const std::vector<RagVec>& v, cudaStream_t s) {
+  rag_launch<RagVec>((int)v.size(), k_zero_rag<T>, dim3(256), 0, s, [&](int q, RagVec& a, int& gx, int&) {
+    a = v[q];
+    gx = (int)cdiv(v[q].g.vstride, (long long)1024);
+    return true;
+  });
+}
+template void launch_zero_rag<double>(const std::vector<RagVec>&, cudaStream_t);
+template void launch_zero_rag<float>(const std::vector<RagVec>&, cudaStream_t);
+
+template <class T> void launch_prolong_add_rag(const std::vector<RagXfer<T>>& v, const Xfer& xw, cudaStream_t s) {
+  rag_launch<PaA<T>>((int)v.size(), k_prolong_add_rag<T>, dim3(BX, BY), 0, s, [&](int q, PaA<T>& a, int& gx, int& gy) {
+    const RagXfer<T>& X = v[q];
+    a = PaA<T>{X.gf, X.gc, X.rc, X.xf, X.active, xw};
+    const dim3 d = pack_grid(X.gf, 1, PK<T>::NP);
+    gx = (int)d.x;
+    gy = (int)d.y;
+    return true;
+  });
+}
+template void launch_prolong_add_rag<double>(const std::vector<RagXfer<double>>&, const Xfer&, cudaStream_t);
+template void launch_prolong_add_rag<float>(const std::vector<RagXfer<float>>&, const Xfer&, cudaStream_t);
+
+void launch_update_mixed_rag(const std::vector<RagOuter>& v, cudaStream_t s) {
+  rag_launch<UmA>((int)v.size(), k_update_mixed_rag, dim3(BX, BY), 0, s, [&](int q, UmA& a, int& gx, int& gy) {
+    const RagOuter& O = v[q];
+    a = UmA{O.g, O.x, O.e, O.c.active};
+    const dim3 d = node_grid(O.g, 1);
+    gx = (int)d.x;
+    gy = (int)d.y;
+    return true;
+  });
+}
+
+void launch_resid_cast_stop_rag(const std::vector<RagOuter>& v, int count, cudaStream_t s) {
+  rag_launch<RcA>((int)v.size(), k_resid_cast_stop_rag, dim3(BX, BY), 0, s, [&](int q, RcA& a, int& gx, int& gy) {
+    const RagOuter& O = v[q];
+    a = RcA{O.g, O.op, O.x, O.b, O.r32, O.c, count};
+    const dim3 d = node_grid(O.g, 1);
+    gx = (int)d.x;
+    gy = (int)d.y;
+    return true;
+  });
+}
+
+void launch_resnorm_stop_rag(const std::vector<RagOuter>& v, int count, cudaStream_t s) {
+  using A = RsA<double, Op0<double>>;
+  rag_launch<A>((int)v.size(), k_resnorm_stop_rag<double, Op0<double>>, dim3(BX, BY), 0, s,
+                [&](int q, A& a, int& gx, int& gy) {
+                  const RagOuter& O = v[q];
+                  a = A{O.g, O.op, O.x, O.b, O.c, count};
+                  const dim3 d = pack_grid(O.g, 1, PK<double>::NP);
+                  gx = (int)d.x;
+                  gy = (int)d.y;
+                  return true;
+                });
+}
+
+struct GatherArgs {
+  int np;
+  const int* counts[RMAXP];
+};
+__global__ void k_gather_counts(const __grid_constant__ GatherArgs a, int* __restrict__ out, int stride) {
+  const int p = threadIdx.x;
+  if (p < a.np) {
+    out[p] = a.counts[p][0];
+    out[stride + p] = a.counts[p][1];
+  }
+}
+void launch_gather_counts(const std::vector<const int*>& counts, int* out, cudaStream_t s) {
+  const int n = (int)counts.size();
+  for (int q0 = 0; q0 < n; q0 += RMAXP) {
+    GatherArgs a{};
+    a.np = std::min(RMAXP, n - q0);
+    for (int q = 0; q < a.np; ++q) a.counts[q] = counts[q0 + q];
+    k_gather_counts<<<1, RMAXP, 0, s>>>(a, out + q0, n);
+  }
+}
+
 void launch_gradient(int nx, int ny, double h, const double* m, double omega_f, const double2* u, const double2* lam,
                      int nsrc, double* g, cudaStream_t s) {
   k_gradient<<<dim3(cdiv(nx + 1, BX), cdiv(ny + 1, BY)), dim3(BX, BY), 0, s>>>(nx, ny, h, m, omega_f, u, lam, nsrc, g);

@@ -17,6 +17,8 @@
 
 #include "gmres.cuh"
 #include "internal.h"
+#include "ragged.cuh"
+#include "ragged_api.h"
 
 namespace hmg {
 
@@ -28,6 +30,27 @@ struct KGeo {
   int ncw;      // 32-column groups
   int ch;       // rows per chunk
   int nchunks;
+};
+
+// Arguments of the column marches for one problem (the flattened launches of a
+// ragged batch carry one per problem); each kernel reads the fields it takes.
+template <class T, int R> struct KmA {
+  Grid g;
+  KGeo kg;
+  OpK<T, R> op;
+  const cx<T>* x;
+  const cx<T>* b;
+  cx<T>* u0;
+  cx<T>* u1;
+  cx<T>* u2;
+  cx<T>* w;
+  const cx<T>* win;
+  cx<T>* uJ;
+  cx<T>* wout;
+  double* st;
+  double* partial;
+  unsigned* tickets;
+  const int* active;
 };
 
 template <int P, int K, class F> __device__ __forceinline__ void kmarch_phases(int r, int last, F& f) {
@@ -230,9 +253,11 @@ template <class T, int R> struct KRing {
 
 // u0 = b - A x, partial |u0|^2 (as g_init)
 template <class T, int R>
-__global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ x,
-                                              const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
-                                              double* partial, unsigned* tickets, const int* __restrict__ active) {
+__device__ __forceinline__ void km_init_body(uint3 vblk, dim3 vgrid, Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st, double* partial, unsigned* tickets, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   KPRO
   T a0[1] = {T(0)};
   if (has) {
@@ -255,12 +280,26 @@ __global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op
     fin_init<T>(st + (long long)rhs * GS, v);
 }
 
+template <class T, int R>
+__global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st, double* partial, unsigned* tickets, const int* __restrict__ active) {
+  km_init_body<T, R>(blockIdx, gridDim, g, kg, op, x, b, u0, st, partial, tickets, active);
+}
+
+template <class T, int R>
+__global__ void __launch_bounds__(KW * 32) km_init_rag(const __grid_constant__ RagLaunch<KmA<T, R>> L) {
+  uint3 vb;
+  dim3 vg;
+  const KmA<T, R>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  km_init_body<T, R>(vb, vg, a.g, a.kg, a.op, a.x, a.b, a.u0, a.st, a.partial, a.tickets, a.active);
+}
+
 // w = s_J A u_J; partial dots <u_l, w>, l <= J (as g_arn_a)
 template <class T, int R, int J>
-__global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ u0,
-                                               const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
-                                               cx<T>* __restrict__ w, double* __restrict__ st, double* partial,
-                                               unsigned* tickets, const int* __restrict__ active) {
+__device__ __forceinline__ void km_arn_a_body(uint3 vblk, dim3 vgrid, Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2, cx<T>* __restrict__ w, double* __restrict__ st, double* partial, unsigned* tickets, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   KPRO
   double* S = st + (long long)rhs * GS;
   if (S[G_BRK] != 0.0 || S[G_M] < J) return;   // uniform per RHS
@@ -293,6 +332,19 @@ __global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> o
   double v[2 * (J + 1)];
   if (reduce_last<2 * (J + 1), T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
     staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
+}
+
+template <class T, int R, int J>
+__global__ void __launch_bounds__(KW * 32) km_arn_a(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2, cx<T>* __restrict__ w, double* __restrict__ st, double* partial, unsigned* tickets, const int* __restrict__ active) {
+  km_arn_a_body<T, R, J>(blockIdx, gridDim, g, kg, op, u0, u1, u2, w, st, partial, tickets, active);
+}
+
+template <class T, int R, int J>
+__global__ void __launch_bounds__(KW * 32) km_arn_a_rag(const __grid_constant__ RagLaunch<KmA<T, R>> L) {
+  uint3 vb;
+  dim3 vg;
+  const KmA<T, R>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  km_arn_a_body<T, R, J>(vb, vg, a.g, a.kg, a.op, a.u0, a.u1, a.u2, a.w, a.st, a.partial, a.tickets, a.active);
 }
 
 // ---------------------------------------------------------------- fused passes
@@ -407,11 +459,11 @@ template <class T, int R, int NS> struct KRingF {
 // Resident blocks per SM the register budget must allow: as many as the
 // shared memory holds (six for radius 2 with J = 1, five otherwise).
 template <class T, int R, int J>
-__global__ void __launch_bounds__(KW * 32, R == 2 && J == 1 ? 6 : 5) km_arn_ab(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ win,
-                                                const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1,
-                                                cx<T>* __restrict__ uJ, cx<T>* __restrict__ wout,
-                                                double* __restrict__ st, double* partial, unsigned* tickets,
-                                                const int* __restrict__ active) {
+__device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ win, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, cx<T>* __restrict__ uJ, cx<T>* __restrict__ wout, double* __restrict__ st, double* partial, unsigned* tickets, const int* __restrict__ active) {
+  const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
+  const dim3 gridDim = vgrid;
+  (void)blockIdx;
+  (void)gridDim;
   constexpr int NS = J + 1;             // staged: w, u_0 .. u_{J-1}
   constexpr int NB = 1 + 2 * J;         // fin_b<J-1>: |u_J|^2, <u_J, u_l> (l < J)
   constexpr int NA = 2 * (J + 1);       // fin_a<J>: <u_l, w'> (l <= J)
@@ -497,6 +549,19 @@ __global__ void __launch_bounds__(KW * 32, R == 2 && J == 1 ? 6 : 5) km_arn_ab(G
         fin_a<J, T>(s, d);
       }
     });
+}
+
+template <class T, int R, int J>
+__global__ void __launch_bounds__(KW * 32, R == 2 && J == 1 ? 6 : 5) km_arn_ab(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ win, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1, cx<T>* __restrict__ uJ, cx<T>* __restrict__ wout, double* __restrict__ st, double* partial, unsigned* tickets, const int* __restrict__ active) {
+  km_arn_ab_body<T, R, J>(blockIdx, gridDim, g, kg, op, win, u0, u1, uJ, wout, st, partial, tickets, active);
+}
+
+template <class T, int R, int J>
+__global__ void __launch_bounds__(KW * 32, R == 2 && J == 1 ? 6 : 5) km_arn_ab_rag(const __grid_constant__ RagLaunch<KmA<T, R>> L) {
+  uint3 vb;
+  dim3 vg;
+  const KmA<T, R>& a = L.a[rag_problem(L, blockIdx.x, vb, vg)];
+  km_arn_ab_body<T, R, J>(vb, vg, a.g, a.kg, a.op, a.win, a.u0, a.u1, a.uJ, a.wout, a.st, a.partial, a.tickets, a.active);
 }
 
 constexpr int KCH[] = {64, 48, 32, 24, 16, 12, 8};   // candidate rows per chunk
@@ -613,6 +678,76 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
     run(with_rows(OpK<T, 3>{opv.gx, opv.wx, opv.hy, opv.wy, opv.dinv, g.nx, g.ny}), std::integral_constant<int, 3>{});
 }
 
+// The same smoothing steps on every problem of a ragged batch (the problems'
+// levels at the same depth share the radius): each kernel of a step is one
+// flattened launch over the problems' own chunk geometries.
+template <class T>
+void gmres_smooth_kron_rag(const std::vector<RagLevel<T>>& v, int nu, cudaStream_t s) {
+  if (v.empty()) return;
+  const int n = (int)v.size();
+  auto run = [&](auto rad) {
+    constexpr int R = decltype(rad)::value;
+    const bool fused = KFUSE<T> && v[0].gb.w2 != nullptr;
+    std::vector<KmA<T, R>> A(n);
+    for (int q = 0; q < n; ++q) {
+      const RagLevel<T>& L = v[q];
+      const OpView<T>& o = L.op;
+      OpK<T, R> op{o.gx, o.wx, o.hy, o.wy, o.dinv, L.g.nx, L.g.ny};
+      op.ty0 = o.ty0;
+      op.ty1 = o.ty1;
+      for (int k = 0; k < 2 * R + 1; ++k) {
+        op.hyc[k] = o.hyc[k];
+        op.wyc[k] = o.wyc[k];
+      }
+      const KGeo kg = kron_geo(L.g, 1, R, kron_capacity<T, R>(fused));
+      A[q] = KmA<T, R>{L.g, kg, op, L.x, L.b, (cx<T>*)L.gb.u[0], (cx<T>*)L.gb.u[1], (cx<T>*)L.gb.u[2],
+                       (cx<T>*)L.gb.w, nullptr, nullptr, nullptr, L.gb.st, L.gb.partial, L.gb.tickets, L.active};
+    }
+    auto launch = [&](auto kern, auto set) {
+      rag_launch<KmA<T, R>>(n, kern, dim3(KW * 32), 0, s, [&](int q, KmA<T, R>& a, int& gx, int&) {
+        a = A[q];
+        set(a, v[q]);
+        gx = cdiv((long long)a.kg.ncw * a.kg.nchunks, KW);
+        return true;
+      });
+    };
+    auto none = [](KmA<T, R>&, const RagLevel<T>&) {};
+    for (int step = 0; step < nu; ++step) {
+      launch(km_init_rag<T, R>, none);
+      launch(km_arn_a_rag<T, R, 0>, none);
+      bool done = false;
+      if constexpr (KFUSE<T>) {
+        if (fused) {   // arn_b<0> + arn_a<1>, arn_b<1> + arn_a<2>, as gmres_smooth_kron
+          launch(km_arn_ab_rag<T, R, 1>, [](KmA<T, R>& a, const RagLevel<T>& L) {
+            a.win = (const cx<T>*)L.gb.w;
+            a.uJ = (cx<T>*)L.gb.u[1];
+            a.wout = (cx<T>*)L.gb.w2;
+          });
+          launch(km_arn_ab_rag<T, R, 2>, [](KmA<T, R>& a, const RagLevel<T>& L) {
+            a.win = (const cx<T>*)L.gb.w2;
+            a.uJ = (cx<T>*)L.gb.u[2];
+            a.wout = (cx<T>*)L.gb.w;
+          });
+          launch_arn_b_rag<T, 2>(v, false, 2, s);
+          done = true;
+        }
+      }
+      if (!done) {
+        launch_arn_b_rag<T, 0>(v, true, -1, s);
+        launch(km_arn_a_rag<T, R, 1>, none);
+        launch_arn_b_rag<T, 1>(v, true, -1, s);
+        launch(km_arn_a_rag<T, R, 2>, none);
+        launch_arn_b_rag<T, 2>(v, false, -1, s);
+      }
+      launch_gmres_update_rag<T>(v, s);
+    }
+  };
+  if (v[0].op.kind == 4) run(std::integral_constant<int, 2>{});
+  else run(std::integral_constant<int, 3>{});
+}
+
+template void gmres_smooth_kron_rag<double>(const std::vector<RagLevel<double>>&, int, cudaStream_t);
+template void gmres_smooth_kron_rag<float>(const std::vector<RagLevel<float>>&, int, cudaStream_t);
 template void gmres_smooth_kron<double>(const Grid&, const OpView<double>&, double2*, const double2*, int, int,
                                         const int*, const GmresBufs&, cudaStream_t);
 template void gmres_smooth_kron<float>(const Grid&, const OpView<float>&, float2*, const float2*, int, int,

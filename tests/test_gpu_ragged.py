@@ -1,8 +1,11 @@
 """Ragged batch: problems of different sizes in one handle; each problem's
-result and cycle count must equal the oracle's solve of that problem alone."""
+result and cycle count must equal the oracle's solve of that problem alone,
+whether the batch runs one flattened launch per kernel over all problems or
+one cycle graph per problem (the two agree bit for bit)."""
 import numpy as np
 import pytest
 
+import parity_util as pu
 import synth
 from oracle import cycle as ocycle
 from oracle import hierarchy as ohier
@@ -35,4 +38,67 @@ def test_ragged_batch_matches_oracle_per_problem(smoother, beta2):
         x = xs[p].cpu().numpy().ravel()
         bound = 1e-10 if smoother == "jacobi" else 1e-6
         assert np.linalg.norm(x - ref.x) <= bound * np.linalg.norm(ref.x), p
+    rs.close()
+
+
+# Problems large enough that the flattened launches cover the fine level's
+# row marches, Kronecker levels of both radii and the coarse-cycle launch.
+FLAT_SIZES = [(160, 160, 100.0), (128, 64, 80.0), (96, 96, 60.0), (32, 32, 20.0), (64, 128, 70.0)]
+
+
+def _ragged(sizes, **kw):
+    probs, rhs = [], []
+    for q, (nx, ny, k) in enumerate(sizes):
+        h = 1.0 / max(nx, ny)
+        probs.append((nx, ny, h, k))
+        b = synth.point_source(nx, ny, h) + 1e-2 * synth.random_complex((ny + 1, nx + 1), 40 + q) / h**2
+        rhs.append(torch.from_numpy(b).cuda())
+    beta2 = [1.0 / k for _, _, k in sizes]
+    return probs, rhs, beta2
+
+
+@pytest.mark.parametrize("precision,cycle", [("fp64", "V"), ("mixed", "V"), ("fp64", "W")])
+def test_flattened_launches_equal_per_problem_graphs(precision, cycle):
+    """One launch per kernel over all problems (flat=1) computes, problem by
+    problem, bit for bit what each problem's own cycle graph computes
+    (flat=0): the same kernel bodies on the same geometries, with every
+    reduction in a fixed order."""
+    probs, rhs, beta2 = _ragged(FLAT_SIZES)
+    out = []
+    for flat in (1, 0):
+        rs = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision=precision,
+                             cycle=cycle, march=1, flat=flat)
+        xs, st, cyc, rr = rs.solve(rhs, tol=1e-8)
+        assert st == hm.MG_OK
+        out.append(([x.cpu().numpy() for x in xs], cyc, rr))
+        rs.close()
+    (x1, c1, r1), (x0, c0, r0) = out
+    assert c1 == c0 and r1 == r0
+    for p in range(len(probs)):
+        assert np.array_equal(x1[p], x0[p]), p
+
+
+def test_flattened_ragged_matches_oracle():
+    """FP64, flattened: one cycle from x = 0 equals each problem's oracle
+    iterate to 1e-10 node by node, and the whole solve takes each problem's
+    oracle cycle count."""
+    probs, rhs, beta2 = _ragged(FLAT_SIZES)
+    opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
+    refs = []
+    for p, (nx, ny, h, k) in enumerate(probs):
+        H = ohier.build_hierarchy(nx, ny, h, k, beta2[p])
+        refs.append(ocycle.mg_solve(H, rhs[p].cpu().numpy().ravel(), 1e-7, opt, keep_iterates=True))
+    rs1 = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, max_cycles=1)
+    xs, st, cyc, rr = rs1.solve(rhs, tol=1e-300)
+    assert st == hm.MG_EMAXIT and all(c == 1 for c in cyc)
+    for p, (nx, ny, h, k) in enumerate(probs):
+        pu.assert_close(xs[p].cpu().numpy(), refs[p].iterates[0].reshape(ny + 1, nx + 1), 1e-10, (ny + 1, nx + 1),
+                        f"problem {p}")
+    rs1.close()
+    rs = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2)
+    xs, st, cyc, rr = rs.solve(rhs, tol=1e-7)
+    assert st == hm.MG_OK
+    for p in range(len(probs)):
+        assert cyc[p] == refs[p].cycles, p
+        pu.assert_close(xs[p].cpu().numpy().ravel(), refs[p].x, 1e-6, None, f"problem {p}")
     rs.close()
