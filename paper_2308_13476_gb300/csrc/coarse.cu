@@ -29,94 +29,112 @@ namespace hmg {
   const int j = q / n1_;           \
   const int p = (L).g.at(i, j);
 
+// Arnoldi step J of GMRES(3) inside one CTA: w = s_J A u_J, the Gram-form
+// MGS coefficients (fin_a), u_{J+1} = w - sum_l h_lJ v_l and its norm and
+// Gram entries (fin_b).  The per-RHS state S lives in shared memory in the
+// working precision T: the scalar steps compute in T and store T values, so
+// this is the same arithmetic as with FP64 storage, and with T = float no
+// thread issues FP64 instructions outside the block sums (the FP64 pipe is
+// narrow).  Returns false, block-uniformly, once the Arnoldi process has
+// stopped (breakdown, or fewer than J columns).
+template <int J, class T>
+__device__ __forceinline__ bool cta_arnoldi(const CLevel<T>& L, cx<T>* const (&u)[3], cx<T>* w, T* S, double* sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (S[G_BRK] != T(0) || S[G_M] < T(J)) return false;   // uniform: shared state after a barrier
+  const T sJ = S[G_S + J];
+  constexpr int ND = 2 * (J + 1);
+  T dt[ND];
+#pragma unroll
+  for (int l = 0; l < ND; ++l) dt[l] = T(0);
+  CTA_NODES(L) {
+    CTA_IJP(L)
+    const cx<T> a = scl<T>(sJ, lv_apply<T>(L, u[J], p, i, j));
+    w[p] = a;
+#pragma unroll
+    for (int l = 0; l <= J; ++l) {
+      const cx<T> e = cmul<T>(u[l][p], a);
+      dt[2 * l] += e.x;
+      dt[2 * l + 1] += e.y;
+    }
+  }
+  {
+    double d[ND];
+    block_sum_t<ND, T>(dt, sh, d);
+    if (tid == 0) fin_a<J, T, T>(S, d);
+    __syncthreads();
+  }
+  cx<T> c[J + 1];
+#pragma unroll
+  for (int l = 0; l <= J; ++l) {
+    const T sl = S[G_S + l];
+    c[l] = mk<T>(S[G_H + 2 * (l * 3 + J)] * sl, S[G_H + 2 * (l * 3 + J) + 1] * sl);
+  }
+  constexpr int NE = J < 2 ? 1 + 2 * (J + 1) : 1;
+  T et[NE];
+#pragma unroll
+  for (int l = 0; l < NE; ++l) et[l] = T(0);
+  CTA_NODES(L) {
+    CTA_IJP(L)
+    cx<T> a = w[p];
+    cx<T> uu[J + 1];
+#pragma unroll
+    for (int l = 0; l <= J; ++l) {
+      uu[l] = u[l][p];
+      a = sub<T>(a, mul<T>(c[l], uu[l]));
+    }
+    et[0] += abs2<T>(a);
+    if constexpr (J < 2) {
+      u[J + 1][p] = a;
+#pragma unroll
+      for (int l = 0; l <= J; ++l) {
+        const cx<T> e = cmul<T>(a, uu[l]);
+        et[1 + 2 * l] += e.x;
+        et[2 + 2 * l] += e.y;
+      }
+    }
+  }
+  {
+    double e[NE];
+    block_sum_t<NE, T>(et, sh, e);
+    if (tid == 0) fin_b<J, T, T>(S, e);
+    __syncthreads();
+  }
+  return true;
+}
+
 template <class T>
-__device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, double* S, double* sh) {
+__device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, T* S, double* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const cx<T>* b = L.b + off;
-  cx<T>* u[3] = {L.u[0] + off, L.u[1] + off, L.u[2] + off};
+  cx<T>* const u[3] = {L.u[0] + off, L.u[1] + off, L.u[2] + off};
   cx<T>* w = L.w + off;
   for (int step = 0; step < nu; ++step) {
-    T a0 = T(0);
+    T a0[1] = {T(0)};
     CTA_NODES(L) {
       CTA_IJP(L)
       const cx<T> r = sub<T>(b[p], lv_apply<T>(L, x, p, i, j));
       u[0][p] = r;
-      a0 += abs2<T>(r);
+      a0[0] += abs2<T>(r);
     }
     {
-      double t[1] = {(double)a0};
-      block_sum<1>(t, sh);
-      if (tid == 0) fin_init<T>(S, t);
+      double t[1];
+      block_sum_t<1, T>(a0, sh, t);
+      if (tid == 0) fin_init<T, T>(S, t);
       __syncthreads();
     }
-#pragma unroll
-    for (int J = 0; J < 3; ++J) {
-      if (S[G_BRK] != 0.0 || S[G_M] < J) break;   // uniform: shared state after a barrier
-      const T sJ = (T)S[G_S + J];
-      T dt[6] = {0, 0, 0, 0, 0, 0};
-      CTA_NODES(L) {
-        CTA_IJP(L)
-        const cx<T> a = scl<T>(sJ, lv_apply<T>(L, u[J], p, i, j));
-        w[p] = a;
-        for (int l = 0; l <= J; ++l) {
-          const cx<T> e = cmul<T>(u[l][p], a);
-          dt[2 * l] += e.x;
-          dt[2 * l + 1] += e.y;
-        }
-      }
-      double d[6];
-      for (int l = 0; l < 6; ++l) d[l] = (double)dt[l];
-      block_sum<6>(d, sh);
-      if (tid == 0) {
-        if (J == 0) fin_a<0, T>(S, d);
-        else if (J == 1) fin_a<1, T>(S, d);
-        else fin_a<2, T>(S, d);
-      }
-      __syncthreads();
-      cx<T> c[3];
-      for (int l = 0; l < 3; ++l) {
-        const double sl = S[G_S + l];
-        c[l] = l <= J ? mk<T>((T)(S[G_H + 2 * (l * 3 + J)] * sl), (T)(S[G_H + 2 * (l * 3 + J) + 1] * sl))
-                      : mk<T>(0, 0);
-      }
-      T et[5] = {0, 0, 0, 0, 0};
-      CTA_NODES(L) {
-        CTA_IJP(L)
-        cx<T> a = w[p];
-        cx<T> uu[3];
-        for (int l = 0; l <= J; ++l) {
-          uu[l] = u[l][p];
-          a = sub<T>(a, mul<T>(c[l], uu[l]));
-        }
-        if (J < 2) u[J + 1][p] = a;
-        et[0] += abs2<T>(a);
-        if (J < 2)
-          for (int l = 0; l <= J; ++l) {
-            const cx<T> e = cmul<T>(a, uu[l]);
-            et[1 + 2 * l] += e.x;
-            et[2 + 2 * l] += e.y;
-          }
-      }
-      double e5[5];
-      for (int l = 0; l < 5; ++l) e5[l] = (double)et[l];
-      block_sum<5>(e5, sh);
-      if (tid == 0) {
-        if (J == 0) fin_b<0, T>(S, e5);
-        else if (J == 1) fin_b<1, T>(S, e5);
-        else fin_b<2, T>(S, e5);
-      }
-      __syncthreads();
-    }
+    if (cta_arnoldi<0, T>(L, u, w, S, sh) && cta_arnoldi<1, T>(L, u, w, S, sh)) cta_arnoldi<2, T>(L, u, w, S, sh);
     const int m = (int)S[G_M];
     if (m > 0) {
       cx<T> c[3];
+#pragma unroll
       for (int l = 0; l < 3; ++l) {
-        const double sl = S[G_S + l];
-        c[l] = mk<T>((T)(S[G_Y + 2 * l] * sl), (T)(S[G_Y + 2 * l + 1] * sl));
+        const T sl = S[G_S + l];
+        c[l] = mk<T>(S[G_Y + 2 * l] * sl, S[G_Y + 2 * l + 1] * sl);
       }
       CTA_NODES(L) {
         CTA_IJP(L)
         cx<T> a = x[p];
+#pragma unroll
         for (int l = 0; l < 3; ++l)
           if (l < m) a = fma_c<T>(c[l], u[l][p], a);
         x[p] = a;
@@ -134,7 +152,7 @@ __device__ __forceinline__ void k_coarse_cycle_body(uint3 vblk, dim3 vgrid, cons
   (void)gridDim;
   extern __shared__ double2 rs[];            // coarsest right-hand side, N entries
   __shared__ double sh[NVMAX * 32];
-  __shared__ double S[GS];
+  __shared__ T S[GS];
   const int rhs = blockIdx.x;
   if (active && !active[rhs]) return;
   const int tid = threadIdx.x, nt = blockDim.x;

@@ -213,6 +213,23 @@ template <class T, int R> struct OpK {
   }
 };
 
+// Final stage of the block sums below: value k of the block is the sum of
+// the warps' partial sums sh[k][0..nwarps) added in warp order.  Lane k of
+// warp 0 adds value k, all NV values at once (one FP64 add instruction per
+// warp instead of one per warp and value: the FP64 pipe is narrow), and the
+// totals are shuffled to lane 0.  out is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void warp_sums_to_thread0(const double* sh, int nwarps, int warp, int lane,
+                                                     double (&out)[NV]) {
+  static_assert(NV <= 32, "one lane per value");
+  if (warp != 0) return;
+  double t = 0;
+  if (lane < NV)
+    for (int w = 0; w < nwarps; ++w) t += sh[lane * 32 + w];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = __shfl_sync(0xffffffffu, t, k);
+}
+
 // Block-wide sum of NV doubles; result valid in thread 0.  Fixed shape and
 // order, so results are bitwise reproducible run to run.
 template <int NV>
@@ -228,14 +245,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32
     if (lane == 0) sh[k * 32 + warp] = t;
   }
   __syncthreads();
-  if (tid == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = 0;
-      for (int w = 0; w < nwarps; ++w) t += sh[k * 32 + w];
-      v[k] = t;
-    }
-  }
+  warp_sums_to_thread0<NV>(sh, nwarps, warp, lane, v);
   __syncthreads();
 }
 
@@ -255,15 +265,21 @@ __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double* sh /* [NV]
     if (lane == 0) sh[k * 32 + warp] = (double)t;
   }
   __syncthreads();
-  if (tid == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = 0;
-      for (int w = 0; w < nwarps; ++w) t += sh[k * 32 + w];
-      out[k] = t;
-    }
-  }
+  warp_sums_to_thread0<NV>(sh, nwarps, warp, lane, out);
   __syncthreads();
+}
+
+// Thread tid's share of the partial records q[0..nrec) (NVMAX doubles
+// each) summed in record order tid, tid + nt, ...; the first record is taken
+// as it is rather than added to zero.
+template <int NV>
+__device__ __forceinline__ void last_block_partials(double (&acc)[NV], const double* q, int nrec, int tid, int nt) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = tid < nrec ? __ldcg(q + (long long)tid * NVMAX + k) : 0.0;
+  for (int b = tid + nt; b < nrec; b += nt) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(q + (long long)b * NVMAX + k);
+  }
 }
 
 // Grid-wide deterministic sum of NV doubles for one right-hand side, inside
@@ -293,13 +309,7 @@ __device__ __forceinline__ bool reduce_last(const T (&vin)[NV], double (&v)[NV],
   if (!s_last) return false;
   __threadfence();
   double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int b = tid; b < nblk; b += nt) {
-    const double* q = partial + ((long long)rhs * nblk + b) * NVMAX;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(q + k);
-  }
+  last_block_partials<NV>(acc, partial + (long long)rhs * nblk * NVMAX, nblk, tid, nt);
   block_sum<NV>(acc, sh);
   if (tid == 0) {
 #pragma unroll
@@ -343,13 +353,7 @@ __device__ __forceinline__ bool reduce_last_at(const T (&vin)[NV], double (&v)[N
   if (!s_last) return false;
   __threadfence();
   double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  for (int b = tid; b < nrec; b += nt) {
-    const double* q = partial + ((long long)rhs * nrec + b) * NVMAX;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(q + k);
-  }
+  last_block_partials<NV>(acc, partial + (long long)rhs * nrec * NVMAX, nrec, tid, nt);
   block_sum<NV>(acc, sh);
   if (tid == 0) {
 #pragma unroll

@@ -21,8 +21,10 @@ constexpr int G_BRK = 71;   // 1 = stop (breakdown or beta == 0)
 
 // min || beta e1 - Hbar y || by Givens rotations; Hbar is (m+1) x m.  The
 // arithmetic runs in Ts (FP64 for the complex128 path, FP32 for the
-// complex64 cycles of the mixed path); the state S is stored in FP64.
-template <class Ts> __device__ __forceinline__ void lsq(double* S) {
+// complex64 cycles of the mixed path); the state S is stored in St: FP64 in
+// global memory, or Ts where one thread block owns the state (every stored
+// value is a Ts value, so both storages give the same results).
+template <class Ts, class St = double> __device__ __forceinline__ void lsq(St* S) {
   const int m = (int)S[G_M];
   if (m <= 0) return;
   Ts Hr[4][3], Hi[4][3], gr[4], gi[4];
@@ -77,24 +79,24 @@ template <class Ts> __device__ __forceinline__ void lsq(double* S) {
     yi[c] = (ti * dr - tr * di) / dd;
   }
   for (int c = 0; c < 3; ++c) {
-    S[G_Y + 2 * c] = c < m ? (double)yr[c] : 0.0;
-    S[G_Y + 2 * c + 1] = c < m ? (double)yi[c] : 0.0;
+    S[G_Y + 2 * c] = c < m ? (St)yr[c] : St(0);
+    S[G_Y + 2 * c + 1] = c < m ? (St)yi[c] : St(0);
   }
 }
 
 // ---- scalar steps of one Arnoldi pass, run by one thread ----
 
-template <class Ts> __device__ __forceinline__ void fin_init(double* S, const double* v) {
-  for (int k = 0; k < GS; ++k) S[k] = 0.0;
+template <class Ts, class St = double> __device__ __forceinline__ void fin_init(St* S, const double* v) {
+  for (int k = 0; k < GS; ++k) S[k] = St(0);
   const Ts beta = sqrt((Ts)v[0]);
-  S[G_BETA] = (double)beta;
-  S[G_M] = 0;
-  if (beta == Ts(0)) S[G_BRK] = 1.0;
-  else S[G_S + 0] = (double)(Ts(1) / beta);
+  S[G_BETA] = (St)beta;
+  S[G_M] = St(0);
+  if (beta == Ts(0)) S[G_BRK] = St(1);
+  else S[G_S + 0] = (St)(Ts(1) / beta);
 }
 
 // h_lJ = <v_l, w> - sum_{q<l} h_qJ <v_l, v_q>, with <v_l, w> = s_l <u_l, w>
-template <int J, class Ts> __device__ __forceinline__ void fin_a(double* S, const double* v) {
+template <int J, class Ts, class St = double> __device__ __forceinline__ void fin_a(St* S, const double* v) {
   Ts hr[J + 1], hi[J + 1];
   for (int l = 0; l <= J; ++l) {
     const Ts sl = (Ts)S[G_S + l];
@@ -106,32 +108,32 @@ template <int J, class Ts> __device__ __forceinline__ void fin_a(double* S, cons
     }
     hr[l] = dr;
     hi[l] = di;
-    S[G_H + 2 * (l * 3 + J)] = (double)dr;
-    S[G_H + 2 * (l * 3 + J) + 1] = (double)di;
+    S[G_H + 2 * (l * 3 + J)] = (St)dr;
+    S[G_H + 2 * (l * 3 + J) + 1] = (St)di;
   }
 }
 
 // h_{J+1,J} = ||u_{J+1}||, breakdown test, Gram entries of v_{J+1}; the least
 // squares problem is solved once the Arnoldi process stops.
-template <int J, class Ts> __device__ __forceinline__ void fin_b(double* S, const double* v) {
+template <int J, class Ts, class St = double> __device__ __forceinline__ void fin_b(St* S, const double* v) {
   const Ts hn = sqrt((Ts)v[0]);
-  S[G_H + 2 * ((J + 1) * 3 + J)] = (double)hn;
-  S[G_H + 2 * ((J + 1) * 3 + J) + 1] = 0.0;
-  S[G_M] = J + 1;
+  S[G_H + 2 * ((J + 1) * 3 + J)] = (St)hn;
+  S[G_H + 2 * ((J + 1) * 3 + J) + 1] = St(0);
+  S[G_M] = St(J + 1);
   if (hn <= Ts(1e-14) * (Ts)S[G_BETA]) {
-    S[G_BRK] = 1.0;
+    S[G_BRK] = St(1);
   } else {
     const Ts sn = Ts(1) / hn;
-    S[G_S + J + 1] = (double)sn;
+    S[G_S + J + 1] = (St)sn;
     if (J < 2) {
       for (int l = 0; l <= J; ++l) {   // <v_{J+1}, v_l> = s_{J+1} s_l <u_{J+1}, u_l>
         const Ts f = sn * (Ts)S[G_S + l];
-        S[G_G + 2 * ((J + 1) * 4 + l)] = (double)(f * (Ts)v[1 + 2 * l]);
-        S[G_G + 2 * ((J + 1) * 4 + l) + 1] = (double)(f * (Ts)v[2 + 2 * l]);
+        S[G_G + 2 * ((J + 1) * 4 + l)] = (St)(f * (Ts)v[1 + 2 * l]);
+        S[G_G + 2 * ((J + 1) * 4 + l) + 1] = (St)(f * (Ts)v[2 + 2 * l]);
       }
     }
   }
-  if (J == 2 || S[G_BRK] != 0.0) lsq<Ts>(S);
+  if (J == 2 || S[G_BRK] != St(0)) lsq<Ts, St>(S);
 }
 
 // Runs a scalar step on the RHS state in shared memory (all threads of the
