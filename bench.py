@@ -75,8 +75,10 @@ def parse():
     p.add_argument("--max-cycles", type=int, default=2)
     p.add_argument("--flat", type=int, default=1, choices=[0, 1],
                    help="ragged workload: 1 = one flattened launch per kernel over all problems, 0 = a graph per problem")
-    p.add_argument("--coarse-nodes", type=int, default=-1)
-    p.add_argument("--coarse-mode", type=int, default=-1)
+    p.add_argument("--coarse-nodes", type=int, default=-1,
+                   help=">= 0: levels with at most this many nodes run in the coarse-cycle launch (overrides the "
+                        "autotuner's choice)")
+    p.add_argument("--coarse-mode", type=int, default=-1, help=">= 0: coarse-cycle launch organisation (override)")
     p.add_argument("--no-autotune", action="store_true", help="library default launch shapes instead of the autotuner's")
     a = p.parse_args()
     if a.warmup < 3:
@@ -367,6 +369,9 @@ def run_ours(a):
         tuned, _ = autotune.tune(n, n, h, k, a.beta2, rhs, smoother=a.smoother, cycle=a.cycle, nu=a.nu,
                                  precision=a.precision, cache_path=os.path.join(ROOT, "paper_2308_13476_gb300",
                                                                                 "autotune_cache.json"))
+    for name in ("coarse_nodes", "coarse_mode"):   # explicit overrides of the tuned shapes
+        if getattr(a, name) >= 0:
+            tuned = dict(tuned or {}, **{name: getattr(a, name)})
 
     def make(precision, shapes=None):
         t0 = time.perf_counter()

@@ -715,6 +715,22 @@ static void emit_ragged_iteration(mg_ctx* c, cudaStream_t s) {
   cudaMemcpyAsync(c->h_counts, c->d_counts, sizeof(int) * 2 * P, cudaMemcpyDeviceToHost, s);
 }
 
+// Instantiates a captured graph and counts its kernel nodes.
+static mg_status instantiate_graph(cudaGraph_t g, cudaGraphExec_t* exec, long long* kernels) {
+  CK(cudaGraphInstantiate(exec, g, 0));
+  size_t n = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CK(cudaGraphGetNodes(g, nodes.data(), &n));
+  *kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    *kernels += t == cudaGraphNodeTypeKernel;
+  }
+  return MG_OK;
+}
+
 static mg_status capture_ragged(mg_ctx* c) {
   if (c->gexec) return MG_OK;
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -723,18 +739,7 @@ static mg_status capture_ragged(mg_ctx* c) {
   cudaError_t e = cudaStreamEndCapture(c->cap, &g);
   if (e != cudaSuccess) FAIL(MG_ECUDA, "graph capture of the flattened ragged cycle failed: %s", cudaGetErrorString(e));
   c->graph = g;
-  CK(cudaGraphInstantiate(&c->gexec, g, 0));
-  size_t n = 0;
-  CK(cudaGraphGetNodes(g, nullptr, &n));
-  std::vector<cudaGraphNode_t> nodes(n);
-  CK(cudaGraphGetNodes(g, nodes.data(), &n));
-  c->graph_kernels = 0;
-  for (auto nd : nodes) {
-    cudaGraphNodeType t;
-    CK(cudaGraphNodeGetType(nd, &t));
-    c->graph_kernels += t == cudaGraphNodeTypeKernel;
-  }
-  return MG_OK;
+  return instantiate_graph(g, &c->gexec, &c->graph_kernels);
 }
 
 extern "C" {
@@ -1162,18 +1167,7 @@ static mg_status capture(mg_ctx* c) {
   cudaError_t e = cudaStreamEndCapture(c->cap, &g);
   if (e != cudaSuccess) FAIL(MG_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
   c->graph = g;
-  CK(cudaGraphInstantiate(&c->gexec, g, 0));
-  size_t n = 0;
-  CK(cudaGraphGetNodes(g, nullptr, &n));
-  std::vector<cudaGraphNode_t> nodes(n);
-  CK(cudaGraphGetNodes(g, nodes.data(), &n));
-  c->graph_kernels = 0;
-  for (auto nd : nodes) {
-    cudaGraphNodeType t;
-    CK(cudaGraphNodeGetType(nd, &t));
-    c->graph_kernels += t == cudaGraphNodeTypeKernel;
-  }
-  return MG_OK;
+  return instantiate_graph(g, &c->gexec, &c->graph_kernels);
 }
 
 // Graph of one preconditioning cycle for the FGMRES outer loop: the cycle
@@ -1197,18 +1191,7 @@ static mg_status capture_precond(mg_ctx* c) {
   cudaError_t e = cudaStreamEndCapture(c->cap, &g);
   if (e != cudaSuccess) FAIL(MG_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
   c->pgraph = g;
-  CK(cudaGraphInstantiate(&c->pexec, g, 0));
-  size_t n = 0;
-  CK(cudaGraphGetNodes(g, nullptr, &n));
-  std::vector<cudaGraphNode_t> nodes(n);
-  CK(cudaGraphGetNodes(g, nodes.data(), &n));
-  c->pgraph_kernels = 0;
-  for (auto nd : nodes) {
-    cudaGraphNodeType t;
-    CK(cudaGraphNodeGetType(nd, &t));
-    c->pgraph_kernels += t == cudaGraphNodeTypeKernel;
-  }
-  return MG_OK;
+  return instantiate_graph(g, &c->pexec, &c->pgraph_kernels);
 }
 
 // FGMRES(m) with the cycle as the right preconditioner (fgmres.cu): every

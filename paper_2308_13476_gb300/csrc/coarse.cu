@@ -29,13 +29,38 @@ namespace hmg {
   const int j = q / n1_;           \
   const int p = (L).g.at(i, j);
 
+// Block-wide sum in the working precision T: a shuffle tree within each warp,
+// then one over the warps' sums in warp 0.  Fixed shape and order
+// (reproducible); with T = float the interpreter's reductions issue no FP64
+// instructions (the FP64 pipe is narrow and its latency would sit on the
+// interpreter's serial path).  out is valid in thread 0.
+template <int NV, class T>
+__device__ __forceinline__ void cta_sum(const T (&v)[NV], T* sh /* [NV][32] */, T (&out)[NV]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T t = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[k * 32 + warp] = t;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      T t = lane < nwarps ? sh[k * 32 + lane] : T(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      out[k] = t;
+    }
+  }
+}
+
 // Arnoldi step J of GMRES(3) inside one CTA: w = s_J A u_J, the Gram-form
 // MGS coefficients (fin_a), u_{J+1} = w - sum_l h_lJ v_l and its norm and
 // Gram entries (fin_b).  The per-RHS state S lives in shared memory in the
-// working precision T: the scalar steps compute in T and store T values, so
-// this is the same arithmetic as with FP64 storage, and with T = float no
-// thread issues FP64 instructions outside the block sums (the FP64 pipe is
-// narrow).  Returns false, block-uniformly, once the Arnoldi process has
+// working precision T, and the block sums run in T (cta_sum): with T = float
+// the interpreter's GMRES(3) issues no FP64 instruction.  Returns false, block-uniformly, once the Arnoldi process has
 // stopped (breakdown, or fewer than J columns).
 template <int J, class T>
 __device__ __forceinline__ bool cta_arnoldi(const CLevel<T>& L, cx<T>* const (&u)[3], cx<T>* w, T* S, double* sh) {
@@ -58,9 +83,9 @@ __device__ __forceinline__ bool cta_arnoldi(const CLevel<T>& L, cx<T>* const (&u
     }
   }
   {
-    double d[ND];
-    block_sum_t<ND, T>(dt, sh, d);
-    if (tid == 0) fin_a<J, T, T>(S, d);
+    T d[ND];
+    cta_sum<ND, T>(dt, reinterpret_cast<T*>(sh), d);
+    if (tid == 0) fin_a<J, T, T, T>(S, d);
     __syncthreads();
   }
   cx<T> c[J + 1];
@@ -94,9 +119,9 @@ __device__ __forceinline__ bool cta_arnoldi(const CLevel<T>& L, cx<T>* const (&u
     }
   }
   {
-    double e[NE];
-    block_sum_t<NE, T>(et, sh, e);
-    if (tid == 0) fin_b<J, T, T>(S, e);
+    T e[NE];
+    cta_sum<NE, T>(et, reinterpret_cast<T*>(sh), e);
+    if (tid == 0) fin_b<J, T, T, T>(S, e);
     __syncthreads();
   }
   return true;
@@ -117,9 +142,9 @@ __device__ void cta_gmres(const CLevel<T>& L, cx<T>* x, long long off, int nu, T
       a0[0] += abs2<T>(r);
     }
     {
-      double t[1];
-      block_sum_t<1, T>(a0, sh, t);
-      if (tid == 0) fin_init<T, T>(S, t);
+      T t[1];
+      cta_sum<1, T>(a0, reinterpret_cast<T*>(sh), t);
+      if (tid == 0) fin_init<T, T, T>(S, t);
       __syncthreads();
     }
     if (cta_arnoldi<0, T>(L, u, w, S, sh) && cta_arnoldi<1, T>(L, u, w, S, sh)) cta_arnoldi<2, T>(L, u, w, S, sh);

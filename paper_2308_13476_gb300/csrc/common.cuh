@@ -269,6 +269,27 @@ __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double* sh /* [NV]
   __syncthreads();
 }
 
+// The last block's sum over few partial records (nrec <= 32), run by warp 0:
+// the records are staged in shared memory and lane k adds value k over the
+// records in order, all NV values at once (nrec FP64 adds in sequence instead
+// of a shuffle tree of 5 adds per value).  v is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void last_block_sum_few(double (&v)[NV], const double* q, int nrec, double* sh, int lane) {
+  static_assert(NV <= NVMAX, "record size");
+  for (int e = lane; e < nrec * NV; e += 32) {
+    const int b = e / NV, k = e - b * NV;
+    sh[e] = __ldcg(q + (long long)b * NVMAX + k);
+  }
+  __syncwarp();
+  double t = 0.0;
+  if (lane < NV) {
+    t = sh[lane];
+    for (int b = 1; b < nrec; ++b) t += sh[b * NV + lane];
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = __shfl_sync(0xffffffffu, t, k);
+}
+
 // Thread tid's share of the partial records q[0..nrec) (NVMAX doubles
 // each) summed in record order tid, tid + nt, ...; the first record is taken
 // as it is rather than added to zero.
@@ -308,6 +329,11 @@ __device__ __forceinline__ bool reduce_last(const T (&vin)[NV], double (&v)[NV],
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
+  if (nblk <= 32) {   // block-uniform
+    if (tid < 32) last_block_sum_few<NV>(v, partial + (long long)rhs * nblk * NVMAX, nblk, sh, tid);
+    if (tid == 0) tickets[rhs] = 0u;
+    return true;
+  }
   double acc[NV];
   last_block_partials<NV>(acc, partial + (long long)rhs * nblk * NVMAX, nblk, tid, nt);
   block_sum<NV>(acc, sh);
@@ -352,6 +378,11 @@ __device__ __forceinline__ bool reduce_last_at(const T (&vin)[NV], double (&v)[N
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
+  if (nrec <= 32) {   // block-uniform
+    if (tid < 32) last_block_sum_few<NV>(v, partial + (long long)rhs * nrec * NVMAX, nrec, sh, tid);
+    if (tid == 0) tickets[rhs] = 0u;
+    return true;
+  }
   double acc[NV];
   last_block_partials<NV>(acc, partial + (long long)rhs * nrec * NVMAX, nrec, tid, nt);
   block_sum<NV>(acc, sh);

@@ -23,7 +23,9 @@ constexpr int G_BRK = 71;   // 1 = stop (breakdown or beta == 0)
 // arithmetic runs in Ts (FP64 for the complex128 path, FP32 for the
 // complex64 cycles of the mixed path); the state S is stored in St: FP64 in
 // global memory, or Ts where one thread block owns the state (every stored
-// value is a Ts value, so both storages give the same results).
+// value is a Ts value, so both storages give the same results).  The summed
+// inputs v of the fin_* steps come in V: FP64 from the grid-wide sums, Ts
+// from the block sums of the coarse-cycle interpreter.
 template <class Ts, class St = double> __device__ __forceinline__ void lsq(St* S) {
   const int m = (int)S[G_M];
   if (m <= 0) return;
@@ -86,7 +88,7 @@ template <class Ts, class St = double> __device__ __forceinline__ void lsq(St* S
 
 // ---- scalar steps of one Arnoldi pass, run by one thread ----
 
-template <class Ts, class St = double> __device__ __forceinline__ void fin_init(St* S, const double* v) {
+template <class Ts, class St = double, class V = double> __device__ __forceinline__ void fin_init(St* S, const V* v) {
   for (int k = 0; k < GS; ++k) S[k] = St(0);
   const Ts beta = sqrt((Ts)v[0]);
   S[G_BETA] = (St)beta;
@@ -96,7 +98,7 @@ template <class Ts, class St = double> __device__ __forceinline__ void fin_init(
 }
 
 // h_lJ = <v_l, w> - sum_{q<l} h_qJ <v_l, v_q>, with <v_l, w> = s_l <u_l, w>
-template <int J, class Ts, class St = double> __device__ __forceinline__ void fin_a(St* S, const double* v) {
+template <int J, class Ts, class St = double, class V = double> __device__ __forceinline__ void fin_a(St* S, const V* v) {
   Ts hr[J + 1], hi[J + 1];
   for (int l = 0; l <= J; ++l) {
     const Ts sl = (Ts)S[G_S + l];
@@ -115,7 +117,7 @@ template <int J, class Ts, class St = double> __device__ __forceinline__ void fi
 
 // h_{J+1,J} = ||u_{J+1}||, breakdown test, Gram entries of v_{J+1}; the least
 // squares problem is solved once the Arnoldi process stops.
-template <int J, class Ts, class St = double> __device__ __forceinline__ void fin_b(St* S, const double* v) {
+template <int J, class Ts, class St = double, class V = double> __device__ __forceinline__ void fin_b(St* S, const V* v) {
   const Ts hn = sqrt((Ts)v[0]);
   S[G_H + 2 * ((J + 1) * 3 + J)] = (St)hn;
   S[G_H + 2 * ((J + 1) * 3 + J) + 1] = St(0);
