@@ -73,8 +73,9 @@ def parse():
     p.add_argument("--probe", action="store_true",
                    help="profiling probe: set up the workload and run two solves capped at --max-cycles; no timing")
     p.add_argument("--max-cycles", type=int, default=2)
-    p.add_argument("--flat", type=int, default=1, choices=[0, 1],
-                   help="ragged workload: 1 = one flattened launch per kernel over all problems, 0 = a graph per problem")
+    p.add_argument("--flat", type=int, default=0, choices=[0, 1],
+                   help="ragged workload: 0 = problems of one shape batched, a graph per group (library default); "
+                        "1 = one flattened launch per kernel over all problems")
     p.add_argument("--coarse-nodes", type=int, default=-1,
                    help=">= 0: levels with at most this many nodes run in the coarse-cycle launch (overrides the "
                         "autotuner's choice)")

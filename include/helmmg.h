@@ -118,22 +118,26 @@ typedef struct {
                        (paper default); 1 = linear interpolation, the
                        "Linear" column of Table conv1 (an ablation: the paper
                        finds the two-grid map no longer contracting)      */
-  int flat;         /* ragged batches: 1 = every kernel of a cycle is one
-                       launch over all problems of the batch (their blocks
-                       numbered one after the other, each problem with its own
-                       grid, geometry and convergence mask) when the options
-                       allow it (GMRES(3), fuse 1, march != 0, precision 0 or 1,
-                       krylov 0, coarse_mode 0 and a coarse_nodes that puts
-                       every problem's coarsest grid in the coarse-cycle
-                       launch); 0 = one cycle graph per problem on its own
-                       stream.  Either way each problem computes the same
-                       values.  Ignored by single-problem handles.         */
+  int flat;         /* ragged batches: 0 = problems with the same grid, cell
+                       size, wavenumber and shift share one hierarchy and are
+                       solved as the right-hand sides of one batched handle,
+                       each handle with its own cycle graph and stream;
+                       1 = every problem has its own hierarchy and every
+                       kernel of a cycle is one launch over all problems
+                       (their blocks numbered one after the other, each
+                       problem with its own grid, geometry and convergence
+                       mask) when the options allow it (GMRES(3), fuse 1,
+                       march != 0, precision 0 or 1, krylov 0, coarse_mode 0
+                       and a coarse_nodes that puts every problem's coarsest
+                       grid in the coarse-cycle launch), else one cycle graph
+                       per problem.  Either way each problem computes its own
+                       solve.  Ignored by single-problem handles.         */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
  * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0, fuse 1,
- * tile_rows 0; march -1; krylov 0; transfer 0; flat 1; default stream. */
+ * tile_rows 0; march -1; krylov 0; transfer 0; flat 0; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).
@@ -156,12 +160,15 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
  * the same options and one right-hand side each, so opt->batch must be 1).  mg_solve / mg_adjoint on this handle take rhs and x
  * as the problems' grids packed back to back (problem p starts after
  * sum_{q<p} (nx[q]+1)(ny[q]+1) complex128 values) and report cycles and
- * relative residuals per problem.  Every problem has its own hierarchy.  With
- * opt->flat = 1 (and options that allow it) a cycle of all problems is one
+ * relative residuals per problem.  With opt->flat = 0 (the default)
+ * problems with identical parameters share a hierarchy and are solved as
+ * one batch of right-hand sides (staged side by side in a device buffer the
+ * handle owns); every such group has its own cycle graph and stream
+ * (prioritised by problem size) and starts its next cycle as soon as its
+ * last one has been tested.  With opt->flat = 1 (and options that allow it)
+ * every problem has its own hierarchy and a cycle of all problems is one
  * CUDA graph whose every kernel is a single launch over all problems (a
- * problem that has converged leaves its blocks idle); otherwise every problem
- * has its own cycle graph and stream (prioritised by problem size) and
- * starts its next cycle as soon as its last one has been tested.  Inspection
+ * problem that has converged leaves its blocks idle).  Inspection
  * calls return MG_ESTATE on a ragged handle. */
 mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* ny, const double* h,
                           const double* k_const, const double* beta2, const mg_options* opt);

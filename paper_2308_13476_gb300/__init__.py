@@ -283,9 +283,10 @@ class RaggedSolver:
 
     RaggedSolver(sizes=[(nx, ny, h, k), ...], beta2, **options), beta2 a
     scalar or one shift per problem.  solve() takes and returns a list of
-    complex128 CUDA grids (ny+1, nx+1).  ``flat=1`` (the default) runs a
-    cycle of all problems as one launch per kernel when the options allow
-    it, ``flat=0`` one cycle graph per problem."""
+    complex128 CUDA grids (ny+1, nx+1).  ``flat=0`` (the default) solves
+    problems with identical parameters as one batch of right-hand sides,
+    each group with its own cycle graph; ``flat=1`` runs a cycle of all
+    problems as one launch per kernel when the options allow it."""
 
     def __init__(self, sizes, beta2, **options):
         self.sizes = [(int(a), int(b), float(c), float(d)) for a, b, c, d in sizes]

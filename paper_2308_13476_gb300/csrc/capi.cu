@@ -124,7 +124,9 @@ struct mg_ctx {
   long long graph_kernels = 0;     // kernel nodes in the cycle graph
   long long last_launches = 0, last_graphs = 0;
   int done = 0;                    // cycles of the current solve
-  std::vector<mg_ctx*> sub;        // ragged batch: one handle per problem
+  std::vector<mg_ctx*> sub;        // ragged batch: one handle per group of identical problems
+  std::vector<std::vector<int>> members;  // ragged batch: the problems (caller's indices) of each handle
+  std::vector<double2*> stage;     // ragged batch: per handle of several problems, their rhs and x side by side
   cudaStream_t own_stream = nullptr;
   bool flat = false;               // ragged batch: one flattened launch per kernel over all problems
   int* d_counts = nullptr;         // ragged flat: [2 P] active counts and barrier flags (device)
@@ -762,7 +764,7 @@ void mg_default_options(mg_options* o) {
   o->march = -1;
   o->krylov = 0;
   o->transfer = 0;
-  o->flat = 1;
+  o->flat = 0;
   o->stream = nullptr;
 }
 
@@ -1083,27 +1085,48 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
   if (o.batch != 1) FAIL(MG_EINVAL, "a ragged batch solves one right-hand side per problem (batch must be 1)");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
+  // Problems with the same grid, cell size, wavenumber and shift (compared
+  // bit for bit) share one hierarchy and are solved as the right-hand sides
+  // of one batched handle (flat = 0); with flat = 1 every problem has its
+  // own handle, as the flattened launches need.
+  std::vector<std::vector<int>> groups;
+  for (int p = 0; p < nprob; ++p) {
+    int gi = -1;
+    if (o.flat == 0)
+      for (int q = 0; q < (int)groups.size() && gi < 0; ++q) {
+        const int r = groups[q][0];
+        if (nx[r] == nx[p] && ny[r] == ny[p] && h[r] == h[p] && k_const[r] == k_const[p] && beta2[r] == beta2[p])
+          gi = q;
+      }
+    if (gi < 0) {
+      gi = (int)groups.size();
+      groups.emplace_back();
+    }
+    groups[gi].push_back(p);
+  }
+  const int ng = (int)groups.size();
   // stream priorities by problem size: the largest problems (the longest
   // chains of cycles) get the highest priority, so their blocks are
   // scheduled first whenever the problems compete for the GPU
   int prio_least = 0, prio_greatest = 0;
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   const int nprio = prio_least - prio_greatest + 1;
-  std::vector<int> order(nprob);
+  auto nodes_of = [&](int q) { return (long long)(nx[groups[q][0]] + 1) * (ny[groups[q][0]] + 1); };
+  std::vector<int> order(ng);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return (long long)(nx[a] + 1) * (ny[a] + 1) > (long long)(nx[b] + 1) * (ny[b] + 1);
-  });
-  std::vector<int> prio(nprob, prio_least);
-  for (int r = 0; r < nprob; ++r) prio[order[r]] = prio_greatest + (int)((long long)r * nprio / nprob);
-  for (int p = 0; p < nprob; ++p) {
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nodes_of(a) > nodes_of(b); });
+  std::vector<int> prio(ng, prio_least);
+  for (int r = 0; r < ng; ++r) prio[order[r]] = prio_greatest + (int)((long long)r * nprio / ng);
+  for (int q = 0; q < ng; ++q) {
+    const int p = groups[q][0];
     cudaStream_t sp;
-    if (cudaStreamCreateWithPriority(&sp, cudaStreamNonBlocking, prio[p]) != cudaSuccess) {
+    if (cudaStreamCreateWithPriority(&sp, cudaStreamNonBlocking, prio[q]) != cudaSuccess) {
       delete c;
       FAIL(MG_ECUDA, "stream creation failed");
     }
     mg_options op = o;
     op.stream = sp;
+    op.batch = (int)groups[q].size();
     mg_handle hp = nullptr;
     mg_status st = mg_setup(&hp, nx[p], ny[p], h[p], nullptr, k_const[p], beta2[p], 0, &op);
     if (st != MG_OK) {
@@ -1114,10 +1137,18 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
     }
     hp->own_stream = sp;
     c->sub.push_back(hp);
+    c->members.push_back(groups[q]);
+    double2* stg = nullptr;
+    if (groups[q].size() > 1 &&
+        dalloc(c, (void**)&stg, sizeof(double2) * 2 * groups[q].size() * (size_t)nodes_of(q)) != cudaSuccess) {
+      delete c;
+      FAIL(MG_ENOMEM, "ragged batch: staging buffers of problem %d's group", p);
+    }
+    c->stage.push_back(stg);
   }
   long long total = 0;
-  for (mg_ctx* q : c->sub) total += (long long)(q->nx + 1) * (q->ny + 1);
-  for (mg_ctx* q : c->sub) q->peer_nodes = total - (long long)(q->nx + 1) * (q->ny + 1);
+  for (mg_ctx* q : c->sub) total += (long long)(q->nx + 1) * (q->ny + 1) * q->B;
+  for (mg_ctx* q : c->sub) q->peer_nodes = total - (long long)(q->nx + 1) * (q->ny + 1) * q->B;
   c->nx = c->sub[0]->nx;
   c->ny = c->sub[0]->ny;
   c->nlev = c->sub[0]->nlev;
@@ -1404,32 +1435,81 @@ static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, i
                               int conj) {
   if (!rhs || !x) FAIL(MG_EINVAL, "rhs and x must be device pointers");
   CK(cudaStreamSynchronize((cudaStream_t)c->opt.stream));   // the caller's inputs are ready
-  const int P = (int)c->sub.size();
-  std::vector<size_t> off(P + 1, 0);
-  for (int p = 0; p < P; ++p) off[p + 1] = off[p] + (size_t)(c->sub[p]->nx + 1) * (c->sub[p]->ny + 1);
-  if (c->opt.krylov > 0) {   // FGMRES: the problems one after the other
-    mg_status worst = MG_OK;
-    std::string msg;
-    long long launches = 0;
+  const int P = (int)c->sub.size();   // handles; handle p solves the problems members[p]
+  int nprob = 0;
+  for (const auto& m : c->members) nprob += (int)m.size();
+  std::vector<size_t> pn(nprob), off(nprob + 1, 0);   // each problem's nodes and offset in rhs and x
+  for (int p = 0; p < P; ++p)
+    for (int m : c->members[p]) pn[m] = (size_t)(c->sub[p]->nx + 1) * (c->sub[p]->ny + 1);
+  for (int m = 0; m < nprob; ++m) off[m + 1] = off[m] + pn[m];
+  const double2* R = (const double2*)rhs;
+  double2* X = (double2*)x;
+  // handle p's right-hand sides and iterates: the caller's arrays for a
+  // single problem, else the staging buffer (rhs of every member, then x)
+  // filled on the handle's stream
+  auto in_rhs = [&](int p) -> const double2* {
+    return c->members[p].size() == 1 ? R + off[c->members[p][0]] : c->stage[p];
+  };
+  auto in_x = [&](int p) -> double2* {
+    const size_t B = c->members[p].size();
+    return B == 1 ? X + off[c->members[p][0]] : c->stage[p] + B * pn[c->members[p][0]];
+  };
+  for (int p = 0; p < P; ++p) {
+    const size_t B = c->members[p].size();
+    if (B == 1) continue;
+    cudaStream_t sp = (cudaStream_t)c->sub[p]->opt.stream;
+    for (size_t i = 0; i < B; ++i) {
+      const int m = c->members[p][i];
+      CK(cudaMemcpyAsync(c->stage[p] + i * pn[m], R + off[m], sizeof(double2) * pn[m], cudaMemcpyDeviceToDevice, sp));
+      CK(cudaMemcpyAsync(in_x(p) + i * pn[m], X + off[m], sizeof(double2) * pn[m], cudaMemcpyDeviceToDevice, sp));
+    }
+  }
+  // handle p's results back into the caller's arrays
+  auto scatter = [&](int p, const int* cb, const double* rb) -> mg_status {
+    const size_t B = c->members[p].size();
+    for (size_t i = 0; i < B; ++i) {
+      const int m = c->members[p][i];
+      if (cycles_out) cycles_out[m] = cb[i];
+      if (relres_out) relres_out[m] = rb[i];
+    }
+    if (B == 1) return MG_OK;
+    cudaStream_t sp = (cudaStream_t)c->sub[p]->opt.stream;
+    for (size_t i = 0; i < B; ++i) {
+      const int m = c->members[p][i];
+      CK(cudaMemcpyAsync(X + off[m], in_x(p) + i * pn[m], sizeof(double2) * pn[m], cudaMemcpyDeviceToDevice, sp));
+    }
+    CK(cudaStreamSynchronize(sp));
+    return MG_OK;
+  };
+  mg_status worst = MG_OK;
+  std::string msg;
+  auto note = [&](mg_status st) {
+    if (st != MG_OK && (worst == MG_OK || st == MG_EDIVERGED)) {
+      worst = st;
+      msg = g_err;
+    }
+  };
+  long long launches = 0;
+  if (c->opt.krylov > 0) {   // FGMRES: the handles one after the other
     for (int p = 0; p < P; ++p) {
-      mg_status st = solve_fgmres(c->sub[p], (const double2*)rhs + off[p], (double2*)x + off[p], tol, conj,
-                                  cycles_out ? cycles_out + p : nullptr, relres_out ? relres_out + p : nullptr);
+      const size_t B = c->members[p].size();
+      std::vector<int> cb(B);
+      std::vector<double> rb(B);
+      mg_status st = solve_fgmres(c->sub[p], in_rhs(p), in_x(p), tol, conj, cb.data(), rb.data());
       launches += c->sub[p]->last_launches;
-      if (st != MG_OK && (worst == MG_OK || st == MG_EDIVERGED)) {
-        worst = st;
-        msg = g_err;
-      }
+      note(st);
       if (st != MG_OK && st != MG_EMAXIT && st != MG_EDIVERGED) return st;
+      mg_status sc = scatter(p, cb.data(), rb.data());
+      if (sc != MG_OK) return sc;
     }
     c->last_launches = launches;
     if (worst != MG_OK) FAIL(worst, "problem(s) of the ragged batch: %s", msg.c_str());
     return MG_OK;
   }
   for (int p = 0; p < P; ++p) {
-    mg_status st = solve_begin(c->sub[p], (const double2*)rhs + off[p], (double2*)x + off[p], tol, conj);
+    mg_status st = solve_begin(c->sub[p], in_rhs(p), in_x(p), tol, conj);
     if (st != MG_OK) return st;
   }
-  long long launches = 0;
   if (c->flat) {   // every cycle one graph over all problems (emit_ragged_iteration)
     for (int p = 0; p < P; ++p) CK(cudaStreamSynchronize((cudaStream_t)c->sub[p]->opt.stream));
     mg_status st = capture_ragged(c);
@@ -1445,42 +1525,42 @@ static mg_status solve_ragged(mg_ctx* c, const void* rhs, void* x, double tol, i
       for (int p = 0; p < P; ++p) left += c->h_counts[p] > 0;
     }
   } else {
-  // Each problem runs its own cycles: a problem whose stream has drained
-  // (its active count read back) gets its next cycle at once, without
-  // waiting for the slower problems, so the small problems finish early and
-  // the largest one, on the highest-priority stream, is never held back by a
-  // round barrier.
-  std::vector<char> running(P, 1);
-  int left = P;
-  while (left > 0) {
-    bool progressed = false;
-    for (int p = 0; p < P; ++p) {
-      if (!running[p]) continue;
-      const cudaError_t q = cudaStreamQuery((cudaStream_t)c->sub[p]->opt.stream);
-      if (q == cudaErrorNotReady) continue;
-      CK(q);
-      progressed = true;
-      if (solve_more(c->sub[p])) {
-        mg_status st = solve_launch(c->sub[p]);
-        if (st != MG_OK) return st;
-      } else {
-        running[p] = 0;
-        --left;
+    // Each handle runs its own cycles: a handle whose stream has drained (its
+    // active count read back) gets its next cycle at once, without waiting
+    // for the slower ones, so the small problems finish early and the
+    // largest one, on the highest-priority stream, is never held back by a
+    // round barrier.
+    std::vector<char> running(P, 1);
+    int left = P;
+    while (left > 0) {
+      bool progressed = false;
+      for (int p = 0; p < P; ++p) {
+        if (!running[p]) continue;
+        const cudaError_t q = cudaStreamQuery((cudaStream_t)c->sub[p]->opt.stream);
+        if (q == cudaErrorNotReady) continue;
+        CK(q);
+        progressed = true;
+        if (solve_more(c->sub[p])) {
+          mg_status st = solve_launch(c->sub[p]);
+          if (st != MG_OK) return st;
+        } else {
+          running[p] = 0;
+          --left;
+        }
       }
+      if (!progressed) std::this_thread::yield();
     }
-    if (!progressed) std::this_thread::yield();
   }
-  }
-  mg_status worst = MG_OK;
-  std::string msg;
   for (int p = 0; p < P; ++p) {
-    mg_status st = solve_end(c->sub[p], (double2*)x + off[p], conj, cycles_out ? cycles_out + p : nullptr,
-                             relres_out ? relres_out + p : nullptr);
+    const size_t B = c->members[p].size();
+    std::vector<int> cb(B);
+    std::vector<double> rb(B);
+    mg_status st = solve_end(c->sub[p], in_x(p), conj, cb.data(), rb.data());
     launches += c->sub[p]->last_launches;
-    if (st != MG_OK && (worst == MG_OK || st == MG_EDIVERGED)) {
-      worst = st;
-      msg = g_err;
-    }
+    note(st);
+    if (st != MG_OK && st != MG_EMAXIT && st != MG_EDIVERGED) return st;
+    mg_status sc = scatter(p, cb.data(), rb.data());
+    if (sc != MG_OK) return sc;
   }
   c->last_launches = launches;
   if (worst != MG_OK) FAIL(worst, "problem(s) of the ragged batch: %s", msg.c_str());

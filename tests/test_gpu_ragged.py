@@ -9,6 +9,7 @@ import parity_util as pu
 import synth
 from oracle import cycle as ocycle
 from oracle import hierarchy as ohier
+from oracle import problem as oprob
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -102,3 +103,87 @@ def test_flattened_ragged_matches_oracle():
         assert cyc[p] == refs[p].cycles, p
         pu.assert_close(xs[p].cpu().numpy().ravel(), refs[p].x, 1e-6, None, f"problem {p}")
     rs.close()
+
+
+# Repeated shapes: with flat = 0 the problems of one shape share a batched
+# handle (their right-hand sides side by side); each must still get its own
+# oracle solve.
+GROUPED_SIZES = [(64, 64, 40.0), (48, 96, 45.0), (64, 64, 40.0), (32, 32, 20.0), (48, 96, 45.0), (64, 64, 40.0)]
+
+
+def _ragged_distinct_rhs(sizes):
+    probs, rhs = [], []
+    for q, (nx, ny, k) in enumerate(sizes):
+        h = 1.0 / max(nx, ny)
+        probs.append((nx, ny, h, k))
+        b = synth.point_source(nx, ny, h, i=(q * 7) % (nx - 1) + 1, j=(q * 5) % (ny - 1) + 1)
+        b = b + 1e-2 * synth.random_complex((ny + 1, nx + 1), 70 + q) / h**2
+        rhs.append(torch.from_numpy(b).cuda())
+    return probs, rhs, [1.0 / k for _, _, k in sizes]
+
+
+def test_grouped_problems_match_oracle():
+    """flat = 0 with repeated shapes, FP64: one cycle from x = 0 equals each
+    problem's oracle iterate to 1e-10 node by node, and the whole solve takes
+    each problem's oracle cycle count, results scattered back in the
+    caller's order."""
+    probs, rhs, beta2 = _ragged_distinct_rhs(GROUPED_SIZES)
+    opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
+    refs = []
+    for p, (nx, ny, h, k) in enumerate(probs):
+        H = ohier.build_hierarchy(nx, ny, h, k, beta2[p])
+        refs.append(ocycle.mg_solve(H, rhs[p].cpu().numpy().ravel(), 1e-7, opt, keep_iterates=True))
+    rs1 = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, flat=0, max_cycles=1)
+    xs, st, cyc, rr = rs1.solve(rhs, tol=1e-300)
+    assert st == hm.MG_EMAXIT and all(c == 1 for c in cyc)
+    for p, (nx, ny, h, k) in enumerate(probs):
+        pu.assert_close(xs[p].cpu().numpy(), refs[p].iterates[0].reshape(ny + 1, nx + 1), 1e-10, (ny + 1, nx + 1),
+                        f"problem {p}")
+    rs1.close()
+    rs = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, flat=0)
+    xs, st, cyc, rr = rs.solve(rhs, tol=1e-7)
+    assert st == hm.MG_OK
+    for p in range(len(probs)):
+        assert cyc[p] == refs[p].cycles, p
+        pu.assert_close(xs[p].cpu().numpy().ravel(), refs[p].x, 1e-6, None, f"problem {p}")
+    rs.close()
+
+
+def test_grouped_problems_mixed_precision():
+    """flat = 0 with repeated shapes, mixed path: every problem's FP64
+    residual, recomputed with the oracle's matrix, meets the tolerance and
+    equals the reported one; the cycle counts are within one of the
+    oracle's."""
+    probs, rhs, beta2 = _ragged_distinct_rhs(GROUPED_SIZES)
+    opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
+    rs = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision="mixed", flat=0)
+    xs, st, cyc, rr = rs.solve(rhs, tol=1e-7)
+    assert st == hm.MG_OK
+    for p, (nx, ny, h, k) in enumerate(probs):
+        b = rhs[p].cpu().numpy().ravel()
+        A = oprob.helmholtz_matrix(nx, ny, h, k)
+        r = b - A @ xs[p].cpu().numpy().ravel()
+        rel = np.linalg.norm(r) / np.linalg.norm(b)
+        assert rel <= 1e-7 and abs(rel - rr[p]) <= 1e-3 * rr[p], p
+        H = ohier.build_hierarchy(nx, ny, h, k, beta2[p])
+        ref = ocycle.mg_solve(H, b, 1e-7, opt)
+        assert abs(cyc[p] - ref.cycles) <= 1, p
+    rs.close()
+
+
+def test_grouped_problems_with_fgmres():
+    """The grouped handles also serve the FGMRES outer loop: each problem
+    equals the same solve through its own single-problem handle to the solve
+    tolerance."""
+    probs, rhs, beta2 = _ragged_distinct_rhs(GROUPED_SIZES)
+    for kw in (dict(krylov=5), dict()):
+        rs = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision="fp64", flat=0, **kw)
+        xs, st, cyc, rr = rs.solve(rhs, tol=1e-10)
+        assert st == hm.MG_OK
+        for p, (nx, ny, h, k) in enumerate(probs):
+            s = hm.Solver(nx, ny, h, k, beta2[p], smoother="gmres3", nu_pre=2, nu_post=2, precision="fp64", **kw)
+            x1, st1, cyc1, rr1 = s.solve(rhs[p], tol=1e-10)
+            assert st1 == hm.MG_OK and abs(cyc1[0] - cyc[p]) <= 1, p
+            pu.assert_close(xs[p].cpu().numpy().ravel(), x1.cpu().numpy().ravel(), 1e-8, None, f"problem {p}")
+            s.close()
+        rs.close()
