@@ -280,13 +280,15 @@ static bool use_march(const mg_ctx* c, int l) {
 }
 
 template <class T>
-static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, const int* active, cudaStream_t s) {
+static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, const int* active, cudaStream_t s,
+                        double2* outer = nullptr) {
   const Grid& g = c->lev[l].g;
   const OpView<T> op = opT<T>(c, l);
   GmresBufs gb = vecs<T>(c)[l].gb;
   gb.side = c->side;
   gb.ev_fork = c->ev_fork;
   gb.ev_join = c->ev_join;
+  gb.outer = outer;
   const bool m = use_march(c, l);
   if (m && op.kind == 1) gmres_smooth_march<T>(g, op, x, b, nu, c->B, active, gb, s);
   else if (m && op.kind >= 4) gmres_smooth_kron<T>(g, op, x, b, nu, c->B, active, gb, s);
@@ -299,8 +301,12 @@ template <class T> struct Emit {
   std::vector<cx<T>*> cur, oth;
   int lc;                        // first level run by the coarse-cycle interpreter
   const CoarsePlan<T>* plan;
+  // complex64 cycle of the FP64 refinement: the FP64 iterate that the
+  // level-0 post-smoothing's last GMRES(3) update adds the cycle's result to
+  // (the fused refinement update); null: the caller adds it
+  double2* outer0 = nullptr;
 
-  void smooth(int l, int nu) {
+  void smooth(int l, int nu, double2* outer = nullptr) {
     if (nu <= 0) return;
     auto& V = vecs<T>(c)[l];
     const Grid& g = c->lev[l].g;
@@ -317,7 +323,7 @@ template <class T> struct Emit {
         std::swap(cur[l], oth[l]);
       }
     } else {
-      gmres_level<T>(c, l, cur[l], V.b, nu, c->active, s);
+      gmres_level<T>(c, l, cur[l], V.b, nu, c->active, s, outer);
     }
   }
 
@@ -357,7 +363,7 @@ template <class T> struct Emit {
       for (int q = 0; q < c->opt.cycle; ++q) cycle(l + 1);
     }
     launch_prolong_add<T>(g, gc, cur[l + 1], cur[l], c->B, c->active, c->xw, s);
-    smooth(l, c->opt.nu_post);
+    smooth(l, c->opt.nu_post, l == 0 ? outer0 : nullptr);
   }
 
   void init() {
@@ -471,6 +477,12 @@ static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
   Emit<float> e{c, s, {}, {}, c->lc, &c->plan32};
   e.init();
   const Grid& g0 = c->lev[0].g;
+  // the refinement update x64 += e fused into the cycle's last kernel: the
+  // level-0 post-smoothing's last GMRES(3) update (a level-0 smoothing run by
+  // the cycle's own kernels, precision 1)
+  const bool fused = c->opt.precision == 1 && c->opt.smoother == 1 && c->opt.nu_post > 0 && c->lc > 0 &&
+                     c->nlev > 1;
+  if (fused) e.outer0 = c->v64[0].x;
   cudaMemsetAsync(c->v32[0].x, 0, sizeof(float2) * (size_t)g0.vstride * c->B, s);
   e.cycle(0);
   if (c->opt.precision == 2) {
@@ -478,7 +490,7 @@ static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
     launch_ff_resid_cast_stop(g0, c->hffc, c->kf64, c->h, c->ffdiag, c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B,
                               ctl(c), 1, s);
   } else {
-    launch_update_mixed(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
+    if (!fused) launch_update_mixed(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
     launch_resid_cast_stop(g0, op64(c, 0), c->v64[0].x, c->v64[0].b, c->v32[0].b, c->B, ctl(c), 1, s);
   }
 }

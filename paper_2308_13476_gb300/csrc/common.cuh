@@ -43,6 +43,41 @@ template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
   return mk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 template <class T> __device__ __forceinline__ T abs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
+
+// IEEE 754 conversions between binary64 and binary32 in integer arithmetic.
+// The hardware conversions execute on the FP64 pipe, which is narrow on this
+// GPU and is what bounds the FP64 refinement passes; these take the integer
+// pipe for normal numbers and give the same results: binary64 to binary32
+// rounds to nearest, ties to even (the fraction keeps its 23 leading bits and
+// the 29 dropped bits decide the rounding; a carry out of the fraction raises
+// the exponent, up to infinity), and binary32 to binary64 is exact (the
+// exponent rebiased by 1023 - 127, the fraction shifted into place).  Zeros,
+// subnormal inputs or results, infinities and NaNs take the hardware
+// conversion.
+__device__ __forceinline__ float f32_from_f64_rn(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu) - (1023 - 127);   // biased binary32 exponent
+  if (e >= 1 && e <= 254) {
+    const unsigned long long frac = u & 0x000fffffffffffffull;
+    unsigned f = ((unsigned)e << 23) | (unsigned)(frac >> 29);
+    const unsigned rem = (unsigned)frac & 0x1fffffffu;
+    f += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & f & 1u);
+    return __uint_as_float((hi & 0x80000000u) | f);
+  }
+  return __double2float_rn(d);
+}
+__device__ __forceinline__ double f64_from_f32(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u) {   // normal
+    const unsigned long long r = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + (1023 - 127)) << 52) |
+                                 ((unsigned long long)(u & 0x007fffffu) << 29);
+    return __longlong_as_double((long long)r);
+  }
+  return (double)v;
+}
 template <class T> __device__ __forceinline__ cx<T> cinv(cx<T> a) {
   T d = a.x * a.x + a.y * a.y;
   return mk<T>(a.x / d, -a.y / d);

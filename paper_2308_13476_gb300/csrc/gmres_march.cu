@@ -764,6 +764,12 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
     pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
          [&] { gm_step3<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
          [&] { gm_step3<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
+    if constexpr (sizeof(T) == 4) {
+      if (step == nu - 1 && gb.outer) {
+        launch_gmres_update_outer(g, x, gb, B, active, s);
+        continue;
+      }
+    }
     launch_gmres_update<T>(g, x, gb, B, active, s);
   }
 }

@@ -149,7 +149,14 @@ struct GmresBufs {
   cudaStream_t side;   // optional second stream (with the two events) on
   cudaEvent_t ev_fork; // which the fine level's boundary launches run beside
   cudaEvent_t ev_join; // the interior ones; null: one stream
+  double2* outer;      // complex64 level 0 inside the FP64 refinement: the FP64
+                       // iterate to which the last smoothing step's result is
+                       // added by the fused update (null: none)
 };
+// The last GMRES(3) update of a complex64 level-0 smoothing fused with the
+// FP64 refinement update x64 += x (kernels_gmres.cu).
+void launch_gmres_update_outer(const Grid& g, const float2* x, const GmresBufs& gb, int B, const int* active,
+                               cudaStream_t s);
 template <class T> void gmres_smooth(const Grid& g, const OpView<T>& op, cx<T>* x, const cx<T>* b, int nu, int B,
                                      const int* active, const GmresBufs& gb, cudaStream_t s);
 

@@ -251,6 +251,58 @@ __global__ void __launch_bounds__(BX * BY) g_update(Grid g, cx<T>* __restrict__ 
   g_update_body<T>(blockIdx, gridDim, g, x, u0, u1, u2, st, active);
 }
 
+// The last GMRES(3) update of the level-0 post-smoothing of a complex64
+// cycle inside the FP64 refinement, fused with the refinement's update: the
+// updated complex64 iterate is the cycle's correction e, added to the FP64
+// iterate at once (x64 += e, the widening on the integer pipe) instead of
+// being stored and read back by a separate pass.  The complex64 iterate is
+// not stored (the next cycle starts from zero).  With no Arnoldi column
+// (m = 0) e is the iterate as it stands.
+__global__ void __launch_bounds__(BX * BY) g_update_outer(Grid g, const float2* __restrict__ x,
+                                                          const float2* __restrict__ u0, const float2* __restrict__ u1,
+                                                          const float2* __restrict__ u2, const double* __restrict__ st,
+                                                          double2* __restrict__ x64, const int* __restrict__ active) {
+  using T = float;
+  constexpr int NP = PK<T>::NP;
+  const int rhs = blockIdx.z;
+  const int i0 = (blockIdx.x * BX + threadIdx.x) * NP;
+  const int nv = min(NP, g.nx + 1 - i0);
+  const long long off = (long long)rhs * g.vstride;
+  if (active && !active[rhs]) return;
+  if (nv <= 0) return;
+  const double* S = st + (long long)rhs * GS;
+  const int m = (int)S[G_M];
+  const cx<T>* us[3] = {u0, u1, u2};
+  cx<T> c[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const double sl = S[G_S + l];
+    c[l] = mk<T>((T)(S[G_Y + 2 * l] * sl), (T)(S[G_Y + 2 * l + 1] * sl));
+  }
+  GROWS {
+    if (j > g.ny) break;
+    const int p = g.at(i0, j);
+    Pack<T> a = load_pack(x + off, p);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      if (l < m) {
+        const Pack<T> ul = load_pack(us[l] + off, p);
+#pragma unroll
+        for (int n = 0; n < NP; ++n) a.v[n] = fma_c<T>(c[l], ul.v[n], a.v[n]);
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < NP; ++n) {
+      if (n < nv) {
+        double2 xv = x64[off + p + n];
+        xv.x += f64_from_f32(a.v[n].x);
+        xv.y += f64_from_f32(a.v[n].y);
+        x64[off + p + n] = xv;
+      }
+    }
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(BX * BY) g_update_rag(const __grid_constant__ RagLaunch<GuA<T>> L) {
   uint3 vb;
@@ -281,6 +333,12 @@ void gmres_smooth(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T>* b,
       g_arn_b<T, 1><<<grd, blk, 0, s>>>(g, u0, u1, u2, u2, w, st, P, tk, active, -1);
       g_arn_a<T, Op, 2><<<grd, blk, 0, s>>>(g, op, u0, u1, u2, w, st, P, tk, active);
       g_arn_b<T, 2><<<grd, blk, 0, s>>>(g, u0, u1, u2, nullptr, w, st, P, tk, active, -1);
+      if constexpr (sizeof(T) == 4) {
+        if (step == nu - 1 && gb.outer) {
+          launch_gmres_update_outer(g, x, gb, B, active, s);
+          continue;
+        }
+      }
       g_update<T><<<grd, blk, 0, s>>>(g, x, u0, u1, u2, st, active);
     }
   });
@@ -291,6 +349,13 @@ void launch_gmres_update(const Grid& g, cx<T>* x, const GmresBufs& gb, int B, co
   dim3 grd(cdiv(g.nx + 1, BX * PK<T>::NP), cdiv(g.ny + 1, BY * g.ry), B);
   g_update<T><<<grd, dim3(BX, BY), 0, s>>>(g, x, (const cx<T>*)gb.u[0], (const cx<T>*)gb.u[1],
                                           (const cx<T>*)gb.u[2], gb.st, active);
+}
+
+void launch_gmres_update_outer(const Grid& g, const float2* x, const GmresBufs& gb, int B, const int* active,
+                               cudaStream_t s) {
+  dim3 grd(cdiv(g.nx + 1, BX * PK<float>::NP), cdiv(g.ny + 1, BY * g.ry), B);
+  g_update_outer<<<grd, dim3(BX, BY), 0, s>>>(g, x, (const float2*)gb.u[0], (const float2*)gb.u[1],
+                                              (const float2*)gb.u[2], gb.st, gb.outer, active);
 }
 
 template <class T, int J>

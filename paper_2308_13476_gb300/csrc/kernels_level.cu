@@ -184,8 +184,10 @@ __global__ void __launch_bounds__(BX * BY) k_resnorm_stop_rag(const __grid_const
 // b - A x is two FMAs per component after the neighbour sum,
 // b - d x_P + (1/h^2)(x_E + x_W + x_N + x_S), d = 4/h^2 - k^2 (boundary nodes
 // take Op0::apply5); and the norm is summed from the float residual the
-// pass writes anyway (FP32 within a thread, FP64 across threads), which
-// resolves the stopping test's relative residual to about 1e-7 of itself.
+// pass writes anyway (FP32 within a thread and a warp, FP64 across warps and
+// blocks), which resolves the stopping test's relative residual to about
+// 1e-7 of itself.  The conversions to float take the integer pipe
+// (f32_from_f64_rn, the same rounding as the hardware's).
 __device__ __forceinline__ void k_resid_cast_stop_body(uint3 vblk, dim3 vgrid, Grid g, Op0<double> op, const double2* __restrict__ x, const double2* __restrict__ b, float2* __restrict__ r32, Ctl c, int count) {
   const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
   const dim3 gridDim = vgrid;
@@ -216,14 +218,14 @@ __device__ __forceinline__ void k_resid_cast_stop_body(uint3 vblk, dim3 vgrid, G
       } else {
         r = sub<double>(bb, op.apply(xs, p, g.pitch, i, j));
       }
-      const float2 rf = make_float2((float)r.x, (float)r.y);
+      const float2 rf = make_float2(f32_from_f64_rn(r.x), f32_from_f64_rn(r.y));
       r32[off + p] = rf;
       af = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, af));
     }
   }
-  const double a0[1] = {(double)af};
+  const float a0[1] = {af};
   double v[1];
-  if (reduce_last<1, double>(a0, v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
+  if (reduce_last<1, float>(a0, v, sh, c.partial, c.tickets, rhs, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x) &&
       threadIdx.x == 0 && threadIdx.y == 0)
     stop_update(c, rhs, v[0], count);
 }
@@ -252,8 +254,8 @@ __device__ __forceinline__ void k_update_mixed_body(uint3 vblk, dim3 vgrid, Grid
     const long long p = off + g.at(i, j);
     const float2 d = e[p];
     double2 xv = x[p];
-    xv.x += (double)d.x;
-    xv.y += (double)d.y;
+    xv.x += f64_from_f32(d.x);
+    xv.y += f64_from_f32(d.y);
     x[p] = xv;
   }
 }
