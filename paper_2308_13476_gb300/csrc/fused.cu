@@ -85,45 +85,71 @@ __device__ __forceinline__ void k_resid_restrict_body(uint3 vblk, dim3 vgrid, Gr
     // and each footprint node combines the 2R + 1 rows around it along y.
     // The sums and the combination run in the order of OpK::apply, so every
     // residual is the same value; the work per node drops from 6 (2R+1)^2
-    // to about 12 (2R+1) FMAs.
+    // to about 12 (2R+1) FMAs, and each thread loads the operator's
+    // coefficients of one column (row) once.
     constexpr int KR = KronRadius<Op>::R, K = 2 * KR + 1, SR = RFY + 2 * KR;
+    constexpr int NT = CTX * CTY;
     __shared__ cx<T> s1t[SR][RFX], s2t[SR][RFX];
-    for (int q = tid; q < SR * RFX; q += CTX * CTY) {
-      const int li = q % RFX, lr = q / RFX;
-      const int i = fx0 + li, j = fy0 - KR + lr;
-      cx<T> a = mk<T>(0, 0), c = mk<T>(0, 0);   // unused outside the grid's columns and their row halo
-      if (i >= 0 && i <= gf.nx && j >= -KR && j <= gf.ny + KR) {
-        const cx<T>* G = op.gx + i * K;
-        const T* Wx = op.wx + i * K;
-        const cx<T>* row = xs + gf.at(i, j);
+    // row sums: a thread keeps one footprint column (and its column's x
+    // coefficients in registers) and takes every CG-th row
+    constexpr int CG = NT / RFX;
+    if (tid < CG * RFX) {
+      const int li = tid % RFX, i = fx0 + li;
+      const bool icol = i >= 0 && i <= gf.nx;
+      cx<T> G[K];
+      T Wx[K];
 #pragma unroll
-        for (int dx = -KR; dx <= KR; ++dx) {
-          const cx<T> xv = row[dx];
-          a = fma_c<T>(G[dx + KR], xv, a);
-          c = mk<T>(fma(Wx[dx + KR], xv.x, c.x), fma(Wx[dx + KR], xv.y, c.y));
-        }
+      for (int k = 0; k < K; ++k) {
+        G[k] = icol ? op.gx[i * K + k] : mk<T>(0, 0);
+        Wx[k] = icol ? op.wx[i * K + k] : T(0);
       }
-      s1t[lr][li] = a;
-      s2t[lr][li] = c;
+      for (int lr = tid / RFX; lr < SR; lr += CG) {
+        const int j = fy0 - KR + lr;
+        cx<T> a = mk<T>(0, 0), c = mk<T>(0, 0);   // unused outside the grid's columns and their row halo
+        if (icol && j >= -KR && j <= gf.ny + KR) {
+          const cx<T>* row = xs + gf.at(i, j);
+#pragma unroll
+          for (int dx = -KR; dx <= KR; ++dx) {
+            const cx<T> xv = row[dx];
+            a = fma_c<T>(G[dx + KR], xv, a);
+            c = mk<T>(fma(Wx[dx + KR], xv.x, c.x), fma(Wx[dx + KR], xv.y, c.y));
+          }
+        }
+        s1t[lr][li] = a;
+        s2t[lr][li] = c;
+      }
     }
     __syncthreads();
-    for (int q = tid; q < RFX * RFY; q += CTX * CTY) {
-      const int li = q % RFX, lj = q / RFX;
-      const int i = fx0 + li, j = fy0 + lj;
-      cx<T> r = mk<T>(0, 0);   // outside the grid the fine residual is zero
-      if (i >= 0 && i <= gf.nx && j >= 0 && j <= gf.ny) {
-        const cx<T>* H = op.hy + j * K;
-        const T* Wy = op.wy + j * K;
-        cx<T> acc = mk<T>(0, 0);
+    // combination along y: a thread keeps one footprint row (and its row's y
+    // coefficients in registers, the parameter bank's copy for the
+    // translation-invariant interior rows) and takes every RG-th column
+    constexpr int RG = NT / RFY;
+    if (tid < RG * RFY) {
+      const int lj = tid % RFY, j = fy0 + lj;
+      const bool jrow = j >= 0 && j <= gf.ny;
+      cx<T> H[K];
+      T Wy[K];
+      const bool inv = j >= op.ty0 && j < op.ty1;
 #pragma unroll
-        for (int dy = -KR; dy <= KR; ++dy) {
-          const cx<T> a = s1t[lj + KR + dy][li], c = s2t[lj + KR + dy][li];
-          acc = mk<T>(fma(Wy[dy + KR], a.x, acc.x), fma(Wy[dy + KR], a.y, acc.y));
-          acc = fma_c<T>(H[dy + KR], c, acc);
-        }
-        r = sub<T>(bs[gf.at(i, j)], acc);
+      for (int k = 0; k < K; ++k) {
+        H[k] = inv ? op.hyc[k] : jrow ? op.hy[j * K + k] : mk<T>(0, 0);
+        Wy[k] = inv ? op.wyc[k] : jrow ? op.wy[j * K + k] : T(0);
       }
-      rt[lj][li] = r;
+      for (int li = tid / RFY; li < RFX; li += RG) {
+        const int i = fx0 + li;
+        cx<T> r = mk<T>(0, 0);   // outside the grid the fine residual is zero
+        if (jrow && i >= 0 && i <= gf.nx) {
+          cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+          for (int dy = -KR; dy <= KR; ++dy) {
+            const cx<T> a = s1t[lj + KR + dy][li], c = s2t[lj + KR + dy][li];
+            acc = mk<T>(fma(Wy[dy + KR], a.x, acc.x), fma(Wy[dy + KR], a.y, acc.y));
+            acc = fma_c<T>(H[dy + KR], c, acc);
+          }
+          r = sub<T>(bs[gf.at(i, j)], acc);
+        }
+        rt[lj][li] = r;
+      }
     }
   } else {
     for (int q = tid; q < RFX * RFY; q += CTX * CTY) {

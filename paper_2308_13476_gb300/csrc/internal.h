@@ -30,13 +30,26 @@ template <class T> struct OpView {
 __host__ __device__ inline int op_radius(int kind) { return kind == 1 ? 1 : (kind == 2 || kind == 4) ? 2 : 3; }
 
 // Dispatch a generic lambda on the operator functor of a view.
+// The Kronecker-form operator of a view, with its translation-invariant
+// y-factor rows (parameter-bank copies) when it has them.
+template <class T, int R> inline OpK<T, R> kron_op(const OpView<T>& v, int nx, int ny) {
+  OpK<T, R> o{v.gx, v.wx, v.hy, v.wy, v.dinv, nx, ny};
+  o.ty0 = v.ty0;
+  o.ty1 = v.ty1;
+  for (int k = 0; k < 2 * R + 1; ++k) {
+    o.hyc[k] = v.hyc[k];
+    o.wyc[k] = v.wyc[k];
+  }
+  return o;
+}
+
 template <class T, class F> inline void with_op(const OpView<T>& v, int nx, int ny, F&& f) {
   switch (v.kind) {
     case 1: f(Op0<T>{v.c0, v.kf, nx, ny}); break;
     case 2: f(OpS<T, 2>{v.st, v.dinv, v.plane, nx, ny}); break;
     case 3: f(OpS<T, 3>{v.st, v.dinv, v.plane, nx, ny}); break;
-    case 4: f(OpK<T, 2>{v.gx, v.wx, v.hy, v.wy, v.dinv, nx, ny}); break;
-    default: f(OpK<T, 3>{v.gx, v.wx, v.hy, v.wy, v.dinv, nx, ny}); break;
+    case 4: f(kron_op<T, 2>(v, nx, ny)); break;
+    default: f(kron_op<T, 3>(v, nx, ny)); break;
   }
 }
 

@@ -662,20 +662,8 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
       launch_gmres_update<T>(g, x, gb, B, active, s);
     }
   };
-  auto with_rows = [&](auto op) {   // the translation-invariant y-factor rows
-    constexpr int K = 2 * decltype(op)::radius + 1;
-    op.ty0 = opv.ty0;
-    op.ty1 = opv.ty1;
-    for (int k = 0; k < K; ++k) {
-      op.hyc[k] = opv.hyc[k];
-      op.wyc[k] = opv.wyc[k];
-    }
-    return op;
-  };
-  if (opv.kind == 4)
-    run(with_rows(OpK<T, 2>{opv.gx, opv.wx, opv.hy, opv.wy, opv.dinv, g.nx, g.ny}), std::integral_constant<int, 2>{});
-  else
-    run(with_rows(OpK<T, 3>{opv.gx, opv.wx, opv.hy, opv.wy, opv.dinv, g.nx, g.ny}), std::integral_constant<int, 3>{});
+  if (opv.kind == 4) run(kron_op<T, 2>(opv, g.nx, g.ny), std::integral_constant<int, 2>{});
+  else run(kron_op<T, 3>(opv, g.nx, g.ny), std::integral_constant<int, 3>{});
 }
 
 // The same smoothing steps on every problem of a ragged batch (the problems'
@@ -692,13 +680,7 @@ void gmres_smooth_kron_rag(const std::vector<RagLevel<T>>& v, int nu, cudaStream
     for (int q = 0; q < n; ++q) {
       const RagLevel<T>& L = v[q];
       const OpView<T>& o = L.op;
-      OpK<T, R> op{o.gx, o.wx, o.hy, o.wy, o.dinv, L.g.nx, L.g.ny};
-      op.ty0 = o.ty0;
-      op.ty1 = o.ty1;
-      for (int k = 0; k < 2 * R + 1; ++k) {
-        op.hyc[k] = o.hyc[k];
-        op.wyc[k] = o.wyc[k];
-      }
+      const OpK<T, R> op = kron_op<T, R>(o, L.g.nx, L.g.ny);
       const KGeo kg = kron_geo(L.g, 1, R, kron_capacity<T, R>(fused));
       A[q] = KmA<T, R>{L.g, kg, op, L.x, L.b, (cx<T>*)L.gb.u[0], (cx<T>*)L.gb.u[1], (cx<T>*)L.gb.u[2],
                        (cx<T>*)L.gb.w, nullptr, nullptr, nullptr, L.gb.st, L.gb.partial, L.gb.tickets, L.active};
