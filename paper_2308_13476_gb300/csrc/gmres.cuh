@@ -138,12 +138,23 @@ template <int J, class Ts, class St = double, class V = double> __device__ __for
   if (J == 2 || S[G_BRK] != St(0)) lsq<Ts, St>(S);
 }
 
+// The per-RHS state in global memory: GS values of the cycle's working
+// precision T per right-hand side (the scalar steps compute in T and store T
+// values, so FP32 storage gives what FP64 storage would; kernels of a
+// complex64 cycle then read their coefficients without FP64 instructions).
+template <class T> __device__ __forceinline__ T* gstate(double* st, int rhs) {
+  return reinterpret_cast<T*>(st) + (long long)rhs * GS;
+}
+template <class T> __device__ __forceinline__ const T* gstate(const double* st, int rhs) {
+  return reinterpret_cast<const T*>(st) + (long long)rhs * GS;
+}
+
 // Runs a scalar step on the RHS state in shared memory (all threads of the
 // block copy it in and out; thread 0 computes), so its many dependent reads
 // and writes stay on chip.
-template <class T, class F>
-__device__ __forceinline__ void staged(double* S, const double* v, F f) {
-  __shared__ double Ssh[GS];
+template <class T, class St, class F>
+__device__ __forceinline__ void staged(St* S, const double* v, F f) {
+  __shared__ St Ssh[GS];
   const int tid = threadIdx.x + threadIdx.y * blockDim.x, nt = blockDim.x * blockDim.y;
   for (int k = tid; k < GS; k += nt) Ssh[k] = S[k];
   __syncthreads();

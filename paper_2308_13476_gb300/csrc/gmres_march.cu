@@ -460,7 +460,7 @@ template <class T> struct GmA {
   const int cs = strip * strip_w<T>() - 2;                                    \
   const int i = cs + NP * lane;                                               \
   const bool outl = NP * lane >= 2 && NP * lane + NP <= 32 * NP - 2;          \
-  double* S = st + (long long)rhs * GS;                                       \
+  T* S = gstate<T>(st, rhs);                                                  \
   const MCtx<T, MD> ctx{op, g, i, j0, j1, outl};
 
 // Runs pass P on the warp's strip and chunk (rows j0-2 .. t1 read) and
@@ -492,7 +492,7 @@ __device__ __forceinline__ void run_pass(const MCtx<T, MD>& c, int t1, const voi
 // blk: the block's index inside its own launch (the body's blockIdx.x).
 template <int MD, int NV, class T, class F>
 __device__ __forceinline__ void finish(const T (&acc)[NV], double* sh, double* partial, unsigned* tickets, int rhs,
-                                       int blk, const MGeo& mg, double* S, F f) {
+                                       int blk, const MGeo& mg, T* S, F f) {
   double v[NV];
   const int nrec = mg.nrec();
   if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blk, mg.template rec0<MD>(), nrec))
@@ -514,9 +514,9 @@ __device__ __forceinline__ void gm_init_body(uint3 vblk, Grid g, MGeo mg, Op0<T>
     p.m.src[1] = b + off;
     p.us = u0 + off;
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](auto* s, const double* q) {
     fin_init<T>(s, q);
-    if (s[G_BRK] == 0.0) {   // <u0, w> with w = s0 A u0
+    if (s[G_BRK] == 0) {   // <u0, w> with w = s0 A u0
       const double d[2] = {q[1] * s[G_S], q[2] * s[G_S]};
       fin_a<0, T>(s, d);
     }
@@ -545,7 +545,7 @@ __device__ __forceinline__ void gm_step1_body(uint3 vblk, Grid g, MGeo mg, Op0<T
                                                unsigned* tickets, const int* __restrict__ active) {
   const uint3 blockIdx = vblk;   // the block index inside this problem's launch
   MPRO
-  if (S[G_BRK] != 0.0) return;   // uniform per RHS
+  if (S[G_BRK] != 0) return;   // uniform per RHS
   const T s0 = (T)S[G_S];
   const cx<T> c0 = mk<T>((T)(S[G_H] * S[G_S]), (T)(S[G_H + 1] * S[G_S]));
   T acc[7];
@@ -557,9 +557,9 @@ __device__ __forceinline__ void gm_step1_body(uint3 vblk, Grid g, MGeo mg, Op0<T
     p.s0 = s0;
     p.c0 = c0;
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](auto* s, const double* q) {
     fin_b<0, T>(s, q);
-    if (s[G_BRK] == 0.0) {
+    if (s[G_BRK] == 0) {
       const double s1 = s[G_S + 1];
       const double d[4] = {q[3] * s1, q[4] * s1, q[5] * s1, q[6] * s1};
       fin_a<1, T>(s, d);
@@ -590,7 +590,7 @@ __device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T
                                                double* partial, unsigned* tickets, const int* __restrict__ active) {
   const uint3 blockIdx = vblk;   // the block index inside this problem's launch
   MPRO
-  if (S[G_BRK] != 0.0 || S[G_M] < 1) return;
+  if (S[G_BRK] != 0 || S[G_M] < 1) return;
   const T s1 = (T)S[G_S + 1];
   const cx<T> c0 = mk<T>((T)(S[G_H + 2 * 1] * S[G_S]), (T)(S[G_H + 2 * 1 + 1] * S[G_S]));
   const cx<T> c1 = mk<T>((T)(S[G_H + 2 * 4] * S[G_S + 1]), (T)(S[G_H + 2 * 4 + 1] * S[G_S + 1]));
@@ -605,9 +605,9 @@ __device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T
     p.c0 = c0;
     p.c1 = c1;
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) {
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](auto* s, const double* q) {
     fin_b<1, T>(s, q);
-    if (s[G_BRK] == 0.0) {
+    if (s[G_BRK] == 0) {
       const double s2 = s[G_S + 2];
       const double d[6] = {q[5] * s2, q[6] * s2, q[7] * s2, q[8] * s2, q[9] * s2, q[10] * s2};
       fin_a<2, T>(s, d);
@@ -639,7 +639,7 @@ __device__ __forceinline__ void gm_step3_body(uint3 vblk, Grid g, MGeo mg, Op0<T
                                                const int* __restrict__ active) {
   const uint3 blockIdx = vblk;   // the block index inside this problem's launch
   MPRO
-  if (S[G_BRK] != 0.0 || S[G_M] < 2) return;
+  if (S[G_BRK] != 0 || S[G_M] < 2) return;
   const T s2 = (T)S[G_S + 2];
   cx<T> cl[3];
 #pragma unroll
@@ -657,7 +657,7 @@ __device__ __forceinline__ void gm_step3_body(uint3 vblk, Grid g, MGeo mg, Op0<T
     p.cl[1] = cl[1];
     p.cl[2] = cl[2];
   });
-  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](double* s, const double* q) { fin_b<2, T>(s, q); });
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](auto* s, const double* q) { fin_b<2, T>(s, q); });
 }
 
 template <class T, int MD>

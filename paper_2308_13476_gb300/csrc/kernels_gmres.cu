@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(BX * BY) g_init(Grid g, Op op, const cx<T>* __
     }
   }
   double v[1];
-  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(st + (long long)rhs * GS, v);
+  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(gstate<T>(st, rhs), v);
 }
 
 // w = A v_J (v_J = s_J u_J); partial dots <u_i, w> for i <= J
@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
   __shared__ double sh[NVMAX * 32];
   GNODE
   if (active && !active[rhs]) return;
-  double* S = st + (long long)rhs * GS;
-  if (S[G_BRK] != 0.0 || S[G_M] < J) return;   // block-uniform
+  T* S = gstate<T>(st, rhs);
+  if (S[G_BRK] != 0 || S[G_M] < J) return;   // block-uniform
   const cx<T>* uJ = J == 0 ? u0 : (J == 1 ? u1 : u2);
   T acc[2 * (J + 1)];
 #pragma unroll
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
     }
   }
   double v[2 * (J + 1)];
-  if (reduce_last<2 * (J + 1), T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
+  if (reduce_last<2 * (J + 1), T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](auto* s, const double* q) { fin_a<J, T>(s, q); });
 }
 
 // u_{J+1} = w - sum_{i<=J} h_iJ s_i u_i ; partials |u_{J+1}|^2 and <u_{J+1}, u_l>, l <= J (J < 2)
@@ -142,8 +142,8 @@ __device__ __forceinline__ void g_arn_b_body(uint3 vblk, dim3 vgrid, Grid g, con
   __shared__ double sh[NVMAX * 32];
   GNODE
   if (active && !active[rhs]) return;
-  double* S = st + (long long)rhs * GS;
-  if (S[G_BRK] != 0.0 || S[G_M] < J) return;
+  T* S = gstate<T>(st, rhs);
+  if (S[G_BRK] != 0 || S[G_M] < J) return;
   T acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = T(0);
@@ -152,8 +152,8 @@ __device__ __forceinline__ void g_arn_b_body(uint3 vblk, dim3 vgrid, Grid g, con
     cx<T> c[J + 1];
 #pragma unroll
     for (int l = 0; l <= J; ++l) {
-      const double hr = S[G_H + 2 * (l * 3 + J)], hi = S[G_H + 2 * (l * 3 + J) + 1];
-      const double sl = S[G_S + l];
+      const T hr = S[G_H + 2 * (l * 3 + J)], hi = S[G_H + 2 * (l * 3 + J) + 1];
+      const T sl = S[G_S + l];
       c[l] = mk<T>((T)(hr * sl), (T)(hi * sl));
     }
     // ws >= 0: w was stored without its scale s_ws (fused Kronecker marches)
@@ -190,7 +190,7 @@ __device__ __forceinline__ void g_arn_b_body(uint3 vblk, dim3 vgrid, Grid g, con
     }
   }
   double v[NV];
-  if (reduce_last<NV, T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](double* s, const double* q) { fin_b<J, T>(s, q); });
+  if (reduce_last<NV, T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](auto* s, const double* q) { fin_b<J, T>(s, q); });
 }
 
 template <class T, int J>
@@ -220,14 +220,14 @@ __device__ __forceinline__ void g_update_body(uint3 vblk, dim3 vgrid, Grid g, cx
   const long long off = (long long)rhs * g.vstride;
   if (active && !active[rhs]) return;
   if (nv <= 0) return;
-  const double* S = st + (long long)rhs * GS;
+  const T* S = gstate<T>(st, rhs);
   const int m = (int)S[G_M];
   if (m <= 0) return;
   const cx<T>* us[3] = {u0, u1, u2};
   cx<T> c[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const double sl = S[G_S + l];
+    const T sl = S[G_S + l];
     c[l] = mk<T>((T)(S[G_Y + 2 * l] * sl), (T)(S[G_Y + 2 * l + 1] * sl));
   }
   GROWS {
@@ -270,13 +270,13 @@ __global__ void __launch_bounds__(BX * BY) g_update_outer(Grid g, const float2* 
   const long long off = (long long)rhs * g.vstride;
   if (active && !active[rhs]) return;
   if (nv <= 0) return;
-  const double* S = st + (long long)rhs * GS;
+  const T* S = gstate<T>(st, rhs);
   const int m = (int)S[G_M];
   const cx<T>* us[3] = {u0, u1, u2};
   cx<T> c[3];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const double sl = S[G_S + l];
+    const T sl = S[G_S + l];
     c[l] = mk<T>((T)(S[G_Y + 2 * l] * sl), (T)(S[G_Y + 2 * l + 1] * sl));
   }
   GROWS {

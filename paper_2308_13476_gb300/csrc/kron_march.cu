@@ -277,7 +277,7 @@ __device__ __forceinline__ void km_init_body(uint3 vblk, dim3 vgrid, Grid g, KGe
   }
   double v[1];
   if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && threadIdx.x == 0)
-    fin_init<T>(st + (long long)rhs * GS, v);
+    fin_init<T>(gstate<T>(st, rhs), v);
 }
 
 template <class T, int R>
@@ -301,8 +301,8 @@ __device__ __forceinline__ void km_arn_a_body(uint3 vblk, dim3 vgrid, Grid g, KG
   (void)blockIdx;
   (void)gridDim;
   KPRO
-  double* S = st + (long long)rhs * GS;
-  if (S[G_BRK] != 0.0 || S[G_M] < J) return;   // uniform per RHS
+  T* S = gstate<T>(st, rhs);
+  if (S[G_BRK] != 0 || S[G_M] < J) return;   // uniform per RHS
   const cx<T>* uJ = J == 0 ? u0 : (J == 1 ? u1 : u2);
   T acc[2 * (J + 1)];
 #pragma unroll
@@ -331,7 +331,7 @@ __device__ __forceinline__ void km_arn_a_body(uint3 vblk, dim3 vgrid, Grid g, KG
   }
   double v[2 * (J + 1)];
   if (reduce_last<2 * (J + 1), T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
-    staged<T>(S, v, [](double* s, const double* q) { fin_a<J, T>(s, q); });
+    staged<T>(S, v, [](auto* s, const double* q) { fin_a<J, T>(s, q); });
 }
 
 template <class T, int R, int J>
@@ -480,8 +480,8 @@ __device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, K
   const int j0 = (has ? gw / kg.ncw : 0) * kg.ch, j1 = min(j0 + kg.ch, g.ny + 1);
   const bool col = has && i <= g.nx;
   const int nblk = gridDim.x, blk = blockIdx.x;
-  double* S = st + (long long)rhs * GS;
-  if (S[G_BRK] != 0.0 || S[G_M] < J - 1) return;   // the guard of g_arn_b<J-1>; uniform per RHS
+  T* S = gstate<T>(st, rhs);
+  if (S[G_BRK] != 0 || S[G_M] < J - 1) return;   // the guard of g_arn_b<J-1>; uniform per RHS
   T acc[NB + NA];
 #pragma unroll
   for (int k = 0; k < NB + NA; ++k) acc[k] = T(0);
@@ -492,7 +492,7 @@ __device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, K
     cx<T> c[NS - 1];
 #pragma unroll
     for (int l = 0; l < J; ++l) {
-      const double sl = S[G_S + l];
+      const T sl = S[G_S + l];
       c[l] = mk<T>((T)(S[G_H + 2 * (l * 3 + J - 1)] * sl), (T)(S[G_H + 2 * (l * 3 + J - 1) + 1] * sl));
     }
     KRingF<T, R, NS> ring;
@@ -539,9 +539,9 @@ __device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, K
   }
   double v[NB + NA];
   if (reduce_last<NB + NA, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
-    staged<T>(S, v, [](double* s, const double* q) {
+    staged<T>(S, v, [](auto* s, const double* q) {
       fin_b<J - 1, T>(s, q);
-      if (s[G_BRK] == 0.0) {
+      if (s[G_BRK] == 0) {
         double d[NA];
         const double sJ = s[G_S + J];
 #pragma unroll
