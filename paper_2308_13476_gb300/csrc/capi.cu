@@ -1160,7 +1160,17 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
   }
   long long total = 0;
   for (mg_ctx* q : c->sub) total += (long long)(q->nx + 1) * (q->ny + 1) * q->B;
-  for (mg_ctx* q : c->sub) q->peer_nodes = total - (long long)(q->nx + 1) * (q->ny + 1) * q->B;
+  // The fine-level kernels (use_march) are chosen for the whole batch's
+  // load, except on the largest problems: they run the most cycles, their
+  // chain of cycles is the batch's critical path, and they decide by their
+  // own size (a single large right-hand side runs its fine level faster
+  // node-parallel than as row marches).
+  long long nmax = 0;
+  for (mg_ctx* q : c->sub) nmax = std::max(nmax, (long long)(q->nx + 1) * (q->ny + 1));
+  for (mg_ctx* q : c->sub) {
+    const long long own = (long long)(q->nx + 1) * (q->ny + 1);
+    q->peer_nodes = own == nmax ? 0 : total - own * q->B;
+  }
   c->nx = c->sub[0]->nx;
   c->ny = c->sub[0]->ny;
   c->nlev = c->sub[0]->nlev;
