@@ -123,6 +123,28 @@ __device__ __forceinline__ void stage_kron_row(cx<T>* dst, const cx<T>* vs, cons
   }
 }
 
+// Copy row r's own 32 columns cw0 .. cw0 + 31 of vs into dst (no halo): a
+// vector read only at the lane's own node, staged with the applied one so
+// that its loads are in flight KD rows ahead too.
+template <class T>
+__device__ __forceinline__ void stage_own_row(cx<T>* dst, const cx<T>* vs, const Grid& g, int cw0, int lane, int r) {
+  if constexpr (sizeof(cx<T>) == 8) {
+    if (lane < 16) {
+      const int col = cw0 + 2 * lane;
+      const bool ok = col <= g.nx;
+      const cx<T>* src = vs + g.at(ok ? col : 0, r);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + 2 * lane);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+    }
+  } else {
+    const int col = cw0 + lane;
+    const bool ok = col <= g.nx;
+    const cx<T>* src = vs + g.at(ok ? col : 0, r);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + lane);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+  }
+}
+
 // combination along y for output row m = r - R, r the row just taken in
 // slot P of a ring of the last K = 2R+1 row sums: row m + dy sits in slot
 // (P + 1 + R + dy) mod K, or in slot dy + R of a shifting ring (KU = 1).
@@ -166,6 +188,8 @@ template <class T, int R> struct KRing {
   int cw0, lane;     // the warp's first column, the lane
   cx<T>* sm;         // the warp's ring, [KSL][WD]
   int r0;            // first row of the march (slot 0)
+  const cx<T>* os = nullptr;   // optional vector read at the lane's own nodes (no halo)
+  cx<T>* osm = nullptr;        // its ring, [KSL][32]
 
   __device__ __forceinline__ void init(const OpK<T, R>& op, int i, bool col) {
 #pragma unroll
@@ -179,7 +203,12 @@ template <class T, int R> struct KRing {
   // copy row r's staged columns into its slot
   __device__ __forceinline__ void issue(int r) {
     stage_kron_row<T, RA>(sm + ((r - r0) & (KSL - 1)) * WD, vs, g, cw0, lane, r);
+    if (os) stage_own_row<T>(osm + ((r - r0) & (KSL - 1)) * 32, os, g, cw0, lane, r);
   }
+  // the applied vector and the own-node vector at row m (m >= r - KSL + KD,
+  // r the row last taken: the slot is not yet reused), the lane's column
+  __device__ __forceinline__ cx<T> staged_at(int m) const { return sm[((m - r0) & (KSL - 1)) * WD + lane + RA]; }
+  __device__ __forceinline__ cx<T> own_at(int m) const { return osm[((m - r0) & (KSL - 1)) * 32 + lane]; }
   __device__ __forceinline__ static void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
   // rows r0 .. r0 + KD - 1 in flight
   __device__ __forceinline__ void prime(int last) {
@@ -260,15 +289,27 @@ __device__ __forceinline__ void km_init_body(uint3 vblk, dim3 vgrid, Grid g, KGe
   (void)gridDim;
   KPRO
   T a0[1] = {T(0)};
+  __shared__ __align__(16) cx<T> kbsm[KW][KSL][32];   // b, staged with x
   if (has) {
-    KMARCH_SETUP(x + off)
+    KRing<T, R> ring;
+    ring.init(op, i, col);
+    ring.vs = x + off;
+    ring.g = g;
+    ring.cw0 = cw0;
+    ring.lane = lane;
+    ring.sm = &ksm[wib][0][0];
+    ring.r0 = j0 - R;
+    ring.os = b + off;
+    ring.osm = &kbsm[wib][0][0];
+    const int last = j1 + R - 1;
+    ring.prime(last);
     kmarch<KU<T, R>>(j0 - R, last, [&](auto ph, int r) {
       constexpr int P = decltype(ph)::value;
       ring.template advance<P>(r, last);
       const int m = r - R;
       if (m >= j0 && col) {
         const int p = g.at(i, m);
-        const cx<T> res = sub<T>(b[off + p], ring.template combine<P>(op, m));
+        const cx<T> res = sub<T>(ring.own_at(m), ring.template combine<P>(op, m));
         u0[off + p] = res;
         a0[0] += abs2<T>(res);
       }
@@ -320,8 +361,8 @@ __device__ __forceinline__ void km_arn_a_body(uint3 vblk, dim3 vgrid, Grid g, KG
         const cx<T> a = scl<T>(sJ, ring.template combine<P>(op, m));
         w[off + p] = a;
 #pragma unroll
-        for (int l = 0; l <= J; ++l) {
-          const cx<T> d = cmul<T>(us[l][p], a);
+        for (int l = 0; l <= J; ++l) {   // u_J is the staged vector
+          const cx<T> d = cmul<T>(l == J ? ring.staged_at(m) : us[l][p], a);
           acc[2 * l] += d.x;
           acc[2 * l + 1] += d.y;
         }
