@@ -103,7 +103,10 @@ __device__ __forceinline__ void k_resid_restrict_body(uint3 vblk, dim3 vgrid, Gr
         G[k] = icol ? op.gx[i * K + k] : mk<T>(0, 0);
         Wx[k] = icol ? op.wx[i * K + k] : T(0);
       }
-      for (int lr = tid / RFX; lr < SR; lr += CG) {
+#pragma unroll
+      for (int kk = 0; kk < (SR + CG - 1) / CG; ++kk) {   // a fixed trip count: the loads of all rows in flight together
+        const int lr = tid / RFX + kk * CG;
+        if (lr >= SR) break;
         const int j = fy0 - KR + lr;
         cx<T> a = mk<T>(0, 0), c = mk<T>(0, 0);   // unused outside the grid's columns and their row halo
         if (icol && j >= -KR && j <= gf.ny + KR) {
@@ -135,7 +138,10 @@ __device__ __forceinline__ void k_resid_restrict_body(uint3 vblk, dim3 vgrid, Gr
         H[k] = inv ? op.hyc[k] : jrow ? op.hy[j * K + k] : mk<T>(0, 0);
         Wy[k] = inv ? op.wyc[k] : jrow ? op.wy[j * K + k] : T(0);
       }
-      for (int li = tid / RFY; li < RFX; li += RG) {
+#pragma unroll
+      for (int kk = 0; kk < (RFX + RG - 1) / RG; ++kk) {
+        const int li = tid / RFY + kk * RG;
+        if (li >= RFX) break;
         const int i = fx0 + li;
         cx<T> r = mk<T>(0, 0);   // outside the grid the fine residual is zero
         if (jrow && i >= 0 && i <= gf.nx) {
