@@ -132,12 +132,17 @@ typedef struct {
                        grid in the coarse-cycle launch), else one cycle graph
                        per problem.  Either way each problem computes its own
                        solve.  Ignored by single-problem handles.         */
+  int kron_chunk;   /* rows per chunk of the column marches on Kronecker-form
+                       levels: 0 = chosen per level from the kernels'
+                       occupancy (rounds x rows); n > 0 = n rows (at least 8;
+                       an autotuner axis).  Any value gives the same results
+                       up to the order of the reductions' block partials.  */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
  * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0, fuse 1,
- * tile_rows 0; march -1; krylov 0; transfer 0; flat 0; default stream. */
+ * tile_rows 0; march -1; krylov 0; transfer 0; flat 0; kron_chunk 0; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).

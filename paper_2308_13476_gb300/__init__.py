@@ -42,7 +42,8 @@ class MgOptions(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("min_coarse", ctypes.c_int), ("batch", ctypes.c_int),
                 ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("fuse", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("march", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("transfer", ctypes.c_int), ("flat", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("transfer", ctypes.c_int), ("flat", ctypes.c_int), ("kron_chunk", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -261,7 +262,7 @@ TRANSFERS = {"bezier": 0, "linear": 1}
 
 def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, precision="fp64", batch=1,
              max_cycles=10000, min_coarse=10, coarse_nodes=None, coarse_mode=None, fuse=None, tile_rows=None,
-             march=None, krylov=None, transfer="bezier", flat=None, stream=None):
+             march=None, krylov=None, transfer="bezier", flat=None, kron_chunk=None, stream=None):
     o = mg_default_options()
     o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
     o.smoother = SMOOTHERS[smoother]
@@ -269,7 +270,8 @@ def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, preci
     o.precision = PRECISIONS[precision]
     o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
     for name, val in (("coarse_nodes", coarse_nodes), ("coarse_mode", coarse_mode), ("fuse", fuse),
-                      ("tile_rows", tile_rows), ("march", march), ("krylov", krylov), ("flat", flat)):
+                      ("tile_rows", tile_rows), ("march", march), ("krylov", krylov), ("flat", flat),
+                      ("kron_chunk", kron_chunk)):
         if val is not None:
             setattr(o, name, int(val))
     o.transfer = TRANSFERS[transfer]
@@ -325,7 +327,7 @@ class Solver:
     Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
            nu_pre, nu_post, omega, precision="fp64"|"mixed"|"mixed-ff", batch, levels,
            max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, march, krylov,
-           transfer="bezier"|"linear", stream)
+           transfer="bezier"|"linear", kron_chunk, stream)
     ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
     ``krylov`` = m > 0 wraps the cycle in restarted FGMRES(m) as its right
     preconditioner (cycles then count preconditioner applications).
@@ -336,7 +338,7 @@ class Solver:
     def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
                  precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, coarse_nodes=None,
                  coarse_mode=None, fuse=None, tile_rows=None, march=None, krylov=0, transfer="bezier",
-                 stream=None):
+                 kron_chunk=None, stream=None):
         o = mg_default_options()
         o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
         o.smoother = SMOOTHERS[smoother]
@@ -354,6 +356,8 @@ class Solver:
         if march is not None:
             o.march = int(march)
         o.krylov = int(krylov)
+        if kron_chunk is not None:
+            o.kron_chunk = int(kron_chunk)
         o.transfer = TRANSFERS[transfer]
         o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         self.nx, self.ny, self.h, self.batch = nx, ny, h, batch

@@ -286,6 +286,7 @@ static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, cons
   const OpView<T> op = opT<T>(c, l);
   GmresBufs gb = vecs<T>(c)[l].gb;
   gb.side = c->side;
+  gb.kron_ch = c->opt.kron_chunk;
   gb.ev_fork = c->ev_fork;
   gb.ev_join = c->ev_join;
   gb.outer = outer;
@@ -638,7 +639,9 @@ template <class T> struct EmitR {
     std::vector<RagLevel<T>> v;
     for (int p : G) {
       mg_ctx* h = q(p);
-      v.push_back(RagLevel<T>{h->lev[l].g, opT<T>(h, l), cur(p, l), vecs<T>(h)[l].b, vecs<T>(h)[l].gb, h->active});
+      GmresBufs gb = vecs<T>(h)[l].gb;
+      gb.kron_ch = h->opt.kron_chunk;
+      v.push_back(RagLevel<T>{h->lev[l].g, opT<T>(h, l), cur(p, l), vecs<T>(h)[l].b, gb, h->active});
     }
     if (l == 0) gmres_smooth_march_rag<T>(v, nu, s, c->side, c->ev_fork, c->ev_join);
     else gmres_smooth_kron_rag<T>(v, nu, s);
@@ -777,6 +780,7 @@ void mg_default_options(mg_options* o) {
   o->krylov = 0;
   o->transfer = 0;
   o->flat = 0;
+  o->kron_chunk = 0;
   o->stream = nullptr;
 }
 
@@ -1067,6 +1071,7 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.krylov > 0 && o.precision == 2) FAIL(MG_EINVAL, "the FGMRES outer loop needs precision 0 or 1");
   if (o.transfer != 0 && o.transfer != 1) FAIL(MG_EINVAL, "transfer must be 0 (Eq. (xex)) or 1 (linear)");
   if (o.flat != 0 && o.flat != 1) FAIL(MG_EINVAL, "flat must be 0 or 1");
+  if (o.kron_chunk < 0 || o.kron_chunk > 1024) FAIL(MG_EINVAL, "kron_chunk must be in 0..1024");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;

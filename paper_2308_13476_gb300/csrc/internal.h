@@ -165,6 +165,8 @@ struct GmresBufs {
   double2* outer;      // complex64 level 0 inside the FP64 refinement: the FP64
                        // iterate to which the last smoothing step's result is
                        // added by the fused update (null: none)
+  int kron_ch;         // rows per chunk of the Kronecker-level column marches
+                       // (0: chosen from the kernel's occupancy)
 };
 // The last GMRES(3) update of a complex64 level-0 smoothing fused with the
 // FP64 refinement update x64 += x (kernels_gmres.cu).

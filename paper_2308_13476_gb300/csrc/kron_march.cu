@@ -612,9 +612,14 @@ constexpr int KCH[] = {64, 48, 32, 24, 16, 12, 8};   // candidate rows per chunk
 // at once, so the chunk height minimising rounds x (ch + 2R) is taken (the
 // tallest on ties).  A fixed height can leave a last round of a few blocks:
 // 64-row chunks of a 513^2 level with 64 right-hand sides give 2.05 rounds.
-KGeo kron_geo(const Grid& g, int B, int R, long long cap) {
+KGeo kron_geo(const Grid& g, int B, int R, long long cap, int forced = 0) {
   KGeo k;
   k.ncw = cdiv(g.nx + 1, 32);
+  if (forced > 0) {   // a fixed height (the autotuner's axis), at least the shortest candidate
+    k.ch = std::max(forced, KCH[sizeof(KCH) / sizeof(KCH[0]) - 1]);
+    k.nchunks = cdiv(g.ny + 1, k.ch);
+    return k;
+  }
   long long best = -1;
   for (int ch : KCH) {
     const long long blocks = (long long)cdiv((long long)k.ncw * cdiv(g.ny + 1, ch), KW) * B;
@@ -679,7 +684,7 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
   auto run = [&](auto op, auto rad) {
     constexpr int R = decltype(rad)::value;
     const bool fused = KFUSE<T> && w2 != nullptr;
-    const KGeo kg = kron_geo(g, B, R, kron_capacity<T, R>(fused));
+    const KGeo kg = kron_geo(g, B, R, kron_capacity<T, R>(fused), gb.kron_ch);
     const dim3 grd(cdiv((long long)kg.ncw * kg.nchunks, KW), 1, B);
     for (int step = 0; step < nu; ++step) {
       km_init<T, R><<<grd, KW * 32, 0, s>>>(g, kg, op, x, b, u0, st, P, tk, active);
@@ -722,7 +727,7 @@ void gmres_smooth_kron_rag(const std::vector<RagLevel<T>>& v, int nu, cudaStream
       const RagLevel<T>& L = v[q];
       const OpView<T>& o = L.op;
       const OpK<T, R> op = kron_op<T, R>(o, L.g.nx, L.g.ny);
-      const KGeo kg = kron_geo(L.g, 1, R, kron_capacity<T, R>(fused));
+      const KGeo kg = kron_geo(L.g, 1, R, kron_capacity<T, R>(fused), L.gb.kron_ch);
       A[q] = KmA<T, R>{L.g, kg, op, L.x, L.b, (cx<T>*)L.gb.u[0], (cx<T>*)L.gb.u[1], (cx<T>*)L.gb.u[2],
                        (cx<T>*)L.gb.w, nullptr, nullptr, nullptr, L.gb.st, L.gb.partial, L.gb.tickets, L.active};
     }
