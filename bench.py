@@ -370,15 +370,19 @@ def run_ours(a):
         tuned, _ = autotune.tune(n, n, h, k, a.beta2, rhs, smoother=a.smoother, cycle=a.cycle, nu=a.nu,
                                  precision=a.precision, cache_path=os.path.join(ROOT, "paper_2308_13476_gb300",
                                                                                 "autotune_cache.json"))
+    tuned = dict(tuned or {})
     for name in ("coarse_nodes", "coarse_mode"):   # explicit overrides of the tuned shapes
         if getattr(a, name) >= 0:
-            tuned = dict(tuned or {}, **{name: getattr(a, name)})
+            tuned[name] = getattr(a, name)
+    if a.march != -1 or "march" not in tuned:   # an explicit --march overrides the tuned one
+        tuned["march"] = a.march
 
     def make(precision, shapes=None):
         t0 = time.perf_counter()
+        shapes = dict(shapes or {"march": a.march})
         s = hm.Solver(n, n, h, k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
-                      precision=precision, batch=a.batch, max_cycles=20000, march=a.march, krylov=a.krylov,
-                      transfer=a.transfer, stream=S, **(shapes or {}))
+                      precision=precision, batch=a.batch, max_cycles=20000, krylov=a.krylov,
+                      transfer=a.transfer, stream=S, **shapes)
         torch.cuda.synchronize()
         return s, time.perf_counter() - t0
 
