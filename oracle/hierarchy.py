@@ -58,7 +58,7 @@ class Hierarchy:
 
 
 def build_hierarchy(nx, ny, h, k, beta2, levels=0, kind="bezier", edge="zero",
-                    min_coarse=10, rows="scaled", grid="vertex"):
+                    min_coarse=10, rows="scaled", grid="vertex", abc=1):
     """All operators of the cycle.  ``k`` scalar (MP 2-A) or field (MP 2-B).
 
     ``rows`` and ``grid`` select alternative readings of the discretisation,
@@ -66,13 +66,15 @@ def build_hierarchy(nx, ny, h, k, beta2, levels=0, kind="bezier", edge="zero",
     passed to ``problem.helmholtz_matrix``; ``grid="interior"`` takes only the
     interior nodes as unknowns (``problem.helmholtz_matrix_interior``) with
     the transfers of Eq. (xex) restricted to them (a boundary value of a
-    coarse correction is zero)."""
+    coarse correction is zero).  ``abc=2`` takes the second-order absorbing
+    rows (a variant the paper does not use, ``problem.tangential_abc2``); the
+    coarse operators are the Galerkin products of the same transfers."""
     sizes = level_sizes(nx, ny, levels, min_coarse, grid)
     H = Hierarchy(sizes=sizes, h=h)
     if grid == "interior":
         op = lambda b2: problem.helmholtz_matrix_interior(nx, ny, h, k, b2)
     elif grid == "vertex":
-        op = lambda b2: problem.helmholtz_matrix(nx, ny, h, k, b2, rows)
+        op = lambda b2: problem.helmholtz_matrix(nx, ny, h, k, b2, rows, abc)
     else:
         raise ValueError(grid)
     H.A.append(op(0.0))

@@ -24,6 +24,18 @@ Readings (the paper does not spell these out):
   (1 + i*beta2) k^2, boundary rows keep the unshifted k.  The sign +i makes
   the shift push Im(x^H C x) the same way as the absorbing boundary term; the
   opposite sign gives two-grid norms of 5-16 against the paper's 0.91-0.98.
+
+A variant the paper does not use (``abc=2``): the second-order absorbing
+condition of Engquist and Majda (1977), d u/dn - i k u - (i / 2k) d^2 u / dtau^2
+= 0 along every side (tau tangential; the paraxial expansion
+sqrt(k^2 + d^2/dtau^2) ~ k + d^2/dtau^2 / (2k) of the outgoing normal
+derivative).  In the weak form the tangential term is the boundary stiffness
+(i / 2k) int dtau u dtau v over each side, with no term at the corners (the
+natural corner condition).  On the grid every boundary segment P-Q of a side
+adds c (u_P - u_Q) to row P and c (u_Q - u_P) to row Q, c = i (1/k_P + 1/k_Q)
+/ (4 h^3) in the scaled-row units above (1/h^2 times the finite-volume row):
+an edge node gains (i / 2k h^3) (2 u_P - u_tau+ - u_tau-), a corner one
+segment on each of its two sides.  A stays complex symmetric.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -43,7 +55,7 @@ def _k_field(nx, ny, k):
     return k
 
 
-def helmholtz_matrix(nx, ny, h, k, beta2=0.0, rows="scaled"):
+def helmholtz_matrix(nx, ny, h, k, beta2=0.0, rows="scaled", abc=1):
     """Sparse (CSR, complex128) matrix of -Lap_h - (1 + i beta2) k^2 with
     ghost-eliminated Sommerfeld rows scaled by 1/2 (edge) and 1/4 (corner).
 
@@ -55,8 +67,16 @@ def helmholtz_matrix(nx, ny, h, k, beta2=0.0, rows="scaled"):
     "second-order finite differences"): "scaled" (the default above),
     "unscaled" (the same ghost-eliminated rows without the 1/2, 1/4 factors;
     not symmetric), or "bc1" (``helmholtz_matrix_bc1``: the boundary rows are
-    the first-order one-sided absorbing condition itself).
+    the first-order one-sided absorbing condition itself).  ``abc=2`` adds the
+    second-order absorbing condition's tangential terms to the scaled rows
+    (``tangential_abc2``; see the module notes).
     """
+    if abc not in (1, 2):
+        raise ValueError(abc)
+    if abc == 2:
+        if rows != "scaled":
+            raise ValueError("the second-order absorbing rows are defined on the scaled rows")
+        return (helmholtz_matrix(nx, ny, h, k, beta2) + tangential_abc2(nx, ny, h, k)).tocsr()
     if rows == "bc1":
         return helmholtz_matrix_bc1(nx, ny, h, k, beta2)
     if rows not in ("scaled", "unscaled"):
@@ -104,6 +124,32 @@ def helmholtz_matrix(nx, ny, h, k, beta2=0.0, rows="scaled"):
     # row scaling 1/2 per boundary direction
     w = boundary_weights(nx, ny).ravel()
     return (sp.diags(w) @ A).tocsr()
+
+
+def tangential_abc2(nx, ny, h, k):
+    """The second-order absorbing condition's boundary stiffness (module
+    notes): for every pair P, Q of neighbouring nodes on one side of the
+    boundary, c (u_P - u_Q) in row P and c (u_Q - u_P) in row Q with
+    c = i (1/k_P + 1/k_Q) / (4 h^3).  A sparse (N, N) complex matrix."""
+    kf = _k_field(nx, ny, k)
+    N = (nx + 1) * (ny + 1)
+    segs = []   # (P, Q) flat indices of the boundary segments
+    for j in (0, ny):                     # bottom and top: neighbours along x
+        for i in range(nx):
+            segs.append((node_index(nx, i, j), node_index(nx, i + 1, j)))
+    for i in (0, nx):                     # left and right: neighbours along y
+        for j in range(ny):
+            segs.append((node_index(nx, i, j), node_index(nx, i, j + 1)))
+    kr = kf.ravel()
+    P = np.array([a for a, _ in segs])
+    Q = np.array([b for _, b in segs])
+    c = 1j * (1.0 / kr[P] + 1.0 / kr[Q]) / (4.0 * h ** 3)
+    rows = np.concatenate([P, Q, P, Q])
+    cols = np.concatenate([P, Q, Q, P])
+    vals = np.concatenate([c, c, -c, -c])
+    T = sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+    T.sum_duplicates()
+    return T
 
 
 def helmholtz_matrix_bc1(nx, ny, h, k, beta2=0.0):
