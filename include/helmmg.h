@@ -127,7 +127,7 @@ typedef struct {
                        (their blocks numbered one after the other, each
                        problem with its own grid, geometry and convergence
                        mask) when the options allow it (GMRES(3), fuse 1,
-                       march != 0, precision 0 or 1, krylov 0, coarse_mode 0
+                       march != 0, precision 0 or 1, krylov 0, abc 1, coarse_mode 0
                        and a coarse_nodes that puts every problem's coarsest
                        grid in the coarse-cycle launch), else one cycle graph
                        per problem.  Either way each problem computes its own
@@ -137,12 +137,20 @@ typedef struct {
                        occupancy (rounds x rows); n > 0 = n rows (at least 8;
                        an autotuner axis).  Any value gives the same results
                        up to the order of the reductions' block partials.  */
+  int abc;          /* absorbing boundary rows: 1 = the first-order Sommerfeld
+                       condition of Sec. 2 (paper default); 2 = the
+                       second-order condition of Engquist and Majda,
+                       du/dn - i k u - (i/2k) d2u/dtau2 = 0, as a boundary
+                       stiffness with natural corners (a variant the paper
+                       does not use; coarse levels then take stored
+                       Galerkin stencils; needs precision 0 or 1; mg_gradient
+                       returns MG_EINVAL)                                   */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 
 /* Paper defaults: V(1,1), Jacobi, omega 4.5, complex128, 10000 cycles,
  * min_coarse 10, batch 1; coarse_nodes 1100, coarse_mode 0, fuse 1,
- * tile_rows 0; march -1; krylov 0; transfer 0; flat 0; kron_chunk 0; default stream. */
+ * tile_rows 0; march -1; krylov 0; transfer 0; flat 0; kron_chunk 0; abc 1; default stream. */
 void mg_default_options(mg_options* opt);
 
 /* Build the hierarchy for one problem (Sec. 2, Sec. 3, Sec. 5).

@@ -43,7 +43,7 @@ class MgOptions(ctypes.Structure):
                 ("coarse_nodes", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("fuse", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("march", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("transfer", ctypes.c_int), ("flat", ctypes.c_int), ("kron_chunk", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("abc", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -262,7 +262,7 @@ TRANSFERS = {"bezier": 0, "linear": 1}
 
 def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, precision="fp64", batch=1,
              max_cycles=10000, min_coarse=10, coarse_nodes=None, coarse_mode=None, fuse=None, tile_rows=None,
-             march=None, krylov=None, transfer="bezier", flat=None, kron_chunk=None, stream=None):
+             march=None, krylov=None, transfer="bezier", flat=None, kron_chunk=None, abc=None, stream=None):
     o = mg_default_options()
     o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
     o.smoother = SMOOTHERS[smoother]
@@ -271,7 +271,7 @@ def _options(cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5, preci
     o.batch, o.max_cycles, o.min_coarse = int(batch), int(max_cycles), int(min_coarse)
     for name, val in (("coarse_nodes", coarse_nodes), ("coarse_mode", coarse_mode), ("fuse", fuse),
                       ("tile_rows", tile_rows), ("march", march), ("krylov", krylov), ("flat", flat),
-                      ("kron_chunk", kron_chunk)):
+                      ("kron_chunk", kron_chunk), ("abc", abc)):
         if val is not None:
             setattr(o, name, int(val))
     o.transfer = TRANSFERS[transfer]
@@ -327,7 +327,9 @@ class Solver:
     Solver(nx, ny, h, k, beta2, cycle="V"|"W", smoother="jacobi"|"gmres3",
            nu_pre, nu_post, omega, precision="fp64"|"mixed"|"mixed-ff", batch, levels,
            max_cycles, min_coarse, coarse_nodes, coarse_mode, fuse, tile_rows, march, krylov,
-           transfer="bezier"|"linear", kron_chunk, stream)
+           transfer="bezier"|"linear", kron_chunk, abc=1|2, stream)
+    ``abc=2`` replaces the first-order absorbing rows of Sec. 2 by the
+    second-order Engquist-Majda condition (a variant the paper does not use).
     ``k`` is a float (constant wavenumber) or a float64 tensor (ny+1, nx+1).
     ``krylov`` = m > 0 wraps the cycle in restarted FGMRES(m) as its right
     preconditioner (cycles then count preconditioner applications).
@@ -338,7 +340,7 @@ class Solver:
     def __init__(self, nx, ny, h, k, beta2, cycle="V", smoother="jacobi", nu_pre=1, nu_post=1, omega=4.5,
                  precision="fp64", batch=1, levels=0, max_cycles=10000, min_coarse=10, coarse_nodes=None,
                  coarse_mode=None, fuse=None, tile_rows=None, march=None, krylov=0, transfer="bezier",
-                 kron_chunk=None, stream=None):
+                 kron_chunk=None, abc=1, stream=None):
         o = mg_default_options()
         o.cycle = {"V": 1, "W": 2, 1: 1, 2: 2}[cycle]
         o.smoother = SMOOTHERS[smoother]
@@ -358,6 +360,7 @@ class Solver:
         o.krylov = int(krylov)
         if kron_chunk is not None:
             o.kron_chunk = int(kron_chunk)
+        o.abc = int(abc)
         o.transfer = TRANSFERS[transfer]
         o.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
         self.nx, self.ny, self.h, self.batch = nx, ny, h, batch

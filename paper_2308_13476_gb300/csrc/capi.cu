@@ -781,6 +781,7 @@ void mg_default_options(mg_options* o) {
   o->transfer = 0;
   o->flat = 0;
   o->kron_chunk = 0;
+  o->abc = 1;
   o->stream = nullptr;
 }
 
@@ -828,7 +829,7 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
       launch_to_float_real(c->kf64, c->kf32, N0, s);
     }
   }
-  launch_op0consts(c->c0d, c->c0f, c->h, c->kconst, o.omega, c->beta2, s);
+  launch_op0consts(c->c0d, c->c0f, c->h, c->kconst, o.omega, c->beta2, o.abc, s);
   CK(cudaMemcpyAsync(&c->hc0d, c->c0d, sizeof(Op0Consts<double>), cudaMemcpyDeviceToHost, s));
   if (mixed) CK(cudaMemcpyAsync(&c->hc0f, c->c0f, sizeof(Op0Consts<float>), cudaMemcpyDeviceToHost, s));
   if (ffo) {
@@ -840,8 +841,9 @@ static mg_status setup_impl(mg_ctx* c, const double* k_field) {
   CK(cudaStreamSynchronize(s));
   // Galerkin operators A_{l+1} = R_l C_l P_l.  Constant k: Kronecker form,
   // A_l = W_y (x) G_x + H_y (x) W_x, each factor coarsened in 1D.  Variable
-  // k: per-node stencils from the 2D product.
-  const bool kron = k_field == nullptr;
+  // k, or the second-order absorbing rows (whose tangential boundary terms
+  // are not of that two-term form): per-node stencils from the 2D product.
+  const bool kron = k_field == nullptr && o.abc == 1;
   if (kron && c->nlev > 1) {
     // fine-level 1D factors (radius 1) in scratch, then coarsen level by level
     double2 *g0, *h0, *wx0, *wy0, *tmp;
@@ -1072,6 +1074,9 @@ mg_status mg_setup(mg_handle* out, int nx, int ny, double h, const double* k_fie
   if (o.transfer != 0 && o.transfer != 1) FAIL(MG_EINVAL, "transfer must be 0 (Eq. (xex)) or 1 (linear)");
   if (o.flat != 0 && o.flat != 1) FAIL(MG_EINVAL, "flat must be 0 or 1");
   if (o.kron_chunk < 0 || o.kron_chunk > 1024) FAIL(MG_EINVAL, "kron_chunk must be in 0..1024");
+  if (o.abc != 1 && o.abc != 2) FAIL(MG_EINVAL, "abc must be 1 or 2");
+  if (o.abc == 2 && o.precision == 2)
+    FAIL(MG_EINVAL, "the second-order absorbing rows need precision 0 or 1 (the float-float loop keeps the first-order rows)");
   if ((long long)(nx + 1) * (ny + 1) > (1LL << 31) / 8) FAIL(MG_EINVAL, "grid too large");
   mg_ctx* c = new mg_ctx();
   c->opt = o;
@@ -1182,7 +1187,7 @@ mg_status mg_setup_ragged(mg_handle* out, int nprob, const int* nx, const int* n
   // one flattened launch per kernel over all problems: GMRES(3) smoothing
   // with the march kernels, precision 0 or 1, the stand-alone cycle, and
   // every problem's coarsest grid inside its coarse-cycle launch
-  bool flat = o.flat == 1 && o.smoother == 1 && o.fuse == 1 && o.march != 0 && o.precision <= 1 && o.krylov == 0 &&
+  bool flat = o.flat == 1 && o.smoother == 1 && o.fuse == 1 && o.march != 0 && o.precision <= 1 && o.krylov == 0 && o.abc == 1 &&
               o.coarse_mode == 0;
   for (mg_ctx* q : c->sub) flat = flat && q->lc <= q->nlev - 1 && q->coop_grid == 0;
   if (flat) {
@@ -1625,6 +1630,7 @@ mg_status mg_gradient(mg_handle h, const void* u, const void* lam, int nsrc, con
   if (h && !h->sub.empty()) FAIL(MG_ESTATE, "not available on a ragged-batch handle");
   if (!h) FAIL(MG_EINVAL, "NULL handle");
   if (!u || !lam || !m || !g || nsrc < 1 || !(omega_f > 0)) FAIL(MG_EINVAL, "bad gradient arguments");
+  if (h->opt.abc != 1) FAIL(MG_EINVAL, "the gradient differentiates the first-order absorbing rows only (abc 1)");
   cudaStream_t s = (cudaStream_t)h->opt.stream;
   launch_gradient(h->nx, h->ny, h->h, m, omega_f, (const double2*)u, (const double2*)lam, nsrc, g, s);
   CK(cudaGetLastError());

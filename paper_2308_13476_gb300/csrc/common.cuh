@@ -116,9 +116,13 @@ inline Xfer xfer_of(int kind) { return kind == 1 ? Xfer{1.0, 0.5, 0.0} : Xfer{0.
 // and passed to the kernels by value (copied back once at setup).
 // dinv[by*2+bx] = 1/(omega * A_PP) for constant k and the four boundary
 // classes (bx = node on a vertical boundary line, by = on a horizontal one).
+// abc2 = 1: the second-order absorbing rows (a variant the paper does not
+// use, below), ih3q = 1 / (4 h^3).
 template <class T> struct Op0Consts {
   T inv_h2, inv_h, k, k2, omega, beta2;
   cx<T> dinv[4];
+  int abc2;
+  T ih3q;
 };
 
 // Matrix-free fine-level operator: ghost-eliminated Sommerfeld rows scaled
@@ -126,7 +130,13 @@ template <class T> struct Op0Consts {
 // vertical boundary line (else 1) and wy likewise,
 //   (A x)_P = [4 wx wy x_P - wy (x_E + x_W) - wx (x_N + x_S)] / h^2
 //             - wx wy k_P^2 x_P - i (k_P / h)(bx wy + wx by) x_P
-// and halo nodes read as zero.
+// and halo nodes read as zero.  With c.abc2 the boundary rows carry the
+// second-order absorbing condition of Engquist and Majda, d u/dn - i k u -
+// (i/2k) d^2 u/dtau^2 = 0: its tangential term, in the weak form the
+// boundary stiffness (i/2k) int dtau u dtau v with natural corners, adds
+// for every boundary segment P-Q of a side through P
+//   i c_PQ (x_P - x_Q),  c_PQ = (1/k_P + 1/k_Q) / (4 h^3)
+// (an edge node has two such segments, a corner one on each of its sides).
 template <class T> struct Op0 {
   Op0Consts<T> c;
   const T* kf;     // per-node k, dense (ny+1)*(nx+1), or null for constant k
@@ -160,7 +170,40 @@ template <class T> struct Op0 {
     const T sr = wy * (xe.x + xw.x) + wx * (xn.x + xs.x), si = wy * (xe.y + xw.y) + wx * (xn.y + xs.y);
     const T d = w * fma(-k, k, T(4) * c.inv_h2);
     const T sb = (k * c.inv_h) * (T(bx) * wy + wx * T(by));
-    return mk<T>(fma(d, xp.x, fma(sb, xp.y, -c.inv_h2 * sr)), fma(d, xp.y, fma(-sb, xp.x, -c.inv_h2 * si)));
+    const cx<T> a = mk<T>(fma(d, xp.x, fma(sb, xp.y, -c.inv_h2 * sr)), fma(d, xp.y, fma(-sb, xp.x, -c.inv_h2 * si)));
+    if (!c.abc2) return a;
+    T tr = T(0), ti = T(0);   // sum over the segments of c_PQ (x_P - x_Q)
+    const T ik = T(1) / k;
+    auto seg = [&](cx<T> xq, int iq, int jq) {
+      const T cs = c.ih3q * (ik + T(1) / kval(iq, jq));
+      tr = fma(cs, xp.x - xq.x, tr);
+      ti = fma(cs, xp.y - xq.y, ti);
+    };
+    if (by) {   // bottom or top side: neighbours along x
+      if (i > 0) seg(xw, i - 1, j);
+      if (i < nx) seg(xe, i + 1, j);
+    }
+    if (bx) {   // left or right side: neighbours along y
+      if (j > 0) seg(xs, i, j - 1);
+      if (j < ny) seg(xn, i, j + 1);
+    }
+    return mk<T>(a.x - ti, a.y + tr);
+  }
+  // the second-order absorbing rows' diagonal contribution at (i, j): sum of
+  // c_PQ over the node's boundary segments (times i); 0 off the boundary
+  __device__ __forceinline__ T abc2_diag(int i, int j, int bx, int by) const {
+    if (!c.abc2) return T(0);
+    const T ik = T(1) / kval(i, j);
+    T s = T(0);
+    if (by) {
+      if (i > 0) s += c.ih3q * (ik + T(1) / kval(i - 1, j));
+      if (i < nx) s += c.ih3q * (ik + T(1) / kval(i + 1, j));
+    }
+    if (bx) {
+      if (j > 0) s += c.ih3q * (ik + T(1) / kval(i, j - 1));
+      if (j < ny) s += c.ih3q * (ik + T(1) / kval(i, j + 1));
+    }
+    return s;
   }
   __device__ __forceinline__ cx<T> diag_inv(int i, int j) const {
     T wx, wy; int bx, by;
@@ -169,7 +212,7 @@ template <class T> struct Op0 {
     const T k = kval(i, j);
     const T w = wx * wy;
     const T dr = (T(4) * w) * c.inv_h2 - w * (k * k);
-    const T di = -(k * c.inv_h) * (T(bx) * wy + wx * T(by));
+    const T di = -(k * c.inv_h) * (T(bx) * wy + wx * T(by)) + abc2_diag(i, j, bx, by);
     return cinv<T>(mk<T>(c.omega * dr, c.omega * di));
   }
 };

@@ -126,7 +126,7 @@ template <class T> void launch_coarse_solve(const Grid& g, const double2* inv, i
 
 // Setup kernels (setup.cu).  All FP64.
 void launch_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, double k, double omega,
-                      double beta2, cudaStream_t s);
+                      double beta2, int abc, cudaStream_t s);
 // Galerkin coarse stencil (radius rc) from the fine operator: fine kind 1 uses
 // the matrix-free definition with the CSL shift beta2; kind 2/3 a stored stencil.
 void launch_galerkin(const OpView<double>& fine, int fnx, int fny, double2* coarse_st, int cnx, int cny, int rc,

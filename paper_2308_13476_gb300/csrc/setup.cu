@@ -31,17 +31,31 @@ __device__ double2 op_coef(const OpView<double>& v, int nx, int ny, int i, int j
   const int bx = (i == 0 || i == nx), by = (j == 0 || j == ny);
   const double wx = bx ? 0.5 : 1.0, wy = by ? 0.5 : 1.0, w = wx * wy;
   const double k = v.kf ? v.kf[(long long)j * (nx + 1) + i] : c->k;
+  // the second-order absorbing rows (Op0): i c_PQ on the diagonal and -i c_PQ
+  // to Q for every boundary segment P-Q of a side through P
+  auto kat = [&](int a, int b) { return v.kf ? v.kf[(long long)b * (nx + 1) + a] : c->k; };
+  auto cseg = [&](int a, int b) { return c->ih3q * (1.0 / k + 1.0 / kat(a, b)); };
   if (dx == 0 && dy == 0) {
     const double k2 = k * k;
-    return make_double2(4.0 * w * c->inv_h2 - w * k2, -w * (beta2 * k2) - (k * c->inv_h) * (bx * wy + wx * by));
+    double tang = 0.0;
+    if (c->abc2) {
+      if (by && i > 0) tang += cseg(i - 1, j);
+      if (by && i < nx) tang += cseg(i + 1, j);
+      if (bx && j > 0) tang += cseg(i, j - 1);
+      if (bx && j < ny) tang += cseg(i, j + 1);
+    }
+    return make_double2(4.0 * w * c->inv_h2 - w * k2,
+                        -w * (beta2 * k2) - (k * c->inv_h) * (bx * wy + wx * by) + tang);
   }
-  if (dy == 0 && (dx == 1 || dx == -1)) return make_double2(-wy * c->inv_h2, 0);
-  if (dx == 0 && (dy == 1 || dy == -1)) return make_double2(-wx * c->inv_h2, 0);
+  if (dy == 0 && (dx == 1 || dx == -1))
+    return make_double2(-wy * c->inv_h2, c->abc2 && by ? -cseg(i2, j2) : 0.0);
+  if (dx == 0 && (dy == 1 || dy == -1))
+    return make_double2(-wx * c->inv_h2, c->abc2 && bx ? -cseg(i2, j2) : 0.0);
   return make_double2(0, 0);
 }
 
 __global__ void s_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, double k, double omega,
-                            double beta2) {
+                            double beta2, int abc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Op0Consts<double> c;
   c.inv_h2 = 1.0 / (h * h);
@@ -50,11 +64,15 @@ __global__ void s_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, doubl
   c.k2 = k * k;
   c.omega = omega;
   c.beta2 = beta2;
+  c.abc2 = abc == 2;
+  c.ih3q = 1.0 / (4.0 * h * h * h);
   for (int by = 0; by < 2; ++by)
     for (int bx = 0; bx < 2; ++bx) {
       const double wx = bx ? 0.5 : 1.0, wy = by ? 0.5 : 1.0, w = wx * wy;
       const double dr = 4.0 * w * c.inv_h2 - w * (k * k);
-      const double di = -(k * c.inv_h) * (bx * wy + wx * by);
+      // second-order absorbing rows: an edge node and a corner both have two
+      // boundary segments, each c_PQ = 2 / (4 h^3 k) at constant k
+      const double di = -(k * c.inv_h) * (bx * wy + wx * by) + (c.abc2 && (bx || by) ? 2.0 * (2.0 * c.ih3q / k) : 0.0);
       const double2 d = make_double2(omega * dr, omega * di);
       const double dd = d.x * d.x + d.y * d.y;
       c.dinv[by * 2 + bx] = make_double2(d.x / dd, -d.y / dd);
@@ -68,6 +86,8 @@ __global__ void s_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, doubl
     f.k2 = (float)c.k2;
     f.omega = (float)c.omega;
     f.beta2 = (float)c.beta2;
+    f.abc2 = c.abc2;
+    f.ih3q = (float)c.ih3q;
     for (int q = 0; q < 4; ++q) f.dinv[q] = make_float2((float)c.dinv[q].x, (float)c.dinv[q].y);
     *c32 = f;
   }
@@ -316,8 +336,8 @@ void launch_diaginv_op(const OpView<double>& op, int nx, int ny, double omega, d
 }
 
 void launch_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, double h, double k, double omega, double beta2,
-                      cudaStream_t s) {
-  s_op0consts<<<1, 32, 0, s>>>(c64, c32, h, k, omega, beta2);
+                      int abc, cudaStream_t s) {
+  s_op0consts<<<1, 32, 0, s>>>(c64, c32, h, k, omega, beta2, abc);
 }
 void launch_galerkin(const OpView<double>& fine, int fnx, int fny, double2* cst, int cnx, int cny, int rc, double beta2,
                      const Xfer& xw, cudaStream_t s) {
