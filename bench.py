@@ -59,11 +59,14 @@ def parse():
     p.add_argument("--error-max-cycles", type=int, default=100,
                    help="run the oracle's solve for error_vs_oracle only when it needs at most this many cycles")
     p.add_argument("--workload", default="batched",
-                   choices=["batched", "layered", "ragged", "gradient", "two-grid", "sweep"],
+                   choices=["batched", "layered", "ragged", "gradient", "two-grid", "sweep", "absorbing"],
                    help="batched: the bench line (default); the others print one JSON line for the other "
                         "workloads: layered velocity model at --freq Hz, a ragged batch of 32 problems, the "
                         "adjoint gradient of a receiver misfit")
     p.add_argument("--freq", type=float, default=10.0, help="layered workload: frequency in Hz (10, 20, 40)")
+    p.add_argument("--abc", type=int, default=1, choices=[1, 2],
+                   help="absorbing boundary rows: 1 the first-order condition of Sec. 2, 2 the second-order "
+                        "Engquist-Majda condition (a variant; batched, layered and absorbing workloads)")
     p.add_argument("--transfer", default="bezier", choices=["bezier", "linear"],
                    help="inter-grid transfers: Eq. (xex) or linear interpolation (ablation)")
     p.add_argument("--krylov", type=int, default=0,
@@ -382,7 +385,7 @@ def run_ours(a):
         shapes = dict(shapes or {"march": a.march})
         s = hm.Solver(n, n, h, k, a.beta2, cycle=a.cycle, smoother=a.smoother, nu_pre=a.nu, nu_post=a.nu,
                       precision=precision, batch=a.batch, max_cycles=20000, krylov=a.krylov,
-                      transfer=a.transfer, stream=S, **shapes)
+                      transfer=a.transfer, abc=a.abc, stream=S, **shapes)
         torch.cuda.synchronize()
         return s, time.perf_counter() - t0
 
@@ -650,6 +653,55 @@ def _event_ms(fn, steps):
     return tot / steps, out
 
 
+def run_absorbing(a):
+    """What the second-order absorbing rows buy: a centre point source in a
+    homogeneous medium (k = 0.625 n on the unit square, n = --n), solved with
+    the first- and the second-order rows, each compared with a reference on
+    a domain five times as wide (the same h; first-order rows two domain
+    widths away, where the outgoing wave has spread and been absorbed)
+    restricted to the unit square: the relative difference is the boundary's
+    reflection in the solution.  FP64 path, GMRES(3) V(2,2), tol 1e-10; the
+    cycle counts and DOF-solves/s of both rows on the unit square."""
+    import torch
+    import paper_2308_13476_gb300 as hm
+    import synth
+    torch.cuda.set_device(0)
+    n = a.n if a.n != 1024 else 256
+    k = 0.625 * n
+    h = 1.0 / n
+    N = 5 * n
+    big = hm.Solver(N, N, h, k, 1.0 / k, smoother="gmres3", nu_pre=2, nu_post=2, precision="fp64", max_cycles=20000)
+    bb = torch.from_numpy(synth.point_source(N, N, h, N // 2, N // 2)).cuda()
+    xr, st, cyc_r, _ = big.solve(bb, tol=1e-10)
+    if st != hm.MG_OK:
+        raise RuntimeError(f"reference solve failed: {hm.STATUS_NAMES[st]}")
+    lo = 2 * n   # the unit square's nodes inside the wide domain
+    ref = xr[0, lo:lo + n + 1, lo:lo + n + 1].cpu().numpy()
+    big.close()
+    b = torch.from_numpy(synth.point_source(n, n, h, n // 2, n // 2)).cuda()
+    out = {"workload": f"point source, homogeneous medium, {n} x {n} cells, k = {k:g} (kh = 0.625)",
+           "unit": "relative difference from the wide-domain reference", "data": "synthetic",
+           "reference": f"{N} x {N} cells, same h, source at the centre, first-order rows "
+                        f"({int(cyc_r[0])} cycles to 1e-10)", "smoother": "gmres3", "cycle": "V(2,2)", "tol": 1e-10}
+    for abc in (1, 2):
+        s = hm.Solver(n, n, h, k, 1.0 / k, smoother="gmres3", nu_pre=2, nu_post=2, precision="fp64",
+                      max_cycles=20000, abc=abc)
+        s.solve(b, tol=1e-10)
+        ms, (x, st, cyc, rr) = _event_ms(lambda: s.solve(b, tol=1e-10), a.steps)
+        if st != hm.MG_OK:
+            raise RuntimeError(f"abc {abc} solve failed: {hm.STATUS_NAMES[st]}")
+        u = x[0].cpu().numpy()
+        inner = slice(n // 8, n - n // 8 + 1)   # away from the boundary rows themselves
+        out[f"abc{abc}"] = {"rel_diff": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+                            "rel_diff_inner": float(np.linalg.norm((u - ref)[inner, inner]) /
+                                                    np.linalg.norm(ref[inner, inner])),
+                            "cycles": int(cyc[0]), "ms_per_solve": ms,
+                            "dof_solves_per_s": (n + 1) ** 2 / (ms / 1e3)}
+        s.close()
+    out["value"] = out["abc2"]["rel_diff"]
+    print(json.dumps(out))
+
+
 def run_layered(a):
     """Variable-k workload: the seeded layered model (stand-in for the 9.2 x
     3.0 km benchmark model), h = 1500 / (10 f) m, grid 640 x 224 cells at
@@ -669,10 +721,10 @@ def run_layered(a):
     beta2 = 1.0 / (k.max() * nx * h)
     N = (nx + 1) * (nz + 1)
     out = {"workload": f"layered velocity model, {f:g} Hz, {nx} x {nz} cells, h = {h:g} m", "unit": "DOF-solves/s",
-           "data": "synthetic", "smoother": "gmres3", "cycle": "V(2,2)", "beta2": beta2, "tol": a.tol}
+           "data": "synthetic", "smoother": "gmres3", "cycle": "V(2,2)", "beta2": beta2, "tol": a.tol, "abc": a.abc}
     for prec in ([a.precision, "fp64"] if not a.no_fp64_line and a.precision != "fp64" else [a.precision]):
         s = hm.Solver(nx, nz, h, kd, beta2, smoother="gmres3", nu_pre=2, nu_post=2, precision=prec,
-                      max_cycles=20000, march=a.march)
+                      max_cycles=20000, march=a.march, abc=a.abc)
         s.solve(b, tol=a.tol)   # warm-up (graph capture)
         ms, (x, st, cyc, rr) = _event_ms(lambda: s.solve(b, tol=a.tol), a.steps)
         if st != hm.MG_OK:
@@ -875,7 +927,7 @@ def main():
                 print(json.dumps({"impl": "reference", "unavailable": f"the oracle reference arm covers the batched "
                                   f"workload (the bench headline), not the {a.workload} line"}))
             return
-        {"layered": run_layered, "ragged": run_ragged, "gradient": run_gradient,
+        {"layered": run_layered, "ragged": run_ragged, "gradient": run_gradient, "absorbing": run_absorbing,
          "two-grid": run_two_grid, "sweep": run_sweep}[a.workload](a)
         return
     if a.impl == "reference":
