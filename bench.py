@@ -216,7 +216,7 @@ def run_reference(a):
     from oracle import hierarchy as oh
     h = 1.0 / a.n
     b = (synth.source_row(a.n, a.n, h, a.batch)[0] if a.batch > 1 else synth.point_source(a.n, a.n, h)).ravel()
-    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2, kind=a.transfer)
+    H = oh.build_hierarchy(a.n, a.n, h, a.k, a.beta2, kind=a.transfer, abc=a.abc)
     opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
     x = np.zeros_like(b)
     if a.krylov:   # one FGMRES step (a preconditioning cycle and its Arnoldi work) per step
@@ -258,7 +258,8 @@ def _cycles_from_cache(a):
     try:
         d = json.load(open(p))
         return int(d.get(f"{a.k:g}/{a.n}/{a.smoother}/{a.cycle}{a.nu}/{a.beta2:g}" +
-                         (f"/fgmres{a.krylov}" if a.krylov else "") + ("/linear" if a.transfer == "linear" else "")))
+                         (f"/fgmres{a.krylov}" if a.krylov else "") + ("/linear" if a.transfer == "linear" else "") +
+                         ("/abc2" if getattr(a, "abc", 1) == 2 else "")))
     except Exception:
         return None
 
@@ -284,7 +285,7 @@ def _oracle_rhs0(a):
 def _oracle_setup(a):
     from oracle import cycle as oc
     from oracle import hierarchy as oh
-    H = oh.build_hierarchy(a.n, a.n, 1.0 / a.n, a.k, a.beta2, kind=a.transfer)
+    H = oh.build_hierarchy(a.n, a.n, 1.0 / a.n, a.k, a.beta2, kind=a.transfer, abc=a.abc)
     opt = oc.CycleOptions(1 if a.cycle == "V" else 2, a.smoother, a.nu, a.nu, 4.5)
     return H, opt
 
