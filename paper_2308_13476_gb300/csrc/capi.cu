@@ -274,6 +274,7 @@ template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, c
 // strip, and less work leaves the GPU under-filled).
 static bool use_march(const mg_ctx* c, int l) {
   if (!c->opt.fuse || c->opt.march == 0) return false;
+  if (c->lev[l].kind == 1 && c->opt.abc == 2) return false;   // the row marches carry first-order rows only
   if (c->opt.march == 1 || c->lev[l].kind >= 4) return true;
   const Grid& g = c->lev[l].g;
   return (long long)(g.nx + 1) * (g.ny + 1) * c->B + c->peer_nodes >= (4LL << 20);
@@ -281,7 +282,7 @@ static bool use_march(const mg_ctx* c, int l) {
 
 template <class T>
 static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, const int* active, cudaStream_t s,
-                        double2* outer = nullptr) {
+                        double2* outer = nullptr, bool x_zero = false) {
   const Grid& g = c->lev[l].g;
   const OpView<T> op = opT<T>(c, l);
   GmresBufs gb = vecs<T>(c)[l].gb;
@@ -290,6 +291,7 @@ static void gmres_level(mg_ctx* c, int l, cx<T>* x, const cx<T>* b, int nu, cons
   gb.ev_fork = c->ev_fork;
   gb.ev_join = c->ev_join;
   gb.outer = outer;
+  gb.x_zero = x_zero;
   const bool m = use_march(c, l);
   if (m && op.kind == 1) gmres_smooth_march<T>(g, op, x, b, nu, c->B, active, gb, s);
   else if (m && op.kind >= 4) gmres_smooth_kron<T>(g, op, x, b, nu, c->B, active, gb, s);
@@ -306,8 +308,13 @@ template <class T> struct Emit {
   // level-0 post-smoothing's last GMRES(3) update adds the cycle's result to
   // (the fused refinement update); null: the caller adds it
   double2* outer0 = nullptr;
+  // zx[l]: level l's x is zero (just cleared) until its next smoothing, whose
+  // first GMRES(3) step then takes u0 = b without applying A
+  std::vector<char> zx;
 
   void smooth(int l, int nu, double2* outer = nullptr) {
+    const bool z = zx[l] != 0;
+    zx[l] = 0;
     if (nu <= 0) return;
     auto& V = vecs<T>(c)[l];
     const Grid& g = c->lev[l].g;
@@ -324,7 +331,7 @@ template <class T> struct Emit {
         std::swap(cur[l], oth[l]);
       }
     } else {
-      gmres_level<T>(c, l, cur[l], V.b, nu, c->active, s, outer);
+      gmres_level<T>(c, l, cur[l], V.b, nu, c->active, s, outer, z);
     }
   }
 
@@ -361,6 +368,7 @@ template <class T> struct Emit {
       coarse_solve(l + 1);
     } else {
       cudaMemsetAsync(cur[l + 1], 0, sizeof(cx<T>) * (size_t)gc.vstride * c->B, s);
+      zx[l + 1] = 1;
       for (int q = 0; q < c->opt.cycle; ++q) cycle(l + 1);
     }
     launch_prolong_add<T>(g, gc, cur[l + 1], cur[l], c->B, c->active, c->xw, s);
@@ -375,6 +383,7 @@ template <class T> struct Emit {
       cur[l] = V[l].x;
       oth[l] = V[l].t;
     }
+    zx.assign(c->nlev, 0);
   }
 };
 
@@ -485,6 +494,7 @@ static void emit_mixed_iteration(mg_ctx* c, cudaStream_t s) {
                      c->nlev > 1;
   if (fused) e.outer0 = c->v64[0].x;
   cudaMemsetAsync(c->v32[0].x, 0, sizeof(float2) * (size_t)g0.vstride * c->B, s);
+  e.zx[0] = 1;
   e.cycle(0);
   if (c->opt.precision == 2) {
     launch_ff_update(g0, c->v64[0].x, e.cur[0], c->B, c->active, s);
@@ -1242,11 +1252,13 @@ static mg_status capture_precond(mg_ctx* c) {
   if (c->opt.precision == 0) {
     Emit<double> e{c, c->cap, {}, {}, c->lc, &c->plan64};
     e.init();
+    e.zx[0] = 1;   // the FGMRES restart and orthogonalisation kernels clear the cycle's x
     e.cycle(0);
     if (e.cur[0] != c->v64[0].x) launch_copy_masked<double>(c->lev[0].g, e.cur[0], c->v64[0].x, c->B, c->active, c->cap);
   } else {
     Emit<float> e{c, c->cap, {}, {}, c->lc, &c->plan32};
     e.init();
+    e.zx[0] = 1;
     e.cycle(0);
     if (e.cur[0] != c->v32[0].x) launch_copy_masked<float>(c->lev[0].g, e.cur[0], c->v32[0].x, c->B, c->active, c->cap);
   }

@@ -117,12 +117,13 @@ inline Xfer xfer_of(int kind) { return kind == 1 ? Xfer{1.0, 0.5, 0.0} : Xfer{0.
 // dinv[by*2+bx] = 1/(omega * A_PP) for constant k and the four boundary
 // classes (bx = node on a vertical boundary line, by = on a horizontal one).
 // abc2 = 1: the second-order absorbing rows (a variant the paper does not
-// use, below), ih3q = 1 / (4 h^3).
+// use, below), ih3q = 1 / (4 h^3), tang = 1 / (2 k h^3).
 template <class T> struct Op0Consts {
   T inv_h2, inv_h, k, k2, omega, beta2;
   cx<T> dinv[4];
   int abc2;
   T ih3q;
+  T tang;   // 2 ih3q / k (constant k)
 };
 
 // Matrix-free fine-level operator: ghost-eliminated Sommerfeld rows scaled
@@ -137,7 +138,10 @@ template <class T> struct Op0Consts {
 // for every boundary segment P-Q of a side through P
 //   i c_PQ (x_P - x_Q),  c_PQ = (1/k_P + 1/k_Q) / (4 h^3)
 // (an edge node has two such segments, a corner one on each of its sides).
-template <class T> struct Op0 {
+// The term is compiled only into the A2 = true operator, which handles with
+// the second-order rows use (c.abc2); the first-order kernels carry none of
+// its registers.
+template <class T, bool A2 = false> struct Op0 {
   Op0Consts<T> c;
   const T* kf;     // per-node k, dense (ny+1)*(nx+1), or null for constant k
   int nx, ny;
@@ -171,9 +175,29 @@ template <class T> struct Op0 {
     const T d = w * fma(-k, k, T(4) * c.inv_h2);
     const T sb = (k * c.inv_h) * (T(bx) * wy + wx * T(by));
     const cx<T> a = mk<T>(fma(d, xp.x, fma(sb, xp.y, -c.inv_h2 * sr)), fma(d, xp.y, fma(-sb, xp.x, -c.inv_h2 * si)));
-    if (!c.abc2) return a;
-    T tr = T(0), ti = T(0);   // sum over the segments of c_PQ (x_P - x_Q)
-    const T ik = T(1) / k;
+    if constexpr (!A2) {
+      return a;
+    } else {
+      return add<T>(a, abc2_term(xp, xe, xw, xn, xs, i, j, bx, by));
+    }
+  }
+  // the tangential term: i sum_Q c_PQ (x_P - x_Q)
+  __device__ __forceinline__ cx<T> abc2_term(cx<T> xp, cx<T> xe, cx<T> xw, cx<T> xn, cx<T> xs, int i, int j, bool bx,
+                                             bool by) const {
+    if (kf) return abc2_var(xp, xe, xw, xn, xs, i, j, bx, by);
+    // constant k: every segment has c_PQ = 2 ih3q / k = c.tang
+    const bool sw = by && i > 0, se = by && i < nx, ss = bx && j > 0, sn = bx && j < ny;
+    const T cnt = T(sw) + T(se) + T(ss) + T(sn);
+    const T qr = (sw ? xw.x : T(0)) + (se ? xe.x : T(0)) + (ss ? xs.x : T(0)) + (sn ? xn.x : T(0));
+    const T qi = (sw ? xw.y : T(0)) + (se ? xe.y : T(0)) + (ss ? xs.y : T(0)) + (sn ? xn.y : T(0));
+    const T tr = c.tang * fma(cnt, xp.x, -qr), ti = c.tang * fma(cnt, xp.y, -qi);
+    return mk<T>(-ti, tr);
+  }
+  // the tangential term i sum_Q c_PQ (x_P - x_Q) for variable k
+  __device__ __forceinline__ cx<T> abc2_var(cx<T> xp, cx<T> xe, cx<T> xw, cx<T> xn, cx<T> xs, int i, int j, bool bx,
+                                         bool by) const {
+    T tr = T(0), ti = T(0);
+    const T ik = T(1) / kval(i, j);
     auto seg = [&](cx<T> xq, int iq, int jq) {
       const T cs = c.ih3q * (ik + T(1) / kval(iq, jq));
       tr = fma(cs, xp.x - xq.x, tr);
@@ -187,12 +211,12 @@ template <class T> struct Op0 {
       if (j > 0) seg(xs, i, j - 1);
       if (j < ny) seg(xn, i, j + 1);
     }
-    return mk<T>(a.x - ti, a.y + tr);
+    return mk<T>(-ti, tr);
   }
   // the second-order absorbing rows' diagonal contribution at (i, j): sum of
   // c_PQ over the node's boundary segments (times i); 0 off the boundary
   __device__ __forceinline__ T abc2_diag(int i, int j, int bx, int by) const {
-    if (!c.abc2) return T(0);
+    if constexpr (!A2) return T(0);
     const T ik = T(1) / kval(i, j);
     T s = T(0);
     if (by) {

@@ -68,12 +68,10 @@ __device__ __forceinline__ double warp_sum(double t) {
 }
 
 // The fine operator in precision T (the cycle's level-0 operator).
-template <class T> __device__ __forceinline__ Op0<T> op_t(const FgArgs& a);
-template <> __device__ __forceinline__ Op0<double> op_t<double>(const FgArgs& a) {
-  return Op0<double>{a.c0, a.kf, a.g.nx, a.g.ny};
-}
-template <> __device__ __forceinline__ Op0<float> op_t<float>(const FgArgs& a) {
-  return Op0<float>{a.c0f, a.kf32, a.g.nx, a.g.ny};
+// A2 selects the second-order absorbing rows at compile time.
+template <class T, bool A2> __device__ __forceinline__ Op0<T, A2> op_t(const FgArgs& a) {
+  if constexpr (std::is_same<T, double>::value) return Op0<T, A2>{a.c0, a.kf, a.g.nx, a.g.ny};
+  else return Op0<T, A2>{a.c0f, a.kf32, a.g.nx, a.g.ny};
 }
 
 // Sums four values over a warp in six shuffles: the first two rounds halve
@@ -140,9 +138,9 @@ __device__ bool fg_reduce(const FgArgs& a, int rhs, int nval, const double* mine
 
 // ------------------------------------------------------------------ restart
 
-template <class T>
-__global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> op, cx<T>* __restrict__ cb,
-                                                         cx<T>* __restrict__ cxv) {
+template <class T, bool A2>
+__global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, cx<T>* __restrict__ cb, cx<T>* __restrict__ cxv) {
+  const Op0<double, A2> op = op_t<double, A2>(a);
   __shared__ double red[FBY], tot[1], mine[1];
   const int rhs = blockIdx.z;
   if (a.state[rhs] != 0) return;   // block-uniform
@@ -203,7 +201,7 @@ __global__ void __launch_bounds__(FTHREADS) k_fg_restart(FgArgs a, Op0<double> o
 
 // ------------------------------------------------------------------ dots (MGS coefficients)
 
-template <class T>
+template <class T, bool A2>
 __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_dots(FgArgs a, const cx<T>* __restrict__ z, int jj) {
   __shared__ double red[FNV][FBY];
   __shared__ double mine[FNV], tot[FNV];
@@ -215,7 +213,7 @@ __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_dots(FgArgs a, cons
   __syncthreads();
   const Grid& g = a.g;
   const long long off = (long long)rhs * g.vstride;
-  const Op0<T> op = op_t<T>(a);
+  const Op0<T, A2> op = op_t<T, A2>(a);
   const cx<T>* zs = z + off;
   cx<T>* zj = (cx<T>*)a.Z + jj * a.vlen + off;
   const cx<T>* vj = (const cx<T>*)a.V + jj * a.vlen + off;
@@ -381,7 +379,7 @@ __device__ void fg_finish_step(const FgArgs& a, int rhs, int jj, double sumsq) {
   }
 }
 
-template <class T>
+template <class T, bool A2>
 __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_orth(FgArgs a, int jj, cx<T>* __restrict__ cb,
                                                                   cx<T>* __restrict__ cxv) {
   __shared__ cx<T> hs[FG_MAXM + 1];
@@ -396,7 +394,7 @@ __global__ void __launch_bounds__(FTHREADS, FG_MINB<T>) k_fg_orth(FgArgs a, int 
     hs[tid] = mk<T>((T)(S[L.h(jj, tid)] * si), (T)(S[L.h(jj, tid) + 1] * si));
   }
   __syncthreads();
-  const Op0<T> op = op_t<T>(a);
+  const Op0<T, A2> op = op_t<T, A2>(a);
   const Grid& g = a.g;
   const long long off = (long long)rhs * g.vstride;
   const cx<T>* zj = (const cx<T>*)a.Z + jj * a.vlen + off;
@@ -500,7 +498,6 @@ template <class T> __global__ void __launch_bounds__(FTHREADS) k_fg_update(FgArg
   }
 }
 
-inline Op0<double> fine_op64(const FgArgs& a) { return Op0<double>{a.c0, a.kf, a.g.nx, a.g.ny}; }
 inline dim3 fg_grid(const FgArgs& a) { return dim3(a.nbr, 1, a.B); }
 
 }  // namespace
@@ -511,8 +508,8 @@ void fg_geometry(const Grid& g, int B, bool fp64z, FgArgs& a) {
   int dev = 0, sms = 148, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (fp64z) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fg_dots<double>, FTHREADS, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fg_dots<float>, FTHREADS, 0);
+  if (fp64z) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fg_dots<double, false>, FTHREADS, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fg_dots<float, false>, FTHREADS, 0);
   cudaGetLastError();
   per = per < 1 ? 1 : per;
   // about four waves of blocks over all right-hand sides
@@ -522,13 +519,16 @@ void fg_geometry(const Grid& g, int B, bool fp64z, FgArgs& a) {
 }
 
 template <class T> void launch_fg_restart(const FgArgs& a, cx<T>* cb, cx<T>* cxv, cudaStream_t s) {
-  k_fg_restart<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, fine_op64(a), cb, cxv);
+  if (a.c0.abc2) k_fg_restart<T, true><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, cb, cxv);
+  else k_fg_restart<T, false><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, cb, cxv);
 }
 template <class T> void launch_fg_dots(const FgArgs& a, int j, const cx<T>* z, cudaStream_t s) {
-  k_fg_dots<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, z, j);
+  if (a.c0.abc2) k_fg_dots<T, true><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, z, j);
+  else k_fg_dots<T, false><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, z, j);
 }
 template <class T> void launch_fg_orth(const FgArgs& a, int j, cx<T>* cb, cx<T>* cxv, cudaStream_t s) {
-  k_fg_orth<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j, cb, cxv);
+  if (a.c0.abc2) k_fg_orth<T, true><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j, cb, cxv);
+  else k_fg_orth<T, false><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a, j, cb, cxv);
 }
 template <class T> void launch_fg_update(const FgArgs& a, cudaStream_t s) {
   k_fg_update<T><<<fg_grid(a), dim3(FBX, FBY), 0, s>>>(a);

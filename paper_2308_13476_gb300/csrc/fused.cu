@@ -59,7 +59,7 @@ __device__ __forceinline__ void k_resid_restrict_body(uint3 vblk, dim3 vgrid, Gr
   const int I0 = blockIdx.x * CTX, J0 = blockIdx.y * CTY;
   const int fx0 = 2 * I0 - 2, fy0 = 2 * J0 - 2;   // fine origin of the footprint
   const int tid = threadIdx.y * CTX + threadIdx.x;
-  if constexpr (std::is_same<Op, Op0<T>>::value) {
+  if constexpr (std::is_same<Op, Op0<T>>::value || std::is_same<Op, Op0<T, true>>::value) {
     // matrix-free fine level: a fixed, unrolled count of footprint nodes per
     // thread, each evaluated at its node clamped into the grid (every load is
     // in bounds and unconditional, so the loads of all of them can be in
@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(CTX * CTY) k_resid_restrict_rag(const __grid_c
 constexpr int JTX = 64, JTY = 16;        // output tile of k_jacobi_fused
 constexpr int JMAXNU = 4;                // sweeps fused in one launch (more: several launches)
 
-template <class T>
-__global__ void __launch_bounds__(256) k_jacobi_fused(Grid g, Op0<T> op, const cx<T>* __restrict__ x,
+template <class T, bool A2 = false>
+__global__ void __launch_bounds__(256) k_jacobi_fused(Grid g, Op0<T, A2> op, const cx<T>* __restrict__ x,
                                                       const cx<T>* __restrict__ b, cx<T>* __restrict__ xo, int nu,
                                                       const int* __restrict__ active) {
   extern __shared__ unsigned char smem_raw[];
@@ -270,9 +270,12 @@ template <class T> size_t jacobi_fused_smem(int nu) {
 template <class T>
 void launch_jacobi_fused(const Grid& g, const OpView<T>& v, const cx<T>* x, const cx<T>* b, cx<T>* xo, int nu, int B,
                          const int* active, cudaStream_t s) {
-  Op0<T> op{v.c0, v.kf, g.nx, g.ny};
   const dim3 grd(cdiv(g.nx + 1, JTX), cdiv(g.ny + 1, JTY), B);
-  k_jacobi_fused<T><<<grd, 256, jacobi_fused_smem<T>(nu), s>>>(g, op, x, b, xo, nu, active);
+  if (v.c0.abc2)
+    k_jacobi_fused<T, true><<<grd, 256, jacobi_fused_smem<T>(nu), s>>>(g, Op0<T, true>{v.c0, v.kf, g.nx, g.ny}, x, b, xo,
+                                                                       nu, active);
+  else
+    k_jacobi_fused<T><<<grd, 256, jacobi_fused_smem<T>(nu), s>>>(g, Op0<T>{v.c0, v.kf, g.nx, g.ny}, x, b, xo, nu, active);
 }
 
 int jacobi_fused_max_nu() { return JMAXNU; }
@@ -280,6 +283,12 @@ int jacobi_fused_max_nu() { return JMAXNU; }
 cudaError_t configure_fused_kernels() {   // allow the complex128 window (> 48 KiB) on the current device
   cudaError_t e = cudaFuncSetAttribute(k_jacobi_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)jacobi_fused_smem<double>(JMAXNU));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_jacobi_fused<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)jacobi_fused_smem<double>(JMAXNU));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_jacobi_fused<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)jacobi_fused_smem<float>(JMAXNU));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_jacobi_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)jacobi_fused_smem<float>(JMAXNU));

@@ -264,6 +264,33 @@ template <class T, int MD> struct P0 {
   }
 };
 
+// M0 on a zero x (u0 = b, not stored): b row t arrives; |u0|^2 on row t-1
+// and A u0 on row t-2, in P0's order (the same sums as P0 with x = 0).
+template <class T, int MD> struct P0Z {
+  static constexpr int NP = MNP<T>::NP;
+  MIn<T, MD, 1> m;   // 0: b
+  T acc[3];
+  template <int S> __device__ __forceinline__ void step(int t) {
+    m.template fetch<S>(t);
+    const MCtx<T, MD>& c = m.c;
+    if (t < c.j0) return;
+    const Row<T>(&U)[4] = m.F[0];
+#pragma unroll
+    for (int n = 0; n < NP; ++n)
+      if (c.cnt(n, t - 1)) acc[0] += abs2<T>(U[Sl<S, -1>::v].v[n]);
+    if (t - 2 >= c.j0) {
+      const Row<T> au = c.apply(U[Sl<S, -3>::v], U[Sl<S, -2>::v], U[Sl<S, -1>::v], t - 2);
+#pragma unroll
+      for (int n = 0; n < NP; ++n)
+        if (c.cnt(n, t - 2)) {
+          const cx<T> d = cmul<T>(U[Sl<S, -2>::v].v[n], au.v[n]);
+          acc[1] += d.x;
+          acc[2] += d.y;
+        }
+    }
+  }
+};
+
 // M1 at iteration t: u0 row t arrives; u1 row t-1 formed; A u1 on row t-2.
 template <class T, int MD> struct P1 {
   static constexpr int NP = MNP<T>::NP;
@@ -538,6 +565,25 @@ __global__ void __launch_bounds__(32) gm_init_rag(const __grid_constant__ RagLau
   gm_init_body<T, MD>(vb, a.g, a.mg, a.op, a.x, a.b, a.u0, a.st, a.partial, a.tickets, a.active);
 }
 
+// M0 on a zero x: u0 = b (the caller passes b as u0 to the later passes).
+template <class T, int MD>
+__global__ void __launch_bounds__(32) gm_init_zero(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ b,
+                                                   double* st, double* partial, unsigned* tickets,
+                                                   const int* __restrict__ active) {
+  MPRO
+  T acc[3];
+  __shared__ __align__(16) unsigned char stg[ring_bytes<1>()];
+  double* sh = reinterpret_cast<double*>(stg);
+  run_pass<P0Z>(ctx, j1 + 1, stg, acc, [&](auto& p) { p.m.src[0] = b + off; });
+  finish<MD>(acc, sh, partial, tickets, rhs, (int)blockIdx.x, mg, S, [](auto* s, const double* q) {
+    fin_init<T>(s, q);
+    if (s[G_BRK] == 0) {
+      const double d[2] = {q[1] * s[G_S], q[2] * s[G_S]};
+      fin_a<0, T>(s, d);
+    }
+  });
+}
+
 // M1: u1 = s0 A u0 - c00 u0; |u1|^2, <u1, u0>, then <u0, A u1>, <u1, A u1>.
 template <class T, int MD>
 __device__ __forceinline__ void gm_step1_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
@@ -752,25 +798,36 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
     }
   };
   for (int step = 0; step < nu; ++step) {
-    pass([&] { gm_init<T, 1><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active); },
-         [&] { gm_init<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); },
-         [&] { gm_init<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); });
-    pass([&] { gm_step1<T, 1><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, st, P, tk, active); },
-         [&] { gm_step1<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, u0, u1, st, P, tk, active); },
-         [&] { gm_step1<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, st, P, tk, active); });
-    pass([&] { gm_step2<T, 1><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
-         [&] { gm_step2<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
-         [&] { gm_step2<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
-    pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
-         [&] { gm_step3<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); },
-         [&] { gm_step3<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, u0, u1, u2, st, P, tk, active); });
+    // a zero x: u0 = b itself (read-only in every later pass)
+    const bool z = step == 0 && gb.x_zero;
+    if (z) {
+      pass([&] { gm_init_zero<T, 1><<<gi, 32, 0, s>>>(g, mg, op, b, st, P, tk, active); },
+           [&] { gm_init_zero<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, b, st, P, tk, active); },
+           [&] { gm_init_zero<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, b, st, P, tk, active); });
+    } else {
+      pass([&] { gm_init<T, 1><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active); },
+           [&] { gm_init<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); },
+           [&] { gm_init<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); });
+    }
+    const cx<T>* v0 = z ? b : u0;
+    GmresBufs gs = gb;
+    gs.u[0] = (void*)v0;
+    pass([&] { gm_step1<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, st, P, tk, active); },
+         [&] { gm_step1<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, st, P, tk, active); },
+         [&] { gm_step1<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, st, P, tk, active); });
+    pass([&] { gm_step2<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+         [&] { gm_step2<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+         [&] { gm_step2<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); });
+    pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+         [&] { gm_step3<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+         [&] { gm_step3<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); });
     if constexpr (sizeof(T) == 4) {
       if (step == nu - 1 && gb.outer) {
-        launch_gmres_update_outer(g, x, gb, B, active, s);
+        launch_gmres_update_outer(g, x, gs, B, active, s);
         continue;
       }
     }
-    launch_gmres_update<T>(g, x, gb, B, active, s);
+    launch_gmres_update<T>(g, x, gs, B, active, s);
   }
 }
 

@@ -45,7 +45,10 @@ template <class T, int R> inline OpK<T, R> kron_op(const OpView<T>& v, int nx, i
 
 template <class T, class F> inline void with_op(const OpView<T>& v, int nx, int ny, F&& f) {
   switch (v.kind) {
-    case 1: f(Op0<T>{v.c0, v.kf, nx, ny}); break;
+    case 1:   // the second-order absorbing rows are a separate instantiation
+      if (v.c0.abc2) f(Op0<T, true>{v.c0, v.kf, nx, ny});
+      else f(Op0<T>{v.c0, v.kf, nx, ny});
+      break;
     case 2: f(OpS<T, 2>{v.st, v.dinv, v.plane, nx, ny}); break;
     case 3: f(OpS<T, 3>{v.st, v.dinv, v.plane, nx, ny}); break;
     case 4: f(kron_op<T, 2>(v, nx, ny)); break;
@@ -167,6 +170,9 @@ struct GmresBufs {
                        // added by the fused update (null: none)
   int kron_ch;         // rows per chunk of the Kronecker-level column marches
                        // (0: chosen from the kernel's occupancy)
+  int x_zero;          // x is zero on entry: the first step takes b itself as
+                       // u0 = b - A x (no apply, no u0 write; b is read-only
+                       // in every pass) and only sums |b|^2 for its norm
 };
 // The last GMRES(3) update of a complex64 level-0 smoothing fused with the
 // FP64 refinement update x64 += x (kernels_gmres.cu).

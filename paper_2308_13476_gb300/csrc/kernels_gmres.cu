@@ -88,6 +88,29 @@ __global__ void __launch_bounds__(BX * BY) g_init(Grid g, Op op, const cx<T>* __
   if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(gstate<T>(st, rhs), v);
 }
 
+// g_init with x = 0: u0 = b (the caller takes b as u0), partial |b|^2 in
+// g_init's order, so the state equals g_init's on a zero x.
+template <class T>
+__global__ void __launch_bounds__(BX * BY) g_init_zero(Grid g, const cx<T>* __restrict__ b, double* __restrict__ st,
+                                                       double* partial, unsigned* tickets,
+                                                       const int* __restrict__ active) {
+  __shared__ double sh[NVMAX * 32];
+  GNODE
+  if (active && !active[rhs]) return;
+  T a0[1] = {T(0)};
+  if (nv > 0) {
+    GROWS {
+      if (j > g.ny) break;
+      const Pack<T> r = load_pack(b + off, g.at(i0, j));
+#pragma unroll
+      for (int n = 0; n < NP; ++n)
+        if (n < nv) a0[0] += abs2<T>(r.v[n]);
+    }
+  }
+  double v[1];
+  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && t0) fin_init<T>(gstate<T>(st, rhs), v);
+}
+
 // w = A v_J (v_J = s_J u_J); partial dots <u_i, w> for i <= J
 template <class T, class Op, int J>
 __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* __restrict__ u0, const cx<T>* __restrict__ u1,
@@ -326,23 +349,30 @@ void gmres_smooth(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T>* b,
   with_op<T>(opv, g.nx, g.ny, [&](auto op) {
     using Op = decltype(op);
     for (int step = 0; step < nu; ++step) {
-      g_init<T, Op><<<grd, blk, 0, s>>>(g, op, x, b, u0, st, P, tk, active);
-      g_arn_a<T, Op, 0><<<grd, blk, 0, s>>>(g, op, u0, u1, u2, w, st, P, tk, active);
-      g_arn_b<T, 0><<<grd, blk, 0, s>>>(g, u0, u1, u2, u1, w, st, P, tk, active, -1);
-      g_arn_a<T, Op, 1><<<grd, blk, 0, s>>>(g, op, u0, u1, u2, w, st, P, tk, active);
-      g_arn_b<T, 1><<<grd, blk, 0, s>>>(g, u0, u1, u2, u2, w, st, P, tk, active, -1);
-      g_arn_a<T, Op, 2><<<grd, blk, 0, s>>>(g, op, u0, u1, u2, w, st, P, tk, active);
-      g_arn_b<T, 2><<<grd, blk, 0, s>>>(g, u0, u1, u2, nullptr, w, st, P, tk, active, -1);
+      // a zero x: u0 = b itself (read-only in every later pass), no apply
+      const bool z = step == 0 && gb.x_zero;
+      const cx<T>* v0 = z ? b : u0;
+      if (z) g_init_zero<T><<<grd, blk, 0, s>>>(g, b, st, P, tk, active);
+      else g_init<T, Op><<<grd, blk, 0, s>>>(g, op, x, b, u0, st, P, tk, active);
+      g_arn_a<T, Op, 0><<<grd, blk, 0, s>>>(g, op, v0, u1, u2, w, st, P, tk, active);
+      g_arn_b<T, 0><<<grd, blk, 0, s>>>(g, v0, u1, u2, u1, w, st, P, tk, active, -1);
+      g_arn_a<T, Op, 1><<<grd, blk, 0, s>>>(g, op, v0, u1, u2, w, st, P, tk, active);
+      g_arn_b<T, 1><<<grd, blk, 0, s>>>(g, v0, u1, u2, u2, w, st, P, tk, active, -1);
+      g_arn_a<T, Op, 2><<<grd, blk, 0, s>>>(g, op, v0, u1, u2, w, st, P, tk, active);
+      g_arn_b<T, 2><<<grd, blk, 0, s>>>(g, v0, u1, u2, nullptr, w, st, P, tk, active, -1);
+      GmresBufs gs = gb;
+      gs.u[0] = (void*)v0;
       if constexpr (sizeof(T) == 4) {
         if (step == nu - 1 && gb.outer) {
-          launch_gmres_update_outer(g, x, gb, B, active, s);
+          launch_gmres_update_outer(g, x, gs, B, active, s);
           continue;
         }
       }
-      g_update<T><<<grd, blk, 0, s>>>(g, x, u0, u1, u2, st, active);
+      g_update<T><<<grd, blk, 0, s>>>(g, x, v0, u1, u2, st, active);
     }
   });
 }
+
 
 template <class T>
 void launch_gmres_update(const Grid& g, cx<T>* x, const GmresBufs& gb, int B, const int* active, cudaStream_t s) {

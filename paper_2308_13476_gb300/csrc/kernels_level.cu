@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(BX * BY) k_resnorm_stop_rag(const __grid_const
 // blocks), which resolves the stopping test's relative residual to about
 // 1e-7 of itself.  The conversions to float take the integer pipe
 // (f32_from_f64_rn, the same rounding as the hardware's).
-__device__ __forceinline__ void k_resid_cast_stop_body(uint3 vblk, dim3 vgrid, Grid g, Op0<double> op, const double2* __restrict__ x, const double2* __restrict__ b, float2* __restrict__ r32, Ctl c, int count) {
+template <bool A2>
+__device__ __forceinline__ void k_resid_cast_stop_body(uint3 vblk, dim3 vgrid, Grid g, Op0<double, A2> op, const double2* __restrict__ x, const double2* __restrict__ b, float2* __restrict__ r32, Ctl c, int count) {
   const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
   const dim3 gridDim = vgrid;
   (void)blockIdx;
@@ -230,8 +231,9 @@ __device__ __forceinline__ void k_resid_cast_stop_body(uint3 vblk, dim3 vgrid, G
     stop_update(c, rhs, v[0], count);
 }
 
-__global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double> op, const double2* __restrict__ x, const double2* __restrict__ b, float2* __restrict__ r32, Ctl c, int count) {
-  k_resid_cast_stop_body(blockIdx, gridDim, g, op, x, b, r32, c, count);
+template <bool A2>
+__global__ void __launch_bounds__(BX * BY) k_resid_cast_stop(Grid g, Op0<double, A2> op, const double2* __restrict__ x, const double2* __restrict__ b, float2* __restrict__ r32, Ctl c, int count) {
+  k_resid_cast_stop_body<A2>(blockIdx, gridDim, g, op, x, b, r32, c, count);
 }
 
 __global__ void __launch_bounds__(BX * BY) k_resid_cast_stop_rag(const __grid_constant__ RagLaunch<RcA> L) {
@@ -461,8 +463,12 @@ void launch_resnorm_stop(const Grid& g, const OpView<T>& v, const cx<T>* x, cons
 }
 void launch_resid_cast_stop(const Grid& g, const OpView<double>& v, const double2* x, const double2* b, float2* r32,
                             int B, const Ctl& c, int count, cudaStream_t s) {
-  Op0<double> op{v.c0, v.kf, g.nx, g.ny};  // constants by value
-  k_resid_cast_stop<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, op, x, b, r32, c, count);
+  if (v.c0.abc2)   // constants by value
+    k_resid_cast_stop<true><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, Op0<double, true>{v.c0, v.kf, g.nx, g.ny}, x, b,
+                                                                     r32, c, count);
+  else
+    k_resid_cast_stop<false><<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, Op0<double>{v.c0, v.kf, g.nx, g.ny}, x, b, r32,
+                                                                      c, count);
 }
 void launch_update_mixed(const Grid& g, double2* x, const float2* e, int B, const int* active, cudaStream_t s) {
   k_update_mixed<<<node_grid(g, B), dim3(BX, BY), 0, s>>>(g, x, e, active);

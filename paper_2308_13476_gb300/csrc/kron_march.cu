@@ -321,6 +321,33 @@ __device__ __forceinline__ void km_init_body(uint3 vblk, dim3 vgrid, Grid g, KGe
     fin_init<T>(gstate<T>(st, rhs), v);
 }
 
+// km_init on a zero x: u0 = b (the caller passes b as u0 to the later
+// passes); each lane sums |b|^2 down its column of the chunk, in km_init's
+// order and over its blocks, so the state equals km_init's on a zero x.
+template <class T>
+__global__ void __launch_bounds__(KW * 32) km_init_zero(Grid g, KGeo kg, const cx<T>* __restrict__ b, double* st,
+                                                        double* partial, unsigned* tickets,
+                                                        const int* __restrict__ active) {
+  __shared__ double sh[NVMAX * 32];
+  const int rhs = blockIdx.z;
+  if (active && !active[rhs]) return;
+  const long long off = (long long)rhs * g.vstride;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * KW + (threadIdx.x >> 5);
+  const bool has = gw < kg.ncw * kg.nchunks;
+  const int i = (has ? gw % kg.ncw : 0) * 32 + lane;
+  const int j0 = (has ? gw / kg.ncw : 0) * kg.ch, j1 = min(j0 + kg.ch, g.ny + 1);
+  T a0[1] = {T(0)};
+  if (has && i <= g.nx) {
+    const cx<T>* bs = b + off;
+#pragma unroll 4
+    for (int m = j0; m < j1; ++m) a0[0] += abs2<T>(bs[g.at(i, m)]);
+  }
+  double v[1];
+  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, gridDim.x, blockIdx.x) && threadIdx.x == 0)
+    fin_init<T>(gstate<T>(st, rhs), v);
+}
+
 template <class T, int R>
 __global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st, double* partial, unsigned* tickets, const int* __restrict__ active) {
   km_init_body<T, R>(blockIdx, gridDim, g, kg, op, x, b, u0, st, partial, tickets, active);
@@ -687,25 +714,31 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
     const KGeo kg = kron_geo(g, B, R, kron_capacity<T, R>(fused), gb.kron_ch);
     const dim3 grd(cdiv((long long)kg.ncw * kg.nchunks, KW), 1, B);
     for (int step = 0; step < nu; ++step) {
-      km_init<T, R><<<grd, KW * 32, 0, s>>>(g, kg, op, x, b, u0, st, P, tk, active);
-      km_arn_a<T, R, 0><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
+      // a zero x: u0 = b itself (read-only in every later pass)
+      const bool z = step == 0 && gb.x_zero;
+      const cx<T>* v0 = z ? b : u0;
+      GmresBufs gs = gb;
+      gs.u[0] = (void*)v0;
+      if (z) km_init_zero<T><<<grd, KW * 32, 0, s>>>(g, kg, b, st, P, tk, active);
+      else km_init<T, R><<<grd, KW * 32, 0, s>>>(g, kg, op, x, b, u0, st, P, tk, active);
+      km_arn_a<T, R, 0><<<grd, KW * 32, 0, s>>>(g, kg, op, v0, u1, u2, w, st, P, tk, active);
       bool done = false;
       if constexpr (KFUSE<T>) {
         if (fused) {   // arn_b<0> + arn_a<1>, arn_b<1> + arn_a<2>
-          km_arn_ab<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, w, u0, u0, u1, w2, st, P, tk, active);
-          km_arn_ab<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, w2, u0, u1, u2, w, st, P, tk, active);
-          launch_arn_b<T, 2>(g, gb, nullptr, B, active, s, 2);
+          km_arn_ab<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, w, v0, v0, u1, w2, st, P, tk, active);
+          km_arn_ab<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, w2, v0, u1, u2, w, st, P, tk, active);
+          launch_arn_b<T, 2>(g, gs, nullptr, B, active, s, 2);
           done = true;
         }
       }
       if (!done) {
-        launch_arn_b<T, 0>(g, gb, u1, B, active, s, -1);
-        km_arn_a<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
-        launch_arn_b<T, 1>(g, gb, u2, B, active, s, -1);
-        km_arn_a<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, u0, u1, u2, w, st, P, tk, active);
-        launch_arn_b<T, 2>(g, gb, nullptr, B, active, s, -1);
+        launch_arn_b<T, 0>(g, gs, u1, B, active, s, -1);
+        km_arn_a<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, v0, u1, u2, w, st, P, tk, active);
+        launch_arn_b<T, 1>(g, gs, u2, B, active, s, -1);
+        km_arn_a<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, v0, u1, u2, w, st, P, tk, active);
+        launch_arn_b<T, 2>(g, gs, nullptr, B, active, s, -1);
       }
-      launch_gmres_update<T>(g, x, gb, B, active, s);
+      launch_gmres_update<T>(g, x, gs, B, active, s);
     }
   };
   if (opv.kind == 4) run(kron_op<T, 2>(opv, g.nx, g.ny), std::integral_constant<int, 2>{});

@@ -66,6 +66,7 @@ __global__ void s_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, doubl
   c.beta2 = beta2;
   c.abc2 = abc == 2;
   c.ih3q = 1.0 / (4.0 * h * h * h);
+  c.tang = k > 0 ? 2.0 * c.ih3q / k : 0.0;
   for (int by = 0; by < 2; ++by)
     for (int bx = 0; bx < 2; ++bx) {
       const double wx = bx ? 0.5 : 1.0, wy = by ? 0.5 : 1.0, w = wx * wy;
@@ -88,6 +89,7 @@ __global__ void s_op0consts(Op0Consts<double>* c64, Op0Consts<float>* c32, doubl
     f.beta2 = (float)c.beta2;
     f.abc2 = c.abc2;
     f.ih3q = (float)c.ih3q;
+    f.tang = (float)c.tang;
     for (int q = 0; q < 4; ++q) f.dinv[q] = make_float2((float)c.dinv[q].x, (float)c.dinv[q].y);
     *c32 = f;
   }

@@ -129,3 +129,60 @@ def test_option_validation():
     with pytest.raises(hm.HelmmgError):
         s.gradient(u, u, torch.ones((33, 33), dtype=torch.float64, device="cuda"), 10.0)
     s.close()
+
+
+@pytest.mark.parametrize("cycle,coarse", [("W", {}), ("V", dict(coarse_nodes=10**6, coarse_mode=1)),
+                                          ("V", dict(coarse_nodes=0))])
+def test_w_cycles_and_coarse_launch_organisations(cycle, coarse):
+    """W-cycles, the cooperative coarse-cycle launch over the whole hierarchy
+    and no coarse-cycle launch at all: FP64 iterates of cycles 1-2 to 1e-10
+    and the cycle count of the whole solve equal the oracle's."""
+    n, k = 48, 20.0
+    h = 1.0 / n
+    opt = ocycle.CycleOptions(2 if cycle == "W" else 1, "gmres3", 2, 2, 4.5)
+    H = ohier.build_hierarchy(n, n, h, k, 1 / k, abc=2)
+    b = synth.point_source(n, n, h) + 1e-2 * synth.random_complex((n + 1, n + 1), 21) / h**2
+    ref = ocycle.mg_solve(H, b.ravel(), 1e-8, opt, keep_iterates=True)
+    kw = dict(cycle=cycle, smoother="gmres3", nu_pre=2, nu_post=2, abc=2, **coarse)
+    s1 = hm.Solver(n, n, h, k, 1 / k, max_cycles=1, **kw)
+    x0 = np.zeros_like(b)
+    for m in (1, 2):
+        x, st, cyc, _ = s1.solve(dev(b)[None], x=dev(x0)[None], tol=1e-300)
+        pu.assert_close(x[0].cpu().numpy(), ref.iterates[m - 1].reshape(n + 1, n + 1), 1e-10, (n + 1, n + 1),
+                        f"cycle {m}")
+        x0 = ref.iterates[m - 1].reshape(n + 1, n + 1)
+    s1.close()
+    s = hm.Solver(n, n, h, k, 1 / k, **kw)
+    x, st, cyc, rr = s.solve(dev(b)[None], tol=1e-8)
+    assert st == hm.MG_OK and cyc[0] == ref.cycles
+    s.close()
+
+
+def test_ragged_batch_with_second_order_rows():
+    """A ragged batch with abc=2 (grouped handles; the flattened launches are
+    not used with these rows): every problem's one-cycle FP64 iterate equals
+    its oracle's to 1e-10 and its whole solve takes the oracle's cycles."""
+    sizes = [(48, 48, 30.0), (32, 64, 30.0), (48, 48, 30.0)]
+    probs, rhs = [], []
+    for q, (nx, ny, k) in enumerate(sizes):
+        h = 1.0 / max(nx, ny)
+        probs.append((nx, ny, h, k))
+        b = synth.point_source(nx, ny, h, i=nx // 2 - q, j=ny // 3 + q)
+        rhs.append(torch.from_numpy(b).cuda())
+    beta2 = [1.0 / k for _, _, k in sizes]
+    opt = ocycle.CycleOptions(1, "gmres3", 2, 2, 4.5)
+    refs = []
+    for p, (nx, ny, h, k) in enumerate(probs):
+        H = ohier.build_hierarchy(nx, ny, h, k, beta2[p], abc=2)
+        refs.append(ocycle.mg_solve(H, rhs[p].cpu().numpy().ravel(), 1e-8, opt, keep_iterates=True))
+    for flat in (0, 1):
+        rs1 = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, abc=2, flat=flat, max_cycles=1)
+        xs, st, cyc, rr = rs1.solve(rhs, tol=1e-300)
+        for p, (nx, ny, h, k) in enumerate(probs):
+            pu.assert_close(xs[p].cpu().numpy(), refs[p].iterates[0].reshape(ny + 1, nx + 1), 1e-10, (ny + 1, nx + 1),
+                            f"flat {flat}, problem {p}")
+        rs1.close()
+        rs = hm.RaggedSolver(probs, beta2, smoother="gmres3", nu_pre=2, nu_post=2, abc=2, flat=flat)
+        xs, st, cyc, rr = rs.solve(rhs, tol=1e-8)
+        assert st == hm.MG_OK and cyc == [r.cycles for r in refs], flat
+        rs.close()
