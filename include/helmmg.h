@@ -92,7 +92,8 @@ typedef struct {
                        from each level's size, 1..4 = forced (autotuner knob) */
   int march;        /* GMRES(3) on the fine level as row marches and on
                        Kronecker-form levels with column-march operator
-                       kernels (needs fuse = 1): 1 = always, 0 = never (the
+                       kernels, which then also form the residual before the
+                       restriction (needs fuse = 1): 1 = always, 0 = never (the
                        node-parallel kernels; same results to rounding),
                        -1 = the Kronecker-form levels always, the fine level
                        when it holds at least 4 M nodes over all right-hand

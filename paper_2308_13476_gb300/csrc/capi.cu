@@ -358,7 +358,12 @@ template <class T> struct Emit {
     const Grid& g = c->lev[l].g;
     const Grid& gc = c->lev[l + 1].g;
     smooth(l, c->opt.nu_pre);
-    if (c->opt.fuse) {
+    if (c->opt.fuse && c->lev[l].kind >= 4 && use_march(c, l)) {
+      // a Kronecker-form level: the residual as a column march (about a
+      // twelfth of OpK::apply's arithmetic), then the restriction
+      launch_kron_residual<T>(g, opT<T>(c, l), cur[l], V[l].b, V[l].r, c->B, c->active, c->opt.kron_chunk, s);
+      launch_restrict<T>(g, gc, V[l].r, V[l + 1].b, c->B, c->active, c->xw, s);
+    } else if (c->opt.fuse) {
       launch_resid_restrict<T>(g, gc, opT<T>(c, l), cur[l], V[l].b, V[l + 1].b, c->B, c->active, c->xw, s);
     } else {
       launch_residual<T>(g, opT<T>(c, l), cur[l], V[l].b, V[l].r, c->B, c->active, s);

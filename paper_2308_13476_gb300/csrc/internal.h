@@ -194,6 +194,10 @@ template <class T> void gmres_smooth_march(const Grid& g, const OpView<T>& op, c
 long long kron_march_blocks(const Grid& g, int B);
 template <class T> void gmres_smooth_kron(const Grid& g, const OpView<T>& op, cx<T>* x, const cx<T>* b, int nu, int B,
                                           const int* active, const GmresBufs& gb, cudaStream_t s);
+// r = b - A x on a Kronecker-form level as a column march (the residual that
+// the restriction then reads; kron_ch as in GmresBufs).
+template <class T> void launch_kron_residual(const Grid& g, const OpView<T>& op, const cx<T>* x, const cx<T>* b,
+                                             cx<T>* r, int B, const int* active, int kron_ch, cudaStream_t s);
 
 // Single-CTA coarse-cycle interpreter (coarse.cu).  One CTA per RHS walks a
 // host-recorded list of steps over the levels lc..L-1.

@@ -281,7 +281,9 @@ template <class T, int R> struct KRing {
   ring.prime(last);
 
 // u0 = b - A x, partial |u0|^2 (as g_init)
-template <class T, int R>
+// NRM = false: only u0 = b - A x (the residual before the restriction; no
+// norm, no state)
+template <class T, int R, bool NRM = true>
 __device__ __forceinline__ void km_init_body(uint3 vblk, dim3 vgrid, Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st, double* partial, unsigned* tickets, const int* __restrict__ active) {
   const uint3 blockIdx = vblk;   // the block and grid inside this problem's launch
   const dim3 gridDim = vgrid;
@@ -316,9 +318,11 @@ __device__ __forceinline__ void km_init_body(uint3 vblk, dim3 vgrid, Grid g, KGe
     });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
-  double v[1];
-  if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && threadIdx.x == 0)
-    fin_init<T>(gstate<T>(st, rhs), v);
+  if constexpr (NRM) {
+    double v[1];
+    if (reduce_last<1, T>(a0, v, sh, partial, tickets, rhs, nblk, blk) && threadIdx.x == 0)
+      fin_init<T>(gstate<T>(st, rhs), v);
+  }
 }
 
 // km_init on a zero x: u0 = b (the caller passes b as u0 to the later
@@ -348,9 +352,9 @@ __global__ void __launch_bounds__(KW * 32) km_init_zero(Grid g, KGeo kg, const c
     fin_init<T>(gstate<T>(st, rhs), v);
 }
 
-template <class T, int R>
+template <class T, int R, bool NRM = true>
 __global__ void __launch_bounds__(KW * 32) km_init(Grid g, KGeo kg, OpK<T, R> op, const cx<T>* __restrict__ x, const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st, double* partial, unsigned* tickets, const int* __restrict__ active) {
-  km_init_body<T, R>(blockIdx, gridDim, g, kg, op, x, b, u0, st, partial, tickets, active);
+  km_init_body<T, R, NRM>(blockIdx, gridDim, g, kg, op, x, b, u0, st, partial, tickets, active);
 }
 
 template <class T, int R>
@@ -745,6 +749,19 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
   else run(kron_op<T, 3>(opv, g.nx, g.ny), std::integral_constant<int, 3>{});
 }
 
+template <class T>
+void launch_kron_residual(const Grid& g, const OpView<T>& opv, const cx<T>* x, const cx<T>* b, cx<T>* r, int B,
+                          const int* active, int kron_ch, cudaStream_t s) {
+  auto run = [&](auto op, auto rad) {
+    constexpr int R = decltype(rad)::value;
+    const KGeo kg = kron_geo(g, B, R, kron_capacity<T, R>(KFUSE<T>), kron_ch);
+    const dim3 grd(cdiv((long long)kg.ncw * kg.nchunks, KW), 1, B);
+    km_init<T, R, false><<<grd, KW * 32, 0, s>>>(g, kg, op, x, b, r, nullptr, nullptr, nullptr, active);
+  };
+  if (opv.kind == 4) run(kron_op<T, 2>(opv, g.nx, g.ny), std::integral_constant<int, 2>{});
+  else run(kron_op<T, 3>(opv, g.nx, g.ny), std::integral_constant<int, 3>{});
+}
+
 // The same smoothing steps on every problem of a ragged batch (the problems'
 // levels at the same depth share the radius): each kernel of a step is one
 // flattened launch over the problems' own chunk geometries.
@@ -809,6 +826,10 @@ void gmres_smooth_kron_rag(const std::vector<RagLevel<T>>& v, int nu, cudaStream
 
 template void gmres_smooth_kron_rag<double>(const std::vector<RagLevel<double>>&, int, cudaStream_t);
 template void gmres_smooth_kron_rag<float>(const std::vector<RagLevel<float>>&, int, cudaStream_t);
+template void launch_kron_residual<double>(const Grid&, const OpView<double>&, const double2*, const double2*,
+                                           double2*, int, const int*, int, cudaStream_t);
+template void launch_kron_residual<float>(const Grid&, const OpView<float>&, const float2*, const float2*, float2*,
+                                          int, const int*, int, cudaStream_t);
 template void gmres_smooth_kron<double>(const Grid&, const OpView<double>&, double2*, const double2*, int, int,
                                         const int*, const GmresBufs&, cudaStream_t);
 template void gmres_smooth_kron<float>(const Grid&, const OpView<float>&, float2*, const float2*, int, int,
