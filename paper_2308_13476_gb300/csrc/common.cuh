@@ -44,6 +44,22 @@ template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
 }
 template <class T> __device__ __forceinline__ T abs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
 
+// Packed complex64 arithmetic: one .f32x2 instruction of the FP32 pipe for
+// both components, each rounded as by the scalar instruction (so add2, sub2,
+// mul2 and fma2 give the bits of the scalar add, sub, mul and fma).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 pa, pb, pd;\n mov.b64 pa, {%2, %3};\n mov.b64 pb, {%4, %5};\n"
+      " sub.rn.f32x2 pd, pa, pb;\n mov.b64 {%0, %1}, pd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+
 // IEEE 754 conversions between binary64 and binary32 in integer arithmetic.
 // The hardware conversions execute on the FP64 pipe, which is narrow on this
 // GPU and is what bounds the FP64 refinement passes; these take the integer

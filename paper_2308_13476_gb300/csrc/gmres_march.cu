@@ -120,6 +120,35 @@ template <class T> __device__ __forceinline__ cx<T> shfl_dn1(cx<T> a) {
   return mk<T>(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
 }
 
+// a - b; complex64 in one packed instruction
+template <class T> __device__ __forceinline__ cx<T> psub(cx<T> a, cx<T> b) {
+  if constexpr (sizeof(T) == 4) return sub2(a, b);
+  else return sub<T>(a, b);
+}
+
+// s a - sum_l c_l v_l (the Arnoldi vector of a pass).  complex64: the real
+// parts of the coefficients scale v_l in one packed accumulator and the
+// imaginary parts in another, which are joined once (packed instructions
+// need no component swap that way); complex128 in the scalar order.
+template <class T, int L>
+__device__ __forceinline__ cx<T> scl_minus(T s, cx<T> a, const cx<T> (&c)[L], const cx<T> (&v)[L]) {
+  if constexpr (sizeof(T) == 4) {
+    float2 p = mul2(bc2(s), a), q = mul2(bc2(c[0].y), v[0]);
+    p = fma2(bc2(-c[0].x), v[0], p);
+#pragma unroll
+    for (int l = 1; l < L; ++l) {
+      p = fma2(bc2(-c[l].x), v[l], p);
+      q = fma2(bc2(c[l].y), v[l], q);
+    }
+    return make_float2(p.x + q.y, p.y - q.x);
+  } else {
+    cx<T> u = sub<T>(scl<T>(s, a), mul<T>(c[0], v[0]));
+#pragma unroll
+    for (int l = 1; l < L; ++l) u = sub<T>(u, mul<T>(c[l], v[l]));
+    return u;
+  }
+}
+
 // March modes: MD = 1 interior strips (branch-free stencil), MD = 2 edge
 // strips over interior rows (the same stencil, with the boundary row of
 // Op0::apply5 on columns 0 and nx and zero off the grid), MD = 0 everything
@@ -148,9 +177,14 @@ template <class T, int MD> struct MCtx {
         const cx<T> xn = up.v[n], xs = dn.v[n], xp = c.v[n];
         const int ik = MD == 2 ? min(max(in, 0), op.nx) : in;   // edge strips: k of an in-grid node
         const T k = op.kf ? op.kf[m * (op.nx + 1) + ik] : op.c.k;
-        const T sr = (xe.x + xw.x) + (xn.x + xs.x), si = (xe.y + xw.y) + (xn.y + xs.y);
         const T d = fma(-k, k, T(4) * op.c.inv_h2);
-        r.v[n] = mk<T>(fma(d, xp.x, -op.c.inv_h2 * sr), fma(d, xp.y, -op.c.inv_h2 * si));
+        if constexpr (sizeof(T) == 4) {   // the same operations, both components per instruction
+          const float2 sn = add2(add2(xe, xw), add2(xn, xs));
+          r.v[n] = fma2(bc2(d), xp, mul2(bc2(-op.c.inv_h2), sn));
+        } else {
+          const T sr = (xe.x + xw.x) + (xn.x + xs.x), si = (xe.y + xw.y) + (xn.y + xs.y);
+          r.v[n] = mk<T>(fma(d, xp.x, -op.c.inv_h2 * sr), fma(d, xp.y, -op.c.inv_h2 * si));
+        }
         if (MD == 2) {   // rows are interior here; columns 0 and nx take the
                          // boundary row of Op0::apply5, columns off the grid zero
           const bool bcol = in == 0 || in == op.nx, inside = in >= 0 && in <= op.nx;
@@ -245,7 +279,7 @@ template <class T, int MD> struct P0 {
     const Row<T> ax = c.apply(m.F[0][Sl<S, -2>::v], m.F[0][Sl<S, -1>::v], m.F[0][Sl<S, 0>::v], t - 1);
     Row<T> u;
 #pragma unroll
-    for (int n = 0; n < NP; ++n) u.v[n] = sub<T>(m.F[1][Sl<S, -1>::v].v[n], ax.v[n]);   // both zero outside the grid
+    for (int n = 0; n < NP; ++n) u.v[n] = psub<T>(m.F[1][Sl<S, -1>::v].v[n], ax.v[n]);   // both zero outside the grid
     U[Sl<S, -1>::v] = u;
     if (c.own_row(t - 1)) mstore(us, c.g, c.i, t - 1, u);
 #pragma unroll
@@ -308,7 +342,11 @@ template <class T, int MD> struct P1 {
     const Row<T> av = c.apply(V[Sl<S, -2>::v], V[Sl<S, -1>::v], V[Sl<S, 0>::v], t - 1);
     Row<T> u;
 #pragma unroll
-    for (int n = 0; n < NP; ++n) u.v[n] = sub<T>(scl<T>(s0, av.v[n]), mul<T>(c0, V[Sl<S, -1>::v].v[n]));
+    for (int n = 0; n < NP; ++n) {
+      const cx<T> c[1] = {c0};
+      const cx<T> v[1] = {V[Sl<S, -1>::v].v[n]};
+      u.v[n] = scl_minus<T, 1>(s0, av.v[n], c, v);
+    }
     U[Sl<S, -1>::v] = u;
     if (c.own_row(t - 1)) mstore(ws, c.g, c.i, t - 1, u);
 #pragma unroll
@@ -354,8 +392,9 @@ template <class T, int MD> struct P2 {
     Row<T> u;
 #pragma unroll
     for (int n = 0; n < NP; ++n) {
-      u.v[n] = sub<T>(scl<T>(s1, av.v[n]), mul<T>(c0, Z[Sl<S, -1>::v].v[n]));
-      u.v[n] = sub<T>(u.v[n], mul<T>(c1, V[Sl<S, -1>::v].v[n]));
+      const cx<T> c[2] = {c0, c1};
+      const cx<T> v[2] = {Z[Sl<S, -1>::v].v[n], V[Sl<S, -1>::v].v[n]};
+      u.v[n] = scl_minus<T, 2>(s1, av.v[n], c, v);
     }
     U[Sl<S, -1>::v] = u;
     if (c.own_row(t - 1)) mstore(ws, c.g, c.i, t - 1, u);
@@ -403,9 +442,8 @@ template <class T, int MD> struct P3 {
 #pragma unroll
     for (int n = 0; n < NP; ++n)
       if (c.cnt(n, t - 1)) {
-        cx<T> u = sub<T>(scl<T>(s2, av.v[n]), mul<T>(cl[0], m.F[1][Sl<S, -1>::v].v[n]));
-        u = sub<T>(u, mul<T>(cl[1], m.F[2][Sl<S, -1>::v].v[n]));
-        u = sub<T>(u, mul<T>(cl[2], V[Sl<S, -1>::v].v[n]));
+        const cx<T> v[3] = {m.F[1][Sl<S, -1>::v].v[n], m.F[2][Sl<S, -1>::v].v[n], V[Sl<S, -1>::v].v[n]};
+        const cx<T> u = scl_minus<T, 3>(s2, av.v[n], cl, v);
         acc[0] += abs2<T>(u);
       }
   }
