@@ -60,6 +60,35 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
 
+// a - b; complex64 in one packed instruction
+template <class T> __device__ __forceinline__ cx<T> psub(cx<T> a, cx<T> b) {
+  if constexpr (sizeof(T) == 4) return sub2(a, b);
+  else return sub<T>(a, b);
+}
+
+// s a - sum_l c_l v_l (the Arnoldi vector of a pass).  complex64: the real
+// parts of the coefficients scale v_l in one packed accumulator and the
+// imaginary parts in another, which are joined once (packed instructions
+// need no component swap that way); complex128 in the scalar order.
+template <class T, int L>
+__device__ __forceinline__ cx<T> scl_minus(T s, cx<T> a, const cx<T> (&c)[L], const cx<T> (&v)[L]) {
+  if constexpr (sizeof(T) == 4) {
+    float2 p = mul2(bc2(s), a), q = mul2(bc2(c[0].y), v[0]);
+    p = fma2(bc2(-c[0].x), v[0], p);
+#pragma unroll
+    for (int l = 1; l < L; ++l) {
+      p = fma2(bc2(-c[l].x), v[l], p);
+      q = fma2(bc2(c[l].y), v[l], q);
+    }
+    return make_float2(p.x + q.y, p.y - q.x);
+  } else {
+    cx<T> u = sub<T>(scl<T>(s, a), mul<T>(c[0], v[0]));
+#pragma unroll
+    for (int l = 1; l < L; ++l) u = sub<T>(u, mul<T>(c[l], v[l]));
+    return u;
+  }
+}
+
 // IEEE 754 conversions between binary64 and binary32 in integer arithmetic.
 // The hardware conversions execute on the FP64 pipe, which is narrow on this
 // GPU and is what bounds the FP64 refinement passes; these take the integer
@@ -290,6 +319,14 @@ template <class T, int R> struct OpS {
 // W1 (x) (L1/h^2 - (1 + i beta2) k^2 W1 - i k/h B1) + (L1/h^2 - i k/h B1) (x) W1
 // in terms of the 1D Neumann Laplacian L1, boundary weights W1 and boundary
 // indicator B1).  Rows are [n+1][2R+1], entry R + d the coupling to node + d.
+// Broadcast copies (value, value) of the translation-invariant y-factor row,
+// for the packed complex64 column marches: a .f32x2 multiply-add takes such
+// a pair straight from the parameter bank.  complex128 keeps none.
+template <class T, int K> struct KBank {};
+template <int K> struct KBank<float, K> {
+  float2 hyr[K], hyi[K], wyb[K];   // Re h, Im h, w
+};
+
 template <class T, int R> struct OpK {
   const cx<T>* gx;
   const T* wx;
@@ -304,6 +341,7 @@ template <class T, int R> struct OpK {
   int ty0, ty1;
   cx<T> hyc[2 * R + 1];
   T wyc[2 * R + 1];
+  KBank<T, 2 * R + 1> pk;   // broadcast copies of hyc / wyc
   static constexpr int radius = R;
   __device__ __forceinline__ cx<T> apply(const cx<T>* __restrict__ x, int p, int pitch, int i, int j) const {
     const cx<T>* G = gx + i * (2 * R + 1);

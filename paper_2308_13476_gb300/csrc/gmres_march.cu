@@ -120,35 +120,6 @@ template <class T> __device__ __forceinline__ cx<T> shfl_dn1(cx<T> a) {
   return mk<T>(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1));
 }
 
-// a - b; complex64 in one packed instruction
-template <class T> __device__ __forceinline__ cx<T> psub(cx<T> a, cx<T> b) {
-  if constexpr (sizeof(T) == 4) return sub2(a, b);
-  else return sub<T>(a, b);
-}
-
-// s a - sum_l c_l v_l (the Arnoldi vector of a pass).  complex64: the real
-// parts of the coefficients scale v_l in one packed accumulator and the
-// imaginary parts in another, which are joined once (packed instructions
-// need no component swap that way); complex128 in the scalar order.
-template <class T, int L>
-__device__ __forceinline__ cx<T> scl_minus(T s, cx<T> a, const cx<T> (&c)[L], const cx<T> (&v)[L]) {
-  if constexpr (sizeof(T) == 4) {
-    float2 p = mul2(bc2(s), a), q = mul2(bc2(c[0].y), v[0]);
-    p = fma2(bc2(-c[0].x), v[0], p);
-#pragma unroll
-    for (int l = 1; l < L; ++l) {
-      p = fma2(bc2(-c[l].x), v[l], p);
-      q = fma2(bc2(c[l].y), v[l], q);
-    }
-    return make_float2(p.x + q.y, p.y - q.x);
-  } else {
-    cx<T> u = sub<T>(scl<T>(s, a), mul<T>(c[0], v[0]));
-#pragma unroll
-    for (int l = 1; l < L; ++l) u = sub<T>(u, mul<T>(c[l], v[l]));
-    return u;
-  }
-}
-
 // March modes: MD = 1 interior strips (branch-free stencil), MD = 2 edge
 // strips over interior rows (the same stencil, with the boundary row of
 // Op0::apply5 on columns 0 and nx and zero off the grid), MD = 0 everything

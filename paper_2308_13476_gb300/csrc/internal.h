@@ -39,6 +39,11 @@ template <class T, int R> inline OpK<T, R> kron_op(const OpView<T>& v, int nx, i
   for (int k = 0; k < 2 * R + 1; ++k) {
     o.hyc[k] = v.hyc[k];
     o.wyc[k] = v.wyc[k];
+    if constexpr (sizeof(T) == 4) {
+      o.pk.hyr[k] = make_float2(v.hyc[k].x, v.hyc[k].x);
+      o.pk.hyi[k] = make_float2(v.hyc[k].y, v.hyc[k].y);
+      o.pk.wyb[k] = make_float2(v.wyc[k], v.wyc[k]);
+    }
   }
   return o;
 }

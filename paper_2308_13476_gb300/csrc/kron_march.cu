@@ -155,6 +155,17 @@ template <class T, int R, int K, int KUR, int P>
 __device__ __forceinline__ cx<T> kcombine(const OpK<T, R>& op, int m, const cx<T> (&s1)[K], const cx<T> (&s2)[K]) {
   cx<T> acc = mk<T>(T(0), T(0));
   if (m >= op.ty0 && m < op.ty1) {
+    if constexpr (sizeof(T) == 4 && R == 2) {   // packed: Re h and w_y with s, Im h apart, joined once
+      float2 pr = make_float2(0.f, 0.f), pi = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int dy = -R; dy <= R; ++dy) {
+        const int q = KUR == 1 ? dy + R : (P + 1 + R + dy) % K;
+        pr = fma2(op.pk.wyb[dy + R], s1[q], pr);
+        pr = fma2(op.pk.hyr[dy + R], s2[q], pr);
+        pi = fma2(op.pk.hyi[dy + R], s2[q], pi);
+      }
+      return make_float2(pr.x - pi.y, pr.y + pi.x);
+    }
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy) {
       const int q = KUR == 1 ? dy + R : (P + 1 + R + dy) % K;
@@ -482,12 +493,25 @@ template <class T, int R, int NS> struct KRingF {
       if (lane < WD / 2) {
         const int e = 2 * lane;
         const float4 wv = *reinterpret_cast<const float4*>(sm + sl * WD + e);
-        cx<T> a = scl<T>(cw, mk<T>(wv.x, wv.y)), b = scl<T>(cw, mk<T>(wv.z, wv.w));
+        cx<T> ua[NS - 1], ub[NS - 1];
 #pragma unroll
         for (int l = 0; l < NS - 1; ++l) {
           const float4 q = *reinterpret_cast<const float4*>(sm + ((1 + l) * KSL + sl) * WD + e);
-          a = sub<T>(a, mul<T>(c[l], mk<T>(q.x, q.y)));
-          b = sub<T>(b, mul<T>(c[l], mk<T>(q.z, q.w)));
+          ua[l] = mk<T>(q.x, q.y);
+          ub[l] = mk<T>(q.z, q.w);
+        }
+        cx<T> a, b;
+        if constexpr (R == 2) {   // packed (the radius-3 passes keep their register budget)
+          a = scl_minus<T, NS - 1>(cw, mk<T>(wv.x, wv.y), c, ua);
+          b = scl_minus<T, NS - 1>(cw, mk<T>(wv.z, wv.w), c, ub);
+        } else {
+          a = scl<T>(cw, mk<T>(wv.x, wv.y));
+          b = scl<T>(cw, mk<T>(wv.z, wv.w));
+#pragma unroll
+          for (int l = 0; l < NS - 1; ++l) {
+            a = sub<T>(a, mul<T>(c[l], ua[l]));
+            b = sub<T>(b, mul<T>(c[l], ub[l]));
+          }
         }
         *reinterpret_cast<float4*>(fm + sl * WD + e) = make_float4(a.x, a.y, b.x, b.y);
       }
