@@ -497,7 +497,10 @@ def run_ours(a):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": step_traffic(a, what),
             "kernel": ({0: "level-0 weighted-Jacobi sweep",
-                        4: "level-0 GMRES(3) smoothing step: 4 row-march passes + update, 16 vector passes",
+                        4: ("level-0 GMRES(3) smoothing step: 4 row-march passes + update, 16 vector passes"
+                            if a.precision == "fp64" else
+                            "level-0 GMRES(3) smoothing step: 3 row-march passes + update, 13 vector passes "
+                            "(the last Arnoldi vector's norm from the Gram form)"),
                         5: f"last FGMRES({a.krylov}) Arnoldi step (MGS-coefficient pass + new-vector pass, "
                            f"{2 * a.krylov + 1} FP64 and 3 cycle-precision vector passes)"}[what]) +
                       f" ({'complex128' if a.precision == 'fp64' else 'complex64'}), "

@@ -609,9 +609,12 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
     double gop = 0;   // operator bytes per node and RHS read by one pass
     if (level == 0) gop = op.kf ? sizeof(T) / (double)h->B : 0.0;
     else if (h->lev[level].kind <= 3) gop = opbytes - e / h->B;   // stencil without the inverse diagonal
-    // fine-level row marches + update 16; Kronecker column marches, complex64 (two fused passes) 23; else 28
+    // fine-level row marches + update 16, complex64 13 (no M3: u3's norm from the Gram form); Kronecker column
+    // marches, complex64 (two fused passes, no closing g_arn_b<2>) 19; else 28
     const bool mr = use_march(h, level);
-    const int vec = (mr && h->lev[level].kind == 1) ? 16 : (mr && h->lev[level].kind >= 4 && sizeof(T) == 4) ? 23 : 28;
+    const bool c64 = sizeof(T) == 4;
+    const int vec = (mr && h->lev[level].kind == 1) ? (c64 ? 13 : 16)
+                                                     : (mr && h->lev[level].kind >= 4 && c64) ? 19 : 28;
     *bytes = nodes * (vec * e + 4 * gop);
   }
   launch();

@@ -138,6 +138,20 @@ template <int J, class Ts, class St = double, class V = double> __device__ __for
   if (J == 2 || S[G_BRK] != St(0)) lsq<Ts, St>(S);
 }
 
+// fin_b<2> with |u3|^2 from the Gram form: u3 = A v2 - sum_{l<=2} h_l2 v_l
+// with unit v_l, and each modified Gram-Schmidt step removes |h_l2|^2 from
+// the squared norm, so |u3|^2 = |A v2|^2 - sum_l |h_l2|^2 (aw2 = |A v2|^2).
+// Computed in FP64; a cancellation to zero or below is a breakdown.
+template <class Ts, class St = double> __device__ __forceinline__ void fin_b2_gram(St* S, double aw2) {
+  double r = aw2;
+  for (int l = 0; l <= 2; ++l) {
+    const double hr = (double)S[G_H + 2 * (l * 3 + 2)], hi = (double)S[G_H + 2 * (l * 3 + 2) + 1];
+    r -= hr * hr + hi * hi;
+  }
+  const double v[1] = {r > 0.0 ? r : 0.0};
+  fin_b<2, Ts, St>(S, v);
+}
+
 // The per-RHS state in global memory: GS values of the cycle's working
 // precision T per right-hand side (the scalar steps compute in T and store T
 // values, so FP32 storage gives what FP64 storage would; kernels of a

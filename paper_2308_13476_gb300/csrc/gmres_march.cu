@@ -15,7 +15,8 @@
 //   M2: u2 = s1 A u1 - sum c_l1 u_l       |u2|^2, <u2, u_l>, <u_l, A u2>
 //   M3: u3 = s2 A u2 - sum c_l2 u_l       |u3|^2 (not stored)
 //   then x += sum y_l s_l u_l (g_update).
-// That is 16 vector passes per step.  The scalar steps between passes are the
+// That is 16 vector passes per step.  complex64 steps skip M3: M2 also sums
+// |A u2|^2, and |u3|^2 follows from the Gram form (13 vector passes).  The scalar steps between passes are the
 // same FP64 Gram-matrix updates and Givens solve (gmres.cuh) in the same order
 // as the node-parallel version; only the dots of A u_{j+1} are taken before
 // the scale s_{j+1} is known, and scaled afterwards.
@@ -235,6 +236,15 @@ template <class P> __device__ __forceinline__ void march(P& p, int t0, int t1) {
   }
 }
 
+// complex64 steps take the norm of the last Arnoldi vector u3 = A v2 -
+// sum_l h_l2 v_l from the Gram form instead of a fourth pass: with unit
+// v_l the modified Gram-Schmidt steps give |u3|^2 = |A v2|^2 - sum_l
+// |h_l2|^2 exactly, so M2 also sums |A u2|^2 (s_2 A u2 = A v2) and M3 is
+// not run.  complex128 steps keep M3 (their iterates follow the oracle's
+// explicit norm to rounding).
+template <class T> constexpr bool G3 = sizeof(T) == 4;
+template <class T> constexpr int NV2 = G3<T> ? 12 : 11;
+
 // M0 at iteration t: x and b rows t arrive; u0 row t-1 = b - A x formed from
 // x rows t-2..t; A u0 on row t-2.
 template <class T, int MD> struct P0 {
@@ -352,7 +362,7 @@ template <class T, int MD> struct P2 {
   T s1;
   cx<T> c0, c1;
   Row<T> U[4];
-  T acc[11];
+  T acc[NV2<T>];
   template <int S> __device__ __forceinline__ void step(int t) {
     m.template fetch<S>(t);
     const MCtx<T, MD>& c = m.c;
@@ -392,6 +402,7 @@ template <class T, int MD> struct P2 {
           acc[8] += d1.y;
           acc[9] += d2.x;
           acc[10] += d2.y;
+          if constexpr (G3<T>) acc[11] += abs2<T>(au.v[n]);   // |A u2|^2: u3's norm without M3
         }
     }
   }
@@ -649,7 +660,7 @@ __device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T
   const T s1 = (T)S[G_S + 1];
   const cx<T> c0 = mk<T>((T)(S[G_H + 2 * 1] * S[G_S]), (T)(S[G_H + 2 * 1 + 1] * S[G_S]));
   const cx<T> c1 = mk<T>((T)(S[G_H + 2 * 4] * S[G_S + 1]), (T)(S[G_H + 2 * 4 + 1] * S[G_S + 1]));
-  T acc[11];
+  T acc[NV2<T>];
   __shared__ __align__(16) unsigned char stg[ring_bytes<2>()];
   double* sh = reinterpret_cast<double*>(stg);
   run_pass<P2>(ctx, j1 + 1, stg, acc, [&](auto& p) {
@@ -666,6 +677,7 @@ __device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T
       const double s2 = s[G_S + 2];
       const double d[6] = {q[5] * s2, q[6] * s2, q[7] * s2, q[8] * s2, q[9] * s2, q[10] * s2};
       fin_a<2, T>(s, d);
+      if constexpr (G3<T>) fin_b2_gram<T>(s, q[11] * s2 * s2);
     }
   });
 }
@@ -827,9 +839,11 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
     pass([&] { gm_step2<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
          [&] { gm_step2<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
          [&] { gm_step2<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); });
-    pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
-         [&] { gm_step3<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
-         [&] { gm_step3<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); });
+    if constexpr (!G3<T>) {   // complex64: u3's norm came from the Gram form in M2
+      pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+           [&] { gm_step3<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+           [&] { gm_step3<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); });
+    }
     if constexpr (sizeof(T) == 4) {
       if (step == nu - 1 && gb.outer) {
         launch_gmres_update_outer(g, x, gs, B, active, s);
@@ -882,7 +896,7 @@ void gmres_smooth_march_rag(const std::vector<RagLevel<T>>& v, int nu, cudaStrea
     pass(gm_init_rag<T, 1>, gm_init_rag<T, 2>, gm_init_rag<T, 0>);
     pass(gm_step1_rag<T, 1>, gm_step1_rag<T, 2>, gm_step1_rag<T, 0>);
     pass(gm_step2_rag<T, 1>, gm_step2_rag<T, 2>, gm_step2_rag<T, 0>);
-    pass(gm_step3_rag<T, 1>, gm_step3_rag<T, 2>, gm_step3_rag<T, 0>);
+    if constexpr (!G3<T>) pass(gm_step3_rag<T, 1>, gm_step3_rag<T, 2>, gm_step3_rag<T, 0>);
     launch_gmres_update_rag<T>(v, s);
   }
 }

@@ -563,6 +563,9 @@ __device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, K
   constexpr int NS = J + 1;             // staged: w, u_0 .. u_{J-1}
   constexpr int NB = 1 + 2 * J;         // fin_b<J-1>: |u_J|^2, <u_J, u_l> (l < J)
   constexpr int NA = 2 * (J + 1);       // fin_a<J>: <u_l, w'> (l <= J)
+  // complex64, J = 2: |w'|^2 too, and u3's norm from the Gram form
+  // (fin_b2_gram) instead of the closing g_arn_b<2> pass
+  constexpr int NG = (sizeof(T) == 4 && J == 2) ? 1 : 0;
   __shared__ double sh[NVMAX * 32];
   __shared__ __align__(16) cx<T> ksm[KW][NS][KSL][KRingF<T, R, NS>::WD];
   __shared__ __align__(16) cx<T> kfm[KW][KSL][KRingF<T, R, NS>::WD];
@@ -578,9 +581,9 @@ __device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, K
   const int nblk = gridDim.x, blk = blockIdx.x;
   T* S = gstate<T>(st, rhs);
   if (S[G_BRK] != 0 || S[G_M] < J - 1) return;   // the guard of g_arn_b<J-1>; uniform per RHS
-  T acc[NB + NA];
+  T acc[NB + NA + NG];
 #pragma unroll
-  for (int k = 0; k < NB + NA; ++k) acc[k] = T(0);
+  for (int k = 0; k < NB + NA + NG; ++k) acc[k] = T(0);
   if (has) {
     // u_J = c_w w - sum_l c_l u_l: w from km_arn_a<0> carries s_0 (c_w = 1);
     // w2 from km_arn_ab<1> is unscaled (c_w = s_1)
@@ -629,12 +632,13 @@ __device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, K
           acc[NB + 2 * l] += d.x;
           acc[NB + 2 * l + 1] += d.y;
         }
+        if constexpr (NG == 1) acc[NB + NA] += abs2<T>(a);
       }
     });
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
-  double v[NB + NA];
-  if (reduce_last<NB + NA, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
+  double v[NB + NA + NG];
+  if (reduce_last<NB + NA + NG, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
     staged<T>(S, v, [](auto* s, const double* q) {
       fin_b<J - 1, T>(s, q);
       if (s[G_BRK] == 0) {
@@ -643,6 +647,7 @@ __device__ __forceinline__ void km_arn_ab_body(uint3 vblk, dim3 vgrid, Grid g, K
 #pragma unroll
         for (int k = 0; k < NA; ++k) d[k] = sJ * q[NB + k];
         fin_a<J, T>(s, d);
+        if constexpr (NG == 1) fin_b2_gram<T>(s, q[NB + NA] * sJ * sJ);
       }
     });
 }
@@ -755,8 +760,7 @@ void gmres_smooth_kron(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T
         if (fused) {   // arn_b<0> + arn_a<1>, arn_b<1> + arn_a<2>
           km_arn_ab<T, R, 1><<<grd, KW * 32, 0, s>>>(g, kg, op, w, v0, v0, u1, w2, st, P, tk, active);
           km_arn_ab<T, R, 2><<<grd, KW * 32, 0, s>>>(g, kg, op, w2, v0, u1, u2, w, st, P, tk, active);
-          launch_arn_b<T, 2>(g, gs, nullptr, B, active, s, 2);
-          done = true;
+          done = true;   // u3's norm from the Gram form: no closing g_arn_b<2>
         }
       }
       if (!done) {
@@ -830,8 +834,7 @@ void gmres_smooth_kron_rag(const std::vector<RagLevel<T>>& v, int nu, cudaStream
             a.uJ = (cx<T>*)L.gb.u[2];
             a.wout = (cx<T>*)L.gb.w;
           });
-          launch_arn_b_rag<T, 2>(v, false, 2, s);
-          done = true;
+          done = true;   // u3's norm from the Gram form: no closing g_arn_b<2>
         }
       }
       if (!done) {

@@ -76,3 +76,37 @@ def test_gmres_shift0_spread_inside_the_caps():
     bx, bh = pu.whole_solve_bars(dx, dh)
     assert pu.SPREAD_FACTOR * dx < pu.X_CAP and pu.SPREAD_FACTOR * dh < pu.HIST_CAP
     assert bx < 1e-7 and bh < 1e-4
+
+
+def test_last_arnoldi_norm_from_the_gram_form():
+    """The complex64 GMRES(3) steps take h_32 = |u3| without a pass over u3:
+    with unit basis vectors the modified Gram-Schmidt steps of the Arnoldi
+    process remove |h_l2|^2 from the squared norm one by one, so |u3|^2 =
+    |A v2|^2 - sum_l |h_l2|^2 exactly.  On the fine operator of a bench-like
+    problem, with the coefficients in the Gram-matrix form the kernels use
+    (and in plain MGS), the identity holds to FP64 rounding, and in float32
+    arithmetic to float rounding relative to |A v2|^2."""
+    n, k = 48, 30.0
+    h = 1.0 / n
+    A = ohier.build_hierarchy(n, n, h, k, 1 / k).A[0]
+    b = synth.point_source(n, n, h).ravel() + 1e-2 * synth.random_complex((n + 1) ** 2, 23) / h**2
+    for dt, tol in ((np.complex128, 1e-12), (np.complex64, 3e-6)):
+        Ad = A.astype(dt)
+        v = [(b / np.linalg.norm(b)).astype(dt)]
+        G = np.eye(3, dtype=dt)           # <v_i, v_l>
+        for j in range(3):
+            w = Ad @ v[j]
+            d = np.array([np.vdot(v[l], w) for l in range(j + 1)])
+            hcol = np.zeros(j + 1, dtype=dt)
+            for l in range(j + 1):        # Gram form of MGS: h_l = <v_l, w> - sum_{q<l} h_q <v_l, v_q>
+                hcol[l] = d[l] - sum(hcol[q] * G[l, q] for q in range(l))
+            u = w - sum(hcol[l] * v[l] for l in range(j + 1))
+            gram = np.vdot(w, w).real - np.sum(np.abs(hcol) ** 2)
+            exact = np.vdot(u, u).real
+            assert abs(gram - exact) <= tol * np.vdot(w, w).real, (dt, j, gram, exact)
+            if j < 2:
+                vn = u / np.linalg.norm(u)
+                for l in range(j + 1):
+                    G[j + 1, l] = np.vdot(vn, v[l])
+                    G[l, j + 1] = np.conj(G[j + 1, l])
+                v.append(vn)

@@ -25,15 +25,19 @@ def test_profile_all_kinds_then_solve(precision):
                   march=1)
     e = 16 if precision == "fp64" else 8
     nodes = (n + 1) ** 2 * B
-    expect = {0: 3 * e, 1: 3 * e, 2: 1.25 * e, 3: 2.25 * e, 4: 16 * e}
+    # what 4, a fine-level GMRES(3) step: 16 vector passes in complex128, 13
+    # in complex64 (no fourth march pass: the last Arnoldi vector's norm comes
+    # from the Gram form)
+    expect = {0: 3 * e, 1: 3 * e, 2: 1.25 * e, 3: 2.25 * e, 4: (16 if precision == "fp64" else 13) * e}
     for what, per_node in expect.items():
         ms, nbytes = s.profile(what, 0, reps=3)
         assert ms > 0
         assert abs(nbytes - per_node * nodes) <= 1e-9 * nbytes, what
-    # level 1 (Kronecker form): column marches, two of them fused in complex64
-    # (23 vector passes), the eight unfused passes in complex128 (28)
+    # level 1 (Kronecker form): column marches, two of them fused and no
+    # closing norm pass in complex64 (19 vector passes), the eight unfused
+    # passes in complex128 (28)
     ms, nbytes = s.profile(4, 1, reps=2)
-    vec1 = 28 if precision == "fp64" else 23
+    vec1 = 28 if precision == "fp64" else 19
     assert ms > 0 and abs(nbytes - vec1 * e * (n // 2 + 1) ** 2 * B) <= 1e-9 * nbytes
     rhs = torch.from_numpy(np.stack([synth.point_source(n, n, h)] * B)).cuda()
     x, st, cyc, rr = s.solve(rhs, tol=1e-8)
