@@ -279,7 +279,7 @@ mg_status mg_two_grid(mg_handle h, int nu, int max_iter, double* out);
  * reads and writes per node (complex64: three passes and the update, 13, the
  * last Arnoldi vector's norm coming from the Gram form); on a Kronecker-form
  * level with column marches in complex64, five passes with two of them
- * fused, 19; otherwise eight passes, 28; needs
+ * fused, 19; otherwise eight passes, 28 (complex64: seven, 23); needs
  * smoother = 1), 5 the last Arnoldi step of an FGMRES(m) restart cycle
  * (j = m - 1: the pass for the m MGS coefficients and the pass for the new
  * basis vector, which also writes the cycle's right-hand side and zeroes its

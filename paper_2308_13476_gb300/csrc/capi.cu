@@ -610,11 +610,12 @@ template <class T> static mg_status profile_t(mg_ctx* h, int what, int level, in
     if (level == 0) gop = op.kf ? sizeof(T) / (double)h->B : 0.0;
     else if (h->lev[level].kind <= 3) gop = opbytes - e / h->B;   // stencil without the inverse diagonal
     // fine-level row marches + update 16, complex64 13 (no M3: u3's norm from the Gram form); Kronecker column
-    // marches, complex64 (two fused passes, no closing g_arn_b<2>) 19; else 28
+    // marches, complex64 (two fused passes, no closing g_arn_b<2>) 19; else 28, complex64 23 (no g_arn_b<2>,
+    // and g_arn_a<2> stores no w)
     const bool mr = use_march(h, level);
     const bool c64 = sizeof(T) == 4;
     const int vec = (mr && h->lev[level].kind == 1) ? (c64 ? 13 : 16)
-                                                     : (mr && h->lev[level].kind >= 4 && c64) ? 19 : 28;
+                                                     : (mr && h->lev[level].kind >= 4 && c64) ? 19 : (c64 ? 23 : 28);
     *bytes = nodes * (vec * e + 4 * gop);
   }
   launch();

@@ -123,9 +123,12 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
   T* S = gstate<T>(st, rhs);
   if (S[G_BRK] != 0 || S[G_M] < J) return;   // block-uniform
   const cx<T>* uJ = J == 0 ? u0 : (J == 1 ? u1 : u2);
-  T acc[2 * (J + 1)];
+  // complex64, J = 2: |w|^2 as well, for the Gram form of u3's norm
+  // (fin_b2_gram); w is then not stored (no g_arn_b<2> pass reads it)
+  constexpr int NG = (sizeof(T) == 4 && J == 2) ? 1 : 0;
+  T acc[2 * (J + 1) + NG];
 #pragma unroll
-  for (int k = 0; k < 2 * (J + 1); ++k) acc[k] = T(0);
+  for (int k = 0; k < 2 * (J + 1) + NG; ++k) acc[k] = T(0);
   if (nv > 0) {
     const T sJ = (T)S[G_S + J];
     const cx<T>* us[3] = {u0, u1, u2};
@@ -135,7 +138,13 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
       Pack<T> a = apply_pack<T>(op, uJ + off, p, g.pitch, i0, j);
 #pragma unroll
       for (int n = 0; n < NP; ++n) a.v[n] = scl<T>(sJ, a.v[n]);
-      store_pack(w + off, p, a, nv);
+      if constexpr (NG == 1) {
+#pragma unroll
+        for (int n = 0; n < NP; ++n)
+          if (n < nv) acc[2 * (J + 1)] += abs2<T>(a.v[n]);
+      } else {
+        store_pack(w + off, p, a, nv);
+      }
 #pragma unroll
       for (int l = 0; l <= J; ++l) {
         const Pack<T> ul = load_pack(us[l] + off, p);
@@ -150,8 +159,12 @@ __global__ void __launch_bounds__(BX * BY) g_arn_a(Grid g, Op op, const cx<T>* _
       }
     }
   }
-  double v[2 * (J + 1)];
-  if (reduce_last<2 * (J + 1), T>(acc, v, sh, partial, tickets, rhs, nblk, blk)) staged<T>(S, v, [](auto* s, const double* q) { fin_a<J, T>(s, q); });
+  double v[2 * (J + 1) + NG];
+  if (reduce_last<2 * (J + 1) + NG, T>(acc, v, sh, partial, tickets, rhs, nblk, blk))
+    staged<T>(S, v, [](auto* s, const double* q) {
+      fin_a<J, T>(s, q);
+      if constexpr (NG == 1) fin_b2_gram<T>(s, q[2 * (J + 1)]);
+    });
 }
 
 // u_{J+1} = w - sum_{i<=J} h_iJ s_i u_i ; partials |u_{J+1}|^2 and <u_{J+1}, u_l>, l <= J (J < 2)
@@ -359,7 +372,8 @@ void gmres_smooth(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<T>* b,
       g_arn_a<T, Op, 1><<<grd, blk, 0, s>>>(g, op, v0, u1, u2, w, st, P, tk, active);
       g_arn_b<T, 1><<<grd, blk, 0, s>>>(g, v0, u1, u2, u2, w, st, P, tk, active, -1);
       g_arn_a<T, Op, 2><<<grd, blk, 0, s>>>(g, op, v0, u1, u2, w, st, P, tk, active);
-      g_arn_b<T, 2><<<grd, blk, 0, s>>>(g, v0, u1, u2, nullptr, w, st, P, tk, active, -1);
+      if constexpr (sizeof(T) == 8)   // complex64: u3's norm came from the Gram form in g_arn_a<2>
+        g_arn_b<T, 2><<<grd, blk, 0, s>>>(g, v0, u1, u2, nullptr, w, st, P, tk, active, -1);
       GmresBufs gs = gb;
       gs.u[0] = (void*)v0;
       if constexpr (sizeof(T) == 4) {
