@@ -144,9 +144,8 @@ typedef struct {
                        du/dn - i k u - (i/2k) d2u/dtau2 = 0, as a boundary
                        stiffness with natural corners (a variant the paper
                        does not use; coarse levels then take stored
-                       Galerkin stencils and the fine level the
-                       node-parallel kernels, whatever march says; needs
-                       precision 0 or 1; mg_gradient returns MG_EINVAL)    */
+                       Galerkin stencils; needs precision 0 or 1;
+                       mg_gradient returns MG_EINVAL)                       */
   void* stream;     /* cudaStream_t                                             */
 } mg_options;
 

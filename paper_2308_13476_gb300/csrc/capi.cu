@@ -274,7 +274,6 @@ template <class T> static cudaError_t alloc_vectors(mg_ctx* c, LevelVec<T>& v, c
 // strip, and less work leaves the GPU under-filled).
 static bool use_march(const mg_ctx* c, int l) {
   if (!c->opt.fuse || c->opt.march == 0) return false;
-  if (c->lev[l].kind == 1 && c->opt.abc == 2) return false;   // the row marches carry first-order rows only
   if (c->opt.march == 1 || c->lev[l].kind >= 4) return true;
   const Grid& g = c->lev[l].g;
   return (long long)(g.nx + 1) * (g.ny + 1) * c->B + c->peer_nodes >= (4LL << 20);

@@ -124,11 +124,15 @@ template <class T> __device__ __forceinline__ cx<T> shfl_dn1(cx<T> a) {
 // March modes: MD = 1 interior strips (branch-free stencil), MD = 2 edge
 // strips over interior rows (the same stencil, with the boundary row of
 // Op0::apply5 on columns 0 and nx and zero off the grid), MD = 0 everything
-// else (the 3-row bands; every warp on grids of fewer than 7 rows).
+// else (the 3-row bands; every warp on grids of fewer than 7 rows).  MD + 4
+// (modes 0 and 2 only): the same with the second-order absorbing rows of
+// Op0<T, true> on the boundary nodes (interior strips touch none).
+template <int MD> constexpr int MM = MD & 3;
+template <int MD> constexpr bool MA2 = (MD & 4) != 0;
 // Per-warp march context.
 template <class T, int MD> struct MCtx {
   static constexpr int NP = MNP<T>::NP;
-  Op0<T> op;
+  Op0<T, MA2<MD>> op;
   Grid g;
   int i;       // first node of this lane
   int j0, j1;  // chunk rows [j0, j1)
@@ -145,9 +149,9 @@ template <class T, int MD> struct MCtx {
       const cx<T> xe = n + 1 < NP ? c.v[n + 1 < NP ? n + 1 : 0] : east;
       const cx<T> xw = n > 0 ? c.v[n > 0 ? n - 1 : 0] : west;
       const int in = i + n;
-      if (MD != 0) {   // Op0::apply5, interior case
+      if (MM<MD> != 0) {   // Op0::apply5, interior case
         const cx<T> xn = up.v[n], xs = dn.v[n], xp = c.v[n];
-        const int ik = MD == 2 ? min(max(in, 0), op.nx) : in;   // edge strips: k of an in-grid node
+        const int ik = MM<MD> == 2 ? min(max(in, 0), op.nx) : in;   // edge strips: k of an in-grid node
         const T k = op.kf ? op.kf[m * (op.nx + 1) + ik] : op.c.k;
         const T d = fma(-k, k, T(4) * op.c.inv_h2);
         if constexpr (sizeof(T) == 4) {   // the same operations, both components per instruction
@@ -157,7 +161,7 @@ template <class T, int MD> struct MCtx {
           const T sr = (xe.x + xw.x) + (xn.x + xs.x), si = (xe.y + xw.y) + (xn.y + xs.y);
           r.v[n] = mk<T>(fma(d, xp.x, -op.c.inv_h2 * sr), fma(d, xp.y, -op.c.inv_h2 * si));
         }
-        if (MD == 2) {   // rows are interior here; columns 0 and nx take the
+        if (MM<MD> == 2) {   // rows are interior here; columns 0 and nx take the
                          // boundary row of Op0::apply5, columns off the grid zero
           const bool bcol = in == 0 || in == op.nx, inside = in >= 0 && in <= op.nx;
           if (bcol) r.v[n] = op.apply5(xp, xe, xw, xn, xs, in, m);
@@ -173,7 +177,7 @@ template <class T, int MD> struct MCtx {
   }
   // node n of the lane counts in the dots of row m
   __device__ __forceinline__ bool cnt(int n, int m) const {
-    return outl && (MD == 1 || i + n <= g.nx) && m >= j0 && m < j1;
+    return outl && (MM<MD> == 1 || i + n <= g.nx) && m >= j0 && m < j1;
   }
   __device__ __forceinline__ bool own_row(int m) const { return outl && m >= j0 && m < j1; }
 };
@@ -503,7 +507,7 @@ template <class T> struct GmA {
   const long long off = (long long)rhs * g.vstride;                           \
   const int lane = threadIdx.x & 31;                                          \
   int strip, j0, j1;                                                          \
-  mg.template map<MD>(blockIdx.x, strip, j0, j1);                             \
+  mg.template map<MM<MD>>(blockIdx.x, strip, j0, j1);                         \
   const int cs = strip * strip_w<T>() - 2;                                    \
   const int i = cs + NP * lane;                                               \
   const bool outl = NP * lane >= 2 && NP * lane + NP <= 32 * NP - 2;          \
@@ -542,13 +546,13 @@ __device__ __forceinline__ void finish(const T (&acc)[NV], double* sh, double* p
                                        int blk, const MGeo& mg, T* S, F f) {
   double v[NV];
   const int nrec = mg.nrec();
-  if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blk, mg.template rec0<MD>(), nrec))
+  if (reduce_last_at<NV, T>(acc, v, sh, partial, tickets, rhs, nrec, blk, mg.template rec0<MM<MD>>(), nrec))
     staged<T>(S, v, f);
 }
 
 // M0: u0 = b - A x; |u0|^2 and <u0, A u0>.
 template <class T, int MD>
-__device__ __forceinline__ void gm_init_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
+__device__ __forceinline__ void gm_init_body(uint3 vblk, Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ x,
                                               const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
   const uint3 blockIdx = vblk;   // the block index inside this problem's launch
@@ -571,7 +575,7 @@ __device__ __forceinline__ void gm_init_body(uint3 vblk, Grid g, MGeo mg, Op0<T>
 }
 
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ x,
+__global__ void __launch_bounds__(32) gm_init(Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ x,
                                               const cx<T>* __restrict__ b, cx<T>* __restrict__ u0, double* st,
                                               double* partial, unsigned* tickets, const int* __restrict__ active) {
   gm_init_body<T, MD>(blockIdx, g, mg, op, x, b, u0, st, partial, tickets, active);
@@ -587,7 +591,7 @@ __global__ void __launch_bounds__(32) gm_init_rag(const __grid_constant__ RagLau
 
 // M0 on a zero x: u0 = b (the caller passes b as u0 to the later passes).
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_init_zero(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ b,
+__global__ void __launch_bounds__(32) gm_init_zero(Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ b,
                                                    double* st, double* partial, unsigned* tickets,
                                                    const int* __restrict__ active) {
   MPRO
@@ -606,7 +610,7 @@ __global__ void __launch_bounds__(32) gm_init_zero(Grid g, MGeo mg, Op0<T> op, c
 
 // M1: u1 = s0 A u0 - c00 u0; |u1|^2, <u1, u0>, then <u0, A u1>, <u1, A u1>.
 template <class T, int MD>
-__device__ __forceinline__ void gm_step1_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__device__ __forceinline__ void gm_step1_body(uint3 vblk, Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ u0,
                                                cx<T>* __restrict__ u1, double* st, double* partial,
                                                unsigned* tickets, const int* __restrict__ active) {
   const uint3 blockIdx = vblk;   // the block index inside this problem's launch
@@ -634,7 +638,7 @@ __device__ __forceinline__ void gm_step1_body(uint3 vblk, Grid g, MGeo mg, Op0<T
 }
 
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__global__ void __launch_bounds__(32) gm_step1(Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ u0,
                                                cx<T>* __restrict__ u1, double* st, double* partial,
                                                unsigned* tickets, const int* __restrict__ active) {
   gm_step1_body<T, MD>(blockIdx, g, mg, op, u0, u1, st, partial, tickets, active);
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(32) gm_step1_rag(const __grid_constant__ RagLa
 // M2: u2 = s1 A u1 - c01 u0 - c11 u1; |u2|^2, <u2, u0>, <u2, u1>, then
 // <u_l, A u2> for l = 0, 1, 2.
 template <class T, int MD>
-__device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, cx<T>* __restrict__ u2, double* st,
                                                double* partial, unsigned* tickets, const int* __restrict__ active) {
   const uint3 blockIdx = vblk;   // the block index inside this problem's launch
@@ -683,7 +687,7 @@ __device__ __forceinline__ void gm_step2_body(uint3 vblk, Grid g, MGeo mg, Op0<T
 }
 
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__global__ void __launch_bounds__(32) gm_step2(Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, cx<T>* __restrict__ u2, double* st,
                                                double* partial, unsigned* tickets, const int* __restrict__ active) {
   gm_step2_body<T, MD>(blockIdx, g, mg, op, u0, u1, u2, st, partial, tickets, active);
@@ -700,7 +704,7 @@ __global__ void __launch_bounds__(32) gm_step2_rag(const __grid_constant__ RagLa
 // M3: |u3|^2 with u3 = s2 A u2 - sum_l c_l2 u_l; then the least-squares
 // solve (fin_b<2>).
 template <class T, int MD>
-__device__ __forceinline__ void gm_step3_body(uint3 vblk, Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__device__ __forceinline__ void gm_step3_body(uint3 vblk, Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
                                                double* st, double* partial, unsigned* tickets,
                                                const int* __restrict__ active) {
@@ -728,7 +732,7 @@ __device__ __forceinline__ void gm_step3_body(uint3 vblk, Grid g, MGeo mg, Op0<T
 }
 
 template <class T, int MD>
-__global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T> op, const cx<T>* __restrict__ u0,
+__global__ void __launch_bounds__(32) gm_step3(Grid g, MGeo mg, Op0<T, MA2<MD>> op, const cx<T>* __restrict__ u0,
                                                const cx<T>* __restrict__ u1, const cx<T>* __restrict__ u2,
                                                double* st, double* partial, unsigned* tickets,
                                                const int* __restrict__ active) {
@@ -818,40 +822,47 @@ void gmres_smooth_march(const Grid& g, const OpView<T>& opv, cx<T>* x, const cx<
       cudaStreamWaitEvent(s, gb.ev_join, 0);
     }
   };
-  for (int step = 0; step < nu; ++step) {
-    // a zero x: u0 = b itself (read-only in every later pass)
-    const bool z = step == 0 && gb.x_zero;
-    if (z) {
-      pass([&] { gm_init_zero<T, 1><<<gi, 32, 0, s>>>(g, mg, op, b, st, P, tk, active); },
-           [&] { gm_init_zero<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, b, st, P, tk, active); },
-           [&] { gm_init_zero<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, b, st, P, tk, active); });
-    } else {
-      pass([&] { gm_init<T, 1><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active); },
-           [&] { gm_init<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); },
-           [&] { gm_init<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, x, b, u0, st, P, tk, active); });
-    }
-    const cx<T>* v0 = z ? b : u0;
-    GmresBufs gs = gb;
-    gs.u[0] = (void*)v0;
-    pass([&] { gm_step1<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, st, P, tk, active); },
-         [&] { gm_step1<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, st, P, tk, active); },
-         [&] { gm_step1<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, st, P, tk, active); });
-    pass([&] { gm_step2<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
-         [&] { gm_step2<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
-         [&] { gm_step2<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); });
-    if constexpr (!G3<T>) {   // complex64: u3's norm came from the Gram form in M2
-      pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
-           [&] { gm_step3<T, 2><<<ge, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
-           [&] { gm_step3<T, 0><<<gbd, 32, 0, sb>>>(g, mg, op, v0, u1, u2, st, P, tk, active); });
-    }
-    if constexpr (sizeof(T) == 4) {
-      if (step == nu - 1 && gb.outer) {
-        launch_gmres_update_outer(g, x, gs, B, active, s);
-        continue;
+  // the edge-strip and band launches take the boundary operator: with the
+  // second-order absorbing rows its compile-time variant (modes 6 and 4)
+  auto body = [&](auto opb, auto a2) {
+    constexpr int ME = decltype(a2)::value ? 6 : 2, MB = decltype(a2)::value ? 4 : 0;
+    for (int step = 0; step < nu; ++step) {
+      // a zero x: u0 = b itself (read-only in every later pass)
+      const bool z = step == 0 && gb.x_zero;
+      if (z) {
+        pass([&] { gm_init_zero<T, 1><<<gi, 32, 0, s>>>(g, mg, op, b, st, P, tk, active); },
+             [&] { gm_init_zero<T, ME><<<ge, 32, 0, sb>>>(g, mg, opb, b, st, P, tk, active); },
+             [&] { gm_init_zero<T, MB><<<gbd, 32, 0, sb>>>(g, mg, opb, b, st, P, tk, active); });
+      } else {
+        pass([&] { gm_init<T, 1><<<gi, 32, 0, s>>>(g, mg, op, x, b, u0, st, P, tk, active); },
+             [&] { gm_init<T, ME><<<ge, 32, 0, sb>>>(g, mg, opb, x, b, u0, st, P, tk, active); },
+             [&] { gm_init<T, MB><<<gbd, 32, 0, sb>>>(g, mg, opb, x, b, u0, st, P, tk, active); });
       }
+      const cx<T>* v0 = z ? b : u0;
+      GmresBufs gs = gb;
+      gs.u[0] = (void*)v0;
+      pass([&] { gm_step1<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, st, P, tk, active); },
+           [&] { gm_step1<T, ME><<<ge, 32, 0, sb>>>(g, mg, opb, v0, u1, st, P, tk, active); },
+           [&] { gm_step1<T, MB><<<gbd, 32, 0, sb>>>(g, mg, opb, v0, u1, st, P, tk, active); });
+      pass([&] { gm_step2<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+           [&] { gm_step2<T, ME><<<ge, 32, 0, sb>>>(g, mg, opb, v0, u1, u2, st, P, tk, active); },
+           [&] { gm_step2<T, MB><<<gbd, 32, 0, sb>>>(g, mg, opb, v0, u1, u2, st, P, tk, active); });
+      if constexpr (!G3<T>) {   // complex64: u3's norm came from the Gram form in M2
+        pass([&] { gm_step3<T, 1><<<gi, 32, 0, s>>>(g, mg, op, v0, u1, u2, st, P, tk, active); },
+             [&] { gm_step3<T, ME><<<ge, 32, 0, sb>>>(g, mg, opb, v0, u1, u2, st, P, tk, active); },
+             [&] { gm_step3<T, MB><<<gbd, 32, 0, sb>>>(g, mg, opb, v0, u1, u2, st, P, tk, active); });
+      }
+      if constexpr (sizeof(T) == 4) {
+        if (step == nu - 1 && gb.outer) {
+          launch_gmres_update_outer(g, x, gs, B, active, s);
+          continue;
+        }
+      }
+      launch_gmres_update<T>(g, x, gs, B, active, s);
     }
-    launch_gmres_update<T>(g, x, gs, B, active, s);
-  }
+  };
+  if (opv.c0.abc2) body(Op0<T, true>{opv.c0, opv.kf, g.nx, g.ny}, std::true_type{});
+  else body(op, std::false_type{});
 }
 
 // The same smoothing steps on every problem of a ragged batch: each pass is
